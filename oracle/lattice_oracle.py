@@ -1,0 +1,454 @@
+"""Plain FP64 CPU oracle for the assembled lattice sum with defects and RHOSVD.
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product path may import or call this
+module: only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
+baseline leg use it. It shares no code with the CUDA library; the only common
+ground is the seeded workload description (block sizes, defect lists), which
+holds none of the method's arithmetic.
+
+Every function below is written from the paper (Khoromskaia & Khoromskij,
+"Tucker tensor method for fast grid-based summation of long-range potentials
+on 3D lattices with defects", arXiv 1411.1994) and cites the passage it
+follows. Where the paper is silent or garbled, the reading used is stated in
+the docstring. The code is deliberately slow and literal: explicit loops over
+lattice sites, LAPACK SVD (numpy.linalg.svd -> dgesdd) for the RHOSVD, and
+matrix products only where the definition is a contraction.
+
+Parity status: every function here is pinned by the CPU tests
+(tests/test_oracle_pins.py) to closed forms, exact identities, brute-force
+1/|x-a| sums or the paper's error bound -- except ``fit_t_scale``, whose
+optimality is not pinned (only the error it reports is, by recomputation on a
+denser r-grid).
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+SITES = 0   # a defect that replaces the charge of a box of lattice sites
+POINT = 1   # a defect that adds a charge at an arbitrary position
+
+
+# ---------------------------------------------------------------------------
+# (a0) quadrature and generating vectors, Sec. 2.1
+# ---------------------------------------------------------------------------
+
+def sinc_quadrature(R: int, sinc_step: float, t_scale: float) -> Tuple[np.ndarray, np.ndarray]:
+    """Nodes t_q and weights w_q of the rank-R separable expansion of 1/r.
+
+    Sec. 2.1, Eqs. (laplace), (hM), (sinc_Newt): 1/r = (2/sqrt(pi)) int_0^inf
+    exp(-r^2 t^2) dt, discretised by a sinc rule with nodes on a uniform
+    u-grid. Reading (the printed rule t_k = k h_M does not converge over the
+    needed range of r): substitute t = sinh(u)/s, whose integrand
+    cosh(u)/s * exp(-r^2 sinh(u)^2 / s^2) is even in u, take the sinc rule
+    u_k = k*h, k = -M..M, and merge the equal +k and -k terms. That leaves
+    R = M + 1 distinct Gaussians, q = 0..R-1:
+        t_q = sinh(q h) / s,
+        w_0 = h / (s sqrt(pi)),  w_q = 2 h cosh(q h) / (s sqrt(pi))  (q >= 1).
+    """
+    q = np.arange(R, dtype=np.float64)
+    u = q * sinc_step
+    t = np.sinh(u) / t_scale
+    w = 2.0 * sinc_step * np.cosh(u) / (t_scale * math.sqrt(math.pi))
+    w[0] = sinc_step / (t_scale * math.sqrt(math.pi))
+    return t, w
+
+
+def quadrature_rel_error(t: np.ndarray, w: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """|r * sum_q w_q exp(-t_q^2 r^2) - 1|: relative error of the separable
+    expansion of 1/r at distances r (Sec. 2.1, Eq. sinc_conv)."""
+    r = np.asarray(r, dtype=np.float64)
+    s = np.exp(-np.outer(r * r, t * t)) @ w
+    return np.abs(r * s - 1.0)
+
+
+def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float,
+                n_r: int = 600) -> Tuple[float, float]:
+    """Scale s of the substitution t = sinh(u)/s that minimises the maximum
+    relative error of the expansion over [r_min, r_max] (Sec. 2.1: M, and here
+    s, are chosen so that the kernel is reproduced to a tolerance; the paper's
+    C_0 plays the role of s). Coarse log-scan then golden-section refinement.
+    Returns (s, max relative error on the fitting grid)."""
+    r = np.geomspace(r_min, r_max, n_r)
+
+    def err(log_s):
+        t, w = sinc_quadrature(R, sinc_step, math.exp(log_s))
+        return float(np.max(quadrature_rel_error(t, w, r)))
+
+    grid = np.linspace(math.log(1e-2), math.log(1e5), 241)
+    vals = [err(x) for x in grid]
+    i = int(np.argmin(vals))
+    a, b = grid[max(i - 1, 0)], grid[min(i + 1, len(grid) - 1)]
+    gr = (math.sqrt(5.0) - 1.0) / 2.0
+    c, d = b - gr * (b - a), a + gr * (b - a)
+    fc, fd = err(c), err(d)
+    for _ in range(60):
+        if fc < fd:
+            b, d, fd = d, c, fc
+            c = b - gr * (b - a)
+            fc = err(c)
+        else:
+            a, c, fc = c, d, fd
+            d = a + gr * (b - a)
+            fd = err(d)
+    x = 0.5 * (a + b)
+    return math.exp(x), err(x)
+
+
+def mesh_size(N: int, box_lo: float, box_hi: float) -> float:
+    """h = b/n for the uniform grid on the box (Sec. 2.1)."""
+    return (box_hi - box_lo) / N
+
+
+def cell_centres(N: int, box_lo: float, box_hi: float) -> np.ndarray:
+    """Collocation points x_i = box_lo + (i + 1/2) h, i = 0..N-1 (reading:
+    cell-centred collocation instead of the Galerkin integral of Eq. galten)."""
+    h = mesh_size(N, box_lo, box_hi)
+    return box_lo + (np.arange(N, dtype=np.float64) + 0.5) * h
+
+
+def snap(pos: float, N: int, box_lo: float, box_hi: float) -> int:
+    """Vertex index m of the grid vertex nearest to ``pos`` (vertex m sits at
+    box_lo + m h). Sec. 3.1 places each centre on a grid point and allows
+    off-grid centres with O(h) error (footnote to Eq. sub_tens); reading: snap
+    to the nearest vertex, so that no collocation point coincides with a
+    centre."""
+    h = mesh_size(N, box_lo, box_hi)
+    m = math.floor((pos - box_lo) / h + 0.5)
+    if m < 0 or m > N:
+        raise ValueError(f"centre {pos} outside the box")
+    return int(m)
+
+
+def generating_vectors(N: int, box_lo: float, box_hi: float,
+                       t: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """Canonical vectors of the reference tensor on the doubled grid,
+    Eq. (master_pot): p_q[j] = w_q^(1/3) exp(-t_q^2 xt_j^2) on the 2N cell
+    centres xt_j = (j - N + 1/2) h of [-b, b] (collocation reading). The same
+    vectors serve all three modes (Eq. sinc_general). Shape (R, 2N)."""
+    h = mesh_size(N, box_lo, box_hi)
+    xt = (np.arange(2 * N, dtype=np.float64) - N + 0.5) * h
+    return np.cbrt(w)[:, None] * np.exp(-np.outer(t * t, xt * xt))
+
+
+def window(gq: np.ndarray, m: int, N: int) -> np.ndarray:
+    """Shift-and-window operator W_m of Eq. (sub_tens) applied to one doubled-
+    grid vector: the restriction to the box of the reference vector centred on
+    vertex m, (W_m g)[i] = g[i - m + N], i = 0..N-1. (The printed index range
+    i+n/2 : i+3n/2 has n+1 entries; this is the reading for a centre at a
+    vertex and cell-centred collocation.)"""
+    return gq[N - m: 2 * N - m].copy()
+
+
+# ---------------------------------------------------------------------------
+# (a) assembled lattice sum, Thm 3.1(A); (b) defects, Sec. 4.1 and 4.4
+# ---------------------------------------------------------------------------
+
+def block_vertex_indices(block, N: int, box_lo: float, box_hi: float) -> List[List[int]]:
+    """Per mode, the vertex index of every lattice site of a rectangular block
+    (site k at origin + k * spacing, snapped)."""
+    out = []
+    for a in range(3):
+        out.append([snap(block.origin[a] + k * block.spacing[a], N, box_lo, box_hi)
+                    for k in range(block.L[a])])
+    return out
+
+
+def assembled_vector(gq: np.ndarray, ms: Sequence[int], N: int) -> np.ndarray:
+    """sum_k W_{m_k} g_q, one 1D sum per mode and rank index (Thm 3.1(A),
+    Eq. EwaldTensorGl), by an explicit loop over the sites."""
+    v = np.zeros(N)
+    for m in ms:
+        v += window(gq, m, N)
+    return v
+
+
+def defect_charge(defect, blocks) -> float:
+    """Weight xi of a defect term: a SITES defect replaces the block's charge
+    by ``defect.charge`` (vacancy: 0, so xi = -Z; impurity Z': xi = Z' - Z),
+    Eq. (Can_LatticeSum_full); a POINT defect adds its charge."""
+    if defect.kind == SITES:
+        return defect.charge - blocks[defect.block].charge
+    return defect.charge
+
+
+def canonical_terms(N, box_lo, box_hi, g, blocks, defects):
+    """All canonical terms of the defected lattice sum, deduplicated by window.
+
+    Sec. 4.1, Eq. (Can_LatticeSum_full): P_hat = P_0 + sum_s P_s, where P_0 is
+    the assembled rank-R sum of each rectangular block (Thm 3.1(A); a union of
+    blocks is class (A) of Sec. 4.4) and each defect P_s is a shifted rank-R
+    reference tensor scaled by its charge change (a cluster of sites sums its
+    windows per mode, class (D)). Returns
+
+      cols : 3 arrays (C_l, N) -- distinct canonical vectors per mode (each
+             block's assembled vectors, then one vector per distinct defect
+             window set and rank index),
+      tcol : (T, 3) int -- the column of each term in each mode,
+      xi   : (T,) float -- the weight of each term (charges, not yet
+             including the vector norms).
+
+    Terms are ordered block-major then defect-major, rank index q fastest.
+    """
+    R = g.shape[0]
+    nb = len(blocks)
+    bidx = [block_vertex_indices(b, N, box_lo, box_hi) for b in blocks]
+    cols = [[] for _ in range(3)]
+    keys = [dict() for _ in range(3)]
+    tcol, xi = [], []
+    for bi, b in enumerate(blocks):
+        for q in range(R):
+            for a in range(3):
+                cols[a].append(assembled_vector(g[q], bidx[bi][a], N))
+            tcol.append([bi * R + q] * 3)
+            xi.append(b.charge)
+
+    def defect_windows(d, a):
+        if d.kind == SITES:
+            return tuple(bidx[d.block][a][d.site[a] + e] for e in range(d.extent[a]))
+        return (snap(d.pos[a], N, box_lo, box_hi),)
+
+    for d in defects:
+        base = []
+        for a in range(3):
+            key = defect_windows(d, a)
+            if key not in keys[a]:
+                keys[a][key] = len(keys[a])
+                for q in range(R):
+                    cols[a].append(assembled_vector(g[q], key, N))
+            base.append(nb * R + keys[a][key] * R)
+        z = defect_charge(d, blocks)
+        for q in range(R):
+            tcol.append([base[0] + q, base[1] + q, base[2] + q])
+            xi.append(z)
+    return ([np.array(c) for c in cols], np.array(tcol, dtype=np.int64),
+            np.array(xi, dtype=np.float64))
+
+
+def explicit_terms(cols, tcol, xi):
+    """The same terms with one explicit vector per term and mode (no sharing):
+    the paper's concatenated side matrices, Eq. (SideMTuckS)."""
+    return [cols[a][tcol[:, a]] for a in range(3)], np.arange(len(xi))[:, None].repeat(3, 1), xi
+
+
+# ---------------------------------------------------------------------------
+# full-tensor and brute-force references (Thm 3.1 proof; Eq. EwaldSumE)
+# ---------------------------------------------------------------------------
+
+def full_tensor_sitewise(N, box_lo, box_hi, g, blocks, defects) -> np.ndarray:
+    """The full N^3 tensor sum_sites Z_s W_s P_R, built site by site as in the
+    first line of the proof of Thm 3.1 (Eq. fullsum before the 1D
+    reduction): every charged site contributes its own shifted rank-R
+    reference tensor. Small N only."""
+    R = g.shape[0]
+    charges = {}
+    for bi, b in enumerate(blocks):
+        idx = block_vertex_indices(b, N, box_lo, box_hi)
+        for k1 in range(b.L[0]):
+            for k2 in range(b.L[1]):
+                for k3 in range(b.L[2]):
+                    key = (idx[0][k1], idx[1][k2], idx[2][k3])
+                    charges[key] = charges.get(key, 0.0) + b.charge
+    for d in defects:
+        if d.kind == SITES:
+            b = blocks[d.block]
+            idx = block_vertex_indices(b, N, box_lo, box_hi)
+            for e1 in range(d.extent[0]):
+                for e2 in range(d.extent[1]):
+                    for e3 in range(d.extent[2]):
+                        key = (idx[0][d.site[0] + e1], idx[1][d.site[1] + e2],
+                               idx[2][d.site[2] + e3])
+                        charges[key] = charges.get(key, 0.0) + d.charge - b.charge
+        else:
+            key = tuple(snap(d.pos[a], N, box_lo, box_hi) for a in range(3))
+            charges[key] = charges.get(key, 0.0) + d.charge
+    T = np.zeros((N, N, N))
+    for (m1, m2, m3), z in charges.items():
+        if z == 0.0:
+            continue
+        for q in range(R):
+            T += z * np.einsum("i,j,k->ijk", window(g[q], m1, N), window(g[q], m2, N),
+                               window(g[q], m3, N))
+    return T
+
+
+def charged_centres(N, box_lo, box_hi, blocks, defects):
+    """(positions (K,3), charges (K,)) of all net charges, at their snapped
+    vertex positions: the centres a_nu and charges Z_nu of Eq. (EwaldSumE)
+    with the defects applied."""
+    h = mesh_size(N, box_lo, box_hi)
+    charges = {}
+    for b in blocks:
+        idx = block_vertex_indices(b, N, box_lo, box_hi)
+        for k1 in range(b.L[0]):
+            for k2 in range(b.L[1]):
+                for k3 in range(b.L[2]):
+                    key = (idx[0][k1], idx[1][k2], idx[2][k3])
+                    charges[key] = charges.get(key, 0.0) + b.charge
+    for d in defects:
+        if d.kind == SITES:
+            b = blocks[d.block]
+            idx = block_vertex_indices(b, N, box_lo, box_hi)
+            for e1 in range(d.extent[0]):
+                for e2 in range(d.extent[1]):
+                    for e3 in range(d.extent[2]):
+                        key = (idx[0][d.site[0] + e1], idx[1][d.site[1] + e2],
+                               idx[2][d.site[2] + e3])
+                        charges[key] = charges.get(key, 0.0) + d.charge - b.charge
+        else:
+            key = tuple(snap(d.pos[a], N, box_lo, box_hi) for a in range(3))
+            charges[key] = charges.get(key, 0.0) + d.charge
+    keys = [k for k, z in charges.items() if z != 0.0]
+    pos = box_lo + h * np.array(keys, dtype=np.float64).reshape(-1, 3)
+    z = np.array([charges[k] for k in keys], dtype=np.float64)
+    return pos, z
+
+
+def brute_force(points: np.ndarray, centres: np.ndarray, charges: np.ndarray):
+    """Direct sum sum_nu Z_nu / |x - a_nu| (Eq. EwaldSumE with p = 1/r) at the
+    given points; also returns sum_nu |Z_nu| / |x - a_nu| and the minimum and
+    maximum distance to a centre, which bound the quadrature error."""
+    points = np.atleast_2d(points)
+    val = np.zeros(len(points))
+    absval = np.zeros(len(points))
+    dmin = np.full(len(points), np.inf)
+    dmax = np.zeros(len(points))
+    for c0 in range(0, len(centres), 256):
+        c = centres[c0:c0 + 256]
+        d = np.sqrt(((points[:, None, :] - c[None, :, :]) ** 2).sum(-1))
+        val += (charges[c0:c0 + 256] / d).sum(1)
+        absval += (np.abs(charges[c0:c0 + 256]) / d).sum(1)
+        dmin = np.minimum(dmin, d.min(1))
+        dmax = np.maximum(dmax, d.max(1))
+    return val, absval, dmin, dmax
+
+
+# ---------------------------------------------------------------------------
+# (c) RHOSVD, Def. 4.1, Thm A.1, Sec. 4.3 (Eq. SideMTuckS)
+# ---------------------------------------------------------------------------
+
+def truncation_rank(sigma: np.ndarray, eps: float) -> int:
+    """Smallest r with (sum_{k>r} sigma_k^2)^(1/2) <= eps (sum_k sigma_k^2)^(1/2).
+    Sec. 4.3 lets a threshold eps replace the fixed rank; reading: relative
+    Frobenius norm of the (column-normalised) side matrix, per mode."""
+    s2 = np.asarray(sigma, dtype=np.float64) ** 2
+    tail = np.concatenate([np.cumsum(s2[::-1])[::-1], [0.0]])   # tail[r] = sum_{k>=r}
+    total = tail[0]
+    for r in range(len(s2) + 1):
+        if math.sqrt(tail[r]) <= eps * math.sqrt(total):
+            return max(r, 1) if len(s2) else 0
+    return len(s2)
+
+
+def normalise_terms(cols, tcol, xi):
+    """Eq. (CP_form): canonical vectors of unit length, the norms moved into
+    the weights xi_nu. Returns (normalised cols, norms, xi)."""
+    norms = [np.sqrt((c * c).sum(1)) for c in cols]
+    xin = xi.copy()
+    for a in range(3):
+        xin = xin * norms[a][tcol[:, a]]
+    ncols = [cols[a] / norms[a][:, None] for a in range(3)]
+    return ncols, norms, xin
+
+
+def rhosvd(cols, tcol, xi, eps, ranks=None, core=True):
+    """Reduced HOSVD of the canonical tensor sum_nu xi_nu a1 (x) a2 (x) a3.
+
+    Def. 4.1 and Thm A.1(c),(d): for each mode, the SVD of the side matrix
+    A^(l) (columns = the normalised canonical vectors of every term, Eq.
+    SideMTuckS), Z_l = the leading r_l left singular vectors; the core is the
+    projection mu = sum_nu xi_nu (Z1^T a1_nu) (x) (Z2^T a2_nu) (x) (Z3^T a3_nu).
+
+    ``cols`` may hold each distinct vector once (``tcol`` maps terms to
+    columns). The side matrix with repeated columns has A A^T = sum_c count_c
+    a_c a_c^T, so its left singular vectors and values are those of the
+    distinct columns scaled by sqrt(count) -- an identity, not an
+    approximation (pinned in the tests against the explicit side matrix).
+
+    Returns a dict: Z (3 x (N, r_l)), sigma (3 arrays), r, d (discarded
+    (sum_{k>r} sigma^2)^(1/2) per mode), xi (normalised weights), P (3 x
+    (r_l, C_l)), B (r1, r2, r3) core, bound = ||xi||_2 * sum_l d_l (Thm A.1(d)).
+    ``ranks`` forces the ranks instead of the eps rule.
+    """
+    ncols, norms, xin = normalise_terms(cols, tcol, xi)
+    out = {"Z": [], "sigma": [], "r": [], "d": [], "P": [], "xi": xin, "norms": norms}
+    for a in range(3):
+        count = np.bincount(tcol[:, a], minlength=len(ncols[a])).astype(np.float64)
+        Aw = (ncols[a] * np.sqrt(count)[:, None]).T          # (N, C) weighted side matrix
+        U, S, _ = np.linalg.svd(Aw, full_matrices=False)
+        r = truncation_rank(S, eps) if ranks is None else int(ranks[a])
+        Z = U[:, :r]
+        out["Z"].append(Z)
+        out["sigma"].append(S)
+        out["r"].append(r)
+        out["d"].append(math.sqrt(float(np.sum(S[r:] ** 2))))
+        out["P"].append(Z.T @ ncols[a].T)                  # (r, C): Z^T a_c
+    out["bound"] = float(np.linalg.norm(xin)) * sum(out["d"])
+    if core:
+        out["B"] = core_tensor(out["P"], tcol, xin)
+    return out
+
+
+def core_tensor(P, tcol, xi, chunk=512) -> np.ndarray:
+    """mu[i,j,k] = sum_nu xi_nu P1[i,c1(nu)] P2[j,c2(nu)] P3[k,c3(nu)]
+    (Thm A.1(c), core in canonical form), summed in chunks of terms."""
+    r1, r2, r3 = P[0].shape[0], P[1].shape[0], P[2].shape[0]
+    B = np.zeros((r1, r2 * r3))
+    for s in range(0, len(xi), chunk):
+        sl = slice(s, s + chunk)
+        p1 = P[0][:, tcol[sl, 0]] * xi[sl]
+        kr = (P[1][:, None, tcol[sl, 1]] * P[2][None, :, tcol[sl, 2]]).reshape(r2 * r3, -1)
+        B += p1 @ kr.T
+    return B.reshape(r1, r2, r3)
+
+
+# ---------------------------------------------------------------------------
+# (d) evaluation on slabs (n-mode products, Eq. Tucker_singePot)
+# ---------------------------------------------------------------------------
+
+def tucker_slab(Z, B, i3: int) -> np.ndarray:
+    """Values of the Tucker tensor B x1 Z1 x2 Z2 x3 Z3 on the slab i3
+    (Eq. Tucker_singePot): (B x3 Z3[i3,:]) then Z1 M Z2^T. Shape (N, N),
+    first index = mode 1."""
+    M = B @ Z[2][i3]                 # (r1, r2)
+    return Z[0] @ M @ Z[1].T
+
+
+def canonical_slab(cols, tcol, xi, i3: int) -> np.ndarray:
+    """Values of the untruncated canonical tensor sum_nu xi_nu a1 (x) a2 (x) a3
+    on the slab i3: A1 diag(xi * a3[i3]) A2^T (Eq. CP_form)."""
+    w = xi * cols[2][tcol[:, 2], i3]
+    return (cols[0][tcol[:, 0]].T * w) @ cols[1][tcol[:, 1]]
+
+
+def full_from_tucker(Z, B) -> np.ndarray:
+    """The full tensor B x1 Z1 x2 Z2 x3 Z3 (small N only)."""
+    return np.einsum("abc,ia,jb,kc->ijk", B, Z[0], Z[1], Z[2], optimize=True)
+
+
+def full_from_canonical(cols, tcol, xi) -> np.ndarray:
+    """The full tensor sum_nu xi_nu a1 (x) a2 (x) a3 (small N only)."""
+    return np.einsum("n,ni,nj,nk->ijk", xi, cols[0][tcol[:, 0]], cols[1][tcol[:, 1]],
+                     cols[2][tcol[:, 2]], optimize=True)
+
+
+# ---------------------------------------------------------------------------
+# whole pipeline (a) + (b) + (c), as timed for the CPU baseline
+# ---------------------------------------------------------------------------
+
+def pipeline(wl, t_scale: float, core: bool = True, ranks=None):
+    """Quadrature -> generating vectors -> assembled and defect terms ->
+    RHOSVD, for a workload description (N, box, R, sinc step, blocks,
+    defects, eps). Returns (terms, rhosvd result)."""
+    t, w = sinc_quadrature(wl.R, wl.sinc_step, t_scale)
+    g = generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w)
+    cols, tcol, xi = canonical_terms(wl.N, wl.box_lo, wl.box_hi, g, wl.blocks, wl.defects)
+    res = rhosvd(cols, tcol, xi, wl.eps, ranks=ranks, core=core)
+    return {"t": t, "w": w, "g": g, "cols": cols, "tcol": tcol, "xi": xi}, res
+
+
+def default_r_max(wl) -> float:
+    """Largest centre-to-point distance inside the cubic box: sqrt(3) b."""
+    return math.sqrt(3.0) * (wl.box_hi - wl.box_lo)
