@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Throughput of the lattice-sum hot path on GB300: lattice potentials summed
+per second, one step = create (reference vectors + assembled lattice sums) +
+add_defects + rhosvd_reduce on one seeded synthetic workload (default: the
+16^3 lattice, N = 1024, R = 24, 5% vacancies + 2% impurities, eps = 1e-6).
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1411_1994_gb300 import workloads as W  # noqa: E402
+
+METRIC = "lattice potentials summed/s (build+RHOSVD)"
+FP64_PEAK_TFLOPS_DERIVED = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk x flops x max clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(name):
+    return {"c1": W.config1, "c2": W.config2, "c3": W.config3}[name]()
+
+
+def config_of(wl, args, extra=None):
+    cfg = {"workload": wl.name, "N": wl.N, "R": wl.R, "eps": wl.eps, "sites": wl.n_sites,
+           "defects": len(wl.defects), "units_per_step": wl.units, "box": [wl.box_lo, wl.box_hi],
+           "path": args.precision, "l2": "flushed between steps (512 MB write outside the per-step events)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_step(wl, s):
+    from oracle import lattice_oracle as O
+    O.pipeline(wl, s, core=True)
+
+
+def time_oracle(wl, budget_s, min_steps=1):
+    from oracle import lattice_oracle as O
+    s, _ = O.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, O.default_r_max(wl))
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while len(times) < min_steps or time.perf_counter() < t_end:
+        t0 = time.perf_counter()
+        oracle_step(wl, s)
+        times.append(time.perf_counter() - t0)
+        if len(times) >= 50:
+            break
+    return times
+
+
+def cores_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = workload(args.workload)
+    from oracle import lattice_oracle as O
+    s, _ = O.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, O.default_r_max(wl))
+    for _ in range(args.warmup):
+        oracle_step(wl, s)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(wl, s)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = wl.units / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "potentials/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": config_of(wl, args, {"l2": "n/a (CPU)"}),
+            "cpu_baseline": {"value": value, "unit": "potentials/s", "cores": cores_used(), "kind": "oracle",
+                             "sample": f"{args.steps} full oracle pipelines of {wl.name} "
+                                       "(quadrature, per-site window sums, dgesdd RHOSVD, core einsum)"},
+            "e2e": {"value": value, "unit": "potentials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for ln in f:
+                    p = [x.strip() for x in ln.split(",")]
+                    if len(p) >= 9:
+                        rows.append(p)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        loaded = [x for x in sm if mx and x >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# roofline of the dominant step
+# ---------------------------------------------------------------------------
+
+def step_flops(name, info, N, nslab=0):
+    C, r, T = info["C"], info["r"], info["T"]
+    if name == "gram":
+        return sum(2.0 * N * c * c for c in C)
+    if name == "basis":
+        return sum(2.0 * N * C[a] * r[a] for a in range(3))
+    if name == "cholqr2":
+        return sum(2 * (2.0 * N * r[a] ** 2 + r[a] ** 3 / 3.0 + 1.0 * N * r[a] ** 2) for a in range(3))
+    if name == "project":
+        return sum(2.0 * N * r[a] * C[a] for a in range(3))
+    if name == "core":
+        return 2.0 * r[0] * r[1] * r[2] * T
+    return None
+
+
+def roofline(report, info, N, steps, precision, peaks):
+    st = report.get("steps", {})
+    if not st:
+        return None, None
+    name = max(st, key=lambda k: st[k]["ms"])
+    ms_launch = st[name]["ms"] / max(st[name]["launches"], 1)
+    fl = step_flops(name, info, N)
+    per_launch_units = st[name]["launches"] / max(steps, 1)   # launches of this step per pipeline step
+    out = {"kernel": name, "ms_per_launch": ms_launch}
+    if fl is None:
+        out.update({"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                    "traffic": None, "note": "iterative step, time only"})
+        return out, name
+    fl_launch = fl / per_launch_units
+    achieved = fl_launch / (ms_launch * 1e-3) / 1e12
+    if precision == "fp64" or name in ("gram", "basis", "cholqr2"):
+        peak = FP64_PEAK_TFLOPS_DERIVED
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64, CUDA cores)"})
+    else:
+        peak = peaks.get("bf16_tflops")
+        out.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak if peak else None, "traffic": None,
+                    "peak_source": "of measured bf16 burst (MEASURED_PEAKS.json); BF16x3 passes counted as overhead"})
+    return out, name
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_1411_1994_gb300 import build as B
+    from paper_1411_1994_gb300 import lattice_sum as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    wl = workload(args.workload)
+    prec = L.LS_MIXED if args.precision == "mixed" else L.LS_FP64
+    s, _ = L.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, math.sqrt(3.0) * (wl.box_hi - wl.box_lo))
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+
+    def step():
+        ls = L.LatticeSum.from_workload(wl, s, prec, stream=stream.cuda_stream)
+        ls.add_defects(wl.defects)
+        info = ls.rhosvd_reduce(wl.eps)
+        ls.close()
+        return info
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            info = step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    L.profile(True)
+    clocks.start()
+    t_wall = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            info = step()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    L.profile(False)
+    report = L.profile_report()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * wl.units / (ms_per_step / 1e3)
+    roof, dom = roofline(report, info, wl.N, args.steps, args.precision, peaks)
+
+    # end to end through the public API: host inputs in, Tucker factors out
+    e2e_times = []
+    h2d = d2h = 0
+    L.profile(True)
+    for k in range(max(3, args.steps // 2)):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ls = L.LatticeSum.from_workload(wl, s, prec, stream=stream.cuda_stream)
+        ls.add_defects(wl.defects)
+        ls.rhosvd_reduce(wl.eps)
+        for a in range(3):
+            ls.read(L.LS_READ_BASIS, a)
+        ls.read(L.LS_READ_CORE)
+        ls.close()
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    L.profile(False)
+    rep2 = L.profile_report()
+    n_e2e = len(e2e_times)
+    h2d = rep2["h2d_bytes"] // n_e2e
+    d2h = rep2["d2h_bytes"] // n_e2e
+    e2e_value = world * wl.units / (sum(e2e_times) / n_e2e)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        times = time_oracle(wl, args.cpu_seconds)
+        cpu = {"value": wl.units / statistics.mean(times), "unit": "potentials/s", "cores": cores_used(),
+               "kind": "oracle",
+               "sample": f"{len(times)} full oracle pipelines of {wl.name} on the host cores "
+                         f"(mean {statistics.mean(times):.2f} s each)"}
+    line = {
+        "metric": METRIC + f", {args.precision} path", "value": value, "unit": "potentials/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x3+f64",
+        "data": "synthetic (seeded)", "config": config_of(wl, args, {"parallelism": f"replicas x{world}",
+                                                                     "ranks": info["r"], "columns": info["C"],
+                                                                     "terms": info["T"],
+                                                                     "jacobi_sweeps": info["sweeps"]}),
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "potentials/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(report.get("kernel_launches", 0)),
+        "clocks": clk,
+        "steps_ms": {k: v["ms"] / args.steps for k, v in report.get("steps", {}).items()},
+        "wall_s_timed_region": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,253 @@
+/*
+ * lattice_sum.h -- C ABI of the GB300 (sm_103a) lattice-sum library.
+ *
+ * Grid-based summation of Newton potentials 1/|x - a| over 3D lattices with
+ * defects in canonical / Tucker tensor form, after Khoromskaia & Khoromskij,
+ * "Tucker tensor method for fast grid-based summation of long-range
+ * potentials on 3D lattices with defects" (arXiv 1411.1994):
+ *
+ *   lattice_sum_create        -- Sec. 3.2, Thm 3.1(A), Eq. (EwaldTensorGl):
+ *                                reference canonical vectors on the doubled
+ *                                grid (Eq. master_pot) and their 1D shift-sums
+ *                                over the sites of each rectangular block;
+ *   lattice_sum_add_defects   -- Sec. 4.1, Eq. (Can_LatticeSum_full), and
+ *                                Sec. 4.4 classes (A)/(D): vacancies,
+ *                                impurities, clusters and off-lattice charges
+ *                                appended as shifted rank-R canonical terms;
+ *   lattice_sum_rhosvd_reduce -- Def. 4.1, Sec. 4.3 (Eq. SideMTuckS, an eps
+ *                                threshold instead of a fixed rank) and
+ *                                Thm A.1(c),(d): orthogonalise the side
+ *                                matrices, truncate by discarded singular
+ *                                values, project, contract the Tucker core;
+ *   lattice_sum_eval_slab     -- Eq. (Tucker_singePot): values of the Tucker
+ *                                tensor on z-slabs by n-mode products.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Cubic box [box_lo, box_hi]^3 with an N^3 grid, mesh h = (box_hi -
+ *    box_lo) / N. Collocation points are cell centres x_i = box_lo + (i+1/2)h;
+ *    charges sit on grid vertices box_lo + m h, m in [0, N] (a site is
+ *    snapped to the nearest vertex, m = floor((pos - box_lo)/h + 1/2)).
+ *  - Reference vectors live on the doubled grid: g_q[j] = w_q^(1/3)
+ *    exp(-t_q^2 ((j - N + 1/2) h)^2), j = 0..2N-1, with the sinc nodes
+ *    t_q = sinh(q s_h)/t_scale, w_0 = s_h/(t_scale sqrt(pi)),
+ *    w_q = 2 s_h cosh(q s_h)/(t_scale sqrt(pi)), q = 0..R-1 (s_h = sinc_step).
+ *  - A window of a centre at vertex m is (W_m g_q)[i] = g_q[i - m + N].
+ *  - Return value: LS_OK (0) or a negative LS_ERR_* code; the message is
+ *    available from lattice_sum_last_error(ctx). A call made in the wrong
+ *    order returns LS_ERR_STATE and changes nothing.
+ *  - Ownership: the library owns every device buffer it allocates (reference
+ *    vectors, side matrices, Tucker factors); they live until
+ *    lattice_sum_destroy. Host inputs are read during the call only.
+ *  - Streams: all device work is enqueued on the stream given to
+ *    lattice_sum_create (a cudaStream_t passed as void*; NULL = legacy
+ *    default stream). Calls return without waiting for the device, except
+ *    lattice_sum_rhosvd_reduce (which reads the truncation ranks back) and
+ *    lattice_sum_read (a synchronous copy to host memory).
+ *  - Every kernel is hand-written for sm_103a; there is no CPU fallback. If
+ *    no usable GPU is present the calls return LS_ERR_CUDA.
+ */
+#ifndef LATTICE_SUM_H
+#define LATTICE_SUM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LS_OK               0
+#define LS_ERR_ARG         -1   /* invalid argument (sizes, pointers, ranges) */
+#define LS_ERR_OOM         -2   /* device allocation failed                    */
+#define LS_ERR_CUDA        -3   /* a CUDA call or kernel launch failed         */
+#define LS_ERR_NOCONVERGE  -4   /* the eigen-solver hit its sweep limit        */
+#define LS_ERR_STATE       -5   /* call out of order                           */
+#define LS_ERR_TIMEOUT     -6   /* a bounded device-side wait gave up          */
+
+/* arithmetic of the reduction and evaluation steps */
+#define LS_FP64   0   /* every step in FP64 (CUDA-core DFMA)                         */
+#define LS_MIXED  1   /* FP64 shift-sums, Gram, eigen-solver and CholeskyQR2;          */
+                      /* projection, core contraction and slab evaluation on tcgen05    */
+                      /* tensor cores as BF16x3 split products with FP32 accumulation   */
+
+/* defect kinds */
+#define LS_DEFECT_SITES 0  /* sites block[site : site+extent) get charge `charge`     */
+                           /* (0 = vacancy, Z' = impurity; extent 3,3,3 = a cluster)   */
+#define LS_DEFECT_POINT 1  /* an extra charge `charge` at position `pos` (off-lattice) */
+
+/* output types of lattice_sum_eval_slab */
+#define LS_OUT_F64 0
+#define LS_OUT_F32 1
+
+/* what lattice_sum_read copies */
+#define LS_READ_GENVEC   0  /* double [R][2N]  reference vectors g_q                    */
+#define LS_READ_COLUMNS  1  /* double [C_l][N] canonical vectors of mode l (unit length */
+                            /*                 after rhosvd_reduce, raw before)          */
+#define LS_READ_NORMS    2  /* double [C_l]    norms of the raw canonical vectors        */
+#define LS_READ_TERMS    3  /* int32  [T][3]   column of each term in each mode          */
+#define LS_READ_XI       4  /* double [T]      term weights (charges; after reduce: the  */
+                            /*                 charges times the three vector norms)     */
+#define LS_READ_SIGMA    5  /* double [C_l]    singular values of mode l, descending     */
+#define LS_READ_BASIS    6  /* double [r_l][N] orthonormal Tucker vectors of mode l      */
+#define LS_READ_PROJ     7  /* double [r_l][C_l] projections Z_l^T a_c                   */
+#define LS_READ_CORE     8  /* double [r1][r2][r3] Tucker core (r3 fastest)              */
+
+typedef struct ls_ctx ls_ctx;
+
+typedef struct {
+    int64_t N;          /* grid points per axis of the box (>= 2)                       */
+    double  box_lo;     /* box [box_lo, box_hi] on every axis                           */
+    double  box_hi;
+    int32_t R;          /* canonical rank of the reference tensor (1..64)               */
+    double  sinc_step;  /* sinc quadrature step s_h (> 0)                                */
+    double  t_scale;    /* substitution scale s in t = sinh(u)/s (> 0); see             */
+                        /* lattice_sum_fit_t_scale                                       */
+    int32_t precision;  /* LS_FP64 or LS_MIXED                                           */
+    int32_t flags;      /* reserved, must be 0                                           */
+} ls_params;
+
+typedef struct {
+    int64_t L[3];        /* sites per axis (>= 1)                                        */
+    double  origin[3];   /* position of site (0,0,0)                                     */
+    double  spacing[3];  /* site spacing per axis                                        */
+    double  charge;      /* charge of every site                                         */
+} ls_block;
+
+typedef struct {
+    int32_t kind;        /* LS_DEFECT_SITES or LS_DEFECT_POINT                           */
+    int32_t block;       /* block index (SITES)                                          */
+    int64_t site[3];     /* first site (SITES)                                           */
+    int64_t extent[3];   /* sites per axis (SITES; >= 1)                                 */
+    double  pos[3];      /* position (POINT)                                             */
+    double  charge;      /* new charge of the sites (SITES) / added charge (POINT)       */
+} ls_defect;
+
+typedef struct {
+    int32_t r[3];               /* Tucker ranks                                          */
+    int32_t C[3];               /* distinct canonical vectors per mode                   */
+    int64_t T;                  /* canonical terms R_total                               */
+    double  sigma_discarded[3]; /* (sum_{k>r} sigma_k^2)^(1/2) per mode                  */
+    double  sigma_total[3];     /* (sum_k sigma_k^2)^(1/2) per mode                      */
+    double  xi_norm;            /* ||xi||_2 with the vector norms folded in              */
+    double  bound_abs;          /* xi_norm * sum_l sigma_discarded[l] (Thm A.1(d))       */
+    int32_t sweeps[3];          /* eigen-solver sweeps per mode                          */
+} ls_tucker_info;
+
+/*
+ * lattice_sum_fit_t_scale -- choose the scale s of the sinc substitution.
+ * Sec. 2.1 (Eqs. laplace, hM, sinc_conv): the rank-R expansion reproduces
+ * 1/r only on a range [r_min, r_max]; this host routine picks s to minimise
+ * the maximum relative error |r sum_q w_q exp(-t_q^2 r^2) - 1| over that
+ * range (log-scan then golden section). Pure host arithmetic, done once per
+ * (R, sinc_step, range) and stored by the caller, as the paper stores its
+ * reference vectors. Writes s and the error reached; LS_ERR_ARG on bad input.
+ */
+int lattice_sum_fit_t_scale(int32_t R, double sinc_step, double r_min, double r_max,
+                            double* t_scale_out, double* max_rel_err_out);
+
+/*
+ * lattice_sum_create -- reference vectors and assembled lattice sums.
+ * Thm 3.1(A): for each block, mode l and rank index q the canonical vector
+ * v[i] = sum_k g_q[i - m_k + N] over the block's L_l snapped site vertices
+ * m_k. `blocks` (host, nblocks >= 1 entries) are copied. `stream` is a
+ * cudaStream_t or NULL. On success *out holds a new context.
+ * Errors: LS_ERR_ARG (bad sizes, a site outside the box), LS_ERR_OOM,
+ * LS_ERR_CUDA.
+ */
+int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* blocks,
+                       int32_t nblocks, void* stream);
+
+/*
+ * lattice_sum_add_defects -- append defects as canonical terms.
+ * Eq. (Can_LatticeSum_full): each defect adds R terms xi * (x)_l
+ * (sum over its windows of W_m g_q); xi = charge - block charge (SITES) or
+ * charge (POINT). Vectors shared by several defects are stored once
+ * (distinct window sets per mode). May be called several times before
+ * lattice_sum_rhosvd_reduce. `defects` is host memory with n entries.
+ * Errors: LS_ERR_ARG (block index, site range, position outside the box),
+ * LS_ERR_STATE (after the reduction), LS_ERR_OOM, LS_ERR_CUDA.
+ */
+int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n);
+
+/*
+ * lattice_sum_rhosvd_reduce -- RHOSVD rank reduction to Tucker form.
+ * Def. 4.1 / Thm A.1: per mode, the side matrix of unit canonical vectors
+ * (a vector shared by k terms enters with weight sqrt(k), which leaves
+ * A A^T unchanged) is orthogonalised via its FP64 Gram matrix, a parallel
+ * Jacobi eigen-solver and CholeskyQR2; r_l is the smallest rank whose
+ * discarded singular values satisfy (sum_{k>r} s_k^2)^(1/2) <= eps
+ * (sum_k s_k^2)^(1/2). The projections P_l = Z_l^T A_l and the core
+ * mu = sum_nu xi_nu P1[:,c1] (x) P2[:,c2] (x) P3[:,c3] follow.
+ * `forced_ranks` (host, 3 entries or NULL) overrides the eps rule (each
+ * clipped to C_l). Fills *info (may be NULL). Synchronises the stream.
+ * Errors: LS_ERR_ARG (eps <= 0 and no forced ranks), LS_ERR_STATE (called
+ * twice), LS_ERR_NOCONVERGE, LS_ERR_TIMEOUT, LS_ERR_OOM, LS_ERR_CUDA.
+ */
+int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ranks,
+                              ls_tucker_info* info);
+
+/*
+ * lattice_sum_eval_slab -- Tucker tensor values on z-slabs.
+ * Eq. (Tucker_singePot): for each z index i3, M = B x3 Z3[:, i3] and
+ * out[s][i1][i2] = sum_{a,b} Z1[a][i1] M[a][b] Z2[b][i2] (i2 fastest).
+ * `z_index` is host memory (nslab entries in [0, N)); `out_dev` is device
+ * memory of nslab * N * N elements of `out_dtype` (LS_OUT_F64/LS_OUT_F32),
+ * owned by the caller. Asynchronous on the context's stream.
+ * Errors: LS_ERR_ARG, LS_ERR_STATE (before the reduction), LS_ERR_OOM,
+ * LS_ERR_CUDA.
+ */
+int lattice_sum_eval_slab(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev,
+                          int32_t out_dtype);
+
+/*
+ * lattice_sum_get_factors -- device pointers of the Tucker factors (valid
+ * until lattice_sum_destroy; library-owned): Z[l] = double [r_l][N]
+ * (orthonormal rows), core = double [r1][r2][r3]; ranks[3] receives r_l.
+ * Errors: LS_ERR_STATE before the reduction, LS_ERR_ARG on NULL pointers.
+ */
+int lattice_sum_get_factors(ls_ctx* ctx, const double** Z, const double** core, int32_t* ranks);
+
+/*
+ * lattice_sum_read -- synchronous copy of an internal array to host memory,
+ * for checking and checkpointing. `what` is an LS_READ_* code, `mode` the
+ * mode (0..2) where the array is per mode, `dst` host memory of `bytes`
+ * bytes; the layouts are listed with the LS_READ_* codes. `*needed_bytes`
+ * (may be NULL) receives the size of the array. LS_ERR_ARG when `bytes` is
+ * too small (nothing copied), LS_ERR_STATE when the array does not exist yet.
+ */
+int lattice_sum_read(ls_ctx* ctx, int32_t what, int32_t mode, void* dst, int64_t bytes,
+                     int64_t* needed_bytes);
+
+/*
+ * lattice_sum_profile -- tracing. enable != 0 clears the trace and starts
+ * recording: every step of every context then records a pair of CUDA
+ * events on its stream around its kernels (per step name: genvec,
+ * assemble, norms, gram, jacobi, select, basis, cholqr2, project, core,
+ * eval), and the library counts its kernel launches and host<->device
+ * bytes. enable == 0 stops recording (the trace is kept). Process-wide.
+ */
+int lattice_sum_profile(int32_t enable);
+
+/*
+ * lattice_sum_profile_report -- waits for the recorded events and writes a
+ * NUL-terminated JSON object into `buf` (host, `cap` bytes):
+ *   {"steps": {"<name>": {"launches": n, "kernels": k, "ms": t}, ...},
+ *    "kernel_launches": K, "h2d_bytes": B, "d2h_bytes": B}
+ * `ms` is the summed event time of the step, `launches` how often the step
+ * ran and `kernels` how many kernels it launched. `*needed_bytes` (may be
+ * NULL) receives the length + 1. LS_ERR_ARG when `cap` is too small.
+ */
+int lattice_sum_profile_report(char* buf, int64_t cap, int64_t* needed_bytes);
+
+/* Frees every device buffer of the context (stream-ordered) and the context. */
+void lattice_sum_destroy(ls_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none); ctx may be NULL for
+ * failures of lattice_sum_create. The string lives until the next call. */
+const char* lattice_sum_last_error(const ls_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LATTICE_SUM_H */

@@ -1,0 +1,736 @@
+// Host implementation of the C ABI declared in include/lattice_sum.h.
+//
+// The host side only validates arguments, snaps site positions to grid
+// vertices, deduplicates defect windows and keeps the term -> column maps;
+// every arithmetic step of the path runs in the kernels of ls_f64.cu and
+// ls_tc.cu. Device buffers come from the stream-ordered allocator
+// (cudaMallocAsync), so building and dropping contexts in a loop does not
+// pay for cudaMalloc after the first round.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "ls_common.cuh"
+#include "ls_tc.cuh"
+
+using namespace ls;
+
+namespace ls {
+void count_kernels(int n);
+}
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// ---------------------------------------------------------------------------
+// tracing: CUDA-event pairs per step, kernel-launch and copy-byte counters
+// ---------------------------------------------------------------------------
+struct TraceRec {
+    const char* name;
+    cudaEvent_t a, b;
+    int kernels;
+};
+struct Tracer {
+    std::mutex mu;
+    bool on = false;
+    std::vector<TraceRec> recs;
+    std::vector<cudaEvent_t> pool;
+    std::atomic<long long> kernels{0}, h2d{0}, d2h{0};
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+Tracer& tracer() {
+    static Tracer* t = new Tracer();
+    return *t;
+}
+
+// Records an event pair around a step on a stream when tracing is on.
+struct Scope {
+    const char* name;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    long long k0 = 0;
+    Scope(const char* n, cudaStream_t s) : name(n), st(s) {
+        Tracer& t = tracer();
+        if (!t.on) return;
+        std::lock_guard<std::mutex> g(t.mu);
+        a = t.get();
+        k0 = t.kernels.load();
+        cudaEventRecord(a, st);
+    }
+    ~Scope() {
+        if (!a) return;
+        Tracer& t = tracer();
+        std::lock_guard<std::mutex> g(t.mu);
+        cudaEvent_t b = t.get();
+        cudaEventRecord(b, st);
+        t.recs.push_back({name, a, b, (int)(t.kernels.load() - k0)});
+    }
+};
+
+void count_h2d(int64_t n) { tracer().h2d += n; }
+void count_d2h(int64_t n) { tracer().d2h += n; }
+
+struct HostBlock {
+    ls_block b;
+    std::vector<int32_t> m[3];   // vertex index of each site, per mode
+};
+
+struct ModeCols {
+    int64_t C = 0, cap = 0;
+    double* d_cols = nullptr;                    // [cap][N]
+    std::vector<int32_t> colq, woff, wcnt, win;  // host descriptors
+    int32_t* d_desc = nullptr;                   // colq | woff | wcnt (3 * cap) on device
+    int32_t* d_win = nullptr;
+    int64_t wincap = 0;
+    std::map<std::vector<int32_t>, int32_t> keys;   // defect window set -> key index
+    std::vector<int32_t> count;                     // terms per column
+};
+
+}  // namespace
+
+struct ls_ctx {
+    ls_params p{};
+    cudaStream_t st = nullptr;
+    int num_sms = 0;
+    double h = 0.0;
+    std::string err;
+    std::vector<HostBlock> blocks;
+    double* d_g = nullptr;
+    ModeCols mode[3];
+    std::vector<int32_t> tcol;   // [T][3]
+    std::vector<double> xi;      // [T]
+    bool reduced = false;
+    // reduction outputs
+    int32_t r[3] = {0, 0, 0};
+    double* d_norms[3] = {nullptr, nullptr, nullptr};
+    double* d_sigma[3] = {nullptr, nullptr, nullptr};
+    double* d_Z[3] = {nullptr, nullptr, nullptr};
+    double* d_P[3] = {nullptr, nullptr, nullptr};
+    double* d_B = nullptr;
+    int32_t* d_tcol = nullptr;
+    double* d_xi = nullptr;
+    double* d_xin = nullptr;
+    DevStatus* d_status = nullptr;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+int fail(ls_ctx* ctx, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+#define CU(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? LS_ERR_OOM : LS_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                       \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(ls_ctx* ctx, T** p, int64_t count) {
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, (size_t)count * sizeof(T), ctx->st);
+    if (e != cudaSuccess) return e;
+    ctx->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return cudaSuccess;
+}
+
+void dfree(ls_ctx* ctx, void* p) {
+    if (!p) return;
+    auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
+    if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+    cudaFreeAsync(p, ctx->st);
+}
+
+bool snap_vertex(const ls_ctx* ctx, double pos, int32_t* m) {
+    const double x = floor((pos - ctx->p.box_lo) / ctx->h + 0.5);
+    if (!(x >= 0.0 && x <= (double)ctx->p.N)) return false;
+    *m = (int32_t)x;
+    return true;
+}
+
+void keep_pool(int dev) {
+    static bool done[64] = {false};
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
+}
+
+// make room for `add` more columns in mode l and append their descriptors;
+// then assemble them on the device
+int append_columns(ls_ctx* ctx, int l, const std::vector<int32_t>& q, const std::vector<std::vector<int32_t>>& wins) {
+    ModeCols& mc = ctx->mode[l];
+    const int64_t add = (int64_t)q.size();
+    if (add == 0) return LS_OK;
+    const int64_t N = ctx->p.N;
+    const int64_t c0 = mc.C;
+    if (mc.C + add > mc.cap) {
+        int64_t ncap = std::max<int64_t>(mc.C + add, 2 * mc.cap);
+        double* nc = nullptr;
+        int32_t* nd = nullptr;
+        CU(dalloc(ctx, &nc, ncap * N));
+        CU(dalloc(ctx, &nd, 3 * ncap));
+        if (mc.C > 0) CU(cudaMemcpyAsync(nc, mc.d_cols, (size_t)mc.C * N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+        dfree(ctx, mc.d_cols);
+        dfree(ctx, mc.d_desc);
+        mc.d_cols = nc;
+        mc.d_desc = nd;
+        mc.cap = ncap;
+    }
+    for (int64_t i = 0; i < add; ++i) {
+        mc.colq.push_back(q[i]);
+        mc.woff.push_back((int32_t)mc.win.size());
+        mc.wcnt.push_back((int32_t)wins[i].size());
+        for (int32_t m : wins[i]) mc.win.push_back(m);
+        mc.count.push_back(0);
+    }
+    mc.C += add;
+    if ((int64_t)mc.win.size() > mc.wincap) {
+        int64_t nw = std::max<int64_t>((int64_t)mc.win.size(), 2 * mc.wincap);
+        int32_t* d = nullptr;
+        CU(dalloc(ctx, &d, nw));
+        dfree(ctx, mc.d_win);
+        mc.d_win = d;
+        mc.wincap = nw;
+    }
+    // descriptors live at d_desc: colq [0,cap), woff [cap,2cap), wcnt [2cap,3cap)
+    CU(cudaMemcpyAsync(mc.d_desc, mc.colq.data(), mc.C * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+    count_h2d((int64_t)(mc.C * sizeof(int32_t)));
+    CU(cudaMemcpyAsync(mc.d_desc + mc.cap, mc.woff.data(), mc.C * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+    count_h2d((int64_t)(mc.C * sizeof(int32_t)));
+    CU(cudaMemcpyAsync(mc.d_desc + 2 * mc.cap, mc.wcnt.data(), mc.C * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+    count_h2d((int64_t)(mc.C * sizeof(int32_t)));
+    CU(cudaMemcpyAsync(mc.d_win, mc.win.data(), mc.win.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+    count_h2d((int64_t)(mc.win.size() * sizeof(int32_t)));
+    Scope sc_asm("assemble", ctx->st);
+    CU(launch_assemble(ctx->d_g, N, mc.d_desc, mc.d_desc + mc.cap, mc.d_desc + 2 * mc.cap, mc.d_win, c0, add,
+                       mc.d_cols, ctx->st));
+    // the host vectors may be reallocated by the next append: finish the copies
+    CU(cudaStreamSynchronize(ctx->st));
+    return LS_OK;
+}
+
+double quad_max_err(int R, double hs, double s, const std::vector<double>& r) {
+    std::vector<double> t(R), w(R);
+    const double spi = 1.7724538509055160273;
+    for (int q = 0; q < R; ++q) {
+        t[q] = sinh(q * hs) / s;
+        w[q] = (q == 0) ? hs / (s * spi) : 2.0 * hs * cosh(q * hs) / (s * spi);
+    }
+    double e = 0.0;
+    for (double x : r) {
+        double acc = 0.0;
+        for (int q = 0; q < R; ++q) acc += w[q] * exp(-t[q] * t[q] * x * x);
+        e = std::max(e, fabs(x * acc - 1.0));
+    }
+    return e;
+}
+
+}  // namespace
+
+namespace ls {
+void count_kernels(int n) { tracer().kernels += n; }
+}  // namespace ls
+
+extern "C" {
+
+int lattice_sum_fit_t_scale(int32_t R, double sinc_step, double r_min, double r_max, double* t_scale_out,
+                            double* max_rel_err_out) {
+    ls_ctx* ctx = nullptr;
+    if (R < 1 || R > 256 || !(sinc_step > 0) || !(r_min > 0) || !(r_max > r_min) || !t_scale_out)
+        return fail(ctx, LS_ERR_ARG, "fit_t_scale: bad arguments");
+    std::vector<double> r(600);
+    for (int i = 0; i < 600; ++i) r[i] = r_min * pow(r_max / r_min, i / 599.0);
+    double best = 1e300, bx = 0.0;
+    const double lo = log(1e-2), hi = log(1e5);
+    const int ns = 241;
+    std::vector<double> xs(ns), es(ns);
+    for (int i = 0; i < ns; ++i) {
+        xs[i] = lo + (hi - lo) * i / (ns - 1);
+        es[i] = quad_max_err(R, sinc_step, exp(xs[i]), r);
+        if (es[i] < best) { best = es[i]; bx = i; }
+    }
+    int bi = (int)bx;
+    double a = xs[std::max(bi - 1, 0)], b = xs[std::min(bi + 1, ns - 1)];
+    const double gr = (sqrt(5.0) - 1.0) / 2.0;
+    double c = b - gr * (b - a), d = a + gr * (b - a);
+    double fc = quad_max_err(R, sinc_step, exp(c), r), fd = quad_max_err(R, sinc_step, exp(d), r);
+    for (int it = 0; it < 60; ++it) {
+        if (fc < fd) { b = d; d = c; fd = fc; c = b - gr * (b - a); fc = quad_max_err(R, sinc_step, exp(c), r); }
+        else { a = c; c = d; fc = fd; d = a + gr * (b - a); fd = quad_max_err(R, sinc_step, exp(d), r); }
+    }
+    const double x = 0.5 * (a + b);
+    *t_scale_out = exp(x);
+    if (max_rel_err_out) *max_rel_err_out = quad_max_err(R, sinc_step, exp(x), r);
+    return LS_OK;
+}
+
+int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* blocks, int32_t nblocks,
+                       void* stream) {
+    ls_ctx* ctx = nullptr;
+    if (!out || !params || !blocks || nblocks < 1) return fail(ctx, LS_ERR_ARG, "create: NULL argument or no block");
+    *out = nullptr;
+    const ls_params& p = *params;
+    if (p.N < 2 || p.N > (1 << 20)) return fail(ctx, LS_ERR_ARG, "create: N=%lld out of range", (long long)p.N);
+    if (!(p.box_hi > p.box_lo)) return fail(ctx, LS_ERR_ARG, "create: empty box");
+    if (p.R < 1 || p.R > 64) return fail(ctx, LS_ERR_ARG, "create: R=%d out of range [1,64]", p.R);
+    if (!(p.sinc_step > 0) || !(p.t_scale > 0)) return fail(ctx, LS_ERR_ARG, "create: sinc_step and t_scale must be > 0");
+    if (p.precision != LS_FP64 && p.precision != LS_MIXED) return fail(ctx, LS_ERR_ARG, "create: unknown precision %d", p.precision);
+    if (p.flags != 0) return fail(ctx, LS_ERR_ARG, "create: flags must be 0");
+    ctx = new ls_ctx();
+    ctx->p = p;
+    ctx->st = static_cast<cudaStream_t>(stream);
+    ctx->h = (p.box_hi - p.box_lo) / (double)p.N;
+    for (int b = 0; b < nblocks; ++b) {
+        HostBlock hb;
+        hb.b = blocks[b];
+        for (int a = 0; a < 3; ++a) {
+            if (hb.b.L[a] < 1 || hb.b.L[a] > (1 << 20)) {
+                delete ctx;
+                return fail(nullptr, LS_ERR_ARG, "create: block %d has L[%d]=%lld", b, a, (long long)hb.b.L[a]);
+            }
+            for (int64_t k = 0; k < hb.b.L[a]; ++k) {
+                int32_t m;
+                if (!snap_vertex(ctx, hb.b.origin[a] + (double)k * hb.b.spacing[a], &m)) {
+                    delete ctx;
+                    return fail(nullptr, LS_ERR_ARG, "create: site %lld of block %d (axis %d) outside the box",
+                                (long long)k, b, a);
+                }
+                hb.m[a].push_back(m);
+            }
+        }
+        ctx->blocks.push_back(std::move(hb));
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return fail(nullptr, LS_ERR_CUDA, "create: no usable CUDA device (%s)", cudaGetErrorString(e));
+    }
+    keep_pool(dev);
+    const int64_t N = p.N;
+    const int R = p.R;
+    int rc = LS_OK;
+    {
+        cudaError_t e2 = dalloc(ctx, &ctx->d_g, (int64_t)R * 2 * N);
+        if (e2 == cudaSuccess) e2 = dalloc(ctx, &ctx->d_status, 1);
+        Scope sc_gen("genvec", ctx->st);
+        if (e2 == cudaSuccess) e2 = launch_genvec(ctx->d_g, R, N, ctx->h, p.sinc_step, p.t_scale, ctx->st);
+        if (e2 != cudaSuccess) rc = fail(ctx, LS_ERR_CUDA, "create: %s", cudaGetErrorString(e2));
+    }
+    for (int l = 0; l < 3 && rc == LS_OK; ++l) {
+        std::vector<int32_t> q;
+        std::vector<std::vector<int32_t>> wins;
+        for (size_t b = 0; b < ctx->blocks.size(); ++b)
+            for (int qq = 0; qq < R; ++qq) {
+                q.push_back(qq);
+                wins.push_back(ctx->blocks[b].m[l]);
+            }
+        rc = append_columns(ctx, l, q, wins);
+    }
+    if (rc != LS_OK) {
+        g_create_error = ctx->err;
+        lattice_sum_destroy(ctx);
+        return rc;
+    }
+    for (size_t b = 0; b < ctx->blocks.size(); ++b)
+        for (int qq = 0; qq < R; ++qq) {
+            const int32_t c = (int32_t)(b * R + qq);
+            for (int l = 0; l < 3; ++l) {
+                ctx->tcol.push_back(c);
+                ctx->mode[l].count[c] += 1;
+            }
+            ctx->xi.push_back(ctx->blocks[b].b.charge);
+        }
+    *out = ctx;
+    return LS_OK;
+}
+
+int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n) {
+    if (!ctx) return fail(nullptr, LS_ERR_ARG, "add_defects: NULL context");
+    if (ctx->reduced) return fail(ctx, LS_ERR_STATE, "add_defects: context already reduced");
+    if (n < 0 || (n > 0 && !defects)) return fail(ctx, LS_ERR_ARG, "add_defects: bad defect array");
+    const int R = ctx->p.R;
+    const int nb = (int)ctx->blocks.size();
+    // validate everything first so that a bad entry changes nothing
+    std::vector<std::vector<int32_t>> key(3 * (size_t)n);
+    std::vector<double> dxi(n);
+    for (int64_t i = 0; i < n; ++i) {
+        const ls_defect& d = defects[i];
+        if (d.kind == LS_DEFECT_SITES) {
+            if (d.block < 0 || d.block >= nb) return fail(ctx, LS_ERR_ARG, "defect %lld: block %d", (long long)i, d.block);
+            const HostBlock& hb = ctx->blocks[d.block];
+            for (int a = 0; a < 3; ++a) {
+                if (d.extent[a] < 1 || d.site[a] < 0 || d.site[a] + d.extent[a] > hb.b.L[a])
+                    return fail(ctx, LS_ERR_ARG, "defect %lld: sites out of block range on axis %d", (long long)i, a);
+                for (int64_t e = 0; e < d.extent[a]; ++e) key[3 * i + a].push_back(hb.m[a][d.site[a] + e]);
+            }
+            dxi[i] = d.charge - hb.b.charge;
+        } else if (d.kind == LS_DEFECT_POINT) {
+            for (int a = 0; a < 3; ++a) {
+                int32_t m;
+                if (!snap_vertex(ctx, d.pos[a], &m))
+                    return fail(ctx, LS_ERR_ARG, "defect %lld: position outside the box", (long long)i);
+                key[3 * i + a].push_back(m);
+            }
+            dxi[i] = d.charge;
+        } else {
+            return fail(ctx, LS_ERR_ARG, "defect %lld: unknown kind %d", (long long)i, d.kind);
+        }
+    }
+    std::vector<int32_t> base(3 * (size_t)n);
+    for (int l = 0; l < 3; ++l) {
+        ModeCols& mc = ctx->mode[l];
+        std::vector<int32_t> q;
+        std::vector<std::vector<int32_t>> wins;
+        const int64_t first_new = mc.C;
+        int32_t next = (int32_t)mc.keys.size();
+        for (int64_t i = 0; i < n; ++i) {
+            auto it = mc.keys.find(key[3 * i + l]);
+            int32_t kidx;
+            if (it == mc.keys.end()) {
+                kidx = next++;
+                mc.keys.emplace(key[3 * i + l], kidx);
+                for (int qq = 0; qq < R; ++qq) {
+                    q.push_back(qq);
+                    wins.push_back(key[3 * i + l]);
+                }
+            } else {
+                kidx = it->second;
+            }
+            base[3 * i + l] = (int32_t)(nb * R) + kidx * R;
+        }
+        (void)first_new;
+        int rc = append_columns(ctx, l, q, wins);
+        if (rc != LS_OK) return rc;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int qq = 0; qq < R; ++qq) {
+            for (int l = 0; l < 3; ++l) {
+                const int32_t c = base[3 * i + l] + qq;
+                ctx->tcol.push_back(c);
+                ctx->mode[l].count[c] += 1;
+            }
+            ctx->xi.push_back(dxi[i]);
+        }
+    return LS_OK;
+}
+
+int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ranks, ls_tucker_info* info) {
+    if (!ctx) return fail(nullptr, LS_ERR_ARG, "rhosvd_reduce: NULL context");
+    if (ctx->reduced) return fail(ctx, LS_ERR_STATE, "rhosvd_reduce: already reduced");
+    if (!forced_ranks && !(eps > 0.0)) return fail(ctx, LS_ERR_ARG, "rhosvd_reduce: eps must be > 0");
+    const int64_t N = ctx->p.N;
+    const int64_t T = (int64_t)ctx->xi.size();
+    cudaStream_t st = ctx->st;
+    // term maps and weights
+    CU(dalloc(ctx, &ctx->d_tcol, 3 * T));
+    CU(dalloc(ctx, &ctx->d_xi, T));
+    CU(dalloc(ctx, &ctx->d_xin, T));
+    CU(cudaMemcpyAsync(ctx->d_tcol, ctx->tcol.data(), 3 * T * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    count_h2d((int64_t)(3 * T * sizeof(int32_t)));
+    CU(cudaMemcpyAsync(ctx->d_xi, ctx->xi.data(), T * sizeof(double), cudaMemcpyHostToDevice, st));
+    count_h2d((int64_t)(T * sizeof(double)));
+    double sel[3][3];
+    double* d_sel = nullptr;
+    CU(dalloc(ctx, &d_sel, 9));
+    double* d_G[3];
+    double* d_V[3];
+    int32_t* d_perm[3];
+    double* d_isl[3];
+    double* d_w[3];
+    int sweeps[3] = {0, 0, 0};
+    for (int l = 0; l < 3; ++l) {
+        ModeCols& mc = ctx->mode[l];
+        const int64_t C = mc.C;
+        CU(dalloc(ctx, &ctx->d_norms[l], C));
+        CU(dalloc(ctx, &ctx->d_sigma[l], C));
+        CU(dalloc(ctx, &d_G[l], C * C));
+        CU(dalloc(ctx, &d_V[l], C * C));
+        CU(dalloc(ctx, &d_perm[l], C));
+        CU(dalloc(ctx, &d_isl[l], C));
+        CU(dalloc(ctx, &d_w[l], C));
+        std::vector<double> w(C);
+        for (int64_t c = 0; c < C; ++c) w[c] = sqrt((double)mc.count[c]);
+        CU(cudaMemcpyAsync(d_w[l], w.data(), C * sizeof(double), cudaMemcpyHostToDevice, st));
+        count_h2d((int64_t)(C * sizeof(double)));
+        { Scope sc("norms", st); CU(launch_norm_columns(mc.d_cols, C, N, ctx->d_norms[l], st)); }
+        { Scope sc("gram", st); CU(launch_gram_weighted(mc.d_cols, C, N, d_w[l], d_G[l], st)); }
+        CU(launch_identity(d_V[l], C, st));
+        CU(cudaMemsetAsync(ctx->d_status, 0, sizeof(DevStatus), st));
+        const double abs_floor = 1e-300;
+        { Scope sc("jacobi", st); CU(launch_jacobi(d_G[l], d_V[l], C, ctx->d_status, 60, 1e-15, abs_floor, ctx->num_sms, st)); }
+        DevStatus hs;
+        CU(cudaMemcpyAsync(&hs, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+        count_d2h((int64_t)(sizeof(DevStatus)));
+        CU(cudaStreamSynchronize(st));
+        if (hs.flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Jacobi grid barrier timed out (mode %d)", l);
+        if (hs.flag == FLAG_NOCONVERGE || hs.sweeps <= 0)
+            return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: Jacobi did not converge (mode %d)", l);
+        sweeps[l] = hs.sweeps;
+        const int forced = forced_ranks ? std::max(1, forced_ranks[l]) : 0;
+        { Scope sc("select", st); CU(launch_sort_select(d_G[l], C, eps, forced, d_perm[l], ctx->d_sigma[l], d_isl[l], d_sel + 3 * l, st)); }
+    }
+    CU(cudaMemcpyAsync(sel, d_sel, sizeof sel, cudaMemcpyDeviceToHost, st));
+    count_d2h((int64_t)(sizeof sel));
+    CU(cudaStreamSynchronize(st));
+    for (int l = 0; l < 3; ++l) ctx->r[l] = (int32_t)sel[l][0];
+    for (int l = 0; l < 3; ++l) {
+        ModeCols& mc = ctx->mode[l];
+        const int64_t C = mc.C;
+        const int r = ctx->r[l];
+        double* work = nullptr;
+        CU(dalloc(ctx, &ctx->d_Z[l], (int64_t)r * N));
+        CU(dalloc(ctx, &ctx->d_P[l], (int64_t)r * C));
+        CU(dalloc(ctx, &work, (int64_t)r * r));
+        { Scope sc("basis", st); CU(launch_basis(d_V[l], C, d_perm[l], d_isl[l], d_w[l], mc.d_cols, N, r, ctx->d_Z[l], st)); }
+        CU(cudaMemsetAsync(ctx->d_status, 0, sizeof(DevStatus), st));
+        { Scope sc("cholqr2", st); CU(launch_cholqr2(ctx->d_Z[l], r, N, work, ctx->d_status, ctx->num_sms, st)); }
+        { Scope sc("project", st); CU(launch_project(ctx->d_Z[l], r, mc.d_cols, C, N, ctx->d_P[l], st)); }
+        dfree(ctx, work);
+        DevStatus hs;
+        CU(cudaMemcpyAsync(&hs, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+        count_d2h((int64_t)(sizeof(DevStatus)));
+        CU(cudaStreamSynchronize(st));
+        if (hs.flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Cholesky grid barrier timed out");
+        if (hs.flag == FLAG_NOT_SPD) return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: CholeskyQR2 met a non-positive pivot (mode %d)", l);
+    }
+    { Scope sc("fold", st); CU(launch_fold_norms(ctx->d_xi, ctx->d_tcol, T, ctx->d_norms[0], ctx->d_norms[1], ctx->d_norms[2], ctx->d_xin, st)); }
+    const int64_t core_n = (int64_t)ctx->r[0] * ctx->r[1] * ctx->r[2];
+    CU(dalloc(ctx, &ctx->d_B, core_n));
+    int32_t Cs[3] = {(int32_t)ctx->mode[0].C, (int32_t)ctx->mode[1].C, (int32_t)ctx->mode[2].C};
+    {
+        Scope sc_core("core", st);
+        if (ctx->p.precision == LS_MIXED) {
+            int rc = tc_core(ctx->d_P[0], ctx->d_P[1], ctx->d_P[2], Cs, ctx->r, ctx->d_tcol, ctx->d_xin, T, ctx->d_B,
+                             ctx->num_sms, st, &ctx->err);
+            if (rc != LS_OK) return rc;
+        } else {
+            CU(launch_core_f64(ctx->d_P[0], ctx->d_P[1], ctx->d_P[2], Cs, ctx->r, ctx->d_tcol, ctx->d_xin, T, ctx->d_B,
+                               st));
+        }
+    }
+    for (int l = 0; l < 3; ++l) {
+        dfree(ctx, d_G[l]);
+        dfree(ctx, d_V[l]);
+        dfree(ctx, d_perm[l]);
+        dfree(ctx, d_isl[l]);
+        dfree(ctx, d_w[l]);
+    }
+    dfree(ctx, d_sel);
+    if (info) {
+        memset(info, 0, sizeof *info);
+        double ssum = 0.0;
+        for (int l = 0; l < 3; ++l) {
+            info->r[l] = ctx->r[l];
+            info->C[l] = Cs[l];
+            info->sigma_discarded[l] = sqrt(std::max(sel[l][1], 0.0));
+            info->sigma_total[l] = sqrt(std::max(sel[l][2], 0.0));
+            info->sweeps[l] = sweeps[l];
+            ssum += info->sigma_discarded[l];
+        }
+        info->T = T;
+        // ||xi|| with the norms folded in: a small reduction on the host copy
+        std::vector<double> xin(T);
+        CU(cudaMemcpyAsync(xin.data(), ctx->d_xin, T * sizeof(double), cudaMemcpyDeviceToHost, st));
+        count_d2h((int64_t)(T * sizeof(double)));
+        CU(cudaStreamSynchronize(st));
+        double s2 = 0.0;
+        for (double v : xin) s2 += v * v;
+        info->xi_norm = sqrt(s2);
+        info->bound_abs = info->xi_norm * ssum;
+    }
+    CU(cudaGetLastError());
+    ctx->reduced = true;
+    return LS_OK;
+}
+
+int lattice_sum_eval_slab(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev, int32_t out_dtype) {
+    if (!ctx) return fail(nullptr, LS_ERR_ARG, "eval_slab: NULL context");
+    if (!ctx->reduced) return fail(ctx, LS_ERR_STATE, "eval_slab: call rhosvd_reduce first");
+    if (nslab < 0 || (nslab > 0 && (!z_index || !out_dev))) return fail(ctx, LS_ERR_ARG, "eval_slab: bad arguments");
+    if (out_dtype != LS_OUT_F64 && out_dtype != LS_OUT_F32) return fail(ctx, LS_ERR_ARG, "eval_slab: bad out_dtype");
+    if (nslab == 0) return LS_OK;
+    const int64_t N = ctx->p.N;
+    std::vector<int32_t> z(nslab);
+    for (int s = 0; s < nslab; ++s) {
+        if (z_index[s] < 0 || z_index[s] >= N) return fail(ctx, LS_ERR_ARG, "eval_slab: z index %lld out of range", (long long)z_index[s]);
+        z[s] = (int32_t)z_index[s];
+    }
+    cudaStream_t st = ctx->st;
+    // slabs in chunks that bound the work buffer to ~256 MB
+    const int64_t per = (int64_t)ctx->r[0] * ctx->r[1] + (int64_t)ctx->r[0] * N;
+    int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(nslab, (int64_t)(32 << 20) / std::max<int64_t>(per, 1)));
+    int32_t* d_z = nullptr;
+    double* work = nullptr;
+    CU(dalloc(ctx, &d_z, nslab));
+    CU(dalloc(ctx, &work, per * chunk));
+    CU(cudaMemcpyAsync(d_z, z.data(), nslab * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    count_h2d((int64_t)(nslab * sizeof(int32_t)));
+    const size_t esz = out_dtype == LS_OUT_F32 ? 4 : 8;
+    const double* Zc[3] = {ctx->d_Z[0], ctx->d_Z[1], ctx->d_Z[2]};
+    Scope sc_eval("eval", st);
+    for (int s0 = 0; s0 < nslab; s0 += chunk) {
+        const int ns = std::min(chunk, nslab - s0);
+        char* o = static_cast<char*>(out_dev) + (size_t)s0 * N * N * esz;
+        if (ctx->p.precision == LS_MIXED) {
+            int rc = tc_eval(Zc, ctx->r, ctx->d_B, N, d_z + s0, ns, work, o, out_dtype == LS_OUT_F32, ctx->num_sms, st,
+                             &ctx->err);
+            if (rc != LS_OK) return rc;
+        } else {
+            CU(launch_eval_f64(Zc, ctx->r, ctx->d_B, N, d_z + s0, ns, work, o, out_dtype == LS_OUT_F32, st));
+        }
+    }
+    dfree(ctx, work);
+    dfree(ctx, d_z);
+    return LS_OK;
+}
+
+int lattice_sum_get_factors(ls_ctx* ctx, const double** Z, const double** core, int32_t* ranks) {
+    if (!ctx) return fail(nullptr, LS_ERR_ARG, "get_factors: NULL context");
+    if (!ctx->reduced) return fail(ctx, LS_ERR_STATE, "get_factors: call rhosvd_reduce first");
+    if (!Z || !core || !ranks) return fail(ctx, LS_ERR_ARG, "get_factors: NULL output");
+    for (int l = 0; l < 3; ++l) {
+        Z[l] = ctx->d_Z[l];
+        ranks[l] = ctx->r[l];
+    }
+    *core = ctx->d_B;
+    return LS_OK;
+}
+
+int lattice_sum_read(ls_ctx* ctx, int32_t what, int32_t mode, void* dst, int64_t bytes, int64_t* needed_bytes) {
+    if (!ctx) return fail(nullptr, LS_ERR_ARG, "read: NULL context");
+    if (mode < 0 || mode > 2) return fail(ctx, LS_ERR_ARG, "read: mode %d", mode);
+    const int64_t N = ctx->p.N;
+    const ModeCols& mc = ctx->mode[mode];
+    const void* src = nullptr;
+    int64_t need = 0;
+    std::vector<int32_t> tmp_i;
+    const int64_t T = (int64_t)ctx->xi.size();
+    switch (what) {
+        case LS_READ_GENVEC: src = ctx->d_g; need = (int64_t)ctx->p.R * 2 * N * 8; break;
+        case LS_READ_COLUMNS: src = mc.d_cols; need = mc.C * N * 8; break;
+        case LS_READ_NORMS: src = ctx->d_norms[mode]; need = mc.C * 8; break;
+        case LS_READ_TERMS: need = 3 * T * 4; break;
+        case LS_READ_XI: src = ctx->reduced ? (const void*)ctx->d_xin : nullptr; need = T * 8; break;
+        case LS_READ_SIGMA: src = ctx->d_sigma[mode]; need = mc.C * 8; break;
+        case LS_READ_BASIS: src = ctx->d_Z[mode]; need = (int64_t)ctx->r[mode] * N * 8; break;
+        case LS_READ_PROJ: src = ctx->d_P[mode]; need = (int64_t)ctx->r[mode] * mc.C * 8; break;
+        case LS_READ_CORE: src = ctx->d_B; need = (int64_t)ctx->r[0] * ctx->r[1] * ctx->r[2] * 8; break;
+        default: return fail(ctx, LS_ERR_ARG, "read: unknown item %d", what);
+    }
+    if (needed_bytes) *needed_bytes = need;
+    if (!dst) return LS_OK;
+    if (bytes < need) return fail(ctx, LS_ERR_ARG, "read: buffer of %lld bytes, need %lld", (long long)bytes, (long long)need);
+    if (what == LS_READ_TERMS) {
+        memcpy(dst, ctx->tcol.data(), need);
+        return LS_OK;
+    }
+    if (what == LS_READ_XI && !ctx->reduced) {
+        memcpy(dst, ctx->xi.data(), need);
+        return LS_OK;
+    }
+    if (!src) return fail(ctx, LS_ERR_STATE, "read: item %d not computed yet", what);
+    CU(cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToHost, ctx->st));
+    count_d2h((int64_t)(need));
+    CU(cudaStreamSynchronize(ctx->st));
+    return LS_OK;
+}
+
+int lattice_sum_profile(int32_t enable) {
+    Tracer& t = tracer();
+    std::lock_guard<std::mutex> g(t.mu);
+    if (enable) {
+        for (auto& r : t.recs) {
+            t.pool.push_back(r.a);
+            t.pool.push_back(r.b);
+        }
+        t.recs.clear();
+        t.kernels = 0;
+        t.h2d = 0;
+        t.d2h = 0;
+    }
+    t.on = enable != 0;
+    return LS_OK;
+}
+
+int lattice_sum_profile_report(char* buf, int64_t cap, int64_t* needed_bytes) {
+    Tracer& t = tracer();
+    std::lock_guard<std::mutex> g(t.mu);
+    struct Agg { long long launches = 0, kernels = 0; double ms = 0.0; };
+    std::map<std::string, Agg> agg;
+    for (auto& r : t.recs) {
+        if (cudaEventSynchronize(r.b) != cudaSuccess) return fail(nullptr, LS_ERR_CUDA, "profile_report: event wait failed");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        Agg& a = agg[r.name];
+        a.launches += 1;
+        a.kernels += r.kernels;
+        a.ms += ms;
+    }
+    std::string js = "{\"steps\": {";
+    bool first = true;
+    char tmp[256];
+    for (auto& kv : agg) {
+        snprintf(tmp, sizeof tmp, "%s\"%s\": {\"launches\": %lld, \"kernels\": %lld, \"ms\": %.6f}", first ? "" : ", ",
+                 kv.first.c_str(), kv.second.launches, kv.second.kernels, kv.second.ms);
+        js += tmp;
+        first = false;
+    }
+    snprintf(tmp, sizeof tmp, "}, \"kernel_launches\": %lld, \"h2d_bytes\": %lld, \"d2h_bytes\": %lld}",
+             (long long)t.kernels.load(), (long long)t.h2d.load(), (long long)t.d2h.load());
+    js += tmp;
+    if (needed_bytes) *needed_bytes = (int64_t)js.size() + 1;
+    if (!buf) return LS_OK;
+    if (cap < (int64_t)js.size() + 1) return fail(nullptr, LS_ERR_ARG, "profile_report: buffer too small");
+    memcpy(buf, js.c_str(), js.size() + 1);
+    return LS_OK;
+}
+
+void lattice_sum_destroy(ls_ctx* ctx) {
+    if (!ctx) return;
+    for (void* p : ctx->allocs) cudaFreeAsync(p, ctx->st);
+    ctx->allocs.clear();
+    delete ctx;
+}
+
+const char* lattice_sum_last_error(const ls_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// Internal declarations shared by the CUDA translation units of the
+// lattice-sum library (not part of the public C ABI in include/lattice_sum.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "lattice_sum.h"
+
+namespace ls {
+
+// ---------------------------------------------------------------------------
+// error flags raised by device code (bounded waits, failed pivots)
+// ---------------------------------------------------------------------------
+enum DeviceFlag : int {
+    FLAG_OK = 0,
+    FLAG_TIMEOUT = 1,      // a bounded spin-wait gave up
+    FLAG_NOT_SPD = 2,      // Cholesky met a non-positive pivot
+    FLAG_NOCONVERGE = 3,   // Jacobi sweep limit reached
+};
+
+// Scratch words used by device-side grid barriers and status reporting.
+struct DevStatus {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int flag;
+    int sweeps;
+    unsigned int sweep_active[64];
+};
+
+// ---------------------------------------------------------------------------
+// tracing: every kernel launch site bumps this counter (ls_api.cu owns it)
+// ---------------------------------------------------------------------------
+void count_kernels(int n);
+
+// ---------------------------------------------------------------------------
+// launchers implemented in ls_f64.cu (all enqueue on `st`, return cudaError)
+// ---------------------------------------------------------------------------
+
+// G0: g[q][j] = w_q^(1/3) exp(-t_q^2 ((j - N + 1/2) h)^2), q < R, j < 2N.
+cudaError_t launch_genvec(double* g, int R, int64_t N, double h, double sinc_step, double t_scale,
+                          cudaStream_t st);
+
+// G1/G2: out[c][i] = sum_{k<wcnt[c]} g[colq[c]][i - win[woff[c]+k] + N],
+// for columns c in [c0, c0 + ncols); out has row stride N.
+cudaError_t launch_assemble(const double* g, int64_t N, const int32_t* colq, const int32_t* woff,
+                            const int32_t* wcnt, const int32_t* win, int64_t c0, int64_t ncols,
+                            double* out, cudaStream_t st);
+
+// norms[c] = ||a_c||; a_c /= norms[c] in place (rows of a, stride N).
+cudaError_t launch_norm_columns(double* a, int64_t C, int64_t N, double* norms, cudaStream_t st);
+
+// G[c][c'] = w[c] w[c'] <a_c, a_c'> (a: C rows of length N), FP64.
+cudaError_t launch_gram_weighted(const double* a, int64_t C, int64_t N, const double* w, double* G,
+                                 cudaStream_t st);
+
+// V = I (C x C).
+cudaError_t launch_identity(double* V, int64_t C, cudaStream_t st);
+
+// Parallel cyclic Jacobi on symmetric G (C x C, in place) accumulating V.
+// Cooperative launch; st must be the context stream. Returns the sweeps
+// used in status->sweeps (negative if the limit was hit).
+cudaError_t launch_jacobi(double* G, double* V, int64_t C, DevStatus* status, int max_sweeps,
+                          double tol, double abs_floor, int num_sms, cudaStream_t st);
+
+// Sort eigenvalues (diag of G) descending: perm[k], lam[k]; select the rank
+// (forced if forced > 0) and write out[0] = r, out[1] = discarded^2,
+// out[2] = total (as doubles); also inv_sqrt_lam[k] = 1/sqrt(lam[k]).
+cudaError_t launch_sort_select(const double* G, int64_t C, double eps, int forced, int32_t* perm,
+                               double* lam, double* inv_sqrt_lam, double* out, cudaStream_t st);
+
+// Y[k][i] = inv_sqrt_lam[k] * sum_c V[c][perm[k]] w[c] a[c][i]  (k < r).
+cudaError_t launch_basis(const double* V, int64_t C, const int32_t* perm, const double* inv_sqrt_lam,
+                         const double* w, const double* a, int64_t N, int r, double* Y,
+                         cudaStream_t st);
+
+// Z <- orthonormalised rows of Y (r x N) by CholeskyQR2 (FP64); work holds
+// >= r*r doubles.
+cudaError_t launch_cholqr2(double* Y, int r, int64_t N, double* work, DevStatus* status, int num_sms,
+                           cudaStream_t st);
+
+// P[k][c] = sum_i Z[k][i] a[c][i]   (r x C).
+cudaError_t launch_project(const double* Z, int r, const double* a, int64_t C, int64_t N, double* P,
+                           cudaStream_t st);
+
+// xin[t] = xi[t] * n0[tc[3t]] * n1[tc[3t+1]] * n2[tc[3t+2]].
+cudaError_t launch_fold_norms(const double* xi, const int32_t* tcol, int64_t T, const double* n0,
+                              const double* n1, const double* n2, double* xin, cudaStream_t st);
+
+// Core (FP64): B[i][j][k] = sum_t xin[t] P0[i][c0] P1[j][c1] P2[k][c2].
+cudaError_t launch_core_f64(const double* P0, const double* P1, const double* P2, const int32_t* C,
+                            const int32_t* r, const int32_t* tcol, const double* xin, int64_t T,
+                            double* B, cudaStream_t st);
+
+// Slab evaluation (FP64 arithmetic): out[s][x][y] for nslab z indices.
+// work holds >= r0*r1*nslab + r0*N*nslab doubles.
+cudaError_t launch_eval_f64(const double* const Z[3], const int32_t* r, const double* B, int64_t N,
+                            const int32_t* zidx, int nslab, double* work, void* out, int out_f32,
+                            cudaStream_t st);
+
+}  // namespace ls

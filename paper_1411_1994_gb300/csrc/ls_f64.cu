@@ -1,0 +1,653 @@
+// FP64 kernels of the lattice-sum path (sm_103a).
+//
+// GB300 runs FP64 on CUDA cores at about 2 DFMA/clock/SM (~1.25 TFLOP/s for
+// the whole GPU), ~58x below its FP32 rate. Every FP64 step here is written
+// to spread over all SMs: the contractions use one register-blocked DFMA
+// GEMM (64x64 tiles, 4x4 outputs per thread) with operand gathers done in
+// the tile loaders, and the two inherently sequential algorithms (Jacobi
+// eigen-solver, blocked Cholesky) run as cooperative grids with a bounded
+// software grid barrier instead of one launch per step.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "ls_common.cuh"
+
+namespace ls {
+
+namespace {
+
+constexpr long long kSpinLimit = 1LL << 24;   // ~1-2 s of polling with nanosleep
+
+// ---------------------------------------------------------------------------
+// bounded grid barrier (sense by generation counter); all CTAs must be
+// co-resident (cooperative launch). On timeout the flag is raised and every
+// CTA returns false.
+// ---------------------------------------------------------------------------
+__device__ bool grid_barrier(DevStatus* st) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (gridDim.x == 1) return true;
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = &st->bar_gen;
+        volatile int* vflag = &st->flag;
+        unsigned int g = *vgen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(&st->bar_count, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&st->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == g) {
+                if (*vflag != FLAG_OK) { ok = 0; break; }
+                if (++it > kSpinLimit) { atomicCAS(&st->flag, FLAG_OK, FLAG_TIMEOUT); ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*vflag != FLAG_OK) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// G0 / G1 / G2 and small elementwise kernels
+// ---------------------------------------------------------------------------
+__global__ void k_genvec(double* g, int R, int64_t N, double h, double sinc_step, double t_scale) {
+    const int q = blockIdx.y;
+    const double u = q * sinc_step;
+    const double t = sinh(u) / t_scale;
+    const double spi = 1.7724538509055160273;   // sqrt(pi)
+    const double w = (q == 0) ? sinc_step / (t_scale * spi) : 2.0 * sinc_step * cosh(u) / (t_scale * spi);
+    const double a = cbrt(w);
+    const double t2 = t * t;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < 2 * N;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double x = ((double)(j - N) + 0.5) * h;
+        g[q * 2 * N + j] = a * exp(-t2 * (x * x));
+    }
+}
+
+__global__ void k_assemble(const double* __restrict__ g, int64_t N, const int32_t* __restrict__ colq,
+                           const int32_t* __restrict__ woff, const int32_t* __restrict__ wcnt,
+                           const int32_t* __restrict__ win, int64_t c0, double* __restrict__ out) {
+    const int64_t c = c0 + blockIdx.y;
+    const double* gq = g + (int64_t)colq[c] * 2 * N + N;
+    const int o = woff[c], n = wcnt[c];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) acc += gq[i - win[o + k]];
+        out[c * N + i] = acc;
+    }
+}
+
+__global__ void k_norm_columns(double* a, int64_t N, double* norms) {
+    const int64_t c = blockIdx.x;
+    double* row = a + c * N;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) s += row[i] * row[i];
+    __shared__ double red[32];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) red[0] = s;
+    }
+    __syncthreads();
+    const double nrm = sqrt(red[0]);
+    if (threadIdx.x == 0) norms[c] = nrm;
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) row[i] *= inv;
+}
+
+__global__ void k_identity(double* V, int64_t C) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < C * C;
+         e += (int64_t)gridDim.x * blockDim.x)
+        V[e] = (e / C == e % C) ? 1.0 : 0.0;
+}
+
+__global__ void k_fold_norms(const double* xi, const int32_t* tcol, int64_t T, const double* n0,
+                             const double* n1, const double* n2, double* xin) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T;
+         t += (int64_t)gridDim.x * blockDim.x)
+        xin[t] = xi[t] * n0[tcol[3 * t]] * n1[tcol[3 * t + 1]] * n2[tcol[3 * t + 2]];
+}
+
+// ---------------------------------------------------------------------------
+// register-blocked DFMA GEMM with functor operands
+//   C(z, m, n) = sum_k A(z, m, k) * B(z, k, n)
+// A::kfast / B::kfast say which index is contiguous in memory, so that the
+// tile loaders walk memory in order.
+// ---------------------------------------------------------------------------
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+template <class AOp, class BOp, class COp>
+__global__ void __launch_bounds__(256) k_gemm_f64(int M, int N, int K, AOp A, BOp B, COp Cst) {
+    __shared__ double As[GBK][GBM];
+    __shared__ double Bs[GBK][GBN];
+    const int z = blockIdx.z;
+    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < K; k0 += GBK) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = threadIdx.x + 256 * u;
+            int mm, kk;
+            if (AOp::kfast) { kk = e % GBK; mm = e / GBK; } else { mm = e % GBM; kk = e / GBM; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < M && gk < K) ? A(z, gm, gk) : 0.0;
+            int nn;
+            if (BOp::kfast) { kk = e % GBK; nn = e / GBK; } else { nn = e % GBN; kk = e / GBN; }
+            const int gn = n0 + nn, gk2 = k0 + kk;
+            Bs[kk][nn] = (gn < N && gk2 < K) ? B(z, gk2, gn) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty + 16 * i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx + 16 * j;
+            if (n < N) Cst(z, m, n, acc[i][j]);
+        }
+    }
+}
+
+template <class AOp, class BOp, class COp>
+cudaError_t gemm_f64(int M, int N, int K, int batch, AOp A, BOp B, COp Cst, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+    dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, batch);
+    k_gemm_f64<<<grid, 256, 0, st>>>(M, N, K, A, B, Cst);
+    count_kernels(1);
+    return cudaGetLastError();
+}
+
+// operand functors ----------------------------------------------------------
+struct RowK {            // X(m, k) = p[m * ld + k]        (k contiguous)
+    static constexpr bool kfast = true;
+    const double* p; int64_t ld;
+    __device__ double operator()(int, int m, int k) const { return p[m * ld + k]; }
+};
+struct RowKScaled {      // X(m, k) = s[m] * p[m * ld + k]
+    static constexpr bool kfast = true;
+    const double* p; int64_t ld; const double* s;
+    __device__ double operator()(int, int m, int k) const { return s[m] * p[m * ld + k]; }
+};
+struct KRowN {           // X(k, n) = p[k * ld + n]        (n contiguous)
+    static constexpr bool kfast = false;
+    const double* p; int64_t ld;
+    __device__ double operator()(int, int k, int n) const { return p[k * ld + n]; }
+};
+struct NRowK {           // X(k, n) = p[n * ld + k]        (k contiguous)
+    static constexpr bool kfast = true;
+    const double* p; int64_t ld;
+    __device__ double operator()(int, int k, int n) const { return p[n * ld + k]; }
+};
+struct NRowKScaled {     // X(k, n) = s[n] * p[n * ld + k]
+    static constexpr bool kfast = true;
+    const double* p; int64_t ld; const double* s;
+    __device__ double operator()(int, int k, int n) const { return s[n] * p[n * ld + k]; }
+};
+struct StoreRow {        // C[z*zs + m*ld + n] = v
+    double* p; int64_t ld; int64_t zs;
+    __device__ void operator()(int z, int m, int n, double v) const { p[z * zs + m * ld + n] = v; }
+};
+struct StoreRowW {       // C[m*ld + n] = w[m] w[n] v
+    double* p; int64_t ld; const double* w;
+    __device__ void operator()(int, int m, int n, double v) const { p[m * ld + n] = w[m] * w[n] * v; }
+};
+
+// basis: A(m=k, kk=c) = V[c*C + perm[k]] * w[c] * inv_sqrt_lam[k]
+struct BasisA {
+    static constexpr bool kfast = false;
+    const double* V; int64_t C; const int32_t* perm; const double* w; const double* isl;
+    __device__ double operator()(int, int m, int k) const { return V[k * C + perm[m]] * w[k] * isl[m]; }
+};
+// core: A(m=i, k=t) = P0[i*C0 + c0(t)] * xin[t]
+struct CoreA {
+    static constexpr bool kfast = true;
+    const double* P0; int64_t C0; const int32_t* tcol; const double* xin;
+    __device__ double operator()(int, int m, int k) const { return P0[m * C0 + tcol[3 * k]] * xin[k]; }
+};
+// core: B(k=t, n=j*r2+l) = P1[j*C1 + c1(t)] * P2[l*C2 + c2(t)]
+struct CoreB {
+    static constexpr bool kfast = true;
+    const double* P1; const double* P2; int64_t C1, C2; int r2; const int32_t* tcol;
+    __device__ double operator()(int, int k, int n) const {
+        const int j = n / r2, l = n - j * r2;
+        return P1[j * C1 + tcol[3 * k + 1]] * P2[l * C2 + tcol[3 * k + 2]];
+    }
+};
+// eval step 1: A(m=(a,b), k) = B[m*r2 + k], B(k, n=s) = Z2[k*N + zidx[s]]
+struct EvalZ3 {
+    static constexpr bool kfast = true;
+    const double* Z; int64_t N; const int32_t* zidx;
+    __device__ double operator()(int, int k, int n) const { return Z[k * N + zidx[n]]; }
+};
+// eval step 2: A(z=s; m=a, k=b) = M[(a*r1 + b)*ns + s]
+struct EvalM {
+    static constexpr bool kfast = false;
+    const double* M; int r1; int ns;
+    __device__ double operator()(int z, int m, int k) const { return M[((int64_t)m * r1 + k) * ns + z]; }
+};
+// eval step 3: A(z; m=x, k=a) = Z0[a*N + x] ; B(z; k=a, n=y) = T[z*r0*N + a*N + y]
+struct ColK {           // X(m, k) = p[k * ld + m]   (m contiguous)
+    static constexpr bool kfast = false;
+    const double* p; int64_t ld;
+    __device__ double operator()(int, int m, int k) const { return p[k * ld + m]; }
+};
+struct KRowNBatched {
+    static constexpr bool kfast = false;
+    const double* p; int64_t ld; int64_t zs;
+    __device__ double operator()(int z, int k, int n) const { return p[z * zs + k * ld + n]; }
+};
+struct StoreOut {
+    void* p; int64_t N; int f32;
+    __device__ void operator()(int z, int m, int n, double v) const {
+        const int64_t o = ((int64_t)z * N + m) * N + n;
+        if (f32) static_cast<float*>(p)[o] = (float)v;
+        else static_cast<double*>(p)[o] = v;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// parallel cyclic Jacobi (round-robin pairing), cooperative grid
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void rr_pair(int t, int i, int Cp, int& p, int& q) {
+    const int n1 = Cp - 1;
+    int a, b;
+    if (i == 0) { a = n1; b = t; }
+    else { a = (t + i) % n1; b = (t - i + n1) % n1; }
+    p = min(a, b);
+    q = max(a, b);
+}
+
+__global__ void __launch_bounds__(256) k_jacobi(double* G, double* V, int C, DevStatus* st, int max_sweeps,
+                                                double tol, double abs_floor) {
+    extern __shared__ double sm[];
+    const int Cp = C + (C & 1);
+    const int P = Cp / 2;
+    double* sc = sm;
+    double* ss = sm + P;
+    __shared__ unsigned int s_active;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t items_g = (int64_t)P * P;
+    const int64_t items = items_g + (int64_t)C * P;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) s_active = 0;
+        __syncthreads();
+        for (int t = 0; t < Cp - 1; ++t) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                int p, q;
+                rr_pair(t, i, Cp, p, q);
+                double c = 1.0, s = 0.0;
+                if (q < C) {
+                    const double app = __ldcg(G + (int64_t)p * C + p);
+                    const double aqq = __ldcg(G + (int64_t)q * C + q);
+                    const double apq = __ldcg(G + (int64_t)p * C + q);
+                    if (fabs(apq) > abs_floor && fabs(apq) > tol * sqrt(fabs(app * aqq))) {
+                        const double theta = (aqq - app) / (2.0 * apq);
+                        const double tt = copysign(1.0, theta) / (fabs(theta) + sqrt(1.0 + theta * theta));
+                        c = 1.0 / sqrt(1.0 + tt * tt);
+                        s = tt * c;
+                        if (blockIdx.x == 0) atomicAdd(&s_active, 1u);
+                    }
+                }
+                sc[i] = c;
+                ss[i] = s;
+            }
+            // every CTA must have read this round's pivots before any CTA
+            // overwrites them
+            if (!grid_barrier(st)) return;
+            for (int64_t it = gtid; it < items; it += nthr) {
+                if (it < items_g) {
+                    const int i = (int)(it / P), i2 = (int)(it % P);
+                    const double c1 = sc[i], s1 = ss[i], c2 = sc[i2], s2 = ss[i2];
+                    if (s1 == 0.0 && s2 == 0.0) continue;
+                    int p, q, p2, q2;
+                    rr_pair(t, i, Cp, p, q);
+                    rr_pair(t, i2, Cp, p2, q2);
+                    const bool vq = q < C, vq2 = q2 < C;   // p, p2 < C always (p < q <= Cp-1)
+                    double xpp = __ldcg(G + (int64_t)p * C + p2);
+                    double xpq = vq2 ? __ldcg(G + (int64_t)p * C + q2) : 0.0;
+                    double xqp = vq ? __ldcg(G + (int64_t)q * C + p2) : 0.0;
+                    double xqq = (vq && vq2) ? __ldcg(G + (int64_t)q * C + q2) : 0.0;
+                    // rows: J^T X
+                    const double ypp = c1 * xpp - s1 * xqp, ypq = c1 * xpq - s1 * xqq;
+                    const double yqp = s1 * xpp + c1 * xqp, yqq = s1 * xpq + c1 * xqq;
+                    // columns: Y J
+                    double zpp = c2 * ypp - s2 * ypq, zpq = s2 * ypp + c2 * ypq;
+                    double zqp = c2 * yqp - s2 * yqq, zqq = s2 * yqp + c2 * yqq;
+                    if (i == i2 && s1 != 0.0) { zpq = 0.0; zqp = 0.0; }
+                    __stcg(G + (int64_t)p * C + p2, zpp);
+                    if (vq2) __stcg(G + (int64_t)p * C + q2, zpq);
+                    if (vq) __stcg(G + (int64_t)q * C + p2, zqp);
+                    if (vq && vq2) __stcg(G + (int64_t)q * C + q2, zqq);
+                } else {
+                    const int64_t r = it - items_g;
+                    const int j = (int)(r / P), i2 = (int)(r % P);
+                    const double c2 = sc[i2], s2 = ss[i2];
+                    if (s2 == 0.0) continue;
+                    int p2, q2;
+                    rr_pair(t, i2, Cp, p2, q2);
+                    const double vp = __ldcg(V + (int64_t)j * C + p2);
+                    const double vq = __ldcg(V + (int64_t)j * C + q2);
+                    __stcg(V + (int64_t)j * C + p2, c2 * vp - s2 * vq);
+                    __stcg(V + (int64_t)j * C + q2, s2 * vp + c2 * vq);
+                }
+            }
+            if (!grid_barrier(st)) return;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->sweep_active[sweep & 63] = s_active;
+        if (!grid_barrier(st)) return;
+        const unsigned int act = __ldcg(&st->sweep_active[sweep & 63]);
+        if (act == 0) {
+            if (gtid == 0) st->sweeps = sweep + 1;
+            return;
+        }
+    }
+    if (gtid == 0) {
+        st->sweeps = -max_sweeps;
+        atomicCAS(&st->flag, FLAG_OK, FLAG_NOCONVERGE);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// eigenvalue sort + eps-rank selection (single CTA)
+// ---------------------------------------------------------------------------
+__global__ void k_sort_select(const double* G, int C, double eps, int forced, int32_t* perm, double* lam,
+                              double* isl, double* out) {
+    for (int k = threadIdx.x; k < C; k += blockDim.x) {
+        const double lk = G[(int64_t)k * C + k];
+        int rank = 0;
+        for (int j = 0; j < C; ++j) {
+            const double lj = G[(int64_t)j * C + j];
+            rank += (lj > lk) || (lj == lk && j < k);
+        }
+        perm[rank] = k;
+        lam[rank] = lk;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double total = 0.0;
+        for (int k = C - 1; k >= 0; --k) total += fmax(lam[k], 0.0);
+        int r = C;
+        double tail = 0.0, tail_at_r = 0.0;
+        if (forced > 0) {
+            r = min(forced, C);
+            for (int k = C - 1; k >= r; --k) tail += fmax(lam[k], 0.0);
+            tail_at_r = tail;
+        } else {
+            // suffix sums from the smallest eigenvalue; smallest r >= 1 whose tail qualifies
+            const double lim = eps * eps * total;
+            tail_at_r = 0.0;
+            r = C;
+            for (int k = C - 1; k >= 1; --k) {
+                tail += fmax(lam[k], 0.0);       // tail = sum_{j >= k}
+                if (tail <= lim) { r = k; tail_at_r = tail; }
+                else break;
+            }
+        }
+        out[0] = (double)r;
+        out[1] = tail_at_r;
+        out[2] = total;
+    }
+    __syncthreads();
+    // lam[] becomes the singular values sigma_k = sqrt(max(lambda_k, 0))
+    for (int k = threadIdx.x; k < C; k += blockDim.x) {
+        const double lk = lam[k];
+        isl[k] = lk > 0.0 ? 1.0 / sqrt(lk) : 0.0;
+        lam[k] = sqrt(fmax(lk, 0.0));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// blocked Cholesky (lower, in place on A r x r) as one cooperative grid, and
+// the forward substitution Z = L^{-1} Y (rows of Y independent per column)
+// ---------------------------------------------------------------------------
+constexpr int CHB = 32;
+
+__global__ void __launch_bounds__(256) k_cholesky(double* A, int r, DevStatus* st) {
+    __shared__ double D[CHB][CHB + 1];
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int j0 = 0; j0 < r; j0 += CHB) {
+        const int b = min(CHB, r - j0);
+        // 1) factor the diagonal block (CTA 0)
+        if (blockIdx.x == 0) {
+            for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+                const int i = e / b, k = e % b;
+                D[i][k] = __ldcg(A + (int64_t)(j0 + i) * r + j0 + k);
+            }
+            __syncthreads();
+            for (int k = 0; k < b; ++k) {
+                if (threadIdx.x == 0) {
+                    const double d = D[k][k];
+                    if (!(d > 0.0)) atomicCAS(&st->flag, FLAG_OK, FLAG_NOT_SPD);
+                    D[k][k] = d > 0.0 ? sqrt(d) : 1.0;
+                }
+                __syncthreads();
+                for (int i = k + 1 + threadIdx.x; i < b; i += blockDim.x) D[i][k] /= D[k][k];
+                __syncthreads();
+                for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+                    const int i = e / b, l = e % b;
+                    if (i > k && l > k && l <= i) D[i][l] -= D[i][k] * D[l][k];
+                }
+                __syncthreads();
+            }
+            for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+                const int i = e / b, k = e % b;
+                __stcg(A + (int64_t)(j0 + i) * r + j0 + k, k <= i ? D[i][k] : 0.0);
+            }
+        }
+        if (!grid_barrier(st)) return;
+        // 2) panel below: L21 = A21 L11^{-T}, one thread per row
+        for (int64_t i = j0 + b + gtid; i < r; i += nthr) {
+            double x[CHB];
+            for (int k = 0; k < b; ++k) x[k] = __ldcg(A + i * r + j0 + k);
+            for (int k = 0; k < b; ++k) {
+                double s = x[k];
+                for (int l = 0; l < k; ++l) s -= x[l] * __ldcg(A + (int64_t)(j0 + k) * r + j0 + l);
+                x[k] = s / __ldcg(A + (int64_t)(j0 + k) * r + j0 + k);
+            }
+            for (int k = 0; k < b; ++k) __stcg(A + i * r + j0 + k, x[k]);
+        }
+        if (!grid_barrier(st)) return;
+        // 3) trailing update of the lower triangle
+        const int64_t n2 = r - j0 - b;
+        for (int64_t e = gtid; e < n2 * n2; e += nthr) {
+            const int64_t i = j0 + b + e / n2, k = j0 + b + e % n2;
+            if (k > i) continue;
+            double s = __ldcg(A + i * r + k);
+            for (int l = 0; l < b; ++l) s -= __ldcg(A + i * r + j0 + l) * __ldcg(A + k * r + j0 + l);
+            __stcg(A + i * r + k, s);
+        }
+        if (!grid_barrier(st)) return;
+    }
+}
+
+__global__ void k_trsm_rows(const double* __restrict__ L, int r, double* Y, int64_t N) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int a = 0; a < r; ++a) {
+        double s = Y[(int64_t)a * N + i];
+        const double* La = L + (int64_t)a * r;
+        for (int b = 0; b < a; ++b) s -= La[b] * Y[(int64_t)b * N + i];
+        Y[(int64_t)a * N + i] = s / La[a];
+    }
+}
+
+template <class K>
+int coop_blocks(K kernel, int threads, size_t smem, int num_sms, int64_t want) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int64_t cap = (int64_t)per_sm * num_sms;
+    int64_t n = want < cap ? want : cap;
+    return (int)(n < 1 ? 1 : n);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_genvec(double* g, int R, int64_t N, double h, double sinc_step, double t_scale,
+                          cudaStream_t st) {
+    dim3 grid((unsigned)((2 * N + 255) / 256 < 1024 ? (2 * N + 255) / 256 : 1024), R);
+    k_genvec<<<grid, 256, 0, st>>>(g, R, N, h, sinc_step, t_scale);
+    count_kernels(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const double* g, int64_t N, const int32_t* colq, const int32_t* woff,
+                            const int32_t* wcnt, const int32_t* win, int64_t c0, int64_t ncols,
+                            double* out, cudaStream_t st) {
+    if (ncols <= 0) return cudaSuccess;
+    for (int64_t s = 0; s < ncols; s += 65535) {
+        const int64_t n = ncols - s < 65535 ? ncols - s : 65535;
+        dim3 grid((unsigned)((N + 255) / 256 < 64 ? (N + 255) / 256 : 64), (unsigned)n);
+        k_assemble<<<grid, 256, 0, st>>>(g, N, colq, woff, wcnt, win, c0 + s, out);
+        count_kernels(1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm_columns(double* a, int64_t C, int64_t N, double* norms, cudaStream_t st) {
+    if (C <= 0) return cudaSuccess;
+    k_norm_columns<<<(unsigned)C, 256, 0, st>>>(a, N, norms);
+    count_kernels(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_weighted(const double* a, int64_t C, int64_t N, const double* w, double* G,
+                                 cudaStream_t st) {
+    return gemm_f64((int)C, (int)C, (int)N, 1, RowK{a, N}, NRowK{a, N}, StoreRowW{G, C, w}, st);
+}
+
+cudaError_t launch_identity(double* V, int64_t C, cudaStream_t st) {
+    k_identity<<<(unsigned)((C * C + 255) / 256 < 4096 ? (C * C + 255) / 256 : 4096), 256, 0, st>>>(V, C);
+    count_kernels(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi(double* G, double* V, int64_t C, DevStatus* status, int max_sweeps, double tol,
+                          double abs_floor, int num_sms, cudaStream_t st) {
+    const int Cp = (int)(C + (C & 1));
+    const int P = Cp / 2;
+    const size_t smem = 2 * sizeof(double) * P;
+    const int64_t items = (int64_t)P * P + C * P;
+    const int64_t want = items <= 2048 ? 1 : (items + 1023) / 1024;
+    int nblk = coop_blocks(k_jacobi, 256, smem, num_sms, want);
+    if (nblk > num_sms) nblk = num_sms;
+    int Ci = (int)C;
+    void* args[] = {&G, &V, &Ci, &status, &max_sweeps, &tol, &abs_floor};
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    count_kernels(1);
+    return cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(nblk), dim3(256), args, smem, st);
+}
+
+cudaError_t launch_sort_select(const double* G, int64_t C, double eps, int forced, int32_t* perm, double* lam,
+                               double* inv_sqrt_lam, double* out, cudaStream_t st) {
+    k_sort_select<<<1, 1024, 0, st>>>(G, (int)C, eps, forced, perm, lam, inv_sqrt_lam, out);
+    count_kernels(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_basis(const double* V, int64_t C, const int32_t* perm, const double* inv_sqrt_lam,
+                         const double* w, const double* a, int64_t N, int r, double* Y, cudaStream_t st) {
+    return gemm_f64(r, (int)N, (int)C, 1, BasisA{V, C, perm, w, inv_sqrt_lam}, KRowN{a, N},
+                    StoreRow{Y, N, 0}, st);
+}
+
+cudaError_t launch_cholqr2(double* Y, int r, int64_t N, double* work, DevStatus* status, int num_sms,
+                           cudaStream_t st) {
+    for (int pass = 0; pass < 2; ++pass) {
+        cudaError_t e = gemm_f64(r, r, (int)N, 1, RowK{Y, N}, NRowK{Y, N}, StoreRow{work, r, 0}, st);
+        if (e != cudaSuccess) return e;
+        const int64_t want = ((int64_t)r * r + 255) / 256;
+        int nblk = coop_blocks(k_cholesky, 256, 0, num_sms, want < 1 ? 1 : want);
+        if (nblk > num_sms) nblk = num_sms;
+        void* args[] = {&work, &r, &status};
+        count_kernels(1);
+        e = cudaLaunchCooperativeKernel((void*)k_cholesky, dim3(nblk), dim3(256), args, 0, st);
+        if (e != cudaSuccess) return e;
+        k_trsm_rows<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(work, r, Y, N);
+        count_kernels(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_project(const double* Z, int r, const double* a, int64_t C, int64_t N, double* P,
+                           cudaStream_t st) {
+    return gemm_f64(r, (int)C, (int)N, 1, RowK{Z, N}, NRowK{a, N}, StoreRow{P, C, 0}, st);
+}
+
+cudaError_t launch_fold_norms(const double* xi, const int32_t* tcol, int64_t T, const double* n0,
+                              const double* n1, const double* n2, double* xin, cudaStream_t st) {
+    if (T <= 0) return cudaSuccess;
+    k_fold_norms<<<(unsigned)((T + 255) / 256 < 4096 ? (T + 255) / 256 : 4096), 256, 0, st>>>(xi, tcol, T, n0, n1,
+                                                                                             n2, xin);
+    count_kernels(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_core_f64(const double* P0, const double* P1, const double* P2, const int32_t* C,
+                            const int32_t* r, const int32_t* tcol, const double* xin, int64_t T, double* B,
+                            cudaStream_t st) {
+    return gemm_f64(r[0], r[1] * r[2], (int)T, 1, CoreA{P0, C[0], tcol, xin},
+                    CoreB{P1, P2, C[1], C[2], r[2], tcol}, StoreRow{B, (int64_t)r[1] * r[2], 0}, st);
+}
+
+cudaError_t launch_eval_f64(const double* const Z[3], const int32_t* r, const double* B, int64_t N,
+                            const int32_t* zidx, int nslab, double* work, void* out, int out_f32,
+                            cudaStream_t st) {
+    const int r0 = r[0], r1 = r[1], r2 = r[2];
+    double* M = work;                                  // [(a*r1+b)][s]
+    double* T = work + (int64_t)r0 * r1 * nslab;       // [s][a][y]
+    cudaError_t e = gemm_f64(r0 * r1, nslab, r2, 1, RowK{B, r2}, EvalZ3{Z[2], N, zidx},
+                             StoreRow{M, nslab, 0}, st);
+    if (e != cudaSuccess) return e;
+    // T_s[a][y] = sum_b M_s[a][b] Z1[b][y]
+    e = gemm_f64(r0, (int)N, r1, nslab, EvalM{M, r1, nslab}, KRowN{Z[1], N},
+                 StoreRow{T, N, (int64_t)r0 * N}, st);
+    if (e != cudaSuccess) return e;
+    // S_s[x][y] = sum_a Z0[a][x] T_s[a][y]
+    return gemm_f64((int)N, (int)N, r0, nslab, ColK{Z[0], N}, KRowNBatched{T, N, (int64_t)r0 * N},
+                    StoreOut{out, N, out_f32}, st);
+}
+
+}  // namespace ls

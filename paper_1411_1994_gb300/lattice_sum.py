@@ -1,0 +1,233 @@
+"""Thin ctypes binding of the lattice-sum C ABI (include/lattice_sum.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+PyTorch is used for device memory (output slabs) and streams. If the shared
+library is missing or cannot be loaded, importing this module raises: there
+is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "liblattice_sum.so")
+
+LS_OK, LS_ERR_ARG, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_NOCONVERGE, LS_ERR_STATE, LS_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+LS_FP64, LS_MIXED = 0, 1
+LS_DEFECT_SITES, LS_DEFECT_POINT = 0, 1
+LS_OUT_F64, LS_OUT_F32 = 0, 1
+(LS_READ_GENVEC, LS_READ_COLUMNS, LS_READ_NORMS, LS_READ_TERMS, LS_READ_XI, LS_READ_SIGMA,
+ LS_READ_BASIS, LS_READ_PROJ, LS_READ_CORE) = range(9)
+
+EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_create", "lattice_sum_add_defects",
+            "lattice_sum_rhosvd_reduce", "lattice_sum_eval_slab", "lattice_sum_get_factors",
+            "lattice_sum_read", "lattice_sum_profile", "lattice_sum_profile_report",
+            "lattice_sum_destroy", "lattice_sum_last_error")
+
+
+class ls_params(C.Structure):
+    _fields_ = [("N", C.c_int64), ("box_lo", C.c_double), ("box_hi", C.c_double), ("R", C.c_int32),
+                ("sinc_step", C.c_double), ("t_scale", C.c_double), ("precision", C.c_int32),
+                ("flags", C.c_int32)]
+
+
+class ls_block(C.Structure):
+    _fields_ = [("L", C.c_int64 * 3), ("origin", C.c_double * 3), ("spacing", C.c_double * 3),
+                ("charge", C.c_double)]
+
+
+class ls_defect(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("block", C.c_int32), ("site", C.c_int64 * 3),
+                ("extent", C.c_int64 * 3), ("pos", C.c_double * 3), ("charge", C.c_double)]
+
+
+class ls_tucker_info(C.Structure):
+    _fields_ = [("r", C.c_int32 * 3), ("C", C.c_int32 * 3), ("T", C.c_int64),
+                ("sigma_discarded", C.c_double * 3), ("sigma_total", C.c_double * 3),
+                ("xi_norm", C.c_double), ("bound_abs", C.c_double), ("sweeps", C.c_int32 * 3)]
+
+    def as_dict(self):
+        return {"r": list(self.r), "C": list(self.C), "T": int(self.T),
+                "sigma_discarded": list(self.sigma_discarded), "sigma_total": list(self.sigma_total),
+                "xi_norm": self.xi_norm, "bound_abs": self.bound_abs, "sweeps": list(self.sweeps)}
+
+
+class LatticeSumError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lattice_sum error {code}: {msg}")
+        self.code = code
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"lattice-sum CUDA library not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    P = C.POINTER
+    lib.lattice_sum_fit_t_scale.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_double, P(C.c_double),
+                                            P(C.c_double)]
+    lib.lattice_sum_create.argtypes = [P(C.c_void_p), P(ls_params), P(ls_block), C.c_int32, C.c_void_p]
+    lib.lattice_sum_add_defects.argtypes = [C.c_void_p, P(ls_defect), C.c_int64]
+    lib.lattice_sum_rhosvd_reduce.argtypes = [C.c_void_p, C.c_double, P(C.c_int32), P(ls_tucker_info)]
+    lib.lattice_sum_eval_slab.argtypes = [C.c_void_p, P(C.c_int64), C.c_int32, C.c_void_p, C.c_int32]
+    lib.lattice_sum_get_factors.argtypes = [C.c_void_p, P(C.c_void_p), P(C.c_void_p), P(C.c_int32)]
+    lib.lattice_sum_read.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64, P(C.c_int64)]
+    lib.lattice_sum_profile.argtypes = [C.c_int32]
+    lib.lattice_sum_profile_report.argtypes = [C.c_char_p, C.c_int64, P(C.c_int64)]
+    lib.lattice_sum_destroy.argtypes = [C.c_void_p]
+    lib.lattice_sum_destroy.restype = None
+    lib.lattice_sum_last_error.argtypes = [C.c_void_p]
+    lib.lattice_sum_last_error.restype = C.c_char_p
+    for name in EXPORTED:
+        if name not in ("lattice_sum_destroy", "lattice_sum_last_error"):
+            getattr(lib, name).restype = C.c_int
+    return lib
+
+
+_LIB: Optional[C.CDLL] = None
+
+
+def lib() -> C.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+def _check(rc, ctx=None):
+    if rc != LS_OK:
+        msg = lib().lattice_sum_last_error(ctx).decode(errors="replace")
+        raise LatticeSumError(rc, msg)
+
+
+def profile(enable: bool):
+    """Start (clearing the trace) or stop the library's per-step event tracing."""
+    _check(lib().lattice_sum_profile(1 if enable else 0))
+
+
+def profile_report() -> dict:
+    """Per-step device times, kernel-launch count and copy bytes since the
+    last ``profile(True)``."""
+    import json
+    need = C.c_int64()
+    _check(lib().lattice_sum_profile_report(None, 0, C.byref(need)))
+    buf = C.create_string_buffer(need.value + 64)
+    _check(lib().lattice_sum_profile_report(buf, need.value + 64, None))
+    return json.loads(buf.value.decode())
+
+
+def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float):
+    s, e = C.c_double(), C.c_double()
+    _check(lib().lattice_sum_fit_t_scale(R, sinc_step, r_min, r_max, C.byref(s), C.byref(e)))
+    return s.value, e.value
+
+
+def make_blocks(blocks) -> C.Array:
+    arr = (ls_block * len(blocks))()
+    for i, b in enumerate(blocks):
+        arr[i].L[:] = [int(x) for x in b.L]
+        arr[i].origin[:] = [float(x) for x in b.origin]
+        arr[i].spacing[:] = [float(x) for x in b.spacing]
+        arr[i].charge = float(b.charge)
+    return arr
+
+
+def make_defects(defects) -> C.Array:
+    arr = (ls_defect * max(len(defects), 1))()
+    for i, d in enumerate(defects):
+        arr[i].kind = int(d.kind)
+        arr[i].block = int(d.block)
+        arr[i].site[:] = [int(x) for x in d.site]
+        arr[i].extent[:] = [int(x) for x in d.extent]
+        arr[i].pos[:] = [float(x) for x in d.pos]
+        arr[i].charge = float(d.charge)
+    return arr
+
+
+_READ_DTYPE = {LS_READ_TERMS: np.int32}
+
+
+class LatticeSum:
+    """One lattice-sum context: create -> add_defects -> rhosvd_reduce ->
+    eval_slab, each a direct call of the C ABI."""
+
+    def __init__(self, N, box_lo, box_hi, R, sinc_step, t_scale, blocks, precision=LS_FP64, stream=None):
+        self._lib = lib()
+        p = ls_params(int(N), float(box_lo), float(box_hi), int(R), float(sinc_step), float(t_scale),
+                      int(precision), 0)
+        self._blocks = make_blocks(blocks)
+        ctx = C.c_void_p()
+        rc = self._lib.lattice_sum_create(C.byref(ctx), C.byref(p), self._blocks, len(blocks),
+                                          C.c_void_p(stream) if stream else None)
+        if rc != LS_OK:
+            raise LatticeSumError(rc, self._lib.lattice_sum_last_error(None).decode(errors="replace"))
+        self.ctx = ctx
+        self.N = int(N)
+        self.info = None
+
+    @classmethod
+    def from_workload(cls, wl, t_scale, precision=LS_FP64, stream=None):
+        return cls(wl.N, wl.box_lo, wl.box_hi, wl.R, wl.sinc_step, t_scale, wl.blocks, precision, stream)
+
+    def add_defects(self, defects):
+        if len(defects) == 0:
+            return
+        arr = make_defects(defects)
+        _check(self._lib.lattice_sum_add_defects(self.ctx, arr, len(defects)), self.ctx)
+
+    def rhosvd_reduce(self, eps: float, forced_ranks: Optional[Sequence[int]] = None) -> dict:
+        info = ls_tucker_info()
+        fr = (C.c_int32 * 3)(*[int(x) for x in forced_ranks]) if forced_ranks is not None else None
+        _check(self._lib.lattice_sum_rhosvd_reduce(self.ctx, float(eps), fr, C.byref(info)), self.ctx)
+        self.info = info.as_dict()
+        return self.info
+
+    def eval_slab(self, z_index: Sequence[int], out_ptr: int, out_dtype=LS_OUT_F64):
+        z = (C.c_int64 * max(len(z_index), 1))(*[int(x) for x in z_index])
+        _check(self._lib.lattice_sum_eval_slab(self.ctx, z, len(z_index), C.c_void_p(out_ptr), out_dtype),
+               self.ctx)
+
+    def eval_slab_torch(self, z_index, dtype=None, out=None):
+        import torch
+        dtype = dtype or torch.float64
+        n = len(z_index)
+        if out is None:
+            out = torch.empty((n, self.N, self.N), dtype=dtype, device="cuda")
+        self.eval_slab(z_index, out.data_ptr(), LS_OUT_F32 if dtype == torch.float32 else LS_OUT_F64)
+        return out
+
+    def read(self, what: int, mode: int = 0) -> np.ndarray:
+        need = C.c_int64()
+        _check(self._lib.lattice_sum_read(self.ctx, what, mode, None, 0, C.byref(need)), self.ctx)
+        dt = _READ_DTYPE.get(what, np.float64)
+        arr = np.empty(need.value // np.dtype(dt).itemsize, dtype=dt)
+        _check(self._lib.lattice_sum_read(self.ctx, what, mode, arr.ctypes.data_as(C.c_void_p), need.value,
+                                          None), self.ctx)
+        return arr
+
+    def factors(self):
+        Z = (C.c_void_p * 3)()
+        core = C.c_void_p()
+        r = (C.c_int32 * 3)()
+        _check(self._lib.lattice_sum_get_factors(self.ctx, Z, C.byref(core), r), self.ctx)
+        return [Z[i] for i in range(3)], core.value, list(r)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self._lib.lattice_sum_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
