@@ -240,6 +240,37 @@ int lattice_sum_profile(int32_t enable);
  */
 int lattice_sum_profile_report(char* buf, int64_t cap, int64_t* needed_bytes);
 
+/*
+ * lattice_sum_eval_slab_noalloc -- slab evaluation that allocates nothing.
+ * No counterpart in the paper: this is an interface for callers that cannot
+ * allocate device memory when they evaluate (for example a host application
+ * that reserves all of its device memory in one arena at start-up and forbids
+ * later allocations, or a latency-critical loop that must not wait on the
+ * driver's allocator). It computes what lattice_sum_eval_slab computes, with
+ * the same FP64 kernels, from Tucker factors the caller passes in:
+ *   Z0, Z1, Z2 -- device, double [r_l][N] (e.g. from lattice_sum_get_factors
+ *                 or a checkpoint), core -- device, double [r0][r1][r2],
+ *   ranks      -- host, 3 entries, z_index -- host, nslab entries in [0, N),
+ *   out_dev    -- device, nslab * N * N elements of out_dtype (caller-owned),
+ *   stream     -- cudaStream_t or NULL.
+ * Its scratch is one file-scope __device__ array of 32 MiB (64 KiB of slab
+ * indices, the rest for the two per-slab products), which every GPU that loads
+ * this library holds until the process exits. A slab needs
+ * 8 * (r0 * r1 + r0 * N) bytes of it; larger requests return LS_ERR_ARG and
+ * compute nothing; more slabs than fit at once are processed in chunks. The
+ * call makes no cudaMalloc, cudaFree or other allocating call. The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture on
+ * the device begins. All calls share the one array, and it keeps the last
+ * call's contents (every element a call reads was written earlier in the same
+ * call, so nothing needs clearing): calls whose kernels overlap on the GPU
+ * (other streams, other host threads) race on it, so serialise them. Errors
+ * are read with lattice_sum_last_error(NULL). Asynchronous on `stream`.
+ */
+int lattice_sum_eval_slab_noalloc(const double* Z0, const double* Z1, const double* Z2, const double* core,
+                                  const int32_t* ranks, int64_t N, const int64_t* z_index, int32_t nslab,
+                                  void* out_dev, int32_t out_dtype, void* stream);
+
 /* Frees every device buffer of the context (stream-ordered) and the context. */
 void lattice_sum_destroy(ls_ctx* ctx);
 

@@ -264,6 +264,7 @@ double quad_max_err(int R, double hs, double s, const std::vector<double>& r) {
 
 namespace ls {
 void count_kernels(int n) { tracer().kernels += n; }
+void set_global_error(const char* msg) { g_create_error = msg; }
 }  // namespace ls
 
 extern "C" {

@@ -36,6 +36,9 @@ struct DevStatus {
 // ---------------------------------------------------------------------------
 void count_kernels(int n);
 
+// message returned by lattice_sum_last_error(NULL) (calls without a context)
+void set_global_error(const char* msg);
+
 // ---------------------------------------------------------------------------
 // launchers implemented in ls_f64.cu (all enqueue on `st`, return cudaError)
 // ---------------------------------------------------------------------------

@@ -26,6 +26,7 @@ LS_OUT_F64, LS_OUT_F32 = 0, 1
 EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_create", "lattice_sum_add_defects",
             "lattice_sum_rhosvd_reduce", "lattice_sum_eval_slab", "lattice_sum_get_factors",
             "lattice_sum_read", "lattice_sum_profile", "lattice_sum_profile_report",
+            "lattice_sum_eval_slab_noalloc",
             "lattice_sum_destroy", "lattice_sum_last_error")
 
 
@@ -77,6 +78,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lattice_sum_read.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64, P(C.c_int64)]
     lib.lattice_sum_profile.argtypes = [C.c_int32]
     lib.lattice_sum_profile_report.argtypes = [C.c_char_p, C.c_int64, P(C.c_int64)]
+    lib.lattice_sum_eval_slab_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                  P(C.c_int32), C.c_int64, P(C.c_int64), C.c_int32,
+                                                  C.c_void_p, C.c_int32, C.c_void_p]
     lib.lattice_sum_destroy.argtypes = [C.c_void_p]
     lib.lattice_sum_destroy.restype = None
     lib.lattice_sum_last_error.argtypes = [C.c_void_p]
@@ -117,6 +121,17 @@ def profile_report() -> dict:
     buf = C.create_string_buffer(need.value + 64)
     _check(lib().lattice_sum_profile_report(buf, need.value + 64, None))
     return json.loads(buf.value.decode())
+
+
+def eval_slab_noalloc(Z, core, ranks, N, z_index, out_ptr, out_dtype=LS_OUT_F64, stream=None):
+    """Slab values from caller-owned Tucker factors (device pointers) with no
+    device allocation inside the library."""
+    r = (C.c_int32 * 3)(*[int(x) for x in ranks])
+    z = (C.c_int64 * max(len(z_index), 1))(*[int(x) for x in z_index])
+    _check(lib().lattice_sum_eval_slab_noalloc(C.c_void_p(Z[0]), C.c_void_p(Z[1]), C.c_void_p(Z[2]),
+                                               C.c_void_p(core), r, int(N), z, len(z_index),
+                                               C.c_void_p(out_ptr), out_dtype,
+                                               C.c_void_p(stream) if stream else None))
 
 
 def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float):
