@@ -69,7 +69,8 @@ extern "C" {
 #define LS_FP64   0   /* every step in FP64 (CUDA-core DFMA)                         */
 #define LS_MIXED  1   /* FP64 shift-sums, Gram, eigen-solver and CholeskyQR2;          */
                       /* projection, core contraction and slab evaluation on tcgen05    */
-                      /* tensor cores as BF16x3 split products with FP32 accumulation   */
+                      /* tensor cores: operands split into three BF16 parts, six MMAs   */
+                      /* per k-step, FP32 accumulation in TMEM                          */
 
 /* defect kinds */
 #define LS_DEFECT_SITES 0  /* sites block[site : site+extent) get charge `charge`     */
@@ -130,7 +131,10 @@ typedef struct {
     double  sigma_discarded[3]; /* (sum_{k>r} sigma_k^2)^(1/2) per mode                  */
     double  sigma_total[3];     /* (sum_k sigma_k^2)^(1/2) per mode                      */
     double  xi_norm;            /* ||xi||_2 with the vector norms folded in              */
-    double  bound_abs;          /* xi_norm * sum_l sigma_discarded[l] (Thm A.1(d))       */
+    double  bound_abs;          /* Thm A.1(d) bound xi_norm * sum_l d_l, with           */
+                                /* d_l^2 = sigma_discarded[l]^2 + C_l * floor_l: the     */
+                                /* eigenvalues of the FP64 Gram matrix are resolved to   */
+                                /* C_l * floor_l, floor_l = 8 u T (u = 2^-53)             */
     int32_t sweeps[3];          /* eigen-solver sweeps per mode                          */
 } ls_tucker_info;
 
@@ -180,7 +184,8 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n);
  * (sum_k s_k^2)^(1/2). The projections P_l = Z_l^T A_l and the core
  * mu = sum_nu xi_nu P1[:,c1] (x) P2[:,c2] (x) P3[:,c3] follow.
  * `forced_ranks` (host, 3 entries or NULL) overrides the eps rule (each
- * clipped to C_l). Fills *info (may be NULL). Synchronises the stream.
+ * clipped to C_l and to the eigenvalues of the FP64 Gram matrix above its
+ * resolution C_l * 8 u T). Fills *info (may be NULL). Synchronises the stream.
  * Errors: LS_ERR_ARG (eps <= 0 and no forced ranks), LS_ERR_STATE (called
  * twice), LS_ERR_NOCONVERGE, LS_ERR_TIMEOUT, LS_ERR_OOM, LS_ERR_CUDA.
  */

@@ -128,7 +128,6 @@ struct ls_ctx {
     int32_t* d_tcol = nullptr;
     double* d_xi = nullptr;
     double* d_xin = nullptr;
-    DevStatus* d_status = nullptr;
     std::vector<void*> allocs;
 };
 
@@ -349,7 +348,6 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
     int rc = LS_OK;
     {
         cudaError_t e2 = dalloc(ctx, &ctx->d_g, (int64_t)R * 2 * N);
-        if (e2 == cudaSuccess) e2 = dalloc(ctx, &ctx->d_status, 1);
         Scope sc_gen("genvec", ctx->st);
         if (e2 == cudaSuccess) e2 = launch_genvec(ctx->d_g, R, N, ctx->h, p.sinc_step, p.t_scale, ctx->st);
         if (e2 != cudaSuccess) rc = fail(ctx, LS_ERR_CUDA, "create: %s", cudaGetErrorString(e2));
@@ -464,18 +462,22 @@ int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ran
     CU(dalloc(ctx, &ctx->d_xi, T));
     CU(dalloc(ctx, &ctx->d_xin, T));
     CU(cudaMemcpyAsync(ctx->d_tcol, ctx->tcol.data(), 3 * T * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    count_h2d((int64_t)(3 * T * sizeof(int32_t)));
+    count_h2d(3 * T * sizeof(int32_t));
     CU(cudaMemcpyAsync(ctx->d_xi, ctx->xi.data(), T * sizeof(double), cudaMemcpyHostToDevice, st));
-    count_h2d((int64_t)(T * sizeof(double)));
-    double sel[3][3];
+    count_h2d(T * sizeof(double));
+    DevStatus* d_st = nullptr;   // one status block per mode + one for CholeskyQR2
+    CU(dalloc(ctx, &d_st, 4));
+    CU(cudaMemsetAsync(d_st, 0, 4 * sizeof(DevStatus), st));
     double* d_sel = nullptr;
     CU(dalloc(ctx, &d_sel, 9));
     double* d_G[3];
     double* d_V[3];
+    double* d_snap[3];
     int32_t* d_perm[3];
     double* d_isl[3];
     double* d_w[3];
-    int sweeps[3] = {0, 0, 0};
+    JacobiJob jobs[3];
+    // (c1) unit vectors, weighted Gram matrices, eigen-decomposition of all modes at once
     for (int l = 0; l < 3; ++l) {
         ModeCols& mc = ctx->mode[l];
         const int64_t C = mc.C;
@@ -483,77 +485,143 @@ int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ran
         CU(dalloc(ctx, &ctx->d_sigma[l], C));
         CU(dalloc(ctx, &d_G[l], C * C));
         CU(dalloc(ctx, &d_V[l], C * C));
+        CU(dalloc(ctx, &d_snap[l], 6 * (C / 2 + 1)));
         CU(dalloc(ctx, &d_perm[l], C));
         CU(dalloc(ctx, &d_isl[l], C));
         CU(dalloc(ctx, &d_w[l], C));
         std::vector<double> w(C);
         for (int64_t c = 0; c < C; ++c) w[c] = sqrt((double)mc.count[c]);
         CU(cudaMemcpyAsync(d_w[l], w.data(), C * sizeof(double), cudaMemcpyHostToDevice, st));
-        count_h2d((int64_t)(C * sizeof(double)));
+        count_h2d(C * sizeof(double));
         { Scope sc("norms", st); CU(launch_norm_columns(mc.d_cols, C, N, ctx->d_norms[l], st)); }
         { Scope sc("gram", st); CU(launch_gram_weighted(mc.d_cols, C, N, d_w[l], d_G[l], st)); }
         CU(launch_identity(d_V[l], C, st));
-        CU(cudaMemsetAsync(ctx->d_status, 0, sizeof(DevStatus), st));
-        const double abs_floor = 1e-300;
-        { Scope sc("jacobi", st); CU(launch_jacobi(d_G[l], d_V[l], C, ctx->d_status, 60, 1e-15, abs_floor, ctx->num_sms, st)); }
-        DevStatus hs;
-        CU(cudaMemcpyAsync(&hs, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
-        count_d2h((int64_t)(sizeof(DevStatus)));
-        CU(cudaStreamSynchronize(st));
-        if (hs.flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Jacobi grid barrier timed out (mode %d)", l);
-        if (hs.flag == FLAG_NOCONVERGE || hs.sweeps <= 0)
-            return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: Jacobi did not converge (mode %d)", l);
-        sweeps[l] = hs.sweeps;
-        const int forced = forced_ranks ? std::max(1, forced_ranks[l]) : 0;
-        { Scope sc("select", st); CU(launch_sort_select(d_G[l], C, eps, forced, d_perm[l], ctx->d_sigma[l], d_isl[l], d_sel + 3 * l, st)); }
+        // entries below the rounding noise of the FP64 Gram matrix (~ u * trace, trace = T) are
+        // left alone: rotating them only reshuffles noise
+        // directions whose Rayleigh quotients both stay below tau = 1e-3 eps^2 T / C are discarded
+        // together whatever their mixing (their block has trace < 1e-3 eps^2 T); forced ranks
+        // resolve everything
+        const double tau = forced_ranks ? 0.0 : 1e-3 * eps * eps * (double)T / (double)C;
+        jobs[l] = JacobiJob{d_G[l], d_V[l], d_snap[l], d_st + l, C, 8.0 * 1.1102230246251565e-16 * (double)T, tau};
     }
+    { Scope sc("jacobi", st); CU(launch_jacobi_multi(jobs, 3, 60, 1e-14, ctx->num_sms, st)); }
+    for (int l = 0; l < 3; ++l) {
+        const int forced = forced_ranks ? std::max(1, forced_ranks[l]) : 0;
+        Scope sc("select", st);
+        const double resolution = (double)ctx->mode[l].C * jobs[l].abs_floor;
+        CU(launch_sort_select(d_G[l], ctx->mode[l].C, eps, forced, resolution, d_perm[l], ctx->d_sigma[l], d_isl[l],
+                              d_sel + 3 * l, st));
+    }
+    DevStatus hs[4];
+    double sel[3][3];
+    CU(cudaMemcpyAsync(hs, d_st, 3 * sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    count_d2h(3 * sizeof(DevStatus));
     CU(cudaMemcpyAsync(sel, d_sel, sizeof sel, cudaMemcpyDeviceToHost, st));
-    count_d2h((int64_t)(sizeof sel));
+    count_d2h(sizeof sel);
     CU(cudaStreamSynchronize(st));
-    for (int l = 0; l < 3; ++l) ctx->r[l] = (int32_t)sel[l][0];
+    int sweeps[3];
+    for (int l = 0; l < 3; ++l) {
+        if (hs[l].flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Jacobi grid barrier timed out (mode %d)", l);
+        if (hs[l].flag == FLAG_NOCONVERGE || hs[l].sweeps <= 0)
+            return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: Jacobi did not converge (mode %d)", l);
+        sweeps[l] = hs[l].sweeps;
+        ctx->r[l] = (int32_t)sel[l][0];
+    }
+    // (c1) basis + CholeskyQR2, (c2) projection
     for (int l = 0; l < 3; ++l) {
         ModeCols& mc = ctx->mode[l];
         const int64_t C = mc.C;
         const int r = ctx->r[l];
         double* work = nullptr;
+        double* ytmp = nullptr;
         CU(dalloc(ctx, &ctx->d_Z[l], (int64_t)r * N));
         CU(dalloc(ctx, &ctx->d_P[l], (int64_t)r * C));
-        CU(dalloc(ctx, &work, (int64_t)r * r));
+        CU(dalloc(ctx, &work, 2 * (int64_t)r * r));
+        CU(dalloc(ctx, &ytmp, (int64_t)r * N));
         { Scope sc("basis", st); CU(launch_basis(d_V[l], C, d_perm[l], d_isl[l], d_w[l], mc.d_cols, N, r, ctx->d_Z[l], st)); }
-        CU(cudaMemsetAsync(ctx->d_status, 0, sizeof(DevStatus), st));
-        { Scope sc("cholqr2", st); CU(launch_cholqr2(ctx->d_Z[l], r, N, work, ctx->d_status, ctx->num_sms, st)); }
-        { Scope sc("project", st); CU(launch_project(ctx->d_Z[l], r, mc.d_cols, C, N, ctx->d_P[l], st)); }
-        dfree(ctx, work);
-        DevStatus hs;
-        CU(cudaMemcpyAsync(&hs, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
-        count_d2h((int64_t)(sizeof(DevStatus)));
-        CU(cudaStreamSynchronize(st));
-        if (hs.flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Cholesky grid barrier timed out");
-        if (hs.flag == FLAG_NOT_SPD) return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: CholeskyQR2 met a non-positive pivot (mode %d)", l);
-    }
-    { Scope sc("fold", st); CU(launch_fold_norms(ctx->d_xi, ctx->d_tcol, T, ctx->d_norms[0], ctx->d_norms[1], ctx->d_norms[2], ctx->d_xin, st)); }
-    const int64_t core_n = (int64_t)ctx->r[0] * ctx->r[1] * ctx->r[2];
-    CU(dalloc(ctx, &ctx->d_B, core_n));
-    int32_t Cs[3] = {(int32_t)ctx->mode[0].C, (int32_t)ctx->mode[1].C, (int32_t)ctx->mode[2].C};
-    {
-        Scope sc_core("core", st);
+        { Scope sc("cholqr2", st); CU(launch_cholqr2(ctx->d_Z[l], ytmp, r, N, work, d_st + 3, ctx->num_sms, st)); }
         if (ctx->p.precision == LS_MIXED) {
-            int rc = tc_core(ctx->d_P[0], ctx->d_P[1], ctx->d_P[2], Cs, ctx->r, ctx->d_tcol, ctx->d_xin, T, ctx->d_B,
-                             ctx->num_sms, st, &ctx->err);
+            Scope sc("project", st);
+            int rc = tc_project(ctx->d_Z[l], r, mc.d_cols, C, N, ctx->d_P[l], st, &ctx->err);
             if (rc != LS_OK) return rc;
         } else {
-            CU(launch_core_f64(ctx->d_P[0], ctx->d_P[1], ctx->d_P[2], Cs, ctx->r, ctx->d_tcol, ctx->d_xin, T, ctx->d_B,
-                               st));
+            Scope sc("project", st);
+            CU(launch_project(ctx->d_Z[l], r, mc.d_cols, C, N, ctx->d_P[l], st));
+        }
+        dfree(ctx, work);
+        dfree(ctx, ytmp);
+    }
+    { Scope sc("fold", st); CU(launch_fold_norms(ctx->d_xi, ctx->d_tcol, T, ctx->d_norms[0], ctx->d_norms[1], ctx->d_norms[2], ctx->d_xin, st)); }
+    // (c3) core: terms grouped by their mode-0 vector (counting sort on the host)
+    int32_t Cs[3] = {(int32_t)ctx->mode[0].C, (int32_t)ctx->mode[1].C, (int32_t)ctx->mode[2].C};
+    std::vector<int32_t> off(Cs[0] + 1, 0), perm(T);
+    for (int64_t t = 0; t < T; ++t) off[ctx->tcol[3 * t] + 1] += 1;
+    for (int c = 0; c < Cs[0]; ++c) off[c + 1] += off[c];
+    {
+        std::vector<int32_t> pos(off.begin(), off.end() - 1);
+        for (int64_t t = 0; t < T; ++t) perm[pos[ctx->tcol[3 * t]]++] = (int32_t)t;
+    }
+    int32_t* d_perm_t = nullptr;
+    int32_t* d_off = nullptr;
+    CU(dalloc(ctx, &d_perm_t, T));
+    CU(dalloc(ctx, &d_off, Cs[0] + 1));
+    CU(cudaMemcpyAsync(d_perm_t, perm.data(), T * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    count_h2d(T * sizeof(int32_t));
+    CU(cudaMemcpyAsync(d_off, off.data(), (Cs[0] + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    count_h2d((Cs[0] + 1) * sizeof(int32_t));
+    const int64_t core_n = (int64_t)ctx->r[0] * ctx->r[1] * ctx->r[2];
+    CU(dalloc(ctx, &ctx->d_B, core_n));
+    {
+        Scope sc_core("core", st);
+        const int64_t nn = (int64_t)ctx->r[1] * ctx->r[2];
+        const int64_t w_cols = std::max<int64_t>(1, std::min<int64_t>(Cs[0], (int64_t)(32 << 20) / std::max<int64_t>(nn, 1)));
+        if (ctx->p.precision == LS_MIXED) {
+            int rc = tc_core(ctx->d_P[0], ctx->d_P[1], ctx->d_P[2], Cs, ctx->r, ctx->d_tcol, ctx->d_xin, d_perm_t, d_off,
+                             T, ctx->d_B, ctx->num_sms, st, &ctx->err);
+            if (rc != LS_OK) return rc;
+        } else {
+            double* P1t = nullptr;
+            double* P2t = nullptr;
+            double* W = nullptr;
+            CU(dalloc(ctx, &P1t, (int64_t)Cs[1] * ctx->r[1]));
+            CU(dalloc(ctx, &P2t, (int64_t)Cs[2] * ctx->r[2]));
+            CU(dalloc(ctx, &W, w_cols * nn));
+            CU(launch_transpose(ctx->d_P[1], ctx->r[1], Cs[1], P1t, st));
+            CU(launch_transpose(ctx->d_P[2], ctx->r[2], Cs[2], P2t, st));
+            CU(launch_core_f64(ctx->d_P[0], P1t, P2t, Cs, ctx->r, ctx->d_tcol, ctx->d_xin, d_perm_t, d_off, W, w_cols,
+                               ctx->d_B, st));
+            dfree(ctx, P1t);
+            dfree(ctx, P2t);
+            dfree(ctx, W);
         }
     }
     for (int l = 0; l < 3; ++l) {
         dfree(ctx, d_G[l]);
         dfree(ctx, d_V[l]);
+        dfree(ctx, d_snap[l]);
         dfree(ctx, d_perm[l]);
         dfree(ctx, d_isl[l]);
         dfree(ctx, d_w[l]);
     }
+    dfree(ctx, d_perm_t);
+    dfree(ctx, d_off);
     dfree(ctx, d_sel);
+    // CholeskyQR2 status (read together with the info below)
+    CU(cudaMemcpyAsync(&hs[3], d_st + 3, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    count_d2h(sizeof(DevStatus));
+    double xin_norm2 = 0.0;
+    if (info) {
+        std::vector<double> xin(T);
+        CU(cudaMemcpyAsync(xin.data(), ctx->d_xin, T * sizeof(double), cudaMemcpyDeviceToHost, st));
+        count_d2h(T * sizeof(double));
+        CU(cudaStreamSynchronize(st));
+        for (double v : xin) xin_norm2 += v * v;
+    } else {
+        CU(cudaStreamSynchronize(st));
+    }
+    dfree(ctx, d_st);
+    if (hs[3].flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Cholesky grid barrier timed out");
+    if (hs[3].flag == FLAG_NOT_SPD) return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: CholeskyQR2 met a non-positive pivot");
     if (info) {
         memset(info, 0, sizeof *info);
         double ssum = 0.0;
@@ -563,17 +631,12 @@ int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ran
             info->sigma_discarded[l] = sqrt(std::max(sel[l][1], 0.0));
             info->sigma_total[l] = sqrt(std::max(sel[l][2], 0.0));
             info->sweeps[l] = sweeps[l];
-            ssum += info->sigma_discarded[l];
+            // Thm A.1(d) with the resolution of the Gram route: after the eigen-solver every
+            // off-diagonal entry is below the floor, so each eigenvalue is known to C * floor
+            ssum += sqrt(std::max(sel[l][1], 0.0) + (double)Cs[l] * jobs[l].abs_floor);
         }
         info->T = T;
-        // ||xi|| with the norms folded in: a small reduction on the host copy
-        std::vector<double> xin(T);
-        CU(cudaMemcpyAsync(xin.data(), ctx->d_xin, T * sizeof(double), cudaMemcpyDeviceToHost, st));
-        count_d2h((int64_t)(T * sizeof(double)));
-        CU(cudaStreamSynchronize(st));
-        double s2 = 0.0;
-        for (double v : xin) s2 += v * v;
-        info->xi_norm = sqrt(s2);
+        info->xi_norm = sqrt(xin_norm2);
         info->bound_abs = info->xi_norm * ssum;
     }
     CU(cudaGetLastError());

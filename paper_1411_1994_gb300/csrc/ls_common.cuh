@@ -63,16 +63,24 @@ cudaError_t launch_gram_weighted(const double* a, int64_t C, int64_t N, const do
 // V = I (C x C).
 cudaError_t launch_identity(double* V, int64_t C, cudaStream_t st);
 
-// Parallel cyclic Jacobi on symmetric G (C x C, in place) accumulating V.
-// Cooperative launch; st must be the context stream. Returns the sweeps
-// used in status->sweeps (negative if the limit was hit).
-cudaError_t launch_jacobi(double* G, double* V, int64_t C, DevStatus* status, int max_sweeps,
-                          double tol, double abs_floor, int num_sms, cudaStream_t st);
+// Parallel cyclic Jacobi on up to three symmetric matrices at once (one
+// cooperative launch, CTAs split between the jobs). Each job: G (C x C, only
+// the upper triangle is used; in place -> eigenvalues on the diagonal), V
+// (C x C, starts as I -> eigenvectors in columns), snap (>= 6 * (C/2+1)
+// doubles of scratch), st (zeroed status; sweeps used, or a negative count if
+// the limit was hit). Rotations with |a_pq| below abs_floor, below
+// tol * sqrt(|a_pp a_qq|), or with both a_pp and a_qq below tau are skipped.
+struct JacobiJob {
+    double* G; double* V; double* snap; DevStatus* st; int64_t C; double abs_floor; double tau;
+};
+cudaError_t launch_jacobi_multi(const JacobiJob* jobs, int njobs, int max_sweeps, double tol, int num_sms,
+                                cudaStream_t st);
 
 // Sort eigenvalues (diag of G) descending: perm[k], lam[k]; select the rank
-// (forced if forced > 0) and write out[0] = r, out[1] = discarded^2,
-// out[2] = total (as doubles); also inv_sqrt_lam[k] = 1/sqrt(lam[k]).
-cudaError_t launch_sort_select(const double* G, int64_t C, double eps, int forced, int32_t* perm,
+// (forced if forced > 0, then clipped to the eigenvalues above `resolution`)
+// and write out[0] = r, out[1] = discarded^2, out[2] = total (as doubles);
+// also inv_sqrt_lam[k] = 1/sqrt(lam[k]) and lam[k] <- sqrt(max(lam[k], 0)).
+cudaError_t launch_sort_select(const double* G, int64_t C, double eps, int forced, double resolution, int32_t* perm,
                                double* lam, double* inv_sqrt_lam, double* out, cudaStream_t st);
 
 // Y[k][i] = inv_sqrt_lam[k] * sum_c V[c][perm[k]] w[c] a[c][i]  (k < r).
@@ -80,9 +88,9 @@ cudaError_t launch_basis(const double* V, int64_t C, const int32_t* perm, const 
                          const double* w, const double* a, int64_t N, int r, double* Y,
                          cudaStream_t st);
 
-// Z <- orthonormalised rows of Y (r x N) by CholeskyQR2 (FP64); work holds
-// >= r*r doubles.
-cudaError_t launch_cholqr2(double* Y, int r, int64_t N, double* work, DevStatus* status, int num_sms,
+// Y <- orthonormalised rows of Y (r x N) by CholeskyQR2 (FP64): twice
+// G = Y Y^T, G = L L^T, Y <- L^{-1} Y. Ytmp holds r*N doubles, work >= 2 r^2.
+cudaError_t launch_cholqr2(double* Y, double* Ytmp, int r, int64_t N, double* work, DevStatus* status, int num_sms,
                            cudaStream_t st);
 
 // P[k][c] = sum_i Z[k][i] a[c][i]   (r x C).
@@ -93,10 +101,21 @@ cudaError_t launch_project(const double* Z, int r, const double* a, int64_t C, i
 cudaError_t launch_fold_norms(const double* xi, const int32_t* tcol, int64_t T, const double* n0,
                               const double* n1, const double* n2, double* xin, cudaStream_t st);
 
-// Core (FP64): B[i][j][k] = sum_t xin[t] P0[i][c0] P1[j][c1] P2[k][c2].
-cudaError_t launch_core_f64(const double* P0, const double* P1, const double* P2, const int32_t* C,
-                            const int32_t* r, const int32_t* tcol, const double* xin, int64_t T,
-                            double* B, cudaStream_t st);
+// out = in^T for a rows x cols row-major matrix.
+cudaError_t launch_transpose(const double* in, int64_t rows, int64_t cols, double* out, cudaStream_t st);
+
+// Core (FP64): B[i][j][k] = sum_t xin[t] P0[i][c0] P1[j][c1] P2[k][c2] in two
+// exact steps: terms grouped by c0 (perm/off: terms sorted by c0, CSR
+// offsets) give W[c0][j*r2+k] = sum_{t in group} xin P1[j][c1] P2[k][c2]
+// (P1t, P2t are the transposed projections), then B_(0) = P0 W, in chunks of
+// w_cols groups (W holds w_cols * r1 * r2 doubles).
+cudaError_t launch_core_f64(const double* P0, const double* P1t, const double* P2t, const int32_t* C, const int32_t* r,
+                            const int32_t* tcol, const double* xin, const int32_t* perm, const int32_t* off,
+                            double* W, int64_t w_cols, double* B, cudaStream_t st);
+
+// M[(a*r1 + b)][s] = sum_k B[a][b][k] Z2[k][zidx[s]]  (first n-mode product of a slab).
+cudaError_t launch_eval_m(const double* Z2, const int32_t* r, const double* B, int64_t N, const int32_t* zidx,
+                          int nslab, double* M, cudaStream_t st);
 
 // Slab evaluation (FP64 arithmetic): out[s][x][y] for nslab z indices.
 // work holds >= r0*r1*nslab + r0*N*nslab doubles.

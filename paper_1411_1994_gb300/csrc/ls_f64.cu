@@ -7,8 +7,9 @@
 // the tile loaders, and the two inherently sequential algorithms (Jacobi
 // eigen-solver, blocked Cholesky) run as cooperative grids with a bounded
 // software grid barrier instead of one launch per step.
-#include <cooperative_groups.h>
 #include <math.h>
+
+#include <algorithm>
 
 #include "ls_common.cuh"
 
@@ -23,10 +24,10 @@ constexpr long long kSpinLimit = 1LL << 24;   // ~1-2 s of polling with nanoslee
 // co-resident (cooperative launch). On timeout the flag is raised and every
 // CTA returns false.
 // ---------------------------------------------------------------------------
-__device__ bool grid_barrier(DevStatus* st) {
+__device__ bool group_barrier(DevStatus* st, unsigned int nblocks) {
     __shared__ int s_ok;
     __syncthreads();
-    if (gridDim.x == 1) return true;
+    if (nblocks <= 1) return true;
     if (threadIdx.x == 0) {
         volatile unsigned int* vgen = &st->bar_gen;
         volatile int* vflag = &st->flag;
@@ -34,7 +35,7 @@ __device__ bool grid_barrier(DevStatus* st) {
         __threadfence();
         unsigned int arrived = atomicAdd(&st->bar_count, 1u);
         int ok = 1;
-        if (arrived == gridDim.x - 1) {
+        if (arrived == nblocks - 1) {
             atomicExch(&st->bar_count, 0u);
             __threadfence();
             atomicAdd(&st->bar_gen, 1u);
@@ -43,7 +44,7 @@ __device__ bool grid_barrier(DevStatus* st) {
             while (*vgen == g) {
                 if (*vflag != FLAG_OK) { ok = 0; break; }
                 if (++it > kSpinLimit) { atomicCAS(&st->flag, FLAG_OK, FLAG_TIMEOUT); ok = 0; break; }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -53,6 +54,8 @@ __device__ bool grid_barrier(DevStatus* st) {
     __syncthreads();
     return s_ok != 0;
 }
+
+__device__ __forceinline__ bool grid_barrier(DevStatus* st) { return group_barrier(st, gridDim.x); }
 
 // ---------------------------------------------------------------------------
 // G0 / G1 / G2 and small elementwise kernels
@@ -288,103 +291,194 @@ __device__ __forceinline__ void rr_pair(int t, int i, int Cp, int& p, int& q) {
     p = min(a, b);
     q = max(a, b);
 }
+// partner of index a in round t, and the index of its pair
+__device__ __forceinline__ int rr_partner(int t, int a, int n1) {
+    if (a == n1) return t;
+    if (a == t) return n1;
+    return ((2 * t - a) % n1 + n1) % n1;
+}
+__device__ __forceinline__ int rr_index(int t, int a, int n1) {
+    if (a == n1 || a == t) return 0;
+    const int d = ((a - t) % n1 + n1) % n1;
+    return min(d, n1 - d);
+}
 
-__global__ void __launch_bounds__(256) k_jacobi(double* G, double* V, int C, DevStatus* st, int max_sweeps,
-                                                double tol, double abs_floor) {
+// Parallel cyclic Jacobi for several symmetric matrices at once: CTAs
+// [cta0, cta0 + ncta) of the grid work on job m with their own bounded group
+// barrier. Only the upper triangle of G is read and written. One barrier per
+// round: the three pivot entries of every pair of the next round are copied to
+// a double-buffered snapshot by the threads that write them, so the rotations
+// of a round never read entries that the same round overwrites. A rotation is
+// skipped when |a_pq| is below the absolute floor (the rounding noise of the
+// FP64 Gram matrix), below tol * sqrt(|a_pp a_qq|), or when both diagonal
+// entries are below tau: such directions lie far below the truncation
+// threshold, are discarded together, and mixing them changes neither the
+// retained subspace nor the trace of the discarded block. A sweep without
+// rotations ends the iteration.
+struct JacobiMode {
+    double* G; double* V; double* snap; DevStatus* st; int C; int cta0; int ncta; double abs_floor; double tau;
+};
+struct JacobiArgs {
+    JacobiMode m[3]; int nmodes; int max_sweeps; double tol;
+};
+
+__device__ __forceinline__ double& gsym(double* G, int C, int a, int b) {
+    return a <= b ? G[(int64_t)a * C + b] : G[(int64_t)b * C + a];
+}
+
+__global__ void __launch_bounds__(256) k_jacobi_multi(JacobiArgs A) {
+    int mi = 0;
+    while (mi + 1 < A.nmodes && (int)blockIdx.x >= A.m[mi + 1].cta0) ++mi;
+    const JacobiMode J = A.m[mi];
+    const int lb = blockIdx.x - J.cta0, nb = J.ncta;
+    const int C = J.C, Cp = C + (C & 1), P = Cp / 2, n1 = Cp - 1;
+    // shared: c[P], s[P] (double), p[P], q[P], next partner[Cp], next pair index[Cp] (int)
     extern __shared__ double sm[];
-    const int Cp = C + (C & 1);
-    const int P = Cp / 2;
     double* sc = sm;
     double* ss = sm + P;
+    int* sp = (int*)(ss + P);
+    int* sq = sp + P;
+    int* npart = sq + P;
+    int* nidx = npart + Cp;
     __shared__ unsigned int s_active;
-    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double* G = J.G;
+    double* V = J.V;
+    const int64_t nthr = (int64_t)nb * blockDim.x;
+    const int64_t gtid = (int64_t)lb * blockDim.x + threadIdx.x;
     const int64_t items_g = (int64_t)P * P;
     const int64_t items = items_g + (int64_t)C * P;
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int64_t i = gtid; i < P; i += nthr) {
+        int p, q;
+        rr_pair(0, (int)i, Cp, p, q);
+        J.snap[3 * i + 0] = G[(int64_t)p * C + p];
+        J.snap[3 * i + 1] = q < C ? G[(int64_t)q * C + q] : 0.0;
+        J.snap[3 * i + 2] = q < C ? G[(int64_t)p * C + q] : 0.0;
+    }
+    if (!group_barrier(J.st, nb)) return;
+    int cur = 0;
+    for (int sweep = 0; sweep < A.max_sweeps; ++sweep) {
         if (threadIdx.x == 0) s_active = 0;
         __syncthreads();
-        for (int t = 0; t < Cp - 1; ++t) {
+        for (int t = 0; t < n1; ++t) {
+            const int tn = (t + 1 == n1) ? 0 : t + 1;
+            const double* D = J.snap + (int64_t)cur * 3 * P;
+            double* Dn = J.snap + (int64_t)(cur ^ 1) * 3 * P;
             for (int i = threadIdx.x; i < P; i += blockDim.x) {
                 int p, q;
                 rr_pair(t, i, Cp, p, q);
+                sp[i] = p;
+                sq[i] = q;
                 double c = 1.0, s = 0.0;
                 if (q < C) {
-                    const double app = __ldcg(G + (int64_t)p * C + p);
-                    const double aqq = __ldcg(G + (int64_t)q * C + q);
-                    const double apq = __ldcg(G + (int64_t)p * C + q);
-                    if (fabs(apq) > abs_floor && fabs(apq) > tol * sqrt(fabs(app * aqq))) {
-                        const double theta = (aqq - app) / (2.0 * apq);
-                        const double tt = copysign(1.0, theta) / (fabs(theta) + sqrt(1.0 + theta * theta));
-                        c = 1.0 / sqrt(1.0 + tt * tt);
-                        s = tt * c;
-                        if (blockIdx.x == 0) atomicAdd(&s_active, 1u);
+                    const double app = __ldcg(D + 3 * i), aqq = __ldcg(D + 3 * i + 1), apq = __ldcg(D + 3 * i + 2);
+                    if (fabs(apq) > J.abs_floor && fmax(app, aqq) >= J.tau &&
+                        fabs(apq) * fabs(apq) > A.tol * A.tol * fabs(app * aqq)) {
+                        // The angle only steers convergence, so it is taken in FP32; the rotation
+                        // itself is orthogonal to FP64 rounding: c = (1 + t^2)^(-1/2) by two FP64
+                        // Newton steps from the FP32 estimate, s = t c.
+                        const float theta = (float)((aqq - app) / (2.0 * apq));
+                        const float tf = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+                        const double tt = (double)tf;
+                        const double x = fma(tt, tt, 1.0);
+                        double cc = (double)rsqrtf((float)x);
+                        cc = cc * fma(-0.5 * x, cc * cc, 1.5);
+                        cc = cc * fma(-0.5 * x, cc * cc, 1.5);
+                        c = cc;
+                        s = tt * cc;
+                        if (lb == 0) atomicAdd(&s_active, 1u);
                     }
                 }
                 sc[i] = c;
                 ss[i] = s;
             }
-            // every CTA must have read this round's pivots before any CTA
-            // overwrites them
-            if (!grid_barrier(st)) return;
+            for (int a = threadIdx.x; a < Cp; a += blockDim.x) {
+                npart[a] = rr_partner(tn, a, n1);
+                nidx[a] = rr_index(tn, a, n1);
+            }
+            __syncthreads();
+            if (t == n1 - 1 && lb == 0 && threadIdx.x == 0) J.st->sweep_active[sweep & 63] = s_active;
             for (int64_t it = gtid; it < items; it += nthr) {
                 if (it < items_g) {
-                    const int i = (int)(it / P), i2 = (int)(it % P);
+                    const int i = (int)(it / P), i2 = (int)(it - (int64_t)i * P);
+                    if (i2 < i) continue;                       // upper block triangle only
                     const double c1 = sc[i], s1 = ss[i], c2 = sc[i2], s2 = ss[i2];
-                    if (s1 == 0.0 && s2 == 0.0) continue;
-                    int p, q, p2, q2;
-                    rr_pair(t, i, Cp, p, q);
-                    rr_pair(t, i2, Cp, p2, q2);
-                    const bool vq = q < C, vq2 = q2 < C;   // p, p2 < C always (p < q <= Cp-1)
-                    double xpp = __ldcg(G + (int64_t)p * C + p2);
-                    double xpq = vq2 ? __ldcg(G + (int64_t)p * C + q2) : 0.0;
-                    double xqp = vq ? __ldcg(G + (int64_t)q * C + p2) : 0.0;
-                    double xqq = (vq && vq2) ? __ldcg(G + (int64_t)q * C + q2) : 0.0;
-                    // rows: J^T X
-                    const double ypp = c1 * xpp - s1 * xqp, ypq = c1 * xpq - s1 * xqq;
-                    const double yqp = s1 * xpp + c1 * xqp, yqq = s1 * xpq + c1 * xqq;
-                    // columns: Y J
-                    double zpp = c2 * ypp - s2 * ypq, zpq = s2 * ypp + c2 * ypq;
-                    double zqp = c2 * yqp - s2 * yqq, zqq = s2 * yqp + c2 * yqq;
-                    if (i == i2 && s1 != 0.0) { zpq = 0.0; zqp = 0.0; }
-                    __stcg(G + (int64_t)p * C + p2, zpp);
-                    if (vq2) __stcg(G + (int64_t)p * C + q2, zpq);
-                    if (vq) __stcg(G + (int64_t)q * C + p2, zqp);
-                    if (vq && vq2) __stcg(G + (int64_t)q * C + q2, zqq);
+                    const int p = sp[i], q = sq[i], p2 = sp[i2], q2 = sq[i2];
+                    const bool vq = q < C, vq2 = q2 < C;        // p, p2 < C always
+                    const int rows[2] = {p, q}, cols[2] = {p2, q2};
+                    int piv = 0;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
+#pragma unroll
+                        for (int v = 0; v < 2; ++v) {
+                            const int a = rows[u], b = cols[v];
+                            if (a >= C || b >= C) continue;
+                            if (i == i2 && u > v) continue;      // (q,p) of a diagonal block = (p,q)
+                            if (a == b || npart[a] == b) piv |= 1 << (2 * u + v);
+                        }
+                    const bool active = (s1 != 0.0 || s2 != 0.0);
+                    if (!active && !piv) continue;
+                    double x[4];
+                    x[0] = __ldcg(&gsym(G, C, p, p2));
+                    x[1] = vq2 ? __ldcg(&gsym(G, C, p, q2)) : 0.0;
+                    x[2] = vq ? __ldcg(&gsym(G, C, q, p2)) : 0.0;
+                    x[3] = (vq && vq2) ? __ldcg(&gsym(G, C, q, q2)) : 0.0;
+                    double z[4] = {x[0], x[1], x[2], x[3]};
+                    if (active) {
+                        const double ypp = c1 * x[0] - s1 * x[2], ypq = c1 * x[1] - s1 * x[3];
+                        const double yqp = s1 * x[0] + c1 * x[2], yqq = s1 * x[1] + c1 * x[3];
+                        z[0] = c2 * ypp - s2 * ypq;
+                        z[1] = s2 * ypp + c2 * ypq;
+                        z[2] = c2 * yqp - s2 * yqq;
+                        z[3] = s2 * yqp + c2 * yqq;
+                        __stcg(&gsym(G, C, p, p2), z[0]);
+                        if (vq2) __stcg(&gsym(G, C, p, q2), z[1]);
+                        if (vq && i != i2) __stcg(&gsym(G, C, q, p2), z[2]);
+                        if (vq && vq2) __stcg(&gsym(G, C, q, q2), z[3]);
+                    }
+                    if (piv) {
+#pragma unroll
+                        for (int u = 0; u < 2; ++u)
+#pragma unroll
+                            for (int v = 0; v < 2; ++v) {
+                                if (!(piv & (1 << (2 * u + v)))) continue;
+                                const int a = min(rows[u], cols[v]), b = max(rows[u], cols[v]);
+                                const int k = nidx[a];
+                                const int slot = (a == b) ? (a < npart[a] ? 0 : 1) : 2;
+                                __stcg(Dn + 3 * k + slot, z[2 * u + v]);
+                            }
+                    }
                 } else {
                     const int64_t r = it - items_g;
-                    const int j = (int)(r / P), i2 = (int)(r % P);
+                    const int j = (int)(r / P), i2 = (int)(r - (int64_t)j * P);
                     const double c2 = sc[i2], s2 = ss[i2];
                     if (s2 == 0.0) continue;
-                    int p2, q2;
-                    rr_pair(t, i2, Cp, p2, q2);
+                    const int p2 = sp[i2], q2 = sq[i2];
                     const double vp = __ldcg(V + (int64_t)j * C + p2);
-                    const double vq = __ldcg(V + (int64_t)j * C + q2);
-                    __stcg(V + (int64_t)j * C + p2, c2 * vp - s2 * vq);
-                    __stcg(V + (int64_t)j * C + q2, s2 * vp + c2 * vq);
+                    const double vv = __ldcg(V + (int64_t)j * C + q2);
+                    __stcg(V + (int64_t)j * C + p2, c2 * vp - s2 * vv);
+                    __stcg(V + (int64_t)j * C + q2, s2 * vp + c2 * vv);
                 }
             }
-            if (!grid_barrier(st)) return;
+            if (!group_barrier(J.st, nb)) return;
+            cur ^= 1;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) st->sweep_active[sweep & 63] = s_active;
-        if (!grid_barrier(st)) return;
-        const unsigned int act = __ldcg(&st->sweep_active[sweep & 63]);
+        const unsigned int act = __ldcg(&J.st->sweep_active[sweep & 63]);
         if (act == 0) {
-            if (gtid == 0) st->sweeps = sweep + 1;
+            if (gtid == 0) J.st->sweeps = sweep + 1;
             return;
         }
     }
     if (gtid == 0) {
-        st->sweeps = -max_sweeps;
-        atomicCAS(&st->flag, FLAG_OK, FLAG_NOCONVERGE);
+        J.st->sweeps = -A.max_sweeps;
+        atomicCAS(&J.st->flag, FLAG_OK, FLAG_NOCONVERGE);
     }
 }
 
 // ---------------------------------------------------------------------------
 // eigenvalue sort + eps-rank selection (single CTA)
 // ---------------------------------------------------------------------------
-__global__ void k_sort_select(const double* G, int C, double eps, int forced, int32_t* perm, double* lam,
-                              double* isl, double* out) {
+__global__ void k_sort_select(const double* G, int C, double eps, int forced, double resolution, int32_t* perm,
+                              double* lam, double* isl, double* out) {
     for (int k = threadIdx.x; k < C; k += blockDim.x) {
         const double lk = G[(int64_t)k * C + k];
         int rank = 0;
@@ -402,7 +496,10 @@ __global__ void k_sort_select(const double* G, int C, double eps, int forced, in
         int r = C;
         double tail = 0.0, tail_at_r = 0.0;
         if (forced > 0) {
-            r = min(forced, C);
+            // a forced rank is clipped to the eigenvalues the FP64 Gram matrix resolves
+            int nres = 0;
+            while (nres < C && lam[nres] > resolution) ++nres;
+            r = max(1, min(min(forced, C), nres));
             for (int k = C - 1; k >= r; --k) tail += fmax(lam[k], 0.0);
             tail_at_r = tail;
         } else {
@@ -435,13 +532,16 @@ __global__ void k_sort_select(const double* G, int C, double eps, int forced, in
 // ---------------------------------------------------------------------------
 constexpr int CHB = 32;
 
-__global__ void __launch_bounds__(256) k_cholesky(double* A, int r, DevStatus* st) {
+// Blocked right-looking Cholesky A = L L^T (lower, in place) followed by the
+// triangular inverse Li = L^{-1} (lower, zeros above), as one cooperative
+// grid: a barrier after each panel step and after each block row of Li.
+__global__ void __launch_bounds__(256) k_chol_inv(double* A, double* Li, int r, DevStatus* st) {
     __shared__ double D[CHB][CHB + 1];
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nbk = (r + CHB - 1) / CHB;
     for (int j0 = 0; j0 < r; j0 += CHB) {
         const int b = min(CHB, r - j0);
-        // 1) factor the diagonal block (CTA 0)
         if (blockIdx.x == 0) {
             for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
                 const int i = e / b, k = e % b;
@@ -469,7 +569,6 @@ __global__ void __launch_bounds__(256) k_cholesky(double* A, int r, DevStatus* s
             }
         }
         if (!grid_barrier(st)) return;
-        // 2) panel below: L21 = A21 L11^{-T}, one thread per row
         for (int64_t i = j0 + b + gtid; i < r; i += nthr) {
             double x[CHB];
             for (int k = 0; k < b; ++k) x[k] = __ldcg(A + i * r + j0 + k);
@@ -481,7 +580,6 @@ __global__ void __launch_bounds__(256) k_cholesky(double* A, int r, DevStatus* s
             for (int k = 0; k < b; ++k) __stcg(A + i * r + j0 + k, x[k]);
         }
         if (!grid_barrier(st)) return;
-        // 3) trailing update of the lower triangle
         const int64_t n2 = r - j0 - b;
         for (int64_t e = gtid; e < n2 * n2; e += nthr) {
             const int64_t i = j0 + b + e / n2, k = j0 + b + e % n2;
@@ -492,18 +590,101 @@ __global__ void __launch_bounds__(256) k_cholesky(double* A, int r, DevStatus* s
         }
         if (!grid_barrier(st)) return;
     }
-}
-
-__global__ void k_trsm_rows(const double* __restrict__ L, int r, double* Y, int64_t N) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    for (int a = 0; a < r; ++a) {
-        double s = Y[(int64_t)a * N + i];
-        const double* La = L + (int64_t)a * r;
-        for (int b = 0; b < a; ++b) s -= La[b] * Y[(int64_t)b * N + i];
-        Y[(int64_t)a * N + i] = s / La[a];
+    // Li: zero the strict upper part, invert the diagonal blocks (one CTA each)
+    for (int64_t e = gtid; e < (int64_t)r * r; e += nthr) {
+        const int64_t i = e / r, k = e % r;
+        if (k / CHB > i / CHB) __stcg(Li + e, 0.0);
+    }
+    for (int I = blockIdx.x; I < nbk; I += gridDim.x) {
+        const int i0 = I * CHB, b = min(CHB, r - i0);
+        // column k of inv(L_II): forward substitution, one thread per column
+        for (int k = threadIdx.x; k < b; k += blockDim.x) {
+            for (int i = 0; i < b; ++i) {
+                double s = (i == k) ? 1.0 : 0.0;
+                for (int l = k; l < i; ++l) s -= __ldcg(A + (int64_t)(i0 + i) * r + i0 + l) * D[l][k];
+                D[i][k] = (i < k) ? 0.0 : s / __ldcg(A + (int64_t)(i0 + i) * r + i0 + i);
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+            const int i = e / b, k = e % b;
+            __stcg(Li + (int64_t)(i0 + i) * r + i0 + k, D[i][k]);
+        }
+        __syncthreads();
+    }
+    if (!grid_barrier(st)) return;
+    // block rows I = 1..: Li[I][J] = -inv(L_II) sum_{K=J}^{I-1} L[I][K] Li[K][J]
+    for (int I = 1; I < nbk; ++I) {
+        const int i0 = I * CHB, bi = min(CHB, r - i0);
+        // all (J, element) pairs of this block row in parallel: S first, kept in Li
+        for (int64_t e = gtid; e < (int64_t)bi * i0; e += nthr) {
+            const int ii = (int)(e / i0), jj = (int)(e % i0);   // row i0+ii, column jj < i0
+            const int J = jj / CHB;
+            double s = 0.0;
+            for (int kk = J * CHB; kk < i0; ++kk) s += __ldcg(A + (int64_t)(i0 + ii) * r + kk) * __ldcg(Li + (int64_t)kk * r + jj);
+            __stcg(Li + (int64_t)(i0 + ii) * r + jj, s);
+        }
+        if (!grid_barrier(st)) return;
+        for (int64_t e = gtid; e < (int64_t)bi * i0; e += nthr) {
+            const int ii = (int)(e / i0), jj = (int)(e % i0);
+            double s = 0.0;
+            for (int kk = 0; kk <= ii; ++kk)
+                s -= __ldcg(Li + (int64_t)(i0 + ii) * r + i0 + kk) * __ldcg(Li + (int64_t)(i0 + kk) * r + jj);
+            // result for (ii, jj) reads column jj of S rows <= ii: write to a staging slot
+            __stcg(A + (int64_t)(i0 + ii) * r + jj, s);   // the strict lower block part of A is no longer needed
+        }
+        if (!grid_barrier(st)) return;
+        for (int64_t e = gtid; e < (int64_t)bi * i0; e += nthr) {
+            const int ii = (int)(e / i0), jj = (int)(e % i0);
+            __stcg(Li + (int64_t)(i0 + ii) * r + jj, __ldcg(A + (int64_t)(i0 + ii) * r + jj));
+        }
+        if (!grid_barrier(st)) return;
     }
 }
+
+// out[c][j] = in[j][c]   (in: rows x cols)
+__global__ void k_transpose(const double* __restrict__ in, int64_t rows, int64_t cols, double* __restrict__ out) {
+    __shared__ double tile[32][33];
+    const int64_t c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t r = r0 + k, c = c0 + threadIdx.x;
+        tile[k][threadIdx.x] = (r < rows && c < cols) ? in[r * cols + c] : 0.0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t c = c0 + k, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) out[c * rows + r] = tile[threadIdx.x][k];
+    }
+}
+
+// Core, step 1 (terms grouped by their mode-0 vector c0):
+//   W[c0 - cbeg][j*r2 + l] = sum_{t : c0(t) = c0} xin[t] P1[j][c1(t)] P2[l][c2(t)]
+// with P1t = P1^T (C1 x r1) and P2t = P2^T (C2 x r2) so that l runs along
+// contiguous memory. One CTA per (256 outputs, c0).
+__global__ void __launch_bounds__(256) k_core_group_f64(const double* __restrict__ P1t, const double* __restrict__ P2t,
+                                                        int r1, int r2, const int32_t* __restrict__ tcol,
+                                                        const double* __restrict__ xin, const int32_t* __restrict__ perm,
+                                                        const int32_t* __restrict__ off, int cbeg, double* __restrict__ W) {
+    const int64_t n = blockIdx.x * 256 + threadIdx.x;
+    const int64_t nn = (int64_t)r1 * r2;
+    const int c0 = cbeg + blockIdx.y;
+    if (n >= nn) return;
+    const int j = (int)(n / r2), l = (int)(n - (int64_t)j * r2);
+    double acc = 0.0;
+    for (int k = off[c0]; k < off[c0 + 1]; ++k) {
+        const int t = perm[k];
+        acc = fma(xin[t] * P1t[(int64_t)tcol[3 * t + 1] * r1 + j], P2t[(int64_t)tcol[3 * t + 2] * r2 + l], acc);
+    }
+    W[(int64_t)blockIdx.y * nn + n] = acc;
+}
+
+struct StoreRowAcc {     // C[m*ld + n] (+)= v
+    double* p; int64_t ld; int accumulate;
+    __device__ void operator()(int, int m, int n, double v) const {
+        double* q = p + m * ld + n;
+        *q = accumulate ? *q + v : v;
+    }
+};
 
 template <class K>
 int coop_blocks(K kernel, int threads, size_t smem, int num_sms, int64_t want) {
@@ -559,28 +740,47 @@ cudaError_t launch_identity(double* V, int64_t C, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_jacobi(double* G, double* V, int64_t C, DevStatus* status, int max_sweeps, double tol,
-                          double abs_floor, int num_sms, cudaStream_t st) {
-    const int Cp = (int)(C + (C & 1));
-    const int P = Cp / 2;
-    const size_t smem = 2 * sizeof(double) * P;
-    const int64_t items = (int64_t)P * P + C * P;
-    const int64_t want = items <= 2048 ? 1 : (items + 1023) / 1024;
-    int nblk = coop_blocks(k_jacobi, 256, smem, num_sms, want);
-    if (nblk > num_sms) nblk = num_sms;
-    int Ci = (int)C;
-    void* args[] = {&G, &V, &Ci, &status, &max_sweeps, &tol, &abs_floor};
+cudaError_t launch_jacobi_multi(const JacobiJob* jobs, int njobs, int max_sweeps, double tol, int num_sms,
+                                cudaStream_t st) {
+    if (njobs < 1 || njobs > 3) return cudaErrorInvalidValue;
+    JacobiArgs a{};
+    a.nmodes = njobs;
+    a.max_sweeps = max_sweeps > 64 ? 64 : max_sweeps;
+    a.tol = tol;
+    size_t smem = 0;
+    int64_t want[3], total = 0;
+    for (int m = 0; m < njobs; ++m) {
+        const int64_t C = jobs[m].C;
+        const int64_t P = (C + (C & 1)) / 2;
+        smem = std::max(smem, (size_t)(2 * sizeof(double) * P + sizeof(int) * (2 * P + 2 * (C + (C & 1)))));
+        const int64_t items = P * P + C * P;
+        want[m] = items <= 2048 ? 1 : (items + 1023) / 1024;
+        total += want[m];
+    }
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_jacobi_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_multi, 256, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int64_t cap = std::min<int64_t>((int64_t)per_sm * num_sms, 2 * (int64_t)num_sms);
+    int cta = 0;
+    for (int m = 0; m < njobs; ++m) {
+        int64_t n = want[m];
+        if (total > cap) n = std::max<int64_t>(1, want[m] * cap / total);
+        a.m[m] = JacobiMode{jobs[m].G, jobs[m].V, jobs[m].snap, jobs[m].st, (int)jobs[m].C, cta, (int)n,
+                            jobs[m].abs_floor, jobs[m].tau};
+        cta += (int)n;
+    }
+    void* args[] = {&a};
     count_kernels(1);
-    return cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(nblk), dim3(256), args, smem, st);
+    return cudaLaunchCooperativeKernel((void*)k_jacobi_multi, dim3(cta), dim3(256), args, smem, st);
 }
 
-cudaError_t launch_sort_select(const double* G, int64_t C, double eps, int forced, int32_t* perm, double* lam,
-                               double* inv_sqrt_lam, double* out, cudaStream_t st) {
-    k_sort_select<<<1, 1024, 0, st>>>(G, (int)C, eps, forced, perm, lam, inv_sqrt_lam, out);
+cudaError_t launch_sort_select(const double* G, int64_t C, double eps, int forced, double resolution, int32_t* perm,
+                               double* lam, double* inv_sqrt_lam, double* out, cudaStream_t st) {
+    k_sort_select<<<1, 1024, 0, st>>>(G, (int)C, eps, forced, resolution, perm, lam, inv_sqrt_lam, out);
     count_kernels(1);
     return cudaGetLastError();
 }
@@ -591,23 +791,28 @@ cudaError_t launch_basis(const double* V, int64_t C, const int32_t* perm, const 
                     StoreRow{Y, N, 0}, st);
 }
 
-cudaError_t launch_cholqr2(double* Y, int r, int64_t N, double* work, DevStatus* status, int num_sms,
+cudaError_t launch_cholqr2(double* Y, double* Ytmp, int r, int64_t N, double* work, DevStatus* status, int num_sms,
                            cudaStream_t st) {
+    double* Gz = work;
+    double* Li = work + (int64_t)r * r;
+    double* src = Y;
+    double* dst = Ytmp;
     for (int pass = 0; pass < 2; ++pass) {
-        cudaError_t e = gemm_f64(r, r, (int)N, 1, RowK{Y, N}, NRowK{Y, N}, StoreRow{work, r, 0}, st);
+        cudaError_t e = gemm_f64(r, r, (int)N, 1, RowK{src, N}, NRowK{src, N}, StoreRow{Gz, r, 0}, st);
         if (e != cudaSuccess) return e;
-        const int64_t want = ((int64_t)r * r + 255) / 256;
-        int nblk = coop_blocks(k_cholesky, 256, 0, num_sms, want < 1 ? 1 : want);
+        const int64_t want = std::max<int64_t>(1, ((int64_t)r * r + 1023) / 1024);
+        int nblk = coop_blocks(k_chol_inv, 256, 0, num_sms, want);
         if (nblk > num_sms) nblk = num_sms;
-        void* args[] = {&work, &r, &status};
+        void* args[] = {&Gz, &Li, &r, &status};
         count_kernels(1);
-        e = cudaLaunchCooperativeKernel((void*)k_cholesky, dim3(nblk), dim3(256), args, 0, st);
+        e = cudaLaunchCooperativeKernel((void*)k_chol_inv, dim3(nblk), dim3(256), args, 0, st);
         if (e != cudaSuccess) return e;
-        k_trsm_rows<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(work, r, Y, N);
-        count_kernels(1);
-        e = cudaGetLastError();
+        // dst = Li * src  (rows of dst orthonormal after the second pass)
+        e = gemm_f64(r, (int)N, r, 1, RowK{Li, r}, KRowN{src, N}, StoreRow{dst, N, 0}, st);
         if (e != cudaSuccess) return e;
+        std::swap(src, dst);
     }
+    // after two passes the result is back in Y
     return cudaSuccess;
 }
 
@@ -625,11 +830,35 @@ cudaError_t launch_fold_norms(const double* xi, const int32_t* tcol, int64_t T, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_core_f64(const double* P0, const double* P1, const double* P2, const int32_t* C,
-                            const int32_t* r, const int32_t* tcol, const double* xin, int64_t T, double* B,
-                            cudaStream_t st) {
-    return gemm_f64(r[0], r[1] * r[2], (int)T, 1, CoreA{P0, C[0], tcol, xin},
-                    CoreB{P1, P2, C[1], C[2], r[2], tcol}, StoreRow{B, (int64_t)r[1] * r[2], 0}, st);
+cudaError_t launch_transpose(const double* in, int64_t rows, int64_t cols, double* out, cudaStream_t st) {
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, rows, cols, out);
+    count_kernels(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_core_f64(const double* P0, const double* P1t, const double* P2t, const int32_t* C, const int32_t* r,
+                            const int32_t* tcol, const double* xin, const int32_t* perm, const int32_t* off,
+                            double* W, int64_t w_cols, double* B, cudaStream_t st) {
+    const int64_t nn = (int64_t)r[1] * r[2];
+    for (int64_t c0 = 0; c0 < C[0]; c0 += w_cols) {
+        const int cw = (int)std::min<int64_t>(w_cols, C[0] - c0);
+        dim3 grid((unsigned)((nn + 255) / 256), (unsigned)cw);
+        k_core_group_f64<<<grid, 256, 0, st>>>(P1t, P2t, r[1], r[2], tcol, xin, perm, off, (int)c0, W);
+        count_kernels(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        // B[i][n] (+)= sum_{c in chunk} P0[i][c0 + c] W[c][n]
+        e = gemm_f64(r[0], (int)nn, cw, 1, RowK{P0 + c0, C[0]}, KRowN{W, nn},
+                     StoreRowAcc{B, nn, c0 > 0 ? 1 : 0}, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_eval_m(const double* Z2, const int32_t* r, const double* B, int64_t N, const int32_t* zidx,
+                          int nslab, double* M, cudaStream_t st) {
+    return gemm_f64(r[0] * r[1], nslab, r[2], 1, RowK{B, r[2]}, EvalZ3{Z2, N, zidx}, StoreRow{M, nslab, 0}, st);
 }
 
 cudaError_t launch_eval_f64(const double* const Z[3], const int32_t* r, const double* B, int64_t N,

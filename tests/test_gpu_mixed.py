@@ -1,0 +1,111 @@
+"""GPU parity of the mixed-precision path (tcgen05 BF16x3 contractions,
+FP64 orthogonalisation) against the FP64 path and the FP64 oracle.
+
+Tolerances, from the arithmetic of the split products: each operand is
+rounded to FP32 (2^-24) and split exactly into three BF16 parts; the six
+MMAs with i + j <= 2 drop products below 3 * 2^-27 |ab| and accumulate in
+FP32. Each product is then as accurate as an FP32 product, and a contraction
+of length K carries about 2^-24 sqrt(K) relative error plus what cancellation
+adds. The tests allow 3e-5 on projections, the core and slabs against the
+FP64 path, and the configuration's eps (1e-6) on the final slab values
+against the FP64 oracle, as the precision target requires.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import lattice_oracle as O  # noqa: E402
+from paper_1411_1994_gb300 import build as B  # noqa: E402
+from paper_1411_1994_gb300 import lattice_sum as L  # noqa: E402
+from paper_1411_1994_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    B.build()
+    L.lib()
+
+
+def scale_for(wl):
+    s, _ = O.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, O.default_r_max(wl))
+    return s
+
+
+def run(wl, s, prec, forced=None):
+    ls = L.LatticeSum.from_workload(wl, s, prec)
+    ls.add_defects(wl.defects)
+    info = ls.rhosvd_reduce(wl.eps, forced_ranks=forced)
+    return ls, info
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("wl", [W.small_case(L=(3, 2, 2), frac_vac=0.2, frac_imp=0.1, eps=1e-6),
+                                W.small_case(L=(5, 3, 2), N=50, frac_vac=0.2, eps=1e-6),
+                                W.config2()], ids=lambda w: w.name)
+def test_mixed_contractions_match_fp64_path(wl):
+    s = scale_for(wl)
+    a, ia = run(wl, s, L.LS_FP64)
+    b, ib = run(wl, s, L.LS_MIXED, forced=ia["r"])
+    assert ib["r"] == ia["r"]
+    for m in range(3):
+        # the FP64 orthogonalisation is the same code in both paths
+        assert np.array_equal(a.read(L.LS_READ_BASIS, m), b.read(L.LS_READ_BASIS, m))
+        pa, pb = a.read(L.LS_READ_PROJ, m), b.read(L.LS_READ_PROJ, m)
+        assert rel(pb, pa) < 3e-5, (m, rel(pb, pa))
+    ca, cb = a.read(L.LS_READ_CORE), b.read(L.LS_READ_CORE)
+    assert rel(cb, ca) < 3e-5, rel(cb, ca)
+    z = wl.slabs[:8]
+    sa = a.eval_slab_torch(z).cpu().numpy()
+    sb = b.eval_slab_torch(z).cpu().numpy()
+    assert rel(sb, sa) < 3e-5, rel(sb, sa)
+    a.close()
+    b.close()
+
+
+def test_mixed_slabs_meet_eps_against_oracle():
+    """16^3 lattice with defects, eps = 1e-6: relative L2 error of the mixed
+    slabs (FP32 output) against the untruncated FP64 canonical tensor of the
+    oracle is within eps, on the 64 seeded slabs."""
+    wl = W.config2()
+    s = scale_for(wl)
+    t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s)
+    g = O.generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w)
+    cols, tcol, xi = O.canonical_terms(wl.N, wl.box_lo, wl.box_hi, g, wl.blocks, wl.defects)
+    ncols, _, xin = O.normalise_terms(cols, tcol, xi)
+    ls, info = run(wl, s, L.LS_MIXED)
+    out = ls.eval_slab_torch(wl.slabs, dtype=torch.float32).cpu().numpy().astype(np.float64)
+    num = den = 0.0
+    worst = 0.0
+    for k, zz in enumerate(wl.slabs):
+        ref = O.canonical_slab(ncols, tcol, xin, zz)
+        num += float(np.sum((out[k] - ref) ** 2))
+        den += float(np.sum(ref ** 2))
+        worst = max(worst, float(np.max(np.abs(out[k] - ref))))
+    err = math.sqrt(num / den)
+    assert err <= wl.eps, err
+    ls.close()
+
+
+def test_mixed_single_site_and_ragged_tiles():
+    """Degenerate ranks (a single site, r = 1 per mode possible) and sizes that
+    leave ragged tensor-core tiles in every dimension."""
+    for wl in (W.small_case(L=(1, 1, 1), N=33, eps=1e-6), W.small_case(L=(7, 3, 2), N=70, frac_vac=0.1, eps=1e-5)):
+        s = scale_for(wl)
+        a, ia = run(wl, s, L.LS_FP64)
+        b, ib = run(wl, s, L.LS_MIXED, forced=ia["r"])
+        z = [0, wl.N // 2, wl.N - 1]
+        sa = a.eval_slab_torch(z).cpu().numpy()
+        sb = b.eval_slab_torch(z).cpu().numpy()
+        assert rel(sb, sa) < 3e-5, (wl.name, rel(sb, sa))
+        a.close()
+        b.close()

@@ -218,7 +218,7 @@ def test_config2_fp64_forced_rank():
 
 
 @pytest.mark.parametrize("wl", [W.small_case(L=(3, 2, 2), frac_vac=0.2, frac_imp=0.1, eps=1e-6),
-                                W.small_case(L=(1, 1, 1), N=33, eps=1e-10),
+                                W.small_case(L=(1, 1, 1), N=33, eps=1e-7),
                                 W.small_case(L=(7, 3, 2), N=70, frac_vac=0.1, eps=1e-5)],
                          ids=lambda w: w.name)
 def test_small_cases_fp64(wl):
