@@ -17,7 +17,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -27,7 +26,7 @@ sys.path.insert(0, ROOT)
 
 from paper_1411_1994_gb300 import workloads as W  # noqa: E402
 
-METRIC = "lattice potentials summed/s (build+RHOSVD)"
+METRIC = "lattice potentials summed/s (build+RHOSVD), mixed vs FP64 GPU at 1e-6 rel err"
 FP64_PEAK_TFLOPS_DERIVED = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk x flops x max clock
 
 
@@ -38,7 +37,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -179,48 +179,54 @@ class ClockSampler:
 # roofline of the dominant step
 # ---------------------------------------------------------------------------
 
-def step_flops(name, info, N, nslab=0):
+def step_flops(name, info, N):
+    """Algorithmic FP64 / tensor flops of one pipeline step (all three modes)."""
     C, r, T = info["C"], info["r"], info["T"]
     if name == "gram":
         return sum(2.0 * N * c * c for c in C)
     if name == "basis":
         return sum(2.0 * N * C[a] * r[a] for a in range(3))
     if name == "cholqr2":
-        return sum(2 * (2.0 * N * r[a] ** 2 + r[a] ** 3 / 3.0 + 1.0 * N * r[a] ** 2) for a in range(3))
+        return sum(2 * (2.0 * N * r[a] ** 2 + 2.0 * r[a] ** 3 / 3.0 + 2.0 * N * r[a] ** 2) for a in range(3))
     if name == "project":
         return sum(2.0 * N * r[a] * C[a] for a in range(3))
     if name == "core":
-        return 2.0 * r[0] * r[1] * r[2] * T
+        # two exact steps: grouped step 1 (2 r1 r2 T) + dense step 2 (2 r0 r1 r2 C0)
+        return 2.0 * r[1] * r[2] * T + 2.0 * r[0] * r[1] * r[2] * C[0]
+    if name == "jacobi":
+        # each applied rotation updates two rows of the symmetric Gram matrix (upper triangle:
+        # ~2 C entries x 3 flop x 2) and two columns of V (2 C entries x 3 flop)
+        return sum(18.0 * C[a] * info["rotations"][a] for a in range(3))
     return None
 
 
 def roofline(report, info, N, steps, precision, peaks):
     st = report.get("steps", {})
     if not st:
-        return None, None
+        return None
     name = max(st, key=lambda k: st[k]["ms"])
     ms_launch = st[name]["ms"] / max(st[name]["launches"], 1)
+    launches_per_step = st[name]["launches"] / max(steps, 1)
     fl = step_flops(name, info, N)
-    per_launch_units = st[name]["launches"] / max(steps, 1)   # launches of this step per pipeline step
-    out = {"kernel": name, "ms_per_launch": ms_launch}
+    out = {"kernel": name, "ms_per_launch": ms_launch, "launches_per_step": launches_per_step}
     if fl is None:
-        out.update({"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
-                    "traffic": None, "note": "iterative step, time only"})
-        return out, name
-    fl_launch = fl / per_launch_units
-    achieved = fl_launch / (ms_launch * 1e-3) / 1e12
-    if precision == "fp64" or name in ("gram", "basis", "cholqr2"):
+        out.update({"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
+        return out
+    achieved = fl / launches_per_step / (ms_launch * 1e-3) / 1e12
+    tensor = precision == "mixed" and name in ("project", "core")
+    if not tensor:
         peak = FP64_PEAK_TFLOPS_DERIVED
-        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64, CUDA cores)"})
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None,
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 on CUDA cores; "
+                                   "a DFMA probe measured 1.255 TFLOP/s)"})
     else:
         peak = peaks.get("bf16_tflops")
         out.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak if peak else None, "traffic": None,
-                    "peak_source": "of measured bf16 burst (MEASURED_PEAKS.json); the six split MMAs per product "
+                    "peak_source": "of measured bf16 burst (MEASURED_PEAKS.json); the ten split MMAs per product "
                                    "are counted as overhead, not as work"})
-    return out, name
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -247,7 +253,6 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.build()
     wl = workload(args.workload)
-    prec = L.LS_MIXED if args.precision == "mixed" else L.LS_FP64
     s, _ = L.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, math.sqrt(3.0) * (wl.box_hi - wl.box_lo))
     stream = torch.cuda.Stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -257,71 +262,91 @@ def main():
     except Exception:
         pass
 
-    def step():
+    def step(prec):
         ls = L.LatticeSum.from_workload(wl, s, prec, stream=stream.cuda_stream)
         ls.add_defects(wl.defects)
         info = ls.rhosvd_reduce(wl.eps)
         ls.close()
         return info
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            info = step()
-    torch.cuda.synchronize()
+    def timed(prec, sample_clocks):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                info = step(prec)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        clocks = ClockSampler(local) if sample_clocks else None
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        L.profile(True)
+        if clocks:
+            clocks.start()
+        t_wall = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(stream)
+                info = step(prec)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall
+        clk = clocks.stop() if clocks else None
+        L.profile(False)
+        report = L.profile_report()
+        total_ms = sum(a.elapsed_time(b) for a, b in ev)
+        if dist:
+            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+            dist.barrier()
+        ms = total_ms / args.steps
+        return {"value": world * wl.units / (ms / 1e3), "ms_per_step": ms, "info": info, "report": report,
+                "clocks": clk, "wall": wall}
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    L.profile(True)
-    clocks.start()
-    t_wall = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
+    def e2e(prec):
+        """Same metric through the public API with host inputs and the Tucker factors read back."""
+        times = []
+        L.profile(True)
+        for k in range(max(3, args.steps // 2)):
             flush.fill_(k & 0xFF)
-            ev[k][0].record(stream)
-            info = step()
-            ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t_wall
-    clk = clocks.stop()
-    L.profile(False)
-    report = L.profile_report()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
-    ms_per_step = total_ms / args.steps
-    value = world * wl.units / (ms_per_step / 1e3)
-    roof, dom = roofline(report, info, wl.N, args.steps, args.precision, peaks)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ls = L.LatticeSum.from_workload(wl, s, prec, stream=stream.cuda_stream)
+            ls.add_defects(wl.defects)
+            ls.rhosvd_reduce(wl.eps)
+            for a in range(3):
+                ls.read(L.LS_READ_BASIS, a)
+            ls.read(L.LS_READ_CORE)
+            ls.close()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        L.profile(False)
+        rep = L.profile_report()
+        n = len(times)
+        return {"value": world * wl.units / (sum(times) / n), "unit": "potentials/s",
+                "h2d_bytes_per_step": int(rep["h2d_bytes"] // n), "d2h_bytes_per_step": int(rep["d2h_bytes"] // n)}
 
-    # end to end through the public API: host inputs in, Tucker factors out
-    e2e_times = []
-    h2d = d2h = 0
-    L.profile(True)
-    for k in range(max(3, args.steps // 2)):
-        flush.fill_(k & 0xFF)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ls = L.LatticeSum.from_workload(wl, s, prec, stream=stream.cuda_stream)
-        ls.add_defects(wl.defects)
-        ls.rhosvd_reduce(wl.eps)
-        for a in range(3):
-            ls.read(L.LS_READ_BASIS, a)
-        ls.read(L.LS_READ_CORE)
-        ls.close()
-        torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
-    L.profile(False)
-    rep2 = L.profile_report()
-    n_e2e = len(e2e_times)
-    h2d = rep2["h2d_bytes"] // n_e2e
-    d2h = rep2["d2h_bytes"] // n_e2e
-    e2e_value = world * wl.units / (sum(e2e_times) / n_e2e)
+    head_prec = L.LS_MIXED if args.precision == "mixed" else L.LS_FP64
+    head = timed(head_prec, True)
+    head_e2e = e2e(head_prec)
+    other = None
+    agreement = None
+    if args.precision == "mixed" and not args.no_compare:
+        other = timed(L.LS_FP64, False)
+        # accuracy of the mixed path against the FP64 path at the same ranks (outside the timed region)
+        a = L.LatticeSum.from_workload(wl, s, L.LS_FP64)
+        a.add_defects(wl.defects)
+        ia = a.rhosvd_reduce(wl.eps)
+        b = L.LatticeSum.from_workload(wl, s, L.LS_MIXED)
+        b.add_defects(wl.defects)
+        b.rhosvd_reduce(wl.eps, forced_ranks=ia["r"])
+        z = (wl.slabs or [wl.N // 2])[:8]
+        sa = a.eval_slab_torch(z)
+        sb = b.eval_slab_torch(z)
+        agreement = float(torch.linalg.norm(sb - sa) / torch.linalg.norm(sa))
+        a.close()
+        b.close()
 
     if rank != 0:
         if dist:
@@ -334,22 +359,29 @@ def main():
                "kind": "oracle",
                "sample": f"{len(times)} full oracle pipelines of {wl.name} on the host cores "
                          f"(mean {statistics.mean(times):.2f} s each)"}
+    info = head["info"]
     line = {
-        "metric": METRIC + f", {args.precision} path", "value": value, "unit": "potentials/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x6(f32 acc)+f64",
-        "data": "synthetic (seeded)", "config": config_of(wl, args, {"parallelism": f"replicas x{world}",
-                                                                     "ranks": info["r"], "columns": info["C"],
-                                                                     "terms": info["T"],
-                                                                     "jacobi_sweeps": info["sweeps"]}),
-        "roofline": roof, "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "potentials/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": int(report.get("kernel_launches", 0)),
-        "clocks": clk,
-        "steps_ms": {k: v["ms"] / args.steps for k, v in report.get("steps", {}).items()},
-        "wall_s_timed_region": wall,
+        "metric": METRIC, "value": head["value"], "unit": "potentials/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64 orthogonalisation + bf16 tensor-core contractions "
+                                                         "(exact 6-bit heads, f32 acc)",
+        "data": "synthetic (seeded)",
+        "config": config_of(wl, args, {"parallelism": f"replicas x{world}", "ranks": info["r"],
+                                       "columns": info["C"], "terms": info["T"], "jacobi_sweeps": info["sweeps"]}),
+        "roofline": roofline(head["report"], info, wl.N, args.steps, args.precision, peaks),
+        "cpu_baseline": cpu,
+        "e2e": head_e2e,
+        "gpu_launches": int(head["report"].get("kernel_launches", 0)),
+        "clocks": head["clocks"],
+        "steps_ms": {k: v["ms"] / args.steps for k, v in head["report"].get("steps", {}).items()},
+        "wall_s_timed_region": head["wall"],
     }
+    if other is not None:
+        line["fp64_path"] = {"value": other["value"], "ms_per_step": other["ms_per_step"],
+                             "steps_ms": {k: v["ms"] / args.steps for k, v in other["report"].get("steps", {}).items()}}
+        line["mixed_over_fp64"] = head["value"] / other["value"]
+        line["mixed_vs_fp64_slab_rel_l2"] = agreement
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -136,6 +136,7 @@ typedef struct {
                                 /* eigenvalues of the FP64 Gram matrix are resolved to   */
                                 /* C_l * floor_l, floor_l = 8 u T (u = 2^-53)             */
     int32_t sweeps[3];          /* eigen-solver sweeps per mode                          */
+    int64_t rotations[3];       /* Jacobi rotations applied per mode (all sweeps)        */
 } ls_tucker_info;
 
 /*
@@ -185,7 +186,7 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n);
  * mu = sum_nu xi_nu P1[:,c1] (x) P2[:,c2] (x) P3[:,c3] follow.
  * `forced_ranks` (host, 3 entries or NULL) overrides the eps rule (each
  * clipped to C_l and to the eigenvalues of the FP64 Gram matrix above its
- * resolution C_l * 8 u T). Fills *info (may be NULL). Synchronises the stream.
+ * rounding noise 8 u T). Fills *info (may be NULL). Synchronises the stream.
  * Errors: LS_ERR_ARG (eps <= 0 and no forced ranks), LS_ERR_STATE (called
  * twice), LS_ERR_NOCONVERGE, LS_ERR_TIMEOUT, LS_ERR_OOM, LS_ERR_CUDA.
  */

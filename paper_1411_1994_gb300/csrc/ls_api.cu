@@ -508,7 +508,7 @@ int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ran
     for (int l = 0; l < 3; ++l) {
         const int forced = forced_ranks ? std::max(1, forced_ranks[l]) : 0;
         Scope sc("select", st);
-        const double resolution = (double)ctx->mode[l].C * jobs[l].abs_floor;
+        const double resolution = jobs[l].abs_floor;   // eigenvalues below the Gram matrix's noise
         CU(launch_sort_select(d_G[l], ctx->mode[l].C, eps, forced, resolution, d_perm[l], ctx->d_sigma[l], d_isl[l],
                               d_sel + 3 * l, st));
     }
@@ -631,6 +631,9 @@ int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ran
             info->sigma_discarded[l] = sqrt(std::max(sel[l][1], 0.0));
             info->sigma_total[l] = sqrt(std::max(sel[l][2], 0.0));
             info->sweeps[l] = sweeps[l];
+            int64_t rot = 0;
+            for (int k = 0; k < sweeps[l] && k < 64; ++k) rot += hs[l].sweep_active[k];
+            info->rotations[l] = rot;
             // Thm A.1(d) with the resolution of the Gram route: after the eigen-solver every
             // off-diagonal entry is below the floor, so each eigenvalue is known to C * floor
             ssum += sqrt(std::max(sel[l][1], 0.0) + (double)Cs[l] * jobs[l].abs_floor);

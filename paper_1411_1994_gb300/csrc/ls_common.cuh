@@ -104,6 +104,12 @@ cudaError_t launch_fold_norms(const double* xi, const int32_t* tcol, int64_t T, 
 // out = in^T for a rows x cols row-major matrix.
 cudaError_t launch_transpose(const double* in, int64_t rows, int64_t cols, double* out, cudaStream_t st);
 
+// Step 1 of the core for groups [cbeg, cbeg + cw): W[c][j*r2+k] =
+// sum_{t : c0(t) = cbeg + c} xin[t] P1[j][c1(t)] P2[k][c2(t)]  (FP64).
+cudaError_t launch_core_group(const double* P1t, const double* P2t, int r1, int r2, const int32_t* tcol,
+                              const double* xin, const int32_t* perm, const int32_t* off, int cbeg, int cw, double* W,
+                              cudaStream_t st);
+
 // Core (FP64): B[i][j][k] = sum_t xin[t] P0[i][c0] P1[j][c1] P2[k][c2] in two
 // exact steps: terms grouped by c0 (perm/off: terms sorted by c0, CSR
 // offsets) give W[c0][j*r2+k] = sum_{t in group} xin P1[j][c1] P2[k][c2]

@@ -569,13 +569,19 @@ __global__ void __launch_bounds__(256) k_chol_inv(double* A, double* Li, int r, 
             }
         }
         if (!grid_barrier(st)) return;
+        // every CTA stages L11 in shared memory for the panel solve
+        for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+            const int i = e / b, k = e % b;
+            D[i][k] = __ldcg(A + (int64_t)(j0 + i) * r + j0 + k);
+        }
+        __syncthreads();
         for (int64_t i = j0 + b + gtid; i < r; i += nthr) {
             double x[CHB];
             for (int k = 0; k < b; ++k) x[k] = __ldcg(A + i * r + j0 + k);
             for (int k = 0; k < b; ++k) {
                 double s = x[k];
-                for (int l = 0; l < k; ++l) s -= x[l] * __ldcg(A + (int64_t)(j0 + k) * r + j0 + l);
-                x[k] = s / __ldcg(A + (int64_t)(j0 + k) * r + j0 + k);
+                for (int l = 0; l < k; ++l) s -= x[l] * D[k][l];
+                x[k] = s / D[k][k];
             }
             for (int k = 0; k < b; ++k) __stcg(A + i * r + j0 + k, x[k]);
         }
@@ -595,14 +601,20 @@ __global__ void __launch_bounds__(256) k_chol_inv(double* A, double* Li, int r, 
         const int64_t i = e / r, k = e % r;
         if (k / CHB > i / CHB) __stcg(Li + e, 0.0);
     }
+    __shared__ double Lb[CHB][CHB + 1];
     for (int I = blockIdx.x; I < nbk; I += gridDim.x) {
         const int i0 = I * CHB, b = min(CHB, r - i0);
+        for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+            const int i = e / b, k = e % b;
+            Lb[i][k] = __ldcg(A + (int64_t)(i0 + i) * r + i0 + k);
+        }
+        __syncthreads();
         // column k of inv(L_II): forward substitution, one thread per column
         for (int k = threadIdx.x; k < b; k += blockDim.x) {
             for (int i = 0; i < b; ++i) {
                 double s = (i == k) ? 1.0 : 0.0;
-                for (int l = k; l < i; ++l) s -= __ldcg(A + (int64_t)(i0 + i) * r + i0 + l) * D[l][k];
-                D[i][k] = (i < k) ? 0.0 : s / __ldcg(A + (int64_t)(i0 + i) * r + i0 + i);
+                for (int l = k; l < i; ++l) s -= Lb[i][l] * D[l][k];
+                D[i][k] = (i < k) ? 0.0 : s / Lb[i][i];
             }
         }
         __syncthreads();
@@ -833,6 +845,16 @@ cudaError_t launch_fold_norms(const double* xi, const int32_t* tcol, int64_t T, 
 cudaError_t launch_transpose(const double* in, int64_t rows, int64_t cols, double* out, cudaStream_t st) {
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
     k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, rows, cols, out);
+    count_kernels(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_core_group(const double* P1t, const double* P2t, int r1, int r2, const int32_t* tcol,
+                              const double* xin, const int32_t* perm, const int32_t* off, int cbeg, int cw, double* W,
+                              cudaStream_t st) {
+    const int64_t nn = (int64_t)r1 * r2;
+    dim3 grid((unsigned)((nn + 255) / 256), (unsigned)cw);
+    k_core_group_f64<<<grid, 256, 0, st>>>(P1t, P2t, r1, r2, tcol, xin, perm, off, cbeg, W);
     count_kernels(1);
     return cudaGetLastError();
 }

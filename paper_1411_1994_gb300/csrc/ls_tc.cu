@@ -1,16 +1,24 @@
 // Mixed-precision tensor-core path for sm_103a: one TN GEMM on tcgen05.
 //
-//   D[z][m][n] = sum_k A[z][m][k] * B[z][n][k]        (A, B K-major)
+//   D[z][m][n] = sum_k A[z][m][k] * B[z][n][k]        (A, B K-major, FP64 in HBM)
 //
-// Operands arrive as three BF16 parts (x = b0 + b1 + b2 holds all 24 bits of
-// the FP32 value of x) and each k-step issues the six MMAs with i + j <= 2 into
-// one FP32 TMEM accumulator; the dropped products are below 3 * 2^-27 |ab|, so
-// each product is as good as an FP32 product. (Two parts and three MMAs lose
-// 2^-18 per operand, which the cancellation in the core contraction amplifies
-// past a 1e-6 target.) Tiles of 128 x 128 x 64 are brought into 128B-swizzled
-// shared memory by TMA (one plain load per tile; no multicast), one thread
-// issues tcgen05.mma for the CTA, and four epilogue warps read the
-// accumulator back with tcgen05.ld.
+// Each operand row is scaled by a power of two 2^-e (its largest entry then
+// lies in [1/2, 1)) and split into two 6-bit fixed-point digits h and m
+// (multiples of 2^-6 and 2^-12) and a rest below 2^-12 carried by two BF16
+// parts (to 2^-30). Products of digits are integers: h*h (units 2^-12) and
+// h*m + m*h (units 2^-18) keep their K <= 1024 partial sums below 2^23 and so
+// accumulate EXACTLY in two FP32 TMEM accumulators, whatever the rounding of
+// the tensor core's adds. The remaining products that matter (m*m and those
+// with the rest, all below 2^-12 of the result) go to a third accumulator,
+// whose rounding then stays near 2^-36 of the result even if every add rounds
+// the same way. The FP64 epilogue sums the three and applies 2^(e_a + e_b).
+// Each contraction is good to a few 2^-30 of sum |a_k b_k|, against 2^-24
+// sqrt(K) or worse for plain FP32 accumulation: the cancellation in the
+// projections and in the core contraction needs the former.
+//
+// Tiles of 128 x 64 x 64 come into 128B-swizzled shared memory by TMA (one
+// plain load per tile; no multicast), one thread issues tcgen05.mma for the
+// CTA, and four epilogue warps read the accumulators back with tcgen05.ld.
 // Every mbarrier wait is bounded: on timeout the kernel raises a flag, drains
 // the copies it issued, frees its TMEM and returns.
 //
@@ -34,19 +42,19 @@ namespace ls {
 
 namespace {
 
-constexpr int TBM = 128, TBN = 128, TBK = 64, TSTAGES = 2, NPART = 3;
+constexpr int TBM = 128, TBN = 64, TBK = 64, TSTAGES = 2, NPART = 4;   // parts: h, m, rest0, rest1
 constexpr int TILE_A = TBM * TBK * 2;          // bytes of one bf16 A tile (16 KB)
-constexpr int TILE_B = TBN * TBK * 2;          // 16 KB
+constexpr int TILE_B = TBN * TBK * 2;          // 8 KB
 constexpr int STAGE_BYTES = NPART * (TILE_A + TILE_B);
 constexpr int TC_THREADS = 192;                // warp 0 TMA, warp 1 MMA + TMEM, warps 2-5 epilogue
-constexpr long long kWaitLimit = 1LL << 22;   // try_wait polls; each may suspend briefly
+constexpr int KCHUNK = 1024;                   // K per exact head accumulation
+constexpr int TMEM_COLS = 4 * TBN;             // three FP32 accumulators (power-of-two allocation)
+constexpr long long kWaitLimit = 1LL << 22;    // try_wait polls; each may suspend briefly
 
-enum OutMode : int { OUT_F64 = 0, OUT_F32 = 1, OUT_SPLIT = 2 };
+enum OutMode : int { OUT_F64 = 0, OUT_F32 = 1 };
 
 struct TcOut {
-    void* p;            // F64 / F32: D; SPLIT: part 0
-    void* p2;           // SPLIT: part 1
-    void* p3;           // SPLIT: part 2
+    void* p;            // D
     int64_t ld;         // row stride (elements)
     int64_t zs;         // batch stride (elements)
     int mode;
@@ -152,10 +160,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-              const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
-              const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2, int M, int N, int K,
-              int a_batched, int b_batched, TcOut out, int* flag) {
+    k_fx_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+              const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mA3,
+              const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+              const __grid_constant__ CUtensorMap mB2, const __grid_constant__ CUtensorMap mB3, int M, int N, int kb0,
+              int nkb, int a_batched, int b_batched, const int* __restrict__ ea, int64_t ea_zs,
+              const int* __restrict__ eb, int64_t eb_zs, TcOut out, int* flag) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + TSTAGES * STAGE_BYTES);
@@ -165,7 +175,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = blockIdx.x * TBN, m0 = blockIdx.y * TBM, z = blockIdx.z;
-    const int nk = K / TBK;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TSTAGES; ++s) {
@@ -177,7 +186,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TBN));
+                     "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -188,18 +197,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0 && lane == 0) {
         // TMA producer
         int issued = 0;
-        for (int kb = 0; kb < nk; ++kb) {
+        const int za = a_batched ? z : 0, zb = b_batched ? z : 0;
+        for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % TSTAGES;
             if (kb >= TSTAGES && !mbar_wait(&empty[s], ((kb / TSTAGES) + 1) & 1, flag)) break;
             unsigned char* st = smem + s * STAGE_BYTES;
+            const int kx = (kb0 + kb) * TBK;
             mbar_expect_tx(&full[s], STAGE_BYTES);
-            const int za = a_batched ? z : 0, zb = b_batched ? z : 0;
-            tma_load_3d(st, &mA0, kb * TBK, m0, za, &full[s]);
-            tma_load_3d(st + TILE_A, &mA1, kb * TBK, m0, za, &full[s]);
-            tma_load_3d(st + 2 * TILE_A, &mA2, kb * TBK, m0, za, &full[s]);
-            tma_load_3d(st + 3 * TILE_A, &mB0, kb * TBK, n0, zb, &full[s]);
-            tma_load_3d(st + 3 * TILE_A + TILE_B, &mB1, kb * TBK, n0, zb, &full[s]);
-            tma_load_3d(st + 3 * TILE_A + 2 * TILE_B, &mB2, kb * TBK, n0, zb, &full[s]);
+            tma_load_3d(st + 0 * TILE_A, &mA0, kx, m0, za, &full[s]);
+            tma_load_3d(st + 1 * TILE_A, &mA1, kx, m0, za, &full[s]);
+            tma_load_3d(st + 2 * TILE_A, &mA2, kx, m0, za, &full[s]);
+            tma_load_3d(st + 3 * TILE_A, &mA3, kx, m0, za, &full[s]);
+            unsigned char* sb = st + NPART * TILE_A;
+            tma_load_3d(sb + 0 * TILE_B, &mB0, kx, n0, zb, &full[s]);
+            tma_load_3d(sb + 1 * TILE_B, &mB1, kx, n0, zb, &full[s]);
+            tma_load_3d(sb + 2 * TILE_B, &mB2, kx, n0, zb, &full[s]);
+            tma_load_3d(sb + 3 * TILE_B, &mB3, kx, n0, zb, &full[s]);
             issued = kb + 1;
         }
         // drain: every issued stage must have landed before the CTA may exit
@@ -209,28 +222,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer
+        // MMA issuer: accumulator 0 gets h*h, accumulator 1 gets h*m + m*h (both exact),
+        // accumulator 2 the products below 2^-12 of the result
         const uint32_t idesc = idesc_bf16(TBM, TBN);
-        bool ok = true;
-        for (int kb = 0; kb < nk && ok; ++kb) {
+        const uint32_t t0 = tmem, t1 = tmem + TBN, t2 = tmem + 2 * TBN;
+        for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % TSTAGES;
-            if (!mbar_wait(&full[s], (kb / TSTAGES) & 1, flag)) { ok = false; break; }
+            if (!mbar_wait(&full[s], (kb / TSTAGES) & 1, flag)) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-            const uint64_t dA0 = smem_desc_sw128(base), dA1 = smem_desc_sw128(base + TILE_A),
-                           dA2 = smem_desc_sw128(base + 2 * TILE_A);
-            const uint64_t dB0 = smem_desc_sw128(base + 3 * TILE_A), dB1 = smem_desc_sw128(base + 3 * TILE_A + TILE_B),
-                           dB2 = smem_desc_sw128(base + 3 * TILE_A + 2 * TILE_B);
+            uint64_t a[NPART], b[NPART];
+#pragma unroll
+            for (int i = 0; i < NPART; ++i) {
+                a[i] = smem_desc_sw128(base + i * TILE_A);
+                b[i] = smem_desc_sw128(base + NPART * TILE_A + i * TILE_B);
+            }
 #pragma unroll
             for (int kk = 0; kk < TBK / 16; ++kk) {
-                const uint64_t off = (uint64_t)((kk * 32) >> 4);   // 16 bf16 = 32 bytes along K
-                // small products first, then the leading one
-                mma_bf16(tmem, dA0 + off, dB2 + off, idesc, (kb | kk) ? 1u : 0u);
-                mma_bf16(tmem, dA1 + off, dB1 + off, idesc, 1u);
-                mma_bf16(tmem, dA2 + off, dB0 + off, idesc, 1u);
-                mma_bf16(tmem, dA0 + off, dB1 + off, idesc, 1u);
-                mma_bf16(tmem, dA1 + off, dB0 + off, idesc, 1u);
-                mma_bf16(tmem, dA0 + off, dB0 + off, idesc, 1u);
+                const uint64_t o = (uint64_t)((kk * 32) >> 4);   // 16 bf16 = 32 bytes along K
+                const uint32_t first = (kb | kk) ? 1u : 0u;
+                mma_bf16(t0, a[0] + o, b[0] + o, idesc, first);          // h h
+                mma_bf16(t1, a[0] + o, b[1] + o, idesc, first);          // h m
+                mma_bf16(t1, a[1] + o, b[0] + o, idesc, 1u);             // m h
+                // below 2^-12: smallest first
+                mma_bf16(t2, a[2] + o, b[2] + o, idesc, first);          // r0 r0
+                mma_bf16(t2, a[1] + o, b[3] + o, idesc, 1u);             // m r1
+                mma_bf16(t2, a[3] + o, b[1] + o, idesc, 1u);             // r1 m
+                mma_bf16(t2, a[0] + o, b[3] + o, idesc, 1u);             // h r1
+                mma_bf16(t2, a[3] + o, b[0] + o, idesc, 1u);             // r1 h
+                mma_bf16(t2, a[1] + o, b[2] + o, idesc, 1u);             // m r0
+                mma_bf16(t2, a[2] + o, b[1] + o, idesc, 1u);             // r0 m
+                mma_bf16(t2, a[1] + o, b[1] + o, idesc, 1u);             // m m
+                mma_bf16(t2, a[0] + o, b[2] + o, idesc, 1u);             // h r0
+                mma_bf16(t2, a[2] + o, b[0] + o, idesc, 1u);             // r0 h
             }
             mma_commit(&empty[s]);
         }
@@ -241,29 +265,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int row = m0 + 32 * q + lane;
         if (mbar_wait(accum, 0, flag)) {
             asm volatile("tcgen05.fence::after_thread_sync;");
+            const int erow = (row < M) ? ea[(a_batched ? (int64_t)z * ea_zs : 0) + row] : 0;
+            const int* ebz = eb + (b_batched ? (int64_t)z * eb_zs : 0);
             for (int c = 0; c < TBN; c += 32) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+                float v0[32], v1[32], v2[32];
+                const uint32_t lanes = (uint32_t)(32 * q) << 16;
+                tmem_ld32(tmem + lanes + (uint32_t)c, v0);
+                tmem_ld32(tmem + lanes + (uint32_t)(TBN + c), v1);
+                tmem_ld32(tmem + lanes + (uint32_t)(2 * TBN + c), v2);
                 if (row >= M) continue;
                 const int nb = n0 + c;
                 if (out.mode == OUT_F64) {
                     double* o = (double*)out.p + (int64_t)z * out.zs + (int64_t)row * out.ld + nb;
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        if (nb + j < N) o[j] = out.accumulate ? o[j] + (double)v[j] : (double)v[j];
-                } else if (out.mode == OUT_F32) {
+                        if (nb + j < N) {
+                            const double v =
+                                ldexp((double)v0[j] + (double)v1[j] + (double)v2[j], erow + ebz[nb + j]);
+                            o[j] = out.accumulate ? o[j] + v : v;
+                        }
+                } else {
                     float* o = (float*)out.p + (int64_t)z * out.zs + (int64_t)row * out.ld + nb;
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        if (nb + j < N) o[j] = v[j];
-                } else {
-                    const int64_t o = (int64_t)z * out.zs + (int64_t)row * out.ld + nb;
-                    __nv_bfloat16* o0 = (__nv_bfloat16*)out.p + o;
-                    __nv_bfloat16* o1 = (__nv_bfloat16*)out.p2 + o;
-                    __nv_bfloat16* o2 = (__nv_bfloat16*)out.p3 + o;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (nb + j < N) split3(v[j], o0[j], o1[j], o2[j]);
+                        if (nb + j < N)
+                            o[j] = (float)ldexp((double)v0[j] + (double)v1[j] + (double)v2[j], erow + ebz[nb + j]);
                 }
             }
         }
@@ -272,82 +298,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TBN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
     }
 }
 
 // ---------------------------------------------------------------------------
-// operand preparation: FP64 -> three BF16 parts with zero padding
+// operand preparation: FP64 rows -> exponent + 6-bit head + three-part rest
 // ---------------------------------------------------------------------------
 
-// dst[b][i][k] for i < rows_pad, k < kpad  from  src(b, i, k) = src[b*sb + i*si + k*sk]
-// (zero outside rows x cols).
-__global__ void k_split(const double* __restrict__ src, int64_t rows, int64_t cols, int64_t si, int64_t sk,
-                        int64_t sb, int64_t rows_pad, int64_t kpad, __nv_bfloat16* __restrict__ d0,
-                        __nv_bfloat16* __restrict__ d1, __nv_bfloat16* __restrict__ d2) {
-    const int64_t b = blockIdx.y;
-    const int64_t n = rows_pad * kpad;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / kpad, k = e - i * kpad;
-        const float x = (i < rows && k < cols) ? (float)src[b * sb + i * si + k * sk] : 0.f;
-        split3(x, d0[b * n + e], d1[b * n + e], d2[b * n + e]);
-    }
-}
-
-// Core, step 1 in FP32 (terms grouped by their mode-0 vector c0):
-//   W[n][c0] = sum_{t in group(c0)} xin[t] P1[j][c1(t)] P2[l][c2(t)],  n = j*r2 + l,
-// written as three BF16 parts in K-major rows of length kpad. One thread per n
-// and 32 consecutive groups per CTA column.
-__global__ void __launch_bounds__(128) k_core_group_split(const float* __restrict__ P1t, const float* __restrict__ P2t,
-                                                          int r1, int r2, const int32_t* __restrict__ tcol,
-                                                          const double* __restrict__ xin,
-                                                          const int32_t* __restrict__ perm,
-                                                          const int32_t* __restrict__ off, int C0, int64_t kpad,
-                                                          __nv_bfloat16* __restrict__ w0, __nv_bfloat16* __restrict__ w1,
-                                                          __nv_bfloat16* __restrict__ w2) {
-    const int64_t nn = (int64_t)r1 * r2;
-    const int64_t n = blockIdx.x * 128 + threadIdx.x;
-    const int cb = blockIdx.y * 32;
-    if (n >= nn) return;
-    const int j = (int)(n / r2), l = (int)(n - (int64_t)j * r2);
-    float acc[32];
-#pragma unroll
-    for (int u = 0; u < 32; ++u) {
-        float a = 0.f;
-        const int c = cb + u;
-        if (c < C0) {
-            for (int k = off[c]; k < off[c + 1]; ++k) {
-                const int t = perm[k];
-                a = fmaf((float)xin[t] * P1t[(int64_t)tcol[3 * t + 1] * r1 + j], P2t[(int64_t)tcol[3 * t + 2] * r2 + l], a);
-            }
-        }
-        acc[u] = a;
-    }
-    __align__(16) __nv_bfloat16 h0[32], h1[32], h2[32];
-#pragma unroll
-    for (int u = 0; u < 32; ++u) split3(acc[u], h0[u], h1[u], h2[u]);
-    uint4* o0 = (uint4*)(w0 + n * kpad + cb);
-    uint4* o1 = (uint4*)(w1 + n * kpad + cb);
-    uint4* o2 = (uint4*)(w2 + n * kpad + cb);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        o0[u] = ((const uint4*)h0)[u];
-        o1[u] = ((const uint4*)h1)[u];
-        o2[u] = ((const uint4*)h2)[u];
-    }
-}
-
-__global__ void k_transpose_f32(const double* __restrict__ in, int64_t rows, int64_t cols, float* __restrict__ out) {
-    __shared__ float tile[32][33];
-    const int64_t c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int64_t r = r0 + k, c = c0 + threadIdx.x;
-        tile[k][threadIdx.x] = (r < rows && c < cols) ? (float)in[r * cols + c] : 0.f;
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int64_t c = c0 + k, r = r0 + threadIdx.x;
-        if (c < cols && r < rows) out[c * rows + r] = tile[threadIdx.x][k];
+// One warp per row r of `batch` stacked matrices of `rows` rows:
+//   x(b, i, k) = src[b*sb + i*si + k*sk] for k < cols, 0 for cols <= k < kpad;
+//   e = exponent with max_k |x| in [2^(e-1), 2^e) (0 for a zero row);
+//   x 2^-e = h + m + rest, h = trunc(64 x 2^-e)/64, m = trunc(4096 (x 2^-e - h))/4096,
+//   rest -> two BF16 parts.
+__global__ void k_split_fx(const double* __restrict__ src, int64_t rows, int64_t cols, int64_t si, int64_t sk,
+                           int64_t sb, int64_t batch, int64_t kpad, __nv_bfloat16* __restrict__ ph,
+                           __nv_bfloat16* __restrict__ pm, __nv_bfloat16* __restrict__ p0,
+                           __nv_bfloat16* __restrict__ p1, int* __restrict__ exps) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (warp >= rows * batch) return;
+    const int64_t b = warp / rows, i = warp - b * rows;
+    const double* x = src + b * sb + i * si;
+    double mx = 0.0;
+    for (int64_t k = lane; k < cols; k += 32) mx = fmax(mx, fabs(x[k * sk]));
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = mx > 0.0 ? ilogb(mx) + 1 : 0;
+    if (lane == 0) exps[warp] = e;
+    const int64_t off = warp * kpad;
+    for (int64_t k = lane; k < kpad; k += 32) {
+        const double v = k < cols ? ldexp(x[k * sk], -e) : 0.0;
+        const double hd = trunc(v * 64.0) * (1.0 / 64.0);             // |v - hd| < 2^-6
+        const double md = trunc((v - hd) * 4096.0) * (1.0 / 4096.0);  // |v - hd - md| < 2^-12
+        const double rest = (v - hd) - md;
+        ph[off + k] = __double2bfloat16(hd);   // exact: 6 significant bits
+        pm[off + k] = __double2bfloat16(md);   // exact: 6 significant bits
+        const __nv_bfloat16 r0 = __float2bfloat16_rn((float)rest);
+        p0[off + k] = r0;
+        p1[off + k] = __float2bfloat16_rn((float)(rest - (double)__bfloat162float(r0)));
     }
 }
 
@@ -383,9 +371,10 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t kpad, int6
 
 int64_t pad64(int64_t x) { return (x + 63) / 64 * 64; }
 
-struct Split {   // three BF16 parts of one operand
-    __nv_bfloat16* p[NPART] = {nullptr, nullptr, nullptr};
-    bool ok() const { return p[0] && p[1] && p[2]; }
+struct Fx {   // one operand in split form: head + three rest parts, and a row exponent
+    __nv_bfloat16* p[NPART] = {nullptr, nullptr, nullptr, nullptr};
+    int* e = nullptr;
+    bool ok() const { return p[0] && p[1] && p[2] && p[3] && e; }
 };
 
 // one scratch arena per call, from the stream-ordered allocator
@@ -400,10 +389,11 @@ struct Arena {
         ptrs.push_back(p);
         return (T*)p;
     }
-    Split split(int64_t n) {
-        Split s;
-        for (int i = 0; i < NPART; ++i) s.p[i] = get<__nv_bfloat16>(n);
-        return s;
+    Fx fx(int64_t rows_total, int64_t kpad) {
+        Fx f;
+        for (int i = 0; i < NPART; ++i) f.p[i] = get<__nv_bfloat16>(rows_total * kpad);
+        f.e = get<int>(rows_total);
+        return f;
     }
     ~Arena() {
         for (void* p : ptrs) cudaFreeAsync(p, st);
@@ -415,17 +405,17 @@ int tc_err(std::string* err, const std::string& msg, int code = LS_ERR_CUDA) {
     return code;
 }
 
-cudaError_t launch_split(const double* src, int64_t rows, int64_t cols, int64_t si, int64_t sk, int64_t sb, int64_t batch,
-                         int64_t rows_pad, int64_t kpad, Split d, cudaStream_t st) {
-    const int64_t n = rows_pad * kpad;
-    dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 4096), (unsigned)batch);
-    k_split<<<grid, 256, 0, st>>>(src, rows, cols, si, sk, sb, rows_pad, kpad, d.p[0], d.p[1], d.p[2]);
+cudaError_t launch_split_fx(const double* src, int64_t rows, int64_t cols, int64_t si, int64_t sk, int64_t sb,
+                            int64_t batch, int64_t kpad, Fx d, cudaStream_t st) {
+    const int64_t warps = rows * batch;
+    k_split_fx<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(src, rows, cols, si, sk, sb, batch, kpad, d.p[0],
+                                                                    d.p[1], d.p[2], d.p[3], d.e);
     count_kernels(1);
     return cudaGetLastError();
 }
 
-// D[z] = A[z] B[z]^T with A: batchA x M x kpad, B: batchB x N x kpad (three BF16 parts each)
-int gemm_tc(Split A, int64_t M, int64_t batchA, Split B, int64_t N, int64_t batchB, int64_t kpad, int64_t batch,
+// D[z] (+)= A[z] B[z]^T with A: batchA x M x kpad, B: batchB x N x kpad, both in split form
+int gemm_fx(const Fx& A, int64_t M, int64_t batchA, const Fx& B, int64_t N, int64_t batchB, int64_t kpad, int64_t batch,
             const TcOut& out, int* flag, cudaStream_t st, std::string* err) {
     if (M <= 0 || N <= 0 || batch <= 0) return LS_OK;
     if (kpad % TBK != 0) return tc_err(err, "tc gemm: K not padded", LS_ERR_ARG);
@@ -434,27 +424,37 @@ int gemm_tc(Split A, int64_t M, int64_t batchA, Split B, int64_t N, int64_t batc
         if (!make_map(&mA[i], A.p[i], M, kpad, batchA, TBM) || !make_map(&mB[i], B.p[i], N, kpad, batchB, TBN))
             return tc_err(err, "tc gemm: cuTensorMapEncodeTiled failed");
     const size_t smem = TSTAGES * STAGE_BYTES + 1024 + 256;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return tc_err(err, "tc gemm: cannot reserve shared memory");
-        attr = true;
-    }
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [&] {
+        attr_err = cudaFuncSetAttribute(k_fx_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr_err != cudaSuccess) return tc_err(err, "tc gemm: cannot reserve shared memory");
+    const int nkb_all = (int)(kpad / TBK);
+    const int chunk = KCHUNK / TBK;
     for (int64_t z0 = 0; z0 < batch; z0 += 65535) {
-        dim3 grid((unsigned)((N + TBN - 1) / TBN), (unsigned)((M + TBM - 1) / TBM),
-                  (unsigned)std::min<int64_t>(65535, batch - z0));
-        TcOut o = out;
-        if (z0) {
-            const size_t esz = out.mode == OUT_F64 ? 8 : out.mode == OUT_F32 ? 4 : 2;
-            o.p = (char*)out.p + z0 * out.zs * esz;
-            if (o.p2) o.p2 = (char*)out.p2 + z0 * out.zs * esz;
-            if (o.p3) o.p3 = (char*)out.p3 + z0 * out.zs * esz;
+        const int64_t nz = std::min<int64_t>(65535, batch - z0);
+        dim3 grid((unsigned)((N + TBN - 1) / TBN), (unsigned)((M + TBM - 1) / TBM), (unsigned)nz);
+        for (int kb0 = 0; kb0 < nkb_all; kb0 += chunk) {
+            TcOut o = out;
+            if (kb0 > 0) o.accumulate = 1;
+            const size_t esz = out.mode == OUT_F64 ? 8 : 4;
+            if (z0) o.p = (char*)out.p + z0 * out.zs * esz;
+            if (kb0 > 0 && out.mode != OUT_F64)
+                return tc_err(err, "tc gemm: K beyond one exact chunk needs FP64 output", LS_ERR_ARG);
+            // batched operands: the z offset goes through the tensor-map coordinate; the exponent
+            // arrays and the output are offset here for z0 > 0
+            const int* ea = A.e + (batchA > 1 ? z0 * M : 0);
+            const int* eb = B.e + (batchB > 1 ? z0 * N : 0);
+            if (z0 && (batchA > 1 || batchB > 1))
+                return tc_err(err, "tc gemm: more than 65535 batched slabs per call", LS_ERR_ARG);
+            k_fx_gemm<<<grid, TC_THREADS, smem, st>>>(mA[0], mA[1], mA[2], mA[3], mB[0], mB[1], mB[2], mB[3], (int)M,
+                                                      (int)N, kb0, std::min(chunk, nkb_all - kb0), batchA > 1,
+                                                      batchB > 1, ea, M, eb, N, o, flag);
+            count_kernels(1);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return tc_err(err, std::string("tc gemm launch: ") + cudaGetErrorString(e));
         }
-        k_tc_gemm<<<grid, TC_THREADS, smem, st>>>(mA[0], mA[1], mA[2], mB[0], mB[1], mB[2], (int)M, (int)N, (int)kpad,
-                                                  batchA > 1, batchB > 1, o, flag);
-        count_kernels(1);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return tc_err(err, std::string("tc gemm launch: ") + cudaGetErrorString(e));
     }
     return LS_OK;
 }
@@ -484,13 +484,13 @@ int tc_project(const double* Z, int r, const double* a, int64_t C, int64_t N, do
     Arena ar(st);
     Flag fl(ar, st);
     const int64_t kp = pad64(N);
-    Split zs = ar.split((int64_t)r * kp), as = ar.split(C * kp);
+    Fx zs = ar.fx(r, kp), as = ar.fx(C, kp);
     if (!fl.d || !zs.ok() || !as.ok()) return tc_err(err, "tc_project: out of memory", LS_ERR_OOM);
-    if (launch_split(Z, r, N, N, 1, 0, 1, r, kp, zs, st) != cudaSuccess ||
-        launch_split(a, C, N, N, 1, 0, 1, C, kp, as, st) != cudaSuccess)
+    if (launch_split_fx(Z, r, N, N, 1, 0, 1, kp, zs, st) != cudaSuccess ||
+        launch_split_fx(a, C, N, N, 1, 0, 1, kp, as, st) != cudaSuccess)
         return tc_err(err, "tc_project: split failed");
-    TcOut o{P, nullptr, nullptr, C, 0, OUT_F64, 0};
-    int rc = gemm_tc(zs, r, 1, as, C, 1, kp, 1, o, fl.d, st, err);
+    TcOut o{P, C, 0, OUT_F64, 0};
+    int rc = gemm_fx(zs, r, 1, as, C, 1, kp, 1, o, fl.d, st, err);
     if (rc != LS_OK) return rc;
     return fl.check(err);
 }
@@ -503,31 +503,27 @@ int tc_core(const double* P0, const double* P1, const double* P2, const int32_t*
     Arena ar(st);
     Flag fl(ar, st);
     const int64_t nn = (int64_t)r[1] * r[2];
-    // W rows of all groups would take nn * kpad * 4 bytes; chunk the groups to ~1 GB
-    const int64_t kp_all = pad64(C[0]);
-    const int64_t chunk = std::max<int64_t>(64, std::min<int64_t>(kp_all, ((int64_t)1 << 28) / std::max<int64_t>(nn, 1) / 64 * 64));
-    float* P1t = ar.get<float>((int64_t)C[1] * r[1]);
-    float* P2t = ar.get<float>((int64_t)C[2] * r[2]);
-    Split w = ar.split(nn * chunk);
-    Split p0 = ar.split((int64_t)r[0] * chunk);
-    if (!fl.d || !P1t || !P2t || !w.ok() || !p0.ok()) return tc_err(err, "tc_core: out of memory", LS_ERR_OOM);
-    dim3 tg1((unsigned)((C[1] + 31) / 32), (unsigned)((r[1] + 31) / 32));
-    k_transpose_f32<<<tg1, dim3(32, 8), 0, st>>>(P1, r[1], C[1], P1t);
-    dim3 tg2((unsigned)((C[2] + 31) / 32), (unsigned)((r[2] + 31) / 32));
-    k_transpose_f32<<<tg2, dim3(32, 8), 0, st>>>(P2, r[2], C[2], P2t);
-    count_kernels(2);
+    // step 1 (FP64, grouped by c0): W[c][n]; chunks of the groups bound W to ~256 MB
+    const int64_t chunk = std::max<int64_t>(
+        64, std::min<int64_t>(pad64(C[0]), ((int64_t)32 << 20) / std::max<int64_t>(nn, 1) / 64 * 64));
+    double* P1t = ar.get<double>((int64_t)C[1] * r[1]);
+    double* P2t = ar.get<double>((int64_t)C[2] * r[2]);
+    double* W = ar.get<double>(chunk * nn);
+    Fx w = ar.fx(nn, chunk), p0 = ar.fx(r[0], chunk);
+    if (!fl.d || !P1t || !P2t || !W || !w.ok() || !p0.ok()) return tc_err(err, "tc_core: out of memory", LS_ERR_OOM);
+    if (launch_transpose(P1, r[1], C[1], P1t, st) != cudaSuccess || launch_transpose(P2, r[2], C[2], P2t, st) != cudaSuccess)
+        return tc_err(err, "tc_core: transpose failed");
     for (int64_t c0 = 0; c0 < C[0]; c0 += chunk) {
         const int64_t cw = std::min<int64_t>(chunk, C[0] - c0);
         const int64_t kp = pad64(cw);
-        dim3 g((unsigned)((nn + 127) / 128), (unsigned)(kp / 32));
-        // groups beyond C0 inside the padded range come out as zeros
-        k_core_group_split<<<g, 128, 0, st>>>(P1t, P2t, r[1], r[2], tcol, xin, perm, off + c0, (int)cw, kp, w.p[0],
-                                              w.p[1], w.p[2]);
-        count_kernels(1);
-        if (launch_split(P0 + c0, r[0], cw, C[0], 1, 0, 1, r[0], kp, p0, st) != cudaSuccess)
+        if (launch_core_group(P1t, P2t, r[1], r[2], tcol, xin, perm, off, (int)c0, (int)cw, W, st) != cudaSuccess)
+            return tc_err(err, "tc_core: grouping failed");
+        // step 2 on tensor cores: B_(0)[i][n] (+)= sum_c P0[i][c0 + c] W[c][n]
+        if (launch_split_fx(W, nn, cw, 1, nn, 0, 1, kp, w, st) != cudaSuccess ||
+            launch_split_fx(P0 + c0, r[0], cw, C[0], 1, 0, 1, kp, p0, st) != cudaSuccess)
             return tc_err(err, "tc_core: split failed");
-        TcOut o{B, nullptr, nullptr, nn, 0, OUT_F64, c0 > 0 ? 1 : 0};
-        int rc = gemm_tc(p0, r[0], 1, w, nn, 1, kp, 1, o, fl.d, st, err);
+        TcOut o{B, nn, 0, OUT_F64, c0 > 0 ? 1 : 0};
+        int rc = gemm_fx(p0, r[0], 1, w, nn, 1, kp, 1, o, fl.d, st, err);
         if (rc != LS_OK) return rc;
     }
     if (cudaGetLastError() != cudaSuccess) return tc_err(err, "tc_core: launch failed");
@@ -544,28 +540,26 @@ int tc_eval(const double* const Z[3], const int32_t* r, const double* B, int64_t
     const int64_t k1 = pad64(r1), k0 = pad64(r0);
     // M_s[a][b] = sum_k B[a][b][k] Z2[k][z_s]: small, FP64 CUDA cores
     double* M = ar.get<double>((int64_t)r0 * r1 * nslab);
-    Split z1t = ar.split(N * k1), z0t = ar.split(N * k0), ms = ar.split((int64_t)nslab * r0 * k1);
-    Split tt = ar.split((int64_t)nslab * N * k0);
-    if (!fl.d || !M || !z1t.ok() || !z0t.ok() || !ms.ok() || !tt.ok()) return tc_err(err, "tc_eval: out of memory", LS_ERR_OOM);
+    double* Tt = ar.get<double>((int64_t)nslab * N * r0);
+    Fx z1t = ar.fx(N, k1), z0t = ar.fx(N, k0), ms = ar.fx((int64_t)nslab * r0, k1), tt = ar.fx((int64_t)nslab * N, k0);
+    if (!fl.d || !M || !Tt || !z1t.ok() || !z0t.ok() || !ms.ok() || !tt.ok())
+        return tc_err(err, "tc_eval: out of memory", LS_ERR_OOM);
     cudaError_t e = launch_eval_m(Z[2], r, B, N, zidx, nslab, M, st);
     if (e != cudaSuccess) return tc_err(err, std::string("tc_eval: ") + cudaGetErrorString(e));
     // operands: Z1^T [y][b], Z0^T [x][a] (K-major), M_s [a][b] per slab
-    if (launch_split(Z[1], N, r1, 1, N, 0, 1, N, k1, z1t, st) != cudaSuccess ||
-        launch_split(Z[0], N, r0, 1, N, 0, 1, N, k0, z0t, st) != cudaSuccess ||
-        launch_split(M, r0, r1, (int64_t)r1 * nslab, nslab, 1, nslab, r0, k1, ms, st) != cudaSuccess)
+    if (launch_split_fx(Z[1], N, r1, 1, N, 0, 1, k1, z1t, st) != cudaSuccess ||
+        launch_split_fx(Z[0], N, r0, 1, N, 0, 1, k0, z0t, st) != cudaSuccess ||
+        launch_split_fx(M, r0, r1, (int64_t)r1 * nslab, nslab, 1, nslab, k1, ms, st) != cudaSuccess)
         return tc_err(err, "tc_eval: split failed");
-    // T_s^T[y][a] = sum_b Z1^T[y][b] M_s[a][b], written directly as three BF16 parts
-    TcOut o1{tt.p[0], tt.p[1], tt.p[2], k0, N * k0, OUT_SPLIT, 0};
-    if (k0 > r0) {   // the padding columns a in [r0, k0) of T^T must read as zeros
-        for (int i = 0; i < NPART; ++i)
-            if (cudaMemsetAsync(tt.p[i], 0, (size_t)nslab * N * k0 * 2, st) != cudaSuccess)
-                return tc_err(err, "tc_eval: memset failed");
-    }
-    int rc = gemm_tc(z1t, N, 1, ms, r0, nslab, k1, nslab, o1, fl.d, st, err);
+    // T_s^T[y][a] = sum_b Z1^T[y][b] M_s[a][b]   (FP64 out)
+    TcOut o1{Tt, r0, N * r0, OUT_F64, 0};
+    int rc = gemm_fx(z1t, N, 1, ms, r0, nslab, k1, nslab, o1, fl.d, st, err);
     if (rc != LS_OK) return rc;
+    if (launch_split_fx(Tt, N, r0, r0, 1, N * r0, nslab, k0, tt, st) != cudaSuccess)
+        return tc_err(err, "tc_eval: split failed");
     // S_s[x][y] = sum_a Z0^T[x][a] T_s^T[y][a]
-    TcOut o2{out, nullptr, nullptr, N, N * N, out_f32 ? OUT_F32 : OUT_F64, 0};
-    rc = gemm_tc(z0t, N, 1, tt, N, nslab, k0, nslab, o2, fl.d, st, err);
+    TcOut o2{out, N, N * N, out_f32 ? OUT_F32 : OUT_F64, 0};
+    rc = gemm_fx(z0t, N, 1, tt, N, nslab, k0, nslab, o2, fl.d, st, err);
     if (rc != LS_OK) return rc;
     return fl.check(err);
 }

@@ -49,12 +49,14 @@ class ls_defect(C.Structure):
 class ls_tucker_info(C.Structure):
     _fields_ = [("r", C.c_int32 * 3), ("C", C.c_int32 * 3), ("T", C.c_int64),
                 ("sigma_discarded", C.c_double * 3), ("sigma_total", C.c_double * 3),
-                ("xi_norm", C.c_double), ("bound_abs", C.c_double), ("sweeps", C.c_int32 * 3)]
+                ("xi_norm", C.c_double), ("bound_abs", C.c_double), ("sweeps", C.c_int32 * 3),
+                ("rotations", C.c_int64 * 3)]
 
     def as_dict(self):
         return {"r": list(self.r), "C": list(self.C), "T": int(self.T),
                 "sigma_discarded": list(self.sigma_discarded), "sigma_total": list(self.sigma_total),
-                "xi_norm": self.xi_norm, "bound_abs": self.bound_abs, "sweeps": list(self.sweeps)}
+                "xi_norm": self.xi_norm, "bound_abs": self.bound_abs, "sweeps": list(self.sweeps),
+                "rotations": list(self.rotations)}
 
 
 class LatticeSumError(RuntimeError):
