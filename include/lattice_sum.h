@@ -137,6 +137,7 @@ typedef struct {
                                 /* C_l * floor_l, floor_l = 8 u T (u = 2^-53)             */
     int32_t sweeps[3];          /* eigen-solver sweeps per mode                          */
     int64_t rotations[3];       /* Jacobi rotations applied per mode (all sweeps)        */
+    int32_t pivots[3];          /* columns kept by the pivoted Cholesky pre-compression  */
 } ls_tucker_info;
 
 /*
@@ -192,6 +193,24 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n);
  */
 int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ranks,
                               ls_tucker_info* info);
+
+/*
+ * lattice_sum_batch_reduce -- the batched form: RHOSVD of n independent
+ * contexts (each created and given its defects as usual) in one call.
+ * Every context is reduced exactly as lattice_sum_rhosvd_reduce(ctx, eps)
+ * would reduce it; what changes is the schedule. The pivoted-Cholesky
+ * pre-compression and the Jacobi iteration of all 3n modes run as one
+ * persistent cooperative launch each on the stream of ctxs[0], every mode
+ * on its own group of CTAs (a single CTA, with no grid barrier, when the
+ * batch is large); the per-context steps run on each context's own stream,
+ * ordered against the shared launches by events. `infos` (host, n entries,
+ * may be NULL) receives each context's ls_tucker_info. Synchronises all the
+ * streams. Errors: LS_ERR_ARG (NULL or repeated context, eps <= 0),
+ * LS_ERR_STATE (a context already reduced), and the errors of
+ * lattice_sum_rhosvd_reduce; the message is on the failing context and on
+ * lattice_sum_last_error(NULL).
+ */
+int lattice_sum_batch_reduce(ls_ctx* const* ctxs, int32_t n, double eps, ls_tucker_info* infos);
 
 /*
  * lattice_sum_eval_slab -- Tucker tensor values on z-slabs.

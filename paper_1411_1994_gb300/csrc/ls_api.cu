@@ -450,108 +450,179 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n) {
     return LS_OK;
 }
 
-int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ranks, ls_tucker_info* info) {
-    if (!ctx) return fail(nullptr, LS_ERR_ARG, "rhosvd_reduce: NULL context");
-    if (ctx->reduced) return fail(ctx, LS_ERR_STATE, "rhosvd_reduce: already reduced");
-    if (!forced_ranks && !(eps > 0.0)) return fail(ctx, LS_ERR_ARG, "rhosvd_reduce: eps must be > 0");
-    const int64_t N = ctx->p.N;
-    const int64_t T = (int64_t)ctx->xi.size();
-    cudaStream_t st = ctx->st;
-    // term maps and weights
-    CU(dalloc(ctx, &ctx->d_tcol, 3 * T));
-    CU(dalloc(ctx, &ctx->d_xi, T));
-    CU(dalloc(ctx, &ctx->d_xin, T));
-    CU(cudaMemcpyAsync(ctx->d_tcol, ctx->tcol.data(), 3 * T * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    count_h2d(3 * T * sizeof(int32_t));
-    CU(cudaMemcpyAsync(ctx->d_xi, ctx->xi.data(), T * sizeof(double), cudaMemcpyHostToDevice, st));
-    count_h2d(T * sizeof(double));
+}  // extern "C"
+
+namespace {
+
+// Scratch of one mode of one context during the reduction.
+struct RedMode {
+    double *G = nullptr, *L = nullptr, *pd = nullptr, *cand = nullptr, *H = nullptr, *V = nullptr, *snap = nullptr,
+           *isl = nullptr, *w = nullptr;
+    int32_t *piv = nullptr, *perm = nullptr;
+    int k = 0;
+};
+
+// One context inside a (possibly batched) reduction.
+struct RedState {
+    ls_ctx* ctx = nullptr;
+    double eps = 0.0;
+    const int32_t* forced = nullptr;
     DevStatus* d_st = nullptr;   // one status block per mode + one for CholeskyQR2
-    CU(dalloc(ctx, &d_st, 4));
-    CU(cudaMemsetAsync(d_st, 0, 4 * sizeof(DevStatus), st));
     double* d_sel = nullptr;
-    CU(dalloc(ctx, &d_sel, 9));
-    double* d_G[3];
-    double* d_V[3];
-    double* d_snap[3];
-    int32_t* d_perm[3];
-    double* d_isl[3];
-    double* d_w[3];
-    JacobiJob jobs[3];
-    // (c1) unit vectors, weighted Gram matrices, eigen-decomposition of all modes at once
+    RedMode m[3];
+    int sweeps[3] = {0, 0, 0};
+    double sel[3][3] = {};
+    DevStatus hs[4] = {};
+    double floor_noise = 0.0;
+    int64_t T = 0;
+};
+
+#define CUS(call)                                                                                     \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(R.ctx, e_ == cudaErrorMemoryAllocation ? LS_ERR_OOM : LS_ERR_CUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                                  \
+    } while (0)
+
+// terms to the device, unit vectors, weighted Gram matrices, pivoted-Cholesky jobs
+int red_prepare(RedState& R, PcholJob* pj) {
+    ls_ctx* ctx = R.ctx;
+    cudaStream_t st = ctx->st;
+    const int64_t N = ctx->p.N;
+    const int64_t T = R.T = (int64_t)ctx->xi.size();
+    R.floor_noise = 8.0 * 1.1102230246251565e-16 * (double)T;   // rounding noise of the Gram matrix (trace T)
+    CUS(dalloc(ctx, &ctx->d_tcol, 3 * T));
+    CUS(dalloc(ctx, &ctx->d_xi, T));
+    CUS(dalloc(ctx, &ctx->d_xin, T));
+    CUS(cudaMemcpyAsync(ctx->d_tcol, ctx->tcol.data(), 3 * T * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    count_h2d(3 * T * sizeof(int32_t));
+    CUS(cudaMemcpyAsync(ctx->d_xi, ctx->xi.data(), T * sizeof(double), cudaMemcpyHostToDevice, st));
+    count_h2d(T * sizeof(double));
+    CUS(dalloc(ctx, &R.d_st, 4));
+    CUS(cudaMemsetAsync(R.d_st, 0, 4 * sizeof(DevStatus), st));
+    CUS(dalloc(ctx, &R.d_sel, 9));
     for (int l = 0; l < 3; ++l) {
         ModeCols& mc = ctx->mode[l];
+        RedMode& M = R.m[l];
         const int64_t C = mc.C;
-        CU(dalloc(ctx, &ctx->d_norms[l], C));
-        CU(dalloc(ctx, &ctx->d_sigma[l], C));
-        CU(dalloc(ctx, &d_G[l], C * C));
-        CU(dalloc(ctx, &d_V[l], C * C));
-        CU(dalloc(ctx, &d_snap[l], 6 * (C / 2 + 1)));
-        CU(dalloc(ctx, &d_perm[l], C));
-        CU(dalloc(ctx, &d_isl[l], C));
-        CU(dalloc(ctx, &d_w[l], C));
+        CUS(dalloc(ctx, &ctx->d_norms[l], C));
+        CUS(dalloc(ctx, &ctx->d_sigma[l], C));
+        CUS(dalloc(ctx, &M.G, C * C));
+        CUS(dalloc(ctx, &M.L, C * C));
+        CUS(dalloc(ctx, &M.pd, C));
+        CUS(dalloc(ctx, &M.cand, kPcholCand));
+        CUS(dalloc(ctx, &M.piv, C));
+        CUS(dalloc(ctx, &M.w, C));
+        CUS(cudaMemsetAsync(ctx->d_sigma[l], 0, C * sizeof(double), st));
         std::vector<double> w(C);
         for (int64_t c = 0; c < C; ++c) w[c] = sqrt((double)mc.count[c]);
-        CU(cudaMemcpyAsync(d_w[l], w.data(), C * sizeof(double), cudaMemcpyHostToDevice, st));
+        CUS(cudaMemcpyAsync(M.w, w.data(), C * sizeof(double), cudaMemcpyHostToDevice, st));
         count_h2d(C * sizeof(double));
-        { Scope sc("norms", st); CU(launch_norm_columns(mc.d_cols, C, N, ctx->d_norms[l], st)); }
-        { Scope sc("gram", st); CU(launch_gram_weighted(mc.d_cols, C, N, d_w[l], d_G[l], st)); }
-        CU(launch_identity(d_V[l], C, st));
-        // entries below the rounding noise of the FP64 Gram matrix (~ u * trace, trace = T) are
-        // left alone: rotating them only reshuffles noise
-        // directions whose Rayleigh quotients both stay below tau = 1e-3 eps^2 T / C are discarded
-        // together whatever their mixing (their block has trace < 1e-3 eps^2 T); forced ranks
-        // resolve everything
-        const double tau = forced_ranks ? 0.0 : 1e-3 * eps * eps * (double)T / (double)C;
-        jobs[l] = JacobiJob{d_G[l], d_V[l], d_snap[l], d_st + l, C, 8.0 * 1.1102230246251565e-16 * (double)T, tau};
+        { Scope sc("norms", st); CUS(launch_norm_columns(mc.d_cols, C, N, ctx->d_norms[l], st)); }
+        { Scope sc("gram", st); CUS(launch_gram_weighted(mc.d_cols, C, N, M.w, M.G, st)); }
+        // pivoted Cholesky: the energy left outside the pivot columns (<= delta) is discarded with
+        // the tail; with the eps rule delta = 1e-4 eps^2 T, with forced ranks the Gram noise
+        const double delta = R.forced ? (double)C * R.floor_noise : 1e-4 * R.eps * R.eps * (double)T;
+        pj[l] = PcholJob{M.G, M.L, M.pd, M.cand, M.piv, R.d_st + l, C, (int)C, delta};
     }
-    { Scope sc("jacobi", st); CU(launch_jacobi_multi(jobs, 3, 60, 1e-14, ctx->num_sms, st)); }
+    return LS_OK;
+}
+
+// after the pivoted Cholesky (statuses in R.hs): H = L^T L and the Jacobi jobs
+int red_after_pchol(RedState& R, JacobiJob* jj) {
+    ls_ctx* ctx = R.ctx;
+    cudaStream_t st = ctx->st;
+    for (int l = 0; l < 3; ++l)
+        if (R.hs[l].flag == FLAG_TIMEOUT)
+            return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: pivoted Cholesky barrier timed out (mode %d)", l);
+    CUS(cudaMemsetAsync(R.d_st, 0, 4 * sizeof(DevStatus), st));
     for (int l = 0; l < 3; ++l) {
-        const int forced = forced_ranks ? std::max(1, forced_ranks[l]) : 0;
+        RedMode& M = R.m[l];
+        const int k = M.k = std::max(1, R.hs[l].sweeps);
+        CUS(dalloc(ctx, &M.H, (int64_t)k * k));
+        CUS(dalloc(ctx, &M.V, (int64_t)k * k));
+        CUS(dalloc(ctx, &M.snap, 6 * (k / 2 + 1)));
+        CUS(dalloc(ctx, &M.perm, k));
+        CUS(dalloc(ctx, &M.isl, k));
+        { Scope sc("pchol", st); CUS(launch_pchol_gram(M.L, ctx->mode[l].C, ctx->mode[l].C, k, M.H, st)); }
+        CUS(launch_identity(M.V, k, st));
+        // directions whose Rayleigh quotients both stay below tau = 1e-3 eps^2 T / k are discarded
+        // together whatever their mixing; forced ranks resolve everything
+        const double tau = R.forced ? 0.0 : 1e-3 * R.eps * R.eps * (double)R.T / (double)k;
+        jj[l] = JacobiJob{M.H, M.V, M.snap, R.d_st + l, k, R.floor_noise, tau};
+    }
+    return LS_OK;
+}
+
+// eps-rank selection on the eigenvalues of H (the pivoted-Cholesky residual joins the tail)
+int red_select(RedState& R) {
+    ls_ctx* ctx = R.ctx;
+    cudaStream_t st = ctx->st;
+    for (int l = 0; l < 3; ++l) {
+        RedMode& M = R.m[l];
+        const int forced = R.forced ? std::max(1, R.forced[l]) : 0;
         Scope sc("select", st);
-        const double resolution = jobs[l].abs_floor;   // eigenvalues below the Gram matrix's noise
-        CU(launch_sort_select(d_G[l], ctx->mode[l].C, eps, forced, resolution, d_perm[l], ctx->d_sigma[l], d_isl[l],
-                              d_sel + 3 * l, st));
+        CUS(launch_sort_select(M.H, M.k, R.eps, forced, R.floor_noise, M.cand + kPcholCand - 1, M.perm,
+                               ctx->d_sigma[l], M.isl, R.d_sel + 3 * l, st));
     }
-    DevStatus hs[4];
-    double sel[3][3];
-    CU(cudaMemcpyAsync(hs, d_st, 3 * sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    CUS(cudaMemcpyAsync(R.hs, R.d_st, 3 * sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
     count_d2h(3 * sizeof(DevStatus));
-    CU(cudaMemcpyAsync(sel, d_sel, sizeof sel, cudaMemcpyDeviceToHost, st));
-    count_d2h(sizeof sel);
-    CU(cudaStreamSynchronize(st));
-    int sweeps[3];
+    CUS(cudaMemcpyAsync(R.sel, R.d_sel, sizeof R.sel, cudaMemcpyDeviceToHost, st));
+    count_d2h(sizeof R.sel);
+    return LS_OK;
+}
+
+// after the selection (host copies ready): basis, CholeskyQR2, projection, core, info
+int red_finish(RedState& R, ls_tucker_info* info) {
+    ls_ctx* ctx = R.ctx;
+    cudaStream_t st = ctx->st;
+    const int64_t N = ctx->p.N;
+    const int64_t T = R.T;
     for (int l = 0; l < 3; ++l) {
-        if (hs[l].flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Jacobi grid barrier timed out (mode %d)", l);
-        if (hs[l].flag == FLAG_NOCONVERGE || hs[l].sweeps <= 0)
+        if (R.hs[l].flag == FLAG_TIMEOUT)
+            return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Jacobi grid barrier timed out (mode %d)", l);
+        if (R.hs[l].flag == FLAG_NOCONVERGE || R.hs[l].sweeps <= 0)
             return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: Jacobi did not converge (mode %d)", l);
-        sweeps[l] = hs[l].sweeps;
-        ctx->r[l] = (int32_t)sel[l][0];
+        R.sweeps[l] = R.hs[l].sweeps;
+        ctx->r[l] = (int32_t)R.sel[l][0];
     }
-    // (c1) basis + CholeskyQR2, (c2) projection
+    int64_t rotations[3];
+    for (int l = 0; l < 3; ++l) {
+        int64_t rot = 0;
+        for (int k = 0; k < R.sweeps[l] && k < 64; ++k) rot += R.hs[l].sweep_active[k];
+        rotations[l] = rot;
+    }
     for (int l = 0; l < 3; ++l) {
         ModeCols& mc = ctx->mode[l];
+        RedMode& M = R.m[l];
         const int64_t C = mc.C;
         const int r = ctx->r[l];
-        double* work = nullptr;
-        double* ytmp = nullptr;
-        CU(dalloc(ctx, &ctx->d_Z[l], (int64_t)r * N));
-        CU(dalloc(ctx, &ctx->d_P[l], (int64_t)r * C));
-        CU(dalloc(ctx, &work, 2 * (int64_t)r * r));
-        CU(dalloc(ctx, &ytmp, (int64_t)r * N));
-        { Scope sc("basis", st); CU(launch_basis(d_V[l], C, d_perm[l], d_isl[l], d_w[l], mc.d_cols, N, r, ctx->d_Z[l], st)); }
-        { Scope sc("cholqr2", st); CU(launch_cholqr2(ctx->d_Z[l], ytmp, r, N, work, d_st + 3, ctx->num_sms, st)); }
+        double *work = nullptr, *ytmp = nullptr, *vg = nullptr;
+        CUS(dalloc(ctx, &ctx->d_Z[l], (int64_t)r * N));
+        CUS(dalloc(ctx, &ctx->d_P[l], (int64_t)r * C));
+        CUS(dalloc(ctx, &work, 2 * (int64_t)r * r));
+        CUS(dalloc(ctx, &ytmp, (int64_t)r * N));
+        CUS(dalloc(ctx, &vg, C * M.k));
+        {
+            Scope sc("basis", st);
+            CUS(launch_pchol_vectors(M.L, C, C, M.k, M.V, M.H, vg, st));
+            CUS(launch_basis(vg, C, M.k, M.perm, M.isl, M.w, mc.d_cols, N, r, ctx->d_Z[l], st));
+        }
+        { Scope sc("cholqr2", st); CUS(launch_cholqr2(ctx->d_Z[l], ytmp, r, N, work, R.d_st + 3, ctx->num_sms, st)); }
         if (ctx->p.precision == LS_MIXED) {
             Scope sc("project", st);
             int rc = tc_project(ctx->d_Z[l], r, mc.d_cols, C, N, ctx->d_P[l], st, &ctx->err);
             if (rc != LS_OK) return rc;
         } else {
             Scope sc("project", st);
-            CU(launch_project(ctx->d_Z[l], r, mc.d_cols, C, N, ctx->d_P[l], st));
+            CUS(launch_project(ctx->d_Z[l], r, mc.d_cols, C, N, ctx->d_P[l], st));
         }
         dfree(ctx, work);
         dfree(ctx, ytmp);
+        dfree(ctx, vg);
     }
-    { Scope sc("fold", st); CU(launch_fold_norms(ctx->d_xi, ctx->d_tcol, T, ctx->d_norms[0], ctx->d_norms[1], ctx->d_norms[2], ctx->d_xin, st)); }
+    { Scope sc("fold", st); CUS(launch_fold_norms(ctx->d_xi, ctx->d_tcol, T, ctx->d_norms[0], ctx->d_norms[1], ctx->d_norms[2], ctx->d_xin, st)); }
     // (c3) core: terms grouped by their mode-0 vector (counting sort on the host)
     int32_t Cs[3] = {(int32_t)ctx->mode[0].C, (int32_t)ctx->mode[1].C, (int32_t)ctx->mode[2].C};
     std::vector<int32_t> off(Cs[0] + 1, 0), perm(T);
@@ -561,16 +632,15 @@ int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ran
         std::vector<int32_t> pos(off.begin(), off.end() - 1);
         for (int64_t t = 0; t < T; ++t) perm[pos[ctx->tcol[3 * t]]++] = (int32_t)t;
     }
-    int32_t* d_perm_t = nullptr;
-    int32_t* d_off = nullptr;
-    CU(dalloc(ctx, &d_perm_t, T));
-    CU(dalloc(ctx, &d_off, Cs[0] + 1));
-    CU(cudaMemcpyAsync(d_perm_t, perm.data(), T * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    int32_t *d_perm_t = nullptr, *d_off = nullptr;
+    CUS(dalloc(ctx, &d_perm_t, T));
+    CUS(dalloc(ctx, &d_off, Cs[0] + 1));
+    CUS(cudaMemcpyAsync(d_perm_t, perm.data(), T * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     count_h2d(T * sizeof(int32_t));
-    CU(cudaMemcpyAsync(d_off, off.data(), (Cs[0] + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CUS(cudaMemcpyAsync(d_off, off.data(), (Cs[0] + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     count_h2d((Cs[0] + 1) * sizeof(int32_t));
     const int64_t core_n = (int64_t)ctx->r[0] * ctx->r[1] * ctx->r[2];
-    CU(dalloc(ctx, &ctx->d_B, core_n));
+    CUS(dalloc(ctx, &ctx->d_B, core_n));
     {
         Scope sc_core("core", st);
         const int64_t nn = (int64_t)ctx->r[1] * ctx->r[2];
@@ -580,71 +650,165 @@ int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ran
                              T, ctx->d_B, ctx->num_sms, st, &ctx->err);
             if (rc != LS_OK) return rc;
         } else {
-            double* P1t = nullptr;
-            double* P2t = nullptr;
-            double* W = nullptr;
-            CU(dalloc(ctx, &P1t, (int64_t)Cs[1] * ctx->r[1]));
-            CU(dalloc(ctx, &P2t, (int64_t)Cs[2] * ctx->r[2]));
-            CU(dalloc(ctx, &W, w_cols * nn));
-            CU(launch_transpose(ctx->d_P[1], ctx->r[1], Cs[1], P1t, st));
-            CU(launch_transpose(ctx->d_P[2], ctx->r[2], Cs[2], P2t, st));
-            CU(launch_core_f64(ctx->d_P[0], P1t, P2t, Cs, ctx->r, ctx->d_tcol, ctx->d_xin, d_perm_t, d_off, W, w_cols,
-                               ctx->d_B, st));
+            double *P1t = nullptr, *P2t = nullptr, *W = nullptr;
+            CUS(dalloc(ctx, &P1t, (int64_t)Cs[1] * ctx->r[1]));
+            CUS(dalloc(ctx, &P2t, (int64_t)Cs[2] * ctx->r[2]));
+            CUS(dalloc(ctx, &W, w_cols * nn));
+            CUS(launch_transpose(ctx->d_P[1], ctx->r[1], Cs[1], P1t, st));
+            CUS(launch_transpose(ctx->d_P[2], ctx->r[2], Cs[2], P2t, st));
+            CUS(launch_core_f64(ctx->d_P[0], P1t, P2t, Cs, ctx->r, ctx->d_tcol, ctx->d_xin, d_perm_t, d_off, W, w_cols,
+                                ctx->d_B, st));
             dfree(ctx, P1t);
             dfree(ctx, P2t);
             dfree(ctx, W);
         }
     }
     for (int l = 0; l < 3; ++l) {
-        dfree(ctx, d_G[l]);
-        dfree(ctx, d_V[l]);
-        dfree(ctx, d_snap[l]);
-        dfree(ctx, d_perm[l]);
-        dfree(ctx, d_isl[l]);
-        dfree(ctx, d_w[l]);
+        RedMode& M = R.m[l];
+        for (void* q : {(void*)M.G, (void*)M.L, (void*)M.pd, (void*)M.cand, (void*)M.H, (void*)M.V, (void*)M.snap,
+                        (void*)M.isl, (void*)M.w, (void*)M.piv, (void*)M.perm})
+            dfree(ctx, q);
     }
     dfree(ctx, d_perm_t);
     dfree(ctx, d_off);
-    dfree(ctx, d_sel);
-    // CholeskyQR2 status (read together with the info below)
-    CU(cudaMemcpyAsync(&hs[3], d_st + 3, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    dfree(ctx, R.d_sel);
+    CUS(cudaMemcpyAsync(&R.hs[3], R.d_st + 3, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
     count_d2h(sizeof(DevStatus));
     double xin_norm2 = 0.0;
     if (info) {
         std::vector<double> xin(T);
-        CU(cudaMemcpyAsync(xin.data(), ctx->d_xin, T * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUS(cudaMemcpyAsync(xin.data(), ctx->d_xin, T * sizeof(double), cudaMemcpyDeviceToHost, st));
         count_d2h(T * sizeof(double));
-        CU(cudaStreamSynchronize(st));
+        CUS(cudaStreamSynchronize(st));
         for (double v : xin) xin_norm2 += v * v;
     } else {
-        CU(cudaStreamSynchronize(st));
+        CUS(cudaStreamSynchronize(st));
     }
-    dfree(ctx, d_st);
-    if (hs[3].flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Cholesky grid barrier timed out");
-    if (hs[3].flag == FLAG_NOT_SPD) return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: CholeskyQR2 met a non-positive pivot");
+    dfree(ctx, R.d_st);
+    if (R.hs[3].flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Cholesky grid barrier timed out");
+    if (R.hs[3].flag == FLAG_NOT_SPD) return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: CholeskyQR2 met a non-positive pivot");
     if (info) {
         memset(info, 0, sizeof *info);
         double ssum = 0.0;
         for (int l = 0; l < 3; ++l) {
             info->r[l] = ctx->r[l];
             info->C[l] = Cs[l];
-            info->sigma_discarded[l] = sqrt(std::max(sel[l][1], 0.0));
-            info->sigma_total[l] = sqrt(std::max(sel[l][2], 0.0));
-            info->sweeps[l] = sweeps[l];
-            int64_t rot = 0;
-            for (int k = 0; k < sweeps[l] && k < 64; ++k) rot += hs[l].sweep_active[k];
-            info->rotations[l] = rot;
+            info->sigma_discarded[l] = sqrt(std::max(R.sel[l][1], 0.0));
+            info->sigma_total[l] = sqrt(std::max(R.sel[l][2], 0.0));
+            info->sweeps[l] = R.sweeps[l];
+            info->rotations[l] = rotations[l];
+            info->pivots[l] = R.m[l].k;
             // Thm A.1(d) with the resolution of the Gram route: after the eigen-solver every
             // off-diagonal entry is below the floor, so each eigenvalue is known to C * floor
-            ssum += sqrt(std::max(sel[l][1], 0.0) + (double)Cs[l] * jobs[l].abs_floor);
+            ssum += sqrt(std::max(R.sel[l][1], 0.0) + (double)Cs[l] * R.floor_noise);
         }
         info->T = T;
         info->xi_norm = sqrt(xin_norm2);
         info->bound_abs = info->xi_norm * ssum;
     }
-    CU(cudaGetLastError());
+    CUS(cudaGetLastError());
     ctx->reduced = true;
     return LS_OK;
+}
+
+// make `to` wait for the work enqueued so far on `from`
+cudaError_t join(cudaStream_t to, cudaStream_t from) {
+    if (to == from) return cudaSuccess;
+    cudaEvent_t e;
+    cudaError_t rc = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (rc != cudaSuccess) return rc;
+    rc = cudaEventRecord(e, from);
+    if (rc == cudaSuccess) rc = cudaStreamWaitEvent(to, e, 0);
+    cudaEventDestroy(e);
+    return rc;
+}
+
+// The reduction of n contexts: per-context phases on each context's stream,
+// the pivoted Cholesky and the Jacobi iteration of all 3n modes as one
+// cooperative launch each on the first context's stream.
+int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, ls_tucker_info* infos) {
+    std::vector<RedState> R(n);
+    std::vector<PcholJob> pj(3 * (size_t)n);
+    std::vector<JacobiJob> jj(3 * (size_t)n);
+    ls_ctx* c0 = ctxs[0];
+    cudaStream_t s0 = c0->st;
+    for (int i = 0; i < n; ++i) {
+        R[i].ctx = ctxs[i];
+        R[i].eps = eps;
+        R[i].forced = forced;
+        int rc = red_prepare(R[i], &pj[3 * i]);
+        if (rc != LS_OK) return rc;
+        if (join(s0, ctxs[i]->st) != cudaSuccess) return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: stream join failed");
+    }
+    {
+        Scope sc("pchol", s0);
+        cudaError_t e = launch_pchol_multi(pj.data(), 3 * n, c0->num_sms, s0);
+        if (e != cudaSuccess) return fail(c0, LS_ERR_CUDA, "rhosvd_reduce: pivoted Cholesky launch: %s", cudaGetErrorString(e));
+    }
+    for (int i = 0; i < n; ++i) {
+        if (join(ctxs[i]->st, s0) != cudaSuccess) return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: stream join failed");
+        cudaStream_t st = ctxs[i]->st;
+        if (cudaMemcpyAsync(R[i].hs, R[i].d_st, 3 * sizeof(DevStatus), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: status read failed");
+        count_d2h(3 * sizeof(DevStatus));
+    }
+    for (int i = 0; i < n; ++i)
+        if (cudaStreamSynchronize(ctxs[i]->st) != cudaSuccess) return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: sync failed");
+    for (int i = 0; i < n; ++i) {
+        int rc = red_after_pchol(R[i], &jj[3 * i]);
+        if (rc != LS_OK) return rc;
+        if (join(s0, ctxs[i]->st) != cudaSuccess) return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: stream join failed");
+    }
+    {
+        Scope sc("jacobi", s0);
+        cudaError_t e = launch_jacobi_multi(jj.data(), 3 * n, 60, 1e-14, c0->num_sms, s0);
+        if (e != cudaSuccess) return fail(c0, LS_ERR_CUDA, "rhosvd_reduce: Jacobi launch: %s", cudaGetErrorString(e));
+    }
+    for (int i = 0; i < n; ++i) {
+        if (join(ctxs[i]->st, s0) != cudaSuccess) return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: stream join failed");
+        int rc = red_select(R[i]);
+        if (rc != LS_OK) return rc;
+    }
+    for (int i = 0; i < n; ++i)
+        if (cudaStreamSynchronize(ctxs[i]->st) != cudaSuccess) return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: sync failed");
+    int first_err = LS_OK;
+    for (int i = 0; i < n; ++i) {
+        int rc = red_finish(R[i], infos ? &infos[i] : nullptr);
+        if (rc != LS_OK && first_err == LS_OK) first_err = rc;
+    }
+    return first_err;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ranks, ls_tucker_info* info) {
+    if (!ctx) return fail(nullptr, LS_ERR_ARG, "rhosvd_reduce: NULL context");
+    if (ctx->reduced) return fail(ctx, LS_ERR_STATE, "rhosvd_reduce: already reduced");
+    if (!forced_ranks && !(eps > 0.0)) return fail(ctx, LS_ERR_ARG, "rhosvd_reduce: eps must be > 0");
+    ls_ctx* one[1] = {ctx};
+    return reduce_many(one, 1, eps, forced_ranks, info);
+}
+
+int lattice_sum_batch_reduce(ls_ctx* const* ctxs, int32_t n, double eps, ls_tucker_info* infos) {
+    if (!ctxs || n < 1) return fail(nullptr, LS_ERR_ARG, "batch_reduce: no contexts");
+    if (!(eps > 0.0)) return fail(nullptr, LS_ERR_ARG, "batch_reduce: eps must be > 0");
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return fail(nullptr, LS_ERR_ARG, "batch_reduce: NULL context %d", i);
+        if (ctxs[i]->reduced) return fail(ctxs[i], LS_ERR_STATE, "batch_reduce: context %d already reduced", i);
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return fail(nullptr, LS_ERR_ARG, "batch_reduce: context %d listed twice", i);
+    }
+    int rc = reduce_many(ctxs, n, eps, nullptr, infos);
+    if (rc != LS_OK) {
+        for (int i = 0; i < n; ++i)
+            if (!ctxs[i]->err.empty()) {
+                g_create_error = ctxs[i]->err;
+                break;
+            }
+    }
+    return rc;
 }
 
 int lattice_sum_eval_slab(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev, int32_t out_dtype) {

@@ -80,13 +80,34 @@ cudaError_t launch_jacobi_multi(const JacobiJob* jobs, int njobs, int max_sweeps
 // (forced if forced > 0, then clipped to the eigenvalues above `resolution`)
 // and write out[0] = r, out[1] = discarded^2, out[2] = total (as doubles);
 // also inv_sqrt_lam[k] = 1/sqrt(lam[k]) and lam[k] <- sqrt(max(lam[k], 0)).
-cudaError_t launch_sort_select(const double* G, int64_t C, double eps, int forced, double resolution, int32_t* perm,
-                               double* lam, double* inv_sqrt_lam, double* out, cudaStream_t st);
+// *extra (device, may be NULL) is energy outside the problem that belongs to
+// the discarded tail (and to the total).
+cudaError_t launch_sort_select(const double* G, int64_t C, double eps, int forced, double resolution,
+                               const double* extra, int32_t* perm, double* lam, double* inv_sqrt_lam, double* out,
+                               cudaStream_t st);
 
-// Y[k][i] = inv_sqrt_lam[k] * sum_c V[c][perm[k]] w[c] a[c][i]  (k < r).
-cudaError_t launch_basis(const double* V, int64_t C, const int32_t* perm, const double* inv_sqrt_lam,
-                         const double* w, const double* a, int64_t N, int r, double* Y,
-                         cudaStream_t st);
+// Pivoted Cholesky G P = L L^T (greedy diagonal pivoting) of up to three
+// C x C PSD matrices in one cooperative launch, stopped when the trace of
+// the remaining Schur complement is <= delta or after kmax columns. Each
+// job: L (C x kmax, row-major, column t = t-th pivot step), d (C scratch),
+// cand (kPcholCand doubles of scratch; its last element receives the final
+// residual trace), piv (kmax), st (zeroed; st->sweeps receives the number k
+// of columns).
+constexpr int kPcholCand = 6 * 1024 + 8;
+struct PcholJob {
+    const double* G; double* L; double* d; double* cand; int* piv; DevStatus* st; int64_t C; int kmax; double delta;
+};
+cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cudaStream_t st);
+// H = L^T L (k x k) from the first k columns of L.
+cudaError_t launch_pchol_gram(const double* L, int64_t C, int64_t kmax, int k, double* H, cudaStream_t st);
+// Vg = L U diag(1/sqrt(H_nn)) (C x k): unit eigenvectors of L L^T from the
+// eigenvectors U (k x k, columns) of H after the Jacobi iteration.
+cudaError_t launch_pchol_vectors(const double* L, int64_t C, int64_t kmax, int k, const double* U, const double* H,
+                                 double* Vg, cudaStream_t st);
+
+// Y[k][i] = inv_sqrt_lam[k] * sum_c V[c*ldv + perm[k]] w[c] a[c][i]  (k < r).
+cudaError_t launch_basis(const double* V, int64_t C, int64_t ldv, const int32_t* perm, const double* inv_sqrt_lam,
+                         const double* w, const double* a, int64_t N, int r, double* Y, cudaStream_t st);
 
 // Y <- orthonormalised rows of Y (r x N) by CholeskyQR2 (FP64): twice
 // G = Y Y^T, G = L L^T, Y <- L^{-1} Y. Ytmp holds r*N doubles, work >= 2 r^2.

@@ -10,6 +10,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "ls_common.cuh"
 
@@ -227,11 +228,19 @@ struct StoreRowW {       // C[m*ld + n] = w[m] w[n] v
     __device__ void operator()(int, int m, int n, double v) const { p[m * ld + n] = w[m] * w[n] * v; }
 };
 
-// basis: A(m=k, kk=c) = V[c*C + perm[k]] * w[c] * inv_sqrt_lam[k]
+// basis: A(m=j, kk=c) = V[c*ldv + perm[j]] * w[c] * inv_sqrt_lam[j]
 struct BasisA {
     static constexpr bool kfast = false;
-    const double* V; int64_t C; const int32_t* perm; const double* w; const double* isl;
-    __device__ double operator()(int, int m, int k) const { return V[k * C + perm[m]] * w[k] * isl[m]; }
+    const double* V; int64_t ldv; const int32_t* perm; const double* w; const double* isl;
+    __device__ double operator()(int, int m, int k) const { return V[k * ldv + perm[m]] * w[k] * isl[m]; }
+};
+// eigenvectors of G from those of H = L^T L: column n scaled by 1/sqrt(H_nn)
+struct StoreColScaled {
+    double* p; int64_t ld; const double* H; int64_t ldh;
+    __device__ void operator()(int, int m, int n, double v) const {
+        const double h = H[(int64_t)n * ldh + n];
+        p[m * ld + n] = h > 0.0 ? v / sqrt(h) : 0.0;
+    }
 };
 // core: A(m=i, k=t) = P0[i*C0 + c0(t)] * xin[t]
 struct CoreA {
@@ -319,17 +328,27 @@ struct JacobiMode {
     double* G; double* V; double* snap; DevStatus* st; int C; int cta0; int ncta; double abs_floor; double tau;
 };
 struct JacobiArgs {
-    JacobiMode m[3]; int nmodes; int max_sweeps; double tol;
+    const JacobiMode* m; int nmodes; int max_sweeps; double tol;
 };
+
+// the job whose CTA range [cta0, cta0 + ncta) holds blockIdx.x (jobs sorted by cta0)
+template <class Job>
+__device__ __forceinline__ int find_job(const Job* m, int n) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int)blockIdx.x >= m[mid].cta0) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 __device__ __forceinline__ double& gsym(double* G, int C, int a, int b) {
     return a <= b ? G[(int64_t)a * C + b] : G[(int64_t)b * C + a];
 }
 
 __global__ void __launch_bounds__(256) k_jacobi_multi(JacobiArgs A) {
-    int mi = 0;
-    while (mi + 1 < A.nmodes && (int)blockIdx.x >= A.m[mi + 1].cta0) ++mi;
-    const JacobiMode J = A.m[mi];
+    const JacobiMode J = A.m[find_job(A.m, A.nmodes)];
     const int lb = blockIdx.x - J.cta0, nb = J.ncta;
     const int C = J.C, Cp = C + (C & 1), P = Cp / 2, n1 = Cp - 1;
     // shared: c[P], s[P] (double), p[P], q[P], next partner[Cp], next pair index[Cp] (int)
@@ -475,10 +494,123 @@ __global__ void __launch_bounds__(256) k_jacobi_multi(JacobiArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// pivoted Cholesky of up to three PSD matrices at once (cooperative grid,
+// CTAs split between the jobs): G P = L L^T with greedy diagonal pivoting,
+// stopped when the trace of the Schur complement drops below delta. One group
+// barrier per step: every CTA reduces the per-CTA (max, argmax, sum)
+// candidates of the residual diagonal, stages row p of L in shared memory,
+// computes its rows of the new column (one warp per row) and publishes the
+// candidates of the updated diagonal (double-buffered by step parity).
+// ---------------------------------------------------------------------------
+struct PcholMode {
+    const double* G; double* L; double* d; double* cand; int* piv; DevStatus* st; int C; int kmax; int cta0;
+    int ncta; double delta;
+};
+struct PcholArgs {
+    const PcholMode* m; int nmodes;
+};
+
+__global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
+    const PcholMode J = A.m[find_job(A.m, A.nmodes)];
+    const int lb = blockIdx.x - J.cta0, nb = J.ncta;
+    const int C = J.C;
+    extern __shared__ double lrow[];            // row p of L, kmax entries
+    __shared__ double s_red[2][8];
+    __shared__ int s_redi[8];
+    __shared__ int s_p;
+    __shared__ double s_dmax, s_sum;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // rows of this CTA: [r0, r1)
+    const int per = (C + nb - 1) / nb;
+    const int r0 = min(C, lb * per), r1 = min(C, r0 + per);
+    // initial residual diagonal and candidates (parity 0)
+    auto publish = [&](int parity) {
+        double mx = -1.0, sm = 0.0;
+        int ix = -1;
+        for (int j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
+            const double v = __ldcg(J.d + j);
+            sm += v;
+            if (v > mx) { mx = v; ix = j; }
+        }
+        for (int o = 16; o; o >>= 1) {
+            const double m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, ix, o);
+            if (m2 > mx || (m2 == mx && i2 >= 0 && (ix < 0 || i2 < ix))) { mx = m2; ix = i2; }
+            sm += __shfl_xor_sync(0xffffffffu, sm, o);
+        }
+        if (lane == 0) { s_red[0][warp] = mx; s_redi[warp] = ix; s_red[1][warp] = sm; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double bm = -1.0, bs = 0.0;
+            int bi = -1;
+            for (int w = 0; w < nw; ++w) {
+                const double m2 = s_red[0][w];
+                const int i2 = s_redi[w];
+                if (m2 > bm || (m2 == bm && i2 >= 0 && (bi < 0 || i2 < bi))) { bm = m2; bi = i2; }
+                bs += s_red[1][w];
+            }
+            double* c = J.cand + ((int64_t)parity * nb + lb) * 3;
+            __stcg(c, bm);
+            __stcg(c + 1, (double)bi);
+            __stcg(c + 2, bs);
+        }
+    };
+    for (int j = r0 + threadIdx.x; j < r1; j += blockDim.x) __stcg(J.d + j, __ldcg(J.G + (int64_t)j * C + j));
+    __syncthreads();
+    publish(0);
+    if (!group_barrier(J.st, nb)) return;
+    int k = 0;
+    for (;; ++k) {
+        const int par = k & 1;
+        if (threadIdx.x == 0) {
+            double bm = -1.0, bs = 0.0;
+            int bi = -1;
+            for (int c = 0; c < nb; ++c) {
+                const double* cc = J.cand + ((int64_t)par * nb + c) * 3;
+                const double m2 = __ldcg(cc);
+                const int i2 = (int)__ldcg(cc + 1);
+                if (m2 > bm || (m2 == bm && i2 >= 0 && (bi < 0 || i2 < bi))) { bm = m2; bi = i2; }
+                bs += __ldcg(cc + 2);
+            }
+            s_p = bi;
+            s_dmax = bm;
+            s_sum = bs;
+        }
+        __syncthreads();
+        const int p = s_p;
+        const double dmax = s_dmax;
+        // stop when the residual trace is small enough, or at kmax columns
+        if (k >= J.kmax || !(s_sum > J.delta) || p < 0 || !(dmax > 0.0)) break;
+        for (int t = threadIdx.x; t < k; t += blockDim.x) lrow[t] = __ldcg(J.L + (int64_t)p * J.kmax + t);
+        __syncthreads();
+        const double inv = 1.0 / sqrt(dmax);
+        for (int j = r0 + warp; j < r1; j += nw) {
+            double acc = 0.0;
+            for (int t = lane; t < k; t += 32) acc = fma(__ldcg(J.L + (int64_t)j * J.kmax + t), lrow[t], acc);
+            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) {
+                const double l = (__ldcg(J.G + (int64_t)j * C + p) - acc) * inv;
+                __stcg(J.L + (int64_t)j * J.kmax + k, l);
+                const double dn = (j == p) ? 0.0 : fmax(__ldcg(J.d + j) - l * l, 0.0);
+                __stcg(J.d + j, dn);
+            }
+        }
+        if (lb == 0 && threadIdx.x == 0) J.piv[k] = p;
+        __syncthreads();
+        publish(par ^ 1);
+        if (!group_barrier(J.st, nb)) return;
+    }
+    if (lb == 0 && threadIdx.x == 0) {
+        J.st->sweeps = k;                          // columns of L
+        J.cand[kPcholCand - 1] = s_sum;            // residual trace: energy outside span(L)
+    }
+}
+
+// ---------------------------------------------------------------------------
 // eigenvalue sort + eps-rank selection (single CTA)
 // ---------------------------------------------------------------------------
-__global__ void k_sort_select(const double* G, int C, double eps, int forced, double resolution, int32_t* perm,
-                              double* lam, double* isl, double* out) {
+__global__ void k_sort_select(const double* G, int C, double eps, int forced, double resolution, const double* extra,
+                              int32_t* perm, double* lam, double* isl, double* out) {
     for (int k = threadIdx.x; k < C; k += blockDim.x) {
         const double lk = G[(int64_t)k * C + k];
         int rank = 0;
@@ -491,10 +623,12 @@ __global__ void k_sort_select(const double* G, int C, double eps, int forced, do
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double total = 0.0;
+        // energy outside the compressed problem belongs to the discarded tail
+        const double ex = extra ? fmax(*extra, 0.0) : 0.0;
+        double total = ex;
         for (int k = C - 1; k >= 0; --k) total += fmax(lam[k], 0.0);
         int r = C;
-        double tail = 0.0, tail_at_r = 0.0;
+        double tail = ex, tail_at_r = ex;
         if (forced > 0) {
             // a forced rank is clipped to the eigenvalues the FP64 Gram matrix resolves
             int nres = 0;
@@ -505,7 +639,7 @@ __global__ void k_sort_select(const double* G, int C, double eps, int forced, do
         } else {
             // suffix sums from the smallest eigenvalue; smallest r >= 1 whose tail qualifies
             const double lim = eps * eps * total;
-            tail_at_r = 0.0;
+            tail_at_r = ex;
             r = C;
             for (int k = C - 1; k >= 1; --k) {
                 tail += fmax(lam[k], 0.0);       // tail = sum_{j >= k}
@@ -752,22 +886,34 @@ cudaError_t launch_identity(double* V, int64_t C, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Split `cap` co-resident CTAs between jobs in proportion to `want`, at least
+// one each; jobs beyond `cap` go to later launches. Returns the CTA counts.
+static std::vector<int> split_ctas(const std::vector<int64_t>& want, int64_t cap) {
+    const int n = (int)want.size();
+    int64_t total = 0;
+    for (int64_t w : want) total += w;
+    std::vector<int> out(n, 1);
+    if (total <= cap) {
+        for (int i = 0; i < n; ++i) out[i] = (int)std::max<int64_t>(1, want[i]);
+        return out;
+    }
+    const int64_t spare = std::max<int64_t>(0, cap - n);
+    const int64_t extra_total = std::max<int64_t>(1, total - n);
+    for (int i = 0; i < n; ++i) out[i] = 1 + (int)((std::max<int64_t>(1, want[i]) - 1) * spare / extra_total);
+    return out;
+}
+
 cudaError_t launch_jacobi_multi(const JacobiJob* jobs, int njobs, int max_sweeps, double tol, int num_sms,
                                 cudaStream_t st) {
-    if (njobs < 1 || njobs > 3) return cudaErrorInvalidValue;
-    JacobiArgs a{};
-    a.nmodes = njobs;
-    a.max_sweeps = max_sweeps > 64 ? 64 : max_sweeps;
-    a.tol = tol;
+    if (njobs < 1) return cudaSuccess;
     size_t smem = 0;
-    int64_t want[3], total = 0;
+    std::vector<int64_t> want(njobs);
     for (int m = 0; m < njobs; ++m) {
         const int64_t C = jobs[m].C;
         const int64_t P = (C + (C & 1)) / 2;
         smem = std::max(smem, (size_t)(2 * sizeof(double) * P + sizeof(int) * (2 * P + 2 * (C + (C & 1)))));
         const int64_t items = P * P + C * P;
         want[m] = items <= 2048 ? 1 : (items + 1023) / 1024;
-        total += want[m];
     }
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_jacobi_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -776,31 +922,104 @@ cudaError_t launch_jacobi_multi(const JacobiJob* jobs, int njobs, int max_sweeps
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_multi, 256, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
-    const int64_t cap = std::min<int64_t>((int64_t)per_sm * num_sms, 2 * (int64_t)num_sms);
-    int cta = 0;
-    for (int m = 0; m < njobs; ++m) {
-        int64_t n = want[m];
-        if (total > cap) n = std::max<int64_t>(1, want[m] * cap / total);
-        a.m[m] = JacobiMode{jobs[m].G, jobs[m].V, jobs[m].snap, jobs[m].st, (int)jobs[m].C, cta, (int)n,
-                            jobs[m].abs_floor, jobs[m].tau};
-        cta += (int)n;
+    const int64_t resident = (int64_t)per_sm * num_sms;
+    // a few large jobs: about two CTAs per SM in total (cheaper group barriers); many jobs:
+    // every co-resident CTA
+    const int64_t cap = njobs <= 3 ? std::min<int64_t>(resident, 2 * (int64_t)num_sms) : resident;
+    // waves of at most `resident` jobs (one CTA each at least)
+    for (int j0 = 0; j0 < njobs; j0 += (int)resident) {
+        const int nj = (int)std::min<int64_t>(resident, njobs - j0);
+        std::vector<int64_t> w(want.begin() + j0, want.begin() + j0 + nj);
+        std::vector<int> nc = split_ctas(w, std::min(cap, resident));
+        std::vector<JacobiMode> hm(nj);
+        int cta = 0;
+        for (int m = 0; m < nj; ++m) {
+            const JacobiJob& J = jobs[j0 + m];
+            hm[m] = JacobiMode{J.G, J.V, J.snap, J.st, (int)J.C, cta, nc[m], J.abs_floor, J.tau};
+            cta += nc[m];
+        }
+        JacobiMode* dm = nullptr;
+        cudaError_t e = cudaMallocAsync(&dm, sizeof(JacobiMode) * nj, st);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(dm, hm.data(), sizeof(JacobiMode) * nj, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            JacobiArgs a{dm, nj, max_sweeps > 64 ? 64 : max_sweeps, tol};
+            void* args[] = {&a};
+            count_kernels(1);
+            e = cudaLaunchCooperativeKernel((void*)k_jacobi_multi, dim3(cta), dim3(256), args, smem, st);
+        }
+        cudaFreeAsync(dm, st);
+        if (e != cudaSuccess) return e;
     }
-    void* args[] = {&a};
-    count_kernels(1);
-    return cudaLaunchCooperativeKernel((void*)k_jacobi_multi, dim3(cta), dim3(256), args, smem, st);
+    return cudaSuccess;
 }
 
-cudaError_t launch_sort_select(const double* G, int64_t C, double eps, int forced, double resolution, int32_t* perm,
-                               double* lam, double* inv_sqrt_lam, double* out, cudaStream_t st) {
-    k_sort_select<<<1, 1024, 0, st>>>(G, (int)C, eps, forced, resolution, perm, lam, inv_sqrt_lam, out);
+cudaError_t launch_sort_select(const double* G, int64_t C, double eps, int forced, double resolution,
+                               const double* extra, int32_t* perm, double* lam, double* inv_sqrt_lam, double* out,
+                               cudaStream_t st) {
+    k_sort_select<<<1, 1024, 0, st>>>(G, (int)C, eps, forced, resolution, extra, perm, lam, inv_sqrt_lam, out);
     count_kernels(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_basis(const double* V, int64_t C, const int32_t* perm, const double* inv_sqrt_lam,
+cudaError_t launch_basis(const double* V, int64_t C, int64_t ldv, const int32_t* perm, const double* inv_sqrt_lam,
                          const double* w, const double* a, int64_t N, int r, double* Y, cudaStream_t st) {
-    return gemm_f64(r, (int)N, (int)C, 1, BasisA{V, C, perm, w, inv_sqrt_lam}, KRowN{a, N},
+    return gemm_f64(r, (int)N, (int)C, 1, BasisA{V, ldv, perm, w, inv_sqrt_lam}, KRowN{a, N},
                     StoreRow{Y, N, 0}, st);
+}
+
+cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cudaStream_t st) {
+    if (njobs < 1) return cudaSuccess;
+    size_t smem = 0;
+    std::vector<int64_t> want(njobs);
+    for (int m = 0; m < njobs; ++m) {
+        smem = std::max(smem, (size_t)jobs[m].kmax * sizeof(double));
+        want[m] = std::max<int64_t>(1, (jobs[m].C + 63) / 64);   // a warp per row and step, ~64 rows a CTA
+    }
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_pchol_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pchol_multi, 256, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int64_t resident = (int64_t)per_sm * num_sms;
+    const int64_t cap = std::min<int64_t>(resident, std::max<int64_t>(num_sms, njobs));
+    for (int j0 = 0; j0 < njobs; j0 += (int)resident) {
+        const int nj = (int)std::min<int64_t>(resident, njobs - j0);
+        std::vector<int64_t> w(want.begin() + j0, want.begin() + j0 + nj);
+        std::vector<int> nc = split_ctas(w, cap);
+        std::vector<PcholMode> hm(nj);
+        int cta = 0;
+        for (int m = 0; m < nj; ++m) {
+            const PcholJob& J = jobs[j0 + m];
+            hm[m] = PcholMode{J.G, J.L, J.d, J.cand, J.piv, J.st, (int)J.C, J.kmax, cta, nc[m], J.delta};
+            cta += nc[m];
+        }
+        PcholMode* dm = nullptr;
+        cudaError_t e = cudaMallocAsync(&dm, sizeof(PcholMode) * nj, st);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(dm, hm.data(), sizeof(PcholMode) * nj, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            PcholArgs a{dm, nj};
+            void* args[] = {&a};
+            count_kernels(1);
+            e = cudaLaunchCooperativeKernel((void*)k_pchol_multi, dim3(cta), dim3(256), args, smem, st);
+        }
+        cudaFreeAsync(dm, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_pchol_gram(const double* L, int64_t C, int64_t kmax, int k, double* H, cudaStream_t st) {
+    return gemm_f64(k, k, (int)C, 1, ColK{L, kmax}, KRowN{L, kmax}, StoreRow{H, k, 0}, st);
+}
+
+cudaError_t launch_pchol_vectors(const double* L, int64_t C, int64_t kmax, int k, const double* U, const double* H,
+                                 double* Vg, cudaStream_t st) {
+    // Vg[c][n] = sum_t L[c][t] U[t][n] / sqrt(H_nn): unit eigenvectors of L L^T
+    return gemm_f64((int)C, k, k, 1, RowK{L, kmax}, KRowN{U, k}, StoreColScaled{Vg, k, H, k}, st);
 }
 
 cudaError_t launch_cholqr2(double* Y, double* Ytmp, int r, int64_t N, double* work, DevStatus* status, int num_sms,

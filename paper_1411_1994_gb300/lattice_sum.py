@@ -26,7 +26,7 @@ LS_OUT_F64, LS_OUT_F32 = 0, 1
 EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_create", "lattice_sum_add_defects",
             "lattice_sum_rhosvd_reduce", "lattice_sum_eval_slab", "lattice_sum_get_factors",
             "lattice_sum_read", "lattice_sum_profile", "lattice_sum_profile_report",
-            "lattice_sum_eval_slab_noalloc",
+            "lattice_sum_eval_slab_noalloc", "lattice_sum_batch_reduce",
             "lattice_sum_destroy", "lattice_sum_last_error")
 
 
@@ -50,13 +50,13 @@ class ls_tucker_info(C.Structure):
     _fields_ = [("r", C.c_int32 * 3), ("C", C.c_int32 * 3), ("T", C.c_int64),
                 ("sigma_discarded", C.c_double * 3), ("sigma_total", C.c_double * 3),
                 ("xi_norm", C.c_double), ("bound_abs", C.c_double), ("sweeps", C.c_int32 * 3),
-                ("rotations", C.c_int64 * 3)]
+                ("rotations", C.c_int64 * 3), ("pivots", C.c_int32 * 3)]
 
     def as_dict(self):
         return {"r": list(self.r), "C": list(self.C), "T": int(self.T),
                 "sigma_discarded": list(self.sigma_discarded), "sigma_total": list(self.sigma_total),
                 "xi_norm": self.xi_norm, "bound_abs": self.bound_abs, "sweeps": list(self.sweeps),
-                "rotations": list(self.rotations)}
+                "rotations": list(self.rotations), "pivots": list(self.pivots)}
 
 
 class LatticeSumError(RuntimeError):
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lattice_sum_eval_slab_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                                   P(C.c_int32), C.c_int64, P(C.c_int64), C.c_int32,
                                                   C.c_void_p, C.c_int32, C.c_void_p]
+    lib.lattice_sum_batch_reduce.argtypes = [P(C.c_void_p), C.c_int32, C.c_double, P(ls_tucker_info)]
     lib.lattice_sum_destroy.argtypes = [C.c_void_p]
     lib.lattice_sum_destroy.restype = None
     lib.lattice_sum_last_error.argtypes = [C.c_void_p]
@@ -134,6 +135,22 @@ def eval_slab_noalloc(Z, core, ranks, N, z_index, out_ptr, out_dtype=LS_OUT_F64,
                                                C.c_void_p(core), r, int(N), z, len(z_index),
                                                C.c_void_p(out_ptr), out_dtype,
                                                C.c_void_p(stream) if stream else None))
+
+
+def batch_reduce(contexts, eps: float):
+    """RHOSVD of several LatticeSum contexts in one call (the batched form);
+    returns their info dicts."""
+    n = len(contexts)
+    arr = (C.c_void_p * n)(*[c.ctx.value for c in contexts])
+    infos = (ls_tucker_info * n)()
+    rc = lib().lattice_sum_batch_reduce(arr, n, float(eps), infos)
+    if rc != LS_OK:
+        raise LatticeSumError(rc, lib().lattice_sum_last_error(None).decode(errors="replace"))
+    out = []
+    for c, inf in zip(contexts, infos):
+        c.info = inf.as_dict()
+        out.append(c.info)
+    return out
 
 
 def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float):

@@ -57,10 +57,10 @@ def rel(a, b):
 def test_mixed_contractions_match_fp64_path(wl):
     s = scale_for(wl)
     a, ia = run(wl, s, L.LS_FP64)
-    b, ib = run(wl, s, L.LS_MIXED, forced=ia["r"])
+    b, ib = run(wl, s, L.LS_MIXED)
     assert ib["r"] == ia["r"]
     for m in range(3):
-        # the FP64 orthogonalisation is the same code in both paths
+        # the FP64 orthogonalisation (eps rule, same pre-compression) is the same code in both paths
         assert np.array_equal(a.read(L.LS_READ_BASIS, m), b.read(L.LS_READ_BASIS, m))
         pa, pb = a.read(L.LS_READ_PROJ, m), b.read(L.LS_READ_PROJ, m)
         assert rel(pb, pa) < 1e-7, (m, rel(pb, pa))
@@ -104,7 +104,8 @@ def test_mixed_single_site_and_ragged_tiles():
     for wl in (W.small_case(L=(1, 1, 1), N=33, eps=1e-6), W.small_case(L=(7, 3, 2), N=70, frac_vac=0.1, eps=1e-5)):
         s = scale_for(wl)
         a, ia = run(wl, s, L.LS_FP64)
-        b, ib = run(wl, s, L.LS_MIXED, forced=ia["r"])
+        b, ib = run(wl, s, L.LS_MIXED)
+        assert ib["r"] == ia["r"]
         z = [0, wl.N // 2, wl.N - 1]
         sa = a.eval_slab_torch(z).cpu().numpy()
         sb = b.eval_slab_torch(z).cpu().numpy()
