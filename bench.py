@@ -180,23 +180,30 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 def step_flops(name, info, N):
-    """Algorithmic FP64 / tensor flops of one pipeline step (all three modes)."""
-    C, r, T = info["C"], info["r"], info["T"]
+    """Algorithmic FP64 / tensor flops of one pipeline step (all three modes): a
+    symmetric product (Gram matrix) counts its N C^2 distinct multiply-adds
+    once, a triangular one (L^{-1} Y) its N r^2 / 2."""
+    C, r, T, k = info["C"], info["r"], info["T"], info["pivots"]
     if name == "gram":
-        return sum(2.0 * N * c * c for c in C)
+        return sum(1.0 * N * c * (c + 1) for c in C)
+    if name == "pchol":
+        # k pivot steps of C dot products of length <= k, then H = L^T L (k x k, length C)
+        return sum(1.0 * C[a] * k[a] ** 2 + 1.0 * C[a] * k[a] * (k[a] + 1) for a in range(3))
     if name == "basis":
-        return sum(2.0 * N * C[a] * r[a] for a in range(3))
+        # Vg = L U (C x k x k), Y = Vg^T A_w (r x C x N)
+        return sum(2.0 * C[a] * k[a] ** 2 + 2.0 * N * C[a] * r[a] for a in range(3))
     if name == "cholqr2":
-        return sum(2 * (2.0 * N * r[a] ** 2 + 2.0 * r[a] ** 3 / 3.0 + 2.0 * N * r[a] ** 2) for a in range(3))
+        # two passes: G = Y Y^T, Cholesky, triangular inverse, L^{-1} Y
+        return sum(2 * (1.0 * N * r[a] * (r[a] + 1) + 2.0 * r[a] ** 3 / 3.0 + 1.0 * N * r[a] ** 2) for a in range(3))
     if name == "project":
         return sum(2.0 * N * r[a] * C[a] for a in range(3))
     if name == "core":
         # two exact steps: grouped step 1 (2 r1 r2 T) + dense step 2 (2 r0 r1 r2 C0)
         return 2.0 * r[1] * r[2] * T + 2.0 * r[0] * r[1] * r[2] * C[0]
     if name == "jacobi":
-        # each applied rotation updates two rows of the symmetric Gram matrix (upper triangle:
-        # ~2 C entries x 3 flop x 2) and two columns of V (2 C entries x 3 flop)
-        return sum(18.0 * C[a] * info["rotations"][a] for a in range(3))
+        # each applied rotation of the k x k matrix H = L^T L updates two rows and two columns
+        # of its upper triangle (~2 k entries x 3 flop x 2) and two columns of V (2 k x 3 flop)
+        return sum(18.0 * k[a] * info["rotations"][a] for a in range(3))
     return None
 
 

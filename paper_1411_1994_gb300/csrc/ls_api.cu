@@ -457,7 +457,7 @@ namespace {
 // Scratch of one mode of one context during the reduction.
 struct RedMode {
     double *G = nullptr, *L = nullptr, *pd = nullptr, *cand = nullptr, *H = nullptr, *V = nullptr, *snap = nullptr,
-           *isl = nullptr, *w = nullptr;
+           *isl = nullptr, *w = nullptr, *vg = nullptr, *ytmp = nullptr, *Gz = nullptr, *Li = nullptr;
     int32_t *piv = nullptr, *perm = nullptr;
     int k = 0;
 };
@@ -467,12 +467,14 @@ struct RedState {
     ls_ctx* ctx = nullptr;
     double eps = 0.0;
     const int32_t* forced = nullptr;
-    DevStatus* d_st = nullptr;   // one status block per mode + one for CholeskyQR2
+    DevStatus* d_st = nullptr;   // [0, 3): pivoted Cholesky, then Jacobi, per mode; [3, 6): CholeskyQR2 per mode
     double* d_sel = nullptr;
+    GemmWs gw{};
     RedMode m[3];
     int sweeps[3] = {0, 0, 0};
+    int64_t rotations[3] = {0, 0, 0};
     double sel[3][3] = {};
-    DevStatus hs[4] = {};
+    DevStatus hs[6] = {};
     double floor_noise = 0.0;
     int64_t T = 0;
 };
@@ -499,13 +501,23 @@ int red_prepare(RedState& R, PcholJob* pj) {
     count_h2d(3 * T * sizeof(int32_t));
     CUS(cudaMemcpyAsync(ctx->d_xi, ctx->xi.data(), T * sizeof(double), cudaMemcpyHostToDevice, st));
     count_h2d(T * sizeof(double));
-    CUS(dalloc(ctx, &R.d_st, 4));
-    CUS(cudaMemsetAsync(R.d_st, 0, 4 * sizeof(DevStatus), st));
+    CUS(dalloc(ctx, &R.d_st, 6));
+    CUS(cudaMemsetAsync(R.d_st, 0, 6 * sizeof(DevStatus), st));
     CUS(dalloc(ctx, &R.d_sel, 9));
+    R.gw.num_sms = ctx->num_sms;
+    R.gw.ws_cap = gemm_ws_doubles(ctx->num_sms);
+    R.gw.ctr_cap = gemm_ws_counters(ctx->num_sms);
+    CUS(dalloc(ctx, &R.gw.ws, R.gw.ws_cap));
+    CUS(dalloc(ctx, &R.gw.ctr, R.gw.ctr_cap));
+    CUS(cudaMemsetAsync(R.gw.ctr, 0, R.gw.ctr_cap * sizeof(unsigned int), st));
+    const double* a[3];
+    const double* w[3];
+    double* G[3];
+    int64_t Cs[3];
     for (int l = 0; l < 3; ++l) {
         ModeCols& mc = ctx->mode[l];
         RedMode& M = R.m[l];
-        const int64_t C = mc.C;
+        const int64_t C = Cs[l] = mc.C;
         CUS(dalloc(ctx, &ctx->d_norms[l], C));
         CUS(dalloc(ctx, &ctx->d_sigma[l], C));
         CUS(dalloc(ctx, &M.G, C * C));
@@ -515,17 +527,20 @@ int red_prepare(RedState& R, PcholJob* pj) {
         CUS(dalloc(ctx, &M.piv, C));
         CUS(dalloc(ctx, &M.w, C));
         CUS(cudaMemsetAsync(ctx->d_sigma[l], 0, C * sizeof(double), st));
-        std::vector<double> w(C);
-        for (int64_t c = 0; c < C; ++c) w[c] = sqrt((double)mc.count[c]);
-        CUS(cudaMemcpyAsync(M.w, w.data(), C * sizeof(double), cudaMemcpyHostToDevice, st));
+        std::vector<double> wh(C);
+        for (int64_t c = 0; c < C; ++c) wh[c] = sqrt((double)mc.count[c]);
+        CUS(cudaMemcpyAsync(M.w, wh.data(), C * sizeof(double), cudaMemcpyHostToDevice, st));
         count_h2d(C * sizeof(double));
         { Scope sc("norms", st); CUS(launch_norm_columns(mc.d_cols, C, N, ctx->d_norms[l], st)); }
-        { Scope sc("gram", st); CUS(launch_gram_weighted(mc.d_cols, C, N, M.w, M.G, st)); }
+        a[l] = mc.d_cols;
+        w[l] = M.w;
+        G[l] = M.G;
         // pivoted Cholesky: the energy left outside the pivot columns (<= delta) is discarded with
         // the tail; with the eps rule delta = 1e-4 eps^2 T, with forced ranks the Gram noise
         const double delta = R.forced ? (double)C * R.floor_noise : 1e-4 * R.eps * R.eps * (double)T;
         pj[l] = PcholJob{M.G, M.L, M.pd, M.cand, M.piv, R.d_st + l, C, (int)C, delta};
     }
+    { Scope sc("gram", st); CUS(launch_gram_weighted_n(3, a, Cs, N, w, G, R.gw, st)); }
     return LS_OK;
 }
 
@@ -536,22 +551,29 @@ int red_after_pchol(RedState& R, JacobiJob* jj) {
     for (int l = 0; l < 3; ++l)
         if (R.hs[l].flag == FLAG_TIMEOUT)
             return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: pivoted Cholesky barrier timed out (mode %d)", l);
-    CUS(cudaMemsetAsync(R.d_st, 0, 4 * sizeof(DevStatus), st));
+    CUS(cudaMemsetAsync(R.d_st, 0, 6 * sizeof(DevStatus), st));
+    const double* L[3];
+    double* H[3];
+    int64_t Cs[3];
+    int ks[3];
     for (int l = 0; l < 3; ++l) {
         RedMode& M = R.m[l];
-        const int k = M.k = std::max(1, R.hs[l].sweeps);
+        const int k = ks[l] = M.k = std::max(1, R.hs[l].sweeps);
         CUS(dalloc(ctx, &M.H, (int64_t)k * k));
         CUS(dalloc(ctx, &M.V, (int64_t)k * k));
         CUS(dalloc(ctx, &M.snap, 6 * (k / 2 + 1)));
         CUS(dalloc(ctx, &M.perm, k));
         CUS(dalloc(ctx, &M.isl, k));
-        { Scope sc("pchol", st); CUS(launch_pchol_gram(M.L, ctx->mode[l].C, ctx->mode[l].C, k, M.H, st)); }
         CUS(launch_identity(M.V, k, st));
+        L[l] = M.L;
+        H[l] = M.H;
+        Cs[l] = ctx->mode[l].C;
         // directions whose Rayleigh quotients both stay below tau = 1e-3 eps^2 T / k are discarded
         // together whatever their mixing; forced ranks resolve everything
         const double tau = R.forced ? 0.0 : 1e-3 * R.eps * R.eps * (double)R.T / (double)k;
         jj[l] = JacobiJob{M.H, M.V, M.snap, R.d_st + l, k, R.floor_noise, tau};
     }
+    { Scope sc("pchol", st); CUS(launch_pchol_gram_n(3, L, Cs, ks, Cs, H, R.gw, st)); }
     return LS_OK;
 }
 
@@ -573,12 +595,12 @@ int red_select(RedState& R) {
     return LS_OK;
 }
 
-// after the selection (host copies ready): basis, CholeskyQR2, projection, core, info
-int red_finish(RedState& R, ls_tucker_info* info) {
+// after the selection (host copies ready): eigenvectors of the Gram matrices,
+// the bases Y = A_w Vg Lambda^{-1/2}, and the first Gram matrix of CholeskyQR2
+int red_basis(RedState& R, CholJob* cj) {
     ls_ctx* ctx = R.ctx;
     cudaStream_t st = ctx->st;
     const int64_t N = ctx->p.N;
-    const int64_t T = R.T;
     for (int l = 0; l < 3; ++l) {
         if (R.hs[l].flag == FLAG_TIMEOUT)
             return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Jacobi grid barrier timed out (mode %d)", l);
@@ -586,41 +608,115 @@ int red_finish(RedState& R, ls_tucker_info* info) {
             return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: Jacobi did not converge (mode %d)", l);
         R.sweeps[l] = R.hs[l].sweeps;
         ctx->r[l] = (int32_t)R.sel[l][0];
-    }
-    int64_t rotations[3];
-    for (int l = 0; l < 3; ++l) {
         int64_t rot = 0;
         for (int k = 0; k < R.sweeps[l] && k < 64; ++k) rot += R.hs[l].sweep_active[k];
-        rotations[l] = rot;
+        R.rotations[l] = rot;
     }
+    const double *L[3], *U[3], *Hc[3], *vgc[3], *isl[3], *w[3], *a[3], *Yc[3];
+    const int32_t* perm[3];
+    double *vg[3], *Y[3], *Gz[3];
+    int64_t Cs[3], kl[3];
+    int ks[3], rs[3];
     for (int l = 0; l < 3; ++l) {
         ModeCols& mc = ctx->mode[l];
         RedMode& M = R.m[l];
         const int64_t C = mc.C;
         const int r = ctx->r[l];
-        double *work = nullptr, *ytmp = nullptr, *vg = nullptr;
         CUS(dalloc(ctx, &ctx->d_Z[l], (int64_t)r * N));
         CUS(dalloc(ctx, &ctx->d_P[l], (int64_t)r * C));
-        CUS(dalloc(ctx, &work, 2 * (int64_t)r * r));
-        CUS(dalloc(ctx, &ytmp, (int64_t)r * N));
-        CUS(dalloc(ctx, &vg, C * M.k));
-        {
-            Scope sc("basis", st);
-            CUS(launch_pchol_vectors(M.L, C, C, M.k, M.V, M.H, vg, st));
-            CUS(launch_basis(vg, C, M.k, M.perm, M.isl, M.w, mc.d_cols, N, r, ctx->d_Z[l], st));
+        CUS(dalloc(ctx, &M.Gz, (int64_t)r * r));
+        CUS(dalloc(ctx, &M.Li, (int64_t)r * r));
+        CUS(dalloc(ctx, &M.ytmp, (int64_t)r * N));
+        CUS(dalloc(ctx, &M.vg, C * M.k));
+        L[l] = M.L;
+        U[l] = M.V;
+        Hc[l] = M.H;
+        vg[l] = M.vg;
+        vgc[l] = M.vg;
+        isl[l] = M.isl;
+        w[l] = M.w;
+        a[l] = mc.d_cols;
+        perm[l] = M.perm;
+        Y[l] = ctx->d_Z[l];
+        Yc[l] = ctx->d_Z[l];
+        Gz[l] = M.Gz;
+        Cs[l] = C;
+        kl[l] = M.k;
+        ks[l] = M.k;
+        rs[l] = r;
+        cj[l] = CholJob{M.Gz, M.Li, R.d_st + 3 + l, r};
+    }
+    {
+        Scope sc("basis", st);
+        CUS(launch_pchol_vectors_n(3, L, Cs, ks, Cs, U, Hc, vg, R.gw, st));
+        CUS(launch_basis_n(3, vgc, Cs, kl, perm, isl, w, a, N, rs, Y, R.gw, st));
+    }
+    { Scope sc("cholqr2", st); CUS(launch_syrk_rows_n(3, Yc, rs, N, Gz, R.gw, st)); }
+    return LS_OK;
+}
+
+// CholeskyQR2 between the two factorisations: Y' = L^{-1} Y, then G = Y' Y'^T
+int red_cholqr_mid(RedState& R) {
+    ls_ctx* ctx = R.ctx;
+    cudaStream_t st = ctx->st;
+    const int64_t N = ctx->p.N;
+    const double *Li[3], *src[3], *yc[3];
+    double *dst[3], *Gz[3];
+    int rs[3];
+    for (int l = 0; l < 3; ++l) {
+        Li[l] = R.m[l].Li;
+        src[l] = ctx->d_Z[l];
+        dst[l] = R.m[l].ytmp;
+        yc[l] = R.m[l].ytmp;
+        Gz[l] = R.m[l].Gz;
+        rs[l] = ctx->r[l];
+    }
+    Scope sc("cholqr2", st);
+    CUS(launch_lower_apply_n(3, Li, rs, src, dst, N, R.gw, st));
+    CUS(launch_syrk_rows_n(3, yc, rs, N, Gz, R.gw, st));
+    return LS_OK;
+}
+
+// after the second factorisation: Z = L^{-1} Y', projections, core, info
+int red_finish(RedState& R, ls_tucker_info* info) {
+    ls_ctx* ctx = R.ctx;
+    cudaStream_t st = ctx->st;
+    const int64_t N = ctx->p.N;
+    const int64_t T = R.T;
+    {
+        const double *Li[3], *src[3];
+        double* dst[3];
+        int rs[3];
+        for (int l = 0; l < 3; ++l) {
+            Li[l] = R.m[l].Li;
+            src[l] = R.m[l].ytmp;
+            dst[l] = ctx->d_Z[l];
+            rs[l] = ctx->r[l];
         }
-        { Scope sc("cholqr2", st); CUS(launch_cholqr2(ctx->d_Z[l], ytmp, r, N, work, R.d_st + 3, ctx->num_sms, st)); }
-        if (ctx->p.precision == LS_MIXED) {
-            Scope sc("project", st);
-            int rc = tc_project(ctx->d_Z[l], r, mc.d_cols, C, N, ctx->d_P[l], st, &ctx->err);
+        Scope sc("cholqr2", st);
+        CUS(launch_lower_apply_n(3, Li, rs, src, dst, N, R.gw, st));
+    }
+    if (ctx->p.precision == LS_MIXED) {
+        Scope sc("project", st);
+        for (int l = 0; l < 3; ++l) {
+            int rc = tc_project(ctx->d_Z[l], ctx->r[l], ctx->mode[l].d_cols, ctx->mode[l].C, N, ctx->d_P[l], st,
+                                &ctx->err);
             if (rc != LS_OK) return rc;
-        } else {
-            Scope sc("project", st);
-            CUS(launch_project(ctx->d_Z[l], r, mc.d_cols, C, N, ctx->d_P[l], st));
         }
-        dfree(ctx, work);
-        dfree(ctx, ytmp);
-        dfree(ctx, vg);
+    } else {
+        const double *Z[3], *a[3];
+        double* P[3];
+        int rs[3];
+        int64_t Cs[3];
+        for (int l = 0; l < 3; ++l) {
+            Z[l] = ctx->d_Z[l];
+            a[l] = ctx->mode[l].d_cols;
+            P[l] = ctx->d_P[l];
+            rs[l] = ctx->r[l];
+            Cs[l] = ctx->mode[l].C;
+        }
+        Scope sc("project", st);
+        CUS(launch_project_n(3, Z, rs, a, Cs, N, P, R.gw, st));
     }
     { Scope sc("fold", st); CUS(launch_fold_norms(ctx->d_xi, ctx->d_tcol, T, ctx->d_norms[0], ctx->d_norms[1], ctx->d_norms[2], ctx->d_xin, st)); }
     // (c3) core: terms grouped by their mode-0 vector (counting sort on the host)
@@ -666,14 +762,17 @@ int red_finish(RedState& R, ls_tucker_info* info) {
     for (int l = 0; l < 3; ++l) {
         RedMode& M = R.m[l];
         for (void* q : {(void*)M.G, (void*)M.L, (void*)M.pd, (void*)M.cand, (void*)M.H, (void*)M.V, (void*)M.snap,
-                        (void*)M.isl, (void*)M.w, (void*)M.piv, (void*)M.perm})
+                        (void*)M.isl, (void*)M.w, (void*)M.piv, (void*)M.perm, (void*)M.vg, (void*)M.ytmp,
+                        (void*)M.Gz, (void*)M.Li})
             dfree(ctx, q);
     }
     dfree(ctx, d_perm_t);
     dfree(ctx, d_off);
     dfree(ctx, R.d_sel);
-    CUS(cudaMemcpyAsync(&R.hs[3], R.d_st + 3, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
-    count_d2h(sizeof(DevStatus));
+    dfree(ctx, R.gw.ws);
+    dfree(ctx, R.gw.ctr);
+    CUS(cudaMemcpyAsync(&R.hs[3], R.d_st + 3, 3 * sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    count_d2h(3 * sizeof(DevStatus));
     double xin_norm2 = 0.0;
     if (info) {
         std::vector<double> xin(T);
@@ -685,8 +784,11 @@ int red_finish(RedState& R, ls_tucker_info* info) {
         CUS(cudaStreamSynchronize(st));
     }
     dfree(ctx, R.d_st);
-    if (R.hs[3].flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Cholesky grid barrier timed out");
-    if (R.hs[3].flag == FLAG_NOT_SPD) return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: CholeskyQR2 met a non-positive pivot");
+    for (int l = 3; l < 6; ++l) {
+        if (R.hs[l].flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Cholesky grid barrier timed out");
+        if (R.hs[l].flag == FLAG_NOT_SPD)
+            return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: CholeskyQR2 met a non-positive pivot (mode %d)", l - 3);
+    }
     if (info) {
         memset(info, 0, sizeof *info);
         double ssum = 0.0;
@@ -696,7 +798,7 @@ int red_finish(RedState& R, ls_tucker_info* info) {
             info->sigma_discarded[l] = sqrt(std::max(R.sel[l][1], 0.0));
             info->sigma_total[l] = sqrt(std::max(R.sel[l][2], 0.0));
             info->sweeps[l] = R.sweeps[l];
-            info->rotations[l] = rotations[l];
+            info->rotations[l] = R.rotations[l];
             info->pivots[l] = R.m[l].k;
             // Thm A.1(d) with the resolution of the Gram route: after the eigen-solver every
             // off-diagonal entry is below the floor, so each eigenvalue is known to C * floor
@@ -723,22 +825,49 @@ cudaError_t join(cudaStream_t to, cudaStream_t from) {
     return rc;
 }
 
-// The reduction of n contexts: per-context phases on each context's stream,
-// the pivoted Cholesky and the Jacobi iteration of all 3n modes as one
-// cooperative launch each on the first context's stream.
+// The reduction of n contexts: per-context phases on each context's stream;
+// the cooperative steps (pivoted Cholesky, Jacobi iteration, the two Cholesky
+// factorisations of CholeskyQR2) of all 3n modes as one launch each on the
+// first context's stream, so that no two cooperative grids run at once.
 int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, ls_tucker_info* infos) {
     std::vector<RedState> R(n);
     std::vector<PcholJob> pj(3 * (size_t)n);
     std::vector<JacobiJob> jj(3 * (size_t)n);
+    std::vector<CholJob> cj(3 * (size_t)n);
     ls_ctx* c0 = ctxs[0];
     cudaStream_t s0 = c0->st;
+    auto gather = [&](ls_ctx* c) -> int {
+        if (join(s0, c->st) != cudaSuccess) return fail(c, LS_ERR_CUDA, "rhosvd_reduce: stream join failed");
+        return LS_OK;
+    };
+    auto scatter = [&](ls_ctx* c) -> int {
+        if (join(c->st, s0) != cudaSuccess) return fail(c, LS_ERR_CUDA, "rhosvd_reduce: stream join failed");
+        return LS_OK;
+    };
+    auto sync_all = [&]() -> int {
+        for (int i = 0; i < n; ++i)
+            if (cudaStreamSynchronize(ctxs[i]->st) != cudaSuccess)
+                return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: sync failed");
+        return LS_OK;
+    };
+    auto chol_all = [&]() -> int {
+        for (int i = 0; i < n; ++i)
+            if (int rc = gather(ctxs[i])) return rc;
+        {
+            Scope sc("cholqr2", s0);
+            cudaError_t e = launch_chol_inv_multi(cj.data(), 3 * n, c0->num_sms, s0);
+            if (e != cudaSuccess) return fail(c0, LS_ERR_CUDA, "rhosvd_reduce: Cholesky launch: %s", cudaGetErrorString(e));
+        }
+        for (int i = 0; i < n; ++i)
+            if (int rc = scatter(ctxs[i])) return rc;
+        return LS_OK;
+    };
     for (int i = 0; i < n; ++i) {
         R[i].ctx = ctxs[i];
         R[i].eps = eps;
         R[i].forced = forced;
-        int rc = red_prepare(R[i], &pj[3 * i]);
-        if (rc != LS_OK) return rc;
-        if (join(s0, ctxs[i]->st) != cudaSuccess) return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: stream join failed");
+        if (int rc = red_prepare(R[i], &pj[3 * i])) return rc;
+        if (int rc = gather(ctxs[i])) return rc;
     }
     {
         Scope sc("pchol", s0);
@@ -746,18 +875,15 @@ int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, l
         if (e != cudaSuccess) return fail(c0, LS_ERR_CUDA, "rhosvd_reduce: pivoted Cholesky launch: %s", cudaGetErrorString(e));
     }
     for (int i = 0; i < n; ++i) {
-        if (join(ctxs[i]->st, s0) != cudaSuccess) return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: stream join failed");
-        cudaStream_t st = ctxs[i]->st;
-        if (cudaMemcpyAsync(R[i].hs, R[i].d_st, 3 * sizeof(DevStatus), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        if (int rc = scatter(ctxs[i])) return rc;
+        if (cudaMemcpyAsync(R[i].hs, R[i].d_st, 3 * sizeof(DevStatus), cudaMemcpyDeviceToHost, ctxs[i]->st) != cudaSuccess)
             return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: status read failed");
         count_d2h(3 * sizeof(DevStatus));
     }
-    for (int i = 0; i < n; ++i)
-        if (cudaStreamSynchronize(ctxs[i]->st) != cudaSuccess) return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: sync failed");
+    if (int rc = sync_all()) return rc;
     for (int i = 0; i < n; ++i) {
-        int rc = red_after_pchol(R[i], &jj[3 * i]);
-        if (rc != LS_OK) return rc;
-        if (join(s0, ctxs[i]->st) != cudaSuccess) return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: stream join failed");
+        if (int rc = red_after_pchol(R[i], &jj[3 * i])) return rc;
+        if (int rc = gather(ctxs[i])) return rc;
     }
     {
         Scope sc("jacobi", s0);
@@ -765,12 +891,16 @@ int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, l
         if (e != cudaSuccess) return fail(c0, LS_ERR_CUDA, "rhosvd_reduce: Jacobi launch: %s", cudaGetErrorString(e));
     }
     for (int i = 0; i < n; ++i) {
-        if (join(ctxs[i]->st, s0) != cudaSuccess) return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: stream join failed");
-        int rc = red_select(R[i]);
-        if (rc != LS_OK) return rc;
+        if (int rc = scatter(ctxs[i])) return rc;
+        if (int rc = red_select(R[i])) return rc;
     }
+    if (int rc = sync_all()) return rc;
     for (int i = 0; i < n; ++i)
-        if (cudaStreamSynchronize(ctxs[i]->st) != cudaSuccess) return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: sync failed");
+        if (int rc = red_basis(R[i], &cj[3 * i])) return rc;
+    if (int rc = chol_all()) return rc;
+    for (int i = 0; i < n; ++i)
+        if (int rc = red_cholqr_mid(R[i])) return rc;
+    if (int rc = chol_all()) return rc;
     int first_err = LS_OK;
     for (int i = 0; i < n; ++i) {
         int rc = red_finish(R[i], infos ? &infos[i] : nullptr);

@@ -56,9 +56,53 @@ cudaError_t launch_assemble(const double* g, int64_t N, const int32_t* colq, con
 // norms[c] = ||a_c||; a_c /= norms[c] in place (rows of a, stride N).
 cudaError_t launch_norm_columns(double* a, int64_t C, int64_t N, double* norms, cudaStream_t st);
 
-// G[c][c'] = w[c] w[c'] <a_c, a_c'> (a: C rows of length N), FP64.
-cudaError_t launch_gram_weighted(const double* a, int64_t C, int64_t N, const double* w, double* G,
-                                 cudaStream_t st);
+// Workspace of the grouped FP64 GEMMs: split-K partials (ws_cap doubles) and
+// one counter per output tile (ctr_cap counters, zero at allocation; every
+// launch leaves them zero). A split-K product needs both; with ws == NULL
+// the products run unsplit.
+struct GemmWs {
+    double* ws; int64_t ws_cap; unsigned int* ctr; int64_t ctr_cap; int num_sms;
+};
+// workspace sizes that allow every split the launcher chooses on num_sms SMs
+inline int64_t gemm_ws_doubles(int num_sms) { return 2 * (int64_t)num_sms * 64 * 64; }
+inline int64_t gemm_ws_counters(int num_sms) { return 2 * (int64_t)num_sms; }
+
+// The FP64 products of the reduction, each for n <= 3 modes in one launch
+// (arrays of length n, one entry per mode):
+// G[c][c'] = w[c] w[c'] <a_c, a_c'>  (a: C rows of length N).
+cudaError_t launch_gram_weighted_n(int n, const double* const a[], const int64_t C[], int64_t N,
+                                   const double* const w[], double* const G[], const GemmWs& W, cudaStream_t st);
+// H = L^T L (k x k) from the first k columns of L (C x kmax, row-major).
+cudaError_t launch_pchol_gram_n(int n, const double* const L[], const int64_t kmax[], const int k[],
+                                const int64_t C[], double* const H[], const GemmWs& W, cudaStream_t st);
+// Vg = L U diag(1/sqrt(H_nn)) (C x k): unit eigenvectors of L L^T from the
+// eigenvectors U (k x k, columns) of H after the Jacobi iteration.
+cudaError_t launch_pchol_vectors_n(int n, const double* const L[], const int64_t kmax[], const int k[],
+                                   const int64_t C[], const double* const U[], const double* const H[],
+                                   double* const Vg[], const GemmWs& W, cudaStream_t st);
+// Y[j][i] = inv_sqrt_lam[j] * sum_c V[c*ldv + perm[j]] w[c] a[c][i]  (j < r).
+cudaError_t launch_basis_n(int n, const double* const V[], const int64_t C[], const int64_t ldv[],
+                           const int32_t* const perm[], const double* const isl[], const double* const w[],
+                           const double* const a[], int64_t N, const int r[], double* const Y[], const GemmWs& W,
+                           cudaStream_t st);
+// G = Y Y^T (r x r; Y: r rows of length N).
+cudaError_t launch_syrk_rows_n(int n, const double* const Y[], const int r[], int64_t N, double* const G[],
+                               const GemmWs& W, cudaStream_t st);
+// dst = Li src (Li: r x r, src and dst: r x N).
+cudaError_t launch_lower_apply_n(int n, const double* const Li[], const int r[], const double* const src[],
+                                 double* const dst[], int64_t N, const GemmWs& W, cudaStream_t st);
+// P[k][c] = sum_i Z[k][i] a[c][i]   (r x C).
+cudaError_t launch_project_n(int n, const double* const Z[], const int r[], const double* const a[],
+                             const int64_t C[], int64_t N, double* const P[], const GemmWs& W, cudaStream_t st);
+
+// Cholesky A = L L^T in place (lower; A is r x r row-major, its upper part is
+// overwritten) and Li = L^{-1} (lower, zeros above) for several matrices in
+// one cooperative launch. st: zeroed status per job; a non-positive pivot
+// raises FLAG_NOT_SPD (the pivot is replaced by 1 so the launch completes).
+struct CholJob {
+    double* A; double* Li; DevStatus* st; int r;
+};
+cudaError_t launch_chol_inv_multi(const CholJob* jobs, int njobs, int num_sms, cudaStream_t st);
 
 // V = I (C x C).
 cudaError_t launch_identity(double* V, int64_t C, cudaStream_t st);
@@ -98,26 +142,6 @@ struct PcholJob {
     const double* G; double* L; double* d; double* cand; int* piv; DevStatus* st; int64_t C; int kmax; double delta;
 };
 cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cudaStream_t st);
-// H = L^T L (k x k) from the first k columns of L.
-cudaError_t launch_pchol_gram(const double* L, int64_t C, int64_t kmax, int k, double* H, cudaStream_t st);
-// Vg = L U diag(1/sqrt(H_nn)) (C x k): unit eigenvectors of L L^T from the
-// eigenvectors U (k x k, columns) of H after the Jacobi iteration.
-cudaError_t launch_pchol_vectors(const double* L, int64_t C, int64_t kmax, int k, const double* U, const double* H,
-                                 double* Vg, cudaStream_t st);
-
-// Y[k][i] = inv_sqrt_lam[k] * sum_c V[c*ldv + perm[k]] w[c] a[c][i]  (k < r).
-cudaError_t launch_basis(const double* V, int64_t C, int64_t ldv, const int32_t* perm, const double* inv_sqrt_lam,
-                         const double* w, const double* a, int64_t N, int r, double* Y, cudaStream_t st);
-
-// Y <- orthonormalised rows of Y (r x N) by CholeskyQR2 (FP64): twice
-// G = Y Y^T, G = L L^T, Y <- L^{-1} Y. Ytmp holds r*N doubles, work >= 2 r^2.
-cudaError_t launch_cholqr2(double* Y, double* Ytmp, int r, int64_t N, double* work, DevStatus* status, int num_sms,
-                           cudaStream_t st);
-
-// P[k][c] = sum_i Z[k][i] a[c][i]   (r x C).
-cudaError_t launch_project(const double* Z, int r, const double* a, int64_t C, int64_t N, double* P,
-                           cudaStream_t st);
-
 // xin[t] = xi[t] * n0[tc[3t]] * n1[tc[3t+1]] * n2[tc[3t+2]].
 cudaError_t launch_fold_norms(const double* xi, const int32_t* tcol, int64_t T, const double* n0,
                               const double* n1, const double* n2, double* xin, cudaStream_t st);

@@ -132,30 +132,29 @@ __global__ void k_fold_norms(const double* xi, const int32_t* tcol, int64_t T, c
 // ---------------------------------------------------------------------------
 constexpr int GBM = 64, GBN = 64, GBK = 16;
 
-template <class AOp, class BOp, class COp>
-__global__ void __launch_bounds__(256) k_gemm_f64(int M, int N, int K, AOp A, BOp B, COp Cst) {
-    __shared__ double As[GBK][GBM];
-    __shared__ double Bs[GBK][GBN];
-    const int z = blockIdx.z;
-    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+// acc += A(z, m0:m0+64, kb:ke) * B(z, kb:ke, n0:n0+64) for this thread's 4 x 4 outputs
+// (rows ty + 16 i, columns tx + 16 j of the tile)
+template <class AOp, class BOp>
+__device__ __forceinline__ void gemm_tile(const AOp& A, const BOp& B, int z, int M, int N, int kb, int ke, int m0,
+                                          int n0, double (&As)[GBK][GBM], double (&Bs)[GBK][GBN],
+                                          double (&acc)[4][4]) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-    for (int k0 = 0; k0 < K; k0 += GBK) {
+    for (int k0 = kb; k0 < ke; k0 += GBK) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int e = threadIdx.x + 256 * u;
             int mm, kk;
             if (AOp::kfast) { kk = e % GBK; mm = e / GBK; } else { mm = e % GBM; kk = e / GBM; }
             const int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < M && gk < K) ? A(z, gm, gk) : 0.0;
+            As[kk][mm] = (gm < M && gk < ke) ? A(z, gm, gk) : 0.0;
             int nn;
             if (BOp::kfast) { kk = e % GBK; nn = e / GBK; } else { nn = e % GBN; kk = e / GBN; }
             const int gn = n0 + nn, gk2 = k0 + kk;
-            Bs[kk][nn] = (gn < N && gk2 < K) ? B(z, gk2, gn) : 0.0;
+            Bs[kk][nn] = (gn < N && gk2 < ke) ? B(z, gk2, gn) : 0.0;
         }
         __syncthreads();
 #pragma unroll
@@ -172,6 +171,17 @@ __global__ void __launch_bounds__(256) k_gemm_f64(int M, int N, int K, AOp A, BO
         }
         __syncthreads();
     }
+}
+
+template <class AOp, class BOp, class COp>
+__global__ void __launch_bounds__(256) k_gemm_f64(int M, int N, int K, AOp A, BOp B, COp Cst) {
+    __shared__ double As[GBK][GBM];
+    __shared__ double Bs[GBK][GBN];
+    const int z = blockIdx.z;
+    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+    gemm_tile(A, B, z, M, N, 0, K, m0, n0, As, Bs, acc);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int m = m0 + ty + 16 * i;
@@ -182,6 +192,146 @@ __global__ void __launch_bounds__(256) k_gemm_f64(int M, int N, int K, AOp A, BO
             if (n < N) Cst(z, m, n, acc[i][j]);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// grouped GEMM: up to kMaxGroup independent products (the three modes) in one
+// launch, each optionally split along K. A split writes its partial tile to
+// the workspace; the CTA that completes a tile (counted by an atomic per tile)
+// sums the partials in split order, so the result does not depend on timing,
+// and resets the counter for the next launch. A symmetric job (C = X X^T)
+// computes the tiles on and above the diagonal and stores both halves.
+// ---------------------------------------------------------------------------
+constexpr int kMaxGroup = 3;
+constexpr int kTileElems = GBM * GBN;
+
+template <class AOp, class BOp, class COp>
+struct GJob {
+    AOp A; BOp B; COp C;
+    int M, N, K;
+    int sym;        // 1: C is symmetric (M == N, A(m, k) == B(k, m))
+    int S;          // splits along K
+    int tiles_n;    // tiles along N
+    int ntile;      // tiles computed
+    int b0;         // first block of the job
+    int ctr0;       // first tile counter
+    int64_t ws0;    // first partial (doubles)
+};
+template <class AOp, class BOp, class COp>
+struct GGroup {
+    GJob<AOp, BOp, COp> j[kMaxGroup];
+    int n;
+    double* ws;
+    unsigned int* ctr;
+};
+
+template <class AOp, class BOp, class COp>
+__global__ void __launch_bounds__(256) k_gemm_group(const __grid_constant__ GGroup<AOp, BOp, COp> G) {
+    __shared__ double As[GBK][GBM];
+    __shared__ double Bs[GBK][GBN];
+    __shared__ unsigned int s_last;
+    int ji = 0;
+    while (ji + 1 < G.n && (int)blockIdx.x >= G.j[ji + 1].b0) ++ji;
+    const GJob<AOp, BOp, COp>& J = G.j[ji];
+    const int local = (int)blockIdx.x - J.b0;
+    const int split = local % J.S, tile = local / J.S;
+    int tm, tn;
+    if (J.sym) {   // upper-triangle tiles, row by row
+        int t = tile, len = J.tiles_n;
+        tm = 0;
+        while (t >= len) { t -= len; ++tm; --len; }
+        tn = tm + t;
+    } else {
+        tm = tile / J.tiles_n;
+        tn = tile - tm * J.tiles_n;
+    }
+    const int m0 = tm * GBM, n0 = tn * GBN;
+    const int kper = ((J.K + J.S - 1) / J.S + GBK - 1) / GBK * GBK;
+    const int kb = min(J.K, split * kper), ke = min(J.K, kb + kper);
+    double acc[4][4];
+    gemm_tile(J.A, J.B, 0, J.M, J.N, kb, ke, m0, n0, As, Bs, acc);
+    if (J.S > 1) {
+        double* w = G.ws + J.ws0 + ((int64_t)tile * J.S + split) * kTileElems;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) __stcg(w + (i * 4 + j) * 256 + threadIdx.x, acc[i][j]);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned int* c = G.ctr + J.ctr0 + tile;
+            const unsigned int old = atomicAdd(c, 1u);
+            s_last = (old == (unsigned int)J.S - 1) ? 1u : 0u;
+            if (s_last) *c = 0u;
+        }
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        const double* w0 = G.ws + J.ws0 + (int64_t)tile * J.S * kTileElems;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                double v = 0.0;
+                for (int s = 0; s < J.S; ++s) v += __ldcg(w0 + (int64_t)s * kTileElems + (i * 4 + j) * 256 + threadIdx.x);
+                acc[i][j] = v;
+            }
+    }
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty + 16 * i;
+        if (m >= J.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx + 16 * j;
+            if (n >= J.N) continue;
+            J.C(0, m, n, acc[i][j]);
+            if (J.sym && tm != tn) J.C(0, n, m, acc[i][j]);
+        }
+    }
+}
+
+// Fills in the launch layout of n jobs (A, B, C, M, N, K, sym set by the
+// caller) and launches them; splits along K until about two CTAs per SM are
+// busy, within the workspace.
+template <class AOp, class BOp, class COp>
+cudaError_t gemm_group(GGroup<AOp, BOp, COp>& G, const GemmWs& W, cudaStream_t st) {
+    int64_t tiles = 0;
+    int kmin = 1 << 30;
+    for (int i = 0; i < G.n; ++i) {
+        auto& J = G.j[i];
+        const int tm = (J.M + GBM - 1) / GBM, tn = (J.N + GBN - 1) / GBN;
+        J.tiles_n = tn;
+        J.ntile = (J.M <= 0 || J.N <= 0) ? 0 : (J.sym ? tn * (tn + 1) / 2 : tm * tn);
+        tiles += J.ntile;
+        if (J.ntile > 0) kmin = std::min(kmin, J.K);
+    }
+    if (tiles == 0) return cudaSuccess;
+    const int64_t target = 2 * (int64_t)W.num_sms;
+    int S = 1;
+    if (tiles < target && W.ws && W.ctr) {
+        S = (int)std::min<int64_t>(16, target / tiles);
+        S = std::min(S, std::max(1, kmin / (4 * GBK)));
+        while (S > 1 && (tiles * S * kTileElems > W.ws_cap || tiles > W.ctr_cap)) --S;
+    }
+    int b = 0, c = 0;
+    int64_t w = 0;
+    for (int i = 0; i < G.n; ++i) {
+        auto& J = G.j[i];
+        J.S = S;
+        J.b0 = b;
+        J.ctr0 = c;
+        J.ws0 = w;
+        b += J.ntile * S;
+        c += J.ntile;
+        w += (int64_t)J.ntile * S * kTileElems;
+    }
+    G.ws = W.ws;
+    G.ctr = W.ctr;
+    k_gemm_group<AOp, BOp, COp><<<b, 256, 0, st>>>(G);
+    count_kernels(1);
+    return cudaGetLastError();
 }
 
 template <class AOp, class BOp, class COp>
@@ -510,20 +660,44 @@ struct PcholArgs {
     const PcholMode* m; int nmodes;
 };
 
+// (max, smallest index among equal maxima) is a total order, so the butterfly
+// leaves the same candidate in every lane; the sum is taken in a fixed order.
+__device__ __forceinline__ bool cand_better(double m2, int i2, double m1, int i1) {
+    return m2 > m1 || (m2 == m1 && i2 >= 0 && (i1 < 0 || i2 < i1));
+}
+// CTA-wide (max, argmax, sum); every thread receives the result
+__device__ void cta_reduce_cand(double& mx, int& ix, double& sm, double* s_m, int* s_i, double* s_s) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int o = 16; o; o >>= 1) {
+        const double m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, ix, o);
+        if (cand_better(m2, i2, mx, ix)) { mx = m2; ix = i2; }
+        sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    }
+    __syncthreads();   // earlier readers of the scratch are done
+    if (lane == 0) { s_m[warp] = mx; s_i[warp] = ix; s_s[warp] = sm; }
+    __syncthreads();
+    mx = -1.0;
+    ix = -1;
+    sm = 0.0;
+    for (int w = 0; w < nw; ++w) {
+        if (cand_better(s_m[w], s_i[w], mx, ix)) { mx = s_m[w]; ix = s_i[w]; }
+        sm += s_s[w];
+    }
+}
+
 __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
     const PcholMode J = A.m[find_job(A.m, A.nmodes)];
     const int lb = blockIdx.x - J.cta0, nb = J.ncta;
     const int C = J.C;
     extern __shared__ double lrow[];            // row p of L, kmax entries
-    __shared__ double s_red[2][8];
-    __shared__ int s_redi[8];
-    __shared__ int s_p;
-    __shared__ double s_dmax, s_sum;
+    __shared__ double s_m[8], s_s[8];
+    __shared__ int s_i[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     // rows of this CTA: [r0, r1)
     const int per = (C + nb - 1) / nb;
     const int r0 = min(C, lb * per), r1 = min(C, r0 + per);
-    // initial residual diagonal and candidates (parity 0)
+    // this CTA's (max, argmax, sum) of the residual diagonal, published by step parity
     auto publish = [&](int parity) {
         double mx = -1.0, sm = 0.0;
         int ix = -1;
@@ -532,27 +706,12 @@ __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
             sm += v;
             if (v > mx) { mx = v; ix = j; }
         }
-        for (int o = 16; o; o >>= 1) {
-            const double m2 = __shfl_xor_sync(0xffffffffu, mx, o);
-            const int i2 = __shfl_xor_sync(0xffffffffu, ix, o);
-            if (m2 > mx || (m2 == mx && i2 >= 0 && (ix < 0 || i2 < ix))) { mx = m2; ix = i2; }
-            sm += __shfl_xor_sync(0xffffffffu, sm, o);
-        }
-        if (lane == 0) { s_red[0][warp] = mx; s_redi[warp] = ix; s_red[1][warp] = sm; }
-        __syncthreads();
+        cta_reduce_cand(mx, ix, sm, s_m, s_i, s_s);
         if (threadIdx.x == 0) {
-            double bm = -1.0, bs = 0.0;
-            int bi = -1;
-            for (int w = 0; w < nw; ++w) {
-                const double m2 = s_red[0][w];
-                const int i2 = s_redi[w];
-                if (m2 > bm || (m2 == bm && i2 >= 0 && (bi < 0 || i2 < bi))) { bm = m2; bi = i2; }
-                bs += s_red[1][w];
-            }
             double* c = J.cand + ((int64_t)parity * nb + lb) * 3;
-            __stcg(c, bm);
-            __stcg(c + 1, (double)bi);
-            __stcg(c + 2, bs);
+            __stcg(c, mx);
+            __stcg(c + 1, (double)ix);
+            __stcg(c + 2, sm);
         }
     };
     for (int j = r0 + threadIdx.x; j < r1; j += blockDim.x) __stcg(J.d + j, __ldcg(J.G + (int64_t)j * C + j));
@@ -560,25 +719,21 @@ __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
     publish(0);
     if (!group_barrier(J.st, nb)) return;
     int k = 0;
+    double s_sum = 0.0;
     for (;; ++k) {
         const int par = k & 1;
-        if (threadIdx.x == 0) {
-            double bm = -1.0, bs = 0.0;
-            int bi = -1;
-            for (int c = 0; c < nb; ++c) {
-                const double* cc = J.cand + ((int64_t)par * nb + c) * 3;
-                const double m2 = __ldcg(cc);
-                const int i2 = (int)__ldcg(cc + 1);
-                if (m2 > bm || (m2 == bm && i2 >= 0 && (bi < 0 || i2 < bi))) { bm = m2; bi = i2; }
-                bs += __ldcg(cc + 2);
-            }
-            s_p = bi;
-            s_dmax = bm;
-            s_sum = bs;
+        // every CTA reduces the candidates of all CTAs of the job
+        double dmax = -1.0, sum = 0.0;
+        int p = -1;
+        for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+            const double* cc = J.cand + ((int64_t)par * nb + c) * 3;
+            const double m2 = __ldcg(cc);
+            const int i2 = (int)__ldcg(cc + 1);
+            if (cand_better(m2, i2, dmax, p)) { dmax = m2; p = i2; }
+            sum += __ldcg(cc + 2);
         }
-        __syncthreads();
-        const int p = s_p;
-        const double dmax = s_dmax;
+        cta_reduce_cand(dmax, p, sum, s_m, s_i, s_s);
+        s_sum = sum;
         // stop when the residual trace is small enough, or at kmax columns
         if (k >= J.kmax || !(s_sum > J.delta) || p < 0 || !(dmax > 0.0)) break;
         for (int t = threadIdx.x; t < k; t += blockDim.x) lrow[t] = __ldcg(J.L + (int64_t)p * J.kmax + t);
@@ -667,16 +822,29 @@ __global__ void k_sort_select(const double* G, int C, double eps, int forced, do
 constexpr int CHB = 32;
 
 // Blocked right-looking Cholesky A = L L^T (lower, in place) followed by the
-// triangular inverse Li = L^{-1} (lower, zeros above), as one cooperative
-// grid: a barrier after each panel step and after each block row of Li.
-__global__ void __launch_bounds__(256) k_chol_inv(double* A, double* Li, int r, DevStatus* st) {
+// triangular inverse Li = L^{-1} (lower, zeros above) of several matrices in
+// one cooperative grid, CTAs split between the jobs: a group barrier after
+// each panel step and after each block row of Li.
+struct CholMode {
+    double* A; double* Li; DevStatus* st; int r; int cta0; int ncta;
+};
+struct CholArgs {
+    const CholMode* m; int nmodes;
+};
+__global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
     __shared__ double D[CHB][CHB + 1];
-    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const CholMode J = Ar.m[find_job(Ar.m, Ar.nmodes)];
+    const int lb = blockIdx.x - J.cta0, nb = J.ncta;
+    double* A = J.A;
+    double* Li = J.Li;
+    const int r = J.r;
+    DevStatus* st = J.st;
+    const int64_t nthr = (int64_t)nb * blockDim.x;
+    const int64_t gtid = (int64_t)lb * blockDim.x + threadIdx.x;
     const int nbk = (r + CHB - 1) / CHB;
     for (int j0 = 0; j0 < r; j0 += CHB) {
         const int b = min(CHB, r - j0);
-        if (blockIdx.x == 0) {
+        if (lb == 0) {
             for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
                 const int i = e / b, k = e % b;
                 D[i][k] = __ldcg(A + (int64_t)(j0 + i) * r + j0 + k);
@@ -702,7 +870,7 @@ __global__ void __launch_bounds__(256) k_chol_inv(double* A, double* Li, int r, 
                 __stcg(A + (int64_t)(j0 + i) * r + j0 + k, k <= i ? D[i][k] : 0.0);
             }
         }
-        if (!grid_barrier(st)) return;
+        if (!group_barrier(st, nb)) return;
         // every CTA stages L11 in shared memory for the panel solve
         for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
             const int i = e / b, k = e % b;
@@ -719,7 +887,7 @@ __global__ void __launch_bounds__(256) k_chol_inv(double* A, double* Li, int r, 
             }
             for (int k = 0; k < b; ++k) __stcg(A + i * r + j0 + k, x[k]);
         }
-        if (!grid_barrier(st)) return;
+        if (!group_barrier(st, nb)) return;
         const int64_t n2 = r - j0 - b;
         for (int64_t e = gtid; e < n2 * n2; e += nthr) {
             const int64_t i = j0 + b + e / n2, k = j0 + b + e % n2;
@@ -728,7 +896,7 @@ __global__ void __launch_bounds__(256) k_chol_inv(double* A, double* Li, int r, 
             for (int l = 0; l < b; ++l) s -= __ldcg(A + i * r + j0 + l) * __ldcg(A + k * r + j0 + l);
             __stcg(A + i * r + k, s);
         }
-        if (!grid_barrier(st)) return;
+        if (!group_barrier(st, nb)) return;
     }
     // Li: zero the strict upper part, invert the diagonal blocks (one CTA each)
     for (int64_t e = gtid; e < (int64_t)r * r; e += nthr) {
@@ -736,7 +904,7 @@ __global__ void __launch_bounds__(256) k_chol_inv(double* A, double* Li, int r, 
         if (k / CHB > i / CHB) __stcg(Li + e, 0.0);
     }
     __shared__ double Lb[CHB][CHB + 1];
-    for (int I = blockIdx.x; I < nbk; I += gridDim.x) {
+    for (int I = lb; I < nbk; I += nb) {
         const int i0 = I * CHB, b = min(CHB, r - i0);
         for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
             const int i = e / b, k = e % b;
@@ -758,7 +926,7 @@ __global__ void __launch_bounds__(256) k_chol_inv(double* A, double* Li, int r, 
         }
         __syncthreads();
     }
-    if (!grid_barrier(st)) return;
+    if (!group_barrier(st, nb)) return;
     // block rows I = 1..: Li[I][J] = -inv(L_II) sum_{K=J}^{I-1} L[I][K] Li[K][J]
     for (int I = 1; I < nbk; ++I) {
         const int i0 = I * CHB, bi = min(CHB, r - i0);
@@ -770,7 +938,7 @@ __global__ void __launch_bounds__(256) k_chol_inv(double* A, double* Li, int r, 
             for (int kk = J * CHB; kk < i0; ++kk) s += __ldcg(A + (int64_t)(i0 + ii) * r + kk) * __ldcg(Li + (int64_t)kk * r + jj);
             __stcg(Li + (int64_t)(i0 + ii) * r + jj, s);
         }
-        if (!grid_barrier(st)) return;
+        if (!group_barrier(st, nb)) return;
         for (int64_t e = gtid; e < (int64_t)bi * i0; e += nthr) {
             const int ii = (int)(e / i0), jj = (int)(e % i0);
             double s = 0.0;
@@ -779,12 +947,12 @@ __global__ void __launch_bounds__(256) k_chol_inv(double* A, double* Li, int r, 
             // result for (ii, jj) reads column jj of S rows <= ii: write to a staging slot
             __stcg(A + (int64_t)(i0 + ii) * r + jj, s);   // the strict lower block part of A is no longer needed
         }
-        if (!grid_barrier(st)) return;
+        if (!group_barrier(st, nb)) return;
         for (int64_t e = gtid; e < (int64_t)bi * i0; e += nthr) {
             const int ii = (int)(e / i0), jj = (int)(e % i0);
             __stcg(Li + (int64_t)(i0 + ii) * r + jj, __ldcg(A + (int64_t)(i0 + ii) * r + jj));
         }
-        if (!grid_barrier(st)) return;
+        if (!group_barrier(st, nb)) return;
     }
 }
 
@@ -875,11 +1043,6 @@ cudaError_t launch_norm_columns(double* a, int64_t C, int64_t N, double* norms, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_gram_weighted(const double* a, int64_t C, int64_t N, const double* w, double* G,
-                                 cudaStream_t st) {
-    return gemm_f64((int)C, (int)C, (int)N, 1, RowK{a, N}, NRowK{a, N}, StoreRowW{G, C, w}, st);
-}
-
 cudaError_t launch_identity(double* V, int64_t C, cudaStream_t st) {
     k_identity<<<(unsigned)((C * C + 255) / 256 < 4096 ? (C * C + 255) / 256 : 4096), 256, 0, st>>>(V, C);
     count_kernels(1);
@@ -962,19 +1125,14 @@ cudaError_t launch_sort_select(const double* G, int64_t C, double eps, int force
     return cudaGetLastError();
 }
 
-cudaError_t launch_basis(const double* V, int64_t C, int64_t ldv, const int32_t* perm, const double* inv_sqrt_lam,
-                         const double* w, const double* a, int64_t N, int r, double* Y, cudaStream_t st) {
-    return gemm_f64(r, (int)N, (int)C, 1, BasisA{V, ldv, perm, w, inv_sqrt_lam}, KRowN{a, N},
-                    StoreRow{Y, N, 0}, st);
-}
-
 cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cudaStream_t st) {
     if (njobs < 1) return cudaSuccess;
     size_t smem = 0;
     std::vector<int64_t> want(njobs);
     for (int m = 0; m < njobs; ++m) {
         smem = std::max(smem, (size_t)jobs[m].kmax * sizeof(double));
-        want[m] = std::max<int64_t>(1, (jobs[m].C + 63) / 64);   // a warp per row and step, ~64 rows a CTA
+        // a warp per row and step; the candidate scratch holds 1024 CTAs per job
+        want[m] = std::min<int64_t>(1024, std::max<int64_t>(1, (jobs[m].C + 7) / 8));
     }
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_pchol_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1012,44 +1170,109 @@ cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cud
     return cudaSuccess;
 }
 
-cudaError_t launch_pchol_gram(const double* L, int64_t C, int64_t kmax, int k, double* H, cudaStream_t st) {
-    return gemm_f64(k, k, (int)C, 1, ColK{L, kmax}, KRowN{L, kmax}, StoreRow{H, k, 0}, st);
-}
-
-cudaError_t launch_pchol_vectors(const double* L, int64_t C, int64_t kmax, int k, const double* U, const double* H,
-                                 double* Vg, cudaStream_t st) {
-    // Vg[c][n] = sum_t L[c][t] U[t][n] / sqrt(H_nn): unit eigenvectors of L L^T
-    return gemm_f64((int)C, k, k, 1, RowK{L, kmax}, KRowN{U, k}, StoreColScaled{Vg, k, H, k}, st);
-}
-
-cudaError_t launch_cholqr2(double* Y, double* Ytmp, int r, int64_t N, double* work, DevStatus* status, int num_sms,
-                           cudaStream_t st) {
-    double* Gz = work;
-    double* Li = work + (int64_t)r * r;
-    double* src = Y;
-    double* dst = Ytmp;
-    for (int pass = 0; pass < 2; ++pass) {
-        cudaError_t e = gemm_f64(r, r, (int)N, 1, RowK{src, N}, NRowK{src, N}, StoreRow{Gz, r, 0}, st);
+cudaError_t launch_chol_inv_multi(const CholJob* jobs, int njobs, int num_sms, cudaStream_t st) {
+    if (njobs < 1) return cudaSuccess;
+    std::vector<int64_t> want(njobs);
+    for (int m = 0; m < njobs; ++m) want[m] = std::max<int64_t>(1, ((int64_t)jobs[m].r * jobs[m].r + 1023) / 1024);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_inv_multi, 256, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int64_t resident = (int64_t)per_sm * num_sms;
+    const int64_t cap = std::min<int64_t>(resident, std::max<int64_t>(num_sms, njobs));
+    for (int j0 = 0; j0 < njobs; j0 += (int)resident) {
+        const int nj = (int)std::min<int64_t>(resident, njobs - j0);
+        std::vector<int64_t> w(want.begin() + j0, want.begin() + j0 + nj);
+        std::vector<int> nc = split_ctas(w, cap);
+        std::vector<CholMode> hm(nj);
+        int cta = 0;
+        for (int m = 0; m < nj; ++m) {
+            const CholJob& J = jobs[j0 + m];
+            hm[m] = CholMode{J.A, J.Li, J.st, J.r, cta, nc[m]};
+            cta += nc[m];
+        }
+        CholMode* dm = nullptr;
+        cudaError_t e = cudaMallocAsync(&dm, sizeof(CholMode) * nj, st);
         if (e != cudaSuccess) return e;
-        const int64_t want = std::max<int64_t>(1, ((int64_t)r * r + 1023) / 1024);
-        int nblk = coop_blocks(k_chol_inv, 256, 0, num_sms, want);
-        if (nblk > num_sms) nblk = num_sms;
-        void* args[] = {&Gz, &Li, &r, &status};
-        count_kernels(1);
-        e = cudaLaunchCooperativeKernel((void*)k_chol_inv, dim3(nblk), dim3(256), args, 0, st);
+        e = cudaMemcpyAsync(dm, hm.data(), sizeof(CholMode) * nj, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            CholArgs a{dm, nj};
+            void* args[] = {&a};
+            count_kernels(1);
+            e = cudaLaunchCooperativeKernel((void*)k_chol_inv_multi, dim3(cta), dim3(256), args, 0, st);
+        }
+        cudaFreeAsync(dm, st);
         if (e != cudaSuccess) return e;
-        // dst = Li * src  (rows of dst orthonormal after the second pass)
-        e = gemm_f64(r, (int)N, r, 1, RowK{Li, r}, KRowN{src, N}, StoreRow{dst, N, 0}, st);
-        if (e != cudaSuccess) return e;
-        std::swap(src, dst);
     }
-    // after two passes the result is back in Y
     return cudaSuccess;
 }
 
-cudaError_t launch_project(const double* Z, int r, const double* a, int64_t C, int64_t N, double* P,
+// grouped products of the reduction (one launch for up to three modes) ------
+cudaError_t launch_gram_weighted_n(int n, const double* const a[], const int64_t C[], int64_t N,
+                                   const double* const w[], double* const G[], const GemmWs& W, cudaStream_t st) {
+    GGroup<RowK, NRowK, StoreRowW> g{};
+    g.n = n;
+    for (int i = 0; i < n; ++i)
+        g.j[i] = {RowK{a[i], N}, NRowK{a[i], N}, StoreRowW{G[i], C[i], w[i]}, (int)C[i], (int)C[i], (int)N, 1};
+    return gemm_group(g, W, st);
+}
+
+cudaError_t launch_pchol_gram_n(int n, const double* const L[], const int64_t kmax[], const int k[],
+                                const int64_t C[], double* const H[], const GemmWs& W, cudaStream_t st) {
+    GGroup<ColK, KRowN, StoreRow> g{};
+    g.n = n;
+    for (int i = 0; i < n; ++i)
+        g.j[i] = {ColK{L[i], kmax[i]}, KRowN{L[i], kmax[i]}, StoreRow{H[i], k[i], 0}, k[i], k[i], (int)C[i], 1};
+    return gemm_group(g, W, st);
+}
+
+cudaError_t launch_pchol_vectors_n(int n, const double* const L[], const int64_t kmax[], const int k[],
+                                   const int64_t C[], const double* const U[], const double* const H[],
+                                   double* const Vg[], const GemmWs& W, cudaStream_t st) {
+    GGroup<RowK, KRowN, StoreColScaled> g{};
+    g.n = n;
+    for (int i = 0; i < n; ++i)
+        g.j[i] = {RowK{L[i], kmax[i]}, KRowN{U[i], k[i]}, StoreColScaled{Vg[i], k[i], H[i], k[i]}, (int)C[i], k[i],
+                  k[i], 0};
+    return gemm_group(g, W, st);
+}
+
+cudaError_t launch_basis_n(int n, const double* const V[], const int64_t C[], const int64_t ldv[],
+                           const int32_t* const perm[], const double* const isl[], const double* const w[],
+                           const double* const a[], int64_t N, const int r[], double* const Y[], const GemmWs& W,
                            cudaStream_t st) {
-    return gemm_f64(r, (int)C, (int)N, 1, RowK{Z, N}, NRowK{a, N}, StoreRow{P, C, 0}, st);
+    GGroup<BasisA, KRowN, StoreRow> g{};
+    g.n = n;
+    for (int i = 0; i < n; ++i)
+        g.j[i] = {BasisA{V[i], ldv[i], perm[i], w[i], isl[i]}, KRowN{a[i], N}, StoreRow{Y[i], N, 0}, r[i], (int)N,
+                  (int)C[i], 0};
+    return gemm_group(g, W, st);
+}
+
+cudaError_t launch_syrk_rows_n(int n, const double* const Y[], const int r[], int64_t N, double* const G[],
+                               const GemmWs& W, cudaStream_t st) {
+    GGroup<RowK, NRowK, StoreRow> g{};
+    g.n = n;
+    for (int i = 0; i < n; ++i)
+        g.j[i] = {RowK{Y[i], N}, NRowK{Y[i], N}, StoreRow{G[i], r[i], 0}, r[i], r[i], (int)N, 1};
+    return gemm_group(g, W, st);
+}
+
+cudaError_t launch_lower_apply_n(int n, const double* const Li[], const int r[], const double* const src[],
+                                 double* const dst[], int64_t N, const GemmWs& W, cudaStream_t st) {
+    GGroup<RowK, KRowN, StoreRow> g{};
+    g.n = n;
+    for (int i = 0; i < n; ++i)
+        g.j[i] = {RowK{Li[i], r[i]}, KRowN{src[i], N}, StoreRow{dst[i], N, 0}, r[i], (int)N, r[i], 0};
+    return gemm_group(g, W, st);
+}
+
+cudaError_t launch_project_n(int n, const double* const Z[], const int r[], const double* const a[],
+                             const int64_t C[], int64_t N, double* const P[], const GemmWs& W, cudaStream_t st) {
+    GGroup<RowK, NRowK, StoreRow> g{};
+    g.n = n;
+    for (int i = 0; i < n; ++i)
+        g.j[i] = {RowK{Z[i], N}, NRowK{a[i], N}, StoreRow{P[i], C[i], 0}, r[i], (int)C[i], (int)N, 0};
+    return gemm_group(g, W, st);
 }
 
 cudaError_t launch_fold_norms(const double* xi, const int32_t* tcol, int64_t T, const double* n0,
