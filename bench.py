@@ -211,7 +211,8 @@ def roofline(report, info, N, steps, precision, peaks):
     st = report.get("steps", {})
     if not st:
         return None
-    name = max(st, key=lambda k: st[k]["ms"])
+    # names with a dot are parts of another step (reported, not ranked)
+    name = max((k for k in st if "." not in k), key=lambda k: st[k]["ms"])
     ms_launch = st[name]["ms"] / max(st[name]["launches"], 1)
     launches_per_step = st[name]["launches"] / max(steps, 1)
     fl = step_flops(name, info, N)

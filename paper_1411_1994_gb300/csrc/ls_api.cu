@@ -457,9 +457,12 @@ namespace {
 // Scratch of one mode of one context during the reduction.
 struct RedMode {
     double *G = nullptr, *L = nullptr, *pd = nullptr, *cand = nullptr, *H = nullptr, *V = nullptr, *snap = nullptr,
-           *isl = nullptr, *w = nullptr, *vg = nullptr, *ytmp = nullptr, *Gz = nullptr, *Li = nullptr;
+           *isl = nullptr, *w = nullptr, *vg = nullptr, *ytmp = nullptr, *Gz = nullptr, *Li = nullptr, *D2 = nullptr;
+    // two-stage shared-memory eigen-solver: U0 = I + F1, S = U0^T U0, SLi, Uo, T1 = H Uo, Hp = Uo^T T1, F2
+    double *U0 = nullptr, *S = nullptr, *SLi = nullptr, *Uo = nullptr, *T1 = nullptr, *Hp = nullptr, *F2 = nullptr;
     int32_t *piv = nullptr, *perm = nullptr;
     int k = 0;
+    bool df = false;
 };
 
 // One context inside a (possibly batched) reduction.
@@ -467,14 +470,16 @@ struct RedState {
     ls_ctx* ctx = nullptr;
     double eps = 0.0;
     const int32_t* forced = nullptr;
-    DevStatus* d_st = nullptr;   // [0, 3): pivoted Cholesky, then Jacobi, per mode; [3, 6): CholeskyQR2 per mode
+    // [0, 3): pivoted Cholesky, then the eigen-solver, per mode; [3, 6): CholeskyQR2 per mode;
+    // [6, 9): orthonormalisation inside the two-stage eigen-solver per mode
+    DevStatus* d_st = nullptr;
     double* d_sel = nullptr;
     GemmWs gw{};
     RedMode m[3];
     int sweeps[3] = {0, 0, 0};
     int64_t rotations[3] = {0, 0, 0};
     double sel[3][3] = {};
-    DevStatus hs[6] = {};
+    DevStatus hs[9] = {};
     double floor_noise = 0.0;
     int64_t T = 0;
 };
@@ -501,8 +506,8 @@ int red_prepare(RedState& R, PcholJob* pj) {
     count_h2d(3 * T * sizeof(int32_t));
     CUS(cudaMemcpyAsync(ctx->d_xi, ctx->xi.data(), T * sizeof(double), cudaMemcpyHostToDevice, st));
     count_h2d(T * sizeof(double));
-    CUS(dalloc(ctx, &R.d_st, 6));
-    CUS(cudaMemsetAsync(R.d_st, 0, 6 * sizeof(DevStatus), st));
+    CUS(dalloc(ctx, &R.d_st, 9));
+    CUS(cudaMemsetAsync(R.d_st, 0, 9 * sizeof(DevStatus), st));
     CUS(dalloc(ctx, &R.d_sel, 9));
     R.gw.num_sms = ctx->num_sms;
     R.gw.ws_cap = gemm_ws_doubles(ctx->num_sms);
@@ -551,7 +556,8 @@ int red_after_pchol(RedState& R, JacobiJob* jj) {
     for (int l = 0; l < 3; ++l)
         if (R.hs[l].flag == FLAG_TIMEOUT)
             return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: pivoted Cholesky barrier timed out (mode %d)", l);
-    CUS(cudaMemsetAsync(R.d_st, 0, 6 * sizeof(DevStatus), st));
+    CUS(cudaMemsetAsync(R.d_st, 0, 9 * sizeof(DevStatus), st));
+    const int kdf = jacobi_df_max_k();
     const double* L[3];
     double* H[3];
     int64_t Cs[3];
@@ -565,6 +571,9 @@ int red_after_pchol(RedState& R, JacobiJob* jj) {
         CUS(dalloc(ctx, &M.perm, k));
         CUS(dalloc(ctx, &M.isl, k));
         CUS(launch_identity(M.V, k, st));
+        M.df = k <= kdf;
+        if (M.df)
+            for (double** q : {&M.U0, &M.S, &M.SLi, &M.Uo, &M.T1, &M.Hp, &M.F2}) CUS(dalloc(ctx, q, (int64_t)k * k));
         L[l] = M.L;
         H[l] = M.H;
         Cs[l] = ctx->mode[l].C;
@@ -589,7 +598,8 @@ int red_select(RedState& R) {
                                ctx->d_sigma[l], M.isl, R.d_sel + 3 * l, st));
     }
     CUS(cudaMemcpyAsync(R.hs, R.d_st, 3 * sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
-    count_d2h(3 * sizeof(DevStatus));
+    CUS(cudaMemcpyAsync(R.hs + 6, R.d_st + 6, 3 * sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    count_d2h(6 * sizeof(DevStatus));
     CUS(cudaMemcpyAsync(R.sel, R.d_sel, sizeof R.sel, cudaMemcpyDeviceToHost, st));
     count_d2h(sizeof R.sel);
     return LS_OK;
@@ -604,8 +614,12 @@ int red_basis(RedState& R, CholJob* cj) {
     for (int l = 0; l < 3; ++l) {
         if (R.hs[l].flag == FLAG_TIMEOUT)
             return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Jacobi grid barrier timed out (mode %d)", l);
-        if (R.hs[l].flag == FLAG_NOCONVERGE || R.hs[l].sweeps <= 0)
+        if (R.hs[l].flag == FLAG_NOCONVERGE || R.hs[l].sweeps < 0)
             return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: Jacobi did not converge (mode %d)", l);
+        if (R.hs[6 + l].flag == FLAG_TIMEOUT)
+            return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: eigen-solver Cholesky barrier timed out (mode %d)", l);
+        if (R.hs[6 + l].flag == FLAG_NOT_SPD)
+            return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: eigenvector orthonormalisation failed (mode %d)", l);
         R.sweeps[l] = R.hs[l].sweeps;
         ctx->r[l] = (int32_t)R.sel[l][0];
         int64_t rot = 0;
@@ -626,6 +640,7 @@ int red_basis(RedState& R, CholJob* cj) {
         CUS(dalloc(ctx, &ctx->d_P[l], (int64_t)r * C));
         CUS(dalloc(ctx, &M.Gz, (int64_t)r * r));
         CUS(dalloc(ctx, &M.Li, (int64_t)r * r));
+        CUS(dalloc(ctx, &M.D2, (int64_t)r * r));
         CUS(dalloc(ctx, &M.ytmp, (int64_t)r * N));
         CUS(dalloc(ctx, &M.vg, C * M.k));
         L[l] = M.L;
@@ -655,13 +670,14 @@ int red_basis(RedState& R, CholJob* cj) {
     return LS_OK;
 }
 
-// CholeskyQR2 between the two factorisations: Y' = L^{-1} Y, then G = Y' Y'^T
+// CholeskyQR2 after the first factorisation: Y' = L^{-1} Y, G' = Y' Y'^T, and
+// the second pass T = G'^{-1/2} by its series (G' = I + O(u32 cond(Y)^2))
 int red_cholqr_mid(RedState& R) {
     ls_ctx* ctx = R.ctx;
     cudaStream_t st = ctx->st;
     const int64_t N = ctx->p.N;
-    const double *Li[3], *src[3], *yc[3];
-    double *dst[3], *Gz[3];
+    const double *Li[3], *src[3], *yc[3], *gc[3];
+    double *dst[3], *Gz[3], *D2[3], *T[3];
     int rs[3];
     for (int l = 0; l < 3; ++l) {
         Li[l] = R.m[l].Li;
@@ -669,11 +685,15 @@ int red_cholqr_mid(RedState& R) {
         dst[l] = R.m[l].ytmp;
         yc[l] = R.m[l].ytmp;
         Gz[l] = R.m[l].Gz;
+        gc[l] = R.m[l].Gz;
+        D2[l] = R.m[l].D2;
+        T[l] = R.m[l].Li;
         rs[l] = ctx->r[l];
     }
     Scope sc("cholqr2", st);
     CUS(launch_lower_apply_n(3, Li, rs, src, dst, N, R.gw, st));
     CUS(launch_syrk_rows_n(3, yc, rs, N, Gz, R.gw, st));
+    CUS(launch_lowdin_n(3, gc, rs, D2, T, R.gw, st));
     return LS_OK;
 }
 
@@ -763,7 +783,8 @@ int red_finish(RedState& R, ls_tucker_info* info) {
         RedMode& M = R.m[l];
         for (void* q : {(void*)M.G, (void*)M.L, (void*)M.pd, (void*)M.cand, (void*)M.H, (void*)M.V, (void*)M.snap,
                         (void*)M.isl, (void*)M.w, (void*)M.piv, (void*)M.perm, (void*)M.vg, (void*)M.ytmp,
-                        (void*)M.Gz, (void*)M.Li})
+                        (void*)M.Gz, (void*)M.Li, (void*)M.D2, (void*)M.U0, (void*)M.S, (void*)M.SLi, (void*)M.Uo, (void*)M.T1,
+                        (void*)M.Hp, (void*)M.F2})
             dfree(ctx, q);
     }
     dfree(ctx, d_perm_t);
@@ -825,6 +846,97 @@ cudaError_t join(cudaStream_t to, cudaStream_t from) {
     return rc;
 }
 
+// Eigen-decomposition H = V diag(lambda) V^T of every mode of the batch, on s0.
+// Where k fits the shared-memory solver: a first Jacobi run from H gives
+// U0 = I + F1 (FP32 accuracy), U0 is orthonormalised in FP64 (Cholesky of
+// U0^T U0), H' = Uo^T H Uo is formed in FP64, a second Jacobi run on the
+// nearly diagonal H' gives its eigenvalues (written to the diagonal of H')
+// and I + F2, and V = Uo + Uo F2; H' then takes the place of H. Larger k:
+// the FP64 grid Jacobi. The eps-rule tolerances: 1e-6 for the first run
+// (FP32), 1e-10 for the second; forced ranks use the same.
+int eigen_all(std::vector<RedState>& R, ls_ctx* const* ctxs, int n, const std::vector<JacobiJob>& jj, cudaStream_t s0) {
+    ls_ctx* c0 = ctxs[0];
+    std::vector<JacobiJob> grid;
+    std::vector<DfJob> s1, s2;
+    for (int i = 0; i < n; ++i)
+        for (int l = 0; l < 3; ++l) {
+            RedMode& M = R[i].m[l];
+            const JacobiJob& J = jj[3 * i + l];
+            if (!M.df) { grid.push_back(J); continue; }
+            s1.push_back(DfJob{M.H, M.k, M.T1, 1, M.U0, 1, R[i].d_st + l, J.abs_floor, J.tau, 1e-6});
+            s2.push_back(DfJob{M.Hp, M.k, M.Hp, (int64_t)M.k + 1, M.F2, 0, R[i].d_st + l, J.abs_floor, J.tau, 1e-10});
+        }
+    auto err = [&](cudaError_t e, const char* what) {
+        return fail(c0, e == cudaErrorMemoryAllocation ? LS_ERR_OOM : LS_ERR_CUDA, "rhosvd_reduce: %s: %s", what,
+                    cudaGetErrorString(e));
+    };
+    // per context, the df modes in one grouped launch
+    auto per_ctx = [&](auto&& fn) -> cudaError_t {
+        for (int i = 0; i < n; ++i) {
+            int nm = 0;
+            RedMode* ms[3];
+            for (int l = 0; l < 3; ++l)
+                if (R[i].m[l].df) ms[nm++] = &R[i].m[l];
+            if (nm == 0) continue;
+            cudaError_t e = fn(R[i], ms, nm);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    cudaError_t e;
+    if (!grid.empty()) {
+        e = launch_jacobi_multi(grid.data(), (int)grid.size(), 60, 1e-14, c0->num_sms, s0);
+        if (e != cudaSuccess) return err(e, "Jacobi launch");
+    }
+    if (s1.empty()) return LS_OK;
+    // the block form where every matrix fits it, else the scalar shared-memory form
+    int kmax = 0;
+    for (const DfJob& J : s1) kmax = std::max(kmax, J.k);
+    auto run_df = kmax <= jacobi_blk_max_k() ? launch_jacobi_blk : launch_jacobi_df;
+    {
+        Scope sc("jacobi.run1", s0);
+        if ((e = run_df(s1.data(), (int)s1.size(), 60, s0)) != cudaSuccess) return err(e, "Jacobi (first run)");
+    }
+    {
+        Scope sc_o("jacobi.ortho", s0);
+        e = per_ctx([&](RedState& Rs, RedMode** ms, int nm) {
+            const double *U0[3], *Sc[3], *H[3], *Tc[3], *Uc[3];
+            double *S[3], *D2[3], *T[3], *Uo[3], *T1[3], *Hp[3];
+            int ks[3];
+            for (int j = 0; j < nm; ++j) {
+                RedMode& M = *ms[j];
+                U0[j] = M.U0; S[j] = M.S; Sc[j] = M.S; D2[j] = M.SLi; T[j] = M.T1; Tc[j] = M.T1;
+                Uo[j] = M.Uo; Uc[j] = M.Uo; H[j] = M.H; T1[j] = M.T1; Hp[j] = M.Hp; ks[j] = M.k;
+            }
+            cudaError_t e2 = launch_atb_sym_n(nm, U0, U0, ks, S, Rs.gw, s0);             // S = U0^T U0
+            if (e2 == cudaSuccess) e2 = launch_lowdin_n(nm, Sc, ks, D2, T, Rs.gw, s0);    // T = S^{-1/2}
+            if (e2 == cudaSuccess) e2 = launch_ab_n(nm, U0, Tc, ks, Uo, Rs.gw, s0);       // Uo = U0 T
+            if (e2 == cudaSuccess) e2 = launch_ab_n(nm, H, Uc, ks, T1, Rs.gw, s0);        // T1 = H Uo
+            if (e2 == cudaSuccess) e2 = launch_atb_sym_n(nm, Uc, T1, ks, Hp, Rs.gw, s0);  // H' = Uo^T T1
+            return e2;
+        });
+        if (e != cudaSuccess) return err(e, "re-projection");
+    }
+    {
+        Scope sc("jacobi.run2", s0);
+        if ((e = run_df(s2.data(), (int)s2.size(), 60, s0)) != cudaSuccess) return err(e, "Jacobi (second run)");
+    }
+    e = per_ctx([&](RedState& Rs, RedMode** ms, int nm) {
+        const double *A[3], *B[3];
+        double* out[3];
+        int ks[3];
+        for (int j = 0; j < nm; ++j) { A[j] = ms[j]->Uo; B[j] = ms[j]->F2; out[j] = ms[j]->V; ks[j] = ms[j]->k; }
+        return launch_ab_plus_n(nm, A, B, A, ks, out, Rs.gw, s0);           // V = Uo + Uo F2
+    });
+    if (e != cudaSuccess) return err(e, "eigenvectors");
+    for (int i = 0; i < n; ++i)
+        for (int l = 0; l < 3; ++l) {
+            RedMode& M = R[i].m[l];
+            if (M.df) std::swap(M.H, M.Hp);   // eigenvalues on the diagonal of H'
+        }
+    return LS_OK;
+}
+
 // The reduction of n contexts: per-context phases on each context's stream;
 // the cooperative steps (pivoted Cholesky, Jacobi iteration, the two Cholesky
 // factorisations of CholeskyQR2) of all 3n modes as one launch each on the
@@ -850,12 +962,17 @@ int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, l
                 return fail(ctxs[i], LS_ERR_CUDA, "rhosvd_reduce: sync failed");
         return LS_OK;
     };
+    // first CholeskyQR pass: FP32 shared-memory factorisation where r fits, FP64 grid otherwise
     auto chol_all = [&]() -> int {
         for (int i = 0; i < n; ++i)
             if (int rc = gather(ctxs[i])) return rc;
         {
             Scope sc("cholqr2", s0);
-            cudaError_t e = launch_chol_inv_multi(cj.data(), 3 * n, c0->num_sms, s0);
+            const int rmax = chol32_max_r();
+            std::vector<CholJob> small, large;
+            for (const CholJob& J : cj) (J.r <= rmax ? small : large).push_back(J);
+            cudaError_t e = launch_chol32_multi(small.data(), (int)small.size(), s0);
+            if (e == cudaSuccess) e = launch_chol_inv_multi(large.data(), (int)large.size(), c0->num_sms, s0);
             if (e != cudaSuccess) return fail(c0, LS_ERR_CUDA, "rhosvd_reduce: Cholesky launch: %s", cudaGetErrorString(e));
         }
         for (int i = 0; i < n; ++i)
@@ -887,8 +1004,7 @@ int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, l
     }
     {
         Scope sc("jacobi", s0);
-        cudaError_t e = launch_jacobi_multi(jj.data(), 3 * n, 60, 1e-14, c0->num_sms, s0);
-        if (e != cudaSuccess) return fail(c0, LS_ERR_CUDA, "rhosvd_reduce: Jacobi launch: %s", cudaGetErrorString(e));
+        if (int rc = eigen_all(R, ctxs, n, jj, s0)) return rc;
     }
     for (int i = 0; i < n; ++i) {
         if (int rc = scatter(ctxs[i])) return rc;
@@ -900,7 +1016,6 @@ int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, l
     if (int rc = chol_all()) return rc;
     for (int i = 0; i < n; ++i)
         if (int rc = red_cholqr_mid(R[i])) return rc;
-    if (int rc = chol_all()) return rc;
     int first_err = LS_OK;
     for (int i = 0; i < n; ++i) {
         int rc = red_finish(R[i], infos ? &infos[i] : nullptr);

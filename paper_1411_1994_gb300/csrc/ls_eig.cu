@@ -1,0 +1,854 @@
+// Symmetric eigen-solver of the truncation step (Thm 2.1 / Algorithm 1 take
+// the SVD of each side matrix; here the eigen-decomposition of its k x k
+// Gram matrix H = L^T L after the pivoted Cholesky compression):
+// cyclic two-sided Jacobi held in shared memory by one thread-block cluster
+// per matrix.
+//
+// Representation: the diagonal D of the rotated matrix in FP64, its strict
+// upper triangle E in FP32 (packed), and the accumulated rotation as I + F
+// with F in FP32. Every stored entry carries its own relative rounding, so
+// the iteration keeps the relative accuracy that Jacobi has on graded
+// positive definite matrices; run a second time on the nearly diagonal
+// U^T H U (U from the first run, orthonormalised and re-projected in FP64),
+// the angles are small, E and F are small, and the FP32 rounding of E and F
+// is small in absolute terms: the second run reaches off-diagonal ratios of
+// 1e-10 without any FP64 sweep.
+//
+// Cluster layout: CTA 0 holds D and E, computes the angles of each round,
+// updates D and E, and writes the angles into the shared memory of CTAs
+// 1..nF, which hold contiguous row blocks of F and update them. One cluster
+// barrier per round (angles double-buffered by round parity). A round-robin
+// ordering pairs all indices once per sweep. Before each sweep CTA 0 scans
+// every pair; the iteration stops when no pair qualifies for a rotation, or
+// raises FLAG_NOCONVERGE after max_sweeps.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "ls_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ls {
+
+namespace {
+
+constexpr int kEigThreads = 1024;
+
+struct DfMode {
+    const double* H; double* outD; double* outF; DevStatus* st;
+    int64_t ldd; int k; int add_identity; double abs_floor; double tau; double tol;
+};
+struct DfArgs {
+    const DfMode* m; int max_sweeps; int cs; int rows_per;
+};
+
+__device__ __forceinline__ void rr_pair_e(int t, int i, int Cp, int& p, int& q) {
+    const int n1 = Cp - 1;
+    int a, b;
+    if (i == 0) { a = n1; b = t; }
+    else { a = (t + i) % n1; b = (t - i + n1) % n1; }
+    p = min(a, b);
+    q = max(a, b);
+}
+
+// The diagonal is kept as an unevaluated sum hi + lo of two FP32 numbers
+// (about 48 significant bits) and updated with error-free FP32 additions
+// (Knuth's TwoSum, then a renormalising Fast2Sum): no FP64 instruction in
+// the iteration itself, whose few FP64 lanes per SM would serialise it.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_from(double d) {
+    const float h = (float)d;
+    return DF{h, (float)(d - (double)h)};
+}
+__device__ __forceinline__ double df_to(DF x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ DF df_add(DF x, float y) {
+    const float s = __fadd_rn(x.hi, y);
+    const float bb = __fsub_rn(s, x.hi);
+    const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y, bb));
+    const float lo = __fadd_rn(x.lo, e);
+    const float h2 = __fadd_rn(s, lo);
+    return DF{h2, __fsub_rn(lo, __fsub_rn(h2, s))};
+}
+// a - b rounded to FP32
+__device__ __forceinline__ float df_diff(DF a, DF b) { return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo)); }
+
+// The rotation of a pair from (d_p, d_q, e_pq): the tangent t only steers
+// (an inexact t leaves a residue of that relative size in e_pq, as FP32
+// rounding does), so it is taken with the hardware approximations; c is then
+// made consistent with t, c = (1 + t^2)^(-1/2) with one Newton step on the
+// approximate rsqrt, and s = t c, so that c^2 + s^2 = 1 to an ulp or two.
+// c - 1 = -t^2 c / (1 + 1/c) is kept apart for the accumulated rotations.
+__device__ __forceinline__ float rcp_a(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_a(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_a(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+struct RotCS {
+    float t, c, s, cm1;
+};
+__device__ __forceinline__ RotCS jacobi_rot(float dq_minus_dp, float epq) {
+    const float theta = dq_minus_dp * rcp_a(2.f * epq);
+    const float t = copysignf(rcp_a(fabsf(theta) + sqrt_a(fmaf(theta, theta, 1.f))), theta);
+    const float x = fmaf(t, t, 1.f);
+    float c = rsqrt_a(x);
+    c = c * fmaf(-0.5f * x, c * c, 1.5f);
+    return RotCS{t, c, t * c, -(t * t) * c * rcp_a(fmaf(x, c, 1.f))};
+}
+
+// rotation criterion (a decision only, so taken in FP32; the sweep-start scan
+// and the angle phase use this one function and therefore agree)
+struct Crit {
+    float floor, tau, tol2;
+    __device__ __forceinline__ bool operator()(DF app, DF aqq, float apq) const {
+        const float a = app.hi, b = aqq.hi;
+        return fabsf(apq) > floor && fmaxf(a, b) >= tau && apq * apq > tol2 * fabsf(a * b);
+    }
+};
+
+// one rotation of a round: J = [[c, s], [-s, c]] on (p, q), c - 1 kept apart,
+// with the packed-row offsets of p and q (CTA 0's E)
+struct __align__(16) Rot {
+    float cm1, s;
+    int p, q;
+    float c;
+    int rbp, rbq, pad;
+};
+
+// shared memory: Rot[2][P] and two control words, then the CTA's own part
+__host__ __device__ __forceinline__ size_t df_common(int k) {
+    const int P = (k + (k & 1)) / 2;
+    return ((size_t)2 * P * sizeof(Rot) + 4 * sizeof(int) + 15) & ~(size_t)15;
+}
+// CTA 0: D (k doubles), row offsets (k ints, padded to even), E (k(k-1)/2 floats)
+__host__ __device__ __forceinline__ size_t df_e_bytes(int k) {
+    return df_common(k) + 8 * (size_t)k + 4 * (size_t)(k + (k & 1)) + 4 * (size_t)k * (k - 1) / 2;
+}
+
+__global__ void __launch_bounds__(kEigThreads) k_jacobi_df(DfArgs A) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int job = blockIdx.x / A.cs;
+    const DfMode J = A.m[job];
+    const int k = J.k, Cp = k + (k & 1), P = Cp / 2, n1 = Cp - 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    Rot* rot = reinterpret_cast<Rot*>(smem);                      // [2][P]
+    int* ctl = reinterpret_cast<int*>(rot + 2 * P);               // [2]: 1 = stop
+    unsigned char* rest = smem + df_common(k);
+    __shared__ unsigned int s_active;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    const Crit qualifies{(float)J.abs_floor, (float)J.tau, (float)(J.tol * J.tol)};
+
+    // CTA 0: D (FP64), row offsets of the packed strict upper triangle, E
+    DF* D = reinterpret_cast<DF*>(rest);
+    int* rb = reinterpret_cast<int*>(D + k);                      // E(a, b) = E[rb[a] + b], a < b
+    float* E = reinterpret_cast<float*>(rb + k + (k & 1));
+    // CTAs >= 1: rows [j0, j1) of F
+    float* F = reinterpret_cast<float*>(rest);
+    const int j0 = rank >= 1 ? min(k, (rank - 1) * A.rows_per) : 0;
+    const int j1 = rank >= 1 ? min(k, j0 + A.rows_per) : 0;
+
+    int base = 0;
+    if (rank == 0) {
+        for (int a = tid; a < k; a += nthr) {
+            D[a] = df_from(J.H[(int64_t)a * k + a]);
+            rb[a] = a * (2 * k - a - 1) / 2 - a - 1;
+        }
+        __syncthreads();
+        for (int a = warp; a < k; a += nw)
+            for (int b = a + 1 + lane; b < k; b += 32) E[rb[a] + b] = (float)J.H[(int64_t)a * k + b];
+        if (tid == 0) s_active = 0;
+        base = J.st->sweeps;   // a second run continues the sweep record of the first
+    } else {
+        for (int e = tid; e < (j1 - j0) * k; e += nthr) F[e] = 0.f;
+    }
+    cl.sync();
+
+    int sweep = 0;
+    bool done = false;
+    int gr = 0;   // rounds so far, over all sweeps: the parity of the rotation buffers
+    for (; sweep <= A.max_sweeps && !done; ++sweep) {
+        for (int t = 0; t < n1; ++t, ++gr) {
+            const int par = gr & 1;
+            Rot* R = rot + par * P;
+            if (rank == 0) {
+                int stop = 0;
+                if (t == 0) {
+                    // does any pair still qualify?
+                    int need = 0;
+                    for (int a = warp; a < k && !need; a += nw)
+                        for (int b = a + 1 + lane; b < k; b += 32)
+                            if (qualifies(D[a], D[b], E[rb[a] + b])) { need = 1; break; }
+                    need = __syncthreads_or(need);
+                    if (tid == 0) {
+                        if (sweep > 0) J.st->sweep_active[(base + sweep - 1) & 63] = s_active;
+                        s_active = 0;
+                    }
+                    if (!need) stop = 1;
+                    else if (sweep == A.max_sweeps) {
+                        stop = 1;
+                        if (tid == 0) atomicCAS(&J.st->flag, FLAG_OK, FLAG_NOCONVERGE);
+                    }
+                    __syncthreads();
+                }
+                if (!stop) {
+                    for (int i = tid; i < P; i += nthr) {
+                        Rot r{0.f, 0.f, 0, 0, 1.f, 0, 0, 0};
+                        rr_pair_e(t, i, Cp, r.p, r.q);
+                        r.rbp = rb[r.p];
+                        r.rbq = r.q < k ? rb[r.q] : 0;
+                        if (r.q < k) {
+                            const int ix = rb[r.p] + r.q;
+                            const float epq = E[ix];
+                            if (qualifies(D[r.p], D[r.q], epq)) {
+                                const RotCS g = jacobi_rot(df_diff(D[r.q], D[r.p]), epq);
+                                r.cm1 = g.cm1;
+                                r.s = g.s;
+                                r.c = g.c;
+                                const float te = g.t * epq;
+                                D[r.p] = df_add(D[r.p], -te);
+                                D[r.q] = df_add(D[r.q], te);
+                                E[ix] = 0.f;
+                                atomicAdd(&s_active, 1u);
+                            }
+                        }
+                        R[i] = r;
+                        for (int c = 1; c < A.cs; ++c) cl.map_shared_rank(R, c)[i] = r;
+                    }
+                }
+                if (tid == 0)
+                    for (int c = 0; c < A.cs; ++c) cl.map_shared_rank(ctl, c)[par] = stop;
+            }
+            cl.sync();
+            if (ctl[par]) { done = true; break; }
+            if (rank == 0) {
+                // E <- J^T E J on every block of two pairs (i < i2). Row c of the block triangle
+                // (P - 1 - c blocks) is folded with row P - 2 - c (c + 1 blocks) into P blocks, so
+                // the P(P-1)/2 blocks are dealt out evenly by a linear index.
+                const int nbl = (P / 2) * P;
+                const float invP = 1.f / (float)P;
+                for (int bl = tid; bl < nbl; bl += nthr) {
+                    int c = (int)((float)bl * invP);
+                    int off = bl - c * P;
+                    if (off >= P) { ++c; off -= P; }
+                    else if (off < 0) { --c; off += P; }
+                    int i, i2;
+                    if (off < P - 1 - c) { i = c; i2 = c + 1 + off; }
+                    else { i = P - 2 - c; i2 = off; if (i <= c) continue; }
+                    const Rot a = R[i], b = R[i2];
+                    if (a.s == 0.f && b.s == 0.f) continue;
+                    const bool vq = a.q < k, vq2 = b.q < k;
+                    // packed position of the symmetric entry (x, y): row offset of the smaller index
+                    const int i0 = a.p < b.p ? a.rbp + b.p : b.rbp + a.p;
+                    const int i1 = vq2 ? (a.p < b.q ? a.rbp + b.q : b.rbq + a.p) : 0;
+                    const int ia = vq ? (a.q < b.p ? a.rbq + b.p : b.rbp + a.q) : 0;
+                    const int ib = (vq && vq2) ? (a.q < b.q ? a.rbq + b.q : b.rbq + a.q) : 0;
+                    const float x0 = E[i0], x1 = vq2 ? E[i1] : 0.f, x2 = vq ? E[ia] : 0.f,
+                                x3 = (vq && vq2) ? E[ib] : 0.f;
+                    const float ypp = a.c * x0 - a.s * x2, ypq = a.c * x1 - a.s * x3;
+                    const float yqp = a.s * x0 + a.c * x2, yqq = a.s * x1 + a.c * x3;
+                    E[i0] = b.c * ypp - b.s * ypq;
+                    if (vq2) E[i1] = b.s * ypp + b.c * ypq;
+                    if (vq) E[ia] = b.c * yqp - b.s * yqq;
+                    if (vq && vq2) E[ib] = b.s * yqp + b.c * yqq;
+                }
+                __syncthreads();
+            } else {
+                // (I + F) <- (I + F) J on this CTA's rows: a warp per row, lanes over the pairs
+                const int nr = j1 - j0;
+                for (int jl = warp; jl < nr; jl += nw) {
+                    const int j = j0 + jl;
+                    float* row = F + (int64_t)jl * k;
+                    for (int i = lane; i < P; i += 32) {
+                        const Rot a = R[i];
+                        if (a.s == 0.f || a.q >= k) continue;
+                        const float fp = row[a.p], fq = row[a.q];
+                        float np = fp + (fp * a.cm1 - fq * a.s);
+                        float nq = fq + (fp * a.s + fq * a.cm1);
+                        if (j == a.p) { np += a.cm1; nq += a.s; }
+                        if (j == a.q) { np -= a.s; nq += a.cm1; }
+                        row[a.p] = np;
+                        row[a.q] = nq;
+                    }
+                }
+            }
+        }
+    }
+    // outputs
+    if (rank == 0) {
+        for (int a = tid; a < k; a += nthr) J.outD[(int64_t)a * J.ldd] = df_to(D[a]);
+        if (tid == 0) J.st->sweeps = base + sweep - 1;
+    } else {
+        for (int e = tid; e < (j1 - j0) * k; e += nthr) {
+            const int jl = e / k, n = e - jl * k;
+            const int j = j0 + jl;
+            J.outF[(int64_t)j * k + n] = (double)F[e] + ((J.add_identity && j == n) ? 1.0 : 0.0);
+        }
+    }
+    cl.sync();
+}
+
+// dynamic shared memory available to the kernel (its static variables take a few bytes)
+int smem_optin() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    return std::max(0, v - 1024);
+}
+
+// ---------------------------------------------------------------------------
+// Block form of the same iteration: indices in blocks of BJ = 8, a round-robin
+// over the m blocks pairs them into m/2 pair-blocks of 16 indices per round
+// (m - 1 rounds a sweep). Each pair-block's 16 x 16 subproblem receives one
+// inner cyclic sweep (a warp, in place in E; the diagonal D in FP64), whose
+// rotations accumulate into Q = I + F_Q; then every off-diagonal tile of
+// pair-blocks is rotated as E_AB <- Q_A^T E_AB Q_B (a warp per tile, dense
+// FP32), and F <- F + F_Q + F F_Q on the F rows. In the first round of a
+// sweep the inner sweeps rotate every index pair of each pair-block (so every
+// pair within a block); in the other rounds only the pairs across the two
+// blocks (8 inner rounds). A sweep thus rotates every pair at least once, and
+// a round is dense arithmetic instead of one synchronisation per rotation.
+// E is held in full (symmetric) storage; K = m * BJ <= jacobi_blk_max_k().
+// ---------------------------------------------------------------------------
+constexpr int BJ = 8, BJ2 = 16, BJ2SQ = 256;
+// padded strides: E rows K + 4 (16-byte aligned rows, column walks over 8 banks), 16 x 16
+// scratch rows 17 (row-wise walks conflict-free)
+constexpr int SP = BJ2 + 1, SPSQ = BJ2 * SP;
+
+struct BjArgs {
+    const DfMode* m; int max_sweeps; int cs; int rows_per;
+};
+
+// block (of size BJ) of position u (0..15) in pair-block (I, J)
+__device__ __forceinline__ int bj_index(int I, int J, int u) { return u < BJ ? I * BJ + u : J * BJ + (u - BJ); }
+
+// shared-memory layout: offsets in bytes
+struct BjLayout {
+    int K, ldE, nb;
+    size_t ctl, D, E, Q, Tw, aw, pb, tiles, qrem, F;   // E-CTA: ctl D E Q Tw aw pb tiles; F-CTAs: ctl qrem F
+    size_t e_bytes, f_bytes;
+    __host__ __device__ BjLayout(int k, int rows_per) {
+        int m = (k + BJ - 1) / BJ;
+        m += m & 1;
+        K = m * BJ;
+        ldE = K + 4;
+        nb = m / 2;
+        ctl = 0;
+        D = 16;
+        E = D + 8 * (size_t)K;
+        Q = E + 4 * (size_t)K * ldE;
+        Tw = Q + 4 * (size_t)nb * BJ2SQ;
+        aw = Tw + 4 * (size_t)nb * SPSQ;
+        pb = aw + 16 * (size_t)nb * BJ2;
+        tiles = pb + 4 * (size_t)nb;
+        e_bytes = tiles + 4 * (size_t)nb * nb;
+        qrem = 16;
+        F = qrem + 4 * (size_t)2 * nb * BJ2SQ;
+        f_bytes = F + 4 * (size_t)rows_per * K;
+    }
+};
+
+struct __align__(16) InRot {
+    float c, s, cm1;
+    int uv;   // u | v << 8 (positions 0..15 in the pair-block), bit 16: active
+};
+
+__global__ void __launch_bounds__(kEigThreads) k_jacobi_blk(BjArgs A) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int job = blockIdx.x / A.cs;
+    const DfMode J = A.m[job];
+    const int k = J.k;
+    const BjLayout Ly(k, A.rows_per);
+    const int K = Ly.K, ldE = Ly.ldE, nb = Ly.nb, m = 2 * nb;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* ctl = reinterpret_cast<int*>(smem + Ly.ctl);
+    DF* D = reinterpret_cast<DF*>(smem + Ly.D);
+    float* E = reinterpret_cast<float*>(smem + Ly.E);
+    float* Q = reinterpret_cast<float*>(smem + Ly.Q);
+    float* Tw = reinterpret_cast<float*>(smem + Ly.Tw);
+    InRot* aw = reinterpret_cast<InRot*>(smem + Ly.aw);
+    int* pb = reinterpret_cast<int*>(smem + Ly.pb);          // this round's pair-blocks: I | J << 16
+    int* tiles = reinterpret_cast<int*>(smem + Ly.tiles);    // off-diagonal tiles a | b << 8, a < b
+    float* qrem = reinterpret_cast<float*>(smem + Ly.qrem);
+    float* F = reinterpret_cast<float*>(smem + Ly.F);
+    __shared__ unsigned int s_active;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    const Crit qualifies{(float)J.abs_floor, (float)J.tau, (float)(J.tol * J.tol)};
+    const int j0 = rank >= 1 ? min(K, (rank - 1) * A.rows_per) : 0;
+    const int j1 = rank >= 1 ? min(K, j0 + A.rows_per) : 0;
+    const int ntile = nb * (nb - 1) / 2;
+
+    int base = 0;
+    if (rank == 0) {
+        for (int a = tid; a < K; a += nthr) D[a] = df_from(a < k ? J.H[(int64_t)a * k + a] : 0.0);
+        for (int a = warp; a < K; a += nw)
+            for (int c = lane; c < K; c += 32)
+                E[a * ldE + c] = (a < k && c < k && a != c) ? (float)J.H[(int64_t)a * k + c] : 0.f;
+        if (tid == 0) {
+            s_active = 0;
+            int n = 0;
+            for (int a = 0; a < nb; ++a)
+                for (int b = a + 1; b < nb; ++b) tiles[n++] = a | (b << 8);
+        }
+        base = J.st->sweeps;
+    } else {
+        for (int e = tid; e < (j1 - j0) * K; e += nthr) F[e] = 0.f;
+    }
+    cl.sync();
+
+    int sweep = 0;
+    bool done = false;
+    int gr = 0;
+    for (; sweep <= A.max_sweeps && !done; ++sweep) {
+        for (int t = 0; t < m - 1; ++t, ++gr) {
+            const int par = gr & 1;
+            if (rank == 0) {
+                int stop = 0;
+                if (t == 0) {
+                    int need = 0;
+                    for (int a = warp; a < k && !need; a += nw)
+                        for (int c = a + 1 + lane; c < k; c += 32)
+                            if (qualifies(D[a], D[c], E[a * ldE + c])) { need = 1; break; }
+                    need = __syncthreads_or(need);
+                    if (tid == 0) {
+                        if (sweep > 0) J.st->sweep_active[(base + sweep - 1) & 63] = s_active;
+                        s_active = 0;
+                    }
+                    if (!need) stop = 1;
+                    else if (sweep == A.max_sweeps) {
+                        stop = 1;
+                        if (tid == 0) atomicCAS(&J.st->flag, FLAG_OK, FLAG_NOCONVERGE);
+                    }
+                    __syncthreads();
+                }
+                if (!stop) {
+                    // the inner sweeps of all pair-blocks in lockstep: per inner round, one thread per
+                    // rotation (8 a pair-block) computes the angles, then all threads rotate the 2 x 2
+                    // blocks of E (56 a pair-block) and accumulate F_Q (128 items a pair-block)
+                    const int nrot = nb * (BJ2 / 2);
+                    for (int e = tid; e < nb * SPSQ; e += nthr) Tw[e] = 0.f;
+                    if (tid < nb) {
+                        int I, Jb;
+                        rr_pair_e(t, tid, m, I, Jb);
+                        pb[tid] = I | (Jb << 16);
+                    }
+                    unsigned int cnt = 0;
+                    __syncthreads();
+                    // the first round of a sweep gives each pair-block a full inner sweep (every pair
+                    // within its two blocks); the other rounds only pair the two blocks' indices with
+                    // each other (8 inner rounds), as every block's own pairs were rotated this sweep
+                    const int n_inner = t == 0 ? BJ2 - 1 : BJ;
+                    for (int it = 0; it < n_inner; ++it) {
+                        InRot* ri = aw + (it & 1) * nrot;
+                        if (tid < nrot) {
+                            const int sub = tid >> 3, l = tid & 7;
+                            const int I = pb[sub] & 0xffff, Jb = pb[sub] >> 16;
+                            int u, v;
+                            if (t == 0) rr_pair_e(it, l, BJ2, u, v);
+                            else { u = l; v = BJ + ((l + it) & (BJ - 1)); }
+                            const int p = bj_index(I, Jb, u), q = bj_index(I, Jb, v);
+                            InRot r{1.f, 0.f, 0.f, u | (v << 8)};
+                            if (p < k && q < k) {
+                                const float epq = E[p * ldE + q];
+                                if (qualifies(D[p], D[q], epq)) {
+                                    const RotCS g = jacobi_rot(df_diff(D[q], D[p]), epq);
+                                    r = InRot{g.c, g.s, g.cm1, u | (v << 8) | (1 << 16)};
+                                    const float te = g.t * epq;
+                                    D[p] = df_add(D[p], -te);
+                                    D[q] = df_add(D[q], te);
+                                    E[p * ldE + q] = 0.f;
+                                    E[q * ldE + p] = 0.f;
+                                    ++cnt;
+                                }
+                            }
+                            ri[tid] = r;
+                        }
+                        __syncthreads();
+                        // E <- J^T E J on the 2 x 2 blocks (i, i2), i != i2, of every pair-block
+                        for (int e = tid; e < nb * 64; e += nthr) {
+                            const int sub = e >> 6, i = (e >> 3) & 7, i2 = e & 7;
+                            if (i == i2) continue;
+                            const InRot a = ri[sub * 8 + i], b = ri[sub * 8 + i2];
+                            if (!((a.uv | b.uv) & (1 << 16))) continue;
+                            const int I = pb[sub] & 0xffff, Jb = pb[sub] >> 16;
+                            const int pa = bj_index(I, Jb, a.uv & 255), qa = bj_index(I, Jb, (a.uv >> 8) & 255);
+                            const int pc = bj_index(I, Jb, b.uv & 255), qc = bj_index(I, Jb, (b.uv >> 8) & 255);
+                            const float x0 = E[pa * ldE + pc], x1 = E[pa * ldE + qc];
+                            const float x2 = E[qa * ldE + pc], x3 = E[qa * ldE + qc];
+                            const float ypp = a.c * x0 - a.s * x2, ypq = a.c * x1 - a.s * x3;
+                            const float yqp = a.s * x0 + a.c * x2, yqq = a.s * x1 + a.c * x3;
+                            E[pa * ldE + pc] = b.c * ypp - b.s * ypq;
+                            E[pa * ldE + qc] = b.s * ypp + b.c * ypq;
+                            E[qa * ldE + pc] = b.c * yqp - b.s * yqq;
+                            E[qa * ldE + qc] = b.s * yqp + b.c * yqq;
+                        }
+                        // F_Q <- F_Q J on local positions of every pair-block, c - 1 kept apart
+                        for (int e = tid; e < nb * 8 * BJ2; e += nthr) {
+                            const int sub = e >> 7;
+                            const InRot r = ri[sub * 8 + ((e >> 4) & 7)];
+                            if (!(r.uv & (1 << 16))) continue;
+                            float* fq = Tw + sub * SPSQ;
+                            const int y = e & 15, u = r.uv & 255, v = (r.uv >> 8) & 255;
+                            const float fp = fq[y * SP + u], fv = fq[y * SP + v];
+                            float np = fp + (fp * r.cm1 - fv * r.s);
+                            float nv = fv + (fp * r.s + fv * r.cm1);
+                            if (y == u) { np += r.cm1; nv += r.s; }
+                            if (y == v) { np -= r.s; nv += r.cm1; }
+                            fq[y * SP + u] = np;
+                            fq[y * SP + v] = nv;
+                        }
+                        __syncthreads();
+                    }
+                    if (cnt) atomicAdd(&s_active, cnt);
+                    // F_Q to the F rows' CTAs; Q = I + F_Q kept for the tiles
+                    for (int e = tid; e < nb * BJ2SQ; e += nthr) {
+                        const int sub = e >> 8, f0 = e & 255;
+                        const float f = Tw[sub * SPSQ + (f0 >> 4) * SP + (f0 & 15)];
+                        for (int c = 1; c < A.cs; ++c) cl.map_shared_rank(qrem, c)[par * nb * BJ2SQ + e] = f;
+                        Q[e] = f + (((f0 >> 4) == (f0 & 15)) ? 1.f : 0.f);
+                    }
+                }
+                if (tid == 0)
+                    for (int c = 0; c < A.cs; ++c) cl.map_shared_rank(ctl, c)[par] = stop;
+            }
+            cl.sync();
+            if (ctl[par]) { done = true; break; }
+            if (rank == 0) {
+                // off-diagonal tiles (a < b): E_ab <- Q_a^T E_ab Q_b, two tiles per warp (a half-warp
+                // each); lane: rows r0, r0 + 8 of the tile, columns c0..c0+7 (one block of the
+                // column pair-block). The product with Q_b takes the partner lane's half of the
+                // intermediate rows by shuffle.
+                const int h = lane >> 4, l16 = lane & 15;
+                const int r0 = l16 >> 1, c0 = (l16 & 1) * BJ;
+                for (int task0 = 2 * warp; task0 < ntile; task0 += 2 * nw) {
+                    const int task = task0 + h;
+                    const bool live = task < ntile;
+                    const int ab = live ? tiles[task] : tiles[task0];
+                    const int a = ab & 255, b = ab >> 8;
+                    const int Ia = pb[a] & 0xffff, Ja = pb[a] >> 16, Ib = pb[b] & 0xffff, Jb2 = pb[b] >> 16;
+                    const float* Qa = Q + a * BJ2SQ;
+                    const float* Qb = Q + b * BJ2SQ;
+                    const int colb = c0 ? Jb2 * BJ : Ib * BJ;   // first E column of this lane's 8
+                    float t0[BJ], t1[BJ];
+#pragma unroll
+                    for (int c = 0; c < BJ; ++c) { t0[c] = 0.f; t1[c] = 0.f; }
+#pragma unroll
+                    for (int j = 0; j < BJ2; ++j) {
+                        const float qa0 = Qa[j * BJ2 + r0], qa1 = Qa[j * BJ2 + r0 + BJ];
+                        const float* xr = E + bj_index(Ia, Ja, j) * ldE + colb;
+                        const float4 x0 = *reinterpret_cast<const float4*>(xr);
+                        const float4 x1 = *reinterpret_cast<const float4*>(xr + 4);
+                        const float xv[BJ] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                        for (int c = 0; c < BJ; ++c) {
+                            t0[c] = fmaf(qa0, xv[c], t0[c]);
+                            t1[c] = fmaf(qa1, xv[c], t1[c]);
+                        }
+                    }
+                    // Z[r][c0 + c] = sum_j T[r][j] Qb[j][c0 + c], one row at a time; T[r][j] for j in
+                    // this lane's block from t, for the other block from the partner lane (lane ^ 1)
+                    const int cp = c0 ^ BJ;
+                    const int row0 = bj_index(Ia, Ja, r0), row1 = bj_index(Ia, Ja, r0 + BJ);
+#pragma unroll
+                    for (int half_row = 0; half_row < 2; ++half_row) {
+                        float z[BJ];
+#pragma unroll
+                        for (int c = 0; c < BJ; ++c) z[c] = 0.f;
+#pragma unroll
+                        for (int jj = 0; jj < BJ; ++jj) {
+                            const float tv = half_row ? t1[jj] : t0[jj];
+                            const float ov = __shfl_xor_sync(0xffffffffu, tv, 1);
+                            const float4 qs0 = *reinterpret_cast<const float4*>(Qb + (c0 + jj) * BJ2 + c0);
+                            const float4 qs1 = *reinterpret_cast<const float4*>(Qb + (c0 + jj) * BJ2 + c0 + 4);
+                            const float4 qo0 = *reinterpret_cast<const float4*>(Qb + (cp + jj) * BJ2 + c0);
+                            const float4 qo1 = *reinterpret_cast<const float4*>(Qb + (cp + jj) * BJ2 + c0 + 4);
+                            z[0] = fmaf(tv, qs0.x, fmaf(ov, qo0.x, z[0]));
+                            z[1] = fmaf(tv, qs0.y, fmaf(ov, qo0.y, z[1]));
+                            z[2] = fmaf(tv, qs0.z, fmaf(ov, qo0.z, z[2]));
+                            z[3] = fmaf(tv, qs0.w, fmaf(ov, qo0.w, z[3]));
+                            z[4] = fmaf(tv, qs1.x, fmaf(ov, qo1.x, z[4]));
+                            z[5] = fmaf(tv, qs1.y, fmaf(ov, qo1.y, z[5]));
+                            z[6] = fmaf(tv, qs1.z, fmaf(ov, qo1.z, z[6]));
+                            z[7] = fmaf(tv, qs1.w, fmaf(ov, qo1.w, z[7]));
+                        }
+                        // every lane has read this tile's E rows (first product) before any store
+                        __syncwarp();
+                        if (live) {
+                            const int row = half_row ? row1 : row0;
+                            float* w = E + row * ldE + colb;
+                            *reinterpret_cast<float4*>(w) = make_float4(z[0], z[1], z[2], z[3]);
+                            *reinterpret_cast<float4*>(w + 4) = make_float4(z[4], z[5], z[6], z[7]);
+#pragma unroll
+                            for (int c = 0; c < BJ; ++c) E[(colb + c) * ldE + row] = z[c];
+                        }
+                    }
+                    __syncwarp();
+                }
+                __syncthreads();
+            } else {
+                // F <- F + F_Q + F F_Q: a half-warp per pair-block and a group of rows; lane x of
+                // the half holds column x of F_Q in registers
+                const float* fqs = qrem + (size_t)par * nb * BJ2SQ;
+                const int hw = tid >> 4, x = tid & 15, nhw = nthr >> 4;
+                const unsigned int half = 0xffffu << (lane & 16);
+                const int nr = j1 - j0;
+                const int groups = max(1, nhw / nb);
+                if (hw < groups * nb) {
+                    const int a = hw % nb, g = hw / nb;
+                    int Ia, Ja;
+                    rr_pair_e(t, a, m, Ia, Ja);
+                    float fcol[BJ2];
+#pragma unroll
+                    for (int y = 0; y < BJ2; ++y) fcol[y] = fqs[a * BJ2SQ + y * BJ2 + x];
+                    for (int jl = g; jl < nr; jl += groups) {
+                        const int j = j0 + jl;
+                        float* row = F + (size_t)jl * K;
+                        const float4 f0 = *reinterpret_cast<const float4*>(row + Ia * BJ);
+                        const float4 f1 = *reinterpret_cast<const float4*>(row + Ia * BJ + 4);
+                        const float4 f2 = *reinterpret_cast<const float4*>(row + Ja * BJ);
+                        const float4 f3 = *reinterpret_cast<const float4*>(row + Ja * BJ + 4);
+                        const float fv[BJ2] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w,
+                                               f2.x, f2.y, f2.z, f2.w, f3.x, f3.y, f3.z, f3.w};
+                        float acc = fv[x];
+#pragma unroll
+                        for (int y = 0; y < BJ2; ++y) acc = fmaf(fv[y], fcol[y], acc);
+                        // row j of F_Q (embedded) when j is one of the pair-block's indices
+                        const int bj = j / BJ;
+                        if (bj == Ia) acc += fcol[j - Ia * BJ];
+                        else if (bj == Ja) acc += fcol[BJ + j - Ja * BJ];
+                        __syncwarp(half);
+                        row[bj_index(Ia, Ja, x)] = acc;
+                    }
+                }
+            }
+        }
+    }
+    if (rank == 0) {
+        for (int a = tid; a < k; a += nthr) J.outD[(int64_t)a * J.ldd] = df_to(D[a]);
+        if (tid == 0) J.st->sweeps = base + sweep - 1;
+    } else {
+        for (int e = tid; e < (j1 - j0) * K; e += nthr) {
+            const int jl = e / K, n = e - jl * K;
+            const int j = j0 + jl;
+            if (j < k && n < k) J.outF[(int64_t)j * k + n] = (double)F[e] + ((J.add_identity && j == n) ? 1.0 : 0.0);
+        }
+    }
+    cl.sync();
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky and triangular inverse in FP32, one CTA per matrix, held in shared
+// memory: the first, conditioning pass of CholeskyQR (its result need only
+// make the rows well conditioned; the second pass restores FP64 accuracy).
+// Right-looking unblocked factorisation (a warp per trailing row, lanes over
+// its columns), then the in-place inverse column by column from the last:
+// column j of L^{-1} = -(1/l_jj) L^{-1}_{trailing} l_{j+1:, j}.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kEigThreads) k_chol32_multi(const CholJob* jobs) {
+    const CholJob J = jobs[blockIdx.x];
+    const int r = J.r;
+    extern __shared__ __align__(16) float A[];   // r x r, row-major (lower part)
+    float* tmp = A + (size_t)r * r;               // r
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    for (int i = warp; i < r; i += nw)
+        for (int l = lane; l <= i; l += 32) A[i * r + l] = (float)J.A[(int64_t)i * r + l];
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int j = 0; j < r; ++j) {
+        if (tid == 0) {
+            float d = A[j * r + j];
+            if (!(d > 0.f)) { s_bad = 1; d = 1.f; }
+            A[j * r + j] = sqrtf(d);
+        }
+        __syncthreads();
+        const float inv = 1.f / A[j * r + j];
+        for (int i = j + 1 + tid; i < r; i += nthr) A[i * r + j] *= inv;
+        __syncthreads();
+        for (int i = j + 1 + warp; i < r; i += nw) {
+            const float aij = A[i * r + j];
+            for (int l = j + 1 + lane; l <= i; l += 32) A[i * r + l] = fmaf(-aij, A[l * r + j], A[i * r + l]);
+        }
+        __syncthreads();
+    }
+    for (int j = r - 1; j >= 0; --j) {
+        for (int i = j + 1 + tid; i < r; i += nthr) tmp[i] = A[i * r + j];
+        __syncthreads();
+        const float djj = 1.f / A[j * r + j];
+        for (int i = j + 1 + warp; i < r; i += nw) {
+            float acc = 0.f;
+            for (int l = j + 1 + lane; l <= i; l += 32) acc = fmaf(A[i * r + l], tmp[l], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) A[i * r + j] = -djj * acc;
+        }
+        __syncthreads();
+        if (tid == 0) A[j * r + j] = djj;
+        __syncthreads();
+    }
+    for (int i = warp; i < r; i += nw)
+        for (int l = lane; l < r; l += 32) J.Li[(int64_t)i * r + l] = l <= i ? (double)A[i * r + l] : 0.0;
+    if (tid == 0 && s_bad) atomicCAS(&J.st->flag, FLAG_OK, FLAG_NOT_SPD);
+}
+
+}  // namespace
+
+int jacobi_df_max_k() {
+    const int cap = smem_optin();
+    int k = 2;
+    while (k < 4096 && df_e_bytes(k + 1) <= (size_t)cap) ++k;
+    return k;
+}
+
+cudaError_t launch_jacobi_df(const DfJob* jobs, int njobs, int max_sweeps, cudaStream_t st) {
+    if (njobs < 1) return cudaSuccess;
+    const int cap = smem_optin();
+    int kmax = 1;
+    for (int m = 0; m < njobs; ++m) kmax = std::max(kmax, jobs[m].k);
+    const size_t common = df_common(kmax);
+    const size_t e_bytes = df_e_bytes(kmax);
+    if (e_bytes > (size_t)cap) return cudaErrorInvalidValue;
+    // F rows: at least two CTAs (F carries twice the work of E per round), as many as fit
+    const int64_t rows_fit = std::max<int64_t>(1, ((int64_t)cap - (int64_t)common) / (4 * (int64_t)kmax));
+    int nF = std::max<int>(2, (int)((kmax + rows_fit - 1) / rows_fit));
+    if (nF > 7) return cudaErrorInvalidValue;
+    const int rows_per = (kmax + nF - 1) / nF;
+    const size_t f_bytes = common + 4 * (size_t)rows_per * kmax;
+    const size_t smem = std::max(e_bytes, f_bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_jacobi_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    std::vector<DfMode> hm(njobs);
+    for (int m = 0; m < njobs; ++m) {
+        const DfJob& J = jobs[m];
+        hm[m] = DfMode{J.H, J.outD, J.outF, J.st, J.ldd, J.k, J.add_identity, J.abs_floor, J.tau, J.tol};
+    }
+    DfMode* dm = nullptr;
+    e = cudaMallocAsync(&dm, sizeof(DfMode) * njobs, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(dm, hm.data(), sizeof(DfMode) * njobs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        const int cs = 1 + nF;
+        DfArgs a{dm, max_sweeps > 63 ? 63 : max_sweeps, cs, rows_per};
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(njobs * cs));
+        cfg.blockDim = dim3(kEigThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        count_kernels(1);
+        e = cudaLaunchKernelEx(&cfg, k_jacobi_df, a);
+    }
+    cudaFreeAsync(dm, st);
+    return e;
+}
+
+int chol32_max_r() {
+    const int cap = smem_optin();
+    int r = 1;
+    while (4 * ((size_t)(r + 1) * (r + 1) + (r + 1)) <= (size_t)cap) ++r;
+    return r;
+}
+
+cudaError_t launch_chol32_multi(const CholJob* jobs, int njobs, cudaStream_t st) {
+    if (njobs < 1) return cudaSuccess;
+    int rmax = 1;
+    for (int m = 0; m < njobs; ++m) rmax = std::max(rmax, jobs[m].r);
+    if (rmax > chol32_max_r()) return cudaErrorInvalidValue;
+    const size_t smem = 4 * ((size_t)rmax * rmax + rmax);
+    cudaError_t e = cudaFuncSetAttribute(k_chol32_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    CholJob* dj = nullptr;
+    e = cudaMallocAsync(&dj, sizeof(CholJob) * njobs, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(dj, jobs, sizeof(CholJob) * njobs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        k_chol32_multi<<<njobs, kEigThreads, smem, st>>>(dj);
+        count_kernels(1);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(dj, st);
+    return e;
+}
+
+int jacobi_blk_max_k() {
+    const int cap = smem_optin();
+    int k = BJ2;
+    while (k < 4096 && BjLayout(k + BJ2, 1).e_bytes <= (size_t)cap) k += BJ2;
+    return k;
+}
+
+cudaError_t launch_jacobi_blk(const DfJob* jobs, int njobs, int max_sweeps, cudaStream_t st) {
+    if (njobs < 1) return cudaSuccess;
+    const int cap = smem_optin();
+    int kmax = 1;
+    for (int m = 0; m < njobs; ++m) kmax = std::max(kmax, jobs[m].k);
+    const BjLayout L0(kmax, 1);
+    // one thread per rotation of an inner round
+    if (L0.e_bytes > (size_t)cap || L0.nb * (BJ2 / 2) > kEigThreads) return cudaErrorInvalidValue;
+    // F rows over nF CTAs (the F update carries about as much work as the tiles)
+    int nF = 3;
+    int rows_per = (L0.K + nF - 1) / nF;
+    while (BjLayout(kmax, rows_per).f_bytes > (size_t)cap && nF < 7) rows_per = (L0.K + ++nF - 1) / nF;
+    const BjLayout L1(kmax, rows_per);
+    if (L1.f_bytes > (size_t)cap) return cudaErrorInvalidValue;
+    const size_t smem = std::max(L1.e_bytes, L1.f_bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_jacobi_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    std::vector<DfMode> hm(njobs);
+    for (int m = 0; m < njobs; ++m) {
+        const DfJob& J = jobs[m];
+        hm[m] = DfMode{J.H, J.outD, J.outF, J.st, J.ldd, J.k, J.add_identity, J.abs_floor, J.tau, J.tol};
+    }
+    DfMode* dm = nullptr;
+    e = cudaMallocAsync(&dm, sizeof(DfMode) * njobs, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(dm, hm.data(), sizeof(DfMode) * njobs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        const int cs = 1 + nF;
+        BjArgs a{dm, max_sweeps > 63 ? 63 : max_sweeps, cs, rows_per};
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(njobs * cs));
+        cfg.blockDim = dim3(kEigThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        count_kernels(1);
+        e = cudaLaunchKernelEx(&cfg, k_jacobi_blk, a);
+    }
+    cudaFreeAsync(dm, st);
+    return e;
+}
+
+}  // namespace ls

@@ -312,7 +312,7 @@ cudaError_t gemm_group(GGroup<AOp, BOp, COp>& G, const GemmWs& W, cudaStream_t s
     int S = 1;
     if (tiles < target && W.ws && W.ctr) {
         S = (int)std::min<int64_t>(16, target / tiles);
-        S = std::min(S, std::max(1, kmin / (4 * GBK)));
+        S = std::min(S, std::max(1, kmin / GBK));   // down to one k-step per split
         while (S > 1 && (tiles * S * kTileElems > W.ws_cap || tiles > W.ctr_cap)) --S;
     }
     int b = 0, c = 0;
@@ -1264,6 +1264,84 @@ cudaError_t launch_lower_apply_n(int n, const double* const Li[], const int r[],
     for (int i = 0; i < n; ++i)
         g.j[i] = {RowK{Li[i], r[i]}, KRowN{src[i], N}, StoreRow{dst[i], N, 0}, r[i], (int)N, r[i], 0};
     return gemm_group(g, W, st);
+}
+
+struct StoreRowPlus {   // C[m*ld + n] = v + X[m*ld + n]
+    double* p; int64_t ld; const double* x;
+    __device__ void operator()(int, int m, int n, double v) const { p[m * ld + n] = v + x[m * ld + n]; }
+};
+
+// Delta = S - I as an operand
+struct RowKmI {          // X(m, k) = p[m * ld + k] - [m == k]
+    static constexpr bool kfast = true;
+    const double* p; int64_t ld;
+    __device__ double operator()(int, int m, int k) const { return p[m * ld + k] - (m == k ? 1.0 : 0.0); }
+};
+struct KRowNmI {         // X(k, n) = p[k * ld + n] - [k == n]
+    static constexpr bool kfast = false;
+    const double* p; int64_t ld;
+    __device__ double operator()(int, int k, int n) const { return p[k * ld + n] - (k == n ? 1.0 : 0.0); }
+};
+// T = I - Delta/2 + 3/8 Delta^2 - 5/16 Delta^3, given v = (Delta Delta^2)(m, n)
+struct StoreLowdin {
+    double* T; const double* S; const double* D2; int64_t ld;
+    __device__ void operator()(int, int m, int n, double v) const {
+        const int64_t o = m * ld + n;
+        const double id = (m == n) ? 1.0 : 0.0;
+        T[o] = id - 0.5 * (S[o] - id) + 0.375 * D2[o] - 0.3125 * v;
+    }
+};
+
+cudaError_t launch_lowdin_n(int n, const double* const S[], const int k[], double* const D2[], double* const T[],
+                            const GemmWs& W, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    GGroup<RowKmI, KRowNmI, StoreRow> g{};
+    g.n = n;
+    for (int i = 0; i < n; ++i)
+        g.j[i] = {RowKmI{S[i], k[i]}, KRowNmI{S[i], k[i]}, StoreRow{D2[i], k[i], 0}, k[i], k[i], k[i], 1};
+    cudaError_t e = gemm_group(g, W, st);
+    if (e != cudaSuccess) return e;
+    GGroup<RowKmI, KRowN, StoreLowdin> h{};
+    h.n = n;
+    for (int i = 0; i < n; ++i)
+        h.j[i] = {RowKmI{S[i], k[i]}, KRowN{D2[i], k[i]}, StoreLowdin{T[i], S[i], D2[i], k[i]}, k[i], k[i], k[i], 0};
+    return gemm_group(h, W, st);
+}
+
+cudaError_t launch_atb_sym_n(int n, const double* const A[], const double* const B[], const int k[],
+                             double* const out[], const GemmWs& W, cudaStream_t st) {
+    GGroup<ColK, KRowN, StoreRow> g{};
+    g.n = n;
+    for (int i = 0; i < n; ++i)
+        g.j[i] = {ColK{A[i], k[i]}, KRowN{B[i], k[i]}, StoreRow{out[i], k[i], 0}, k[i], k[i], k[i], 1};
+    return n > 0 ? gemm_group(g, W, st) : cudaSuccess;
+}
+
+cudaError_t launch_ab_n(int n, const double* const A[], const double* const B[], const int k[], double* const out[],
+                        const GemmWs& W, cudaStream_t st) {
+    GGroup<RowK, KRowN, StoreRow> g{};
+    g.n = n;
+    for (int i = 0; i < n; ++i)
+        g.j[i] = {RowK{A[i], k[i]}, KRowN{B[i], k[i]}, StoreRow{out[i], k[i], 0}, k[i], k[i], k[i], 0};
+    return n > 0 ? gemm_group(g, W, st) : cudaSuccess;
+}
+
+cudaError_t launch_abt_n(int n, const double* const A[], const double* const B[], const int k[], double* const out[],
+                         const GemmWs& W, cudaStream_t st) {
+    GGroup<RowK, NRowK, StoreRow> g{};
+    g.n = n;
+    for (int i = 0; i < n; ++i)
+        g.j[i] = {RowK{A[i], k[i]}, NRowK{B[i], k[i]}, StoreRow{out[i], k[i], 0}, k[i], k[i], k[i], 0};
+    return n > 0 ? gemm_group(g, W, st) : cudaSuccess;
+}
+
+cudaError_t launch_ab_plus_n(int n, const double* const A[], const double* const B[], const double* const Cadd[],
+                             const int k[], double* const out[], const GemmWs& W, cudaStream_t st) {
+    GGroup<RowK, KRowN, StoreRowPlus> g{};
+    g.n = n;
+    for (int i = 0; i < n; ++i)
+        g.j[i] = {RowK{A[i], k[i]}, KRowN{B[i], k[i]}, StoreRowPlus{out[i], k[i], Cadd[i]}, k[i], k[i], k[i], 0};
+    return n > 0 ? gemm_group(g, W, st) : cudaSuccess;
 }
 
 cudaError_t launch_project_n(int n, const double* const Z[], const int r[], const double* const a[],
