@@ -987,8 +987,12 @@ int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, l
         if (int rc = gather(ctxs[i])) return rc;
     }
     {
+        // shared-memory cluster form where G and L fit, the grid form otherwise
         Scope sc("pchol", s0);
-        cudaError_t e = launch_pchol_multi(pj.data(), 3 * n, c0->num_sms, s0);
+        std::vector<PcholJob> small, large;
+        for (const PcholJob& J : pj) (pchol_cluster_size((int)J.C, J.kmax) > 0 ? small : large).push_back(J);
+        cudaError_t e = launch_pchol_cluster(small.data(), (int)small.size(), s0);
+        if (e == cudaSuccess) e = launch_pchol_multi(large.data(), (int)large.size(), c0->num_sms, s0);
         if (e != cudaSuccess) return fail(c0, LS_ERR_CUDA, "rhosvd_reduce: pivoted Cholesky launch: %s", cudaGetErrorString(e));
     }
     for (int i = 0; i < n; ++i) {

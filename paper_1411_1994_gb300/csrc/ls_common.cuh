@@ -192,6 +192,11 @@ struct PcholJob {
     const double* G; double* L; double* d; double* cand; int* piv; DevStatus* st; int64_t C; int kmax; double delta;
 };
 cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cudaStream_t st);
+// The same factorisation held in shared memory by one thread-block cluster per
+// matrix (ls_pchol.cu; same jobs and outputs): usable when
+// pchol_cluster_size(C, kmax) > 0 for every job.
+int pchol_cluster_size(int C, int kmax);
+cudaError_t launch_pchol_cluster(const PcholJob* jobs, int njobs, cudaStream_t st);
 // xin[t] = xi[t] * n0[tc[3t]] * n1[tc[3t+1]] * n2[tc[3t+2]].
 cudaError_t launch_fold_norms(const double* xi, const int32_t* tcol, int64_t T, const double* n0,
                               const double* n1, const double* n2, double* xin, cudaStream_t st);

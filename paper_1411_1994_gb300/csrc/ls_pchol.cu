@@ -1,0 +1,247 @@
+// Pivoted Cholesky of the weighted Gram matrix (the compression that precedes
+// the eigen-solver of the truncation step, Thm 2.1 / Algorithm 1), held in
+// shared memory by one thread-block cluster per matrix: CTA r owns rows
+// [r0, r1) of G and of L and their residual diagonal d. Per step every CTA
+// reduces the published (max d, argmax, sum d) candidates of all CTAs in the
+// same order, reads row p of L from its owner's shared memory, computes its
+// rows of the new column l_j = (G_jp - L_j . L_p) / sqrt(d_p) (a thread per
+// row, FP64), updates d and publishes its next candidate into every CTA's shared
+// memory (double-buffered by step parity): one cluster barrier per step and no
+// global-memory traffic inside the loop. Greedy diagonal pivoting with ties to
+// the smaller index; the iteration stops when the remaining trace is <= delta
+// or after kmax columns, as the grid form in ls_f64.cu does.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "ls_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ls {
+
+namespace {
+
+constexpr int kPcThreads = 128;
+
+struct PcMode {
+    const double* G; double* L; double* resid; int* piv; DevStatus* st; int C; int kmax; double delta;
+};
+struct PcArgs {
+    const PcMode* m; int cs; int rows_per;
+};
+struct Cand {
+    double sum, mx;   // sum of d, max d (exact)
+    long long key;    // order of (max d, -index): see cand_key
+    long long pad;
+};
+
+// (max d, smallest index among near-equal maxima) as one integer: FP64 on this
+// part has few lanes, so the arg-max runs on the integer pipe (d >= 0 orders
+// like its bits); the low 24 mantissa bits give way to the index, so maxima
+// within 2^-28 relative go to the smaller index. The pivot's exact value
+// travels with the key.
+__device__ __forceinline__ unsigned long long cand_key(double v, int ix) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b & ~0xffffffull) | (unsigned long long)(0xffffff - ix);   // low 24 bits: index, smaller wins
+}
+
+__global__ void __launch_bounds__(kPcThreads) k_pchol_cluster(PcArgs A) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const PcMode J = A.m[blockIdx.x / A.cs];
+    const int C = J.C, kmax = J.kmax, rp = A.rows_per;
+    const int r0 = min(C, rank * rp), r1 = min(C, r0 + rp), nr = r1 - r0;
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* Gs = reinterpret_cast<double*>(smem);                 // [rp][C]
+    double* Ls = Gs + (size_t)rp * C;                             // [rp][kmax]
+    double* d = Ls + (size_t)rp * kmax;                           // [rp]
+    double* lrow = d + rp;                                        // [kmax]
+    Cand* cand = reinterpret_cast<Cand*>(lrow + kmax);            // [2][cs]
+    __shared__ double s_dmax, s_sum;
+    __shared__ int s_p;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+
+    for (int e = tid; e < nr * C; e += nthr) Gs[e] = J.G[(int64_t)r0 * C + e];
+    __syncthreads();
+    for (int jl = tid; jl < nr; jl += nthr) d[jl] = Gs[(size_t)jl * C + r0 + jl];
+    __syncthreads();
+    // this CTA's candidate (warp 0): the arg-max by integer keys, the sum by a butterfly
+    auto publish = [&](int parity) {
+        if (warp != 0) return;
+        unsigned long long key = 0;
+        double sm = 0.0, mx = 0.0;
+        for (int jl = lane; jl < nr; jl += 32) {
+            const double v = d[jl];
+            sm += v;
+            const unsigned long long kk = cand_key(v, r0 + jl);
+            if (kk > key) { key = kk; mx = v; }
+        }
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+            const double m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+            if (k2 > key) { key = k2; mx = m2; }
+            sm += __shfl_xor_sync(0xffffffffu, sm, o);
+        }
+        if (lane < A.cs) cl.map_shared_rank(cand, lane)[parity * A.cs + rank] = Cand{sm, mx, (long long)key, 0};
+    };
+    publish(0);
+    cl.sync();
+    int k = 0;
+    double sum = 0.0;
+    for (;; ++k) {
+        const int par = k & 1;
+        // every CTA reduces the candidates of all CTAs in rank order
+        if (warp == 0) {
+            unsigned long long key = 0;
+            double sm = 0.0, mx = 0.0;
+            if (lane < A.cs) {
+                const Cand c = cand[par * A.cs + lane];
+                key = (unsigned long long)c.key;
+                sm = c.sum;
+                mx = c.mx;
+            }
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+                const double m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+                if (k2 > key) { key = k2; mx = m2; }
+                sm += __shfl_xor_sync(0xffffffffu, sm, o);
+            }
+            if (lane == 0) {
+                s_p = key == 0 ? -1 : 0xffffff - (int)(key & 0xffffffull);
+                s_dmax = key == 0 ? 0.0 : mx;
+                s_sum = sm;
+            }
+        }
+        __syncthreads();
+        const double dmax = s_dmax;
+        const int p = s_p;
+        sum = s_sum;
+        if (k >= kmax || !(sum > J.delta) || p < 0 || !(dmax > 0.0)) break;
+        // row p of L (columns 0..k-1) from its owner
+        {
+            const int owner = p / rp;
+            const double* src = cl.map_shared_rank(Ls, owner) + (size_t)(p - owner * rp) * kmax;
+            for (int t = tid; t < k; t += nthr) lrow[t] = src[t];
+        }
+        __syncthreads();
+        const double inv = 1.0 / sqrt(dmax);
+        // a thread per row: l_j = (G_jp - L_j . L_p) / sqrt(d_p), four partial sums
+        for (int jl = tid; jl < nr; jl += nthr) {
+            const double* lj = Ls + (size_t)jl * kmax;
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int t = 0;
+            for (; t + 3 < k; t += 4) {
+                a0 = fma(lj[t], lrow[t], a0);
+                a1 = fma(lj[t + 1], lrow[t + 1], a1);
+                a2 = fma(lj[t + 2], lrow[t + 2], a2);
+                a3 = fma(lj[t + 3], lrow[t + 3], a3);
+            }
+            for (; t < k; ++t) a0 = fma(lj[t], lrow[t], a0);
+            const double l = (Gs[(size_t)jl * C + p] - ((a0 + a1) + (a2 + a3))) * inv;
+            Ls[(size_t)jl * kmax + k] = l;
+            d[jl] = (r0 + jl == p) ? 0.0 : fmax(d[jl] - l * l, 0.0);
+        }
+        if (rank == 0 && tid == 0) J.piv[k] = p;
+        __syncthreads();
+        publish(par ^ 1);
+        cl.sync();
+    }
+    // L rows to global memory (C x kmax, row-major; columns k.. are not used)
+    for (int e = tid; e < nr * k; e += nthr) {
+        const int jl = e / k, t = e - jl * k;
+        J.L[(int64_t)(r0 + jl) * kmax + t] = Ls[(size_t)jl * kmax + t];
+    }
+    if (rank == 0 && tid == 0) {
+        J.st->sweeps = k;
+        *J.resid = sum;
+    }
+    cl.sync();
+}
+
+size_t pc_smem(int C, int kmax, int cs, int rp) {
+    return 8 * ((size_t)rp * C + (size_t)rp * kmax + rp + kmax) + sizeof(Cand) * 2 * (size_t)cs;
+}
+
+int smem_cap() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    return std::max(0, v - 1024);
+}
+
+}  // namespace
+
+// largest cluster (16, else 8) whose CTAs can hold rows of G and L for C, kmax
+int pchol_cluster_size(int C, int kmax) {
+    const size_t cap = (size_t)smem_cap();
+    for (int cs : {16, 8}) {
+        const int rp = (C + cs - 1) / cs;
+        if (pc_smem(C, kmax, cs, rp) <= cap) return cs;
+    }
+    return 0;
+}
+
+cudaError_t launch_pchol_cluster(const PcholJob* jobs, int njobs, cudaStream_t st) {
+    if (njobs < 1) return cudaSuccess;
+    int Cmax = 1, kmaxm = 1;
+    for (int m = 0; m < njobs; ++m) {
+        Cmax = std::max<int>(Cmax, (int)jobs[m].C);
+        kmaxm = std::max(kmaxm, jobs[m].kmax);
+    }
+    int cs = pchol_cluster_size(Cmax, kmaxm);
+    if (cs == 0) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (cs > 8) {
+        e = cudaFuncSetAttribute(k_pchol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    const int rp = (Cmax + cs - 1) / cs;
+    const size_t smem = pc_smem(Cmax, kmaxm, cs, rp);
+    e = cudaFuncSetAttribute(k_pchol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kPcThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // a 16-CTA cluster must fit one GPC: fall back to 8 where it does not
+    if (cs > 8) {
+        int nclusters = 0;
+        cfg.gridDim = dim3((unsigned)cs);
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_pchol_cluster, &cfg) != cudaSuccess || nclusters < 1) {
+            cudaGetLastError();
+            cs = 8;
+            if (pc_smem(Cmax, kmaxm, cs, (Cmax + cs - 1) / cs) > (size_t)smem_cap()) return cudaErrorInvalidValue;
+            attr[0].val.clusterDim.x = 8;
+        }
+    }
+    const int rp2 = (Cmax + cs - 1) / cs;
+    cfg.dynamicSmemBytes = pc_smem(Cmax, kmaxm, cs, rp2);
+    std::vector<PcMode> hm(njobs);
+    for (int m = 0; m < njobs; ++m) {
+        const PcholJob& J = jobs[m];
+        hm[m] = PcMode{J.G, J.L, J.cand + kPcholCand - 1, J.piv, J.st, (int)J.C, J.kmax, J.delta};
+    }
+    PcMode* dm = nullptr;
+    e = cudaMallocAsync(&dm, sizeof(PcMode) * njobs, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(dm, hm.data(), sizeof(PcMode) * njobs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        PcArgs a{dm, cs, rp2};
+        cfg.gridDim = dim3((unsigned)(njobs * cs));
+        count_kernels(1);
+        e = cudaLaunchKernelEx(&cfg, k_pchol_cluster, a);
+    }
+    cudaFreeAsync(dm, st);
+    return e;
+}
+
+}  // namespace ls
