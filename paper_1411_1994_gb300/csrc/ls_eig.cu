@@ -324,6 +324,8 @@ int smem_optin() {
 // E is held in full (symmetric) storage; K = m * BJ <= jacobi_blk_max_k().
 // ---------------------------------------------------------------------------
 constexpr int BJ = 8, BJ2 = 16, BJ2SQ = 256;
+// threads of the block kernel: 128 registers a thread, so the tile products stay in registers
+constexpr int kBlkThreads = 512;
 // padded strides: E rows K + 4 (16-byte aligned rows, column walks over 8 banks), 16 x 16
 // scratch rows 17 (row-wise walks conflict-free)
 constexpr int SP = BJ2 + 1, SPSQ = BJ2 * SP;
@@ -366,7 +368,7 @@ struct __align__(16) InRot {
     int uv;   // u | v << 8 (positions 0..15 in the pair-block), bit 16: active
 };
 
-__global__ void __launch_bounds__(kEigThreads) k_jacobi_blk(BjArgs A) {
+__global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int job = blockIdx.x / A.cs;
@@ -624,13 +626,13 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi_blk(BjArgs A) {
                         const float4 f3 = *reinterpret_cast<const float4*>(row + Ja * BJ + 4);
                         const float fv[BJ2] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w,
                                                f2.x, f2.y, f2.z, f2.w, f3.x, f3.y, f3.z, f3.w};
-                        float acc = fv[x];
+                        float acc = row[bj_index(Ia, Ja, x)];
 #pragma unroll
                         for (int y = 0; y < BJ2; ++y) acc = fmaf(fv[y], fcol[y], acc);
                         // row j of F_Q (embedded) when j is one of the pair-block's indices
                         const int bj = j / BJ;
-                        if (bj == Ia) acc += fcol[j - Ia * BJ];
-                        else if (bj == Ja) acc += fcol[BJ + j - Ja * BJ];
+                        if (bj == Ia) acc += fqs[a * BJ2SQ + (j - Ia * BJ) * BJ2 + x];
+                        else if (bj == Ja) acc += fqs[a * BJ2SQ + (BJ + j - Ja * BJ) * BJ2 + x];
                         __syncwarp(half);
                         row[bj_index(Ia, Ja, x)] = acc;
                     }
@@ -810,7 +812,7 @@ cudaError_t launch_jacobi_blk(const DfJob* jobs, int njobs, int max_sweeps, cuda
     for (int m = 0; m < njobs; ++m) kmax = std::max(kmax, jobs[m].k);
     const BjLayout L0(kmax, 1);
     // one thread per rotation of an inner round
-    if (L0.e_bytes > (size_t)cap || L0.nb * (BJ2 / 2) > kEigThreads) return cudaErrorInvalidValue;
+    if (L0.e_bytes > (size_t)cap || L0.nb * (BJ2 / 2) > kBlkThreads) return cudaErrorInvalidValue;
     // F rows over nF CTAs (the F update carries about as much work as the tiles)
     int nF = 3;
     int rows_per = (L0.K + nF - 1) / nF;
@@ -834,7 +836,7 @@ cudaError_t launch_jacobi_blk(const DfJob* jobs, int njobs, int max_sweeps, cuda
         BjArgs a{dm, max_sweeps > 63 ? 63 : max_sweeps, cs, rows_per};
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(njobs * cs));
-        cfg.blockDim = dim3(kEigThreads);
+        cfg.blockDim = dim3(kBlkThreads);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];

@@ -51,11 +51,13 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cluster(PcArgs A) {
     const int rank = (int)cl.block_rank();
     const PcMode J = A.m[blockIdx.x / A.cs];
     const int C = J.C, kmax = J.kmax, rp = A.rows_per;
+    // odd row strides: the threads of a step read one column across their rows
+    const int ldG = C | 1, ldL = kmax | 1;
     const int r0 = min(C, rank * rp), r1 = min(C, r0 + rp), nr = r1 - r0;
     extern __shared__ __align__(16) unsigned char smem[];
-    double* Gs = reinterpret_cast<double*>(smem);                 // [rp][C]
-    double* Ls = Gs + (size_t)rp * C;                             // [rp][kmax]
-    double* d = Ls + (size_t)rp * kmax;                           // [rp]
+    double* Gs = reinterpret_cast<double*>(smem);                 // [rp][ldG]
+    double* Ls = Gs + (size_t)rp * ldG;                           // [rp][ldL]
+    double* d = Ls + (size_t)rp * ldL;                            // [rp]
     double* lrow = d + rp;                                        // [kmax]
     Cand* cand = reinterpret_cast<Cand*>(lrow + kmax);            // [2][cs]
     __shared__ double s_dmax, s_sum;
@@ -63,9 +65,12 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cluster(PcArgs A) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
 
-    for (int e = tid; e < nr * C; e += nthr) Gs[e] = J.G[(int64_t)r0 * C + e];
+    for (int e = tid; e < nr * C; e += nthr) {
+        const int jl = e / C, c = e - jl * C;
+        Gs[(size_t)jl * ldG + c] = J.G[(int64_t)r0 * C + e];
+    }
     __syncthreads();
-    for (int jl = tid; jl < nr; jl += nthr) d[jl] = Gs[(size_t)jl * C + r0 + jl];
+    for (int jl = tid; jl < nr; jl += nthr) d[jl] = Gs[(size_t)jl * ldG + r0 + jl];
     __syncthreads();
     // this CTA's candidate (warp 0): the arg-max by integer keys, the sum by a butterfly
     auto publish = [&](int parity) {
@@ -122,14 +127,14 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cluster(PcArgs A) {
         // row p of L (columns 0..k-1) from its owner
         {
             const int owner = p / rp;
-            const double* src = cl.map_shared_rank(Ls, owner) + (size_t)(p - owner * rp) * kmax;
+            const double* src = cl.map_shared_rank(Ls, owner) + (size_t)(p - owner * rp) * ldL;
             for (int t = tid; t < k; t += nthr) lrow[t] = src[t];
         }
         __syncthreads();
         const double inv = 1.0 / sqrt(dmax);
         // a thread per row: l_j = (G_jp - L_j . L_p) / sqrt(d_p), four partial sums
         for (int jl = tid; jl < nr; jl += nthr) {
-            const double* lj = Ls + (size_t)jl * kmax;
+            const double* lj = Ls + (size_t)jl * ldL;
             double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
             int t = 0;
             for (; t + 3 < k; t += 4) {
@@ -139,8 +144,8 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cluster(PcArgs A) {
                 a3 = fma(lj[t + 3], lrow[t + 3], a3);
             }
             for (; t < k; ++t) a0 = fma(lj[t], lrow[t], a0);
-            const double l = (Gs[(size_t)jl * C + p] - ((a0 + a1) + (a2 + a3))) * inv;
-            Ls[(size_t)jl * kmax + k] = l;
+            const double l = (Gs[(size_t)jl * ldG + p] - ((a0 + a1) + (a2 + a3))) * inv;
+            Ls[(size_t)jl * ldL + k] = l;
             d[jl] = (r0 + jl == p) ? 0.0 : fmax(d[jl] - l * l, 0.0);
         }
         if (rank == 0 && tid == 0) J.piv[k] = p;
@@ -151,7 +156,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cluster(PcArgs A) {
     // L rows to global memory (C x kmax, row-major; columns k.. are not used)
     for (int e = tid; e < nr * k; e += nthr) {
         const int jl = e / k, t = e - jl * k;
-        J.L[(int64_t)(r0 + jl) * kmax + t] = Ls[(size_t)jl * kmax + t];
+        J.L[(int64_t)(r0 + jl) * kmax + t] = Ls[(size_t)jl * ldL + t];
     }
     if (rank == 0 && tid == 0) {
         J.st->sweeps = k;
@@ -161,7 +166,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cluster(PcArgs A) {
 }
 
 size_t pc_smem(int C, int kmax, int cs, int rp) {
-    return 8 * ((size_t)rp * C + (size_t)rp * kmax + rp + kmax) + sizeof(Cand) * 2 * (size_t)cs;
+    return 8 * ((size_t)rp * (C | 1) + (size_t)rp * (kmax | 1) + rp + kmax) + sizeof(Cand) * 2 * (size_t)cs;
 }
 
 int smem_cap() {
