@@ -28,6 +28,7 @@ from paper_1411_1994_gb300 import workloads as W  # noqa: E402
 
 METRIC = "lattice potentials summed/s (build+RHOSVD), mixed vs FP64 GPU at 1e-6 rel err"
 FP64_PEAK_TFLOPS_DERIVED = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk x flops x max clock
+FP32_PEAK_TFLOPS_DERIVED = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FFMA/clk x flops x max clock
 
 
 def parse():
@@ -202,7 +203,8 @@ def step_flops(name, info, N):
         return 2.0 * r[1] * r[2] * T + 2.0 * r[0] * r[1] * r[2] * C[0]
     if name == "jacobi":
         # each applied rotation of the k x k matrix H = L^T L updates two rows and two columns
-        # of its upper triangle (~2 k entries x 3 flop x 2) and two columns of V (2 k x 3 flop)
+        # (~2 k entries x 3 flop x 2) and two columns of the accumulated rotation (2 k x 3 flop);
+        # the rotations run in FP32 (the FP64 re-projection products are not counted)
         return sum(18.0 * k[a] * info["rotations"][a] for a in range(3))
     return None
 
@@ -222,7 +224,14 @@ def roofline(report, info, N, steps, precision, peaks):
         return out
     achieved = fl / launches_per_step / (ms_launch * 1e-3) / 1e12
     tensor = precision == "mixed" and name in ("project", "core")
-    if not tensor:
+    if name == "jacobi":
+        peak = FP32_PEAK_TFLOPS_DERIVED
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None,
+                    "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz (FP32 on CUDA cores; "
+                                   "an FFMA probe measured 73 TFLOP/s); the rotations are sequential rounds, "
+                                   "so this step is bound by latency, not by this peak"})
+    elif not tensor:
         peak = FP64_PEAK_TFLOPS_DERIVED
         out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "traffic": None,
@@ -232,8 +241,8 @@ def roofline(report, info, N, steps, precision, peaks):
         peak = peaks.get("bf16_tflops")
         out.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak if peak else None, "traffic": None,
-                    "peak_source": "of measured bf16 burst (MEASURED_PEAKS.json); the ten split MMAs per product "
-                                   "are counted as overhead, not as work"})
+                    "peak_source": "of measured bf16 burst (MEASURED_PEAKS.json); the 13 digit MMAs per k16 step "
+                                   "of the exact split products are counted as overhead, not as work"})
     return out
 
 

@@ -66,11 +66,14 @@ extern "C" {
 #define LS_ERR_TIMEOUT     -6   /* a bounded device-side wait gave up          */
 
 /* arithmetic of the reduction and evaluation steps */
-#define LS_FP64   0   /* every step in FP64 (CUDA-core DFMA)                         */
-#define LS_MIXED  1   /* FP64 shift-sums, Gram, eigen-solver and CholeskyQR2;          */
-                      /* projection, core contraction and slab evaluation on tcgen05    */
-                      /* tensor cores: operands split into three BF16 parts, six MMAs   */
-                      /* per k-step, FP32 accumulation in TMEM                          */
+#define LS_FP64   0   /* contractions (projection, core, slabs) in FP64 DFMA             */
+#define LS_MIXED  1   /* the same orthogonalisation (FP64 Gram, eigen-solver, CholeskyQR) */
+                      /* with the projection, the core contraction and the slab         */
+                      /* products on tcgen05 tensor cores: each operand row is scaled    */
+                      /* by a power of two and split into two exact 6-bit digits and a  */
+                      /* rest of two BF16 parts; digit products accumulate exactly in    */
+                      /* FP32 TMEM accumulators (13 MMAs per k16 step, K chunks of       */
+                      /* 1024 summed in FP64): about 2^-30 of sum |a_k b_k|              */
 
 /* defect kinds */
 #define LS_DEFECT_SITES 0  /* sites block[site : site+extent) get charge `charge`     */
@@ -180,10 +183,17 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n);
  * lattice_sum_rhosvd_reduce -- RHOSVD rank reduction to Tucker form.
  * Def. 4.1 / Thm A.1: per mode, the side matrix of unit canonical vectors
  * (a vector shared by k terms enters with weight sqrt(k), which leaves
- * A A^T unchanged) is orthogonalised via its FP64 Gram matrix, a parallel
- * Jacobi eigen-solver and CholeskyQR2; r_l is the smallest rank whose
- * discarded singular values satisfy (sum_{k>r} s_k^2)^(1/2) <= eps
- * (sum_k s_k^2)^(1/2). The projections P_l = Z_l^T A_l and the core
+ * A A^T unchanged) is orthogonalised via its FP64 Gram matrix G: a pivoted
+ * Cholesky G ~ L L^T keeps pivot columns until the remaining trace is below
+ * 1e-4 eps^2 T (that remainder joins the discarded tail and the bound); the
+ * k x k matrix H = L^T L is diagonalised by a two-stage Jacobi iteration
+ * (FP32 rotations with the diagonal kept to about 48 bits, then FP64
+ * re-projection and a second iteration to off-diagonal ratios of 1e-10);
+ * the basis Y = A_w L U diag(1/lambda) is orthonormalised by CholeskyQR
+ * (FP32 first factorisation, FP64 inverse-square-root series second).
+ * r_l is the smallest rank whose discarded singular values satisfy
+ * (sum_{k>r} s_k^2)^(1/2) <= eps (sum_k s_k^2)^(1/2). The projections
+ * P_l = Z_l^T A_l and the core
  * mu = sum_nu xi_nu P1[:,c1] (x) P2[:,c2] (x) P3[:,c3] follow.
  * `forced_ranks` (host, 3 entries or NULL) overrides the eps rule (each
  * clipped to C_l and to the eigenvalues of the FP64 Gram matrix above its
@@ -197,13 +207,12 @@ int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ran
 /*
  * lattice_sum_batch_reduce -- the batched form: RHOSVD of n independent
  * contexts (each created and given its defects as usual) in one call.
- * Every context is reduced exactly as lattice_sum_rhosvd_reduce(ctx, eps)
- * would reduce it; what changes is the schedule. The pivoted-Cholesky
- * pre-compression and the Jacobi iteration of all 3n modes run as one
- * persistent cooperative launch each on the stream of ctxs[0], every mode
- * on its own group of CTAs (a single CTA, with no grid barrier, when the
- * batch is large); the per-context steps run on each context's own stream,
- * ordered against the shared launches by events. `infos` (host, n entries,
+ * Every context is reduced as lattice_sum_rhosvd_reduce(ctx, eps) would
+ * reduce it; what changes is the schedule. The pivoted Cholesky, the two
+ * Jacobi runs and the CholeskyQR factorisation of all 3n modes run as one
+ * launch each on the stream of ctxs[0] (one thread-block cluster or CTA
+ * group per mode); the per-context products run on each context's own
+ * stream, ordered against the shared launches by events. `infos` (host, n entries,
  * may be NULL) receives each context's ls_tucker_info. Synchronises all the
  * streams. Errors: LS_ERR_ARG (NULL or repeated context, eps <= 0),
  * LS_ERR_STATE (a context already reduced), and the errors of

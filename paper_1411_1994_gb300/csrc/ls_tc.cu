@@ -61,14 +61,6 @@ struct TcOut {
     int accumulate;     // F64 only: D += result
 };
 
-// x (FP32) = b0 + b1 + b2 exactly: three BF16 parts of 8 significant bits each
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& b0, __nv_bfloat16& b1, __nv_bfloat16& b2) {
-    b0 = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(b0);
-    b1 = __float2bfloat16_rn(r1);
-    b2 = __float2bfloat16_rn(r1 - __bfloat162float(b1));
-}
-
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
