@@ -37,7 +37,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--batch-items", type=int, default=256, help="c4: configurations in the batch")
+    ap.add_argument("--batch-wave", type=int, default=32, help="c4: contexts reduced per batch_reduce call")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-path comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -88,10 +90,53 @@ def cores_used():
         return os.cpu_count() or 1
 
 
+def run_reference_batch(args):
+    """The oracle on the batch of config 4: each step a bounded sample (~15 s) of the items,
+    taken in order and continued from step to step; units and time summed over the sample."""
+    from oracle import lattice_oracle as O
+    items = W.config4(args.batch_items)
+    nxt = 0
+
+    def sample(budget_s):
+        nonlocal nxt
+        units, secs, n = 0, 0.0, 0
+        while secs < budget_s and n < len(items):
+            w = items[nxt % len(items)]
+            s, _ = O.fit_t_scale(w.R, w.sinc_step, w.r_min, O.default_r_max(w))
+            t0 = time.perf_counter()
+            oracle_step(w, s)
+            secs += time.perf_counter() - t0
+            units += w.units
+            nxt += 1
+            n += 1
+        return units, secs, n
+
+    for _ in range(args.warmup):
+        sample(3.0)
+    tot_u, tot_s, tot_n = 0, 0.0, 0
+    for _ in range(args.steps):
+        u, t, n = sample(15.0)
+        tot_u, tot_s, tot_n = tot_u + u, tot_s + t, tot_n + n
+    value = tot_u / tot_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "potentials/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": f"c4_batch{len(items)}_L8-48_N512-2048_R20-28", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "potentials/s", "cores": cores_used(), "kind": "oracle",
+                             "sample": f"{tot_n} of the {len(items)} batch items over {args.steps} steps "
+                                       "(full oracle pipelines, in order)"},
+            "e2e": {"value": value, "unit": "potentials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.workload == "c4":
+        return run_reference_batch(args)
     wl = workload(args.workload)
     from oracle import lattice_oracle as O
     s, _ = O.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, O.default_r_max(wl))
@@ -250,10 +295,119 @@ def roofline(report, info, N, steps, precision, peaks):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def run_batch(args, torch, B, L):
+    """The batched form (config 4): one step reduces every seeded configuration of the batch,
+    lattice_sum_batch_reduce over waves of contexts (mixed path), against the same items
+    reduced one at a time on the FP64 path."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    items = W.config4(args.batch_items)
+    units = sum(w.units for w in items)
+    scale = {}
+    for w in items:
+        key = (w.R, w.sinc_step, w.r_min, w.box_hi - w.box_lo)
+        if key not in scale:
+            scale[key] = L.fit_t_scale(w.R, w.sinc_step, w.r_min, math.sqrt(3.0) * (w.box_hi - w.box_lo))[0]
+    s_of = [scale[(w.R, w.sinc_step, w.r_min, w.box_hi - w.box_lo)] for w in items]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(batched):
+        infos = []
+        for j0 in range(0, len(items), args.batch_wave):
+            ctxs = []
+            for w, s in zip(items[j0:j0 + args.batch_wave], s_of[j0:j0 + args.batch_wave]):
+                c = L.LatticeSum.from_workload(w, s, L.LS_MIXED if batched else L.LS_FP64, stream=stream.cuda_stream)
+                c.add_defects(w.defects)
+                ctxs.append(c)
+            if batched:
+                infos += L.batch_reduce(ctxs, items[0].eps)
+            else:
+                infos += [c.rhosvd_reduce(w.eps) for c, w in zip(ctxs, items[j0:j0 + args.batch_wave])]
+            for c in ctxs:
+                c.close()
+        return infos
+
+    def timed(batched, sample_clocks):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step(batched)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local) if sample_clocks else None
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        L.profile(True)
+        if clocks:
+            clocks.start()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(stream)
+                infos = step(batched)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        L.profile(False)
+        rep = L.profile_report()
+        total_ms = sum(a.elapsed_time(b) for a, b in ev)
+        if dist:
+            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        ms = total_ms / args.steps
+        return {"value": world * units / (ms / 1e3), "ms_per_step": ms, "infos": infos, "report": rep, "clocks": clk}
+
+    head = timed(True, True)
+    seq = None if args.no_compare else timed(False, False)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    rs = [i["r"] for i in head["infos"]]
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": "potentials/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 orthogonalisation + bf16 tensor-core contractions (exact 6-bit heads, f32 acc)",
+        "data": "synthetic (seeded)",
+        "config": {"workload": f"c4_batch{len(items)}_L8-48_N512-2048_R20-28", "items": len(items),
+                   "units_per_step": units, "wave": args.batch_wave, "eps": items[0].eps,
+                   "l2": "flushed between steps (512 MB write outside the per-step events)",
+                   "parallelism": f"replicas x{world}", "rank_range": [min(min(r) for r in rs), max(max(r) for r in rs)],
+                   "columns_range": [min(min(i["C"]) for i in head["infos"]), max(max(i["C"]) for i in head["infos"])]},
+        "gpu_launches": int(head["report"].get("kernel_launches", 0)),
+        "clocks": head["clocks"],
+        "steps_ms": {k: v["ms"] / args.steps for k, v in head["report"].get("steps", {}).items()},
+    }
+    if seq is not None:
+        line["fp64_sequential"] = {"value": seq["value"], "ms_per_step": seq["ms_per_step"]}
+        line["batched_over_sequential_fp64"] = head["value"] / seq["value"]
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c4":
+        import torch
+        from paper_1411_1994_gb300 import build as B
+        from paper_1411_1994_gb300 import lattice_sum as L
+        if not torch.cuda.is_available():
+            raise SystemExit("bench.py needs a CUDA GPU")
+        return run_batch(args, torch, B, L)
     import torch
     from paper_1411_1994_gb300 import build as B
     from paper_1411_1994_gb300 import lattice_sum as L

@@ -974,22 +974,57 @@ __global__ void k_transpose(const double* __restrict__ in, int64_t rows, int64_t
 // Core, step 1 (terms grouped by their mode-0 vector c0):
 //   W[c0 - cbeg][j*r2 + l] = sum_{t : c0(t) = c0} xin[t] P1[j][c1(t)] P2[l][c2(t)]
 // with P1t = P1^T (C1 x r1) and P2t = P2^T (C2 x r2) so that l runs along
-// contiguous memory. One CTA per (256 outputs, c0).
+// contiguous memory. One CTA per (1024 outputs, c0); a thread takes four
+// consecutive outputs, so one product xin P1 serves four FMAs (FP64 issue is
+// the limit here), and the group's term data is staged in shared memory.
+constexpr int kCoreOut = 4;
+constexpr int kCoreStage = 256;
 __global__ void __launch_bounds__(256) k_core_group_f64(const double* __restrict__ P1t, const double* __restrict__ P2t,
                                                         int r1, int r2, const int32_t* __restrict__ tcol,
                                                         const double* __restrict__ xin, const int32_t* __restrict__ perm,
                                                         const int32_t* __restrict__ off, int cbeg, double* __restrict__ W) {
-    const int64_t n = blockIdx.x * 256 + threadIdx.x;
+    __shared__ double s_x[kCoreStage];
+    __shared__ int s_c1[kCoreStage], s_c2[kCoreStage];
     const int64_t nn = (int64_t)r1 * r2;
     const int c0 = cbeg + blockIdx.y;
-    if (n >= nn) return;
-    const int j = (int)(n / r2), l = (int)(n - (int64_t)j * r2);
-    double acc = 0.0;
-    for (int k = off[c0]; k < off[c0 + 1]; ++k) {
-        const int t = perm[k];
-        acc = fma(xin[t] * P1t[(int64_t)tcol[3 * t + 1] * r1 + j], P2t[(int64_t)tcol[3 * t + 2] * r2 + l], acc);
+    const int64_t n0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kCoreOut;
+    int jj[kCoreOut], ll[kCoreOut];
+#pragma unroll
+    for (int u = 0; u < kCoreOut; ++u) {
+        const int64_t n = n0 + u < nn ? n0 + u : nn - 1;
+        jj[u] = (int)(n / r2);
+        ll[u] = (int)(n - (int64_t)jj[u] * r2);
     }
-    W[(int64_t)blockIdx.y * nn + n] = acc;
+    const bool one_row = jj[0] == jj[kCoreOut - 1];
+    double acc[kCoreOut] = {0.0, 0.0, 0.0, 0.0};
+    const int kb = off[c0], ke = off[c0 + 1];
+    for (int k0 = kb; k0 < ke; k0 += kCoreStage) {
+        const int nk = min(kCoreStage, ke - k0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nk; i += blockDim.x) {
+            const int t = perm[k0 + i];
+            s_x[i] = xin[t];
+            s_c1[i] = tcol[3 * t + 1];
+            s_c2[i] = tcol[3 * t + 2];
+        }
+        __syncthreads();
+        if (n0 >= nn) continue;
+        for (int i = 0; i < nk; ++i) {
+            const double* p1 = P1t + (int64_t)s_c1[i] * r1;
+            const double* p2 = P2t + (int64_t)s_c2[i] * r2;
+            if (one_row) {
+                const double a = s_x[i] * p1[jj[0]];
+#pragma unroll
+                for (int u = 0; u < kCoreOut; ++u) acc[u] = fma(a, p2[ll[u]], acc[u]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < kCoreOut; ++u) acc[u] = fma(s_x[i] * p1[jj[u]], p2[ll[u]], acc[u]);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kCoreOut; ++u)
+        if (n0 + u < nn) W[(int64_t)blockIdx.y * nn + n0 + u] = acc[u];
 }
 
 struct StoreRowAcc {     // C[m*ld + n] (+)= v
@@ -1373,7 +1408,7 @@ cudaError_t launch_core_group(const double* P1t, const double* P2t, int r1, int 
                               const double* xin, const int32_t* perm, const int32_t* off, int cbeg, int cw, double* W,
                               cudaStream_t st) {
     const int64_t nn = (int64_t)r1 * r2;
-    dim3 grid((unsigned)((nn + 255) / 256), (unsigned)cw);
+    dim3 grid((unsigned)((nn + 256 * kCoreOut - 1) / (256 * kCoreOut)), (unsigned)cw);
     k_core_group_f64<<<grid, 256, 0, st>>>(P1t, P2t, r1, r2, tcol, xin, perm, off, cbeg, W);
     count_kernels(1);
     return cudaGetLastError();
@@ -1385,7 +1420,7 @@ cudaError_t launch_core_f64(const double* P0, const double* P1t, const double* P
     const int64_t nn = (int64_t)r[1] * r[2];
     for (int64_t c0 = 0; c0 < C[0]; c0 += w_cols) {
         const int cw = (int)std::min<int64_t>(w_cols, C[0] - c0);
-        dim3 grid((unsigned)((nn + 255) / 256), (unsigned)cw);
+        dim3 grid((unsigned)((nn + 256 * kCoreOut - 1) / (256 * kCoreOut)), (unsigned)cw);
         k_core_group_f64<<<grid, 256, 0, st>>>(P1t, P2t, r[1], r[2], tcol, xin, perm, off, (int)c0, W);
         count_kernels(1);
         cudaError_t e = cudaGetLastError();
