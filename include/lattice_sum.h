@@ -222,6 +222,21 @@ int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ran
 int lattice_sum_batch_reduce(ls_ctx* const* ctxs, int32_t n, double eps, ls_tucker_info* infos);
 
 /*
+ * lattice_sum_gemm_nt -- D = A B^T for device FP64 matrices (A: M x K, B:
+ * N x K, D: M x N, all row-major), in the arithmetic the reduction uses for
+ * its dense FP64 products (Gram matrices, CholeskyQR, FP64 projection): each
+ * row scaled by a power of two and written as eight exact base-128 digits,
+ * digit products summed exactly per level in FP32 on tcgen05 tensor cores,
+ * levels recombined in integer and FP64 arithmetic. The error is about
+ * 2^-53 sum_k |a_mk| |b_nk|, as for an FP64 dot product. Exposed so that the
+ * arithmetic can be checked on its own. `stream` is a cudaStream_t or NULL;
+ * the call synchronises it. Errors: LS_ERR_ARG, LS_ERR_OOM, LS_ERR_CUDA,
+ * LS_ERR_TIMEOUT.
+ */
+int lattice_sum_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* D,
+                        void* stream);
+
+/*
  * lattice_sum_eval_slab -- Tucker tensor values on z-slabs.
  * Eq. (Tucker_singePot): for each z index i3, M = B x3 Z3[:, i3] and
  * out[s][i1][i2] = sum_{a,b} Z1[a][i1] M[a][b] Z2[b][i2] (i2 fastest).

@@ -470,8 +470,8 @@ struct RedState {
     ls_ctx* ctx = nullptr;
     double eps = 0.0;
     const int32_t* forced = nullptr;
-    // [0, 3): pivoted Cholesky, then the eigen-solver, per mode; [3, 6): CholeskyQR2 per mode;
-    // [6, 9): orthonormalisation inside the two-stage eigen-solver per mode
+    // [0, 3): pivoted Cholesky, then the eigen-solver, per mode; [3, 6): CholeskyQR per mode;
+    // [6, 9): spare per-mode statuses; [9]: the exact-slice tensor-core products (never reset)
     DevStatus* d_st = nullptr;
     double* d_sel = nullptr;
     GemmWs gw{};
@@ -479,7 +479,7 @@ struct RedState {
     int sweeps[3] = {0, 0, 0};
     int64_t rotations[3] = {0, 0, 0};
     double sel[3][3] = {};
-    DevStatus hs[9] = {};
+    DevStatus hs[10] = {};
     double floor_noise = 0.0;
     int64_t T = 0;
 };
@@ -506,8 +506,8 @@ int red_prepare(RedState& R, PcholJob* pj) {
     count_h2d(3 * T * sizeof(int32_t));
     CUS(cudaMemcpyAsync(ctx->d_xi, ctx->xi.data(), T * sizeof(double), cudaMemcpyHostToDevice, st));
     count_h2d(T * sizeof(double));
-    CUS(dalloc(ctx, &R.d_st, 9));
-    CUS(cudaMemsetAsync(R.d_st, 0, 9 * sizeof(DevStatus), st));
+    CUS(dalloc(ctx, &R.d_st, 10));
+    CUS(cudaMemsetAsync(R.d_st, 0, 10 * sizeof(DevStatus), st));
     CUS(dalloc(ctx, &R.d_sel, 9));
     R.gw.num_sms = ctx->num_sms;
     R.gw.ws_cap = gemm_ws_doubles(ctx->num_sms);
@@ -545,7 +545,13 @@ int red_prepare(RedState& R, PcholJob* pj) {
         const double delta = R.forced ? (double)C * R.floor_noise : 1e-4 * R.eps * R.eps * (double)T;
         pj[l] = PcholJob{M.G, M.L, M.pd, M.cand, M.piv, R.d_st + l, C, (int)C, delta};
     }
-    { Scope sc("gram", st); CUS(launch_gram_weighted_n(3, a, Cs, N, w, G, R.gw, st)); }
+    {
+        // FP64-grade weighted Gram matrices on the tensor cores
+        Scope sc("gram", st);
+        std::string err;
+        int rc = x64_gram(3, a, Cs, N, w, G, &R.d_st[9].flag, st, &err);
+        if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: Gram: %s", err.c_str());
+    }
     return LS_OK;
 }
 
@@ -666,7 +672,13 @@ int red_basis(RedState& R, CholJob* cj) {
         CUS(launch_pchol_vectors_n(3, L, Cs, ks, Cs, U, Hc, vg, R.gw, st));
         CUS(launch_basis_n(3, vgc, Cs, kl, perm, isl, w, a, N, rs, Y, R.gw, st));
     }
-    { Scope sc("cholqr2", st); CUS(launch_syrk_rows_n(3, Yc, rs, N, Gz, R.gw, st)); }
+    {
+        Scope sc("cholqr2", st);
+        const int64_t r64[3] = {rs[0], rs[1], rs[2]};
+        std::string err;
+        int rc = x64_gram(3, Yc, r64, N, nullptr, Gz, &R.d_st[9].flag, st, &err);
+        if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: CholeskyQR: %s", err.c_str());
+    }
     return LS_OK;
 }
 
@@ -691,8 +703,13 @@ int red_cholqr_mid(RedState& R) {
         rs[l] = ctx->r[l];
     }
     Scope sc("cholqr2", st);
-    CUS(launch_lower_apply_n(3, Li, rs, src, dst, N, R.gw, st));
-    CUS(launch_syrk_rows_n(3, yc, rs, N, Gz, R.gw, st));
+    {
+        const int64_t r64[3] = {rs[0], rs[1], rs[2]};
+        std::string err;
+        int rc = x64_apply(3, Li, rs, src, N, dst, &R.d_st[9].flag, st, &err);
+        if (rc == LS_OK) rc = x64_gram(3, yc, r64, N, nullptr, Gz, &R.d_st[9].flag, st, &err);
+        if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: CholeskyQR: %s", err.c_str());
+    }
     CUS(launch_lowdin_n(3, gc, rs, D2, T, R.gw, st));
     return LS_OK;
 }
@@ -714,7 +731,9 @@ int red_finish(RedState& R, ls_tucker_info* info) {
             rs[l] = ctx->r[l];
         }
         Scope sc("cholqr2", st);
-        CUS(launch_lower_apply_n(3, Li, rs, src, dst, N, R.gw, st));
+        std::string err;
+        int rc = x64_apply(3, Li, rs, src, N, dst, &R.d_st[9].flag, st, &err);
+        if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: CholeskyQR: %s", err.c_str());
     }
     if (ctx->p.precision == LS_MIXED) {
         Scope sc("project", st);
@@ -736,7 +755,9 @@ int red_finish(RedState& R, ls_tucker_info* info) {
             Cs[l] = ctx->mode[l].C;
         }
         Scope sc("project", st);
-        CUS(launch_project_n(3, Z, rs, a, Cs, N, P, R.gw, st));
+        std::string err;
+        int rc = x64_project(3, Z, rs, a, Cs, N, P, &R.d_st[9].flag, st, &err);
+        if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: projection: %s", err.c_str());
     }
     { Scope sc("fold", st); CUS(launch_fold_norms(ctx->d_xi, ctx->d_tcol, T, ctx->d_norms[0], ctx->d_norms[1], ctx->d_norms[2], ctx->d_xin, st)); }
     // (c3) core: terms grouped by their mode-0 vector (counting sort on the host)
@@ -793,7 +814,8 @@ int red_finish(RedState& R, ls_tucker_info* info) {
     dfree(ctx, R.gw.ws);
     dfree(ctx, R.gw.ctr);
     CUS(cudaMemcpyAsync(&R.hs[3], R.d_st + 3, 3 * sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
-    count_d2h(3 * sizeof(DevStatus));
+    CUS(cudaMemcpyAsync(&R.hs[9], R.d_st + 9, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    count_d2h(4 * sizeof(DevStatus));
     double xin_norm2 = 0.0;
     if (info) {
         std::vector<double> xin(T);
@@ -805,6 +827,8 @@ int red_finish(RedState& R, ls_tucker_info* info) {
         CUS(cudaStreamSynchronize(st));
     }
     dfree(ctx, R.d_st);
+    if (R.hs[9].flag == FLAG_TIMEOUT)
+        return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: a tensor-core product's bounded wait timed out");
     for (int l = 3; l < 6; ++l) {
         if (R.hs[l].flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Cholesky grid barrier timed out");
         if (R.hs[l].flag == FLAG_NOT_SPD)
@@ -1058,6 +1082,15 @@ int lattice_sum_batch_reduce(ls_ctx* const* ctxs, int32_t n, double eps, ls_tuck
             }
     }
     return rc;
+}
+
+int lattice_sum_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* D, void* stream) {
+    if (!A || !B || !D || M < 0 || N < 0 || K < 1 || M > INT32_MAX || N > INT32_MAX)
+        return fail(nullptr, LS_ERR_ARG, "gemm_nt: bad arguments");
+    std::string err;
+    int rc = x64_gemm_nt(A, B, M, N, K, D, static_cast<cudaStream_t>(stream), &err);
+    if (rc != LS_OK) return fail(nullptr, rc, "gemm_nt: %s", err.c_str());
+    return LS_OK;
 }
 
 int lattice_sum_eval_slab(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev, int32_t out_dtype) {

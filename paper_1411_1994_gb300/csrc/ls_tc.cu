@@ -29,6 +29,8 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <string.h>
+
 #include <algorithm>
 #include <mutex>
 #include <string>
@@ -295,6 +297,230 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// FP64-grade products on the tensor cores: exact slices
+//
+// Each operand row is scaled by 2^-E (its largest entry then below 1/2 in
+// magnitude) and written as eight balanced base-128 digits d_i in [-64, 64]:
+// x = 2^E sum_i d_i 128^-(i+1), to 2^-57 of 2^E. The digits are integers,
+// exact in BF16. Products d_i d_j (|.| <= 2^12) of one level l = i + j (at
+// most eight pairs) summed over K <= 512 stay below 2^24, so each level
+// accumulates EXACTLY in its own FP32 TMEM accumulator; the 36 pairs with
+// l <= 7 are all that lie above 2^-56 of the result. The epilogue recombines
+// the exact level sums by integer Horner steps (levels 0-3 and 4-7), converts
+// once to FP64 and applies 2^(E_a + E_b): a product is good to about 2^-53 of
+// sum_k |a_k| |b_k|, as an FP64 dot product is, while the arithmetic runs on
+// the tensor cores. One stage of 8 slices x (128 + 64) rows x 64 k fills
+// 192 KB of shared memory; the eight accumulators fill TMEM's 512 columns.
+// ---------------------------------------------------------------------------
+constexpr int XSL = 8;                              // slices (digits)
+constexpr int XKCHUNK = 512;                        // K per exact accumulation
+constexpr int XSTAGE = XSL * (TILE_A + TILE_B);     // 192 KB
+constexpr int XTMEM = XSL * TBN;                    // 512 columns
+
+struct X64Job {
+    CUtensorMap a[XSL], b[XSL];
+    int M, N, nkb;        // k-blocks of 64 over all of K
+    int tiles_n, b0;      // tiles along N; first block of the job
+    int transposed;       // D stored at out.p[n * out.ld + m]
+    const int* ea;
+    const int* eb;
+    TcOut out;
+};
+constexpr int kX64MaxJobs = 3;
+struct X64Group {
+    X64Job j[kX64MaxJobs];
+    int n;
+};
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// One 128 x 64 output tile of one job per CTA, all of K: the K-chunks of 512 run in
+// turn on the same eight accumulators (the MMA warp waits until the epilogue has drained
+// them); the epilogue adds each chunk's recombined value into the output tile, which only
+// this CTA writes.
+__global__ void __launch_bounds__(TC_THREADS, 1) k_x64_gemm(const __grid_constant__ X64Group G, int* flag) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + XSTAGE);
+    uint64_t* empty = full + 1;
+    uint64_t* accum = empty + 1;      // accumulators of a chunk complete
+    uint64_t* drained = accum + 1;    // epilogue has read them
+    uint32_t* tmem_slot = (uint32_t*)(drained + 1);
+    int ji = 0;
+    while (ji + 1 < G.n && (int)blockIdx.x >= G.j[ji + 1].b0) ++ji;
+    const X64Job& J = G.j[ji];
+    const int tile = (int)blockIdx.x - J.b0;
+    const int tm = tile / J.tiles_n, tn = tile - tm * J.tiles_n;
+    const int n0 = tn * TBN, m0 = tm * TBM;
+    const int kbc = XKCHUNK / TBK;
+    const int nchunk = (J.nkb + kbc - 1) / kbc;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        mbar_init(full, 1);
+        mbar_init(empty, 1);
+        mbar_init(accum, 1);
+        mbar_init(drained, 4);   // one arrival per epilogue warp
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(XTMEM));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer: one stage, refilled once the MMAs of the previous k-block are done
+        int issued = 0;
+        for (int kb = 0; kb < J.nkb; ++kb) {
+            if (kb > 0 && !mbar_wait(empty, (kb - 1) & 1, flag)) break;
+            const int kx = kb * TBK;
+            mbar_expect_tx(full, XSTAGE);
+#pragma unroll
+            for (int i = 0; i < XSL; ++i) tma_load_3d(smem + i * TILE_A, &J.a[i], kx, m0, 0, full);
+#pragma unroll
+            for (int j = 0; j < XSL; ++j) tma_load_3d(smem + XSL * TILE_A + j * TILE_B, &J.b[j], kx, n0, 0, full);
+            issued = kb + 1;
+        }
+        if (issued > 0) {
+            long long it = 0;
+            while (!mbar_try_wait(full, (issued - 1) & 1) && ++it < kWaitLimit) {
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: pair (i, j) into the accumulator of level i + j; a chunk starts from zero
+        const uint32_t idesc = idesc_bf16(TBM, TBN);
+        bool ok = true;
+        for (int c = 0; c < nchunk && ok; ++c) {
+            if (c > 0 && !mbar_wait(drained, (c - 1) & 1, flag)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int kbe = min(J.nkb, (c + 1) * kbc);
+            for (int kb = c * kbc; kb < kbe; ++kb) {
+                if (!mbar_wait(full, kb & 1, flag)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t base = smem_u32(smem);
+                const bool first_kb = kb == c * kbc;
+#pragma unroll
+                for (int kk = 0; kk < TBK / 16; ++kk) {
+                    const uint64_t o = (uint64_t)((kk * 32) >> 4);
+#pragma unroll
+                    for (int l = 0; l < XSL; ++l)
+#pragma unroll
+                        for (int i = 0; i <= l; ++i) {
+                            const uint64_t a = smem_desc_sw128(base + i * TILE_A) + o;
+                            const uint64_t b = smem_desc_sw128(base + XSL * TILE_A + (l - i) * TILE_B) + o;
+                            mma_bf16(tmem + (uint32_t)(l * TBN), a, b, idesc, (!first_kb || kk || i) ? 1u : 0u);
+                        }
+                }
+                mma_commit(empty);
+            }
+            mma_commit(accum);
+        }
+    } else if (warp >= 2) {
+        const int q = warp & 3;
+        const int row = m0 + 32 * q + lane;
+        const int er = row < J.M ? J.ea[row] : 0;
+        const uint32_t lanes = (uint32_t)(32 * q) << 16;
+        for (int c = 0; c < nchunk; ++c) {
+            if (!mbar_wait(accum, c & 1, flag)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const bool add = c > 0 || J.out.accumulate;
+            for (int cc = 0; cc < TBN; cc += 8) {
+                float S[XSL][8];
+#pragma unroll
+                for (int l = 0; l < XSL; ++l) tmem_ld8(tmem + lanes + (uint32_t)(l * TBN + cc), S[l]);
+                if (row >= J.M) continue;
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int col = n0 + cc + jj;
+                    if (col >= J.N) continue;
+                    // exact level sums (integers below 2^24), recombined by Horner steps in int64
+                    long long hi = 0, lo = 0;
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) hi = hi * 128 + (long long)__float2int_rn(S[l][jj]);
+#pragma unroll
+                    for (int l = 4; l < 8; ++l) lo = lo * 128 + (long long)__float2int_rn(S[l][jj]);
+                    // sum_l S_l 2^(-7(l+2)) = hi 2^-35 + lo 2^-63
+                    const double v = ldexp(fma((double)hi, 0x1p-35, (double)lo * 0x1p-63), er + J.eb[col]);
+                    double* o = (double*)J.out.p +
+                                (J.transposed ? (int64_t)col * J.out.ld + row : (int64_t)row * J.out.ld + col);
+                    *o = add ? *o + v : v;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(drained)) : "memory");
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(XTMEM));
+    }
+}
+
+struct X64Ptrs {
+    __nv_bfloat16* p[XSL];
+};
+
+// The digits of one entry from V = round(x 2^(56 - E)) (|V| < 2^55): balanced base-128
+// digits taken from the least significant by integer steps (V - d is a multiple of 128,
+// so the arithmetic shift is an exact division); one FP64 multiply and one conversion an
+// entry, the rest on the integer pipe.
+__device__ __forceinline__ void x64_digits(double x_scaled, int64_t at, const X64Ptrs& d) {
+    long long V = __double2ll_rn(x_scaled);
+#pragma unroll
+    for (int i = XSL - 1; i > 0; --i) {
+        int r = (int)(V & 127);
+        if (r >= 64) r -= 128;
+        d.p[i][at] = __int2bfloat16_rn(r);
+        V = (V - r) >> 7;
+    }
+    d.p[0][at] = __int2bfloat16_rn((int)V);
+}
+// |x| as an integer: non-negative doubles order like their bit patterns
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// One CTA per row i of a K-contiguous source x(i, k) = src[i*si + k], scaled by rs[i] if
+// given. E = exponent with max_k |x| in [2^(E-2), 2^(E-1)), so that x 2^-E lies in
+// (-1/2, 1/2) and its digits in [-64, 64]; zero digits past cols.
+__global__ void __launch_bounds__(128) k_split_x64(const double* __restrict__ src, int64_t rows, int64_t cols,
+                                                   int64_t si, const double* __restrict__ rs, int64_t kpad, X64Ptrs d,
+                                                   int* __restrict__ exps) {
+    __shared__ unsigned long long s_mb[4];
+    const int64_t i = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long mb = 0;
+    for (int64_t k = threadIdx.x; k < cols; k += blockDim.x) mb = max(mb, abs_bits(src[i * si + k]));
+    for (int o = 16; o; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    if (lane == 0) s_mb[warp] = mb;
+    __syncthreads();
+    mb = max(max(s_mb[0], s_mb[1]), max(s_mb[2], s_mb[3]));
+    const double sc = rs ? fabs(rs[i]) : 1.0;
+    const double mx = sc * __longlong_as_double((long long)mb);
+    const int E = mx > 0.0 ? ilogb(mx) + 2 : 0;
+    if (threadIdx.x == 0) exps[i] = E;
+    const double f = (rs ? rs[i] : 1.0) * ldexp(1.0, 56 - E);
+    for (int64_t k = threadIdx.x; k < kpad; k += blockDim.x)
+        x64_digits(k < cols ? src[i * si + k] * f : 0.0, i * kpad + k, d);
+}
+
+// ---------------------------------------------------------------------------
 // operand preparation: FP64 rows -> exponent + 6-bit head + three-part rest
 // ---------------------------------------------------------------------------
 
@@ -387,6 +613,27 @@ struct Arena {
         f.e = get<int>(rows_total);
         return f;
     }
+    // an operand in exact-slice form: eight digit matrices (rows x kpad) and a row exponent
+    struct X64 {
+        X64Ptrs d{};
+        int* e = nullptr;
+        int64_t rows = 0, kpad = 0;
+        bool ok() const {
+            for (int i = 0; i < XSL; ++i)
+                if (!d.p[i]) return false;
+            return e != nullptr;
+        }
+    };
+    X64 x64(int64_t rows, int64_t kpad) {
+        X64 x;
+        // one allocation for the eight slices
+        __nv_bfloat16* base = get<__nv_bfloat16>((int64_t)XSL * rows * kpad);
+        for (int i = 0; i < XSL; ++i) x.d.p[i] = base ? base + (int64_t)i * rows * kpad : nullptr;
+        x.e = get<int>(rows);
+        x.rows = rows;
+        x.kpad = kpad;
+        return x;
+    }
     ~Arena() {
         for (void* p : ptrs) cudaFreeAsync(p, st);
     }
@@ -448,6 +695,67 @@ int gemm_fx(const Fx& A, int64_t M, int64_t batchA, const Fx& B, int64_t N, int6
             if (e != cudaSuccess) return tc_err(err, std::string("tc gemm launch: ") + cudaGetErrorString(e));
         }
     }
+    return LS_OK;
+}
+
+// rows of x(i, k) = src[i*si + k] times rs[i] (if given) into exact-slice form
+cudaError_t launch_split_x64(const double* src, int64_t rows, int64_t cols, int64_t si, const double* rs,
+                             const Arena::X64& d, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    k_split_x64<<<(unsigned)rows, 128, 0, st>>>(src, rows, cols, si, rs, d.kpad, d.d, d.e);
+    count_kernels(1);
+    return cudaGetLastError();
+}
+
+// one product of a group: D (+)= A B^T, A: M x kpad, B: N x kpad (exact-slice form)
+struct X64Spec {
+    const Arena::X64* A;
+    const Arena::X64* B;
+    int64_t M, N;
+    TcOut out;
+    int transposed;
+};
+
+// up to kX64MaxJobs products in one launch; out.mode must be OUT_F64
+int gemm_x64(const X64Spec* sp, int n, int* flag, cudaStream_t st, std::string* err) {
+    if (n < 1) return LS_OK;
+    if (n > kX64MaxJobs) return tc_err(err, "x64 gemm: too many products", LS_ERR_ARG);
+    X64Group g;
+    memset(&g, 0, sizeof g);
+    int blocks = 0;
+    for (int i = 0; i < n; ++i) {
+        const X64Spec& s0 = sp[i];
+        const int64_t kpad = s0.A->kpad;
+        if (kpad % TBK != 0 || s0.B->kpad != kpad || s0.out.mode != OUT_F64)
+            return tc_err(err, "x64 gemm: bad operands", LS_ERR_ARG);
+        X64Job& J = g.j[i];
+        for (int q = 0; q < XSL; ++q)
+            if (!make_map(&J.a[q], s0.A->d.p[q], s0.M, kpad, 1, TBM) || !make_map(&J.b[q], s0.B->d.p[q], s0.N, kpad, 1, TBN))
+                return tc_err(err, "x64 gemm: cuTensorMapEncodeTiled failed");
+        J.M = (int)s0.M;
+        J.N = (int)s0.N;
+        J.nkb = (int)(kpad / TBK);
+        J.tiles_n = (int)((s0.N + TBN - 1) / TBN);
+        J.b0 = blocks;
+        J.transposed = s0.transposed;
+        J.ea = s0.A->e;
+        J.eb = s0.B->e;
+        J.out = s0.out;
+        blocks += (int)((s0.M + TBM - 1) / TBM) * J.tiles_n;
+    }
+    g.n = n;
+    if (blocks == 0) return LS_OK;
+    const size_t smem = XSTAGE + 1024 + 256;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [&] {
+        attr_err = cudaFuncSetAttribute(k_x64_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr_err != cudaSuccess) return tc_err(err, "x64 gemm: cannot reserve shared memory");
+    k_x64_gemm<<<blocks, TC_THREADS, smem, st>>>(g, flag);
+    count_kernels(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return tc_err(err, std::string("x64 gemm launch: ") + cudaGetErrorString(e));
     return LS_OK;
 }
 
@@ -552,6 +860,82 @@ int tc_eval(const double* const Z[3], const int32_t* r, const double* B, int64_t
     // S_s[x][y] = sum_a Z0^T[x][a] T_s^T[y][a]
     TcOut o2{out, N, N * N, out_f32 ? OUT_F32 : OUT_F64, 0};
     rc = gemm_fx(z0t, N, 1, tt, N, nslab, k0, nslab, o2, fl.d, st, err);
+    if (rc != LS_OK) return rc;
+    return fl.check(err);
+}
+
+// FP64-grade products on the tensor cores (exact slices) -------------------
+// G_l = diag(w_l) A_l A_l^T diag(w_l), A_l: C_l rows of length N
+int x64_gram(int n, const double* const a[], const int64_t C[], int64_t N, const double* const w[], double* const G[],
+             int* flag, cudaStream_t st, std::string* err) {
+    Arena ar(st);
+    std::vector<Arena::X64> xs(n);
+    std::vector<X64Spec> sp(n);
+    for (int l = 0; l < n; ++l) {
+        xs[l] = ar.x64(C[l], pad64(N));
+        if (!xs[l].ok()) return tc_err(err, "x64_gram: out of memory", LS_ERR_OOM);
+        if (launch_split_x64(a[l], C[l], N, N, w ? w[l] : nullptr, xs[l], st) != cudaSuccess)
+            return tc_err(err, "x64_gram: split failed");
+    }
+    for (int l = 0; l < n; ++l) sp[l] = X64Spec{&xs[l], &xs[l], C[l], C[l], TcOut{G[l], C[l], 0, OUT_F64, 0}, 0};
+    return gemm_x64(sp.data(), n, flag, st, err);
+}
+
+// P_l = Z_l A_l^T: Z_l r_l x N, A_l C_l x N (rows), P_l r_l x C_l
+int x64_project(int n, const double* const Z[], const int r[], const double* const a[], const int64_t C[], int64_t N,
+                double* const P[], int* flag, cudaStream_t st, std::string* err) {
+    Arena ar(st);
+    const int64_t kp = pad64(N);
+    std::vector<Arena::X64> zs(n), as(n);
+    std::vector<X64Spec> sp(n);
+    for (int l = 0; l < n; ++l) {
+        zs[l] = ar.x64(r[l], kp);
+        as[l] = ar.x64(C[l], kp);
+        if (!zs[l].ok() || !as[l].ok()) return tc_err(err, "x64_project: out of memory", LS_ERR_OOM);
+        if (launch_split_x64(Z[l], r[l], N, N, nullptr, zs[l], st) != cudaSuccess ||
+            launch_split_x64(a[l], C[l], N, N, nullptr, as[l], st) != cudaSuccess)
+            return tc_err(err, "x64_project: split failed");
+        sp[l] = X64Spec{&zs[l], &as[l], r[l], C[l], TcOut{P[l], C[l], 0, OUT_F64, 0}, 0};
+    }
+    return gemm_x64(sp.data(), n, flag, st, err);
+}
+
+// dst_l = T_l src_l: T_l r_l x r_l, src_l and dst_l r_l x N (rows). Computed as
+// dst^T = src^T T^T (src transposed first) with a transposed store: each epilogue warp
+// writes 32 consecutive entries of a row of dst.
+int x64_apply(int n, const double* const T[], const int r[], const double* const src[], int64_t N,
+              double* const dst[], int* flag, cudaStream_t st, std::string* err) {
+    Arena ar(st);
+    std::vector<Arena::X64> ss(n), ts(n);
+    std::vector<X64Spec> sp(n);
+    for (int l = 0; l < n; ++l) {
+        const int64_t kp = pad64(r[l]);
+        double* srcT = ar.get<double>(N * r[l]);
+        ss[l] = ar.x64(N, kp);
+        ts[l] = ar.x64(r[l], kp);
+        if (!srcT || !ss[l].ok() || !ts[l].ok()) return tc_err(err, "x64_apply: out of memory", LS_ERR_OOM);
+        if (launch_transpose(src[l], r[l], N, srcT, st) != cudaSuccess ||
+            launch_split_x64(srcT, N, r[l], r[l], nullptr, ss[l], st) != cudaSuccess ||
+            launch_split_x64(T[l], r[l], r[l], r[l], nullptr, ts[l], st) != cudaSuccess)
+            return tc_err(err, "x64_apply: split failed");
+        sp[l] = X64Spec{&ss[l], &ts[l], N, r[l], TcOut{dst[l], N, 0, OUT_F64, 0}, 1};
+    }
+    return gemm_x64(sp.data(), n, flag, st, err);
+}
+
+// D = A B^T (A: M x K, B: N x K, D: M x N, row-major), then a synchronised status check
+int x64_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* D, cudaStream_t st,
+                std::string* err) {
+    Arena ar(st);
+    Flag fl(ar, st);
+    const int64_t kp = pad64(std::max<int64_t>(K, 1));
+    Arena::X64 as = ar.x64(M, kp), bs = ar.x64(N, kp);
+    if (!fl.d || !as.ok() || !bs.ok()) return tc_err(err, "gemm_nt: out of memory", LS_ERR_OOM);
+    if (launch_split_x64(A, M, K, K, nullptr, as, st) != cudaSuccess ||
+        launch_split_x64(B, N, K, K, nullptr, bs, st) != cudaSuccess)
+        return tc_err(err, "gemm_nt: split failed");
+    X64Spec sp{&as, &bs, M, N, TcOut{D, N, 0, OUT_F64, 0}, 0};
+    int rc = gemm_x64(&sp, 1, fl.d, st, err);
     if (rc != LS_OK) return rc;
     return fl.check(err);
 }

@@ -26,7 +26,7 @@ LS_OUT_F64, LS_OUT_F32 = 0, 1
 EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_create", "lattice_sum_add_defects",
             "lattice_sum_rhosvd_reduce", "lattice_sum_eval_slab", "lattice_sum_get_factors",
             "lattice_sum_read", "lattice_sum_profile", "lattice_sum_profile_report",
-            "lattice_sum_eval_slab_noalloc", "lattice_sum_batch_reduce",
+            "lattice_sum_eval_slab_noalloc", "lattice_sum_batch_reduce", "lattice_sum_gemm_nt",
             "lattice_sum_destroy", "lattice_sum_last_error")
 
 
@@ -84,6 +84,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                                   P(C.c_int32), C.c_int64, P(C.c_int64), C.c_int32,
                                                   C.c_void_p, C.c_int32, C.c_void_p]
     lib.lattice_sum_batch_reduce.argtypes = [P(C.c_void_p), C.c_int32, C.c_double, P(ls_tucker_info)]
+    lib.lattice_sum_gemm_nt.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
+                                        C.c_void_p]
     lib.lattice_sum_destroy.argtypes = [C.c_void_p]
     lib.lattice_sum_destroy.restype = None
     lib.lattice_sum_last_error.argtypes = [C.c_void_p]
@@ -151,6 +153,22 @@ def batch_reduce(contexts, eps: float):
         c.info = inf.as_dict()
         out.append(c.info)
     return out
+
+
+def gemm_nt(A, B):
+    """D = A B^T for float64 CUDA tensors (A: M x K, B: N x K) in the library's FP64-grade
+    exact-slice tensor-core arithmetic (lattice_sum_gemm_nt)."""
+    import torch
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    N, K2 = B.shape
+    if K2 != K or A.dtype != torch.float64 or B.dtype != torch.float64:
+        raise ValueError("gemm_nt: A (M x K) and B (N x K) must be float64 with the same K")
+    D = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    _check(lib().lattice_sum_gemm_nt(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()), C.c_int64(M),
+                                     C.c_int64(N), C.c_int64(K), C.c_void_p(D.data_ptr()), None))
+    return D
 
 
 def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float):
