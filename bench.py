@@ -498,9 +498,39 @@ def main():
         return {"value": world * wl.units / (sum(times) / n), "unit": "potentials/s",
                 "h2d_bytes_per_step": int(rep["h2d_bytes"] // n), "d2h_bytes_per_step": int(rep["d2h_bytes"] // n)}
 
+    def eval_timing(prec):
+        """Step (d) on its own: the workload's slabs from one reduced context, FP32 output on the
+        mixed path (FP64 on the FP64 path), CUDA events on the library stream after warm-up."""
+        zs = list(wl.slabs or [wl.N // 2])
+        f32 = prec == L.LS_MIXED
+        ls = L.LatticeSum.from_workload(wl, s, prec, stream=stream.cuda_stream)
+        ls.add_defects(wl.defects)
+        ls.rhosvd_reduce(wl.eps)
+        out = torch.empty((len(zs), wl.N, wl.N), dtype=torch.float32 if f32 else torch.float64, device="cuda")
+        reps = 5
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                ls.eval_slab_torch(zs, dtype=out.dtype, out=out)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                ls.eval_slab_torch(zs, dtype=out.dtype, out=out)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        ls.close()
+        pts = len(zs) * wl.N * wl.N
+        written = pts * out.element_size()
+        gbs = written / (ms * 1e-3) / 1e9
+        hbm = peaks.get("hbm_gbs")
+        return {"slabs": len(zs), "N": wl.N, "dtype": "f32" if f32 else "f64", "ms": ms,
+                "points_per_s": pts / (ms * 1e-3), "bytes_written": written, "write_gbs": gbs,
+                "frac_of_measured_hbm": gbs / hbm if hbm else None}
+
     head_prec = L.LS_MIXED if args.precision == "mixed" else L.LS_FP64
     head = timed(head_prec, True)
     head_e2e = e2e(head_prec)
+    head_eval = eval_timing(head_prec)
     other = None
     agreement = None
     if args.precision == "mixed" and not args.no_compare:
@@ -547,6 +577,7 @@ def main():
         "clocks": head["clocks"],
         "steps_ms": {k: v["ms"] / args.steps for k, v in head["report"].get("steps", {}).items()},
         "wall_s_timed_region": head["wall"],
+        "eval_slab": head_eval,
     }
     if other is not None:
         line["fp64_path"] = {"value": other["value"], "ms_per_step": other["ms_per_step"],

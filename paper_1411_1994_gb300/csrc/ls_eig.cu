@@ -388,6 +388,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
     float* qrem = reinterpret_cast<float*>(smem + Ly.qrem);
     float* F = reinterpret_cast<float*>(smem + Ly.F);
     __shared__ unsigned int s_active;
+    __shared__ int s_act[64];   // pair-block rotated this round (its Q differs from I)
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
     const Crit qualifies{(float)J.abs_floor, (float)J.tau, (float)(J.tol * J.tol)};
@@ -448,6 +449,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
                         int I, Jb;
                         rr_pair_e(t, tid, m, I, Jb);
                         pb[tid] = I | (Jb << 16);
+                        s_act[tid] = 0;
                     }
                     unsigned int cnt = 0;
                     __syncthreads();
@@ -475,6 +477,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
                                     D[q] = df_add(D[q], te);
                                     E[p * ldE + q] = 0.f;
                                     E[q * ldE + p] = 0.f;
+                                    s_act[sub] = 1;
                                     ++cnt;
                                 }
                             }
@@ -542,6 +545,9 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
                     const bool live = task < ntile;
                     const int ab = live ? tiles[task] : tiles[task0];
                     const int a = ab & 255, b = ab >> 8;
+                    // a tile between two pair-blocks that did not rotate is unchanged (Q = I on both
+                    // sides); the warp skips when both of its tiles are such
+                    if (__all_sync(0xffffffffu, !live || (!s_act[a] && !s_act[b]))) continue;
                     const int Ia = pb[a] & 0xffff, Ja = pb[a] >> 16, Ib = pb[b] & 0xffff, Jb2 = pb[b] >> 16;
                     const float* Qa = Q + a * BJ2SQ;
                     const float* Qb = Q + b * BJ2SQ;
@@ -615,9 +621,15 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
                     int Ia, Ja;
                     rr_pair_e(t, a, m, Ia, Ja);
                     float fcol[BJ2];
+                    bool nz = false;
 #pragma unroll
-                    for (int y = 0; y < BJ2; ++y) fcol[y] = fqs[a * BJ2SQ + y * BJ2 + x];
-                    for (int jl = g; jl < nr; jl += groups) {
+                    for (int y = 0; y < BJ2; ++y) {
+                        fcol[y] = fqs[a * BJ2SQ + y * BJ2 + x];
+                        nz |= fcol[y] != 0.f;
+                    }
+                    // F_Q = 0 (no rotation in this pair-block): F is unchanged
+                    const bool any = __any_sync(half, nz);
+                    for (int jl = g; jl < nr && any; jl += groups) {
                         const int j = j0 + jl;
                         float* row = F + (size_t)jl * K;
                         const float4 f0 = *reinterpret_cast<const float4*>(row + Ia * BJ);
