@@ -500,12 +500,14 @@ def main():
 
     def eval_timing(prec):
         """Step (d) on its own: the workload's slabs from one reduced context, FP32 output on the
-        mixed path (FP64 on the FP64 path), CUDA events on the library stream after warm-up."""
+        mixed path (FP64 on the FP64 path), CUDA events on the library stream after warm-up; then
+        one traced pass for the split between the small products and the slab product."""
         zs = list(wl.slabs or [wl.N // 2])
         f32 = prec == L.LS_MIXED
         ls = L.LatticeSum.from_workload(wl, s, prec, stream=stream.cuda_stream)
         ls.add_defects(wl.defects)
-        ls.rhosvd_reduce(wl.eps)
+        info = ls.rhosvd_reduce(wl.eps)
+        r0, r1, r2 = info["r"]
         out = torch.empty((len(zs), wl.N, wl.N), dtype=torch.float32 if f32 else torch.float64, device="cuda")
         reps = 5
         with torch.cuda.stream(stream):
@@ -518,14 +520,38 @@ def main():
             e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
+        L.profile(True)
+        with torch.cuda.stream(stream):
+            for _ in range(reps):
+                ls.eval_slab_torch(zs, dtype=out.dtype, out=out)
+        torch.cuda.synchronize()
+        L.profile(False)
+        steps = L.profile_report().get("steps", {})
         ls.close()
-        pts = len(zs) * wl.N * wl.N
+        ns, N = len(zs), wl.N
+        pts = ns * N * N
         written = pts * out.element_size()
-        gbs = written / (ms * 1e-3) / 1e9
         hbm = peaks.get("hbm_gbs")
-        return {"slabs": len(zs), "N": wl.N, "dtype": "f32" if f32 else "f64", "ms": ms,
-                "points_per_s": pts / (ms * 1e-3), "bytes_written": written, "write_gbs": gbs,
-                "frac_of_measured_hbm": gbs / hbm if hbm else None}
+        bf16 = peaks.get("bf16_tflops")
+        # algorithmic flops per slab: 2 r0 r1 r2 (M) + 2 N r0 r1 (T) + 2 N^2 r0 (S)
+        flops = ns * (2.0 * r0 * r1 * r2 + 2.0 * N * r0 * r1 + 2.0 * N * N * r0)
+        res = {"slabs": ns, "N": N, "ranks": [r0, r1, r2], "dtype": "f32" if f32 else "f64", "ms": ms,
+               "points_per_s": pts / (ms * 1e-3), "bytes_written": written,
+               "write_gbs": written / (ms * 1e-3) / 1e9, "algorithmic_tflops": flops / (ms * 1e-3) / 1e12,
+               "steps_ms": {k: v["ms"] / reps for k, v in steps.items() if k.startswith("eval")}}
+        sl = steps.get("eval.slab")
+        if sl and f32:
+            # the slab product S_s = T_s x1 Z0 alone: its flops, its writes, and the tensor-pipe
+            # work of its 11 FP16 products a k-step (the split form's overhead, not counted as work)
+            t = sl["ms"] / reps * 1e-3
+            fl = ns * 2.0 * N * N * r0
+            ach = fl / t / 1e12
+            res["slab_product"] = {
+                "kernel": "k_dt_gemm (S_s = T_s x1 Z0)", "ms": t * 1e3, "launches": sl["kernels"] / reps,
+                "achieved_tflops": ach, "bf16_peak_tflops": bf16, "frac_of_measured_bf16": ach / bf16 if bf16 else None,
+                "products_per_kstep": 11, "tensor_pipe_frac": 11 * ach / bf16 if bf16 else None,
+                "write_gbs": written / t / 1e9, "frac_of_measured_hbm": written / t / 1e9 / hbm if hbm else None}
+        return res
 
     head_prec = L.LS_MIXED if args.precision == "mixed" else L.LS_FP64
     head = timed(head_prec, True)

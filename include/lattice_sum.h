@@ -237,12 +237,39 @@ int lattice_sum_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, 
                         void* stream);
 
 /*
+ * lattice_sum_gemm_nt_mixed -- D = A B^T for device FP64 matrices (A: M x K,
+ * B: N x K, row-major; K <= 2048) in the arithmetic of the mixed slab
+ * evaluation. Each operand row is scaled by a power of two to (-64, 64) and
+ * written as d0 + d1 2^-7 + t1 + t2: d0, d1 nearest integers in [-64, 64],
+ * t1 and t2 11-bit rests, all stored exactly as FP16 (times 2^9). The form
+ * is good to 2^-36 of the row's scale.
+ * On tcgen05 tensor cores the level-0 products d0 d0 and the level-1
+ * products (d0 d1 + d1 d0) 2^-7 accumulate EXACTLY in FP32 (integers below
+ * 2^24 in their units). The eight products below them go to a third
+ * accumulator, whose rounding (the tensor cores' adds truncate) sits below
+ * 2^-14 of the result.
+ * Error: about 2^-32 of max_k|a_mk| max_k|b_nk| per term, from the dropped
+ * d1 t2 and t2 d1 products.
+ * D (device, M x N row-major) is LS_OUT_F32 (the exact sum rounded once) or
+ * LS_OUT_F64 per `out_dtype`. `tile_n` picks the output tile width (32, 64,
+ * 128; 0 = by size). `stream` is a cudaStream_t or NULL; the call
+ * synchronises it. Errors: LS_ERR_ARG, LS_ERR_OOM, LS_ERR_CUDA,
+ * LS_ERR_TIMEOUT.
+ */
+int lattice_sum_gemm_nt_mixed(const double* A, const double* B, int64_t M, int64_t N, int64_t K, void* D,
+                              int32_t out_dtype, int32_t tile_n, void* stream);
+
+/*
  * lattice_sum_eval_slab -- Tucker tensor values on z-slabs.
  * Eq. (Tucker_singePot): for each z index i3, M = B x3 Z3[:, i3] and
  * out[s][i1][i2] = sum_{a,b} Z1[a][i1] M[a][b] Z2[b][i2] (i2 fastest).
  * `z_index` is host memory (nslab entries in [0, N)); `out_dev` is device
  * memory of nslab * N * N elements of `out_dtype` (LS_OUT_F64/LS_OUT_F32),
- * owned by the caller. Asynchronous on the context's stream.
+ * owned by the caller. LS_FP64 contexts: FP64 products, asynchronous on the
+ * context's stream. LS_MIXED contexts: the three products on tcgen05 tensor
+ * cores in the arithmetic of lattice_sum_gemm_nt_mixed, with
+ * the core and the side matrices in that form kept in the context after the
+ * first call; the call synchronises the stream to read the kernels' status.
  * Errors: LS_ERR_ARG, LS_ERR_STATE (before the reduction), LS_ERR_OOM,
  * LS_ERR_CUDA.
  */

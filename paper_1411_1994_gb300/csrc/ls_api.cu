@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "ls_common.cuh"
+#include "ls_eval.cuh"
 #include "ls_tc.cuh"
 
 using namespace ls;
@@ -60,30 +61,6 @@ Tracer& tracer() {
     static Tracer* t = new Tracer();
     return *t;
 }
-
-// Records an event pair around a step on a stream when tracing is on.
-struct Scope {
-    const char* name;
-    cudaStream_t st;
-    cudaEvent_t a = nullptr;
-    long long k0 = 0;
-    Scope(const char* n, cudaStream_t s) : name(n), st(s) {
-        Tracer& t = tracer();
-        if (!t.on) return;
-        std::lock_guard<std::mutex> g(t.mu);
-        a = t.get();
-        k0 = t.kernels.load();
-        cudaEventRecord(a, st);
-    }
-    ~Scope() {
-        if (!a) return;
-        Tracer& t = tracer();
-        std::lock_guard<std::mutex> g(t.mu);
-        cudaEvent_t b = t.get();
-        cudaEventRecord(b, st);
-        t.recs.push_back({name, a, b, (int)(t.kernels.load() - k0)});
-    }
-};
 
 void count_h2d(int64_t n) { tracer().h2d += n; }
 void count_d2h(int64_t n) { tracer().d2h += n; }
@@ -128,6 +105,7 @@ struct ls_ctx {
     int32_t* d_tcol = nullptr;
     double* d_xi = nullptr;
     double* d_xin = nullptr;
+    DtEvalCache* eval_cache = nullptr;   // tensor-core operands of the slab evaluation
     std::vector<void*> allocs;
 };
 
@@ -264,6 +242,24 @@ double quad_max_err(int R, double hs, double s, const std::vector<double>& r) {
 namespace ls {
 void count_kernels(int n) { tracer().kernels += n; }
 void set_global_error(const char* msg) { g_create_error = msg; }
+
+Scope::Scope(const char* n, cudaStream_t s) : name(n), st(s) {
+    Tracer& t = tracer();
+    if (!t.on) return;
+    std::lock_guard<std::mutex> g(t.mu);
+    a = t.get();
+    k0 = t.kernels.load();
+    cudaEventRecord(a, st);
+}
+
+Scope::~Scope() {
+    if (!a) return;
+    Tracer& t = tracer();
+    std::lock_guard<std::mutex> g(t.mu);
+    cudaEvent_t b = t.get();
+    cudaEventRecord(b, st);
+    t.recs.push_back({name, a, b, (int)(t.kernels.load() - k0)});
+}
 }  // namespace ls
 
 extern "C" {
@@ -1093,6 +1089,19 @@ int lattice_sum_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, 
     return LS_OK;
 }
 
+int lattice_sum_gemm_nt_mixed(const double* A, const double* B, int64_t M, int64_t N, int64_t K, void* D,
+                              int32_t out_dtype, int32_t tile_n, void* stream) {
+    if (!A || !B || !D || M < 0 || N < 0 || K < 1 || M > INT32_MAX || N > INT32_MAX ||
+        (out_dtype != LS_OUT_F64 && out_dtype != LS_OUT_F32))
+        return fail(nullptr, LS_ERR_ARG, "gemm_nt_mixed: bad arguments");
+    std::string err;
+    DtOpts o;
+    o.tile_n = tile_n;
+    int rc = dt_gemm_nt(A, B, M, N, K, D, out_dtype == LS_OUT_F32, o, static_cast<cudaStream_t>(stream), &err);
+    if (rc != LS_OK) return fail(nullptr, rc, "gemm_nt_mixed: %s", err.c_str());
+    return LS_OK;
+}
+
 int lattice_sum_eval_slab(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev, int32_t out_dtype) {
     if (!ctx) return fail(nullptr, LS_ERR_ARG, "eval_slab: NULL context");
     if (!ctx->reduced) return fail(ctx, LS_ERR_STATE, "eval_slab: call rhosvd_reduce first");
@@ -1106,28 +1115,29 @@ int lattice_sum_eval_slab(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, vo
         z[s] = (int32_t)z_index[s];
     }
     cudaStream_t st = ctx->st;
-    // slabs in chunks that bound the work buffer to ~256 MB
-    const int64_t per = (int64_t)ctx->r[0] * ctx->r[1] + (int64_t)ctx->r[0] * N;
-    int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(nslab, (int64_t)(32 << 20) / std::max<int64_t>(per, 1)));
     int32_t* d_z = nullptr;
-    double* work = nullptr;
     CU(dalloc(ctx, &d_z, nslab));
-    CU(dalloc(ctx, &work, per * chunk));
     CU(cudaMemcpyAsync(d_z, z.data(), nslab * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     count_h2d((int64_t)(nslab * sizeof(int32_t)));
-    const size_t esz = out_dtype == LS_OUT_F32 ? 4 : 8;
     const double* Zc[3] = {ctx->d_Z[0], ctx->d_Z[1], ctx->d_Z[2]};
     Scope sc_eval("eval", st);
+    if (ctx->p.precision == LS_MIXED) {
+        // the three products on the tensor cores (two exact digits + two tails)
+        int rc = dt_eval(&ctx->eval_cache, Zc, ctx->r, ctx->d_B, N, d_z, nslab, out_dev, out_dtype == LS_OUT_F32,
+                         DtOpts{}, st, &ctx->err);
+        dfree(ctx, d_z);
+        return rc;
+    }
+    // FP64: slabs in chunks that bound the work buffer to ~256 MB
+    const int64_t per = (int64_t)ctx->r[0] * ctx->r[1] + (int64_t)ctx->r[0] * N;
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(nslab, (int64_t)(32 << 20) / std::max<int64_t>(per, 1)));
+    double* work = nullptr;
+    CU(dalloc(ctx, &work, per * chunk));
+    const size_t esz = out_dtype == LS_OUT_F32 ? 4 : 8;
     for (int s0 = 0; s0 < nslab; s0 += chunk) {
         const int ns = std::min(chunk, nslab - s0);
         char* o = static_cast<char*>(out_dev) + (size_t)s0 * N * N * esz;
-        if (ctx->p.precision == LS_MIXED) {
-            int rc = tc_eval(Zc, ctx->r, ctx->d_B, N, d_z + s0, ns, work, o, out_dtype == LS_OUT_F32, ctx->num_sms, st,
-                             &ctx->err);
-            if (rc != LS_OK) return rc;
-        } else {
-            CU(launch_eval_f64(Zc, ctx->r, ctx->d_B, N, d_z + s0, ns, work, o, out_dtype == LS_OUT_F32, st));
-        }
+        CU(launch_eval_f64(Zc, ctx->r, ctx->d_B, N, d_z + s0, ns, work, o, out_dtype == LS_OUT_F32, st));
     }
     dfree(ctx, work);
     dfree(ctx, d_z);
@@ -1237,6 +1247,7 @@ int lattice_sum_profile_report(char* buf, int64_t cap, int64_t* needed_bytes) {
 
 void lattice_sum_destroy(ls_ctx* ctx) {
     if (!ctx) return;
+    dt_eval_free(ctx->eval_cache);
     for (void* p : ctx->allocs) cudaFreeAsync(p, ctx->st);
     ctx->allocs.clear();
     delete ctx;

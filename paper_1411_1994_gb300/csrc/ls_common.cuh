@@ -36,6 +36,19 @@ struct DevStatus {
 // ---------------------------------------------------------------------------
 void count_kernels(int n);
 
+// Records a CUDA-event pair around a step on a stream while tracing is on
+// (lattice_sum_profile); the pairs are reported by name.
+struct Scope {
+    const char* name;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    long long k0 = 0;
+    Scope(const char* n, cudaStream_t s);
+    ~Scope();
+    Scope(const Scope&) = delete;
+    Scope& operator=(const Scope&) = delete;
+};
+
 // message returned by lattice_sum_last_error(NULL) (calls without a context)
 void set_global_error(const char* msg);
 

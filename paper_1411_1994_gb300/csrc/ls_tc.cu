@@ -23,8 +23,7 @@
 // the copies it issued, frees its TMEM and returns.
 //
 // Uses: projection P = Z A^T (Def. 4.1 / Thm A.1(c)), the dense second step of
-// the core contraction (Thm A.1(c)), and the two n-mode products of slab
-// evaluation (Eq. Tucker_singePot).
+// the core contraction (Thm A.1(c)).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -39,10 +38,13 @@
 #include "lattice_sum.h"
 #include "ls_common.cuh"
 #include "ls_tc.cuh"
+#include "ls_tcgen05.cuh"
 
 namespace ls {
 
 namespace {
+
+using namespace tc5;
 
 constexpr int TBM = 128, TBN = 64, TBK = 64, TSTAGES = 2, NPART = 4;   // parts: h, m, rest0, rest1
 constexpr int TILE_A = TBM * TBK * 2;          // bytes of one bf16 A tile (16 KB)
@@ -51,7 +53,6 @@ constexpr int STAGE_BYTES = NPART * (TILE_A + TILE_B);
 constexpr int TC_THREADS = 192;                // warp 0 TMA, warp 1 MMA + TMEM, warps 2-5 epilogue
 constexpr int KCHUNK = 1024;                   // K per exact head accumulation
 constexpr int TMEM_COLS = 4 * TBN;             // three FP32 accumulators (power-of-two allocation)
-constexpr long long kWaitLimit = 1LL << 22;    // try_wait polls; each may suspend briefly
 
 enum OutMode : int { OUT_F64 = 0, OUT_F32 = 1 };
 
@@ -62,96 +63,6 @@ struct TcOut {
     int mode;
     int accumulate;     // F64 only: D += result
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait; returns false (and raises the flag) on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* flag) {
-    long long it = 0;
-    while (!mbar_try_wait(bar, parity)) {
-        if (++it > kWaitLimit) {
-            atomicCAS(flag, 0, FLAG_TIMEOUT);
-            return false;
-        }
-        if (*(volatile int*)flag != 0 && it > 1024) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// K-major operand tile in 128B-swizzled shared memory: rows of 64 bf16 (128 B),
-// 8-row swizzle atoms 1024 B apart.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
-    d |= (uint64_t)(16 >> 4) << 16;                  // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8-row atom
-    d |= (uint64_t)1 << 46;                          // descriptor version for sm_100 family
-    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
-    return d;
-}
-
-// instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_fx_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
@@ -331,16 +242,6 @@ struct X64Group {
     X64Job j[kX64MaxJobs];
     int n;
 };
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // One 128 x 64 output tile of one job per CTA, all of K: the K-chunks of 512 run in
 // turn on the same eight accumulators (the MMA warp waits until the epilogue has drained
@@ -560,19 +461,6 @@ __global__ void k_split_fx(const double* __restrict__ src, int64_t rows, int64_t
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    });
-    return fn;
-}
-
 // rows x kpad bf16 matrices, `batch` of them back to back; box = box_rows x 64
 bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t kpad, int64_t batch, int box_rows) {
     auto fn = encode_fn();
@@ -595,54 +483,36 @@ struct Fx {   // one operand in split form: head + three rest parts, and a row e
     bool ok() const { return p[0] && p[1] && p[2] && p[3] && e; }
 };
 
-// one scratch arena per call, from the stream-ordered allocator
-struct Arena {
-    cudaStream_t st;
-    std::vector<void*> ptrs;
-    explicit Arena(cudaStream_t s) : st(s) {}
-    template <class T>
-    T* get(int64_t n) {
-        void* p = nullptr;
-        if (cudaMallocAsync(&p, (size_t)std::max<int64_t>(n, 1) * sizeof(T), st) != cudaSuccess) return nullptr;
-        ptrs.push_back(p);
-        return (T*)p;
-    }
-    Fx fx(int64_t rows_total, int64_t kpad) {
-        Fx f;
-        for (int i = 0; i < NPART; ++i) f.p[i] = get<__nv_bfloat16>(rows_total * kpad);
-        f.e = get<int>(rows_total);
-        return f;
-    }
-    // an operand in exact-slice form: eight digit matrices (rows x kpad) and a row exponent
-    struct X64 {
-        X64Ptrs d{};
-        int* e = nullptr;
-        int64_t rows = 0, kpad = 0;
-        bool ok() const {
-            for (int i = 0; i < XSL; ++i)
-                if (!d.p[i]) return false;
-            return e != nullptr;
-        }
-    };
-    X64 x64(int64_t rows, int64_t kpad) {
-        X64 x;
-        // one allocation for the eight slices
-        __nv_bfloat16* base = get<__nv_bfloat16>((int64_t)XSL * rows * kpad);
-        for (int i = 0; i < XSL; ++i) x.d.p[i] = base ? base + (int64_t)i * rows * kpad : nullptr;
-        x.e = get<int>(rows);
-        x.rows = rows;
-        x.kpad = kpad;
-        return x;
-    }
-    ~Arena() {
-        for (void* p : ptrs) cudaFreeAsync(p, st);
+Fx fx_alloc(Arena& ar, int64_t rows_total, int64_t kpad) {
+    Fx f;
+    for (int i = 0; i < NPART; ++i) f.p[i] = ar.get<__nv_bfloat16>(rows_total * kpad);
+    f.e = ar.get<int>(rows_total);
+    return f;
+}
+
+// an operand in exact-slice form: eight digit matrices (rows x kpad) and a row exponent
+struct X64Op {
+    X64Ptrs d{};
+    int* e = nullptr;
+    int64_t rows = 0, kpad = 0;
+    bool ok() const {
+        for (int i = 0; i < XSL; ++i)
+            if (!d.p[i]) return false;
+        return e != nullptr;
     }
 };
 
-int tc_err(std::string* err, const std::string& msg, int code = LS_ERR_CUDA) {
-    if (err) *err = msg;
-    return code;
+X64Op x64_alloc(Arena& ar, int64_t rows, int64_t kpad) {
+    X64Op x;
+    // one allocation for the eight slices
+    __nv_bfloat16* base = ar.get<__nv_bfloat16>((int64_t)XSL * rows * kpad);
+    for (int i = 0; i < XSL; ++i) x.d.p[i] = base ? base + (int64_t)i * rows * kpad : nullptr;
+    x.e = ar.get<int>(rows);
+    x.rows = rows;
+    x.kpad = kpad;
+    return x;
 }
+
 
 cudaError_t launch_split_fx(const double* src, int64_t rows, int64_t cols, int64_t si, int64_t sk, int64_t sb,
                             int64_t batch, int64_t kpad, Fx d, cudaStream_t st) {
@@ -700,7 +570,7 @@ int gemm_fx(const Fx& A, int64_t M, int64_t batchA, const Fx& B, int64_t N, int6
 
 // rows of x(i, k) = src[i*si + k] times rs[i] (if given) into exact-slice form
 cudaError_t launch_split_x64(const double* src, int64_t rows, int64_t cols, int64_t si, const double* rs,
-                             const Arena::X64& d, cudaStream_t st) {
+                             const X64Op& d, cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
     k_split_x64<<<(unsigned)rows, 128, 0, st>>>(src, rows, cols, si, rs, d.kpad, d.d, d.e);
     count_kernels(1);
@@ -709,8 +579,8 @@ cudaError_t launch_split_x64(const double* src, int64_t rows, int64_t cols, int6
 
 // one product of a group: D (+)= A B^T, A: M x kpad, B: N x kpad (exact-slice form)
 struct X64Spec {
-    const Arena::X64* A;
-    const Arena::X64* B;
+    const X64Op* A;
+    const X64Op* B;
     int64_t M, N;
     TcOut out;
     int transposed;
@@ -759,23 +629,6 @@ int gemm_x64(const X64Spec* sp, int n, int* flag, cudaStream_t st, std::string* 
     return LS_OK;
 }
 
-// device flag shared by the tensor-core kernels of one call; checked after the call
-struct Flag {
-    int* d = nullptr;
-    cudaStream_t st;
-    Flag(Arena& a, cudaStream_t s) : st(s) {
-        d = a.get<int>(1);
-        if (d) cudaMemsetAsync(d, 0, sizeof(int), st);
-    }
-    int check(std::string* err) {
-        int h = 0;
-        if (cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            return tc_err(err, "tc: status read failed");
-        if (h == FLAG_TIMEOUT) return tc_err(err, "tc gemm: a bounded mbarrier wait timed out", LS_ERR_TIMEOUT);
-        return LS_OK;
-    }
-};
 
 }  // namespace
 
@@ -784,7 +637,7 @@ int tc_project(const double* Z, int r, const double* a, int64_t C, int64_t N, do
     Arena ar(st);
     Flag fl(ar, st);
     const int64_t kp = pad64(N);
-    Fx zs = ar.fx(r, kp), as = ar.fx(C, kp);
+    Fx zs = fx_alloc(ar, r, kp), as = fx_alloc(ar, C, kp);
     if (!fl.d || !zs.ok() || !as.ok()) return tc_err(err, "tc_project: out of memory", LS_ERR_OOM);
     if (launch_split_fx(Z, r, N, N, 1, 0, 1, kp, zs, st) != cudaSuccess ||
         launch_split_fx(a, C, N, N, 1, 0, 1, kp, as, st) != cudaSuccess)
@@ -809,7 +662,7 @@ int tc_core(const double* P0, const double* P1, const double* P2, const int32_t*
     double* P1t = ar.get<double>((int64_t)C[1] * r[1]);
     double* P2t = ar.get<double>((int64_t)C[2] * r[2]);
     double* W = ar.get<double>(chunk * nn);
-    Fx w = ar.fx(nn, chunk), p0 = ar.fx(r[0], chunk);
+    Fx w = fx_alloc(ar, nn, chunk), p0 = fx_alloc(ar, r[0], chunk);
     if (!fl.d || !P1t || !P2t || !W || !w.ok() || !p0.ok()) return tc_err(err, "tc_core: out of memory", LS_ERR_OOM);
     if (launch_transpose(P1, r[1], C[1], P1t, st) != cudaSuccess || launch_transpose(P2, r[2], C[2], P2t, st) != cudaSuccess)
         return tc_err(err, "tc_core: transpose failed");
@@ -830,49 +683,15 @@ int tc_core(const double* P0, const double* P1, const double* P2, const int32_t*
     return fl.check(err);
 }
 
-int tc_eval(const double* const Z[3], const int32_t* r, const double* B, int64_t N, const int32_t* zidx, int nslab,
-            double* work, void* out, int out_f32, int num_sms, cudaStream_t st, std::string* err) {
-    (void)num_sms;
-    (void)work;
-    Arena ar(st);
-    Flag fl(ar, st);
-    const int r0 = r[0], r1 = r[1];
-    const int64_t k1 = pad64(r1), k0 = pad64(r0);
-    // M_s[a][b] = sum_k B[a][b][k] Z2[k][z_s]: small, FP64 CUDA cores
-    double* M = ar.get<double>((int64_t)r0 * r1 * nslab);
-    double* Tt = ar.get<double>((int64_t)nslab * N * r0);
-    Fx z1t = ar.fx(N, k1), z0t = ar.fx(N, k0), ms = ar.fx((int64_t)nslab * r0, k1), tt = ar.fx((int64_t)nslab * N, k0);
-    if (!fl.d || !M || !Tt || !z1t.ok() || !z0t.ok() || !ms.ok() || !tt.ok())
-        return tc_err(err, "tc_eval: out of memory", LS_ERR_OOM);
-    cudaError_t e = launch_eval_m(Z[2], r, B, N, zidx, nslab, M, st);
-    if (e != cudaSuccess) return tc_err(err, std::string("tc_eval: ") + cudaGetErrorString(e));
-    // operands: Z1^T [y][b], Z0^T [x][a] (K-major), M_s [a][b] per slab
-    if (launch_split_fx(Z[1], N, r1, 1, N, 0, 1, k1, z1t, st) != cudaSuccess ||
-        launch_split_fx(Z[0], N, r0, 1, N, 0, 1, k0, z0t, st) != cudaSuccess ||
-        launch_split_fx(M, r0, r1, (int64_t)r1 * nslab, nslab, 1, nslab, k1, ms, st) != cudaSuccess)
-        return tc_err(err, "tc_eval: split failed");
-    // T_s^T[y][a] = sum_b Z1^T[y][b] M_s[a][b]   (FP64 out)
-    TcOut o1{Tt, r0, N * r0, OUT_F64, 0};
-    int rc = gemm_fx(z1t, N, 1, ms, r0, nslab, k1, nslab, o1, fl.d, st, err);
-    if (rc != LS_OK) return rc;
-    if (launch_split_fx(Tt, N, r0, r0, 1, N * r0, nslab, k0, tt, st) != cudaSuccess)
-        return tc_err(err, "tc_eval: split failed");
-    // S_s[x][y] = sum_a Z0^T[x][a] T_s^T[y][a]
-    TcOut o2{out, N, N * N, out_f32 ? OUT_F32 : OUT_F64, 0};
-    rc = gemm_fx(z0t, N, 1, tt, N, nslab, k0, nslab, o2, fl.d, st, err);
-    if (rc != LS_OK) return rc;
-    return fl.check(err);
-}
-
 // FP64-grade products on the tensor cores (exact slices) -------------------
 // G_l = diag(w_l) A_l A_l^T diag(w_l), A_l: C_l rows of length N
 int x64_gram(int n, const double* const a[], const int64_t C[], int64_t N, const double* const w[], double* const G[],
              int* flag, cudaStream_t st, std::string* err) {
     Arena ar(st);
-    std::vector<Arena::X64> xs(n);
+    std::vector<X64Op> xs(n);
     std::vector<X64Spec> sp(n);
     for (int l = 0; l < n; ++l) {
-        xs[l] = ar.x64(C[l], pad64(N));
+        xs[l] = x64_alloc(ar, C[l], pad64(N));
         if (!xs[l].ok()) return tc_err(err, "x64_gram: out of memory", LS_ERR_OOM);
         if (launch_split_x64(a[l], C[l], N, N, w ? w[l] : nullptr, xs[l], st) != cudaSuccess)
             return tc_err(err, "x64_gram: split failed");
@@ -886,11 +705,11 @@ int x64_project(int n, const double* const Z[], const int r[], const double* con
                 double* const P[], int* flag, cudaStream_t st, std::string* err) {
     Arena ar(st);
     const int64_t kp = pad64(N);
-    std::vector<Arena::X64> zs(n), as(n);
+    std::vector<X64Op> zs(n), as(n);
     std::vector<X64Spec> sp(n);
     for (int l = 0; l < n; ++l) {
-        zs[l] = ar.x64(r[l], kp);
-        as[l] = ar.x64(C[l], kp);
+        zs[l] = x64_alloc(ar, r[l], kp);
+        as[l] = x64_alloc(ar, C[l], kp);
         if (!zs[l].ok() || !as[l].ok()) return tc_err(err, "x64_project: out of memory", LS_ERR_OOM);
         if (launch_split_x64(Z[l], r[l], N, N, nullptr, zs[l], st) != cudaSuccess ||
             launch_split_x64(a[l], C[l], N, N, nullptr, as[l], st) != cudaSuccess)
@@ -906,13 +725,13 @@ int x64_project(int n, const double* const Z[], const int r[], const double* con
 int x64_apply(int n, const double* const T[], const int r[], const double* const src[], int64_t N,
               double* const dst[], int* flag, cudaStream_t st, std::string* err) {
     Arena ar(st);
-    std::vector<Arena::X64> ss(n), ts(n);
+    std::vector<X64Op> ss(n), ts(n);
     std::vector<X64Spec> sp(n);
     for (int l = 0; l < n; ++l) {
         const int64_t kp = pad64(r[l]);
         double* srcT = ar.get<double>(N * r[l]);
-        ss[l] = ar.x64(N, kp);
-        ts[l] = ar.x64(r[l], kp);
+        ss[l] = x64_alloc(ar, N, kp);
+        ts[l] = x64_alloc(ar, r[l], kp);
         if (!srcT || !ss[l].ok() || !ts[l].ok()) return tc_err(err, "x64_apply: out of memory", LS_ERR_OOM);
         if (launch_transpose(src[l], r[l], N, srcT, st) != cudaSuccess ||
             launch_split_x64(srcT, N, r[l], r[l], nullptr, ss[l], st) != cudaSuccess ||
@@ -929,7 +748,7 @@ int x64_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t 
     Arena ar(st);
     Flag fl(ar, st);
     const int64_t kp = pad64(std::max<int64_t>(K, 1));
-    Arena::X64 as = ar.x64(M, kp), bs = ar.x64(N, kp);
+    X64Op as = x64_alloc(ar, M, kp), bs = x64_alloc(ar, N, kp);
     if (!fl.d || !as.ok() || !bs.ok()) return tc_err(err, "gemm_nt: out of memory", LS_ERR_OOM);
     if (launch_split_x64(A, M, K, K, nullptr, as, st) != cudaSuccess ||
         launch_split_x64(B, N, K, K, nullptr, bs, st) != cudaSuccess)

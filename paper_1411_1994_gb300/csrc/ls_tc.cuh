@@ -18,10 +18,6 @@ int tc_core(const double* P0, const double* P1, const double* P2, const int32_t*
 int tc_project(const double* Z, int r, const double* a, int64_t C, int64_t N, double* P, cudaStream_t st,
                std::string* err);
 
-// Slab evaluation on tcgen05 tensor cores.
-int tc_eval(const double* const Z[3], const int32_t* r, const double* B, int64_t N, const int32_t* zidx,
-            int nslab, double* work, void* out, int out_f32, int num_sms, cudaStream_t st, std::string* err);
-
 // FP64-grade products on tcgen05 tensor cores: every operand row in eight
 // exact base-128 digits, digit products accumulated exactly per level in TMEM,
 // recombined in integer and FP64 arithmetic (error about 2^-53 of

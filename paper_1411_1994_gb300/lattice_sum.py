@@ -27,7 +27,7 @@ EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_create", "lattice_sum_add_de
             "lattice_sum_rhosvd_reduce", "lattice_sum_eval_slab", "lattice_sum_get_factors",
             "lattice_sum_read", "lattice_sum_profile", "lattice_sum_profile_report",
             "lattice_sum_eval_slab_noalloc", "lattice_sum_batch_reduce", "lattice_sum_gemm_nt",
-            "lattice_sum_destroy", "lattice_sum_last_error")
+            "lattice_sum_gemm_nt_mixed", "lattice_sum_destroy", "lattice_sum_last_error")
 
 
 class ls_params(C.Structure):
@@ -86,6 +86,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lattice_sum_batch_reduce.argtypes = [P(C.c_void_p), C.c_int32, C.c_double, P(ls_tucker_info)]
     lib.lattice_sum_gemm_nt.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
                                         C.c_void_p]
+    lib.lattice_sum_gemm_nt_mixed.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
+                                              C.c_int32, C.c_int32, C.c_void_p]
     lib.lattice_sum_destroy.argtypes = [C.c_void_p]
     lib.lattice_sum_destroy.restype = None
     lib.lattice_sum_last_error.argtypes = [C.c_void_p]
@@ -168,6 +170,27 @@ def gemm_nt(A, B):
     D = torch.empty((M, N), dtype=torch.float64, device=A.device)
     _check(lib().lattice_sum_gemm_nt(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()), C.c_int64(M),
                                      C.c_int64(N), C.c_int64(K), C.c_void_p(D.data_ptr()), None))
+    return D
+
+
+def gemm_nt_mixed(A, B, dtype=None, tile_n: int = 0):
+    """D = A B^T for float64 CUDA tensors (A: M x K, B: N x K, K <= 2048) in the mixed slab
+    evaluation's tensor-core arithmetic (lattice_sum_gemm_nt_mixed): two exact digits and two
+    11-bit tails (FP16), the two leading levels accumulated exactly; `tile_n` 32/64/128 (0 = by size);
+    D in `dtype` (torch.float32 or torch.float64, default float32)."""
+    import torch
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    N, K2 = B.shape
+    if K != K2 or A.dtype != torch.float64 or B.dtype != torch.float64:
+        raise ValueError("gemm_nt_mixed: A (M x K) and B (N x K) must be float64 with the same K")
+    dtype = dtype or torch.float32
+    D = torch.empty((M, N), dtype=dtype, device=A.device)
+    _check(lib().lattice_sum_gemm_nt_mixed(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()), C.c_int64(M),
+                                           C.c_int64(N), C.c_int64(K), C.c_void_p(D.data_ptr()),
+                                           C.c_int32(LS_OUT_F32 if dtype == torch.float32 else LS_OUT_F64),
+                                           C.c_int32(tile_n), None))
     return D
 
 
