@@ -62,9 +62,6 @@ Tracer& tracer() {
     return *t;
 }
 
-void count_h2d(int64_t n) { tracer().h2d += n; }
-void count_d2h(int64_t n) { tracer().d2h += n; }
-
 struct HostBlock {
     ls_block b;
     std::vector<int32_t> m[3];   // vertex index of each site, per mode
@@ -241,6 +238,8 @@ double quad_max_err(int R, double hs, double s, const std::vector<double>& r) {
 
 namespace ls {
 void count_kernels(int n) { tracer().kernels += n; }
+void count_h2d(int64_t n) { tracer().h2d += n; }
+void count_d2h(int64_t n) { tracer().d2h += n; }
 void set_global_error(const char* msg) { g_create_error = msg; }
 
 Scope::Scope(const char* n, cudaStream_t s) : name(n), st(s) {
@@ -731,14 +730,9 @@ int red_finish(RedState& R, ls_tucker_info* info) {
         int rc = x64_apply(3, Li, rs, src, N, dst, &R.d_st[9].flag, st, &err);
         if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: CholeskyQR: %s", err.c_str());
     }
-    if (ctx->p.precision == LS_MIXED) {
-        Scope sc("project", st);
-        for (int l = 0; l < 3; ++l) {
-            int rc = tc_project(ctx->d_Z[l], ctx->r[l], ctx->mode[l].d_cols, ctx->mode[l].C, N, ctx->d_P[l], st,
-                                &ctx->err);
-            if (rc != LS_OK) return rc;
-        }
-    } else {
+    {
+        // (c2) projection P_l = Z_l^T A_l, both paths: FP64-grade exact-slice products on the
+        // tensor cores (the dense FP64 contraction the truncation rests on)
         const double *Z[3], *a[3];
         double* P[3];
         int rs[3];
@@ -766,12 +760,6 @@ int red_finish(RedState& R, ls_tucker_info* info) {
         for (int64_t t = 0; t < T; ++t) perm[pos[ctx->tcol[3 * t]]++] = (int32_t)t;
     }
     int32_t *d_perm_t = nullptr, *d_off = nullptr;
-    CUS(dalloc(ctx, &d_perm_t, T));
-    CUS(dalloc(ctx, &d_off, Cs[0] + 1));
-    CUS(cudaMemcpyAsync(d_perm_t, perm.data(), T * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    count_h2d(T * sizeof(int32_t));
-    CUS(cudaMemcpyAsync(d_off, off.data(), (Cs[0] + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    count_h2d((Cs[0] + 1) * sizeof(int32_t));
     const int64_t core_n = (int64_t)ctx->r[0] * ctx->r[1] * ctx->r[2];
     CUS(dalloc(ctx, &ctx->d_B, core_n));
     {
@@ -779,10 +767,18 @@ int red_finish(RedState& R, ls_tucker_info* info) {
         const int64_t nn = (int64_t)ctx->r[1] * ctx->r[2];
         const int64_t w_cols = std::max<int64_t>(1, std::min<int64_t>(Cs[0], (int64_t)(32 << 20) / std::max<int64_t>(nn, 1)));
         if (ctx->p.precision == LS_MIXED) {
-            int rc = tc_core(ctx->d_P[0], ctx->d_P[1], ctx->d_P[2], Cs, ctx->r, ctx->d_tcol, ctx->d_xin, d_perm_t, d_off,
-                             T, ctx->d_B, ctx->num_sms, st, &ctx->err);
-            if (rc != LS_OK) return rc;
+            // both steps on the tensor cores (two exact digits + two tails)
+            std::string err;
+            int rc = dt_core(ctx->d_P[0], ctx->d_P[1], ctx->d_P[2], Cs, ctx->r, ctx->d_tcol, ctx->d_xin, perm.data(),
+                             off.data(), T, ctx->d_B, &R.d_st[9].flag, st, &err);
+            if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: core: %s", err.c_str());
         } else {
+            CUS(dalloc(ctx, &d_perm_t, T));
+            CUS(dalloc(ctx, &d_off, Cs[0] + 1));
+            CUS(cudaMemcpyAsync(d_perm_t, perm.data(), T * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            count_h2d(T * sizeof(int32_t));
+            CUS(cudaMemcpyAsync(d_off, off.data(), (Cs[0] + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            count_h2d((Cs[0] + 1) * sizeof(int32_t));
             double *P1t = nullptr, *P2t = nullptr, *W = nullptr;
             CUS(dalloc(ctx, &P1t, (int64_t)Cs[1] * ctx->r[1]));
             CUS(dalloc(ctx, &P2t, (int64_t)Cs[2] * ctx->r[2]));

@@ -35,6 +35,9 @@ struct DevStatus {
 // tracing: every kernel launch site bumps this counter (ls_api.cu owns it)
 // ---------------------------------------------------------------------------
 void count_kernels(int n);
+// host<->device bytes copied by the library (the e2e accounting)
+void count_h2d(int64_t n);
+void count_d2h(int64_t n);
 
 // Records a CUDA-event pair around a step on a stream while tracing is on
 // (lattice_sum_profile); the pairs are reported by name.
@@ -217,12 +220,6 @@ cudaError_t launch_fold_norms(const double* xi, const int32_t* tcol, int64_t T, 
 // out = in^T for a rows x cols row-major matrix.
 cudaError_t launch_transpose(const double* in, int64_t rows, int64_t cols, double* out, cudaStream_t st);
 
-// Step 1 of the core for groups [cbeg, cbeg + cw): W[c][j*r2+k] =
-// sum_{t : c0(t) = cbeg + c} xin[t] P1[j][c1(t)] P2[k][c2(t)]  (FP64).
-cudaError_t launch_core_group(const double* P1t, const double* P2t, int r1, int r2, const int32_t* tcol,
-                              const double* xin, const int32_t* perm, const int32_t* off, int cbeg, int cw, double* W,
-                              cudaStream_t st);
-
 // Core (FP64): B[i][j][k] = sum_t xin[t] P0[i][c0] P1[j][c1] P2[k][c2] in two
 // exact steps: terms grouped by c0 (perm/off: terms sorted by c0, CSR
 // offsets) give W[c0][j*r2+k] = sum_{t in group} xin P1[j][c1] P2[k][c2]
@@ -231,10 +228,6 @@ cudaError_t launch_core_group(const double* P1t, const double* P2t, int r1, int 
 cudaError_t launch_core_f64(const double* P0, const double* P1t, const double* P2t, const int32_t* C, const int32_t* r,
                             const int32_t* tcol, const double* xin, const int32_t* perm, const int32_t* off,
                             double* W, int64_t w_cols, double* B, cudaStream_t st);
-
-// M[(a*r1 + b)][s] = sum_k B[a][b][k] Z2[k][zidx[s]]  (first n-mode product of a slab).
-cudaError_t launch_eval_m(const double* Z2, const int32_t* r, const double* B, int64_t N, const int32_t* zidx,
-                          int nslab, double* M, cudaStream_t st);
 
 // Slab evaluation (FP64 arithmetic): out[s][x][y] for nslab z indices.
 // work holds >= r0*r1*nslab + r0*N*nslab doubles.

@@ -49,11 +49,10 @@
 // - Warp 0: TMA producer, through a ring of shared-memory stages (k-blocks
 //   of 32, 64-byte swizzle).
 // - Warp 1: allocates TMEM and issues the MMAs.
-// - Warps 2-9: epilogue. Two warps per TMEM lane quadrant, each taking half
-//   of the tile's columns.
-// With FP32 output the epilogue pulls its accumulators into registers and
-// releases TMEM before it stores, so the next tile's MMAs overlap the stores.
-// Tiles up to 64 wide also double-buffer TMEM.
+// - Warps 2-17: epilogue. Four warps per TMEM lane quadrant, each taking a
+//   quarter of the tile's columns. Each pulls its accumulators into
+//   registers and releases TMEM before it stores, so the next tile's MMAs
+//   overlap the stores. Tiles up to 64 wide also double-buffer TMEM.
 // Every mbarrier wait is bounded. On timeout the kernel raises the flag; the
 // producer drains its copies, the MMA warp waits for its MMAs, and TMEM is
 // freed before exit.
@@ -78,7 +77,7 @@ namespace {
 
 using namespace tc5;
 
-constexpr int DT_BM = 128, DT_BK = 32, DT_PARTS = 4, DT_EPI_WARPS = 8;
+constexpr int DT_BM = 128, DT_BK = 32, DT_PARTS = 4, DT_EPI_WARPS = 16;
 constexpr int DT_THREADS = 64 + 32 * DT_EPI_WARPS;       // TMA warp, MMA warp, epilogue warps
 constexpr int DT_TA = DT_BM * DT_BK * 2;                 // one A part tile: 8 KB
 constexpr int DT_MAXK = 2048;                            // exact level-1 accumulation
@@ -105,14 +104,42 @@ struct DtJob {
     CUtensorMap a, b;          // (kpad, rows, 4 * batch) fp16, 64-byte swizzle
     int M, N, nkb;             // k-blocks of 32
     int tiles_m, tiles_n, ntiles;
+    int n_fast;                // tile order: n fastest (the A operand streams once) or m fastest
     int a_batch, b_batch;      // batches held by each operand (1: shared)
     const int* ea;             // row exponents [batch][rows]
     const int* eb;
     int64_t ea_zs, eb_zs;
     void* out;                 // out[z * zs + n * ldn + m]
     int64_t ldn, zs;
-    int mode;                  // DtOutMode
+    int mode;                  // DtOutMode (also the kernel's template argument)
+    int accumulate;            // DT_F64 only: out += D
+    const int* kb_lo;          // per-z k-block ranges [kb_lo[z], kb_lo[z + 1]) (grouped form), or
+    int kb_begin, kb_end;      // one range for every z
 };
+
+// tile t -> (batch z, m-tile, n-tile)
+__device__ __forceinline__ void tile_of(const DtJob& J, int t, int& z, int& tm, int& tn) {
+    const int per_z = J.tiles_m * J.tiles_n;
+    z = t / per_z;
+    const int rem = t - z * per_z;
+    if (J.n_fast) {
+        tm = rem / J.tiles_n;
+        tn = rem - tm * J.tiles_n;
+    } else {
+        tn = rem / J.tiles_m;
+        tm = rem - tn * J.tiles_m;
+    }
+}
+
+__device__ __forceinline__ void k_range(const DtJob& J, int z, int& k0, int& k1) {
+    if (J.kb_lo) {
+        k0 = J.kb_lo[z];
+        k1 = J.kb_lo[z + 1];
+    } else {
+        k0 = J.kb_begin;
+        k1 = J.kb_end;
+    }
+}
 
 __device__ __forceinline__ float pow2f(int e) {           // e in [-126, 127]
     return __int_as_float((e + 127) << 23);
@@ -122,6 +149,39 @@ __device__ __forceinline__ float pow2f(int e) {           // e in [-126, 127]
 __device__ __forceinline__ float scale_f32(float v, int e) {
     const int e1 = max(-126, min(127, e));
     return (v * pow2f(e1)) * pow2f(max(-126, min(127, e - e1)));
+}
+
+// (hi + lo) 2^e as a double without FP64 arithmetic, for a pair from combine3
+// (|lo| <= ulp(hi) / 2). hi's significand goes to bit 52 of a 53-bit integer,
+// lo is aligned to it and added (bits of lo below the double's last place are
+// dropped: < 1 ulp), the sum renormalised by at most one place and the exponent
+// biased by e. Zero, subnormal and out-of-range cases take the FP64 route.
+__device__ __forceinline__ double pair_to_f64(float hi, float lo, int e) {
+    const unsigned hb = __float_as_uint(hi), lb = __float_as_uint(lo);
+    const int eh = (int)((hb >> 23) & 0xff), el = (int)((lb >> 23) & 0xff);
+    int ed = eh - 127 + 1023 + e;
+    if (eh == 0 || eh == 0xff || ed < 2 || ed > 2045) {
+        const int e1 = max(-1022, min(1023, e));
+        return (((double)hi + (double)lo) * __longlong_as_double((long long)(e1 + 1023) << 52)) *
+               __longlong_as_double((long long)(max(-1022, min(1023, e - e1)) + 1023) << 52);
+    }
+    long long M = (long long)((hb & 0x7fffffu) | 0x800000u) << 29;        // units 2^(eh - 127 - 52)
+    if (el != 0) {
+        const long long ml = (long long)((lb & 0x7fffffu) | 0x800000u);
+        const int k = el - eh + 29;                                        // lo = ml 2^k units, k <= 5
+        const long long lv = k >= 0 ? ml << k : (k > -40 ? ml >> -k : 0);
+        M += ((hb ^ lb) >> 31) ? -lv : lv;
+    }
+    if (M >= (1ll << 53)) {
+        M >>= 1;
+        ++ed;
+    } else if (M < (1ll << 52)) {
+        M <<= 1;
+        --ed;
+    }
+    const unsigned long long bits =
+        ((unsigned long long)(hb >> 31) << 63) | ((unsigned long long)ed << 52) | ((unsigned long long)M & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
 }
 
 // a0 + a1 + a2 (a0, a1 exact, |a2| small) as an unevaluated pair hi + lo, by two
@@ -136,11 +196,11 @@ __device__ __forceinline__ void combine3(float a0, float a1, float a2, float& hi
     lo = (s - (hi - b2)) + (t - b2);
 }
 
-template <int BN>
+template <int BN, int MODE>
 __global__ void __launch_bounds__(DT_THREADS, 1) k_dt_gemm(const __grid_constant__ DtJob J, int* flag) {
     using C = DtCfg<BN>;
     constexpr int S = C::STAGES, NBUF = C::NBUF;
-    constexpr int HALF = BN / 2;                  // columns per epilogue warp
+    constexpr int QC = BN / 4;                    // columns per epilogue warp
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + S * C::STAGE);
@@ -150,7 +210,6 @@ __global__ void __launch_bounds__(DT_THREADS, 1) k_dt_gemm(const __grid_constant
     uint64_t* mdone = tempty + 2;      // every MMA of this CTA has completed
     uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int per_z = J.tiles_m * J.tiles_n;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -179,10 +238,12 @@ __global__ void __launch_bounds__(DT_THREADS, 1) k_dt_gemm(const __grid_constant
         uint32_t it = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < J.ntiles && ok; t += gridDim.x) {
-            const int z = t / per_z, rem = t - z * per_z;
-            const int tn = rem / J.tiles_m, tm = rem - tn * J.tiles_m;
+            int z, tm, tn;
+            tile_of(J, t, z, tm, tn);
             const int za = J.a_batch > 1 ? z : 0, zb = J.b_batch > 1 ? z : 0;
-            for (int kb = 0; kb < J.nkb; ++kb, ++it) {
+            int k0, k1;
+            k_range(J, z, k0, k1);
+            for (int kb = k0; kb < k1; ++kb, ++it) {
                 const uint32_t s = it % S, u = it / S;
                 if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1, flag)) { ok = false; break; }
                 unsigned char* st = smem + s * C::STAGE;
@@ -207,7 +268,9 @@ __global__ void __launch_bounds__(DT_THREADS, 1) k_dt_gemm(const __grid_constant
             if (u > 0 && !mbar_wait(&tempty[buf], (u - 1) & 1, flag)) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t c0 = tmem + buf * 3 * BN, c1 = c0 + BN, c2 = c0 + 2 * BN;
-            for (int kb = 0; kb < J.nkb; ++kb, ++it) {
+            int k0, k1;
+            k_range(J, t / (J.tiles_m * J.tiles_n), k0, k1);
+            for (int kb = k0; kb < k1; ++kb, ++it) {
                 const uint32_t s = it % S;
                 if (!mbar_wait(&full[s], (it / S) & 1, flag)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
@@ -219,7 +282,7 @@ __global__ void __launch_bounds__(DT_THREADS, 1) k_dt_gemm(const __grid_constant
                                    a2 = smem_desc_sw64(sa + 2 * DT_TA) + o, a3 = smem_desc_sw64(sa + 3 * DT_TA) + o;
                     const uint64_t b0 = smem_desc_sw64(sb) + o, b1 = smem_desc_sw64(sb + C::TB) + o,
                                    b2 = smem_desc_sw64(sb + 2 * C::TB) + o, b3 = smem_desc_sw64(sb + 3 * C::TB) + o;
-                    const uint32_t acc = (kb | kk) ? 1u : 0u;
+                    const uint32_t acc = (kb != k0 || kk) ? 1u : 0u;
                     mma_bf16(c0, a0, b0, idesc, acc);            // d0 d0: exact
                     mma_bf16(c1, a0, b1, idesc, acc);            // d0 d1, d1 d0: exact
                     mma_bf16(c1, a1, b0, idesc, 1u);
@@ -241,7 +304,9 @@ __global__ void __launch_bounds__(DT_THREADS, 1) k_dt_gemm(const __grid_constant
         mma_commit(mdone);
         mbar_drain(mdone, 0);
     } else if (warp >= 2) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns of its half of the tile
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and a quarter of the tile's
+        // columns; it takes all of its values into registers, releases the accumulators to
+        // the next tile's MMAs, then scales and stores
         const int q = warp & 3, hc = (warp - 2) >> 2;
         const uint32_t lanes = (uint32_t)(32 * q) << 16;
         uint32_t lt = 0;
@@ -249,69 +314,48 @@ __global__ void __launch_bounds__(DT_THREADS, 1) k_dt_gemm(const __grid_constant
             const uint32_t buf = lt % NBUF;
             if (!mbar_wait(&tfull[buf], (lt / NBUF) & 1, flag)) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const int z = t / per_z, rem = t - z * per_z;
-            const int tn = rem / J.tiles_m, tm = rem - tn * J.tiles_m;
-            const int m = tm * DT_BM + 32 * q + lane, n0 = tn * BN + hc * HALF;
-            const bool mv = m < J.M;
-            const int ea = mv ? J.ea[(J.a_batch > 1 ? z : 0) * J.ea_zs + m] - 30 : 0;
-            const int* eb = J.eb + (J.b_batch > 1 ? z : 0) * J.eb_zs;
-            const int nn = max(0, min(HALF, J.N - n0));
-            const uint32_t col = tmem + lanes + buf * 3 * BN + hc * HALF;
+            int z, tm, tn;
+            tile_of(J, t, z, tm, tn);
+            const int m = tm * DT_BM + 32 * q + lane, n0 = tn * BN + hc * QC;
+            const int nn = max(0, min(QC, J.N - n0));
+            const uint32_t col = tmem + lanes + buf * 3 * BN + hc * QC;
+            int k0, k1;
+            k_range(J, z, k0, k1);
+            const bool live = k1 > k0;   // an empty K range leaves the accumulators unwritten: zeros
+            float hv[QC], lv[QC];
+#pragma unroll
+            for (int c = 0; c < QC; c += 8) {
+                if (c < nn) {
+                    float v0[8], v1[8], v2[8];
+                    tmem_ld8(col + c, v0);
+                    tmem_ld8(col + BN + c, v1);
+                    tmem_ld8(col + 2 * BN + c, v2);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        combine3(live ? v0[j] : 0.f, live ? v1[j] : 0.f, live ? v2[j] : 0.f, hv[c + j], lv[c + j]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+            if (m >= J.M) continue;
+            const int ea = J.ea[(J.a_batch > 1 ? z : 0) * J.ea_zs + m] - 30;
+            const int* eb = J.eb + (J.b_batch > 1 ? z : 0) * J.eb_zs + n0;
             const int64_t base = (int64_t)z * J.zs + (int64_t)n0 * J.ldn + m;
-            if (J.mode == DT_F32) {
-                // all of this warp's values into registers, TMEM released, then the stores
-                float hv[HALF];
 #pragma unroll
-                for (int c = 0; c < HALF; c += 16) {
-                    float v0[16], v1[16], v2[16];
-                    if (c < nn) {
-                        tmem_ld16(col + c, v0);
-                        tmem_ld16(col + BN + c, v1);
-                        tmem_ld16(col + 2 * BN + c, v2);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            float lo;
-                            combine3(v0[j], v1[j], v2[j], hv[c + j], lo);
-                        }
-                    }
+            for (int j = 0; j < QC; ++j) {
+                if (j >= nn) break;
+                const int e = ea + eb[j];
+                const int64_t at = base + (int64_t)j * J.ldn;
+                if (MODE == DT_F32) {
+                    reinterpret_cast<float*>(J.out)[at] = scale_f32(hv[j], e);
+                } else if (MODE == DT_PAIR) {
+                    reinterpret_cast<float2*>(J.out)[at] = make_float2(scale_f32(hv[j], e), scale_f32(lv[j], e));
+                } else {
+                    const double sv = pair_to_f64(hv[j], lv[j], e);
+                    double* o = reinterpret_cast<double*>(J.out) + at;
+                    *o = J.accumulate ? *o + sv : sv;
                 }
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[buf]);
-                if (mv) {
-                    float* o = (float*)J.out + base;
-#pragma unroll
-                    for (int j = 0; j < HALF; ++j)
-                        if (j < nn) o[j * J.ldn] = scale_f32(hv[j], ea + eb[n0 + j]);
-                }
-            } else {
-                for (int c = 0; c < nn; c += 16) {
-                    float v0[16], v1[16], v2[16];
-                    tmem_ld16(col + c, v0);
-                    tmem_ld16(col + BN + c, v1);
-                    tmem_ld16(col + 2 * BN + c, v2);
-                    if (!mv) continue;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        if (c + j >= nn) break;
-                        float hi, lo;
-                        combine3(v0[j], v1[j], v2[j], hi, lo);
-                        const int e = ea + eb[n0 + c + j];
-                        const int64_t at = base + (int64_t)(c + j) * J.ldn;
-                        if (J.mode == DT_PAIR) {
-                            reinterpret_cast<float2*>(J.out)[at] = make_float2(scale_f32(hi, e), scale_f32(lo, e));
-                        } else {
-                            const double v = (double)hi + (double)lo;
-                            const int e1 = max(-1022, min(1023, e));
-                            reinterpret_cast<double*>(J.out)[at] =
-                                (v * __longlong_as_double((long long)(e1 + 1023) << 52)) *
-                                __longlong_as_double((long long)(max(-1022, min(1023, e - e1)) + 1023) << 52);
-                        }
-                    }
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[buf]);
             }
         }
     }
@@ -403,70 +447,207 @@ __device__ __forceinline__ unsigned short f16_of_fixed(long long R, long long& q
     return (unsigned short)((neg << 15) | bits);
 }
 
-// sources: FP64 values, or FP32 pairs (hi, lo) whose sum is the value
+// Split sources: element (b, i, k) of `batch` stacked operands (row i, column k).
+//   SrcF64:    p[b*sb + row(i)*si + k*sk], row(i) = ridx ? ridx[i] : i
+//   SrcPair:   the same over FP32 pairs (hi, lo) whose sum is the value
+//   SrcGather: w[t] P[i*ld + tcol[3t + mode]] with t = tmap[k] (0 where t < 0): the
+//              columns of a projected side matrix that the canonical terms use, in the
+//              order of a term list (one batch)
+// mag() orders like |x|; exp_of() gives E with max|x| in [2^(E-1), 2^E) from it.
 struct SrcF64 {
+    static constexpr bool pair = false;
     const double* p;
-    __device__ unsigned long long mag(int64_t i) const {   // orders like |x|
-        return (unsigned long long)__double_as_longlong(p[i]) & 0x7fffffffffffffffull;
+    int64_t si, sk, sb;
+    const int32_t* ridx;
+    __device__ double at(int64_t b, int64_t i, int64_t k) const { return p[b * sb + (ridx ? ridx[i] : i) * si + k * sk]; }
+    __device__ unsigned long long mag(int64_t b, int64_t i, int64_t k) const {
+        return (unsigned long long)__double_as_longlong(at(b, i, k)) & 0x7fffffffffffffffull;
     }
-    __device__ static int exp_of(unsigned long long mb) {  // E with max|x| in [2^(E-1), 2^E)
+    __device__ static int exp_of(unsigned long long mb) {
         const int ex = (int)(mb >> 52);
         return ex ? ex - 1022 : (63 - __clzll((long long)mb)) - 1073;
     }
-    __device__ long long fixed(int64_t i, int s) const { return fixed_of(p[i], s); }
+    __device__ long long fixed(int64_t b, int64_t i, int64_t k, int s) const { return fixed_of(at(b, i, k), s); }
 };
 struct SrcPair {
+    static constexpr bool pair = true;
     const float2* p;
-    __device__ unsigned long long mag(int64_t i) const { return __float_as_uint(p[i].x) & 0x7fffffffu; }
+    int64_t si, sk, sb;
+    __device__ float2 at(int64_t b, int64_t i, int64_t k) const { return p[b * sb + i * si + k * sk]; }
+    __device__ unsigned long long mag(int64_t b, int64_t i, int64_t k) const {
+        return __float_as_uint(at(b, i, k).x) & 0x7fffffffu;
+    }
     __device__ static int exp_of(unsigned long long mb) {
         const int ex = (int)(mb >> 23);
         return ex ? ex - 126 : (63 - __clzll((long long)mb)) - 148;
     }
-    __device__ long long fixed(int64_t i, int s) const {
-        const float2 v = p[i];
+    __device__ long long fixed(int64_t b, int64_t i, int64_t k, int s) const {
+        const float2 v = at(b, i, k);
         return fixed_of(v.x, s) + fixed_of(v.y, s);
     }
 };
+struct SrcGather {
+    static constexpr bool pair = false;
+    const double* P;
+    int64_t ld;
+    const int32_t* tmap;
+    const int32_t* tcol;
+    int mode;
+    const double* w;
+    __device__ double at(int64_t, int64_t i, int64_t k) const {
+        const int t = tmap[k];
+        if (t < 0) return 0.0;
+        const double v = P[i * ld + tcol[3 * (int64_t)t + mode]];
+        return w ? w[t] * v : v;
+    }
+    __device__ unsigned long long mag(int64_t b, int64_t i, int64_t k) const {
+        return (unsigned long long)__double_as_longlong(at(b, i, k)) & 0x7fffffffffffffffull;
+    }
+    __device__ static int exp_of(unsigned long long mb) { return SrcF64::exp_of(mb); }
+    __device__ long long fixed(int64_t b, int64_t i, int64_t k, int s) const { return fixed_of(at(b, i, k), s); }
+};
 
-// One warp per row (b, i) of `batch` stacked operands:
-//   x(k) = src[b*sb + row(i)*si + k*sk] for k < cols, 0 for cols <= k < kpad,
-//   row(i) = ridx ? ridx[i] : i;
-// written as FP16 d0 2^9, d1 2^2, t1 2^9, t2 2^9 into parts[p][b][i][k], with the row
-// exponent E in exps[b*rows + i].
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// The same four parts from an FP32 pair (hi, lo) in FP32 arithmetic: the scaled
+// value as a pair, nearest-integer digits (the differences are exact), the rest
+// carried by TwoSum, the tails by the hardware FP16 conversion. Agrees with the
+// integer route to the form's accuracy.
+__device__ __forceinline__ void split_pair(float2 v, int E, unsigned short& p0, unsigned short& p1, unsigned short& p2,
+                                           unsigned short& p3) {
+    const float hs = scale_f32(v.x, 6 - E), ls = scale_f32(v.y, 6 - E);
+    const float d0 = rintf(hs);
+    float rh, rl;
+    two_sum(hs - d0, ls, rh, rl);                    // the rest after d0, |.| <= 1/2
+    const float d1 = rintf(rh * 128.f);
+    float vh, vl;
+    two_sum((rh * 128.f - d1) * 4.f, rl * 512.f, vh, vl);   // the rest after d1, times 2^9
+    const __half t1 = __float2half_rn(vh);
+    const __half t2 = __float2half_rn((vh - __half2float(t1)) + vl);
+    p0 = __half_as_ushort(__float2half_rn(d0 * 512.f));
+    p1 = __half_as_ushort(__float2half_rn(d1 * 4.f));
+    p2 = __half_as_ushort(t1);
+    p3 = __half_as_ushort(t2);
+}
+
+// the four parts of one entry, given its row exponent E
 template <class Src>
-__global__ void k_split_dt(Src src, const int32_t* __restrict__ ridx, int64_t rows, int64_t cols, int64_t si,
-                           int64_t sk, int64_t sb, int64_t batch, int64_t kpad, unsigned short* __restrict__ parts,
-                           int* __restrict__ exps) {
+__device__ __forceinline__ void split_entry(const Src& src, int64_t b, int64_t i, int64_t k, int E, unsigned short& p0,
+                                            unsigned short& p1, unsigned short& p2, unsigned short& p3) {
+    if constexpr (Src::pair) {
+        split_pair(src.at(b, i, k), E, p0, p1, p2, p3);
+        return;
+    }
+    const long long W = src.fixed(b, i, k, 6 - E + FXB);        // |W| < 2^(6 + FXB)
+    const long long d0 = (W + (1ll << (FXB - 1))) >> FXB;     // nearest, |d0| <= 64
+    long long R = W - (d0 << FXB);                             // |R| <= 2^(FXB - 1)
+    const long long d1 = (R + (1ll << (FXB - 8))) >> (FXB - 7);  // nearest, |d1| <= 64
+    R -= d1 << (FXB - 7);                                      // |R| <= 2^(FXB - 8)
+    long long q;
+    p2 = f16_of_fixed(R, q);
+    R -= q;
+    p3 = f16_of_fixed(R, q);
+    p0 = __half_as_ushort(__float2half_rn((float)(d0 * 512)));   // exact
+    p1 = __half_as_ushort(__float2half_rn((float)(d1 * 4)));     // exact
+}
+
+// One warp per row (b, i) of `batch` stacked operands: x(k) = src(b, i, k) for k < cols,
+// 0 for cols <= k < kpad; written as FP16 d0 2^9, d1 2^2, t1 2^9, t2 2^9 into
+// parts[p][b][i][k], with the row exponent E in exps[b*rows + i].
+template <class Src>
+__global__ void k_split_dt(Src src, int64_t rows, int64_t cols, int64_t batch, int64_t kpad,
+                           unsigned short* __restrict__ parts, int* __restrict__ exps) {
     const int lane = threadIdx.x & 31;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (w >= rows * batch) return;
     const int64_t b = w / rows, i = w - b * rows;
-    const int64_t x0 = b * sb + (int64_t)(ridx ? ridx[i] : i) * si;
     unsigned long long mb = 0;
-    for (int64_t k = lane; k < cols; k += 32) mb = max(mb, src.mag(x0 + k * sk));
+    for (int64_t k = lane; k < cols; k += 32) mb = max(mb, src.mag(b, i, k));
     for (int o = 16; o; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
     const int E = mb ? Src::exp_of(mb) : 0;
     if (lane == 0) exps[w] = E;
     const int64_t ps = batch * rows * kpad, off = w * kpad;
     for (int64_t k = lane; k < kpad; k += 32) {
         unsigned short p0 = 0, p1 = 0, p2 = 0, p3 = 0;
-        if (k < cols) {
-            const long long W = src.fixed(x0 + k * sk, 6 - E + FXB);   // |W| < 2^(6 + FXB)
-            const long long d0 = (W + (1ll << (FXB - 1))) >> FXB;     // nearest, |d0| <= 64
-            long long R = W - (d0 << FXB);                             // |R| <= 2^(FXB - 1)
-            const long long d1 = (R + (1ll << (FXB - 8))) >> (FXB - 7);  // nearest, |d1| <= 64
-            R -= d1 << (FXB - 7);                                      // |R| <= 2^(FXB - 8)
-            long long q;
-            p2 = f16_of_fixed(R, q);
-            R -= q;
-            p3 = f16_of_fixed(R, q);
-            p0 = __half_as_ushort(__float2half_rn((float)(d0 * 512)));   // exact
-            p1 = __half_as_ushort(__float2half_rn((float)(d1 * 4)));     // exact
-        }
+        if (k < cols) split_entry(src, b, i, k, E, p0, p1, p2, p3);
         parts[off + k] = p0;
         parts[ps + off + k] = p1;
         parts[2 * ps + off + k] = p2;
         parts[3 * ps + off + k] = p3;
+    }
+}
+
+// Long rows, in two passes with the whole grid busy. Pass 1: mb[row] = max |x| bits
+// (blocks of 256 threads over 1024-entry segments of one row; mb zeroed before).
+template <class Src>
+__global__ void k_rowmax(Src src, int64_t rows, int64_t cols, unsigned long long* __restrict__ mb) {
+    const int64_t row = blockIdx.y, b = row / rows, i = row - b * rows;
+    unsigned long long m = 0;
+    for (int64_t k = blockIdx.x * 1024 + threadIdx.x; k < min(cols, (int64_t)(blockIdx.x + 1) * 1024); k += 256)
+        m = max(m, src.mag(b, i, k));
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(mb + row, m);
+}
+// Pass 2: one thread per entry (row, k).
+template <class Src>
+__global__ void k_split_rows(Src src, int64_t rows, int64_t cols, int64_t batch, int64_t kpad,
+                             const unsigned long long* __restrict__ mb, unsigned short* __restrict__ parts,
+                             int* __restrict__ exps) {
+    const int64_t row = blockIdx.y, b = row / rows, i = row - b * rows;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= kpad) return;
+    const int E = mb[row] ? Src::exp_of(mb[row]) : 0;
+    if (k == 0) exps[row] = E;
+    unsigned short p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+    if (k < cols) split_entry(src, b, i, k, E, p0, p1, p2, p3);
+    const int64_t ps = batch * rows * kpad, off = row * kpad + k;
+    parts[off] = p0;
+    parts[ps + off] = p1;
+    parts[2 * ps + off] = p2;
+    parts[3 * ps + off] = p3;
+}
+
+// Operand rows n of a pair matrix stored transposed, x(n, k) = W[k * ld + n] (k < cols):
+// pass 1 has a thread per row walk k (reads coalesced across rows); pass 2 splits
+// 32 x 64 tiles through shared memory so that both the reads (along n) and the
+// writes (along k) are contiguous.
+__global__ void k_rowmax_tr(const float2* __restrict__ W, int64_t ld, int64_t rows, int64_t cols,
+                            unsigned long long* __restrict__ mb) {
+    const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (n >= rows) return;
+    unsigned int m = 0;
+    for (int64_t k = 0; k < cols; ++k) m = max(m, __float_as_uint(W[k * ld + n].x) & 0x7fffffffu);
+    mb[n] = m;
+}
+__global__ void __launch_bounds__(256) k_split_tr(const float2* __restrict__ W, int64_t ld, int64_t rows, int64_t cols,
+                                                  int64_t kpad, const unsigned long long* __restrict__ mb,
+                                                  unsigned short* __restrict__ parts, int* __restrict__ exps) {
+    __shared__ unsigned int tile[4][64][17];   // [part][row][k pairs of u16], padded
+    const int64_t n0 = blockIdx.x * 64, k0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // 64 rows x 4 k-lanes
+    const int64_t n = n0 + tx;
+    const SrcPair src{W, 1, ld, 0};
+    const int E = (n < rows && mb[n]) ? SrcPair::exp_of(mb[n]) : 0;
+    if (blockIdx.y == 0 && ty == 0 && n < rows) exps[n] = E;
+    for (int kk = ty * 2; kk < 32; kk += 8) {
+        unsigned short a[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+        if (n < rows && k0 + kk < cols) split_entry(src, 0, n, k0 + kk, E, a[0], a[1], a[2], a[3]);
+        if (n < rows && k0 + kk + 1 < cols) split_entry(src, 0, n, k0 + kk + 1, E, c[0], c[1], c[2], c[3]);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) tile[p][tx][kk >> 1] = (unsigned)a[p] | ((unsigned)c[p] << 16);
+    }
+    __syncthreads();
+    // write: each row n of the tile is 32 u16 = 16 words per part
+    const int64_t ps = rows * kpad;
+    for (int e = threadIdx.x; e < 4 * 64 * 16; e += 256) {
+        const int p = e / (64 * 16), rr = (e / 16) % 64, w = e % 16;
+        const int64_t nn = n0 + rr, kk = k0 + 2 * w;
+        if (nn < rows && kk < kpad)
+            reinterpret_cast<unsigned int*>(parts + p * ps + nn * kpad + kk)[0] = tile[p][rr][w];
     }
 }
 
@@ -484,16 +665,16 @@ bool make_map_dt(CUtensorMap* m, const DtOp& op, int box_rows) {
     return r == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, int MODE>
 cudaError_t launch_dt(const DtJob& J, int grid, int* flag, cudaStream_t st) {
     using C = DtCfg<BN>;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(k_dt_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        attr = cudaFuncSetAttribute(k_dt_gemm<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     });
     if (attr != cudaSuccess) return attr;
-    k_dt_gemm<BN><<<grid, DT_THREADS, C::SMEM, st>>>(J, flag);
+    k_dt_gemm<BN, MODE><<<grid, DT_THREADS, C::SMEM, st>>>(J, flag);
     count_kernels(1);
     return cudaGetLastError();
 }
@@ -520,22 +701,61 @@ DtOp dt_alloc(Arena& ar, int64_t rows, int64_t kpad, int64_t batch) {
 }
 
 template <class Src>
-cudaError_t dt_split(Src src, const int32_t* ridx, int64_t cols, int64_t si, int64_t sk, int64_t sb, const DtOp& d,
-                     cudaStream_t st) {
-    const int64_t warps = d.rows * d.batch;
-    if (warps <= 0) return cudaSuccess;
+cudaError_t dt_split(Src src, int64_t cols, const DtOp& d, cudaStream_t st) {
+    const int64_t nrows = d.rows * d.batch;
+    if (nrows <= 0) return cudaSuccess;
     if (cols > d.kpad) return cudaErrorInvalidValue;
-    k_split_dt<Src><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(src, ridx, d.rows, cols, si, sk, sb, d.batch,
-                                                                          d.kpad, d.p, d.e);
-    count_kernels(1);
+    if (cols <= 1024) {
+        // a warp per row, one pass
+        k_split_dt<Src><<<(unsigned)((nrows * 32 + 255) / 256), 256, 0, st>>>(src, d.rows, cols, d.batch, d.kpad, d.p,
+                                                                               d.e);
+        count_kernels(1);
+        return cudaGetLastError();
+    }
+    if (nrows > 65535) return cudaErrorInvalidValue;
+    Arena ar(st);
+    unsigned long long* mb = ar.get<unsigned long long>(nrows);
+    if (!mb) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMemsetAsync(mb, 0, nrows * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_rowmax<Src><<<dim3((unsigned)((cols + 1023) / 1024), (unsigned)nrows), 256, 0, st>>>(src, d.rows, cols, mb);
+    k_split_rows<Src><<<dim3((unsigned)((d.kpad + 255) / 256), (unsigned)nrows), 256, 0, st>>>(
+        src, d.rows, cols, d.batch, d.kpad, mb, d.p, d.e);
+    count_kernels(2);
     return cudaGetLastError();
 }
 
+// rows n < d.rows of x(n, k) = W[k * ld + n], k < cols (W: FP32 pairs), into d (one batch)
+cudaError_t dt_split_tr(const float2* W, int64_t ld, int64_t cols, const DtOp& d, cudaStream_t st) {
+    if (d.rows <= 0) return cudaSuccess;
+    if (cols > d.kpad || d.batch != 1 || d.kpad % 32) return cudaErrorInvalidValue;
+    Arena ar(st);
+    unsigned long long* mb = ar.get<unsigned long long>(d.rows);
+    if (!mb) return cudaErrorMemoryAllocation;
+    k_rowmax_tr<<<(unsigned)((d.rows + 255) / 256), 256, 0, st>>>(W, ld, d.rows, cols, mb);
+    k_split_tr<<<dim3((unsigned)((d.rows + 63) / 64), (unsigned)(d.kpad / 32)), 256, 0, st>>>(W, ld, d.rows, cols,
+                                                                                           d.kpad, mb, d.p, d.e);
+    count_kernels(2);
+    return cudaGetLastError();
+}
+
+// K ranges of a product, in k-blocks of 32: kb_lo (device, batch + 1 entries) gives
+// batch z the range [kb_lo[z], kb_lo[z + 1]); otherwise every batch takes
+// [kb_begin, kb_end) (kb_end < 0: all of kpad). No range may exceed 2048 entries.
+struct DtK {
+    const int* kb_lo = nullptr;
+    int kb_begin = 0, kb_end = -1;
+};
+
 int dt_gemm(const DtOp& A, const DtOp& B, int64_t M, int64_t N, int64_t batch, const DtOut& out, const DtOpts& opt,
-            int* flag, cudaStream_t st, std::string* err) {
+            int* flag, cudaStream_t st, std::string* err, DtK kr = DtK{}) {
     if (M <= 0 || N <= 0 || batch <= 0) return LS_OK;
-    if (A.kpad != B.kpad || A.kpad % DT_BK != 0 || A.kpad > DT_MAXK || M > A.rows || N > B.rows ||
-        (A.batch != 1 && A.batch != batch) || (B.batch != 1 && B.batch != batch))
+    const int nkb = (int)(A.kpad / DT_BK);
+    if (kr.kb_end < 0) kr.kb_end = nkb;
+    if (A.kpad != B.kpad || A.kpad % DT_BK != 0 || M > A.rows || N > B.rows ||
+        (A.batch != 1 && A.batch != batch) || (B.batch != 1 && B.batch != batch) ||
+        (!kr.kb_lo && (kr.kb_begin < 0 || kr.kb_end > nkb || kr.kb_end - kr.kb_begin > DT_MAXK / DT_BK)) ||
+        (out.accumulate && out.mode != DT_F64))
         return tc_err(err, "dt gemm: bad operands", LS_ERR_ARG);
     int bn = opt.tile_n;
     if (bn == 0) bn = N <= 32 ? 32 : N <= 64 ? 64 : 128;
@@ -546,12 +766,14 @@ int dt_gemm(const DtOp& A, const DtOp& B, int64_t M, int64_t N, int64_t batch, c
         return tc_err(err, "dt gemm: cuTensorMapEncodeTiled failed");
     J.M = (int)M;
     J.N = (int)N;
-    J.nkb = (int)(A.kpad / DT_BK);
+    J.nkb = nkb;
     J.tiles_m = (int)((M + DT_BM - 1) / DT_BM);
     J.tiles_n = (int)((N + bn - 1) / bn);
     const int64_t nt = (int64_t)J.tiles_m * J.tiles_n * batch;
     if (nt > INT32_MAX) return tc_err(err, "dt gemm: too many tiles", LS_ERR_ARG);
     J.ntiles = (int)nt;
+    // the smaller operand stays resident in L2 while the larger one streams once
+    J.n_fast = M * A.batch > N * B.batch;
     J.a_batch = (int)A.batch;
     J.b_batch = (int)B.batch;
     J.ea = A.e;
@@ -562,10 +784,23 @@ int dt_gemm(const DtOp& A, const DtOp& B, int64_t M, int64_t N, int64_t batch, c
     J.ldn = out.ldn;
     J.zs = out.zs;
     J.mode = out.mode;
+    J.accumulate = out.accumulate;
+    J.kb_lo = kr.kb_lo;
+    J.kb_begin = kr.kb_begin;
+    J.kb_end = kr.kb_end;
     const int grid = (int)std::min<int64_t>(nt, num_sms_now());
-    cudaError_t e = bn == 32 ? launch_dt<32>(J, grid, flag, st)
-                    : bn == 64 ? launch_dt<64>(J, grid, flag, st)
-                               : launch_dt<128>(J, grid, flag, st);
+    cudaError_t e;
+    switch ((bn << 2) | out.mode) {
+        case (32 << 2) | DT_F32: e = launch_dt<32, DT_F32>(J, grid, flag, st); break;
+        case (32 << 2) | DT_F64: e = launch_dt<32, DT_F64>(J, grid, flag, st); break;
+        case (32 << 2) | DT_PAIR: e = launch_dt<32, DT_PAIR>(J, grid, flag, st); break;
+        case (64 << 2) | DT_F32: e = launch_dt<64, DT_F32>(J, grid, flag, st); break;
+        case (64 << 2) | DT_F64: e = launch_dt<64, DT_F64>(J, grid, flag, st); break;
+        case (64 << 2) | DT_PAIR: e = launch_dt<64, DT_PAIR>(J, grid, flag, st); break;
+        case (128 << 2) | DT_F32: e = launch_dt<128, DT_F32>(J, grid, flag, st); break;
+        case (128 << 2) | DT_F64: e = launch_dt<128, DT_F64>(J, grid, flag, st); break;
+        default: e = launch_dt<128, DT_PAIR>(J, grid, flag, st); break;
+    }
     if (e != cudaSuccess) return tc_err(err, std::string("dt gemm launch: ") + cudaGetErrorString(e));
     return LS_OK;
 }
@@ -621,10 +856,10 @@ int dt_eval(DtEvalCache** cache, const double* const Z[3], const int32_t* r, con
         }
         // Z_l is r_l x N (rows are basis vectors): transpose, then split rows of length r_l
         if (launch_transpose(Z[0], r0, N, zt, st) != cudaSuccess ||
-            dt_split(SrcF64{zt}, nullptr, r0, r0, 1, 0, c->z0t, st) != cudaSuccess ||
+            dt_split(SrcF64{zt, r0, 1, 0, nullptr}, r0, c->z0t, st) != cudaSuccess ||
             launch_transpose(Z[1], r1, N, zt, st) != cudaSuccess ||
-            dt_split(SrcF64{zt}, nullptr, r1, r1, 1, 0, c->z1t, st) != cudaSuccess ||
-            dt_split(SrcF64{B}, nullptr, r2, r2, 1, 0, c->core, st) != cudaSuccess) {
+            dt_split(SrcF64{zt, r1, 1, 0, nullptr}, r1, c->z1t, st) != cudaSuccess ||
+            dt_split(SrcF64{B, r2, 1, 0, nullptr}, r2, c->core, st) != cudaSuccess) {
             dt_eval_free(c);
             return tc_err(err, "eval: operand preparation failed");
         }
@@ -652,17 +887,17 @@ int dt_eval(DtEvalCache** cache, const double* const Z[3], const int32_t* r, con
         {
             Scope sc("eval.mt", st);
             // rows s of Z2^T: Z2[c][z_s], gathered
-            if (dt_split(SrcF64{Z[2]}, zidx + s0, r2, 1, N, 0, z2, st) != cudaSuccess)
+            if (dt_split(SrcF64{Z[2], 1, N, 0, zidx + s0}, r2, z2, st) != cudaSuccess)
                 return tc_err(err, "eval: split failed");
             // M[s][(a, b)] = sum_c core[(a, b)][c] Z2[c][z_s]
             rc = dt_gemm(c.core, z2, r0 * r1, ns, 1, DtOut{Mt, r0 * r1, 0, DT_PAIR}, opt, fl.d, st, err);
             if (rc != LS_OK) return rc;
-            if (dt_split(SrcPair{Mt}, nullptr, r1, r1, 1, r0 * r1, m, st) != cudaSuccess)
+            if (dt_split(SrcPair{Mt, r1, 1, r0 * r1}, r1, m, st) != cudaSuccess)
                 return tc_err(err, "eval: split failed");
             // T_s[y][a] = sum_b M_s[a][b] Z1^T[y][b]   (D[a][y], a on the lanes)
             rc = dt_gemm(m, c.z1t, r0, N, ns, DtOut{Tt, r0, N * r0, DT_PAIR}, opt, fl.d, st, err);
             if (rc != LS_OK) return rc;
-            if (dt_split(SrcPair{Tt}, nullptr, r0, r0, 1, N * r0, t, st) != cudaSuccess)
+            if (dt_split(SrcPair{Tt, r0, 1, N * r0}, r0, t, st) != cudaSuccess)
                 return tc_err(err, "eval: split failed");
         }
         {
@@ -680,18 +915,96 @@ int dt_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t K
                const DtOpts& opt, cudaStream_t st, std::string* err) {
     if (M <= 0 || N <= 0) return LS_OK;
     const int64_t kp = pad32(std::max<int64_t>(K, 1));
-    if (kp > DT_MAXK) return tc_err(err, "gemm_nt_mixed: K above 2048", LS_ERR_ARG);
+    if (kp > DT_MAXK && out_f32) return tc_err(err, "gemm_nt_mixed: K above 2048 needs FP64 output", LS_ERR_ARG);
     Arena ar(st);
     Flag fl(ar, st);
     DtOp a = dt_alloc(ar, M, kp, 1), b = dt_alloc(ar, N, kp, 1);
     if (!fl.d || !a.ok() || !b.ok()) return tc_err(err, "gemm_nt_mixed: out of memory", LS_ERR_OOM);
-    if (dt_split(SrcF64{A}, nullptr, K, K, 1, 0, a, st) != cudaSuccess ||
-        dt_split(SrcF64{B}, nullptr, K, K, 1, 0, b, st) != cudaSuccess)
+    if (dt_split(SrcF64{A, K, 1, 0, nullptr}, K, a, st) != cudaSuccess ||
+        dt_split(SrcF64{B, K, 1, 0, nullptr}, K, b, st) != cudaSuccess)
         return tc_err(err, "gemm_nt_mixed: split failed");
-    // D[m][n] row-major = the kernel's D with n on the lanes: swap the operands
-    int rc = dt_gemm(b, a, N, M, 1, DtOut{D, N, 0, out_f32 ? DT_F32 : DT_F64}, opt, fl.d, st, err);
-    if (rc != LS_OK) return rc;
+    // D[m][n] row-major = the kernel's D with n on the lanes: swap the operands; K in
+    // chunks of 2048 (each exact in its leading levels), added in FP64
+    const int nkb = (int)(kp / DT_BK), ckb = DT_MAXK / DT_BK;
+    for (int k0 = 0; k0 < nkb; k0 += ckb) {
+        DtOut o{D, N, 0, out_f32 ? DT_F32 : DT_F64};
+        o.accumulate = k0 > 0;
+        DtK kr;
+        kr.kb_begin = k0;
+        kr.kb_end = std::min(nkb, k0 + ckb);
+        int rc = dt_gemm(b, a, N, M, 1, o, opt, fl.d, st, err, kr);
+        if (rc != LS_OK) return rc;
+    }
     return fl.check(err);
+}
+
+int dt_core(const double* P0, const double* P1, const double* P2, const int32_t* C, const int32_t* r,
+            const int32_t* tcol, const double* xin, const int32_t* perm, const int32_t* off, int64_t T, double* Bc,
+            int* flag, cudaStream_t st, std::string* err) {
+    const int64_t C0 = C[0], r0 = r[0], r1 = r[1], r2 = r[2], nn = r1 * r2;
+    if (C0 <= 0 || T <= 0) return LS_OK;
+    // groups of terms by mode-0 column, each padded to whole k-blocks
+    std::vector<int> kb_lo(C0 + 1, 0);
+    for (int64_t g = 0; g < C0; ++g) {
+        const int n = off[g + 1] - off[g];
+        if (n > DT_MAXK) return tc_err(err, "core: more than 2048 terms share one mode-0 column", LS_ERR_ARG);
+        kb_lo[g + 1] = kb_lo[g] + (n + DT_BK - 1) / DT_BK;
+    }
+    const int64_t tpad = (int64_t)kb_lo[C0] * DT_BK;
+    std::vector<int32_t> tmap(tpad, -1);
+    for (int64_t g = 0; g < C0; ++g)
+        for (int u = 0; u < off[g + 1] - off[g]; ++u) tmap[(int64_t)kb_lo[g] * DT_BK + u] = perm[off[g] + u];
+    Arena ar(st);
+    int* d_kb = ar.get<int>(C0 + 1);
+    int32_t* d_tmap = ar.get<int32_t>(tpad);
+    DtOp a = dt_alloc(ar, r2, tpad, 1), b = dt_alloc(ar, r1, tpad, 1);
+    if (!d_kb || !d_tmap || !a.ok() || !b.ok()) return tc_err(err, "core: out of memory", LS_ERR_OOM);
+    {
+        Scope sc("core.operands", st);
+        if (cudaMemcpyAsync(d_kb, kb_lo.data(), (C0 + 1) * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(d_tmap, tmap.data(), tpad * sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return tc_err(err, "core: upload failed");
+        count_h2d((int64_t)((C0 + 1) * sizeof(int) + tpad * sizeof(int32_t)));
+        // step 1 operands over the padded term list: A[k][t] = P2[k][c2(t)], B[j][t] = xin[t] P1[j][c1(t)]
+        if (dt_split(SrcGather{P2, (int64_t)C[2], d_tmap, tcol, 2, nullptr}, tpad, a, st) != cudaSuccess ||
+            dt_split(SrcGather{P1, (int64_t)C[1], d_tmap, tcol, 1, xin}, tpad, b, st) != cudaSuccess)
+            return tc_err(err, "core: split failed");
+    }
+    // groups in chunks: W (pairs) and its split form stay within about 4 GB, and each chunk
+    // is one exact K range of step 2
+    const int64_t gc = std::max<int64_t>(1, std::min<int64_t>({C0, (int64_t)DT_MAXK, ((int64_t)4 << 30) / (16 * nn)}));
+    float2* W = ar.get<float2>(gc * nn);
+    DtOp ws = dt_alloc(ar, nn, pad32(gc), 1), p0s = dt_alloc(ar, r0, pad32(gc), 1);
+    if (!W || !ws.ok() || !p0s.ok()) return tc_err(err, "core: out of memory", LS_ERR_OOM);
+    const DtOpts opt;
+    for (int64_t g0 = 0; g0 < C0; g0 += gc) {
+        const int64_t ng = std::min(gc, C0 - g0);
+        int rc;
+        {
+            Scope sc("core.step1", st);
+            // step 1: W[g][j][k] = sum_{t in group g} xin[t] P1[j][c1(t)] P2[k][c2(t)]  (k on the lanes)
+            DtK k1;
+            k1.kb_lo = d_kb + g0;
+            rc = dt_gemm(a, b, r2, r1, ng, DtOut{W, r2, nn, DT_PAIR}, opt, flag, st, err, k1);
+            if (rc != LS_OK) return rc;
+        }
+        DtOp w = ws, p = p0s;
+        {
+            Scope sc("core.wsplit", st);
+            if (dt_split_tr(W, nn, ng, w, st) != cudaSuccess ||
+                dt_split(SrcF64{P0 + g0, C0, 1, 0, nullptr}, ng, p, st) != cudaSuccess)
+                return tc_err(err, "core: split failed");
+        }
+        {
+            Scope sc("core.step2", st);
+            // step 2: B[i][(j, k)] (+)= sum_g W[g][(j, k)] P0[i][g]  ((j, k) on the lanes)
+            DtOut o{Bc, nn, 0, DT_F64};
+            o.accumulate = g0 > 0;
+            rc = dt_gemm(w, p, nn, r0, 1, o, opt, flag, st, err);
+            if (rc != LS_OK) return rc;
+        }
+    }
+    return LS_OK;
 }
 
 }  // namespace ls

@@ -1404,16 +1404,6 @@ cudaError_t launch_transpose(const double* in, int64_t rows, int64_t cols, doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_core_group(const double* P1t, const double* P2t, int r1, int r2, const int32_t* tcol,
-                              const double* xin, const int32_t* perm, const int32_t* off, int cbeg, int cw, double* W,
-                              cudaStream_t st) {
-    const int64_t nn = (int64_t)r1 * r2;
-    dim3 grid((unsigned)((nn + 256 * kCoreOut - 1) / (256 * kCoreOut)), (unsigned)cw);
-    k_core_group_f64<<<grid, 256, 0, st>>>(P1t, P2t, r1, r2, tcol, xin, perm, off, cbeg, W);
-    count_kernels(1);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_core_f64(const double* P0, const double* P1t, const double* P2t, const int32_t* C, const int32_t* r,
                             const int32_t* tcol, const double* xin, const int32_t* perm, const int32_t* off,
                             double* W, int64_t w_cols, double* B, cudaStream_t st) {
@@ -1431,11 +1421,6 @@ cudaError_t launch_core_f64(const double* P0, const double* P1t, const double* P
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
-}
-
-cudaError_t launch_eval_m(const double* Z2, const int32_t* r, const double* B, int64_t N, const int32_t* zidx,
-                          int nslab, double* M, cudaStream_t st) {
-    return gemm_f64(r[0] * r[1], nslab, r[2], 1, RowK{B, r[2]}, EvalZ3{Z2, N, zidx}, StoreRow{M, nslab, 0}, st);
 }
 
 cudaError_t launch_eval_f64(const double* const Z[3], const int32_t* r, const double* B, int64_t N,

@@ -1,4 +1,4 @@
-// Tensor-core (tcgen05) kernels of the mixed-precision path.
+// FP64-grade tensor-core (tcgen05) products: exact slices; see ls_tc.cu.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -7,16 +7,6 @@
 #include <string>
 
 namespace ls {
-
-// Core contraction on tcgen05 tensor cores (BF16x3 split products, FP32
-// accumulation in TMEM): B[i][j][k] = sum_t xin[t] P0[i][c0] P1[j][c1] P2[k][c2].
-int tc_core(const double* P0, const double* P1, const double* P2, const int32_t* C, const int32_t* r,
-            const int32_t* tcol, const double* xin, const int32_t* perm, const int32_t* off, int64_t T, double* B,
-            int num_sms, cudaStream_t st, std::string* err);
-
-// Projection on tcgen05 tensor cores: P[k][c] = sum_i Z[k][i] a[c][i].
-int tc_project(const double* Z, int r, const double* a, int64_t C, int64_t N, double* P, cudaStream_t st,
-               std::string* err);
 
 // FP64-grade products on tcgen05 tensor cores: every operand row in eight
 // exact base-128 digits, digit products accumulated exactly per level in TMEM,
