@@ -663,9 +663,12 @@ int red_basis(RedState& R, CholJob* cj) {
         cj[l] = CholJob{M.Gz, M.Li, R.d_st + 3 + l, r};
     }
     {
+        // FP64-grade products on the tensor cores (exact slices)
         Scope sc("basis", st);
-        CUS(launch_pchol_vectors_n(3, L, Cs, ks, Cs, U, Hc, vg, R.gw, st));
-        CUS(launch_basis_n(3, vgc, Cs, kl, perm, isl, w, a, N, rs, Y, R.gw, st));
+        std::string err;
+        int rc = x64_pchol_vectors(3, L, Cs, ks, Cs, U, Hc, vg, &R.d_st[9].flag, st, &err);
+        if (rc == LS_OK) rc = x64_basis(3, vgc, kl, perm, w, isl, a, Cs, N, rs, Y, &R.d_st[9].flag, st, &err);
+        if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: basis: %s", err.c_str());
     }
     {
         Scope sc("cholqr2", st);

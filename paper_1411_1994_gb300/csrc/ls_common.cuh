@@ -91,16 +91,6 @@ cudaError_t launch_gram_weighted_n(int n, const double* const a[], const int64_t
 // H = L^T L (k x k) from the first k columns of L (C x kmax, row-major).
 cudaError_t launch_pchol_gram_n(int n, const double* const L[], const int64_t kmax[], const int k[],
                                 const int64_t C[], double* const H[], const GemmWs& W, cudaStream_t st);
-// Vg = L U diag(1/sqrt(H_nn)) (C x k): unit eigenvectors of L L^T from the
-// eigenvectors U (k x k, columns) of H after the Jacobi iteration.
-cudaError_t launch_pchol_vectors_n(int n, const double* const L[], const int64_t kmax[], const int k[],
-                                   const int64_t C[], const double* const U[], const double* const H[],
-                                   double* const Vg[], const GemmWs& W, cudaStream_t st);
-// Y[j][i] = inv_sqrt_lam[j] * sum_c V[c*ldv + perm[j]] w[c] a[c][i]  (j < r).
-cudaError_t launch_basis_n(int n, const double* const V[], const int64_t C[], const int64_t ldv[],
-                           const int32_t* const perm[], const double* const isl[], const double* const w[],
-                           const double* const a[], int64_t N, const int r[], double* const Y[], const GemmWs& W,
-                           cudaStream_t st);
 // G = Y Y^T (r x r; Y: r rows of length N).
 cudaError_t launch_syrk_rows_n(int n, const double* const Y[], const int r[], int64_t N, double* const G[],
                                const GemmWs& W, cudaStream_t st);

@@ -379,19 +379,6 @@ struct StoreRowW {       // C[m*ld + n] = w[m] w[n] v
 };
 
 // basis: A(m=j, kk=c) = V[c*ldv + perm[j]] * w[c] * inv_sqrt_lam[j]
-struct BasisA {
-    static constexpr bool kfast = false;
-    const double* V; int64_t ldv; const int32_t* perm; const double* w; const double* isl;
-    __device__ double operator()(int, int m, int k) const { return V[k * ldv + perm[m]] * w[k] * isl[m]; }
-};
-// eigenvectors of G from those of H = L^T L: column n scaled by 1/sqrt(H_nn)
-struct StoreColScaled {
-    double* p; int64_t ld; const double* H; int64_t ldh;
-    __device__ void operator()(int, int m, int n, double v) const {
-        const double h = H[(int64_t)n * ldh + n];
-        p[m * ld + n] = h > 0.0 ? v / sqrt(h) : 0.0;
-    }
-};
 // core: A(m=i, k=t) = P0[i*C0 + c0(t)] * xin[t]
 struct CoreA {
     static constexpr bool kfast = true;
@@ -1257,29 +1244,6 @@ cudaError_t launch_pchol_gram_n(int n, const double* const L[], const int64_t km
     g.n = n;
     for (int i = 0; i < n; ++i)
         g.j[i] = {ColK{L[i], kmax[i]}, KRowN{L[i], kmax[i]}, StoreRow{H[i], k[i], 0}, k[i], k[i], (int)C[i], 1};
-    return gemm_group(g, W, st);
-}
-
-cudaError_t launch_pchol_vectors_n(int n, const double* const L[], const int64_t kmax[], const int k[],
-                                   const int64_t C[], const double* const U[], const double* const H[],
-                                   double* const Vg[], const GemmWs& W, cudaStream_t st) {
-    GGroup<RowK, KRowN, StoreColScaled> g{};
-    g.n = n;
-    for (int i = 0; i < n; ++i)
-        g.j[i] = {RowK{L[i], kmax[i]}, KRowN{U[i], k[i]}, StoreColScaled{Vg[i], k[i], H[i], k[i]}, (int)C[i], k[i],
-                  k[i], 0};
-    return gemm_group(g, W, st);
-}
-
-cudaError_t launch_basis_n(int n, const double* const V[], const int64_t C[], const int64_t ldv[],
-                           const int32_t* const perm[], const double* const isl[], const double* const w[],
-                           const double* const a[], int64_t N, const int r[], double* const Y[], const GemmWs& W,
-                           cudaStream_t st) {
-    GGroup<BasisA, KRowN, StoreRow> g{};
-    g.n = n;
-    for (int i = 0; i < n; ++i)
-        g.j[i] = {BasisA{V[i], ldv[i], perm[i], w[i], isl[i]}, KRowN{a[i], N}, StoreRow{Y[i], N, 0}, r[i], (int)N,
-                  (int)C[i], 0};
     return gemm_group(g, W, st);
 }
 

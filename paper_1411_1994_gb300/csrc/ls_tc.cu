@@ -424,6 +424,79 @@ int x64_apply(int n, const double* const T[], const int r[], const double* const
     return gemm_x64(sp.data(), n, flag, st, err);
 }
 
+// Y_l[m][x] = isl[m] sum_c V_l[c][perm[m]] w[c] a_l[c][x]  (the basis step): the row
+// factor A~[m][c] = isl[m] V[c][perm[m]] w[c] is formed first, a_l is transposed, and
+// the product is taken as Y^T = a_l^T A~^T with a transposed store.
+__global__ void k_basis_rows(const double* __restrict__ V, int64_t ldv, const int32_t* __restrict__ perm,
+                             const double* __restrict__ w, const double* __restrict__ isl, int64_t C, int r,
+                             double* __restrict__ At) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)r * C) return;
+    const int m = (int)(e / C);
+    const int64_t c = e - (int64_t)m * C;
+    At[e] = V[c * ldv + perm[m]] * w[c] * isl[m];
+}
+
+int x64_basis(int n, const double* const V[], const int64_t ldv[], const int32_t* const perm[],
+              const double* const w[], const double* const isl[], const double* const a[], const int64_t C[],
+              int64_t N, const int r[], double* const Y[], int* flag, cudaStream_t st, std::string* err) {
+    Arena ar(st);
+    std::vector<X64Op> as(n), ys(n);
+    std::vector<X64Spec> sp(n);
+    for (int l = 0; l < n; ++l) {
+        const int64_t kp = pad64(C[l]);
+        double* At = ar.get<double>((int64_t)r[l] * C[l]);
+        double* aT = ar.get<double>(N * C[l]);
+        as[l] = x64_alloc(ar, N, kp);
+        ys[l] = x64_alloc(ar, r[l], kp);
+        if (!At || !aT || !as[l].ok() || !ys[l].ok()) return tc_err(err, "x64_basis: out of memory", LS_ERR_OOM);
+        const int64_t ne = (int64_t)r[l] * C[l];
+        k_basis_rows<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(V[l], ldv[l], perm[l], w[l], isl[l], C[l], r[l], At);
+        count_kernels(1);
+        if (cudaGetLastError() != cudaSuccess || launch_transpose(a[l], C[l], N, aT, st) != cudaSuccess ||
+            launch_split_x64(aT, N, C[l], C[l], nullptr, as[l], st) != cudaSuccess ||
+            launch_split_x64(At, r[l], C[l], C[l], nullptr, ys[l], st) != cudaSuccess)
+            return tc_err(err, "x64_basis: split failed");
+        sp[l] = X64Spec{&as[l], &ys[l], N, r[l], TcOut{Y[l], N, 0, OUT_F64, 0}, 1};
+    }
+    return gemm_x64(sp.data(), n, flag, st, err);
+}
+
+// rs[j] = 1/sqrt(H[j][j]) where positive, else 0
+__global__ void k_diag_rsqrt(const double* __restrict__ H, int k, double* __restrict__ rs) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= k) return;
+    const double h = H[(int64_t)j * k + j];
+    rs[j] = h > 0.0 ? 1.0 / sqrt(h) : 0.0;
+}
+
+// Vg_l[c][j] = sum_i L_l[c][i] U_l[i][j] / sqrt(H_l[j][j])  (C_l x k_l, row stride k_l; L_l has
+// row stride kmax_l): eigenvectors of the compressed Gram matrix, as Vg^T = (U^T scaled) L^T
+// with a transposed store.
+int x64_pchol_vectors(int n, const double* const L[], const int64_t kmax[], const int k[], const int64_t C[],
+                      const double* const U[], const double* const H[], double* const Vg[], int* flag,
+                      cudaStream_t st, std::string* err) {
+    Arena ar(st);
+    std::vector<X64Op> us(n), ls(n);
+    std::vector<X64Spec> sp(n);
+    for (int l = 0; l < n; ++l) {
+        const int64_t kp = pad64(k[l]);
+        double* Ut = ar.get<double>((int64_t)k[l] * k[l]);
+        double* rs = ar.get<double>(k[l]);
+        us[l] = x64_alloc(ar, k[l], kp);
+        ls[l] = x64_alloc(ar, C[l], kp);
+        if (!Ut || !rs || !us[l].ok() || !ls[l].ok()) return tc_err(err, "x64_pchol_vectors: out of memory", LS_ERR_OOM);
+        k_diag_rsqrt<<<(k[l] + 127) / 128, 128, 0, st>>>(H[l], k[l], rs);
+        count_kernels(1);
+        if (cudaGetLastError() != cudaSuccess || launch_transpose(U[l], k[l], k[l], Ut, st) != cudaSuccess ||
+            launch_split_x64(Ut, k[l], k[l], k[l], rs, us[l], st) != cudaSuccess ||
+            launch_split_x64(L[l], C[l], k[l], kmax[l], nullptr, ls[l], st) != cudaSuccess)
+            return tc_err(err, "x64_pchol_vectors: split failed");
+        sp[l] = X64Spec{&us[l], &ls[l], k[l], C[l], TcOut{Vg[l], k[l], 0, OUT_F64, 0}, 1};
+    }
+    return gemm_x64(sp.data(), n, flag, st, err);
+}
+
 // D = A B^T (A: M x K, B: N x K, D: M x N, row-major), then a synchronised status check
 int x64_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* D, cudaStream_t st,
                 std::string* err) {

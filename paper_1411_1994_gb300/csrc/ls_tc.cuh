@@ -23,6 +23,17 @@ int x64_project(int n, const double* const Z[], const int r[], const double* con
 // dst_l = T_l src_l  (T_l: r_l x r_l, src_l and dst_l: r_l x N).
 int x64_apply(int n, const double* const T[], const int r[], const double* const src[], int64_t N,
               double* const dst[], int* flag, cudaStream_t st, std::string* err);
+// Y_l[m][x] = isl_l[m] sum_c V_l[c][perm_l[m]] w_l[c] a_l[c][x]  (V_l: C_l x ldv_l;
+// a_l: C_l x N; Y_l: r_l x N): the basis vectors from the eigenvectors of the
+// compressed Gram matrix.
+int x64_basis(int n, const double* const V[], const int64_t ldv[], const int32_t* const perm[],
+              const double* const w[], const double* const isl[], const double* const a[], const int64_t C[],
+              int64_t N, const int r[], double* const Y[], int* flag, cudaStream_t st, std::string* err);
+// Vg_l[c][j] = sum_i L_l[c][i] U_l[i][j] / sqrt(H_l[j][j])  (0 where H_jj <= 0; L_l: C_l rows of
+// stride kmax_l; U_l, H_l: k_l x k_l; Vg_l: C_l x k_l).
+int x64_pchol_vectors(int n, const double* const L[], const int64_t kmax[], const int k[], const int64_t C[],
+                      const double* const U[], const double* const H[], double* const Vg[], int* flag,
+                      cudaStream_t st, std::string* err);
 // D = A B^T (row-major, device memory), synchronised, with the status checked.
 int x64_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* D, cudaStream_t st,
                 std::string* err);
