@@ -805,6 +805,39 @@ int dt_gemm(const DtOp& A, const DtOp& B, int64_t M, int64_t N, int64_t batch, c
     return LS_OK;
 }
 
+// One pinned host buffer per process for the core's uploads, so that the copy is
+// asynchronous: a pageable upload of this size makes the host wait for the stream to
+// drain, and the GPU then idles while the host enqueues the next kernels. The next
+// upload waits for the previous copy (long finished: every reduction synchronises
+// its stream before it returns).
+struct PinnedStage {
+    std::mutex mu;
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+};
+PinnedStage& pinned_stage() {
+    static PinnedStage* s = new PinnedStage();
+    return *s;
+}
+cudaError_t upload_pinned(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    PinnedStage& S = pinned_stage();
+    std::lock_guard<std::mutex> g(S.mu);
+    cudaError_t e;
+    if (S.done && (e = cudaEventSynchronize(S.done)) != cudaSuccess) return e;
+    if (bytes > S.cap) {
+        if (S.p) cudaFreeHost(S.p);
+        S.p = nullptr;
+        S.cap = 0;
+        if ((e = cudaMallocHost(&S.p, bytes)) != cudaSuccess) return e;
+        S.cap = bytes;
+    }
+    if (!S.done && (e = cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming)) != cudaSuccess) return e;
+    memcpy(S.p, src, bytes);
+    if ((e = cudaMemcpyAsync(dst, S.p, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    return cudaEventRecord(S.done, st);
+}
+
 }  // namespace
 
 // Operands of the slab evaluation that depend only on the reduced tensor, built
@@ -951,20 +984,22 @@ int dt_core(const double* P0, const double* P1, const double* P2, const int32_t*
         kb_lo[g + 1] = kb_lo[g] + (n + DT_BK - 1) / DT_BK;
     }
     const int64_t tpad = (int64_t)kb_lo[C0] * DT_BK;
-    std::vector<int32_t> tmap(tpad, -1);
+    // one upload: the group k-block offsets, then the padded term list
+    std::vector<int32_t> up((C0 + 1) + tpad, -1);
+    std::copy(kb_lo.begin(), kb_lo.end(), up.begin());
+    int32_t* tmap = up.data() + (C0 + 1);
     for (int64_t g = 0; g < C0; ++g)
         for (int u = 0; u < off[g + 1] - off[g]; ++u) tmap[(int64_t)kb_lo[g] * DT_BK + u] = perm[off[g] + u];
     Arena ar(st);
-    int* d_kb = ar.get<int>(C0 + 1);
-    int32_t* d_tmap = ar.get<int32_t>(tpad);
+    int* d_kb = ar.get<int>((C0 + 1) + tpad);
+    int32_t* d_tmap = d_kb + (C0 + 1);
     DtOp a = dt_alloc(ar, r2, tpad, 1), b = dt_alloc(ar, r1, tpad, 1);
-    if (!d_kb || !d_tmap || !a.ok() || !b.ok()) return tc_err(err, "core: out of memory", LS_ERR_OOM);
+    if (!d_kb || !a.ok() || !b.ok()) return tc_err(err, "core: out of memory", LS_ERR_OOM);
     {
         Scope sc("core.operands", st);
-        if (cudaMemcpyAsync(d_kb, kb_lo.data(), (C0 + 1) * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(d_tmap, tmap.data(), tpad * sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        if (upload_pinned(d_kb, up.data(), up.size() * sizeof(int32_t), st) != cudaSuccess)
             return tc_err(err, "core: upload failed");
-        count_h2d((int64_t)((C0 + 1) * sizeof(int) + tpad * sizeof(int32_t)));
+        count_h2d((int64_t)(up.size() * sizeof(int32_t)));
         // step 1 operands over the padded term list: A[k][t] = P2[k][c2(t)], B[j][t] = xin[t] P1[j][c1(t)]
         if (dt_split(SrcGather{P2, (int64_t)C[2], d_tmap, tcol, 2, nullptr}, tpad, a, st) != cudaSuccess ||
             dt_split(SrcGather{P1, (int64_t)C[1], d_tmap, tcol, 1, xin}, tpad, b, st) != cudaSuccess)
