@@ -558,7 +558,9 @@ int red_after_pchol(RedState& R, JacobiJob* jj) {
         if (R.hs[l].flag == FLAG_TIMEOUT)
             return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: pivoted Cholesky barrier timed out (mode %d)", l);
     CUS(cudaMemsetAsync(R.d_st, 0, 9 * sizeof(DevStatus), st));
-    const int kdf = jacobi_df_max_k();
+    // the two-stage FP32 Jacobi for every k up to this (the block form in shared memory or
+    // in one cooperative grid); beyond it the FP64 grid Jacobi
+    const int kdf = 8192;
     const double* L[3];
     double* H[3];
     int64_t Cs[3];
@@ -870,8 +872,9 @@ cudaError_t join(cudaStream_t to, cudaStream_t from) {
 // U0 = I + F1 (FP32 accuracy), U0 is orthonormalised in FP64 (Cholesky of
 // U0^T U0), H' = Uo^T H Uo is formed in FP64, a second Jacobi run on the
 // nearly diagonal H' gives its eigenvalues (written to the diagonal of H')
-// and I + F2, and V = Uo + Uo F2; H' then takes the place of H. Larger k:
-// the FP64 grid Jacobi. The eps-rule tolerances: 1e-6 for the first run
+// and I + F2, and V = Uo + Uo F2; H' then takes the place of H. Both runs use
+// the block Jacobi, in one cluster's shared memory where k fits and in one
+// cooperative grid otherwise; beyond k = 8192 the FP64 grid Jacobi. The eps-rule tolerances: 1e-6 for the first run
 // (FP32), 1e-10 for the second; forced ranks use the same.
 int eigen_all(std::vector<RedState>& R, ls_ctx* const* ctxs, int n, const std::vector<JacobiJob>& jj, cudaStream_t s0) {
     ls_ctx* c0 = ctxs[0];
@@ -908,10 +911,19 @@ int eigen_all(std::vector<RedState>& R, ls_ctx* const* ctxs, int n, const std::v
         if (e != cudaSuccess) return err(e, "Jacobi launch");
     }
     if (s1.empty()) return LS_OK;
-    // the block form where every matrix fits it, else the scalar shared-memory form
-    int kmax = 0;
-    for (const DfJob& J : s1) kmax = std::max(kmax, J.k);
-    auto run_df = kmax <= jacobi_blk_max_k() ? launch_jacobi_blk : launch_jacobi_df;
+    // the block form: in one cluster's shared memory where k fits, else in one cooperative grid
+    // with the matrices in global memory
+    const int kblk = jacobi_blk_max_k();
+    const int nsm = c0->num_sms;
+    auto run_df = [kblk, nsm](const DfJob* jobs, int nj, int max_sweeps, cudaStream_t st) -> cudaError_t {
+        std::vector<DfJob> small, large;
+        for (int i = 0; i < nj; ++i) (jobs[i].k <= kblk ? small : large).push_back(jobs[i]);
+        cudaError_t e = cudaSuccess;
+        if (!small.empty()) e = launch_jacobi_blk(small.data(), (int)small.size(), max_sweeps, st);
+        if (e == cudaSuccess && !large.empty())
+            e = launch_jacobi_gblk(large.data(), (int)large.size(), max_sweeps, nsm, st);
+        return e;
+    };
     {
         Scope sc("jacobi.run1", s0);
         if ((e = run_df(s1.data(), (int)s1.size(), 60, s0)) != cudaSuccess) return err(e, "Jacobi (first run)");

@@ -159,6 +159,9 @@ cudaError_t launch_jacobi_df(const DfJob* jobs, int njobs, int max_sweeps, cudaS
 // blocks instead of k - 1.
 int jacobi_blk_max_k();
 cudaError_t launch_jacobi_blk(const DfJob* jobs, int njobs, int max_sweeps, cudaStream_t st);
+// The block form in one cooperative grid with the matrices in global memory
+// (any k; the same rounds, criteria and arithmetic; one confirming sweep more).
+cudaError_t launch_jacobi_gblk(const DfJob* jobs, int njobs, int max_sweeps, int num_sms, cudaStream_t st);
 
 // V = I (C x C).
 cudaError_t launch_identity(double* V, int64_t C, cudaStream_t st);

@@ -26,6 +26,7 @@
 #include <algorithm>
 
 #include "ls_common.cuh"
+#include "ls_grid.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -725,6 +726,355 @@ __global__ void __launch_bounds__(kEigThreads) k_chol32_multi(const CholJob* job
     if (tid == 0 && s_bad) atomicCAS(&J.st->flag, FLAG_OK, FLAG_NOT_SPD);
 }
 
+
+// ---------------------------------------------------------------------------
+// The same block Jacobi for matrices beyond one CTA's shared memory: one
+// cooperative grid for every matrix of the launch, D (hi/lo FP32), E (FP32,
+// full symmetric storage), the rotation accumulator F and the pair-block
+// rotations Q in global memory (L2-resident: about 2 MB a matrix at k = 512).
+// A round runs in two phases between bounded grid barriers:
+//   A: a warp per pair-block loads its 16 x 16 diagonal block and 16 diagonal
+//      entries into shared memory, runs the inner sweep(s) exactly as the
+//      cluster kernel does (same rotations, same order, same arithmetic),
+//      and writes back the block, D and Q = I + F_Q;
+//   B: a half-warp per off-diagonal tile of two pair-blocks of which one
+//      rotated (E_ab <- Q_a^T E_ab Q_b, both triangles), and a half-warp per
+//      pair-block and group of 16 F rows (F <- F + F_Q + F F_Q).
+// Matrices of different sizes keep their own round and sweep counters. A
+// matrix stops after a sweep in which no pair qualified, or at the sweep
+// limit. The decision is read by every CTA from the same counter after the
+// same barrier, so control flow stays uniform. The outputs and the sweep
+// report are those of the cluster kernel. For the same input it gives the
+// same result, with one more sweep reported: that sweep is the empty one
+// that confirms convergence, where the cluster kernel scans instead.
+// ---------------------------------------------------------------------------
+constexpr int kGbThreads = 512;
+constexpr int kGbMaxModes = 128;
+
+struct GbMode {
+    const double* H; double* outD; double* outF; DevStatus* st;
+    int64_t ldd; int k; int add_identity;
+    float floor, tau, tol2;
+    int K, ldE, nb, m;
+    DF* D; float* E; float* F; float* Q; int* act; unsigned int* cnt;   // cnt[2]: rotations a sweep (parity)
+};
+struct GbArgs {
+    const GbMode* m; int nm; int max_sweeps; DevStatus* bar;
+};
+
+// per-warp scratch of phase A
+struct GbWarp {
+    float Eb[BJ2][SP];
+    float Fq[BJ2][SP];
+    DF Dl[BJ2];
+    InRot ri[BJ2 / 2];
+};
+
+__global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
+    __shared__ int s_sweep[kGbMaxModes], s_round[kGbMaxModes], s_done[kGbMaxModes], s_base[kGbMaxModes];
+    __shared__ int s_pa[kGbMaxModes + 1], s_pt[kGbMaxModes + 1], s_pf[kGbMaxModes + 1];
+    __shared__ int s_live;
+    extern __shared__ __align__(16) unsigned char gb_smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nwarp_cta = kGbThreads / 32;
+    GbWarp& W = reinterpret_cast<GbWarp*>(gb_smem)[warp];
+    const int gwarp = blockIdx.x * nwarp_cta + warp, nwarps = gridDim.x * nwarp_cta;
+    const int nm = A.nm;
+
+    // initial state: D from diag(H), E from the off-diagonal of H, F = 0, counters 0
+    for (int j = 0; j < nm; ++j) {
+        const GbMode& J = A.m[j];
+        const int64_t ne = (int64_t)J.K * J.ldE;
+        for (int64_t e = blockIdx.x * (int64_t)kGbThreads + tid; e < ne; e += (int64_t)gridDim.x * kGbThreads) {
+            const int r = (int)(e / J.ldE), c = (int)(e - (int64_t)r * J.ldE);
+            J.E[e] = (r < J.k && c < J.k && r != c) ? (float)J.H[(int64_t)r * J.k + c] : 0.f;
+            if (c == 0) J.D[r] = df_from(r < J.k ? J.H[(int64_t)r * J.k + r] : 0.0);
+        }
+        const int64_t nf = (int64_t)J.K * J.K;
+        for (int64_t e = blockIdx.x * (int64_t)kGbThreads + tid; e < nf; e += (int64_t)gridDim.x * kGbThreads) J.F[e] = 0.f;
+        if (blockIdx.x == 0 && tid < 2) J.cnt[tid] = 0;
+    }
+    if (tid < nm) {
+        s_sweep[tid] = 0;
+        s_round[tid] = 0;
+        s_done[tid] = 0;
+        s_base[tid] = A.m[tid].st->sweeps;
+    }
+    bool ok = group_barrier(A.bar, gridDim.x);
+
+    while (ok) {
+        // this round's work: prefix counts over the live matrices (same in every CTA)
+        if (tid == 0) {
+            int pa = 0, pt = 0, pf = 0, live = 0;
+            for (int j = 0; j < nm; ++j) {
+                s_pa[j] = pa;
+                s_pt[j] = pt;
+                s_pf[j] = pf;
+                if (!s_done[j]) {
+                    const GbMode& J = A.m[j];
+                    pa += J.nb;
+                    pt += J.nb * (J.nb - 1) / 2;
+                    pf += J.nb * (J.K / BJ2);
+                    live = 1;
+                }
+            }
+            s_pa[nm] = pa;
+            s_pt[nm] = pt;
+            s_pf[nm] = pf;
+            s_live = live;
+        }
+        __syncthreads();
+        if (!s_live) break;
+
+        // ---- phase A: inner sweeps, a warp per pair-block
+        for (int item = gwarp; item < s_pa[nm]; item += nwarps) {
+            int j = 0;
+            while (j < nm - 1 && (s_pa[j + 1] <= item || s_done[j])) ++j;
+            const GbMode& J = A.m[j];
+            const int a = item - s_pa[j], t = s_round[j];
+            const Crit qualifies{J.floor, J.tau, J.tol2};
+            int I, Jb;
+            rr_pair_e(t, a, J.m, I, Jb);
+            for (int e = lane; e < BJ2SQ; e += 32) {
+                const int u = e >> 4, v = e & 15;
+                W.Eb[u][v] = u != v ? J.E[(int64_t)bj_index(I, Jb, u) * J.ldE + bj_index(I, Jb, v)] : 0.f;
+                W.Fq[u][v] = 0.f;
+            }
+            if (lane < BJ2) W.Dl[lane] = J.D[bj_index(I, Jb, lane)];
+            __syncwarp();
+            const int n_inner = t == 0 ? BJ2 - 1 : BJ;
+            unsigned int nrot = 0;
+            for (int it = 0; it < n_inner; ++it) {
+                if (lane < BJ2 / 2) {
+                    int u, v;
+                    if (t == 0) rr_pair_e(it, lane, BJ2, u, v);
+                    else { u = lane; v = BJ + ((lane + it) & (BJ - 1)); }
+                    InRot r{1.f, 0.f, 0.f, u | (v << 8)};
+                    if (bj_index(I, Jb, u) < J.k && bj_index(I, Jb, v) < J.k) {
+                        const float epq = W.Eb[u][v];
+                        if (qualifies(W.Dl[u], W.Dl[v], epq)) {
+                            const RotCS g = jacobi_rot(df_diff(W.Dl[v], W.Dl[u]), epq);
+                            r = InRot{g.c, g.s, g.cm1, u | (v << 8) | (1 << 16)};
+                            const float te = g.t * epq;
+                            W.Dl[u] = df_add(W.Dl[u], -te);
+                            W.Dl[v] = df_add(W.Dl[v], te);
+                            W.Eb[u][v] = 0.f;
+                            W.Eb[v][u] = 0.f;
+                            ++nrot;
+                        }
+                    }
+                    W.ri[lane] = r;
+                }
+                __syncwarp();
+                // E <- J^T E J on the 2 x 2 blocks (i, i2), i != i2
+                for (int e = lane; e < 64; e += 32) {
+                    const int i = e >> 3, i2 = e & 7;
+                    if (i == i2) continue;
+                    const InRot ra = W.ri[i], rb = W.ri[i2];
+                    if (!((ra.uv | rb.uv) & (1 << 16))) continue;
+                    const int pa = ra.uv & 255, qa = (ra.uv >> 8) & 255, pc = rb.uv & 255, qc = (rb.uv >> 8) & 255;
+                    const float x0 = W.Eb[pa][pc], x1 = W.Eb[pa][qc];
+                    const float x2 = W.Eb[qa][pc], x3 = W.Eb[qa][qc];
+                    const float ypp = ra.c * x0 - ra.s * x2, ypq = ra.c * x1 - ra.s * x3;
+                    const float yqp = ra.s * x0 + ra.c * x2, yqq = ra.s * x1 + ra.c * x3;
+                    W.Eb[pa][pc] = rb.c * ypp - rb.s * ypq;
+                    W.Eb[pa][qc] = rb.s * ypp + rb.c * ypq;
+                    W.Eb[qa][pc] = rb.c * yqp - rb.s * yqq;
+                    W.Eb[qa][qc] = rb.s * yqp + rb.c * yqq;
+                }
+                // F_Q <- F_Q J, c - 1 kept apart
+                for (int e = lane; e < 8 * BJ2; e += 32) {
+                    const InRot r = W.ri[e >> 4];
+                    if (!(r.uv & (1 << 16))) continue;
+                    const int y = e & 15, u = r.uv & 255, v = (r.uv >> 8) & 255;
+                    const float fp = W.Fq[y][u], fv = W.Fq[y][v];
+                    float np = fp + (fp * r.cm1 - fv * r.s);
+                    float nv = fv + (fp * r.s + fv * r.cm1);
+                    if (y == u) { np += r.cm1; nv += r.s; }
+                    if (y == v) { np -= r.s; nv += r.cm1; }
+                    W.Fq[y][u] = np;
+                    W.Fq[y][v] = nv;
+                }
+                __syncwarp();
+            }
+            for (int o = 16; o; o >>= 1) nrot += __shfl_xor_sync(0xffffffffu, nrot, o);
+            float* Qa = J.Q + (int64_t)a * BJ2SQ;
+            for (int e = lane; e < BJ2SQ; e += 32) {
+                const int u = e >> 4, v = e & 15;
+                if (u != v) J.E[(int64_t)bj_index(I, Jb, u) * J.ldE + bj_index(I, Jb, v)] = W.Eb[u][v];
+                Qa[e] = W.Fq[u][v];   // F_Q; Q = I + F_Q
+            }
+            if (lane < BJ2) J.D[bj_index(I, Jb, lane)] = W.Dl[lane];
+            if (lane == 0) {
+                J.act[a] = nrot > 0;
+                if (nrot) atomicAdd(&J.cnt[s_sweep[j] & 1], nrot);
+            }
+            __syncwarp();
+        }
+        if (!(ok = group_barrier(A.bar, gridDim.x))) break;
+
+        // ---- sweep ends: every CTA reads the finished sweep's count (stable in this phase)
+        if (tid < nm && !s_done[tid]) {
+            const GbMode& J = A.m[tid];
+            if (s_round[tid] == J.m - 2) {
+                const int sw = s_sweep[tid];
+                const unsigned int c = *(volatile unsigned int*)&J.cnt[sw & 1];
+                if (blockIdx.x == 0) {
+                    J.st->sweep_active[(s_base[tid] + sw) & 63] = c;
+                    J.cnt[(sw + 1) & 1] = 0;
+                }
+                if (c == 0) {
+                    s_done[tid] = 2;          // converged: this sweep confirmed it
+                } else if (sw + 1 >= A.max_sweeps) {
+                    s_done[tid] = 3;          // sweep limit
+                    if (blockIdx.x == 0) atomicCAS(&J.st->flag, FLAG_OK, FLAG_NOCONVERGE);
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- phase B: tiles (two per warp, a half-warp each) and F rows
+        {
+            const int h = lane >> 4, l16 = lane & 15;
+            const int r0 = l16 >> 1, c0 = (l16 & 1) * BJ;
+            const int ntile = s_pt[nm];
+            for (int task0 = 2 * gwarp; task0 < ntile; task0 += 2 * nwarps) {
+                const int task = task0 + h;
+                const bool live = task < ntile;
+                const int tt = live ? task : task0;
+                int j = 0;
+                while (j < nm - 1 && (s_pt[j + 1] <= tt || s_done[j] == 1)) ++j;
+                const GbMode& J = A.m[j];
+                // tile index -> (a, b), a < b: row a has nb - 1 - a tiles
+                int rem = tt - s_pt[j], a = 0;
+                while (a < J.nb - 1 && rem >= J.nb - 1 - a) { rem -= J.nb - 1 - a; ++a; }
+                const int b = a + 1 + rem;
+                const bool need = live && (J.act[a] | J.act[b]);
+                if (!__any_sync(0xffffffffu, need)) continue;
+                const int t = s_round[j];
+                int Ia, Ja, Ib, Jb2;
+                rr_pair_e(t, a, J.m, Ia, Ja);
+                rr_pair_e(t, b, J.m, Ib, Jb2);
+                const float* Qa = J.Q + (int64_t)a * BJ2SQ;
+                const float* Qb = J.Q + (int64_t)b * BJ2SQ;
+                float* E = J.E;
+                const int ldE = J.ldE;
+                const int colb = c0 ? Jb2 * BJ : Ib * BJ;
+                float t0[BJ], t1[BJ];
+#pragma unroll
+                for (int c = 0; c < BJ; ++c) { t0[c] = 0.f; t1[c] = 0.f; }
+#pragma unroll
+                for (int jj = 0; jj < BJ2; ++jj) {
+                    const float qa0 = Qa[jj * BJ2 + r0] + (jj == r0 ? 1.f : 0.f);
+                    const float qa1 = Qa[jj * BJ2 + r0 + BJ] + (jj == r0 + BJ ? 1.f : 0.f);
+                    const float* xr = E + (int64_t)bj_index(Ia, Ja, jj) * ldE + colb;
+                    const float4 x0 = *reinterpret_cast<const float4*>(xr);
+                    const float4 x1 = *reinterpret_cast<const float4*>(xr + 4);
+                    const float xv[BJ] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                    for (int c = 0; c < BJ; ++c) {
+                        t0[c] = fmaf(qa0, xv[c], t0[c]);
+                        t1[c] = fmaf(qa1, xv[c], t1[c]);
+                    }
+                }
+                const int cp = c0 ^ BJ;
+                const int row0 = bj_index(Ia, Ja, r0), row1 = bj_index(Ia, Ja, r0 + BJ);
+#pragma unroll
+                for (int half_row = 0; half_row < 2; ++half_row) {
+                    float z[BJ];
+#pragma unroll
+                    for (int c = 0; c < BJ; ++c) z[c] = 0.f;
+#pragma unroll
+                    for (int jj = 0; jj < BJ; ++jj) {
+                        const float tv = half_row ? t1[jj] : t0[jj];
+                        const float ov = __shfl_xor_sync(0xffffffffu, tv, 1);
+#pragma unroll
+                        for (int c = 0; c < BJ; ++c) {
+                            const float qs = Qb[(c0 + jj) * BJ2 + c0 + c] + ((c0 + jj) == (c0 + c) ? 1.f : 0.f);
+                            const float qo = Qb[(cp + jj) * BJ2 + c0 + c] + ((cp + jj) == (c0 + c) ? 1.f : 0.f);
+                            z[c] = fmaf(tv, qs, fmaf(ov, qo, z[c]));
+                        }
+                    }
+                    // every lane has read this tile's E rows (first product) before any store
+                    __syncwarp();
+                    if (live && need) {
+                        const int row = half_row ? row1 : row0;
+                        float* w = E + (int64_t)row * ldE + colb;
+                        *reinterpret_cast<float4*>(w) = make_float4(z[0], z[1], z[2], z[3]);
+                        *reinterpret_cast<float4*>(w + 4) = make_float4(z[4], z[5], z[6], z[7]);
+#pragma unroll
+                        for (int c = 0; c < BJ; ++c) E[(int64_t)(colb + c) * ldE + row] = z[c];
+                    }
+                }
+                __syncwarp();
+            }
+            // F <- F + F_Q + F F_Q: a half-warp per (pair-block, group of 16 rows)
+            const int nhw = nwarps * 2, ghw = gwarp * 2 + h;
+            const unsigned int half = 0xffffu << (lane & 16);
+            const int x = l16;
+            for (int item = ghw; item < s_pf[nm]; item += nhw) {
+                int j = 0;
+                while (j < nm - 1 && (s_pf[j + 1] <= item || s_done[j] == 1)) ++j;
+                const GbMode& J = A.m[j];
+                const int rest = item - s_pf[j], groups = J.K / BJ2;
+                const int a = rest / groups, g = rest - a * groups;
+                if (!J.act[a]) continue;   // uniform over the half-warp
+                int Ia, Ja;
+                rr_pair_e(s_round[j], a, J.m, Ia, Ja);
+                const float* fq = J.Q + (int64_t)a * BJ2SQ;
+                float fcol[BJ2];
+#pragma unroll
+                for (int y = 0; y < BJ2; ++y) fcol[y] = fq[y * BJ2 + x];
+                for (int jl = 0; jl < BJ2; ++jl) {
+                    const int jr = g * BJ2 + jl;
+                    float* row = J.F + (int64_t)jr * J.K;
+                    const float4 f0 = *reinterpret_cast<const float4*>(row + Ia * BJ);
+                    const float4 f1 = *reinterpret_cast<const float4*>(row + Ia * BJ + 4);
+                    const float4 f2 = *reinterpret_cast<const float4*>(row + Ja * BJ);
+                    const float4 f3 = *reinterpret_cast<const float4*>(row + Ja * BJ + 4);
+                    const float fv[BJ2] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w,
+                                           f2.x, f2.y, f2.z, f2.w, f3.x, f3.y, f3.z, f3.w};
+                    float acc = row[bj_index(Ia, Ja, x)];
+#pragma unroll
+                    for (int y = 0; y < BJ2; ++y) acc = fmaf(fv[y], fcol[y], acc);
+                    const int bj = jr / BJ;
+                    if (bj == Ia) acc += fq[(jr - Ia * BJ) * BJ2 + x];
+                    else if (bj == Ja) acc += fq[(BJ + jr - Ja * BJ) * BJ2 + x];
+                    __syncwarp(half);
+                    row[bj_index(Ia, Ja, x)] = acc;
+                }
+            }
+        }
+        // matrices that finished at this sweep end take no further part (after every warp of
+        // this CTA has finished decoding this round's items)
+        __syncthreads();
+        if (tid < nm && s_done[tid] >= 2) s_done[tid] = 1;
+        if (!(ok = group_barrier(A.bar, gridDim.x))) break;
+        // next round
+        if (tid < nm && !s_done[tid]) {
+            if (++s_round[tid] == A.m[tid].m - 1) {
+                s_round[tid] = 0;
+                ++s_sweep[tid];
+            }
+        }
+        __syncthreads();
+    }
+    // results (also after a failed barrier, so the host sees the flag and the partial state)
+    const bool timed_out = !ok;
+    for (int j = 0; j < nm; ++j) {
+        const GbMode& J = A.m[j];
+        for (int64_t e = blockIdx.x * (int64_t)kGbThreads + tid; e < (int64_t)J.k * J.k; e += (int64_t)gridDim.x * kGbThreads) {
+            const int r = (int)(e / J.k), c = (int)(e - (int64_t)r * J.k);
+            J.outF[e] = (double)J.F[(int64_t)r * J.K + c] + ((J.add_identity && r == c) ? 1.0 : 0.0);
+        }
+        for (int r = blockIdx.x * kGbThreads + tid; r < J.k; r += gridDim.x * kGbThreads) J.outD[(int64_t)r * J.ldd] = df_to(J.D[r]);
+        if (blockIdx.x == 0 && tid == 0) {
+            J.st->sweeps = s_base[j] + s_sweep[j] + 1;
+            if (timed_out) atomicCAS(&J.st->flag, FLAG_OK, FLAG_TIMEOUT);
+        }
+    }
+}
+
 }  // namespace
 
 int jacobi_df_max_k() {
@@ -863,6 +1213,67 @@ cudaError_t launch_jacobi_blk(const DfJob* jobs, int njobs, int max_sweeps, cuda
     }
     cudaFreeAsync(dm, st);
     return e;
+}
+
+// The grid block form: every job of the launch in one cooperative grid, the
+// matrices in global memory (any k). Jobs beyond kGbMaxModes run in further launches.
+cudaError_t launch_jacobi_gblk(const DfJob* jobs, int njobs, int max_sweeps, int num_sms, cudaStream_t st) {
+    for (int j0 = 0; j0 < njobs; j0 += kGbMaxModes) {
+        const int nm = std::min(kGbMaxModes, njobs - j0);
+        std::vector<GbMode> hm(nm);
+        std::vector<size_t> off(nm);
+        size_t total = 256;   // barrier status first
+        auto carve = [&](size_t bytes) {
+            const size_t o = total;
+            total += (bytes + 255) / 256 * 256;
+            return o;
+        };
+        struct Offs { size_t D, E, F, Q, act, cnt; };
+        std::vector<Offs> of(nm);
+        for (int i = 0; i < nm; ++i) {
+            const DfJob& J = jobs[j0 + i];
+            int m = (J.k + BJ - 1) / BJ;
+            m += m & 1;
+            if (m < 2) m = 2;
+            const int K = m * BJ, ldE = K + 4, nb = m / 2;
+            of[i] = Offs{carve(sizeof(DF) * (size_t)K), carve(4 * (size_t)K * ldE), carve(4 * (size_t)K * K),
+                         carve(4 * (size_t)nb * BJ2SQ), carve(4 * (size_t)nb), carve(8)};
+            hm[i] = GbMode{J.H, J.outD, J.outF, J.st, J.ldd, J.k, J.add_identity,
+                           (float)J.abs_floor, (float)J.tau, (float)(J.tol * J.tol), K, ldE, nb, m,
+                           nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        }
+        const size_t modes_at = carve(sizeof(GbMode) * nm);
+        unsigned char* ws = nullptr;
+        cudaError_t e = cudaMallocAsync(&ws, total, st);
+        if (e != cudaSuccess) return e;
+        for (int i = 0; i < nm; ++i) {
+            hm[i].D = reinterpret_cast<DF*>(ws + of[i].D);
+            hm[i].E = reinterpret_cast<float*>(ws + of[i].E);
+            hm[i].F = reinterpret_cast<float*>(ws + of[i].F);
+            hm[i].Q = reinterpret_cast<float*>(ws + of[i].Q);
+            hm[i].act = reinterpret_cast<int*>(ws + of[i].act);
+            hm[i].cnt = reinterpret_cast<unsigned int*>(ws + of[i].cnt);
+        }
+        e = cudaMemsetAsync(ws, 0, 256, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ws + modes_at, hm.data(), sizeof(GbMode) * nm, cudaMemcpyHostToDevice, st);
+        const size_t smem = sizeof(GbWarp) * (kGbThreads / 32);
+        int per_sm = 0;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_gblk, kGbThreads, smem);
+        if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+        if (e == cudaSuccess) {
+            GbArgs a{reinterpret_cast<const GbMode*>(ws + modes_at), nm, max_sweeps > 63 ? 63 : max_sweeps,
+                     reinterpret_cast<DevStatus*>(ws)};
+            void* args[] = {&a};
+            count_kernels(1);
+            e = cudaLaunchCooperativeKernel((void*)k_jacobi_gblk, dim3((unsigned)std::max(1, num_sms)),
+                                            dim3(kGbThreads), args, smem, st);
+        }
+        cudaFreeAsync(ws, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace ls

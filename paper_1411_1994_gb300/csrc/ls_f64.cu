@@ -13,48 +13,11 @@
 #include <vector>
 
 #include "ls_common.cuh"
+#include "ls_grid.cuh"
 
 namespace ls {
 
 namespace {
-
-constexpr long long kSpinLimit = 1LL << 24;   // ~1-2 s of polling with nanosleep
-
-// ---------------------------------------------------------------------------
-// bounded grid barrier (sense by generation counter); all CTAs must be
-// co-resident (cooperative launch). On timeout the flag is raised and every
-// CTA returns false.
-// ---------------------------------------------------------------------------
-__device__ bool group_barrier(DevStatus* st, unsigned int nblocks) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (nblocks <= 1) return true;
-    if (threadIdx.x == 0) {
-        volatile unsigned int* vgen = &st->bar_gen;
-        volatile int* vflag = &st->flag;
-        unsigned int g = *vgen;
-        __threadfence();
-        unsigned int arrived = atomicAdd(&st->bar_count, 1u);
-        int ok = 1;
-        if (arrived == nblocks - 1) {
-            atomicExch(&st->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&st->bar_gen, 1u);
-        } else {
-            long long it = 0;
-            while (*vgen == g) {
-                if (*vflag != FLAG_OK) { ok = 0; break; }
-                if (++it > kSpinLimit) { atomicCAS(&st->flag, FLAG_OK, FLAG_TIMEOUT); ok = 0; break; }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-        if (*vflag != FLAG_OK) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 __device__ __forceinline__ bool grid_barrier(DevStatus* st) { return group_barrier(st, gridDim.x); }
 
