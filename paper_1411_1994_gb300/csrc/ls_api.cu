@@ -710,7 +710,11 @@ int red_cholqr_mid(RedState& R) {
         if (rc == LS_OK) rc = x64_gram(3, yc, r64, N, nullptr, Gz, &R.d_st[9].flag, st, &err);
         if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: CholeskyQR: %s", err.c_str());
     }
-    CUS(launch_lowdin_n(3, gc, rs, D2, T, R.gw, st));
+    {
+        std::string err;
+        int rc = x64_lowdin(3, gc, rs, D2, T, &R.d_st[9].flag, st, &err);
+        if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: CholeskyQR series: %s", err.c_str());
+    }
     return LS_OK;
 }
 
@@ -939,12 +943,17 @@ int eigen_all(std::vector<RedState>& R, ls_ctx* const* ctxs, int n, const std::v
                 U0[j] = M.U0; S[j] = M.S; Sc[j] = M.S; D2[j] = M.SLi; T[j] = M.T1; Tc[j] = M.T1;
                 Uo[j] = M.Uo; Uc[j] = M.Uo; H[j] = M.H; T1[j] = M.T1; Hp[j] = M.Hp; ks[j] = M.k;
             }
-            cudaError_t e2 = launch_atb_sym_n(nm, U0, U0, ks, S, Rs.gw, s0);             // S = U0^T U0
-            if (e2 == cudaSuccess) e2 = launch_lowdin_n(nm, Sc, ks, D2, T, Rs.gw, s0);    // T = S^{-1/2}
-            if (e2 == cudaSuccess) e2 = launch_ab_n(nm, U0, Tc, ks, Uo, Rs.gw, s0);       // Uo = U0 T
-            if (e2 == cudaSuccess) e2 = launch_ab_n(nm, H, Uc, ks, T1, Rs.gw, s0);        // T1 = H Uo
-            if (e2 == cudaSuccess) e2 = launch_atb_sym_n(nm, Uc, T1, ks, Hp, Rs.gw, s0);  // H' = Uo^T T1
-            return e2;
+            // FP64-grade products on the tensor cores (exact slices)
+            int* fl = &Rs.d_st[9].flag;
+            const int no[3] = {0, 0, 0}, yes[3] = {1, 1, 1};
+            std::string err;
+            int rc = x64_small(nm, U0, yes, U0, no, ks, S, nullptr, fl, s0, &err);            // S = U0^T U0
+            if (rc == LS_OK) rc = x64_lowdin(nm, Sc, ks, D2, T, fl, s0, &err);               // T = S^{-1/2}
+            if (rc == LS_OK) rc = x64_small(nm, U0, no, Tc, no, ks, Uo, nullptr, fl, s0, &err);   // Uo = U0 T
+            if (rc == LS_OK) rc = x64_small(nm, H, no, Uc, no, ks, T1, nullptr, fl, s0, &err);    // T1 = H Uo
+            const double* T1c[3] = {T1[0], T1[1], T1[2]};
+            if (rc == LS_OK) rc = x64_small(nm, Uc, yes, T1c, no, ks, Hp, nullptr, fl, s0, &err); // H' = Uo^T T1
+            return rc == LS_OK ? cudaSuccess : (rc == LS_ERR_OOM ? cudaErrorMemoryAllocation : cudaErrorLaunchFailure);
         });
         if (e != cudaSuccess) return err(e, "re-projection");
     }
@@ -957,7 +966,10 @@ int eigen_all(std::vector<RedState>& R, ls_ctx* const* ctxs, int n, const std::v
         double* out[3];
         int ks[3];
         for (int j = 0; j < nm; ++j) { A[j] = ms[j]->Uo; B[j] = ms[j]->F2; out[j] = ms[j]->V; ks[j] = ms[j]->k; }
-        return launch_ab_plus_n(nm, A, B, A, ks, out, Rs.gw, s0);           // V = Uo + Uo F2
+        const int no[3] = {0, 0, 0};
+        std::string err;
+        const int rc = x64_small(nm, A, no, B, no, ks, out, A, &Rs.d_st[9].flag, s0, &err);   // V = Uo + Uo F2
+        return rc == LS_OK ? cudaSuccess : (rc == LS_ERR_OOM ? cudaErrorMemoryAllocation : cudaErrorLaunchFailure);
     });
     if (e != cudaSuccess) return err(e, "eigenvectors");
     for (int i = 0; i < n; ++i)

@@ -1025,23 +1025,34 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                 float fcol[BJ2];
 #pragma unroll
                 for (int y = 0; y < BJ2; ++y) fcol[y] = fq[y * BJ2 + x];
-                for (int jl = 0; jl < BJ2; ++jl) {
-                    const int jr = g * BJ2 + jl;
-                    float* row = J.F + (int64_t)jr * J.K;
-                    const float4 f0 = *reinterpret_cast<const float4*>(row + Ia * BJ);
-                    const float4 f1 = *reinterpret_cast<const float4*>(row + Ia * BJ + 4);
-                    const float4 f2 = *reinterpret_cast<const float4*>(row + Ja * BJ);
-                    const float4 f3 = *reinterpret_cast<const float4*>(row + Ja * BJ + 4);
-                    const float fv[BJ2] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w,
-                                           f2.x, f2.y, f2.z, f2.w, f3.x, f3.y, f3.z, f3.w};
-                    float acc = row[bj_index(Ia, Ja, x)];
+                // two rows at a time, their loads issued together
+                for (int jl = 0; jl < BJ2; jl += 2) {
+                    float fv[2][BJ2], acc[2];
 #pragma unroll
-                    for (int y = 0; y < BJ2; ++y) acc = fmaf(fv[y], fcol[y], acc);
-                    const int bj = jr / BJ;
-                    if (bj == Ia) acc += fq[(jr - Ia * BJ) * BJ2 + x];
-                    else if (bj == Ja) acc += fq[(BJ + jr - Ja * BJ) * BJ2 + x];
+                    for (int q = 0; q < 2; ++q) {
+                        const float* row = J.F + (int64_t)(g * BJ2 + jl + q) * J.K;
+                        const float4 f0 = *reinterpret_cast<const float4*>(row + Ia * BJ);
+                        const float4 f1 = *reinterpret_cast<const float4*>(row + Ia * BJ + 4);
+                        const float4 f2 = *reinterpret_cast<const float4*>(row + Ja * BJ);
+                        const float4 f3 = *reinterpret_cast<const float4*>(row + Ja * BJ + 4);
+                        fv[q][0] = f0.x; fv[q][1] = f0.y; fv[q][2] = f0.z; fv[q][3] = f0.w;
+                        fv[q][4] = f1.x; fv[q][5] = f1.y; fv[q][6] = f1.z; fv[q][7] = f1.w;
+                        fv[q][8] = f2.x; fv[q][9] = f2.y; fv[q][10] = f2.z; fv[q][11] = f2.w;
+                        fv[q][12] = f3.x; fv[q][13] = f3.y; fv[q][14] = f3.z; fv[q][15] = f3.w;
+                        acc[q] = row[bj_index(Ia, Ja, x)];
+                    }
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int jr = g * BJ2 + jl + q;
+#pragma unroll
+                        for (int y = 0; y < BJ2; ++y) acc[q] = fmaf(fv[q][y], fcol[y], acc[q]);
+                        const int bj = jr / BJ;
+                        if (bj == Ia) acc[q] += fq[(jr - Ia * BJ) * BJ2 + x];
+                        else if (bj == Ja) acc[q] += fq[(BJ + jr - Ja * BJ) * BJ2 + x];
+                    }
                     __syncwarp(half);
-                    row[bj_index(Ia, Ja, x)] = acc;
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) J.F[(int64_t)(g * BJ2 + jl + q) * J.K + bj_index(Ia, Ja, x)] = acc[q];
                 }
             }
         }

@@ -497,6 +497,98 @@ int x64_pchol_vectors(int n, const double* const L[], const int64_t kmax[], cons
     return gemm_x64(sp.data(), n, flag, st, err);
 }
 
+// out_l = op(A_l) op(B_l) (+ add_l) for k_l x k_l row-major matrices, op = identity or
+// transpose (ta, tb): the small dense products of the eigen-solver and of CholeskyQR.
+// The product is taken as X Y^T with X = op(A) and Y = op(B)^T in K-major rows
+// (transposed copies where needed); add_l (may alias nothing, may be null) is copied to
+// out_l first and the product added to it.
+int x64_small(int n, const double* const A[], const int ta[], const double* const B[], const int tb[],
+              const int k[], double* const out[], const double* const add[], int* flag, cudaStream_t st,
+              std::string* err) {
+    for (int g0 = 0; g0 < n; g0 += kX64MaxJobs) {
+        const int ng = std::min(kX64MaxJobs, n - g0);
+        Arena ar(st);
+        std::vector<X64Op> xs(ng), ys(ng);
+        std::vector<X64Spec> sp(ng);
+        for (int i = 0; i < ng; ++i) {
+            const int l = g0 + i, kk = k[l];
+            const int64_t kp = pad64(kk);
+            const double* X = A[l];
+            const double* Y = B[l];
+            if (ta[l] || !tb[l]) {
+                double* t = ar.get<double>((int64_t)kk * kk * 2);
+                if (!t) return tc_err(err, "x64_small: out of memory", LS_ERR_OOM);
+                if (ta[l]) {
+                    if (launch_transpose(A[l], kk, kk, t, st) != cudaSuccess) return tc_err(err, "x64_small: transpose");
+                    X = t;
+                }
+                if (!tb[l]) {
+                    if (launch_transpose(B[l], kk, kk, t + (int64_t)kk * kk, st) != cudaSuccess)
+                        return tc_err(err, "x64_small: transpose");
+                    Y = t + (int64_t)kk * kk;
+                }
+            }
+            xs[i] = x64_alloc(ar, kk, kp);
+            ys[i] = x64_alloc(ar, kk, kp);
+            if (!xs[i].ok() || !ys[i].ok()) return tc_err(err, "x64_small: out of memory", LS_ERR_OOM);
+            if (launch_split_x64(X, kk, kk, kk, nullptr, xs[i], st) != cudaSuccess ||
+                launch_split_x64(Y, kk, kk, kk, nullptr, ys[i], st) != cudaSuccess)
+                return tc_err(err, "x64_small: split failed");
+            if (add && add[l] && add[l] != out[l] &&
+                cudaMemcpyAsync(out[l], add[l], sizeof(double) * kk * kk, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return tc_err(err, "x64_small: copy failed");
+            sp[i] = X64Spec{&xs[i], &ys[i], kk, kk, TcOut{out[l], kk, 0, OUT_F64, (add && add[l]) ? 1 : 0}, 0};
+        }
+        int rc = gemm_x64(sp.data(), ng, flag, st, err);
+        if (rc != LS_OK) return rc;
+    }
+    return LS_OK;
+}
+
+// T = S^{-1/2} by the series I - Delta/2 + 3/8 Delta^2 - 5/16 Delta^3, Delta = S - I
+// (S close to I): Delta formed in place of D2's partner, the two powers on the tensor
+// cores, then the combination.
+__global__ void k_minus_identity(const double* __restrict__ S, int k, double* __restrict__ D) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)k * k) return;
+    D[e] = S[e] - ((e / k) == (e % k) ? 1.0 : 0.0);
+}
+__global__ void k_lowdin_combine(const double* __restrict__ Dl, const double* __restrict__ D2,
+                                 const double* __restrict__ D3, int k, double* __restrict__ T) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)k * k) return;
+    const double id = (e / k) == (e % k) ? 1.0 : 0.0;
+    T[e] = id - 0.5 * Dl[e] + 0.375 * D2[e] - 0.3125 * D3[e];
+}
+
+int x64_lowdin(int n, const double* const S[], const int k[], double* const D2[], double* const T[], int* flag,
+               cudaStream_t st, std::string* err) {
+    Arena ar(st);
+    std::vector<double*> Dl(n), D3(n);
+    std::vector<const double*> Dlc(n), D2c(n);
+    std::vector<int> zero(n, 0), one(n, 1);
+    for (int l = 0; l < n; ++l) {
+        const int64_t kk = (int64_t)k[l] * k[l];
+        Dl[l] = ar.get<double>(kk);
+        D3[l] = ar.get<double>(kk);
+        if (!Dl[l] || !D3[l]) return tc_err(err, "x64_lowdin: out of memory", LS_ERR_OOM);
+        k_minus_identity<<<(unsigned)((kk + 255) / 256), 256, 0, st>>>(S[l], k[l], Dl[l]);
+        count_kernels(1);
+        Dlc[l] = Dl[l];
+        D2c[l] = D2[l];
+    }
+    // Delta is symmetric: Delta^2 = Delta Delta^T and Delta^3 = Delta^2 Delta^T need no transposes
+    int rc = x64_small(n, Dlc.data(), zero.data(), Dlc.data(), one.data(), k, D2, nullptr, flag, st, err);
+    if (rc == LS_OK) rc = x64_small(n, D2c.data(), zero.data(), Dlc.data(), one.data(), k, D3.data(), nullptr, flag, st, err);
+    if (rc != LS_OK) return rc;
+    for (int l = 0; l < n; ++l) {
+        const int64_t kk = (int64_t)k[l] * k[l];
+        k_lowdin_combine<<<(unsigned)((kk + 255) / 256), 256, 0, st>>>(Dl[l], D2[l], D3[l], k[l], T[l]);
+        count_kernels(1);
+    }
+    return cudaGetLastError() == cudaSuccess ? LS_OK : tc_err(err, "x64_lowdin: launch failed");
+}
+
 // D = A B^T (A: M x K, B: N x K, D: M x N, row-major), then a synchronised status check
 int x64_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* D, cudaStream_t st,
                 std::string* err) {

@@ -34,6 +34,15 @@ int x64_basis(int n, const double* const V[], const int64_t ldv[], const int32_t
 int x64_pchol_vectors(int n, const double* const L[], const int64_t kmax[], const int k[], const int64_t C[],
                       const double* const U[], const double* const H[], double* const Vg[], int* flag,
                       cudaStream_t st, std::string* err);
+// out_l = op(A_l) op(B_l) (+ add_l) for k_l x k_l row-major matrices (ta/tb: 1 = transpose;
+// add may be null).
+int x64_small(int n, const double* const A[], const int ta[], const double* const B[], const int tb[],
+              const int k[], double* const out[], const double* const add[], int* flag, cudaStream_t st,
+              std::string* err);
+// T_l = S_l^{-1/2} by the series I - Delta/2 + 3/8 Delta^2 - 5/16 Delta^3 (Delta = S_l - I);
+// D2_l receives Delta^2 (scratch of the caller).
+int x64_lowdin(int n, const double* const S[], const int k[], double* const D2[], double* const T[], int* flag,
+               cudaStream_t st, std::string* err);
 // D = A B^T (row-major, device memory), synchronised, with the status checked.
 int x64_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* D, cudaStream_t st,
                 std::string* err);
