@@ -1112,6 +1112,33 @@ int lattice_sum_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, 
     return LS_OK;
 }
 
+int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, int32_t form, double* D, double* V,
+                           int32_t* sweeps, void* stream) {
+    if (!H || !D || !V || k < 1 || !(tol > 0.0) || (form != 1 && form != 2))
+        return fail(nullptr, LS_ERR_ARG, "jacobi_eig: bad arguments");
+    if (form == 1 && k > jacobi_blk_max_k())
+        return fail(nullptr, LS_ERR_ARG, "jacobi_eig: k = %d exceeds the cluster form (%d)", k, jacobi_blk_max_k());
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevStatus* ds = nullptr;
+    cudaError_t e = cudaMallocAsync(&ds, sizeof(DevStatus), st);
+    if (e != cudaSuccess) return fail(nullptr, LS_ERR_OOM, "jacobi_eig: %s", cudaGetErrorString(e));
+    DevStatus h{};
+    e = cudaMemsetAsync(ds, 0, sizeof(DevStatus), st);
+    const DfJob J{H, k, D, 1, V, 1, ds, 0.0, 0.0, tol};
+    int dev = 0, nsm = 1;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = form == 1 ? launch_jacobi_blk(&J, 1, 60, st) : launch_jacobi_gblk(&J, 1, 60, nsm, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ds, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(ds, st);
+    if (e != cudaSuccess) return fail(nullptr, LS_ERR_CUDA, "jacobi_eig: %s", cudaGetErrorString(e));
+    if (sweeps) *sweeps = h.sweeps;
+    if (h.flag == FLAG_TIMEOUT) return fail(nullptr, LS_ERR_TIMEOUT, "jacobi_eig: a bounded wait timed out");
+    if (h.flag == FLAG_NOCONVERGE) return fail(nullptr, LS_ERR_NOCONVERGE, "jacobi_eig: no convergence in 60 sweeps");
+    return LS_OK;
+}
+
 int lattice_sum_gemm_nt_mixed(const double* A, const double* B, int64_t M, int64_t N, int64_t K, void* D,
                               int32_t out_dtype, int32_t tile_n, void* stream) {
     if (!A || !B || !D || M < 0 || N < 0 || K < 1 || M > INT32_MAX || N > INT32_MAX ||

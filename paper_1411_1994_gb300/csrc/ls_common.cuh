@@ -83,23 +83,9 @@ struct GemmWs {
 inline int64_t gemm_ws_doubles(int num_sms) { return 2 * (int64_t)num_sms * 64 * 64; }
 inline int64_t gemm_ws_counters(int num_sms) { return 2 * (int64_t)num_sms; }
 
-// The FP64 products of the reduction, each for n <= 3 modes in one launch
-// (arrays of length n, one entry per mode):
-// G[c][c'] = w[c] w[c'] <a_c, a_c'>  (a: C rows of length N).
-cudaError_t launch_gram_weighted_n(int n, const double* const a[], const int64_t C[], int64_t N,
-                                   const double* const w[], double* const G[], const GemmWs& W, cudaStream_t st);
 // H = L^T L (k x k) from the first k columns of L (C x kmax, row-major).
 cudaError_t launch_pchol_gram_n(int n, const double* const L[], const int64_t kmax[], const int k[],
                                 const int64_t C[], double* const H[], const GemmWs& W, cudaStream_t st);
-// G = Y Y^T (r x r; Y: r rows of length N).
-cudaError_t launch_syrk_rows_n(int n, const double* const Y[], const int r[], int64_t N, double* const G[],
-                               const GemmWs& W, cudaStream_t st);
-// dst = Li src (Li: r x r, src and dst: r x N).
-cudaError_t launch_lower_apply_n(int n, const double* const Li[], const int r[], const double* const src[],
-                                 double* const dst[], int64_t N, const GemmWs& W, cudaStream_t st);
-// P[k][c] = sum_i Z[k][i] a[c][i]   (r x C).
-cudaError_t launch_project_n(int n, const double* const Z[], const int r[], const double* const a[],
-                             const int64_t C[], int64_t N, double* const P[], const GemmWs& W, cudaStream_t st);
 
 // Cholesky A = L L^T in place (lower; A is r x r row-major, its upper part is
 // overwritten) and Li = L^{-1} (lower, zeros above) for several matrices in
@@ -110,26 +96,6 @@ struct CholJob {
 };
 cudaError_t launch_chol_inv_multi(const CholJob* jobs, int njobs, int num_sms, cudaStream_t st);
 
-// k x k products for the eigen-solver, per mode (row-major, ld = k):
-// out = A^T B, stored as a symmetric matrix (tiles on and above the diagonal, mirrored)
-cudaError_t launch_atb_sym_n(int n, const double* const A[], const double* const B[], const int k[],
-                             double* const out[], const GemmWs& W, cudaStream_t st);
-// out = A B
-cudaError_t launch_ab_n(int n, const double* const A[], const double* const B[], const int k[], double* const out[],
-                        const GemmWs& W, cudaStream_t st);
-// out = A B^T
-cudaError_t launch_abt_n(int n, const double* const A[], const double* const B[], const int k[], double* const out[],
-                         const GemmWs& W, cudaStream_t st);
-// out = A B + Cadd
-cudaError_t launch_ab_plus_n(int n, const double* const A[], const double* const B[], const double* const Cadd[],
-                             const int k[], double* const out[], const GemmWs& W, cudaStream_t st);
-
-// T = (I + Delta)^{-1/2} to third order for S = I + Delta (k x k symmetric,
-// ||Delta|| small): T = I - Delta/2 + 3/8 Delta^2 - 5/16 Delta^3, whose error
-// is 35/128 Delta^4 + ...; D2 receives Delta^2 (scratch).
-cudaError_t launch_lowdin_n(int n, const double* const S[], const int k[], double* const D2[], double* const T[],
-                            const GemmWs& W, cudaStream_t st);
-
 // Cholesky A = L L^T and Li = L^{-1} in FP32 arithmetic, one CTA per matrix
 // with the matrix in shared memory (r <= chol32_max_r()): A is read (lower
 // part, FP64) and left unchanged, Li (r x r FP64, zeros above) is written.
@@ -137,26 +103,22 @@ cudaError_t launch_lowdin_n(int n, const double* const S[], const int k[], doubl
 cudaError_t launch_chol32_multi(const CholJob* jobs, int njobs, cudaStream_t st);
 int chol32_max_r();
 
-// Cyclic Jacobi of symmetric k x k matrices in shared memory, one thread-block
-// cluster per matrix (ls_eig.cu): diagonal in FP64, off-diagonal part and the
-// accumulated rotation I + F in FP32. Reads H (row-major, upper triangle),
+// Block Jacobi of symmetric k x k matrices (ls_eig.cu): diagonal as an FP32
+// hi/lo pair, off-diagonal part and the accumulated rotation I + F in FP32.
+// Reads H (row-major, upper triangle),
 // writes the diagonal after convergence to outD[a * ldd] and I + F
 // (add_identity) or F to outF (k x k, row-major, eigenvectors in columns).
 // st->sweeps (on entry: sweeps already recorded, 0 for a fresh status) is
 // advanced by the sweeps taken, sweep_active[] records the rotations of
 // each sweep; FLAG_NOCONVERGE after max_sweeps. A pair rotates when
 // |e_pq| > abs_floor, max(d_p, d_q) >= tau and e_pq^2 > tol^2 |d_p d_q|.
-// k must not exceed jacobi_df_max_k().
 struct DfJob {
     const double* H; int k; double* outD; int64_t ldd; double* outF; int add_identity; DevStatus* st;
     double abs_floor; double tau; double tol;
 };
-int jacobi_df_max_k();
-cudaError_t launch_jacobi_df(const DfJob* jobs, int njobs, int max_sweeps, cudaStream_t st);
-// The same iteration in block form (pairs of 8-index blocks per round, one inner
-// sweep per 16 x 16 subproblem, dense tile rotations; same inputs, outputs and
-// criteria) for k <= jacobi_blk_max_k(): m - 1 synchronisations a sweep for m
-// blocks instead of k - 1.
+// Pairs of 8-index blocks per round, one inner sweep per 16 x 16 subproblem,
+// dense tile rotations: m - 1 synchronisations a sweep for m blocks. One
+// thread-block cluster per matrix, in shared memory, for k <= jacobi_blk_max_k():
 int jacobi_blk_max_k();
 cudaError_t launch_jacobi_blk(const DfJob* jobs, int njobs, int max_sweeps, cudaStream_t st);
 // The block form in one cooperative grid with the matrices in global memory

@@ -1,26 +1,24 @@
 // Symmetric eigen-solver of the truncation step (Thm 2.1 / Algorithm 1 take
 // the SVD of each side matrix; here the eigen-decomposition of its k x k
-// Gram matrix H = L^T L after the pivoted Cholesky compression):
-// cyclic two-sided Jacobi held in shared memory by one thread-block cluster
-// per matrix.
+// Gram matrix H = L^T L after the pivoted Cholesky compression): cyclic
+// two-sided block Jacobi.
 //
-// Representation: the diagonal D of the rotated matrix in FP64, its strict
-// upper triangle E in FP32 (packed), and the accumulated rotation as I + F
-// with F in FP32. Every stored entry carries its own relative rounding, so
-// the iteration keeps the relative accuracy that Jacobi has on graded
-// positive definite matrices; run a second time on the nearly diagonal
-// U^T H U (U from the first run, orthonormalised and re-projected in FP64),
-// the angles are small, E and F are small, and the FP32 rounding of E and F
-// is small in absolute terms: the second run reaches off-diagonal ratios of
-// 1e-10 without any FP64 sweep.
+// Representation: the diagonal D of the rotated matrix as an unevaluated
+// hi + lo FP32 pair, the off-diagonal part E in FP32 (full symmetric
+// storage), and the accumulated rotation as I + F with F in FP32. Every
+// stored entry carries its own relative rounding, so the iteration keeps the
+// relative accuracy that Jacobi has on graded positive definite matrices.
+// Run a second time on the nearly diagonal U^T H U (U from the first run,
+// orthonormalised and re-projected in FP64-grade arithmetic), the angles are
+// small, E and F are small, and the FP32 rounding of E and F is small in
+// absolute terms: the second run reaches off-diagonal ratios of 1e-10 without
+// any FP64 sweep.
 //
-// Cluster layout: CTA 0 holds D and E, computes the angles of each round,
-// updates D and E, and writes the angles into the shared memory of CTAs
-// 1..nF, which hold contiguous row blocks of F and update them. One cluster
-// barrier per round (angles double-buffered by round parity). A round-robin
-// ordering pairs all indices once per sweep. Before each sweep CTA 0 scans
-// every pair; the iteration stops when no pair qualifies for a rotation, or
-// raises FLAG_NOCONVERGE after max_sweeps.
+// Two forms of the same rounds: one thread-block cluster per matrix with the
+// matrix in shared memory (k_jacobi_blk), and one cooperative grid for
+// every matrix of a launch with the matrices in global memory (k_jacobi_gblk,
+// any k). The file also holds the FP32 Cholesky + inverse of CholeskyQR's
+// first pass (k_chol32_multi).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -39,9 +37,6 @@ constexpr int kEigThreads = 1024;
 struct DfMode {
     const double* H; double* outD; double* outF; DevStatus* st;
     int64_t ldd; int k; int add_identity; double abs_floor; double tau; double tol;
-};
-struct DfArgs {
-    const DfMode* m; int max_sweeps; int cs; int rows_per;
 };
 
 __device__ __forceinline__ void rr_pair_e(int t, int i, int Cp, int& p, int& q) {
@@ -118,189 +113,6 @@ struct Crit {
         return fabsf(apq) > floor && fmaxf(a, b) >= tau && apq * apq > tol2 * fabsf(a * b);
     }
 };
-
-// one rotation of a round: J = [[c, s], [-s, c]] on (p, q), c - 1 kept apart,
-// with the packed-row offsets of p and q (CTA 0's E)
-struct __align__(16) Rot {
-    float cm1, s;
-    int p, q;
-    float c;
-    int rbp, rbq, pad;
-};
-
-// shared memory: Rot[2][P] and two control words, then the CTA's own part
-__host__ __device__ __forceinline__ size_t df_common(int k) {
-    const int P = (k + (k & 1)) / 2;
-    return ((size_t)2 * P * sizeof(Rot) + 4 * sizeof(int) + 15) & ~(size_t)15;
-}
-// CTA 0: D (k doubles), row offsets (k ints, padded to even), E (k(k-1)/2 floats)
-__host__ __device__ __forceinline__ size_t df_e_bytes(int k) {
-    return df_common(k) + 8 * (size_t)k + 4 * (size_t)(k + (k & 1)) + 4 * (size_t)k * (k - 1) / 2;
-}
-
-__global__ void __launch_bounds__(kEigThreads) k_jacobi_df(DfArgs A) {
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    const int job = blockIdx.x / A.cs;
-    const DfMode J = A.m[job];
-    const int k = J.k, Cp = k + (k & 1), P = Cp / 2, n1 = Cp - 1;
-    extern __shared__ __align__(16) unsigned char smem[];
-    Rot* rot = reinterpret_cast<Rot*>(smem);                      // [2][P]
-    int* ctl = reinterpret_cast<int*>(rot + 2 * P);               // [2]: 1 = stop
-    unsigned char* rest = smem + df_common(k);
-    __shared__ unsigned int s_active;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
-    const Crit qualifies{(float)J.abs_floor, (float)J.tau, (float)(J.tol * J.tol)};
-
-    // CTA 0: D (FP64), row offsets of the packed strict upper triangle, E
-    DF* D = reinterpret_cast<DF*>(rest);
-    int* rb = reinterpret_cast<int*>(D + k);                      // E(a, b) = E[rb[a] + b], a < b
-    float* E = reinterpret_cast<float*>(rb + k + (k & 1));
-    // CTAs >= 1: rows [j0, j1) of F
-    float* F = reinterpret_cast<float*>(rest);
-    const int j0 = rank >= 1 ? min(k, (rank - 1) * A.rows_per) : 0;
-    const int j1 = rank >= 1 ? min(k, j0 + A.rows_per) : 0;
-
-    int base = 0;
-    if (rank == 0) {
-        for (int a = tid; a < k; a += nthr) {
-            D[a] = df_from(J.H[(int64_t)a * k + a]);
-            rb[a] = a * (2 * k - a - 1) / 2 - a - 1;
-        }
-        __syncthreads();
-        for (int a = warp; a < k; a += nw)
-            for (int b = a + 1 + lane; b < k; b += 32) E[rb[a] + b] = (float)J.H[(int64_t)a * k + b];
-        if (tid == 0) s_active = 0;
-        base = J.st->sweeps;   // a second run continues the sweep record of the first
-    } else {
-        for (int e = tid; e < (j1 - j0) * k; e += nthr) F[e] = 0.f;
-    }
-    cl.sync();
-
-    int sweep = 0;
-    bool done = false;
-    int gr = 0;   // rounds so far, over all sweeps: the parity of the rotation buffers
-    for (; sweep <= A.max_sweeps && !done; ++sweep) {
-        for (int t = 0; t < n1; ++t, ++gr) {
-            const int par = gr & 1;
-            Rot* R = rot + par * P;
-            if (rank == 0) {
-                int stop = 0;
-                if (t == 0) {
-                    // does any pair still qualify?
-                    int need = 0;
-                    for (int a = warp; a < k && !need; a += nw)
-                        for (int b = a + 1 + lane; b < k; b += 32)
-                            if (qualifies(D[a], D[b], E[rb[a] + b])) { need = 1; break; }
-                    need = __syncthreads_or(need);
-                    if (tid == 0) {
-                        if (sweep > 0) J.st->sweep_active[(base + sweep - 1) & 63] = s_active;
-                        s_active = 0;
-                    }
-                    if (!need) stop = 1;
-                    else if (sweep == A.max_sweeps) {
-                        stop = 1;
-                        if (tid == 0) atomicCAS(&J.st->flag, FLAG_OK, FLAG_NOCONVERGE);
-                    }
-                    __syncthreads();
-                }
-                if (!stop) {
-                    for (int i = tid; i < P; i += nthr) {
-                        Rot r{0.f, 0.f, 0, 0, 1.f, 0, 0, 0};
-                        rr_pair_e(t, i, Cp, r.p, r.q);
-                        r.rbp = rb[r.p];
-                        r.rbq = r.q < k ? rb[r.q] : 0;
-                        if (r.q < k) {
-                            const int ix = rb[r.p] + r.q;
-                            const float epq = E[ix];
-                            if (qualifies(D[r.p], D[r.q], epq)) {
-                                const RotCS g = jacobi_rot(df_diff(D[r.q], D[r.p]), epq);
-                                r.cm1 = g.cm1;
-                                r.s = g.s;
-                                r.c = g.c;
-                                const float te = g.t * epq;
-                                D[r.p] = df_add(D[r.p], -te);
-                                D[r.q] = df_add(D[r.q], te);
-                                E[ix] = 0.f;
-                                atomicAdd(&s_active, 1u);
-                            }
-                        }
-                        R[i] = r;
-                        for (int c = 1; c < A.cs; ++c) cl.map_shared_rank(R, c)[i] = r;
-                    }
-                }
-                if (tid == 0)
-                    for (int c = 0; c < A.cs; ++c) cl.map_shared_rank(ctl, c)[par] = stop;
-            }
-            cl.sync();
-            if (ctl[par]) { done = true; break; }
-            if (rank == 0) {
-                // E <- J^T E J on every block of two pairs (i < i2). Row c of the block triangle
-                // (P - 1 - c blocks) is folded with row P - 2 - c (c + 1 blocks) into P blocks, so
-                // the P(P-1)/2 blocks are dealt out evenly by a linear index.
-                const int nbl = (P / 2) * P;
-                const float invP = 1.f / (float)P;
-                for (int bl = tid; bl < nbl; bl += nthr) {
-                    int c = (int)((float)bl * invP);
-                    int off = bl - c * P;
-                    if (off >= P) { ++c; off -= P; }
-                    else if (off < 0) { --c; off += P; }
-                    int i, i2;
-                    if (off < P - 1 - c) { i = c; i2 = c + 1 + off; }
-                    else { i = P - 2 - c; i2 = off; if (i <= c) continue; }
-                    const Rot a = R[i], b = R[i2];
-                    if (a.s == 0.f && b.s == 0.f) continue;
-                    const bool vq = a.q < k, vq2 = b.q < k;
-                    // packed position of the symmetric entry (x, y): row offset of the smaller index
-                    const int i0 = a.p < b.p ? a.rbp + b.p : b.rbp + a.p;
-                    const int i1 = vq2 ? (a.p < b.q ? a.rbp + b.q : b.rbq + a.p) : 0;
-                    const int ia = vq ? (a.q < b.p ? a.rbq + b.p : b.rbp + a.q) : 0;
-                    const int ib = (vq && vq2) ? (a.q < b.q ? a.rbq + b.q : b.rbq + a.q) : 0;
-                    const float x0 = E[i0], x1 = vq2 ? E[i1] : 0.f, x2 = vq ? E[ia] : 0.f,
-                                x3 = (vq && vq2) ? E[ib] : 0.f;
-                    const float ypp = a.c * x0 - a.s * x2, ypq = a.c * x1 - a.s * x3;
-                    const float yqp = a.s * x0 + a.c * x2, yqq = a.s * x1 + a.c * x3;
-                    E[i0] = b.c * ypp - b.s * ypq;
-                    if (vq2) E[i1] = b.s * ypp + b.c * ypq;
-                    if (vq) E[ia] = b.c * yqp - b.s * yqq;
-                    if (vq && vq2) E[ib] = b.s * yqp + b.c * yqq;
-                }
-                __syncthreads();
-            } else {
-                // (I + F) <- (I + F) J on this CTA's rows: a warp per row, lanes over the pairs
-                const int nr = j1 - j0;
-                for (int jl = warp; jl < nr; jl += nw) {
-                    const int j = j0 + jl;
-                    float* row = F + (int64_t)jl * k;
-                    for (int i = lane; i < P; i += 32) {
-                        const Rot a = R[i];
-                        if (a.s == 0.f || a.q >= k) continue;
-                        const float fp = row[a.p], fq = row[a.q];
-                        float np = fp + (fp * a.cm1 - fq * a.s);
-                        float nq = fq + (fp * a.s + fq * a.cm1);
-                        if (j == a.p) { np += a.cm1; nq += a.s; }
-                        if (j == a.q) { np -= a.s; nq += a.cm1; }
-                        row[a.p] = np;
-                        row[a.q] = nq;
-                    }
-                }
-            }
-        }
-    }
-    // outputs
-    if (rank == 0) {
-        for (int a = tid; a < k; a += nthr) J.outD[(int64_t)a * J.ldd] = df_to(D[a]);
-        if (tid == 0) J.st->sweeps = base + sweep - 1;
-    } else {
-        for (int e = tid; e < (j1 - j0) * k; e += nthr) {
-            const int jl = e / k, n = e - jl * k;
-            const int j = j0 + jl;
-            J.outF[(int64_t)j * k + n] = (double)F[e] + ((J.add_identity && j == n) ? 1.0 : 0.0);
-        }
-    }
-    cl.sync();
-}
 
 // dynamic shared memory available to the kernel (its static variables take a few bytes)
 int smem_optin() {
@@ -1087,61 +899,6 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
 }
 
 }  // namespace
-
-int jacobi_df_max_k() {
-    const int cap = smem_optin();
-    int k = 2;
-    while (k < 4096 && df_e_bytes(k + 1) <= (size_t)cap) ++k;
-    return k;
-}
-
-cudaError_t launch_jacobi_df(const DfJob* jobs, int njobs, int max_sweeps, cudaStream_t st) {
-    if (njobs < 1) return cudaSuccess;
-    const int cap = smem_optin();
-    int kmax = 1;
-    for (int m = 0; m < njobs; ++m) kmax = std::max(kmax, jobs[m].k);
-    const size_t common = df_common(kmax);
-    const size_t e_bytes = df_e_bytes(kmax);
-    if (e_bytes > (size_t)cap) return cudaErrorInvalidValue;
-    // F rows: at least two CTAs (F carries twice the work of E per round), as many as fit
-    const int64_t rows_fit = std::max<int64_t>(1, ((int64_t)cap - (int64_t)common) / (4 * (int64_t)kmax));
-    int nF = std::max<int>(2, (int)((kmax + rows_fit - 1) / rows_fit));
-    if (nF > 7) return cudaErrorInvalidValue;
-    const int rows_per = (kmax + nF - 1) / nF;
-    const size_t f_bytes = common + 4 * (size_t)rows_per * kmax;
-    const size_t smem = std::max(e_bytes, f_bytes);
-    cudaError_t e = cudaFuncSetAttribute(k_jacobi_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    std::vector<DfMode> hm(njobs);
-    for (int m = 0; m < njobs; ++m) {
-        const DfJob& J = jobs[m];
-        hm[m] = DfMode{J.H, J.outD, J.outF, J.st, J.ldd, J.k, J.add_identity, J.abs_floor, J.tau, J.tol};
-    }
-    DfMode* dm = nullptr;
-    e = cudaMallocAsync(&dm, sizeof(DfMode) * njobs, st);
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(dm, hm.data(), sizeof(DfMode) * njobs, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) {
-        const int cs = 1 + nF;
-        DfArgs a{dm, max_sweeps > 63 ? 63 : max_sweeps, cs, rows_per};
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(njobs * cs));
-        cfg.blockDim = dim3(kEigThreads);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = (unsigned)cs;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        count_kernels(1);
-        e = cudaLaunchKernelEx(&cfg, k_jacobi_df, a);
-    }
-    cudaFreeAsync(dm, st);
-    return e;
-}
 
 int chol32_max_r() {
     const int cap = smem_optin();

@@ -322,11 +322,6 @@ struct KRowN {           // X(k, n) = p[k * ld + n]        (n contiguous)
     const double* p; int64_t ld;
     __device__ double operator()(int, int k, int n) const { return p[k * ld + n]; }
 };
-struct NRowK {           // X(k, n) = p[n * ld + k]        (k contiguous)
-    static constexpr bool kfast = true;
-    const double* p; int64_t ld;
-    __device__ double operator()(int, int k, int n) const { return p[n * ld + k]; }
-};
 struct NRowKScaled {     // X(k, n) = s[n] * p[n * ld + k]
     static constexpr bool kfast = true;
     const double* p; int64_t ld; const double* s;
@@ -341,13 +336,6 @@ struct StoreRowW {       // C[m*ld + n] = w[m] w[n] v
     __device__ void operator()(int, int m, int n, double v) const { p[m * ld + n] = w[m] * w[n] * v; }
 };
 
-// basis: A(m=j, kk=c) = V[c*ldv + perm[j]] * w[c] * inv_sqrt_lam[j]
-// core: A(m=i, k=t) = P0[i*C0 + c0(t)] * xin[t]
-struct CoreA {
-    static constexpr bool kfast = true;
-    const double* P0; int64_t C0; const int32_t* tcol; const double* xin;
-    __device__ double operator()(int, int m, int k) const { return P0[m * C0 + tcol[3 * k]] * xin[k]; }
-};
 // core: B(k=t, n=j*r2+l) = P1[j*C1 + c1(t)] * P2[l*C2 + c2(t)]
 struct CoreB {
     static constexpr bool kfast = true;
@@ -1192,15 +1180,6 @@ cudaError_t launch_chol_inv_multi(const CholJob* jobs, int njobs, int num_sms, c
 }
 
 // grouped products of the reduction (one launch for up to three modes) ------
-cudaError_t launch_gram_weighted_n(int n, const double* const a[], const int64_t C[], int64_t N,
-                                   const double* const w[], double* const G[], const GemmWs& W, cudaStream_t st) {
-    GGroup<RowK, NRowK, StoreRowW> g{};
-    g.n = n;
-    for (int i = 0; i < n; ++i)
-        g.j[i] = {RowK{a[i], N}, NRowK{a[i], N}, StoreRowW{G[i], C[i], w[i]}, (int)C[i], (int)C[i], (int)N, 1};
-    return gemm_group(g, W, st);
-}
-
 cudaError_t launch_pchol_gram_n(int n, const double* const L[], const int64_t kmax[], const int k[],
                                 const int64_t C[], double* const H[], const GemmWs& W, cudaStream_t st) {
     GGroup<ColK, KRowN, StoreRow> g{};
@@ -1210,110 +1189,7 @@ cudaError_t launch_pchol_gram_n(int n, const double* const L[], const int64_t km
     return gemm_group(g, W, st);
 }
 
-cudaError_t launch_syrk_rows_n(int n, const double* const Y[], const int r[], int64_t N, double* const G[],
-                               const GemmWs& W, cudaStream_t st) {
-    GGroup<RowK, NRowK, StoreRow> g{};
-    g.n = n;
-    for (int i = 0; i < n; ++i)
-        g.j[i] = {RowK{Y[i], N}, NRowK{Y[i], N}, StoreRow{G[i], r[i], 0}, r[i], r[i], (int)N, 1};
-    return gemm_group(g, W, st);
-}
 
-cudaError_t launch_lower_apply_n(int n, const double* const Li[], const int r[], const double* const src[],
-                                 double* const dst[], int64_t N, const GemmWs& W, cudaStream_t st) {
-    GGroup<RowK, KRowN, StoreRow> g{};
-    g.n = n;
-    for (int i = 0; i < n; ++i)
-        g.j[i] = {RowK{Li[i], r[i]}, KRowN{src[i], N}, StoreRow{dst[i], N, 0}, r[i], (int)N, r[i], 0};
-    return gemm_group(g, W, st);
-}
-
-struct StoreRowPlus {   // C[m*ld + n] = v + X[m*ld + n]
-    double* p; int64_t ld; const double* x;
-    __device__ void operator()(int, int m, int n, double v) const { p[m * ld + n] = v + x[m * ld + n]; }
-};
-
-// Delta = S - I as an operand
-struct RowKmI {          // X(m, k) = p[m * ld + k] - [m == k]
-    static constexpr bool kfast = true;
-    const double* p; int64_t ld;
-    __device__ double operator()(int, int m, int k) const { return p[m * ld + k] - (m == k ? 1.0 : 0.0); }
-};
-struct KRowNmI {         // X(k, n) = p[k * ld + n] - [k == n]
-    static constexpr bool kfast = false;
-    const double* p; int64_t ld;
-    __device__ double operator()(int, int k, int n) const { return p[k * ld + n] - (k == n ? 1.0 : 0.0); }
-};
-// T = I - Delta/2 + 3/8 Delta^2 - 5/16 Delta^3, given v = (Delta Delta^2)(m, n)
-struct StoreLowdin {
-    double* T; const double* S; const double* D2; int64_t ld;
-    __device__ void operator()(int, int m, int n, double v) const {
-        const int64_t o = m * ld + n;
-        const double id = (m == n) ? 1.0 : 0.0;
-        T[o] = id - 0.5 * (S[o] - id) + 0.375 * D2[o] - 0.3125 * v;
-    }
-};
-
-cudaError_t launch_lowdin_n(int n, const double* const S[], const int k[], double* const D2[], double* const T[],
-                            const GemmWs& W, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    GGroup<RowKmI, KRowNmI, StoreRow> g{};
-    g.n = n;
-    for (int i = 0; i < n; ++i)
-        g.j[i] = {RowKmI{S[i], k[i]}, KRowNmI{S[i], k[i]}, StoreRow{D2[i], k[i], 0}, k[i], k[i], k[i], 1};
-    cudaError_t e = gemm_group(g, W, st);
-    if (e != cudaSuccess) return e;
-    GGroup<RowKmI, KRowN, StoreLowdin> h{};
-    h.n = n;
-    for (int i = 0; i < n; ++i)
-        h.j[i] = {RowKmI{S[i], k[i]}, KRowN{D2[i], k[i]}, StoreLowdin{T[i], S[i], D2[i], k[i]}, k[i], k[i], k[i], 0};
-    return gemm_group(h, W, st);
-}
-
-cudaError_t launch_atb_sym_n(int n, const double* const A[], const double* const B[], const int k[],
-                             double* const out[], const GemmWs& W, cudaStream_t st) {
-    GGroup<ColK, KRowN, StoreRow> g{};
-    g.n = n;
-    for (int i = 0; i < n; ++i)
-        g.j[i] = {ColK{A[i], k[i]}, KRowN{B[i], k[i]}, StoreRow{out[i], k[i], 0}, k[i], k[i], k[i], 1};
-    return n > 0 ? gemm_group(g, W, st) : cudaSuccess;
-}
-
-cudaError_t launch_ab_n(int n, const double* const A[], const double* const B[], const int k[], double* const out[],
-                        const GemmWs& W, cudaStream_t st) {
-    GGroup<RowK, KRowN, StoreRow> g{};
-    g.n = n;
-    for (int i = 0; i < n; ++i)
-        g.j[i] = {RowK{A[i], k[i]}, KRowN{B[i], k[i]}, StoreRow{out[i], k[i], 0}, k[i], k[i], k[i], 0};
-    return n > 0 ? gemm_group(g, W, st) : cudaSuccess;
-}
-
-cudaError_t launch_abt_n(int n, const double* const A[], const double* const B[], const int k[], double* const out[],
-                         const GemmWs& W, cudaStream_t st) {
-    GGroup<RowK, NRowK, StoreRow> g{};
-    g.n = n;
-    for (int i = 0; i < n; ++i)
-        g.j[i] = {RowK{A[i], k[i]}, NRowK{B[i], k[i]}, StoreRow{out[i], k[i], 0}, k[i], k[i], k[i], 0};
-    return n > 0 ? gemm_group(g, W, st) : cudaSuccess;
-}
-
-cudaError_t launch_ab_plus_n(int n, const double* const A[], const double* const B[], const double* const Cadd[],
-                             const int k[], double* const out[], const GemmWs& W, cudaStream_t st) {
-    GGroup<RowK, KRowN, StoreRowPlus> g{};
-    g.n = n;
-    for (int i = 0; i < n; ++i)
-        g.j[i] = {RowK{A[i], k[i]}, KRowN{B[i], k[i]}, StoreRowPlus{out[i], k[i], Cadd[i]}, k[i], k[i], k[i], 0};
-    return n > 0 ? gemm_group(g, W, st) : cudaSuccess;
-}
-
-cudaError_t launch_project_n(int n, const double* const Z[], const int r[], const double* const a[],
-                             const int64_t C[], int64_t N, double* const P[], const GemmWs& W, cudaStream_t st) {
-    GGroup<RowK, NRowK, StoreRow> g{};
-    g.n = n;
-    for (int i = 0; i < n; ++i)
-        g.j[i] = {RowK{Z[i], N}, NRowK{a[i], N}, StoreRow{P[i], C[i], 0}, r[i], (int)C[i], (int)N, 0};
-    return gemm_group(g, W, st);
-}
 
 cudaError_t launch_fold_norms(const double* xi, const int32_t* tcol, int64_t T, const double* n0,
                               const double* n1, const double* n2, double* xin, cudaStream_t st) {

@@ -27,7 +27,7 @@ EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_create", "lattice_sum_add_de
             "lattice_sum_rhosvd_reduce", "lattice_sum_eval_slab", "lattice_sum_get_factors",
             "lattice_sum_read", "lattice_sum_profile", "lattice_sum_profile_report",
             "lattice_sum_eval_slab_noalloc", "lattice_sum_batch_reduce", "lattice_sum_gemm_nt",
-            "lattice_sum_gemm_nt_mixed", "lattice_sum_destroy", "lattice_sum_last_error")
+            "lattice_sum_gemm_nt_mixed", "lattice_sum_jacobi_eig", "lattice_sum_destroy", "lattice_sum_last_error")
 
 
 class ls_params(C.Structure):
@@ -88,6 +88,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                         C.c_void_p]
     lib.lattice_sum_gemm_nt_mixed.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
                                               C.c_int32, C.c_int32, C.c_void_p]
+    lib.lattice_sum_jacobi_eig.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p]
     lib.lattice_sum_destroy.argtypes = [C.c_void_p]
     lib.lattice_sum_destroy.restype = None
     lib.lattice_sum_last_error.argtypes = [C.c_void_p]
@@ -192,6 +194,20 @@ def gemm_nt_mixed(A, B, dtype=None, tile_n: int = 0):
                                            C.c_int32(LS_OUT_F32 if dtype == torch.float32 else LS_OUT_F64),
                                            C.c_int32(tile_n), None))
     return D
+
+
+def jacobi_eig(H, tol: float = 1e-7, form: int = 2):
+    """One run of the block Jacobi (lattice_sum_jacobi_eig) on a symmetric float64 CUDA tensor:
+    returns (diagonal, V = I + F, sweeps); form 1 = cluster (shared memory), 2 = grid."""
+    import torch
+    H = H.contiguous()
+    k = H.shape[0]
+    D = torch.empty(k, dtype=torch.float64, device=H.device)
+    V = torch.empty((k, k), dtype=torch.float64, device=H.device)
+    sw = C.c_int32()
+    _check(lib().lattice_sum_jacobi_eig(C.c_void_p(H.data_ptr()), C.c_int32(k), C.c_double(tol), C.c_int32(form),
+                                        C.c_void_p(D.data_ptr()), C.c_void_p(V.data_ptr()), C.byref(sw), None))
+    return D, V, sw.value
 
 
 def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float):
