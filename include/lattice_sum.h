@@ -243,20 +243,22 @@ int lattice_sum_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, 
  * decomposition of each compressed Gram matrix).
  * - Arithmetic: the diagonal as an FP32 hi/lo pair, the off-diagonal part
  *   and the accumulated rotation in FP32. A pair rotates while
- *   e_pq^2 > tol^2 |d_p d_q|.
+ *   |e_pq| > abs_floor and e_pq^2 > tol^2 |d_p d_q|. abs_floor should be
+ *   above the FP32 noise of E (the reduction passes its resolution floor),
+ *   or pairs of tiny eigenvalues never settle.
  * - Outputs: D (device, k) receives the diagonal after convergence, V
  *   (device, k x k row-major) the accumulated rotation I + F, whose columns
  *   are the eigenvectors; *sweeps (may be NULL) the sweeps taken.
  * - form 1: one thread-block cluster with the matrix in shared memory
- *   (k up to a device-dependent limit, about 232). form 2: one cooperative
+ *   (k up to a device-dependent limit: 208 on GB300). form 2: one cooperative
  *   grid with the matrix in global memory (any k). On the same input both
  *   forms give the same D and V.
  * - Synchronises `stream` (a cudaStream_t or NULL).
  * - Errors: LS_ERR_ARG, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_NOCONVERGE (60
  *   sweeps), LS_ERR_TIMEOUT.
  */
-int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, int32_t form, double* D, double* V,
-                           int32_t* sweeps, void* stream);
+int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, double abs_floor, int32_t form, double* D,
+                           double* V, int32_t* sweeps, void* stream);
 
 /*
  * lattice_sum_gemm_nt_mixed -- D = A B^T for device FP64 matrices (A: M x K,

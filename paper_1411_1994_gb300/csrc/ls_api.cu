@@ -1112,9 +1112,9 @@ int lattice_sum_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, 
     return LS_OK;
 }
 
-int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, int32_t form, double* D, double* V,
-                           int32_t* sweeps, void* stream) {
-    if (!H || !D || !V || k < 1 || !(tol > 0.0) || (form != 1 && form != 2))
+int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, double abs_floor, int32_t form, double* D,
+                           double* V, int32_t* sweeps, void* stream) {
+    if (!H || !D || !V || k < 1 || !(tol > 0.0) || !(abs_floor >= 0.0) || (form != 1 && form != 2))
         return fail(nullptr, LS_ERR_ARG, "jacobi_eig: bad arguments");
     if (form == 1 && k > jacobi_blk_max_k())
         return fail(nullptr, LS_ERR_ARG, "jacobi_eig: k = %d exceeds the cluster form (%d)", k, jacobi_blk_max_k());
@@ -1124,7 +1124,7 @@ int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, int32_t form,
     if (e != cudaSuccess) return fail(nullptr, LS_ERR_OOM, "jacobi_eig: %s", cudaGetErrorString(e));
     DevStatus h{};
     e = cudaMemsetAsync(ds, 0, sizeof(DevStatus), st);
-    const DfJob J{H, k, D, 1, V, 1, ds, 0.0, 0.0, tol};
+    const DfJob J{H, k, D, 1, V, 1, ds, abs_floor, 0.0, tol};
     int dev = 0, nsm = 1;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

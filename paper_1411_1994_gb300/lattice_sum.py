@@ -88,8 +88,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                         C.c_void_p]
     lib.lattice_sum_gemm_nt_mixed.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
                                               C.c_int32, C.c_int32, C.c_void_p]
-    lib.lattice_sum_jacobi_eig.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
-                                           C.c_void_p, C.c_void_p]
+    lib.lattice_sum_jacobi_eig.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_void_p]
     lib.lattice_sum_destroy.argtypes = [C.c_void_p]
     lib.lattice_sum_destroy.restype = None
     lib.lattice_sum_last_error.argtypes = [C.c_void_p]
@@ -196,7 +196,7 @@ def gemm_nt_mixed(A, B, dtype=None, tile_n: int = 0):
     return D
 
 
-def jacobi_eig(H, tol: float = 1e-7, form: int = 2):
+def jacobi_eig(H, tol: float = 1e-7, abs_floor: float = 0.0, form: int = 2):
     """One run of the block Jacobi (lattice_sum_jacobi_eig) on a symmetric float64 CUDA tensor:
     returns (diagonal, V = I + F, sweeps); form 1 = cluster (shared memory), 2 = grid."""
     import torch
@@ -205,7 +205,8 @@ def jacobi_eig(H, tol: float = 1e-7, form: int = 2):
     D = torch.empty(k, dtype=torch.float64, device=H.device)
     V = torch.empty((k, k), dtype=torch.float64, device=H.device)
     sw = C.c_int32()
-    _check(lib().lattice_sum_jacobi_eig(C.c_void_p(H.data_ptr()), C.c_int32(k), C.c_double(tol), C.c_int32(form),
+    _check(lib().lattice_sum_jacobi_eig(C.c_void_p(H.data_ptr()), C.c_int32(k), C.c_double(tol),
+                                        C.c_double(abs_floor), C.c_int32(form),
                                         C.c_void_p(D.data_ptr()), C.c_void_p(V.data_ptr()), C.byref(sw), None))
     return D, V, sw.value
 
