@@ -234,28 +234,46 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
     return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
-// One CTA per row i of a K-contiguous source x(i, k) = src[i*si + k], scaled by rs[i] if
-// given. E = exponent with max_k |x| in [2^(E-2), 2^(E-1)), so that x 2^-E lies in
-// (-1/2, 1/2) and its digits in [-64, 64]; zero digits past cols.
-__global__ void __launch_bounds__(128) k_split_x64(const double* __restrict__ src, int64_t rows, int64_t cols,
-                                                   int64_t si, const double* __restrict__ rs, int64_t kpad, X64Ptrs d,
-                                                   int* __restrict__ exps) {
+// Operands of one or more products, split in one launch: source j contributes rows
+// i < rows of x(i, k) = src[i*si + k*sk] (k < cols), scaled by rs[i] if given; its
+// CTAs start at cta0. One CTA per row. E = exponent with max_k |x| in
+// [2^(E-2), 2^(E-1)), so that x 2^-E lies in (-1/2, 1/2) and its digits in [-64, 64];
+// zero digits past cols. A transposed source is read with si = 1, sk = its row stride.
+struct X64Split {
+    const double* src;
+    int64_t rows, cols, si, sk;
+    const double* rs;
+    X64Ptrs d;
+    int* e;
+    int64_t kpad, cta0;
+};
+constexpr int kX64MaxSplits = 6;
+struct X64SplitGroup {
+    X64Split s[kX64MaxSplits];
+    int n;
+};
+
+__global__ void __launch_bounds__(128) k_split_x64(const __grid_constant__ X64SplitGroup G) {
     __shared__ unsigned long long s_mb[4];
-    const int64_t i = blockIdx.x;
+    int j = 0;
+    while (j + 1 < G.n && (int64_t)blockIdx.x >= G.s[j + 1].cta0) ++j;
+    const X64Split& S = G.s[j];
+    const int64_t i = blockIdx.x - S.cta0;
+    const double* x = S.src + i * S.si;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long mb = 0;
-    for (int64_t k = threadIdx.x; k < cols; k += blockDim.x) mb = max(mb, abs_bits(src[i * si + k]));
+    for (int64_t k = threadIdx.x; k < S.cols; k += blockDim.x) mb = max(mb, abs_bits(x[k * S.sk]));
     for (int o = 16; o; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
     if (lane == 0) s_mb[warp] = mb;
     __syncthreads();
     mb = max(max(s_mb[0], s_mb[1]), max(s_mb[2], s_mb[3]));
-    const double sc = rs ? fabs(rs[i]) : 1.0;
+    const double sc = S.rs ? fabs(S.rs[i]) : 1.0;
     const double mx = sc * __longlong_as_double((long long)mb);
     const int E = mx > 0.0 ? ilogb(mx) + 2 : 0;
-    if (threadIdx.x == 0) exps[i] = E;
-    const double f = (rs ? rs[i] : 1.0) * ldexp(1.0, 56 - E);
-    for (int64_t k = threadIdx.x; k < kpad; k += blockDim.x)
-        x64_digits(k < cols ? src[i * si + k] * f : 0.0, i * kpad + k, d);
+    if (threadIdx.x == 0) S.e[i] = E;
+    const double f = (S.rs ? S.rs[i] : 1.0) * ldexp(1.0, 56 - E);
+    for (int64_t k = threadIdx.x; k < S.kpad; k += blockDim.x)
+        x64_digits(k < S.cols ? x[k * S.sk] * f : 0.0, i * S.kpad + k, S.d);
 }
 
 // ---------------------------------------------------------------------------
@@ -301,14 +319,31 @@ X64Op x64_alloc(Arena& ar, int64_t rows, int64_t kpad) {
 }
 
 
-// rows of x(i, k) = src[i*si + k] times rs[i] (if given) into exact-slice form
-cudaError_t launch_split_x64(const double* src, int64_t rows, int64_t cols, int64_t si, const double* rs,
-                             const X64Op& d, cudaStream_t st) {
-    if (rows <= 0) return cudaSuccess;
-    k_split_x64<<<(unsigned)rows, 128, 0, st>>>(src, rows, cols, si, rs, d.kpad, d.d, d.e);
-    count_kernels(1);
-    return cudaGetLastError();
-}
+// Operand splits collected and launched together (flushed when full or on demand)
+struct SplitBatch {
+    cudaStream_t st;
+    X64SplitGroup g{};
+    int64_t ctas = 0;
+    cudaError_t err = cudaSuccess;
+    explicit SplitBatch(cudaStream_t s) : st(s) { g.n = 0; }
+    // rows of x(i, k) = src[i*si + k*sk] times rs[i] (if given) into d
+    void add(const double* src, int64_t rows, int64_t cols, int64_t si, int64_t sk, const double* rs, const X64Op& d) {
+        if (rows <= 0) return;
+        if (g.n == kX64MaxSplits) flush();
+        g.s[g.n++] = X64Split{src, rows, cols, si, sk, rs, d.d, d.e, d.kpad, ctas};
+        ctas += rows;
+    }
+    cudaError_t flush() {
+        if (g.n > 0 && err == cudaSuccess) {
+            k_split_x64<<<(unsigned)ctas, 128, 0, st>>>(g);
+            count_kernels(1);
+            err = cudaGetLastError();
+        }
+        g.n = 0;
+        ctas = 0;
+        return err;
+    }
+};
 
 // one product of a group: D (+)= A B^T, A: M x kpad, B: N x kpad (exact-slice form)
 struct X64Spec {
@@ -370,14 +405,15 @@ int gemm_x64(const X64Spec* sp, int n, int* flag, cudaStream_t st, std::string* 
 int x64_gram(int n, const double* const a[], const int64_t C[], int64_t N, const double* const w[], double* const G[],
              int* flag, cudaStream_t st, std::string* err) {
     Arena ar(st);
+    SplitBatch sb(st);
     std::vector<X64Op> xs(n);
     std::vector<X64Spec> sp(n);
     for (int l = 0; l < n; ++l) {
         xs[l] = x64_alloc(ar, C[l], pad64(N));
         if (!xs[l].ok()) return tc_err(err, "x64_gram: out of memory", LS_ERR_OOM);
-        if (launch_split_x64(a[l], C[l], N, N, w ? w[l] : nullptr, xs[l], st) != cudaSuccess)
-            return tc_err(err, "x64_gram: split failed");
+        sb.add(a[l], C[l], N, N, 1, w ? w[l] : nullptr, xs[l]);
     }
+    if (sb.flush() != cudaSuccess) return tc_err(err, "x64_gram: split failed");
     for (int l = 0; l < n; ++l) sp[l] = X64Spec{&xs[l], &xs[l], C[l], C[l], TcOut{G[l], C[l], 0, OUT_F64, 0}, 0};
     return gemm_x64(sp.data(), n, flag, st, err);
 }
@@ -386,6 +422,7 @@ int x64_gram(int n, const double* const a[], const int64_t C[], int64_t N, const
 int x64_project(int n, const double* const Z[], const int r[], const double* const a[], const int64_t C[], int64_t N,
                 double* const P[], int* flag, cudaStream_t st, std::string* err) {
     Arena ar(st);
+    SplitBatch sb(st);
     const int64_t kp = pad64(N);
     std::vector<X64Op> zs(n), as(n);
     std::vector<X64Spec> sp(n);
@@ -393,34 +430,33 @@ int x64_project(int n, const double* const Z[], const int r[], const double* con
         zs[l] = x64_alloc(ar, r[l], kp);
         as[l] = x64_alloc(ar, C[l], kp);
         if (!zs[l].ok() || !as[l].ok()) return tc_err(err, "x64_project: out of memory", LS_ERR_OOM);
-        if (launch_split_x64(Z[l], r[l], N, N, nullptr, zs[l], st) != cudaSuccess ||
-            launch_split_x64(a[l], C[l], N, N, nullptr, as[l], st) != cudaSuccess)
-            return tc_err(err, "x64_project: split failed");
+        sb.add(Z[l], r[l], N, N, 1, nullptr, zs[l]);
+        sb.add(a[l], C[l], N, N, 1, nullptr, as[l]);
         sp[l] = X64Spec{&zs[l], &as[l], r[l], C[l], TcOut{P[l], C[l], 0, OUT_F64, 0}, 0};
     }
+    if (sb.flush() != cudaSuccess) return tc_err(err, "x64_project: split failed");
     return gemm_x64(sp.data(), n, flag, st, err);
 }
 
 // dst_l = T_l src_l: T_l r_l x r_l, src_l and dst_l r_l x N (rows). Computed as
-// dst^T = src^T T^T (src transposed first) with a transposed store: each epilogue warp
-// writes 32 consecutive entries of a row of dst.
+// dst^T = src^T T^T (src read transposed by the split) with a transposed store: each
+// epilogue warp writes 32 consecutive entries of a row of dst.
 int x64_apply(int n, const double* const T[], const int r[], const double* const src[], int64_t N,
               double* const dst[], int* flag, cudaStream_t st, std::string* err) {
     Arena ar(st);
+    SplitBatch sb(st);
     std::vector<X64Op> ss(n), ts(n);
     std::vector<X64Spec> sp(n);
     for (int l = 0; l < n; ++l) {
         const int64_t kp = pad64(r[l]);
-        double* srcT = ar.get<double>(N * r[l]);
         ss[l] = x64_alloc(ar, N, kp);
         ts[l] = x64_alloc(ar, r[l], kp);
-        if (!srcT || !ss[l].ok() || !ts[l].ok()) return tc_err(err, "x64_apply: out of memory", LS_ERR_OOM);
-        if (launch_transpose(src[l], r[l], N, srcT, st) != cudaSuccess ||
-            launch_split_x64(srcT, N, r[l], r[l], nullptr, ss[l], st) != cudaSuccess ||
-            launch_split_x64(T[l], r[l], r[l], r[l], nullptr, ts[l], st) != cudaSuccess)
-            return tc_err(err, "x64_apply: split failed");
+        if (!ss[l].ok() || !ts[l].ok()) return tc_err(err, "x64_apply: out of memory", LS_ERR_OOM);
+        sb.add(src[l], N, r[l], 1, N, nullptr, ss[l]);
+        sb.add(T[l], r[l], r[l], r[l], 1, nullptr, ts[l]);
         sp[l] = X64Spec{&ss[l], &ts[l], N, r[l], TcOut{dst[l], N, 0, OUT_F64, 0}, 1};
     }
+    if (sb.flush() != cudaSuccess) return tc_err(err, "x64_apply: split failed");
     return gemm_x64(sp.data(), n, flag, st, err);
 }
 
@@ -441,24 +477,24 @@ int x64_basis(int n, const double* const V[], const int64_t ldv[], const int32_t
               const double* const w[], const double* const isl[], const double* const a[], const int64_t C[],
               int64_t N, const int r[], double* const Y[], int* flag, cudaStream_t st, std::string* err) {
     Arena ar(st);
+    SplitBatch sb(st);
     std::vector<X64Op> as(n), ys(n);
     std::vector<X64Spec> sp(n);
     for (int l = 0; l < n; ++l) {
         const int64_t kp = pad64(C[l]);
         double* At = ar.get<double>((int64_t)r[l] * C[l]);
-        double* aT = ar.get<double>(N * C[l]);
         as[l] = x64_alloc(ar, N, kp);
         ys[l] = x64_alloc(ar, r[l], kp);
-        if (!At || !aT || !as[l].ok() || !ys[l].ok()) return tc_err(err, "x64_basis: out of memory", LS_ERR_OOM);
+        if (!At || !as[l].ok() || !ys[l].ok()) return tc_err(err, "x64_basis: out of memory", LS_ERR_OOM);
         const int64_t ne = (int64_t)r[l] * C[l];
         k_basis_rows<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(V[l], ldv[l], perm[l], w[l], isl[l], C[l], r[l], At);
         count_kernels(1);
-        if (cudaGetLastError() != cudaSuccess || launch_transpose(a[l], C[l], N, aT, st) != cudaSuccess ||
-            launch_split_x64(aT, N, C[l], C[l], nullptr, as[l], st) != cudaSuccess ||
-            launch_split_x64(At, r[l], C[l], C[l], nullptr, ys[l], st) != cudaSuccess)
-            return tc_err(err, "x64_basis: split failed");
+        if (cudaGetLastError() != cudaSuccess) return tc_err(err, "x64_basis: launch failed");
+        sb.add(a[l], N, C[l], 1, N, nullptr, as[l]);      // a_l^T, read transposed
+        sb.add(At, r[l], C[l], C[l], 1, nullptr, ys[l]);
         sp[l] = X64Spec{&as[l], &ys[l], N, r[l], TcOut{Y[l], N, 0, OUT_F64, 0}, 1};
     }
+    if (sb.flush() != cudaSuccess) return tc_err(err, "x64_basis: split failed");
     return gemm_x64(sp.data(), n, flag, st, err);
 }
 
@@ -477,23 +513,23 @@ int x64_pchol_vectors(int n, const double* const L[], const int64_t kmax[], cons
                       const double* const U[], const double* const H[], double* const Vg[], int* flag,
                       cudaStream_t st, std::string* err) {
     Arena ar(st);
+    SplitBatch sb(st);
     std::vector<X64Op> us(n), ls(n);
     std::vector<X64Spec> sp(n);
     for (int l = 0; l < n; ++l) {
         const int64_t kp = pad64(k[l]);
-        double* Ut = ar.get<double>((int64_t)k[l] * k[l]);
         double* rs = ar.get<double>(k[l]);
         us[l] = x64_alloc(ar, k[l], kp);
         ls[l] = x64_alloc(ar, C[l], kp);
-        if (!Ut || !rs || !us[l].ok() || !ls[l].ok()) return tc_err(err, "x64_pchol_vectors: out of memory", LS_ERR_OOM);
+        if (!rs || !us[l].ok() || !ls[l].ok()) return tc_err(err, "x64_pchol_vectors: out of memory", LS_ERR_OOM);
         k_diag_rsqrt<<<(k[l] + 127) / 128, 128, 0, st>>>(H[l], k[l], rs);
         count_kernels(1);
-        if (cudaGetLastError() != cudaSuccess || launch_transpose(U[l], k[l], k[l], Ut, st) != cudaSuccess ||
-            launch_split_x64(Ut, k[l], k[l], k[l], rs, us[l], st) != cudaSuccess ||
-            launch_split_x64(L[l], C[l], k[l], kmax[l], nullptr, ls[l], st) != cudaSuccess)
-            return tc_err(err, "x64_pchol_vectors: split failed");
+        if (cudaGetLastError() != cudaSuccess) return tc_err(err, "x64_pchol_vectors: launch failed");
+        sb.add(U[l], k[l], k[l], 1, k[l], rs, us[l]);          // U^T, read transposed, rows scaled
+        sb.add(L[l], C[l], k[l], kmax[l], 1, nullptr, ls[l]);
         sp[l] = X64Spec{&us[l], &ls[l], k[l], C[l], TcOut{Vg[l], k[l], 0, OUT_F64, 0}, 1};
     }
+    if (sb.flush() != cudaSuccess) return tc_err(err, "x64_pchol_vectors: split failed");
     return gemm_x64(sp.data(), n, flag, st, err);
 }
 
@@ -508,37 +544,24 @@ int x64_small(int n, const double* const A[], const int ta[], const double* cons
     for (int g0 = 0; g0 < n; g0 += kX64MaxJobs) {
         const int ng = std::min(kX64MaxJobs, n - g0);
         Arena ar(st);
+        SplitBatch sb(st);
         std::vector<X64Op> xs(ng), ys(ng);
         std::vector<X64Spec> sp(ng);
         for (int i = 0; i < ng; ++i) {
             const int l = g0 + i, kk = k[l];
             const int64_t kp = pad64(kk);
-            const double* X = A[l];
-            const double* Y = B[l];
-            if (ta[l] || !tb[l]) {
-                double* t = ar.get<double>((int64_t)kk * kk * 2);
-                if (!t) return tc_err(err, "x64_small: out of memory", LS_ERR_OOM);
-                if (ta[l]) {
-                    if (launch_transpose(A[l], kk, kk, t, st) != cudaSuccess) return tc_err(err, "x64_small: transpose");
-                    X = t;
-                }
-                if (!tb[l]) {
-                    if (launch_transpose(B[l], kk, kk, t + (int64_t)kk * kk, st) != cudaSuccess)
-                        return tc_err(err, "x64_small: transpose");
-                    Y = t + (int64_t)kk * kk;
-                }
-            }
             xs[i] = x64_alloc(ar, kk, kp);
             ys[i] = x64_alloc(ar, kk, kp);
             if (!xs[i].ok() || !ys[i].ok()) return tc_err(err, "x64_small: out of memory", LS_ERR_OOM);
-            if (launch_split_x64(X, kk, kk, kk, nullptr, xs[i], st) != cudaSuccess ||
-                launch_split_x64(Y, kk, kk, kk, nullptr, ys[i], st) != cudaSuccess)
-                return tc_err(err, "x64_small: split failed");
+            // X = op(A) in rows; Y = op(B)^T in rows: transposes are strided reads
+            sb.add(A[l], kk, kk, ta[l] ? 1 : kk, ta[l] ? kk : 1, nullptr, xs[i]);
+            sb.add(B[l], kk, kk, tb[l] ? kk : 1, tb[l] ? 1 : kk, nullptr, ys[i]);
             if (add && add[l] && add[l] != out[l] &&
                 cudaMemcpyAsync(out[l], add[l], sizeof(double) * kk * kk, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
                 return tc_err(err, "x64_small: copy failed");
             sp[i] = X64Spec{&xs[i], &ys[i], kk, kk, TcOut{out[l], kk, 0, OUT_F64, (add && add[l]) ? 1 : 0}, 0};
         }
+        if (sb.flush() != cudaSuccess) return tc_err(err, "x64_small: split failed");
         int rc = gemm_x64(sp.data(), ng, flag, st, err);
         if (rc != LS_OK) return rc;
     }
@@ -546,47 +569,71 @@ int x64_small(int n, const double* const A[], const int ta[], const double* cons
 }
 
 // T = S^{-1/2} by the series I - Delta/2 + 3/8 Delta^2 - 5/16 Delta^3, Delta = S - I
-// (S close to I): Delta formed in place of D2's partner, the two powers on the tensor
-// cores, then the combination.
-__global__ void k_minus_identity(const double* __restrict__ S, int k, double* __restrict__ D) {
+// (S close to I): Delta, the two powers on the tensor cores, then the combination; the
+// elementwise steps take every matrix in one launch (blockIdx.y).
+struct LowdinSet {
+    const double* S[kX64MaxJobs];
+    double* Dl[kX64MaxJobs];
+    const double* D2[kX64MaxJobs];
+    const double* D3[kX64MaxJobs];
+    double* T[kX64MaxJobs];
+    int k[kX64MaxJobs];
+};
+__global__ void k_minus_identity(const __grid_constant__ LowdinSet L) {
+    const int j = blockIdx.y, k = L.k[j];
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= (int64_t)k * k) return;
-    D[e] = S[e] - ((e / k) == (e % k) ? 1.0 : 0.0);
+    L.Dl[j][e] = L.S[j][e] - ((e / k) == (e % k) ? 1.0 : 0.0);
 }
-__global__ void k_lowdin_combine(const double* __restrict__ Dl, const double* __restrict__ D2,
-                                 const double* __restrict__ D3, int k, double* __restrict__ T) {
+__global__ void k_lowdin_combine(const __grid_constant__ LowdinSet L) {
+    const int j = blockIdx.y, k = L.k[j];
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= (int64_t)k * k) return;
     const double id = (e / k) == (e % k) ? 1.0 : 0.0;
-    T[e] = id - 0.5 * Dl[e] + 0.375 * D2[e] - 0.3125 * D3[e];
+    L.T[j][e] = id - 0.5 * L.Dl[j][e] + 0.375 * L.D2[j][e] - 0.3125 * L.D3[j][e];
 }
 
 int x64_lowdin(int n, const double* const S[], const int k[], double* const D2[], double* const T[], int* flag,
                cudaStream_t st, std::string* err) {
-    Arena ar(st);
-    std::vector<double*> Dl(n), D3(n);
-    std::vector<const double*> Dlc(n), D2c(n);
-    std::vector<int> zero(n, 0), one(n, 1);
-    for (int l = 0; l < n; ++l) {
-        const int64_t kk = (int64_t)k[l] * k[l];
-        Dl[l] = ar.get<double>(kk);
-        D3[l] = ar.get<double>(kk);
-        if (!Dl[l] || !D3[l]) return tc_err(err, "x64_lowdin: out of memory", LS_ERR_OOM);
-        k_minus_identity<<<(unsigned)((kk + 255) / 256), 256, 0, st>>>(S[l], k[l], Dl[l]);
+    for (int g0 = 0; g0 < n; g0 += kX64MaxJobs) {
+        const int ng = std::min(kX64MaxJobs, n - g0);
+        Arena ar(st);
+        LowdinSet L{};
+        std::vector<const double*> Dlc(ng), D2c(ng);
+        std::vector<double*> D3(ng), D2m(ng);
+        std::vector<int> zero(ng, 0), one(ng, 1), kk(ng);
+        int64_t emax = 1;
+        for (int i = 0; i < ng; ++i) {
+            const int l = g0 + i;
+            const int64_t e = (int64_t)k[l] * k[l];
+            L.S[i] = S[l];
+            L.Dl[i] = ar.get<double>(e);
+            D3[i] = ar.get<double>(e);
+            if (!L.Dl[i] || !D3[i]) return tc_err(err, "x64_lowdin: out of memory", LS_ERR_OOM);
+            L.D2[i] = D2[l];
+            L.D3[i] = D3[i];
+            L.T[i] = T[l];
+            L.k[i] = kk[i] = k[l];
+            Dlc[i] = L.Dl[i];
+            D2c[i] = D2[l];
+            D2m[i] = D2[l];
+            emax = std::max(emax, e);
+        }
+        const dim3 grid((unsigned)((emax + 255) / 256), (unsigned)ng);
+        k_minus_identity<<<grid, 256, 0, st>>>(L);
         count_kernels(1);
-        Dlc[l] = Dl[l];
-        D2c[l] = D2[l];
-    }
-    // Delta is symmetric: Delta^2 = Delta Delta^T and Delta^3 = Delta^2 Delta^T need no transposes
-    int rc = x64_small(n, Dlc.data(), zero.data(), Dlc.data(), one.data(), k, D2, nullptr, flag, st, err);
-    if (rc == LS_OK) rc = x64_small(n, D2c.data(), zero.data(), Dlc.data(), one.data(), k, D3.data(), nullptr, flag, st, err);
-    if (rc != LS_OK) return rc;
-    for (int l = 0; l < n; ++l) {
-        const int64_t kk = (int64_t)k[l] * k[l];
-        k_lowdin_combine<<<(unsigned)((kk + 255) / 256), 256, 0, st>>>(Dl[l], D2[l], D3[l], k[l], T[l]);
+        // Delta is symmetric: Delta^2 = Delta Delta^T and Delta^3 = Delta^2 Delta^T need no transposes
+        int rc = x64_small(ng, Dlc.data(), zero.data(), Dlc.data(), one.data(), kk.data(), D2m.data(), nullptr, flag, st,
+                           err);
+        if (rc == LS_OK)
+            rc = x64_small(ng, D2c.data(), zero.data(), Dlc.data(), one.data(), kk.data(), D3.data(), nullptr, flag, st,
+                           err);
+        if (rc != LS_OK) return rc;
+        k_lowdin_combine<<<grid, 256, 0, st>>>(L);
         count_kernels(1);
+        if (cudaGetLastError() != cudaSuccess) return tc_err(err, "x64_lowdin: launch failed");
     }
-    return cudaGetLastError() == cudaSuccess ? LS_OK : tc_err(err, "x64_lowdin: launch failed");
+    return LS_OK;
 }
 
 // D = A B^T (A: M x K, B: N x K, D: M x N, row-major), then a synchronised status check
@@ -597,9 +644,10 @@ int x64_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t 
     const int64_t kp = pad64(std::max<int64_t>(K, 1));
     X64Op as = x64_alloc(ar, M, kp), bs = x64_alloc(ar, N, kp);
     if (!fl.d || !as.ok() || !bs.ok()) return tc_err(err, "gemm_nt: out of memory", LS_ERR_OOM);
-    if (launch_split_x64(A, M, K, K, nullptr, as, st) != cudaSuccess ||
-        launch_split_x64(B, N, K, K, nullptr, bs, st) != cudaSuccess)
-        return tc_err(err, "gemm_nt: split failed");
+    SplitBatch sb(st);
+    sb.add(A, M, K, K, 1, nullptr, as);
+    sb.add(B, N, K, K, 1, nullptr, bs);
+    if (sb.flush() != cudaSuccess) return tc_err(err, "gemm_nt: split failed");
     X64Spec sp{&as, &bs, M, N, TcOut{D, N, 0, OUT_F64, 0}, 0};
     int rc = gemm_x64(&sp, 1, fl.d, st, err);
     if (rc != LS_OK) return rc;
