@@ -253,86 +253,84 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
                     __syncthreads();
                 }
                 if (!stop) {
-                    // the inner sweeps of all pair-blocks in lockstep: per inner round, one thread per
-                    // rotation (8 a pair-block) computes the angles, then all threads rotate the 2 x 2
-                    // blocks of E (56 a pair-block) and accumulate F_Q (128 items a pair-block)
-                    const int nrot = nb * (BJ2 / 2);
-                    for (int e = tid; e < nb * SPSQ; e += nthr) Tw[e] = 0.f;
-                    if (tid < nb) {
-                        int I, Jb;
-                        rr_pair_e(t, tid, m, I, Jb);
-                        pb[tid] = I | (Jb << 16);
-                        s_act[tid] = 0;
-                    }
-                    unsigned int cnt = 0;
-                    __syncthreads();
-                    // the first round of a sweep gives each pair-block a full inner sweep (every pair
+                    // the inner sweeps, a warp per pair-block (their indices are disjoint, so the
+                    // warps need no CTA barrier): per inner round lanes 0..7 compute the angles, then
+                    // the warp rotates the 2 x 2 blocks of E (56) and accumulates F_Q (128 items).
+                    // The first round of a sweep gives each pair-block a full inner sweep (every pair
                     // within its two blocks); the other rounds only pair the two blocks' indices with
                     // each other (8 inner rounds), as every block's own pairs were rotated this sweep
                     const int n_inner = t == 0 ? BJ2 - 1 : BJ;
-                    for (int it = 0; it < n_inner; ++it) {
-                        InRot* ri = aw + (it & 1) * nrot;
-                        if (tid < nrot) {
-                            const int sub = tid >> 3, l = tid & 7;
-                            const int I = pb[sub] & 0xffff, Jb = pb[sub] >> 16;
-                            int u, v;
-                            if (t == 0) rr_pair_e(it, l, BJ2, u, v);
-                            else { u = l; v = BJ + ((l + it) & (BJ - 1)); }
-                            const int p = bj_index(I, Jb, u), q = bj_index(I, Jb, v);
-                            InRot r{1.f, 0.f, 0.f, u | (v << 8)};
-                            if (p < k && q < k) {
-                                const float epq = E[p * ldE + q];
-                                if (qualifies(D[p], D[q], epq)) {
-                                    const RotCS g = jacobi_rot(df_diff(D[q], D[p]), epq);
-                                    r = InRot{g.c, g.s, g.cm1, u | (v << 8) | (1 << 16)};
-                                    const float te = g.t * epq;
-                                    D[p] = df_add(D[p], -te);
-                                    D[q] = df_add(D[q], te);
-                                    E[p * ldE + q] = 0.f;
-                                    E[q * ldE + p] = 0.f;
-                                    s_act[sub] = 1;
-                                    ++cnt;
+                    for (int sub = warp; sub < nb; sub += nw) {
+                        int I, Jb;
+                        rr_pair_e(t, sub, m, I, Jb);
+                        float* fq = Tw + sub * SPSQ;
+                        InRot* ri = aw + sub * (BJ2 / 2);
+                        for (int e = lane; e < SPSQ; e += 32) fq[e] = 0.f;
+                        if (lane == 0) pb[sub] = I | (Jb << 16);
+                        __syncwarp();
+                        unsigned int nrot = 0;
+                        for (int it = 0; it < n_inner; ++it) {
+                            if (lane < BJ2 / 2) {
+                                int u, v;
+                                if (t == 0) rr_pair_e(it, lane, BJ2, u, v);
+                                else { u = lane; v = BJ + ((lane + it) & (BJ - 1)); }
+                                const int p = bj_index(I, Jb, u), q = bj_index(I, Jb, v);
+                                InRot r{1.f, 0.f, 0.f, u | (v << 8)};
+                                if (p < k && q < k) {
+                                    const float epq = E[p * ldE + q];
+                                    if (qualifies(D[p], D[q], epq)) {
+                                        const RotCS g = jacobi_rot(df_diff(D[q], D[p]), epq);
+                                        r = InRot{g.c, g.s, g.cm1, u | (v << 8) | (1 << 16)};
+                                        const float te = g.t * epq;
+                                        D[p] = df_add(D[p], -te);
+                                        D[q] = df_add(D[q], te);
+                                        E[p * ldE + q] = 0.f;
+                                        E[q * ldE + p] = 0.f;
+                                        ++nrot;
+                                    }
                                 }
+                                ri[lane] = r;
                             }
-                            ri[tid] = r;
+                            __syncwarp();
+                            // E <- J^T E J on the 2 x 2 blocks (i, i2), i != i2
+                            for (int e = lane; e < 64; e += 32) {
+                                const int i = e >> 3, i2 = e & 7;
+                                if (i == i2) continue;
+                                const InRot ra = ri[i], rb = ri[i2];
+                                if (!((ra.uv | rb.uv) & (1 << 16))) continue;
+                                const int pa = bj_index(I, Jb, ra.uv & 255), qa = bj_index(I, Jb, (ra.uv >> 8) & 255);
+                                const int pc = bj_index(I, Jb, rb.uv & 255), qc = bj_index(I, Jb, (rb.uv >> 8) & 255);
+                                const float x0 = E[pa * ldE + pc], x1 = E[pa * ldE + qc];
+                                const float x2 = E[qa * ldE + pc], x3 = E[qa * ldE + qc];
+                                const float ypp = ra.c * x0 - ra.s * x2, ypq = ra.c * x1 - ra.s * x3;
+                                const float yqp = ra.s * x0 + ra.c * x2, yqq = ra.s * x1 + ra.c * x3;
+                                E[pa * ldE + pc] = rb.c * ypp - rb.s * ypq;
+                                E[pa * ldE + qc] = rb.s * ypp + rb.c * ypq;
+                                E[qa * ldE + pc] = rb.c * yqp - rb.s * yqq;
+                                E[qa * ldE + qc] = rb.s * yqp + rb.c * yqq;
+                            }
+                            // F_Q <- F_Q J on local positions, c - 1 kept apart
+                            for (int e = lane; e < 8 * BJ2; e += 32) {
+                                const InRot r = ri[e >> 4];
+                                if (!(r.uv & (1 << 16))) continue;
+                                const int y = e & 15, u = r.uv & 255, v = (r.uv >> 8) & 255;
+                                const float fp = fq[y * SP + u], fv = fq[y * SP + v];
+                                float np = fp + (fp * r.cm1 - fv * r.s);
+                                float nv = fv + (fp * r.s + fv * r.cm1);
+                                if (y == u) { np += r.cm1; nv += r.s; }
+                                if (y == v) { np -= r.s; nv += r.cm1; }
+                                fq[y * SP + u] = np;
+                                fq[y * SP + v] = nv;
+                            }
+                            __syncwarp();
                         }
-                        __syncthreads();
-                        // E <- J^T E J on the 2 x 2 blocks (i, i2), i != i2, of every pair-block
-                        for (int e = tid; e < nb * 64; e += nthr) {
-                            const int sub = e >> 6, i = (e >> 3) & 7, i2 = e & 7;
-                            if (i == i2) continue;
-                            const InRot a = ri[sub * 8 + i], b = ri[sub * 8 + i2];
-                            if (!((a.uv | b.uv) & (1 << 16))) continue;
-                            const int I = pb[sub] & 0xffff, Jb = pb[sub] >> 16;
-                            const int pa = bj_index(I, Jb, a.uv & 255), qa = bj_index(I, Jb, (a.uv >> 8) & 255);
-                            const int pc = bj_index(I, Jb, b.uv & 255), qc = bj_index(I, Jb, (b.uv >> 8) & 255);
-                            const float x0 = E[pa * ldE + pc], x1 = E[pa * ldE + qc];
-                            const float x2 = E[qa * ldE + pc], x3 = E[qa * ldE + qc];
-                            const float ypp = a.c * x0 - a.s * x2, ypq = a.c * x1 - a.s * x3;
-                            const float yqp = a.s * x0 + a.c * x2, yqq = a.s * x1 + a.c * x3;
-                            E[pa * ldE + pc] = b.c * ypp - b.s * ypq;
-                            E[pa * ldE + qc] = b.s * ypp + b.c * ypq;
-                            E[qa * ldE + pc] = b.c * yqp - b.s * yqq;
-                            E[qa * ldE + qc] = b.s * yqp + b.c * yqq;
+                        for (int o = 16; o; o >>= 1) nrot += __shfl_xor_sync(0xffffffffu, nrot, o);
+                        if (lane == 0) {
+                            s_act[sub] = nrot > 0;
+                            if (nrot) atomicAdd(&s_active, nrot);
                         }
-                        // F_Q <- F_Q J on local positions of every pair-block, c - 1 kept apart
-                        for (int e = tid; e < nb * 8 * BJ2; e += nthr) {
-                            const int sub = e >> 7;
-                            const InRot r = ri[sub * 8 + ((e >> 4) & 7)];
-                            if (!(r.uv & (1 << 16))) continue;
-                            float* fq = Tw + sub * SPSQ;
-                            const int y = e & 15, u = r.uv & 255, v = (r.uv >> 8) & 255;
-                            const float fp = fq[y * SP + u], fv = fq[y * SP + v];
-                            float np = fp + (fp * r.cm1 - fv * r.s);
-                            float nv = fv + (fp * r.s + fv * r.cm1);
-                            if (y == u) { np += r.cm1; nv += r.s; }
-                            if (y == v) { np -= r.s; nv += r.cm1; }
-                            fq[y * SP + u] = np;
-                            fq[y * SP + v] = nv;
-                        }
-                        __syncthreads();
                     }
-                    if (cnt) atomicAdd(&s_active, cnt);
+                    __syncthreads();
                     // F_Q to the F rows' CTAs; Q = I + F_Q kept for the tiles
                     for (int e = tid; e < nb * BJ2SQ; e += nthr) {
                         const int sub = e >> 8, f0 = e & 255;
