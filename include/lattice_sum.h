@@ -262,18 +262,21 @@ int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, double abs_fl
 
 /*
  * lattice_sum_gemm_nt_mixed -- D = A B^T for device FP64 matrices (A: M x K,
- * B: N x K, row-major; K <= 2048) in the arithmetic of the mixed slab
+ * B: N x K, row-major; K <= 4096 with FP32 output, any K with FP64 output:
+ * chunks of 4096 added in FP64) in the arithmetic of the mixed slab
  * evaluation. Each operand row is scaled by a power of two to (-64, 64) and
  * written as d0 + d1 2^-7 + t1 + t2: d0, d1 nearest integers in [-64, 64],
  * t1 and t2 11-bit rests, all stored exactly as FP16 (times 2^9). The form
  * is good to 2^-36 of the row's scale.
  * On tcgen05 tensor cores the level-0 products d0 d0 and the level-1
  * products (d0 d1 + d1 d0) 2^-7 accumulate EXACTLY in FP32 (integers below
- * 2^24 in their units). The eight products below them go to a third
+ * 2^24 in their units; above K = 2048 d0 d1 and d1 d0 take an accumulator
+ * each). The eight products below them go to a third
  * accumulator, whose rounding (the tensor cores' adds truncate) sits below
  * 2^-14 of the result.
  * Error: about 2^-32 of max_k|a_mk| max_k|b_nk| per term, from the dropped
- * d1 t2 and t2 d1 products.
+ * d1 t2 and t2 d1 products, plus the third accumulator's drift (its adds
+ * truncate): on random data 2^-38 K^1.5 of max|a| max|b| or less.
  * D (device, M x N row-major) is LS_OUT_F32 (the exact sum rounded once) or
  * LS_OUT_F64 per `out_dtype`. `tile_n` picks the output tile width (32, 64,
  * 128; 0 = by size). `stream` is a cudaStream_t or NULL; the call

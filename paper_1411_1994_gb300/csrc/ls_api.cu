@@ -469,7 +469,6 @@ struct RedState {
     // [6, 9): spare per-mode statuses; [9]: the exact-slice tensor-core products (never reset)
     DevStatus* d_st = nullptr;
     double* d_sel = nullptr;
-    GemmWs gw{};
     RedMode m[3];
     int sweeps[3] = {0, 0, 0};
     int64_t rotations[3] = {0, 0, 0};
@@ -504,12 +503,6 @@ int red_prepare(RedState& R, PcholJob* pj) {
     CUS(dalloc(ctx, &R.d_st, 10));
     CUS(cudaMemsetAsync(R.d_st, 0, 10 * sizeof(DevStatus), st));
     CUS(dalloc(ctx, &R.d_sel, 9));
-    R.gw.num_sms = ctx->num_sms;
-    R.gw.ws_cap = gemm_ws_doubles(ctx->num_sms);
-    R.gw.ctr_cap = gemm_ws_counters(ctx->num_sms);
-    CUS(dalloc(ctx, &R.gw.ws, R.gw.ws_cap));
-    CUS(dalloc(ctx, &R.gw.ctr, R.gw.ctr_cap));
-    CUS(cudaMemsetAsync(R.gw.ctr, 0, R.gw.ctr_cap * sizeof(unsigned int), st));
     const double* a[3];
     const double* w[3];
     double* G[3];
@@ -585,7 +578,13 @@ int red_after_pchol(RedState& R, JacobiJob* jj) {
         const double tau = R.forced ? 0.0 : 1e-3 * R.eps * R.eps * (double)R.T / (double)k;
         jj[l] = JacobiJob{M.H, M.V, M.snap, R.d_st + l, k, R.floor_noise, tau};
     }
-    { Scope sc("pchol", st); CUS(launch_pchol_gram_n(3, L, Cs, ks, Cs, H, R.gw, st)); }
+    {
+        // H = L^T L: FP64-grade products on the tensor cores (exact slices)
+        Scope sc("pchol", st);
+        std::string err;
+        int rc = x64_pchol_gram(3, L, Cs, ks, Cs, H, &R.d_st[9].flag, st, &err);
+        if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: L^T L: %s", err.c_str());
+    }
     return LS_OK;
 }
 
@@ -812,8 +811,6 @@ int red_finish(RedState& R, ls_tucker_info* info) {
     dfree(ctx, d_perm_t);
     dfree(ctx, d_off);
     dfree(ctx, R.d_sel);
-    dfree(ctx, R.gw.ws);
-    dfree(ctx, R.gw.ctr);
     CUS(cudaMemcpyAsync(&R.hs[3], R.d_st + 3, 3 * sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
     CUS(cudaMemcpyAsync(&R.hs[9], R.d_st + 9, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
     count_d2h(4 * sizeof(DevStatus));
@@ -1080,7 +1077,18 @@ int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ran
     if (ctx->reduced) return fail(ctx, LS_ERR_STATE, "rhosvd_reduce: already reduced");
     if (!forced_ranks && !(eps > 0.0)) return fail(ctx, LS_ERR_ARG, "rhosvd_reduce: eps must be > 0");
     ls_ctx* one[1] = {ctx};
-    return reduce_many(one, 1, eps, forced_ranks, info);
+    const int rc = reduce_many(one, 1, eps, forced_ranks, info);
+    // a large reduction leaves tens of GB of freed scratch in the stream-ordered pool
+    // (the stream is synchronised here): when the device runs short, give it back beyond a
+    // few GB, so that other allocators on the device can use it
+    size_t fr = 0, tot = 0;
+    if (rc == LS_OK && cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr < ((size_t)32 << 30)) {
+        cudaMemPool_t pool;
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
+            cudaMemPoolTrimTo(pool, (size_t)4 << 30);
+    }
+    return rc;
 }
 
 int lattice_sum_batch_reduce(ls_ctx* const* ctxs, int32_t n, double eps, ls_tucker_info* infos) {

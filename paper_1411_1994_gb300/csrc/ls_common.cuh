@@ -72,21 +72,6 @@ cudaError_t launch_assemble(const double* g, int64_t N, const int32_t* colq, con
 // norms[c] = ||a_c||; a_c /= norms[c] in place (rows of a, stride N).
 cudaError_t launch_norm_columns(double* a, int64_t C, int64_t N, double* norms, cudaStream_t st);
 
-// Workspace of the grouped FP64 GEMMs: split-K partials (ws_cap doubles) and
-// one counter per output tile (ctr_cap counters, zero at allocation; every
-// launch leaves them zero). A split-K product needs both; with ws == NULL
-// the products run unsplit.
-struct GemmWs {
-    double* ws; int64_t ws_cap; unsigned int* ctr; int64_t ctr_cap; int num_sms;
-};
-// workspace sizes that allow every split the launcher chooses on num_sms SMs
-inline int64_t gemm_ws_doubles(int num_sms) { return 2 * (int64_t)num_sms * 64 * 64; }
-inline int64_t gemm_ws_counters(int num_sms) { return 2 * (int64_t)num_sms; }
-
-// H = L^T L (k x k) from the first k columns of L (C x kmax, row-major).
-cudaError_t launch_pchol_gram_n(int n, const double* const L[], const int64_t kmax[], const int k[],
-                                const int64_t C[], double* const H[], const GemmWs& W, cudaStream_t st);
-
 // Cholesky A = L L^T in place (lower; A is r x r row-major, its upper part is
 // overwritten) and Li = L^{-1} (lower, zeros above) for several matrices in
 // one cooperative launch. st: zeroed status per job; a non-positive pivot

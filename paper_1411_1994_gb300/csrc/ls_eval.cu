@@ -32,10 +32,14 @@
 //   acc2 = the products below 2^-7 of a digit unit squared, smallest first:
 //     d0 t2, t2 d0, t1 t1, d1 t1, t1 d1, d1 d1, d0 t1, t1 d0 (11 MMAs a
 //     k-step in all).
+// K ranges above 2048 (up to 4096) take a fourth accumulator: acc1 keeps
+// d0 d1 and acc3 d1 d0, each a sum of multiples of 2^-7 below 2^12 K, exact
+// for K <= 4096.
 // The two leading levels are exact, whatever rounding the tensor core's adds
 // use. That matters: they truncate, and a float accumulator holding terms at
 // 2^-7 of the result drifts by about half an ulp per MMA. acc2 sits below
-// 2^-14 of the result, where that drift is negligible. The dropped products
+// 2^-14 of the result, where that drift stays small: on random data about
+// 2^-38 K^1.5 of max|a| max|b| or less (measured: 2^-21 at K = 4096). The dropped products
 // (d1 t2, t2 d1, t1 t2, ...) are below 2^-32 of 2^(E_a + E_b) per term.
 //
 // The epilogue adds the three accumulators as an unevaluated FP32 pair
@@ -80,10 +84,11 @@ using namespace tc5;
 constexpr int DT_BM = 128, DT_BK = 32, DT_PARTS = 4, DT_EPI_WARPS = 16;
 constexpr int DT_THREADS = 64 + 32 * DT_EPI_WARPS;       // TMA warp, MMA warp, epilogue warps
 constexpr int DT_TA = DT_BM * DT_BK * 2;                 // one A part tile: 8 KB
-constexpr int DT_MAXK = 2048;                            // exact level-1 accumulation
+constexpr int DT_MAXK = 2048;                            // exact level-1 accumulation, three accumulators
+constexpr int DT_MAXK4 = 4096;                           // the same with four
 constexpr int FXB = 50;                                  // fraction bits of the fixed-point split
 
-constexpr int pow2ceil(int x) {
+__host__ __device__ constexpr int pow2ceil(int x) {
     int p = 32;
     while (p < x) p <<= 1;
     return p;
@@ -94,11 +99,13 @@ struct DtCfg {
     static constexpr int TB = BN * DT_BK * 2;
     static constexpr int STAGE = DT_PARTS * (DT_TA + TB);
     static constexpr int STAGES = std::min(8, (220 * 1024) / STAGE);
-    static constexpr int NBUF = 3 * BN * 2 <= 512 ? 2 : 1;
-    static constexpr int TMEM_COLS = pow2ceil(3 * BN * NBUF);
     static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024 + 256;
-    static_assert(3 * BN * NBUF <= 512, "three accumulators per buffer must fit TMEM");
+    static_assert(4 * BN <= 512, "four accumulators must fit TMEM");
 };
+// accumulator buffers (two when both fit TMEM, so that a tile's MMAs overlap the
+// previous tile's epilogue) and the TMEM columns they take
+__host__ __device__ constexpr int dt_nbuf(int bn, int nacc) { return nacc * bn * 2 <= 512 ? 2 : 1; }
+__host__ __device__ constexpr int dt_tmem_cols(int bn, int nacc) { return pow2ceil(nacc * bn * dt_nbuf(bn, nacc)); }
 
 struct DtJob {
     CUtensorMap a, b;          // (kpad, rows, 4 * batch) fp16, 64-byte swizzle
@@ -112,6 +119,7 @@ struct DtJob {
     void* out;                 // out[z * zs + n * ldn + m]
     int64_t ldn, zs;
     int mode;                  // DtOutMode (also the kernel's template argument)
+    int nacc;                  // accumulators: 3 (K ranges <= 2048) or 4 (<= 4096)
     int accumulate;            // DT_F64 only: out += D
     const int* kb_lo;          // per-z k-block ranges [kb_lo[z], kb_lo[z + 1]) (grouped form), or
     int kb_begin, kb_end;      // one range for every z
@@ -184,22 +192,27 @@ __device__ __forceinline__ double pair_to_f64(float hi, float lo, int e) {
     return __longlong_as_double((long long)bits);
 }
 
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
 // a0 + a1 + a2 (a0, a1 exact, |a2| small) as an unevaluated pair hi + lo, by two
 // TwoSums: hi is the sum rounded once, lo the rest to about 2^-48 of it
 __device__ __forceinline__ void combine3(float a0, float a1, float a2, float& hi, float& lo) {
-    const float s = a0 + a1;
-    const float bb = s - a0;
-    const float e = (a0 - (s - bb)) + (a1 - bb);
+    float s, e;
+    two_sum(a0, a1, s, e);
     const float t = e + a2;
     hi = s + t;
     const float b2 = hi - s;
     lo = (s - (hi - b2)) + (t - b2);
 }
-
 template <int BN, int MODE>
 __global__ void __launch_bounds__(DT_THREADS, 1) k_dt_gemm(const __grid_constant__ DtJob J, int* flag) {
     using C = DtCfg<BN>;
-    constexpr int S = C::STAGES, NBUF = C::NBUF;
+    constexpr int S = C::STAGES;
+    const int nacc = J.nacc, NBUF = dt_nbuf(BN, nacc), tcols = dt_tmem_cols(BN, nacc);
     constexpr int QC = BN / 4;                    // columns per epilogue warp
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -225,7 +238,7 @@ __global__ void __launch_bounds__(DT_THREADS, 1) k_dt_gemm(const __grid_constant
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(C::TMEM_COLS));
+                     "r"(tcols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -267,7 +280,8 @@ __global__ void __launch_bounds__(DT_THREADS, 1) k_dt_gemm(const __grid_constant
             const uint32_t buf = lt % NBUF, u = lt / NBUF;
             if (u > 0 && !mbar_wait(&tempty[buf], (u - 1) & 1, flag)) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t c0 = tmem + buf * 3 * BN, c1 = c0 + BN, c2 = c0 + 2 * BN;
+            const uint32_t c0 = tmem + buf * nacc * BN, c1 = c0 + BN, c2 = c0 + 2 * BN,
+                           c3 = nacc == 4 ? c0 + 3 * BN : c1;
             int k0, k1;
             k_range(J, t / (J.tiles_m * J.tiles_n), k0, k1);
             for (int kb = k0; kb < k1; ++kb, ++it) {
@@ -285,7 +299,7 @@ __global__ void __launch_bounds__(DT_THREADS, 1) k_dt_gemm(const __grid_constant
                     const uint32_t acc = (kb != k0 || kk) ? 1u : 0u;
                     mma_bf16(c0, a0, b0, idesc, acc);            // d0 d0: exact
                     mma_bf16(c1, a0, b1, idesc, acc);            // d0 d1, d1 d0: exact
-                    mma_bf16(c1, a1, b0, idesc, 1u);
+                    mma_bf16(c3, a1, b0, idesc, nacc == 4 ? acc : 1u);
                     mma_bf16(c2, a0, b3, idesc, acc);            // the rest, smallest first
                     mma_bf16(c2, a3, b0, idesc, 1u);
                     mma_bf16(c2, a2, b2, idesc, 1u);
@@ -318,7 +332,7 @@ __global__ void __launch_bounds__(DT_THREADS, 1) k_dt_gemm(const __grid_constant
             tile_of(J, t, z, tm, tn);
             const int m = tm * DT_BM + 32 * q + lane, n0 = tn * BN + hc * QC;
             const int nn = max(0, min(QC, J.N - n0));
-            const uint32_t col = tmem + lanes + buf * 3 * BN + hc * QC;
+            const uint32_t col = tmem + lanes + buf * nacc * BN + hc * QC;
             int k0, k1;
             k_range(J, z, k0, k1);
             const bool live = k1 > k0;   // an empty K range leaves the accumulators unwritten: zeros
@@ -327,9 +341,21 @@ __global__ void __launch_bounds__(DT_THREADS, 1) k_dt_gemm(const __grid_constant
             for (int c = 0; c < QC; c += 8) {
                 if (c < nn) {
                     float v0[8], v1[8], v2[8];
+                    if (nacc == 4) {
+                        // the two level-1 sums by TwoSum; its rounding error joins acc2
+                        float v3[8];
+                        tmem_ld8(col + BN + c, v1);
+                        tmem_ld8(col + 3 * BN + c, v3);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) two_sum(v1[j], v3[j], v1[j], v3[j]);
+                        tmem_ld8(col + 2 * BN + c, v2);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) v2[j] += v3[j];
+                    } else {
+                        tmem_ld8(col + BN + c, v1);
+                        tmem_ld8(col + 2 * BN + c, v2);
+                    }
                     tmem_ld8(col + c, v0);
-                    tmem_ld8(col + BN + c, v1);
-                    tmem_ld8(col + 2 * BN + c, v2);
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
                         combine3(live ? v0[j] : 0.f, live ? v1[j] : 0.f, live ? v2[j] : 0.f, hv[c + j], lv[c + j]);
@@ -363,7 +389,7 @@ __global__ void __launch_bounds__(DT_THREADS, 1) k_dt_gemm(const __grid_constant
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
     }
 }
 
@@ -506,12 +532,6 @@ struct SrcGather {
     __device__ static int exp_of(unsigned long long mb) { return SrcF64::exp_of(mb); }
     __device__ long long fixed(int64_t b, int64_t i, int64_t k, int s) const { return fixed_of(at(b, i, k), s); }
 };
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
 
 // The same four parts from an FP32 pair (hi, lo) in FP32 arithmetic: the scaled
 // value as a pair, nearest-integer digits (the differences are exact), the rest
@@ -705,8 +725,8 @@ cudaError_t dt_split(Src src, int64_t cols, const DtOp& d, cudaStream_t st) {
     const int64_t nrows = d.rows * d.batch;
     if (nrows <= 0) return cudaSuccess;
     if (cols > d.kpad) return cudaErrorInvalidValue;
-    if (cols <= 1024) {
-        // a warp per row, one pass
+    if (cols <= 1024 || nrows > 65535) {
+        // a warp per row, one pass (short rows, or enough rows to fill the GPU)
         k_split_dt<Src><<<(unsigned)((nrows * 32 + 255) / 256), 256, 0, st>>>(src, d.rows, cols, d.batch, d.kpad, d.p,
                                                                                d.e);
         count_kernels(1);
@@ -740,8 +760,9 @@ cudaError_t dt_split_tr(const float2* W, int64_t ld, int64_t cols, const DtOp& d
 }
 
 // K ranges of a product, in k-blocks of 32: kb_lo (device, batch + 1 entries) gives
-// batch z the range [kb_lo[z], kb_lo[z + 1]); otherwise every batch takes
-// [kb_begin, kb_end) (kb_end < 0: all of kpad). No range may exceed 2048 entries.
+// batch z the range [kb_lo[z], kb_lo[z + 1]) (the caller guarantees at most 2048
+// entries each); otherwise every batch takes [kb_begin, kb_end) (kb_end < 0: all of
+// kpad), at most 4096 entries.
 struct DtK {
     const int* kb_lo = nullptr;
     int kb_begin = 0, kb_end = -1;
@@ -754,7 +775,7 @@ int dt_gemm(const DtOp& A, const DtOp& B, int64_t M, int64_t N, int64_t batch, c
     if (kr.kb_end < 0) kr.kb_end = nkb;
     if (A.kpad != B.kpad || A.kpad % DT_BK != 0 || M > A.rows || N > B.rows ||
         (A.batch != 1 && A.batch != batch) || (B.batch != 1 && B.batch != batch) ||
-        (!kr.kb_lo && (kr.kb_begin < 0 || kr.kb_end > nkb || kr.kb_end - kr.kb_begin > DT_MAXK / DT_BK)) ||
+        (!kr.kb_lo && (kr.kb_begin < 0 || kr.kb_end > nkb || kr.kb_end - kr.kb_begin > DT_MAXK4 / DT_BK)) ||
         (out.accumulate && out.mode != DT_F64))
         return tc_err(err, "dt gemm: bad operands", LS_ERR_ARG);
     int bn = opt.tile_n;
@@ -784,6 +805,7 @@ int dt_gemm(const DtOp& A, const DtOp& B, int64_t M, int64_t N, int64_t batch, c
     J.ldn = out.ldn;
     J.zs = out.zs;
     J.mode = out.mode;
+    J.nacc = (!kr.kb_lo && kr.kb_end - kr.kb_begin > DT_MAXK / DT_BK) ? 4 : 3;
     J.accumulate = out.accumulate;
     J.kb_lo = kr.kb_lo;
     J.kb_begin = kr.kb_begin;
@@ -838,6 +860,15 @@ cudaError_t upload_pinned(void* dst, const void* src, size_t bytes, cudaStream_t
     return cudaEventRecord(S.done, st);
 }
 
+// Scratch for a chunked product: the free device memory / div, clamped to [lo, hi]; a
+// need of at most lo is granted without asking the driver.
+int64_t scratch_budget(int64_t need, int div, int64_t lo, int64_t hi) {
+    if (need <= lo) return lo;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
+    return std::max(lo, std::min(hi, (int64_t)(fr / div)));
+}
+
 }  // namespace
 
 // Operands of the slab evaluation that depend only on the reduced tensor, built
@@ -860,7 +891,7 @@ int dt_eval(DtEvalCache** cache, const double* const Z[3], const int32_t* r, con
             std::string* err) {
     const int64_t r0 = r[0], r1 = r[1], r2 = r[2];
     const int64_t k0 = pad32(r0), k1 = pad32(r1), k2 = pad32(r2);
-    if (k0 > DT_MAXK || k1 > DT_MAXK || k2 > DT_MAXK) return tc_err(err, "eval: rank above 2048", LS_ERR_ARG);
+    if (k0 > DT_MAXK4 || k1 > DT_MAXK4 || k2 > DT_MAXK4) return tc_err(err, "eval: rank above 4096", LS_ERR_ARG);
     if (nslab <= 0) return LS_OK;
     if (!*cache) {
         Scope sc("eval.prepare", st);
@@ -899,46 +930,57 @@ int dt_eval(DtEvalCache** cache, const double* const Z[3], const int32_t* r, con
         *cache = c;
     }
     const DtEvalCache& c = **cache;
-    // slabs in chunks that bound the per-call scratch to about 1 GB
-    const int64_t per = r0 * r1 * 8 + DT_PARTS * r0 * k1 * 2 + r0 * 4 + N * r0 * 8 + DT_PARTS * N * k0 * 2 + N * 4 +
-                        DT_PARTS * k2 * 2 + 4;
-    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(nslab, ((int64_t)1 << 30) / per));
+    // Slabs in two levels of chunks. An outer chunk takes M for its slabs in one pass
+    // over the core (M as pairs, r0 r1 a slab); an inner chunk then splits its M, and
+    // forms T and S. Scratch: about a quarter of the free memory, 1 to 16 GB.
+    const int64_t per_m = r0 * r1 * 8 + DT_PARTS * k2 * 2 + 4;
+    const int64_t per_t = DT_PARTS * r0 * k1 * 2 + r0 * 4 + N * r0 * 8 + DT_PARTS * N * k0 * 2 + N * 4;
+    const int64_t budget = scratch_budget((int64_t)nslab * (per_m + per_t) * 2, 4, (int64_t)1 << 30, (int64_t)16 << 30);
+    const int mchunk = (int)std::max<int64_t>(1, std::min<int64_t>(nslab, budget / 2 / per_m));
+    const int tchunk = (int)std::max<int64_t>(1, std::min<int64_t>(mchunk, budget / 2 / per_t));
     Arena ar(st);
     Flag fl(ar, st);
-    DtOp z2s = dt_alloc(ar, chunk, k2, 1), ms = dt_alloc(ar, r0, k1, chunk), ts = dt_alloc(ar, N, k0, chunk);
-    float2* Mt = ar.get<float2>((int64_t)chunk * r0 * r1);
-    float2* Tt = ar.get<float2>((int64_t)chunk * N * r0);
+    DtOp z2s = dt_alloc(ar, mchunk, k2, 1), ms = dt_alloc(ar, r0, k1, tchunk), ts = dt_alloc(ar, N, k0, tchunk);
+    float2* Mt = ar.get<float2>((int64_t)mchunk * r0 * r1);
+    float2* Tt = ar.get<float2>((int64_t)tchunk * N * r0);
     if (!fl.d || !z2s.ok() || !ms.ok() || !ts.ok() || !Mt || !Tt) return tc_err(err, "eval: out of memory", LS_ERR_OOM);
     const size_t esz = out_f32 ? 4 : 8;
-    for (int s0 = 0; s0 < nslab; s0 += chunk) {
-        const int ns = std::min(chunk, nslab - s0);
-        DtOp z2 = z2s, m = ms, t = ts;
-        z2.rows = ns;
-        m.batch = ns;
-        t.batch = ns;
+    for (int s0 = 0; s0 < nslab; s0 += mchunk) {
+        const int nm = std::min(mchunk, nslab - s0);
         int rc;
         {
             Scope sc("eval.mt", st);
+            DtOp z2 = z2s;
+            z2.rows = nm;
             // rows s of Z2^T: Z2[c][z_s], gathered
             if (dt_split(SrcF64{Z[2], 1, N, 0, zidx + s0}, r2, z2, st) != cudaSuccess)
                 return tc_err(err, "eval: split failed");
             // M[s][(a, b)] = sum_c core[(a, b)][c] Z2[c][z_s]
-            rc = dt_gemm(c.core, z2, r0 * r1, ns, 1, DtOut{Mt, r0 * r1, 0, DT_PAIR}, opt, fl.d, st, err);
+            rc = dt_gemm(c.core, z2, r0 * r1, nm, 1, DtOut{Mt, r0 * r1, 0, DT_PAIR}, opt, fl.d, st, err);
             if (rc != LS_OK) return rc;
-            if (dt_split(SrcPair{Mt, r1, 1, r0 * r1}, r1, m, st) != cudaSuccess)
-                return tc_err(err, "eval: split failed");
-            // T_s[y][a] = sum_b M_s[a][b] Z1^T[y][b]   (D[a][y], a on the lanes)
-            rc = dt_gemm(m, c.z1t, r0, N, ns, DtOut{Tt, r0, N * r0, DT_PAIR}, opt, fl.d, st, err);
-            if (rc != LS_OK) return rc;
-            if (dt_split(SrcPair{Tt, r0, 1, N * r0}, r0, t, st) != cudaSuccess)
-                return tc_err(err, "eval: split failed");
         }
-        {
-            Scope sc("eval.slab", st);
-            // S_s[x][y] = sum_a T_s[y][a] Z0^T[x][a]   (D[y][x], y on the lanes: rows of S contiguous)
-            void* o = static_cast<char*>(out) + (size_t)s0 * N * N * esz;
-            rc = dt_gemm(t, c.z0t, N, N, ns, DtOut{o, N, N * N, out_f32 ? DT_F32 : DT_F64}, opt, fl.d, st, err);
-            if (rc != LS_OK) return rc;
+        for (int s1 = 0; s1 < nm; s1 += tchunk) {
+            const int ns = std::min(tchunk, nm - s1);
+            DtOp m = ms, t = ts;
+            m.batch = ns;
+            t.batch = ns;
+            {
+                Scope sc("eval.mt", st);
+                if (dt_split(SrcPair{Mt + (int64_t)s1 * r0 * r1, r1, 1, r0 * r1}, r1, m, st) != cudaSuccess)
+                    return tc_err(err, "eval: split failed");
+                // T_s[y][a] = sum_b M_s[a][b] Z1^T[y][b]   (D[a][y], a on the lanes)
+                rc = dt_gemm(m, c.z1t, r0, N, ns, DtOut{Tt, r0, N * r0, DT_PAIR}, opt, fl.d, st, err);
+                if (rc != LS_OK) return rc;
+                if (dt_split(SrcPair{Tt, r0, 1, N * r0}, r0, t, st) != cudaSuccess)
+                    return tc_err(err, "eval: split failed");
+            }
+            {
+                Scope sc("eval.slab", st);
+                // S_s[x][y] = sum_a T_s[y][a] Z0^T[x][a]   (D[y][x], y on the lanes: rows of S contiguous)
+                void* o = static_cast<char*>(out) + (size_t)(s0 + s1) * N * N * esz;
+                rc = dt_gemm(t, c.z0t, N, N, ns, DtOut{o, N, N * N, out_f32 ? DT_F32 : DT_F64}, opt, fl.d, st, err);
+                if (rc != LS_OK) return rc;
+            }
         }
     }
     return fl.check(err);
@@ -948,7 +990,7 @@ int dt_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t K
                const DtOpts& opt, cudaStream_t st, std::string* err) {
     if (M <= 0 || N <= 0) return LS_OK;
     const int64_t kp = pad32(std::max<int64_t>(K, 1));
-    if (kp > DT_MAXK && out_f32) return tc_err(err, "gemm_nt_mixed: K above 2048 needs FP64 output", LS_ERR_ARG);
+    if (kp > DT_MAXK4 && out_f32) return tc_err(err, "gemm_nt_mixed: K above 4096 needs FP64 output", LS_ERR_ARG);
     Arena ar(st);
     Flag fl(ar, st);
     DtOp a = dt_alloc(ar, M, kp, 1), b = dt_alloc(ar, N, kp, 1);
@@ -957,8 +999,8 @@ int dt_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t K
         dt_split(SrcF64{B, K, 1, 0, nullptr}, K, b, st) != cudaSuccess)
         return tc_err(err, "gemm_nt_mixed: split failed");
     // D[m][n] row-major = the kernel's D with n on the lanes: swap the operands; K in
-    // chunks of 2048 (each exact in its leading levels), added in FP64
-    const int nkb = (int)(kp / DT_BK), ckb = DT_MAXK / DT_BK;
+    // chunks of 4096 (each exact in its leading levels), added in FP64
+    const int nkb = (int)(kp / DT_BK), ckb = DT_MAXK4 / DT_BK;
     for (int k0 = 0; k0 < nkb; k0 += ckb) {
         DtOut o{D, N, 0, out_f32 ? DT_F32 : DT_F64};
         o.accumulate = k0 > 0;
@@ -993,50 +1035,66 @@ int dt_core(const double* P0, const double* P1, const double* P2, const int32_t*
     Arena ar(st);
     int* d_kb = ar.get<int>((C0 + 1) + tpad);
     int32_t* d_tmap = d_kb + (C0 + 1);
-    DtOp a = dt_alloc(ar, r2, tpad, 1), b = dt_alloc(ar, r1, tpad, 1);
-    if (!d_kb || !a.ok() || !b.ok()) return tc_err(err, "core: out of memory", LS_ERR_OOM);
+    // Output columns (j, k) in ranges of jc values of j, groups in chunks of gc (each
+    // one exact K range of step 2, up to 4096): W (pairs) and its split form take
+    // 16 bytes a (group, j, k), within about a third of the free memory (1 to 32 GB).
+    const int64_t budget = scratch_budget(16 * std::min<int64_t>(C0, DT_MAXK4) * nn, 3, (int64_t)1 << 30, (int64_t)32 << 30);
+    int64_t gc = std::min<int64_t>(C0, DT_MAXK4);
+    if (16 * gc * r2 > budget) gc = std::max<int64_t>(DT_BK, budget / (16 * r2) / DT_BK * DT_BK);
+    const int64_t jc = std::max<int64_t>(1, std::min<int64_t>(r1, budget / (16 * gc * r2)));
+    DtOp a = dt_alloc(ar, r2, tpad, 1), b = dt_alloc(ar, jc, tpad, 1);
+    float2* W = ar.get<float2>(gc * jc * r2);
+    DtOp ws = dt_alloc(ar, jc * r2, pad32(gc), 1), p0s = dt_alloc(ar, r0, pad32(gc), 1);
+    if (!d_kb || !a.ok() || !b.ok() || !W || !ws.ok() || !p0s.ok()) return tc_err(err, "core: out of memory", LS_ERR_OOM);
     {
         Scope sc("core.operands", st);
         if (upload_pinned(d_kb, up.data(), up.size() * sizeof(int32_t), st) != cudaSuccess)
             return tc_err(err, "core: upload failed");
         count_h2d((int64_t)(up.size() * sizeof(int32_t)));
-        // step 1 operands over the padded term list: A[k][t] = P2[k][c2(t)], B[j][t] = xin[t] P1[j][c1(t)]
-        if (dt_split(SrcGather{P2, (int64_t)C[2], d_tmap, tcol, 2, nullptr}, tpad, a, st) != cudaSuccess ||
-            dt_split(SrcGather{P1, (int64_t)C[1], d_tmap, tcol, 1, xin}, tpad, b, st) != cudaSuccess)
+        // step 1's A operand over the padded term list: A[k][t] = P2[k][c2(t)]
+        if (dt_split(SrcGather{P2, (int64_t)C[2], d_tmap, tcol, 2, nullptr}, tpad, a, st) != cudaSuccess)
             return tc_err(err, "core: split failed");
     }
-    // groups in chunks: W (pairs) and its split form stay within about 4 GB, and each chunk
-    // is one exact K range of step 2
-    const int64_t gc = std::max<int64_t>(1, std::min<int64_t>({C0, (int64_t)DT_MAXK, ((int64_t)4 << 30) / (16 * nn)}));
-    float2* W = ar.get<float2>(gc * nn);
-    DtOp ws = dt_alloc(ar, nn, pad32(gc), 1), p0s = dt_alloc(ar, r0, pad32(gc), 1);
-    if (!W || !ws.ok() || !p0s.ok()) return tc_err(err, "core: out of memory", LS_ERR_OOM);
     const DtOpts opt;
-    for (int64_t g0 = 0; g0 < C0; g0 += gc) {
-        const int64_t ng = std::min(gc, C0 - g0);
-        int rc;
+    for (int64_t j0 = 0; j0 < r1; j0 += jc) {
+        const int64_t nj = std::min(jc, r1 - j0);
+        DtOp bj = b;
+        bj.rows = nj;
         {
-            Scope sc("core.step1", st);
-            // step 1: W[g][j][k] = sum_{t in group g} xin[t] P1[j][c1(t)] P2[k][c2(t)]  (k on the lanes)
-            DtK k1;
-            k1.kb_lo = d_kb + g0;
-            rc = dt_gemm(a, b, r2, r1, ng, DtOut{W, r2, nn, DT_PAIR}, opt, flag, st, err, k1);
-            if (rc != LS_OK) return rc;
-        }
-        DtOp w = ws, p = p0s;
-        {
-            Scope sc("core.wsplit", st);
-            if (dt_split_tr(W, nn, ng, w, st) != cudaSuccess ||
-                dt_split(SrcF64{P0 + g0, C0, 1, 0, nullptr}, ng, p, st) != cudaSuccess)
+            Scope sc("core.operands", st);
+            // step 1's B operand: B[j][t] = xin[t] P1[j][c1(t)], rows j0 .. j0 + nj
+            if (dt_split(SrcGather{P1 + j0 * C[1], (int64_t)C[1], d_tmap, tcol, 1, xin}, tpad, bj, st) != cudaSuccess)
                 return tc_err(err, "core: split failed");
         }
-        {
-            Scope sc("core.step2", st);
-            // step 2: B[i][(j, k)] (+)= sum_g W[g][(j, k)] P0[i][g]  ((j, k) on the lanes)
-            DtOut o{Bc, nn, 0, DT_F64};
-            o.accumulate = g0 > 0;
-            rc = dt_gemm(w, p, nn, r0, 1, o, opt, flag, st, err);
-            if (rc != LS_OK) return rc;
+        for (int64_t g0 = 0; g0 < C0; g0 += gc) {
+            const int64_t ng = std::min(gc, C0 - g0);
+            int rc;
+            {
+                Scope sc("core.step1", st);
+                // step 1: W[g][j][k] = sum_{t in group g} xin[t] P1[j][c1(t)] P2[k][c2(t)]  (k on the lanes)
+                DtK k1;
+                k1.kb_lo = d_kb + g0;
+                rc = dt_gemm(a, bj, r2, nj, ng, DtOut{W, r2, nj * r2, DT_PAIR}, opt, flag, st, err, k1);
+                if (rc != LS_OK) return rc;
+            }
+            DtOp w = ws, p = p0s;
+            w.rows = nj * r2;
+            {
+                Scope sc("core.wsplit", st);
+                if (dt_split_tr(W, nj * r2, ng, w, st) != cudaSuccess ||
+                    dt_split(SrcF64{P0 + g0, C0, 1, 0, nullptr}, ng, p, st) != cudaSuccess)
+                    return tc_err(err, "core: split failed");
+            }
+            {
+                Scope sc("core.step2", st);
+                // step 2: B[i][(j, k)] (+)= sum_g W[g][(j, k)] P0[i][g]  ((j, k) on the lanes)
+                DtOut o{Bc + j0 * r2, nn, 0, DT_F64};
+                o.accumulate = g0 > 0;
+                DtK k2;
+                k2.kb_end = (int)(pad32(ng) / DT_BK);
+                rc = dt_gemm(w, p, nj * r2, r0, 1, o, opt, flag, st, err, k2);
+                if (rc != LS_OK) return rc;
+            }
         }
     }
     return LS_OK;

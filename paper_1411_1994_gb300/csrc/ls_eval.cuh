@@ -42,13 +42,13 @@ void dt_eval_free(DtEvalCache* c);
 // S_s[x][y] = sum_{a,b,c} B[a][b][c] Z0[a][x] Z1[b][y] Z2[c][zidx[s]] for the
 // nslab slabs (zidx: device int32), into out (nslab x N x N, FP32 if out_f32
 // else FP64). Builds *cache on first use. Synchronises to read the kernels'
-// status flag. Ranks up to 2048.
+// status flag. Ranks up to 4096.
 int dt_eval(DtEvalCache** cache, const double* const Z[3], const int32_t* r, const double* B, int64_t N,
             const int32_t* zidx, int nslab, void* out, int out_f32, const DtOpts& opt, cudaStream_t st,
             std::string* err);
 
 // D = A B^T (A: M x K, B: N x K, D: M x N row-major; device memory) by the same
-// product, synchronised, with the status checked. K above 2048 runs in exact chunks
+// product, synchronised, with the status checked. K above 4096 runs in exact chunks
 // added in FP64 (FP64 output only).
 int dt_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t K, void* D, int out_f32,
                const DtOpts& opt, cudaStream_t st, std::string* err);

@@ -157,146 +157,6 @@ __global__ void __launch_bounds__(256) k_gemm_f64(int M, int N, int K, AOp A, BO
     }
 }
 
-// ---------------------------------------------------------------------------
-// grouped GEMM: up to kMaxGroup independent products (the three modes) in one
-// launch, each optionally split along K. A split writes its partial tile to
-// the workspace; the CTA that completes a tile (counted by an atomic per tile)
-// sums the partials in split order, so the result does not depend on timing,
-// and resets the counter for the next launch. A symmetric job (C = X X^T)
-// computes the tiles on and above the diagonal and stores both halves.
-// ---------------------------------------------------------------------------
-constexpr int kMaxGroup = 3;
-constexpr int kTileElems = GBM * GBN;
-
-template <class AOp, class BOp, class COp>
-struct GJob {
-    AOp A; BOp B; COp C;
-    int M, N, K;
-    int sym;        // 1: C is symmetric (M == N, A(m, k) == B(k, m))
-    int S;          // splits along K
-    int tiles_n;    // tiles along N
-    int ntile;      // tiles computed
-    int b0;         // first block of the job
-    int ctr0;       // first tile counter
-    int64_t ws0;    // first partial (doubles)
-};
-template <class AOp, class BOp, class COp>
-struct GGroup {
-    GJob<AOp, BOp, COp> j[kMaxGroup];
-    int n;
-    double* ws;
-    unsigned int* ctr;
-};
-
-template <class AOp, class BOp, class COp>
-__global__ void __launch_bounds__(256) k_gemm_group(const __grid_constant__ GGroup<AOp, BOp, COp> G) {
-    __shared__ double As[GBK][GBM];
-    __shared__ double Bs[GBK][GBN];
-    __shared__ unsigned int s_last;
-    int ji = 0;
-    while (ji + 1 < G.n && (int)blockIdx.x >= G.j[ji + 1].b0) ++ji;
-    const GJob<AOp, BOp, COp>& J = G.j[ji];
-    const int local = (int)blockIdx.x - J.b0;
-    const int split = local % J.S, tile = local / J.S;
-    int tm, tn;
-    if (J.sym) {   // upper-triangle tiles, row by row
-        int t = tile, len = J.tiles_n;
-        tm = 0;
-        while (t >= len) { t -= len; ++tm; --len; }
-        tn = tm + t;
-    } else {
-        tm = tile / J.tiles_n;
-        tn = tile - tm * J.tiles_n;
-    }
-    const int m0 = tm * GBM, n0 = tn * GBN;
-    const int kper = ((J.K + J.S - 1) / J.S + GBK - 1) / GBK * GBK;
-    const int kb = min(J.K, split * kper), ke = min(J.K, kb + kper);
-    double acc[4][4];
-    gemm_tile(J.A, J.B, 0, J.M, J.N, kb, ke, m0, n0, As, Bs, acc);
-    if (J.S > 1) {
-        double* w = G.ws + J.ws0 + ((int64_t)tile * J.S + split) * kTileElems;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) __stcg(w + (i * 4 + j) * 256 + threadIdx.x, acc[i][j]);
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned int* c = G.ctr + J.ctr0 + tile;
-            const unsigned int old = atomicAdd(c, 1u);
-            s_last = (old == (unsigned int)J.S - 1) ? 1u : 0u;
-            if (s_last) *c = 0u;
-        }
-        __syncthreads();
-        if (!s_last) return;
-        __threadfence();
-        const double* w0 = G.ws + J.ws0 + (int64_t)tile * J.S * kTileElems;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                double v = 0.0;
-                for (int s = 0; s < J.S; ++s) v += __ldcg(w0 + (int64_t)s * kTileElems + (i * 4 + j) * 256 + threadIdx.x);
-                acc[i][j] = v;
-            }
-    }
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int m = m0 + ty + 16 * i;
-        if (m >= J.M) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int n = n0 + tx + 16 * j;
-            if (n >= J.N) continue;
-            J.C(0, m, n, acc[i][j]);
-            if (J.sym && tm != tn) J.C(0, n, m, acc[i][j]);
-        }
-    }
-}
-
-// Fills in the launch layout of n jobs (A, B, C, M, N, K, sym set by the
-// caller) and launches them; splits along K until about two CTAs per SM are
-// busy, within the workspace.
-template <class AOp, class BOp, class COp>
-cudaError_t gemm_group(GGroup<AOp, BOp, COp>& G, const GemmWs& W, cudaStream_t st) {
-    int64_t tiles = 0;
-    int kmin = 1 << 30;
-    for (int i = 0; i < G.n; ++i) {
-        auto& J = G.j[i];
-        const int tm = (J.M + GBM - 1) / GBM, tn = (J.N + GBN - 1) / GBN;
-        J.tiles_n = tn;
-        J.ntile = (J.M <= 0 || J.N <= 0) ? 0 : (J.sym ? tn * (tn + 1) / 2 : tm * tn);
-        tiles += J.ntile;
-        if (J.ntile > 0) kmin = std::min(kmin, J.K);
-    }
-    if (tiles == 0) return cudaSuccess;
-    const int64_t target = 2 * (int64_t)W.num_sms;
-    int S = 1;
-    if (tiles < target && W.ws && W.ctr) {
-        S = (int)std::min<int64_t>(16, target / tiles);
-        S = std::min(S, std::max(1, kmin / GBK));   // down to one k-step per split
-        while (S > 1 && (tiles * S * kTileElems > W.ws_cap || tiles > W.ctr_cap)) --S;
-    }
-    int b = 0, c = 0;
-    int64_t w = 0;
-    for (int i = 0; i < G.n; ++i) {
-        auto& J = G.j[i];
-        J.S = S;
-        J.b0 = b;
-        J.ctr0 = c;
-        J.ws0 = w;
-        b += J.ntile * S;
-        c += J.ntile;
-        w += (int64_t)J.ntile * S * kTileElems;
-    }
-    G.ws = W.ws;
-    G.ctr = W.ctr;
-    k_gemm_group<AOp, BOp, COp><<<b, 256, 0, st>>>(G);
-    count_kernels(1);
-    return cudaGetLastError();
-}
-
 template <class AOp, class BOp, class COp>
 cudaError_t gemm_f64(int M, int N, int K, int batch, AOp A, BOp B, COp Cst, cudaStream_t st) {
     if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
@@ -1178,18 +1038,6 @@ cudaError_t launch_chol_inv_multi(const CholJob* jobs, int njobs, int num_sms, c
     }
     return cudaSuccess;
 }
-
-// grouped products of the reduction (one launch for up to three modes) ------
-cudaError_t launch_pchol_gram_n(int n, const double* const L[], const int64_t kmax[], const int k[],
-                                const int64_t C[], double* const H[], const GemmWs& W, cudaStream_t st) {
-    GGroup<ColK, KRowN, StoreRow> g{};
-    g.n = n;
-    for (int i = 0; i < n; ++i)
-        g.j[i] = {ColK{L[i], kmax[i]}, KRowN{L[i], kmax[i]}, StoreRow{H[i], k[i], 0}, k[i], k[i], (int)C[i], 1};
-    return gemm_group(g, W, st);
-}
-
-
 
 cudaError_t launch_fold_norms(const double* xi, const int32_t* tcol, int64_t T, const double* n0,
                               const double* n1, const double* n2, double* xin, cudaStream_t st) {

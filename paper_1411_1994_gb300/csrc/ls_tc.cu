@@ -533,6 +533,30 @@ int x64_pchol_vectors(int n, const double* const L[], const int64_t kmax[], cons
     return gemm_x64(sp.data(), n, flag, st, err);
 }
 
+// H_l = L_l^T L_l over the first k_l columns of L_l (C_l rows of stride kmax_l): the
+// compressed Gram matrix after the pivoted Cholesky, as X X^T with X = L^T read transposed.
+int x64_pchol_gram(int n, const double* const L[], const int64_t kmax[], const int k[], const int64_t C[],
+                   double* const H[], int* flag, cudaStream_t st, std::string* err) {
+    for (int g0 = 0; g0 < n; g0 += kX64MaxJobs) {
+        const int ng = std::min(kX64MaxJobs, n - g0);
+        Arena ar(st);
+        SplitBatch sb(st);
+        std::vector<X64Op> ls(ng);
+        std::vector<X64Spec> sp(ng);
+        for (int i = 0; i < ng; ++i) {
+            const int l = g0 + i;
+            ls[i] = x64_alloc(ar, k[l], pad64(C[l]));
+            if (!ls[i].ok()) return tc_err(err, "x64_pchol_gram: out of memory", LS_ERR_OOM);
+            sb.add(L[l], k[l], C[l], 1, kmax[l], nullptr, ls[i]);
+            sp[i] = X64Spec{&ls[i], &ls[i], k[l], k[l], TcOut{H[l], k[l], 0, OUT_F64, 0}, 0};
+        }
+        if (sb.flush() != cudaSuccess) return tc_err(err, "x64_pchol_gram: split failed");
+        int rc = gemm_x64(sp.data(), ng, flag, st, err);
+        if (rc != LS_OK) return rc;
+    }
+    return LS_OK;
+}
+
 // out_l = op(A_l) op(B_l) (+ add_l) for k_l x k_l row-major matrices, op = identity or
 // transpose (ta, tb): the small dense products of the eigen-solver and of CholeskyQR.
 // The product is taken as X Y^T with X = op(A) and Y = op(B)^T in K-major rows

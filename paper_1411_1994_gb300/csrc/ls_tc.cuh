@@ -34,6 +34,9 @@ int x64_basis(int n, const double* const V[], const int64_t ldv[], const int32_t
 int x64_pchol_vectors(int n, const double* const L[], const int64_t kmax[], const int k[], const int64_t C[],
                       const double* const U[], const double* const H[], double* const Vg[], int* flag,
                       cudaStream_t st, std::string* err);
+// H_l = L_l^T L_l over the first k_l columns of L_l (C_l rows of stride kmax_l; H_l: k_l x k_l).
+int x64_pchol_gram(int n, const double* const L[], const int64_t kmax[], const int k[], const int64_t C[],
+                   double* const H[], int* flag, cudaStream_t st, std::string* err);
 // out_l = op(A_l) op(B_l) (+ add_l) for k_l x k_l row-major matrices (ta/tb: 1 = transpose;
 // add may be null).
 int x64_small(int n, const double* const A[], const int ta[], const double* const B[], const int tb[],

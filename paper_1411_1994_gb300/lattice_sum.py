@@ -176,7 +176,7 @@ def gemm_nt(A, B):
 
 
 def gemm_nt_mixed(A, B, dtype=None, tile_n: int = 0):
-    """D = A B^T for float64 CUDA tensors (A: M x K, B: N x K, K <= 2048) in the mixed slab
+    """D = A B^T for float64 CUDA tensors (A: M x K, B: N x K; K <= 4096 for float32 output) in the mixed slab
     evaluation's tensor-core arithmetic (lattice_sum_gemm_nt_mixed): two exact digits and two
     11-bit tails (FP16), the two leading levels accumulated exactly; `tile_n` 32/64/128 (0 = by size);
     D in `dtype` (torch.float32 or torch.float64, default float32)."""

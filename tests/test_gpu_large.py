@@ -1,4 +1,7 @@
-"""Full-size parity on the step-shaped lattice (a 48x48x24 and a 24^3 block,
+"""Full-size parity on the two large configurations, run as bench.py runs them
+(create, add_defects, rhosvd_reduce, then slabs).
+
+The step-shaped lattice (a 48x48x24 and a 24^3 block,
 3% vacancies, N = 4096, R = 28, eps = 1e-6): the configuration of the
 precision comparison, run as bench.py runs it (create, add_defects,
 rhosvd_reduce, then slabs), for both arithmetic paths.
@@ -13,6 +16,11 @@ values) must lie within eps of those values in relative L2 (the Frobenius
 error of the Tucker result is bounded by Thm A.1(d); random rows estimate
 the relative Frobenius error), and the reported bound must dominate the
 observed error on the samples.
+
+The 256^3 lattice with 1000 3x3x3 defect clusters (N = 16384, R = 32,
+eps = 1e-6; C ~ 8000 columns and ranks ~ 2200 per mode, a core of ~1.1e10
+entries) runs the mixed path only and is checked the same way on 4 of its
+slabs (8 rows each, 524288 values).
 """
 import math
 
@@ -76,5 +84,42 @@ def test_step_lattice_sampled_rows_within_eps(step_lattice, precision):
     err = math.sqrt(num / den)
     assert err <= wl.eps, err
     # the absolute Thm A.1(d) bound dominates the absolute error on the samples
+    assert math.sqrt(num) <= info["bound_abs"], (math.sqrt(num), info["bound_abs"])
+    ls.close()
+
+
+@pytest.fixture(scope="module")
+def cluster_lattice():
+    wl = W.config5()
+    s, _ = O.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, O.default_r_max(wl))
+    t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s)
+    g = O.generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w)
+    cols, tcol, xi = O.canonical_terms(wl.N, wl.box_lo, wl.box_hi, g, wl.blocks, wl.defects)
+    ncols, _, xin = O.normalise_terms(cols, tcol, xi)
+    return wl, s, ncols, tcol, xin
+
+
+def test_cluster_lattice_sampled_rows_within_eps(cluster_lattice):
+    wl, s, ncols, tcol, xin = cluster_lattice
+    ls = L.LatticeSum.from_workload(wl, s, L.LS_MIXED)
+    ls.add_defects(wl.defects)
+    info = ls.rhosvd_reduce(wl.eps)
+    assert info["T"] == tcol.shape[0]
+    assert all(c == n.shape[0] for c, n in zip(info["C"], ncols))
+    assert all(1 <= r <= c for r, c in zip(info["r"], info["C"]))
+    rng = np.random.default_rng(16384)
+    zs = [int(z) for z in wl.slabs[:4]]
+    slabs = ls.eval_slab_torch(zs)
+    num = den = 0.0
+    for k, z in enumerate(zs):
+        xs = [int(x) for x in rng.choice(wl.N, size=8, replace=False)]
+        rows = slabs[k, xs].cpu().numpy()
+        for i, x in enumerate(xs):
+            ref = canonical_row(ncols, tcol, xin, x, z)
+            num += float(np.sum((rows[i] - ref) ** 2))
+            den += float(np.sum(ref ** 2))
+    del slabs
+    err = math.sqrt(num / den)
+    assert err <= wl.eps, err
     assert math.sqrt(num) <= info["bound_abs"], (math.sqrt(num), info["bound_abs"])
     ls.close()
