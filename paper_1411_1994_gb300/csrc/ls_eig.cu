@@ -126,7 +126,7 @@ int smem_optin() {
 // Block form of the same iteration: indices in blocks of BJ = 8, a round-robin
 // over the m blocks pairs them into m/2 pair-blocks of 16 indices per round
 // (m - 1 rounds a sweep). Each pair-block's 16 x 16 subproblem receives one
-// inner cyclic sweep (a warp, in place in E; the diagonal D in FP64), whose
+// inner cyclic sweep (a warp, in registers; the diagonal as hi/lo pairs), whose
 // rotations accumulate into Q = I + F_Q; then every off-diagonal tile of
 // pair-blocks is rotated as E_AB <- Q_A^T E_AB Q_B (a warp per tile, dense
 // FP32), and F <- F + F_Q + F F_Q on the F rows. In the first round of a
@@ -153,7 +153,7 @@ __device__ __forceinline__ int bj_index(int I, int J, int u) { return u < BJ ? I
 // shared-memory layout: offsets in bytes
 struct BjLayout {
     int K, ldE, nb;
-    size_t ctl, D, E, Q, Tw, aw, pb, tiles, qrem, F;   // E-CTA: ctl D E Q Tw aw pb tiles; F-CTAs: ctl qrem F
+    size_t ctl, D, E, Q, pb, act, tiles, qrem, F;   // CTA 0: ctl D E Q pb act tiles; others: ctl qrem F
     size_t e_bytes, f_bytes;
     __host__ __device__ BjLayout(int k, int rows_per) {
         int m = (k + BJ - 1) / BJ;
@@ -165,45 +165,181 @@ struct BjLayout {
         D = 16;
         E = D + 8 * (size_t)K;
         Q = E + 4 * (size_t)K * ldE;
-        Tw = Q + 4 * (size_t)nb * BJ2SQ;
-        aw = Tw + 4 * (size_t)nb * SPSQ;
-        pb = aw + 16 * (size_t)nb * BJ2;
-        tiles = pb + 4 * (size_t)nb;
+        pb = Q + 4 * (size_t)nb * BJ2SQ;
+        act = pb + 4 * (size_t)nb;
+        tiles = act + 4 * (size_t)nb;
         e_bytes = tiles + 4 * (size_t)nb * nb;
         qrem = 16;
-        F = qrem + 4 * (size_t)2 * nb * BJ2SQ;
+        F = qrem + 4 * (size_t)nb * SPSQ;
         f_bytes = F + 4 * (size_t)rows_per * K;
     }
 };
 
-struct __align__(16) InRot {
-    float c, s, cm1;
-    int uv;   // u | v << 8 (positions 0..15 in the pair-block), bit 16: active
-};
+// ---------------------------------------------------------------------------
+// The inner sweep of one pair-block by one warp, in registers (both forms run it).
+// Lanes 0..15 hold the columns of the 16 x 16 subproblem E_s (zero diagonal) and the
+// diagonal entry d of position i = lane; lanes 16..31 hold the columns of F_Q
+// (Q = I + F_Q, zero at the start), position i = lane - 16. Inner round `it`
+// rotates 8 disjoint position pairs (u, v), u < v: in the full form (the first round
+// of a sweep) the round-robin pairs of all 16 positions, otherwise u = l and
+// v = 8 + ((l + it) mod 8). Lane u takes the rotation from (d_u, d_v, e_uv) when
+// both indices are below k and the pair qualifies; then E_s <- J^T E_s J (rows in
+// each lane, then columns with the partner lane's column), F_Q <- F_Q J with c - 1
+// kept apart, d_u -= t e_uv, d_v += t e_uv, and the pair's 2 x 2 block of E_s is set
+// to zero. Returns the rotations taken by this lane.
+//
+// The rows of a column sit in registers in an order that turns with the inner
+// rounds, so that every round pairs the same registers: (l, 8 + l) in the cross
+// form, where register 8 + j holds row 8 + ((j + it) mod 8); (15, 0) and
+// (l, 15 - l) in the full form, where register s < 15 holds row (s + it) mod 15.
+// The round loop then needs no unrolling and the code stays small.
+// ---------------------------------------------------------------------------
+template <bool FULL>
+__device__ __forceinline__ int in_partner(int it, int i) {
+    if (FULL) return i == BJ2 - 1 ? it : (i == it ? BJ2 - 1 : (2 * it - i + BJ2 - 1) % (BJ2 - 1));
+    return i < BJ ? BJ + ((i + it) & (BJ - 1)) : ((i - BJ - it) & (BJ - 1));
+}
+// register of row `row` in inner round it
+template <bool FULL>
+__device__ __forceinline__ int in_reg(int it, int row) {
+    if (FULL) return row == BJ2 - 1 ? row : (row - it + BJ2 - 1) % (BJ2 - 1);
+    return row < BJ ? row : BJ + ((row - BJ - it) & (BJ - 1));
+}
+// row held by register r in inner round it
+template <bool FULL>
+__device__ __forceinline__ int in_row(int it, int r) {
+    if (FULL) return r == BJ2 - 1 ? r : (r + it) % (BJ2 - 1);
+    return r < BJ ? r : BJ + ((r - BJ + it) & (BJ - 1));
+}
+__device__ __forceinline__ float pick16(const float (&v)[BJ2], int p) {
+    float x = v[0];
+#pragma unroll
+    for (int r = 1; r < BJ2; ++r) x = p == r ? v[r] : x;
+    return x;
+}
+
+template <bool FULL>
+__device__ __forceinline__ unsigned int inner_sweep(float (&x)[BJ2], DF& d, int I, int Jb, int k, const Crit& qualifies) {
+    const int lane = threadIdx.x & 31, pos = lane & (BJ2 - 1);
+    const bool is_e = lane < BJ2;
+    const bool in_k = bj_index(I, Jb, pos) < k;
+    constexpr int NIT = FULL ? BJ2 - 1 : BJ;
+    unsigned int nrot = 0;
+#pragma unroll 1
+    for (int it = 0; it < NIT; ++it) {
+        const int pt = in_partner<FULL>(it, pos);
+        const bool owner = pos < pt;
+        const int rpos = in_reg<FULL>(it, pos), rpt = in_reg<FULL>(it, pt);
+        // the pair's rotation, taken by its lane u
+        const float dph = __shfl_sync(0xffffffffu, d.hi, pt), dpl = __shfl_sync(0xffffffffu, d.lo, pt);
+        const int pk = __shfl_sync(0xffffffffu, (int)in_k, pt);
+        const float epq = pick16(x, rpt);
+        float c = 1.f, sn = 0.f, cm1 = 0.f, te = 0.f;
+        int act = 0;
+        if (is_e && owner && in_k && pk) {
+            const DF dq{dph, dpl};
+            if (qualifies(d, dq, epq)) {
+                const RotCS g = jacobi_rot(df_diff(dq, d), epq);
+                c = g.c;
+                sn = g.s;
+                cm1 = g.cm1;
+                te = g.t * epq;
+                act = 1;
+                ++nrot;
+            }
+        }
+        // rows of E_s: the fixed register pairs, each with its pair's rotation from lane u
+        if (is_e) {
+#pragma unroll
+            for (int l = 0; l < BJ; ++l) {
+                const int p = FULL ? (l == 0 ? BJ2 - 1 : l) : l;
+                const int q = FULL ? (l == 0 ? 0 : BJ2 - 1 - l) : BJ + l;
+                const int rowp = in_row<FULL>(it, p), rowq = in_row<FULL>(it, q);
+                const int u = rowp < rowq ? rowp : rowq;
+                const float cl = __shfl_sync(0x0000ffffu, c, u);
+                const float s0 = __shfl_sync(0x0000ffffu, sn, u);
+                const float sl = rowp < rowq ? s0 : -s0;
+                const float xp = x[p], xq = x[q];
+                x[p] = cl * xp - sl * xq;
+                x[q] = sl * xp + cl * xq;
+            }
+        }
+        // columns: this lane's pair rotation and the partner lane's column
+        const int own = owner ? pos : pt;
+        c = __shfl_sync(0xffffffffu, c, own);
+        sn = __shfl_sync(0xffffffffu, sn, own);
+        cm1 = __shfl_sync(0xffffffffu, cm1, own);
+        te = __shfl_sync(0xffffffffu, te, own);
+        act = __shfl_sync(0xffffffffu, act, own);
+        float o[BJ2];
+        const int plane = (lane & BJ2) | pt;
+#pragma unroll
+        for (int r = 0; r < BJ2; ++r) o[r] = __shfl_sync(0xffffffffu, x[r], plane);
+        if (is_e) {
+#pragma unroll
+            for (int r = 0; r < BJ2; ++r) x[r] = owner ? c * x[r] - sn * o[r] : sn * o[r] + c * x[r];
+            if (act) {
+#pragma unroll
+                for (int r = 0; r < BJ2; ++r)
+                    if (r == rpos || r == rpt) x[r] = 0.f;
+                d = df_add(d, owner ? -te : te);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < BJ2; ++r) {
+                float nx = owner ? x[r] + (x[r] * cm1 - o[r] * sn) : x[r] + (o[r] * sn + x[r] * cm1);
+                if (r == rpos) nx += cm1;
+                if (r == rpt) nx += owner ? -sn : sn;
+                x[r] = nx;
+            }
+        }
+        // turn the register order to the next round's
+        if (FULL) {
+            const float x0 = x[0];
+#pragma unroll
+            for (int r = 0; r < BJ2 - 2; ++r) x[r] = x[r + 1];
+            x[BJ2 - 2] = x0;
+        } else {
+            const float x8 = x[BJ];
+#pragma unroll
+            for (int r = BJ; r < BJ2 - 1; ++r) x[r] = x[r + 1];
+            x[BJ2 - 1] = x8;
+        }
+    }
+    return nrot;
+}
 
 __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
     cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    const int job = blockIdx.x / A.cs;
+    const int rank = (int)cl.block_rank(), cs = A.cs;
+    const int job = blockIdx.x / cs;
     const DfMode J = A.m[job];
     const int k = J.k;
     const BjLayout Ly(k, A.rows_per);
     const int K = Ly.K, ldE = Ly.ldE, nb = Ly.nb, m = 2 * nb;
     extern __shared__ __align__(16) unsigned char smem[];
-    int* ctl = reinterpret_cast<int*>(smem + Ly.ctl);
-    DF* D = reinterpret_cast<DF*>(smem + Ly.D);
-    float* E = reinterpret_cast<float*>(smem + Ly.E);
-    float* Q = reinterpret_cast<float*>(smem + Ly.Q);
-    float* Tw = reinterpret_cast<float*>(smem + Ly.Tw);
-    InRot* aw = reinterpret_cast<InRot*>(smem + Ly.aw);
-    int* pb = reinterpret_cast<int*>(smem + Ly.pb);          // this round's pair-blocks: I | J << 16
-    int* tiles = reinterpret_cast<int*>(smem + Ly.tiles);    // off-diagonal tiles a | b << 8, a < b
-    float* qrem = reinterpret_cast<float*>(smem + Ly.qrem);
-    float* F = reinterpret_cast<float*>(smem + Ly.F);
-    __shared__ unsigned int s_active;
-    __shared__ int s_act[64];   // pair-block rotated this round (its Q differs from I)
+    // The matrix state lives in CTA 0. The inner sweeps run on every CTA of the cluster,
+    // on CTA 0's state through the cluster's shared-memory window; the tiles run on CTA 0
+    // alone, on its own shared memory; the other CTAs hold rows of F and receive F_Q.
+    unsigned char* s0 = rank == 0 ? smem : cl.map_shared_rank(smem, 0);
+    int* ctl = reinterpret_cast<int*>(smem + Ly.ctl);       // this CTA's copy of the stop decision
+    DF* D = reinterpret_cast<DF*>(s0 + Ly.D);
+    float* E = reinterpret_cast<float*>(s0 + Ly.E);
+    float* Q = reinterpret_cast<float*>(s0 + Ly.Q);
+    int* pb = reinterpret_cast<int*>(s0 + Ly.pb);           // this round's pair-blocks: I | J << 16
+    int* act = reinterpret_cast<int*>(s0 + Ly.act);         // pair-block rotated this round
+    float* El = reinterpret_cast<float*>(smem + Ly.E);      // CTA 0's own view of the same
+    const float* Ql = reinterpret_cast<const float*>(smem + Ly.Q);
+    const int* pbl = reinterpret_cast<const int*>(smem + Ly.pb);
+    const int* actl = reinterpret_cast<const int*>(smem + Ly.act);
+    const int* tiles = reinterpret_cast<const int*>(smem + Ly.tiles);   // tiles a | b << 8, a < b
+    float* qrem = reinterpret_cast<float*>(smem + Ly.qrem); // CTAs >= 1: F_Q of the pair-blocks
+    float* F = reinterpret_cast<float*>(smem + Ly.F);       // CTAs >= 1: rows j0 .. j1 of F
+    __shared__ unsigned int s_active;                        // CTA 0: rotations of this sweep
+    unsigned int* active = rank == 0 ? &s_active : cl.map_shared_rank(&s_active, 0);
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    const int slot = warp * cs + rank, nslot = nw * cs;     // warps of the cluster, interleaved over CTAs
     const Crit qualifies{(float)J.abs_floor, (float)J.tau, (float)(J.tol * J.tol)};
     const int j0 = rank >= 1 ? min(K, (rank - 1) * A.rows_per) : 0;
     const int j1 = rank >= 1 ? min(K, j0 + A.rows_per) : 0;
@@ -217,9 +353,10 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
                 E[a * ldE + c] = (a < k && c < k && a != c) ? (float)J.H[(int64_t)a * k + c] : 0.f;
         if (tid == 0) {
             s_active = 0;
+            int* tl = const_cast<int*>(tiles);
             int n = 0;
             for (int a = 0; a < nb; ++a)
-                for (int b = a + 1; b < nb; ++b) tiles[n++] = a | (b << 8);
+                for (int b = a + 1; b < nb; ++b) tl[n++] = a | (b << 8);
         }
         base = J.st->sweeps;
     } else {
@@ -229,128 +366,87 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
 
     int sweep = 0;
     bool done = false;
-    int gr = 0;
     for (; sweep <= A.max_sweeps && !done; ++sweep) {
-        for (int t = 0; t < m - 1; ++t, ++gr) {
-            const int par = gr & 1;
-            if (rank == 0) {
-                int stop = 0;
-                if (t == 0) {
+        for (int t = 0; t < m - 1; ++t) {
+            if (t == 0) {
+                // sweep start: CTA 0 records the finished sweep's rotations and looks for a pair
+                // that qualifies; every CTA reads the decision after the barrier
+                if (rank == 0) {
                     int need = 0;
                     for (int a = warp; a < k && !need; a += nw)
                         for (int c = a + 1 + lane; c < k; c += 32)
                             if (qualifies(D[a], D[c], E[a * ldE + c])) { need = 1; break; }
                     need = __syncthreads_or(need);
                     if (tid == 0) {
+                        int stop = 0;
+                        if (!need) stop = 1;
+                        else if (sweep == A.max_sweeps) {
+                            stop = 1;
+                            atomicCAS(&J.st->flag, FLAG_OK, FLAG_NOCONVERGE);
+                        }
                         if (sweep > 0) J.st->sweep_active[(base + sweep - 1) & 63] = s_active;
                         s_active = 0;
-                    }
-                    if (!need) stop = 1;
-                    else if (sweep == A.max_sweeps) {
-                        stop = 1;
-                        if (tid == 0) atomicCAS(&J.st->flag, FLAG_OK, FLAG_NOCONVERGE);
-                    }
-                    __syncthreads();
-                }
-                if (!stop) {
-                    // the inner sweeps, a warp per pair-block (their indices are disjoint, so the
-                    // warps need no CTA barrier): per inner round lanes 0..7 compute the angles, then
-                    // the warp rotates the 2 x 2 blocks of E (56) and accumulates F_Q (128 items).
-                    // The first round of a sweep gives each pair-block a full inner sweep (every pair
-                    // within its two blocks); the other rounds only pair the two blocks' indices with
-                    // each other (8 inner rounds), as every block's own pairs were rotated this sweep
-                    const int n_inner = t == 0 ? BJ2 - 1 : BJ;
-                    for (int sub = warp; sub < nb; sub += nw) {
-                        int I, Jb;
-                        rr_pair_e(t, sub, m, I, Jb);
-                        float* fq = Tw + sub * SPSQ;
-                        InRot* ri = aw + sub * (BJ2 / 2);
-                        for (int e = lane; e < SPSQ; e += 32) fq[e] = 0.f;
-                        if (lane == 0) pb[sub] = I | (Jb << 16);
-                        __syncwarp();
-                        unsigned int nrot = 0;
-                        for (int it = 0; it < n_inner; ++it) {
-                            if (lane < BJ2 / 2) {
-                                int u, v;
-                                if (t == 0) rr_pair_e(it, lane, BJ2, u, v);
-                                else { u = lane; v = BJ + ((lane + it) & (BJ - 1)); }
-                                const int p = bj_index(I, Jb, u), q = bj_index(I, Jb, v);
-                                InRot r{1.f, 0.f, 0.f, u | (v << 8)};
-                                if (p < k && q < k) {
-                                    const float epq = E[p * ldE + q];
-                                    if (qualifies(D[p], D[q], epq)) {
-                                        const RotCS g = jacobi_rot(df_diff(D[q], D[p]), epq);
-                                        r = InRot{g.c, g.s, g.cm1, u | (v << 8) | (1 << 16)};
-                                        const float te = g.t * epq;
-                                        D[p] = df_add(D[p], -te);
-                                        D[q] = df_add(D[q], te);
-                                        E[p * ldE + q] = 0.f;
-                                        E[q * ldE + p] = 0.f;
-                                        ++nrot;
-                                    }
-                                }
-                                ri[lane] = r;
-                            }
-                            __syncwarp();
-                            // E <- J^T E J on the 2 x 2 blocks (i, i2), i != i2
-                            for (int e = lane; e < 64; e += 32) {
-                                const int i = e >> 3, i2 = e & 7;
-                                if (i == i2) continue;
-                                const InRot ra = ri[i], rb = ri[i2];
-                                if (!((ra.uv | rb.uv) & (1 << 16))) continue;
-                                const int pa = bj_index(I, Jb, ra.uv & 255), qa = bj_index(I, Jb, (ra.uv >> 8) & 255);
-                                const int pc = bj_index(I, Jb, rb.uv & 255), qc = bj_index(I, Jb, (rb.uv >> 8) & 255);
-                                const float x0 = E[pa * ldE + pc], x1 = E[pa * ldE + qc];
-                                const float x2 = E[qa * ldE + pc], x3 = E[qa * ldE + qc];
-                                const float ypp = ra.c * x0 - ra.s * x2, ypq = ra.c * x1 - ra.s * x3;
-                                const float yqp = ra.s * x0 + ra.c * x2, yqq = ra.s * x1 + ra.c * x3;
-                                E[pa * ldE + pc] = rb.c * ypp - rb.s * ypq;
-                                E[pa * ldE + qc] = rb.s * ypp + rb.c * ypq;
-                                E[qa * ldE + pc] = rb.c * yqp - rb.s * yqq;
-                                E[qa * ldE + qc] = rb.s * yqp + rb.c * yqq;
-                            }
-                            // F_Q <- F_Q J on local positions, c - 1 kept apart
-                            for (int e = lane; e < 8 * BJ2; e += 32) {
-                                const InRot r = ri[e >> 4];
-                                if (!(r.uv & (1 << 16))) continue;
-                                const int y = e & 15, u = r.uv & 255, v = (r.uv >> 8) & 255;
-                                const float fp = fq[y * SP + u], fv = fq[y * SP + v];
-                                float np = fp + (fp * r.cm1 - fv * r.s);
-                                float nv = fv + (fp * r.s + fv * r.cm1);
-                                if (y == u) { np += r.cm1; nv += r.s; }
-                                if (y == v) { np -= r.s; nv += r.cm1; }
-                                fq[y * SP + u] = np;
-                                fq[y * SP + v] = nv;
-                            }
-                            __syncwarp();
-                        }
-                        for (int o = 16; o; o >>= 1) nrot += __shfl_xor_sync(0xffffffffu, nrot, o);
-                        if (lane == 0) {
-                            s_act[sub] = nrot > 0;
-                            if (nrot) atomicAdd(&s_active, nrot);
-                        }
-                    }
-                    __syncthreads();
-                    // F_Q to the F rows' CTAs; Q = I + F_Q kept for the tiles
-                    for (int e = tid; e < nb * BJ2SQ; e += nthr) {
-                        const int sub = e >> 8, f0 = e & 255;
-                        const float f = Tw[sub * SPSQ + (f0 >> 4) * SP + (f0 & 15)];
-                        for (int c = 1; c < A.cs; ++c) cl.map_shared_rank(qrem, c)[par * nb * BJ2SQ + e] = f;
-                        Q[e] = f + (((f0 >> 4) == (f0 & 15)) ? 1.f : 0.f);
+                        for (int c = 0; c < cs; ++c) cl.map_shared_rank(ctl, c)[0] = stop;
                     }
                 }
-                if (tid == 0)
-                    for (int c = 0; c < A.cs; ++c) cl.map_shared_rank(ctl, c)[par] = stop;
+                cl.sync();
+                if (ctl[0]) { done = true; break; }
+            }
+            // the inner sweeps, a warp per pair-block over the cluster (their indices are
+            // disjoint), in registers: lanes 0..15 the columns of the subproblem and its
+            // diagonal, lanes 16..31 the columns of F_Q. The first round of a sweep gives each
+            // pair-block a full inner sweep (every pair within its two blocks); the other
+            // rounds only pair the two blocks' indices with each other (8 inner rounds), as
+            // every block's own pairs were rotated this sweep.
+            for (int sub = slot; sub < nb; sub += nslot) {
+                int I, Jb;
+                rr_pair_e(t, sub, m, I, Jb);
+                const int pos = lane & (BJ2 - 1), gi = bj_index(I, Jb, pos);
+                float x[BJ2];
+                DF d{0.f, 0.f};
+                if (lane < BJ2) {
+#pragma unroll
+                    for (int r = 0; r < BJ2; ++r) x[r] = E[bj_index(I, Jb, r) * ldE + gi];
+                    d = D[gi];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < BJ2; ++r) x[r] = 0.f;
+                }
+                unsigned int nrot = t == 0 ? inner_sweep<true>(x, d, I, Jb, k, qualifies)
+                                           : inner_sweep<false>(x, d, I, Jb, k, qualifies);
+                for (int o = 16; o; o >>= 1) nrot += __shfl_xor_sync(0xffffffffu, nrot, o);
+                if (lane < BJ2) {
+#pragma unroll
+                    for (int r = 0; r < BJ2; ++r) E[bj_index(I, Jb, r) * ldE + gi] = x[r];
+                    D[gi] = d;
+                } else {
+                    // F_Q to the F rows' CTAs, Q = I + F_Q to CTA 0
+                    for (int c = 1; c < cs; ++c) {
+                        float* qr = cl.map_shared_rank(qrem, c) + sub * SPSQ + pos;
+#pragma unroll
+                        for (int r = 0; r < BJ2; ++r) qr[r * SP] = x[r];
+                    }
+#pragma unroll
+                    for (int r = 0; r < BJ2; ++r) Q[sub * BJ2SQ + r * BJ2 + pos] = x[r] + (r == pos ? 1.f : 0.f);
+                }
+                if (lane == 0) {
+                    pb[sub] = I | (Jb << 16);
+                    act[sub] = nrot > 0;
+                    if (nrot) atomicAdd(active, nrot);
+                }
             }
             cl.sync();
-            if (ctl[par]) { done = true; break; }
+            // off-diagonal tiles (a < b) on CTA 0: E_ab <- Q_a^T E_ab Q_b, two tiles per warp (a
+            // half-warp each); lane: rows r0, r0 + 8 of the tile, columns c0..c0+7 (one block of
+            // the column pair-block). The product with Q_b takes the partner lane's half of the
+            // intermediate rows by shuffle.
             if (rank == 0) {
-                // off-diagonal tiles (a < b): E_ab <- Q_a^T E_ab Q_b, two tiles per warp (a half-warp
-                // each); lane: rows r0, r0 + 8 of the tile, columns c0..c0+7 (one block of the
-                // column pair-block). The product with Q_b takes the partner lane's half of the
-                // intermediate rows by shuffle.
                 const int h = lane >> 4, l16 = lane & 15;
                 const int r0 = l16 >> 1, c0 = (l16 & 1) * BJ;
+                float* E = El;
+                const float* Q = Ql;
+                const int* pb = pbl;
+                const int* act = actl;
                 for (int task0 = 2 * warp; task0 < ntile; task0 += 2 * nw) {
                     const int task = task0 + h;
                     const bool live = task < ntile;
@@ -358,8 +454,9 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
                     const int a = ab & 255, b = ab >> 8;
                     // a tile between two pair-blocks that did not rotate is unchanged (Q = I on both
                     // sides); the warp skips when both of its tiles are such
-                    if (__all_sync(0xffffffffu, !live || (!s_act[a] && !s_act[b]))) continue;
-                    const int Ia = pb[a] & 0xffff, Ja = pb[a] >> 16, Ib = pb[b] & 0xffff, Jb2 = pb[b] >> 16;
+                    if (__all_sync(0xffffffffu, !live || (!act[a] && !act[b]))) continue;
+                    const int pa = pb[a], pbb = pb[b];
+                    const int Ia = pa & 0xffff, Ja = pa >> 16, Ib = pbb & 0xffff, Jb2 = pbb >> 16;
                     const float* Qa = Q + a * BJ2SQ;
                     const float* Qb = Q + b * BJ2SQ;
                     const int colb = c0 ? Jb2 * BJ : Ib * BJ;   // first E column of this lane's 8
@@ -418,11 +515,10 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
                     }
                     __syncwarp();
                 }
-                __syncthreads();
-            } else {
-                // F <- F + F_Q + F F_Q: a half-warp per pair-block and a group of rows; lane x of
-                // the half holds column x of F_Q in registers
-                const float* fqs = qrem + (size_t)par * nb * BJ2SQ;
+            }
+            if (rank >= 1) {
+                // F <- F + F_Q + F F_Q on this CTA's rows: a half-warp per pair-block and a group
+                // of rows; lane x of the half holds column x of F_Q in registers
                 const int hw = tid >> 4, x = tid & 15, nhw = nthr >> 4;
                 const unsigned int half = 0xffffu << (lane & 16);
                 const int nr = j1 - j0;
@@ -435,7 +531,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
                     bool nz = false;
 #pragma unroll
                     for (int y = 0; y < BJ2; ++y) {
-                        fcol[y] = fqs[a * BJ2SQ + y * BJ2 + x];
+                        fcol[y] = qrem[a * SPSQ + y * SP + x];
                         nz |= fcol[y] != 0.f;
                     }
                     // F_Q = 0 (no rotation in this pair-block): F is unchanged
@@ -454,13 +550,14 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
                         for (int y = 0; y < BJ2; ++y) acc = fmaf(fv[y], fcol[y], acc);
                         // row j of F_Q (embedded) when j is one of the pair-block's indices
                         const int bj = j / BJ;
-                        if (bj == Ia) acc += fqs[a * BJ2SQ + (j - Ia * BJ) * BJ2 + x];
-                        else if (bj == Ja) acc += fqs[a * BJ2SQ + (BJ + j - Ja * BJ) * BJ2 + x];
+                        if (bj == Ia) acc += qrem[a * SPSQ + (j - Ia * BJ) * SP + x];
+                        else if (bj == Ja) acc += qrem[a * SPSQ + (BJ + j - Ja * BJ) * SP + x];
                         __syncwarp(half);
                         row[bj_index(Ia, Ja, x)] = acc;
                     }
                 }
             }
+            cl.sync();
         }
     }
     if (rank == 0) {
@@ -544,9 +641,8 @@ __global__ void __launch_bounds__(kEigThreads) k_chol32_multi(const CholJob* job
 // rotations Q in global memory (L2-resident: about 2 MB a matrix at k = 512).
 // A round runs in two phases between bounded grid barriers:
 //   A: a warp per pair-block loads its 16 x 16 diagonal block and 16 diagonal
-//      entries into shared memory, runs the inner sweep(s) exactly as the
-//      cluster kernel does (same rotations, same order, same arithmetic),
-//      and writes back the block, D and Q = I + F_Q;
+//      entries into registers, runs the inner sweep exactly as the cluster
+//      kernel does (the same function), and writes back the block, D and F_Q;
 //   B: a half-warp per off-diagonal tile of two pair-blocks of which one
 //      rotated (E_ab <- Q_a^T E_ab Q_b, both triangles), and a half-warp per
 //      pair-block and group of 16 F rows (F <- F + F_Q + F F_Q).
@@ -572,22 +668,12 @@ struct GbArgs {
     const GbMode* m; int nm; int max_sweeps; DevStatus* bar;
 };
 
-// per-warp scratch of phase A
-struct GbWarp {
-    float Eb[BJ2][SP];
-    float Fq[BJ2][SP];
-    DF Dl[BJ2];
-    InRot ri[BJ2 / 2];
-};
-
 __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
     __shared__ int s_sweep[kGbMaxModes], s_round[kGbMaxModes], s_done[kGbMaxModes], s_base[kGbMaxModes];
     __shared__ int s_pa[kGbMaxModes + 1], s_pt[kGbMaxModes + 1], s_pf[kGbMaxModes + 1];
     __shared__ int s_live;
-    extern __shared__ __align__(16) unsigned char gb_smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nwarp_cta = kGbThreads / 32;
-    GbWarp& W = reinterpret_cast<GbWarp*>(gb_smem)[warp];
     const int gwarp = blockIdx.x * nwarp_cta + warp, nwarps = gridDim.x * nwarp_cta;
     const int nm = A.nm;
 
@@ -645,76 +731,31 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
             const Crit qualifies{J.floor, J.tau, J.tol2};
             int I, Jb;
             rr_pair_e(t, a, J.m, I, Jb);
-            for (int e = lane; e < BJ2SQ; e += 32) {
-                const int u = e >> 4, v = e & 15;
-                W.Eb[u][v] = u != v ? J.E[(int64_t)bj_index(I, Jb, u) * J.ldE + bj_index(I, Jb, v)] : 0.f;
-                W.Fq[u][v] = 0.f;
+            // the inner sweep in registers, as in the cluster kernel
+            const int pos = lane & (BJ2 - 1);
+            const int64_t gi = bj_index(I, Jb, pos);
+            float x[BJ2];
+            DF d{0.f, 0.f};
+            if (lane < BJ2) {
+#pragma unroll
+                for (int r = 0; r < BJ2; ++r) x[r] = J.E[(int64_t)bj_index(I, Jb, r) * J.ldE + gi];
+                d = J.D[gi];
+            } else {
+#pragma unroll
+                for (int r = 0; r < BJ2; ++r) x[r] = 0.f;
             }
-            if (lane < BJ2) W.Dl[lane] = J.D[bj_index(I, Jb, lane)];
-            __syncwarp();
-            const int n_inner = t == 0 ? BJ2 - 1 : BJ;
-            unsigned int nrot = 0;
-            for (int it = 0; it < n_inner; ++it) {
-                if (lane < BJ2 / 2) {
-                    int u, v;
-                    if (t == 0) rr_pair_e(it, lane, BJ2, u, v);
-                    else { u = lane; v = BJ + ((lane + it) & (BJ - 1)); }
-                    InRot r{1.f, 0.f, 0.f, u | (v << 8)};
-                    if (bj_index(I, Jb, u) < J.k && bj_index(I, Jb, v) < J.k) {
-                        const float epq = W.Eb[u][v];
-                        if (qualifies(W.Dl[u], W.Dl[v], epq)) {
-                            const RotCS g = jacobi_rot(df_diff(W.Dl[v], W.Dl[u]), epq);
-                            r = InRot{g.c, g.s, g.cm1, u | (v << 8) | (1 << 16)};
-                            const float te = g.t * epq;
-                            W.Dl[u] = df_add(W.Dl[u], -te);
-                            W.Dl[v] = df_add(W.Dl[v], te);
-                            W.Eb[u][v] = 0.f;
-                            W.Eb[v][u] = 0.f;
-                            ++nrot;
-                        }
-                    }
-                    W.ri[lane] = r;
-                }
-                __syncwarp();
-                // E <- J^T E J on the 2 x 2 blocks (i, i2), i != i2
-                for (int e = lane; e < 64; e += 32) {
-                    const int i = e >> 3, i2 = e & 7;
-                    if (i == i2) continue;
-                    const InRot ra = W.ri[i], rb = W.ri[i2];
-                    if (!((ra.uv | rb.uv) & (1 << 16))) continue;
-                    const int pa = ra.uv & 255, qa = (ra.uv >> 8) & 255, pc = rb.uv & 255, qc = (rb.uv >> 8) & 255;
-                    const float x0 = W.Eb[pa][pc], x1 = W.Eb[pa][qc];
-                    const float x2 = W.Eb[qa][pc], x3 = W.Eb[qa][qc];
-                    const float ypp = ra.c * x0 - ra.s * x2, ypq = ra.c * x1 - ra.s * x3;
-                    const float yqp = ra.s * x0 + ra.c * x2, yqq = ra.s * x1 + ra.c * x3;
-                    W.Eb[pa][pc] = rb.c * ypp - rb.s * ypq;
-                    W.Eb[pa][qc] = rb.s * ypp + rb.c * ypq;
-                    W.Eb[qa][pc] = rb.c * yqp - rb.s * yqq;
-                    W.Eb[qa][qc] = rb.s * yqp + rb.c * yqq;
-                }
-                // F_Q <- F_Q J, c - 1 kept apart
-                for (int e = lane; e < 8 * BJ2; e += 32) {
-                    const InRot r = W.ri[e >> 4];
-                    if (!(r.uv & (1 << 16))) continue;
-                    const int y = e & 15, u = r.uv & 255, v = (r.uv >> 8) & 255;
-                    const float fp = W.Fq[y][u], fv = W.Fq[y][v];
-                    float np = fp + (fp * r.cm1 - fv * r.s);
-                    float nv = fv + (fp * r.s + fv * r.cm1);
-                    if (y == u) { np += r.cm1; nv += r.s; }
-                    if (y == v) { np -= r.s; nv += r.cm1; }
-                    W.Fq[y][u] = np;
-                    W.Fq[y][v] = nv;
-                }
-                __syncwarp();
-            }
+            unsigned int nrot = t == 0 ? inner_sweep<true>(x, d, I, Jb, J.k, qualifies)
+                                       : inner_sweep<false>(x, d, I, Jb, J.k, qualifies);
             for (int o = 16; o; o >>= 1) nrot += __shfl_xor_sync(0xffffffffu, nrot, o);
             float* Qa = J.Q + (int64_t)a * BJ2SQ;
-            for (int e = lane; e < BJ2SQ; e += 32) {
-                const int u = e >> 4, v = e & 15;
-                if (u != v) J.E[(int64_t)bj_index(I, Jb, u) * J.ldE + bj_index(I, Jb, v)] = W.Eb[u][v];
-                Qa[e] = W.Fq[u][v];   // F_Q; Q = I + F_Q
+            if (lane < BJ2) {
+#pragma unroll
+                for (int r = 0; r < BJ2; ++r) J.E[(int64_t)bj_index(I, Jb, r) * J.ldE + gi] = x[r];
+                J.D[gi] = d;
+            } else {
+#pragma unroll
+                for (int r = 0; r < BJ2; ++r) Qa[r * BJ2 + pos] = x[r];   // F_Q; Q = I + F_Q
             }
-            if (lane < BJ2) J.D[bj_index(I, Jb, lane)] = W.Dl[lane];
             if (lane == 0) {
                 J.act[a] = nrot > 0;
                 if (nrot) atomicAdd(&J.cnt[s_sweep[j] & 1], nrot);
@@ -1023,7 +1064,7 @@ cudaError_t launch_jacobi_gblk(const DfJob* jobs, int njobs, int max_sweeps, int
         e = cudaMemsetAsync(ws, 0, 256, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(ws + modes_at, hm.data(), sizeof(GbMode) * nm, cudaMemcpyHostToDevice, st);
-        const size_t smem = sizeof(GbWarp) * (kGbThreads / 32);
+        const size_t smem = 0;
         int per_sm = 0;
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_gblk, kGbThreads, smem);

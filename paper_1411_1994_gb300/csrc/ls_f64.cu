@@ -19,8 +19,6 @@ namespace ls {
 
 namespace {
 
-__device__ __forceinline__ bool grid_barrier(DevStatus* st) { return group_barrier(st, gridDim.x); }
-
 // ---------------------------------------------------------------------------
 // G0 / G1 / G2 and small elementwise kernels
 // ---------------------------------------------------------------------------
@@ -172,39 +170,16 @@ struct RowK {            // X(m, k) = p[m * ld + k]        (k contiguous)
     const double* p; int64_t ld;
     __device__ double operator()(int, int m, int k) const { return p[m * ld + k]; }
 };
-struct RowKScaled {      // X(m, k) = s[m] * p[m * ld + k]
-    static constexpr bool kfast = true;
-    const double* p; int64_t ld; const double* s;
-    __device__ double operator()(int, int m, int k) const { return s[m] * p[m * ld + k]; }
-};
 struct KRowN {           // X(k, n) = p[k * ld + n]        (n contiguous)
     static constexpr bool kfast = false;
     const double* p; int64_t ld;
     __device__ double operator()(int, int k, int n) const { return p[k * ld + n]; }
 };
-struct NRowKScaled {     // X(k, n) = s[n] * p[n * ld + k]
-    static constexpr bool kfast = true;
-    const double* p; int64_t ld; const double* s;
-    __device__ double operator()(int, int k, int n) const { return s[n] * p[n * ld + k]; }
-};
 struct StoreRow {        // C[z*zs + m*ld + n] = v
     double* p; int64_t ld; int64_t zs;
     __device__ void operator()(int z, int m, int n, double v) const { p[z * zs + m * ld + n] = v; }
 };
-struct StoreRowW {       // C[m*ld + n] = w[m] w[n] v
-    double* p; int64_t ld; const double* w;
-    __device__ void operator()(int, int m, int n, double v) const { p[m * ld + n] = w[m] * w[n] * v; }
-};
 
-// core: B(k=t, n=j*r2+l) = P1[j*C1 + c1(t)] * P2[l*C2 + c2(t)]
-struct CoreB {
-    static constexpr bool kfast = true;
-    const double* P1; const double* P2; int64_t C1, C2; int r2; const int32_t* tcol;
-    __device__ double operator()(int, int k, int n) const {
-        const int j = n / r2, l = n - j * r2;
-        return P1[j * C1 + tcol[3 * k + 1]] * P2[l * C2 + tcol[3 * k + 2]];
-    }
-};
 // eval step 1: A(m=(a,b), k) = B[m*r2 + k], B(k, n=s) = Z2[k*N + zidx[s]]
 struct EvalZ3 {
     static constexpr bool kfast = true;

@@ -5,7 +5,10 @@ matrix (with the rotation floor above E's FP32 noise, as in the reduction). The 
 accumulator are FP32. With tol = 1e-7, against bounds taken from that
 FP32 representation accumulated over tens of sweeps (the pipeline's
 second run, on the nearly diagonal U^T H U, is what reaches FP64 level):
-- the eigenvalues come out within 1e-6 of ||H||;
+- the eigenvalues come out within 4e-6 of ||H||: each eigenvalue gathers the
+  roundings (2^-24 of ||H|| each) of the sweeps x k rotations that touch its
+  row, a random sum of about sqrt(13 x 488) 2^-24 = 5e-6 of ||H|| at the
+  largest size here (measured: up to 1.1e-6);
 - the accumulated rotation V = I + F is orthogonal within 1e-4;
 - H V = V diag(D) holds within 1e-5 ||H||.
 The grid form, with the matrices in global memory, performs the same
@@ -72,7 +75,7 @@ def test_grid_form_large(k, spectrum):
     H, lam = _matrix(k, 200 + k, spectrum)
     D, V, sweeps = _run(H, 2)
     norm = np.abs(lam).max()
-    assert np.max(np.abs(np.sort(D)[::-1] - lam)) <= 1e-6 * norm
+    assert np.max(np.abs(np.sort(D)[::-1] - lam)) <= 4e-6 * norm
     assert np.max(np.abs(V.T @ V - np.eye(k))) <= 1e-4
     assert np.max(np.abs(H @ V - V * D)) <= 1e-5 * norm
     assert 1 <= sweeps <= 30
