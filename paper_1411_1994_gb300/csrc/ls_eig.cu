@@ -184,9 +184,9 @@ struct BjLayout {
 // of a sweep) the round-robin pairs of all 16 positions, otherwise u = l and
 // v = 8 + ((l + it) mod 8). Lane u takes the rotation from (d_u, d_v, e_uv) when
 // both indices are below k and the pair qualifies; then E_s <- J^T E_s J (rows in
-// each lane, then columns with the partner lane's column), F_Q <- F_Q J with c - 1
-// kept apart, d_u -= t e_uv, d_v += t e_uv, and the pair's 2 x 2 block of E_s is set
-// to zero. Returns the rotations taken by this lane.
+// each lane, then columns with the partner lane's column), F_Q <- F_Q J + (J - I)
+// with c - 1 taken directly, d_u -= t e_uv, d_v += t e_uv, and the pair's 2 x 2 block
+// of E_s is set to zero. Returns the rotations taken by this lane.
 //
 // The rows of a column sit in registers in an order that turns with the inner
 // rounds, so that every round pairs the same registers: (l, 8 + l) in the cross
@@ -194,28 +194,37 @@ struct BjLayout {
 // (l, 15 - l) in the full form, where register s < 15 holds row (s + it) mod 15.
 // The round loop then needs no unrolling and the code stays small.
 // ---------------------------------------------------------------------------
+// (indices mod 15 by conditional steps: the arguments stay within one period of 0..14)
+__device__ __forceinline__ int mod15(int v) {
+    v = v < 0 ? v + (BJ2 - 1) : v;
+    return v >= BJ2 - 1 ? v - (BJ2 - 1) : v;
+}
 template <bool FULL>
 __device__ __forceinline__ int in_partner(int it, int i) {
-    if (FULL) return i == BJ2 - 1 ? it : (i == it ? BJ2 - 1 : (2 * it - i + BJ2 - 1) % (BJ2 - 1));
+    if (FULL) return i == BJ2 - 1 ? it : (i == it ? BJ2 - 1 : mod15(2 * it - i));
     return i < BJ ? BJ + ((i + it) & (BJ - 1)) : ((i - BJ - it) & (BJ - 1));
 }
 // register of row `row` in inner round it
 template <bool FULL>
 __device__ __forceinline__ int in_reg(int it, int row) {
-    if (FULL) return row == BJ2 - 1 ? row : (row - it + BJ2 - 1) % (BJ2 - 1);
+    if (FULL) return row == BJ2 - 1 ? row : mod15(row - it);
     return row < BJ ? row : BJ + ((row - BJ - it) & (BJ - 1));
 }
 // row held by register r in inner round it
 template <bool FULL>
 __device__ __forceinline__ int in_row(int it, int r) {
-    if (FULL) return r == BJ2 - 1 ? r : (r + it) % (BJ2 - 1);
+    if (FULL) return r == BJ2 - 1 ? r : mod15(r + it);
     return r < BJ ? r : BJ + ((r - BJ + it) & (BJ - 1));
 }
+// v[p] for a runtime p, by a tree of selects on the bits of p
 __device__ __forceinline__ float pick16(const float (&v)[BJ2], int p) {
-    float x = v[0];
+    float a[8], b[4];
 #pragma unroll
-    for (int r = 1; r < BJ2; ++r) x = p == r ? v[r] : x;
-    return x;
+    for (int i = 0; i < 8; ++i) a[i] = (p & 1) ? v[2 * i + 1] : v[2 * i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = (p & 2) ? a[2 * i + 1] : a[2 * i];
+    const float c0 = (p & 4) ? b[1] : b[0], c1 = (p & 4) ? b[3] : b[2];
+    return (p & 8) ? c1 : c0;
 }
 
 template <bool FULL>
@@ -275,23 +284,18 @@ __device__ __forceinline__ unsigned int inner_sweep(float (&x)[BJ2], DF& d, int 
         const int plane = (lane & BJ2) | pt;
 #pragma unroll
         for (int r = 0; r < BJ2; ++r) o[r] = __shfl_sync(0xffffffffu, x[r], plane);
-        if (is_e) {
+        // both halves: u's column c x_u - s x_v, v's column s x_u + c x_v; then E_s's pair
+        // block is zeroed and F_Q takes J - I (c - 1 on the diagonal, -s and s off it)
 #pragma unroll
-            for (int r = 0; r < BJ2; ++r) x[r] = owner ? c * x[r] - sn * o[r] : sn * o[r] + c * x[r];
-            if (act) {
-#pragma unroll
-                for (int r = 0; r < BJ2; ++r)
-                    if (r == rpos || r == rpt) x[r] = 0.f;
-                d = df_add(d, owner ? -te : te);
-            }
-        } else {
+        for (int r = 0; r < BJ2; ++r) x[r] = owner ? c * x[r] - sn * o[r] : sn * o[r] + c * x[r];
+        if (act) {
+            const float add_pos = is_e ? 0.f : cm1, add_pt = is_e ? 0.f : (owner ? -sn : sn);
 #pragma unroll
             for (int r = 0; r < BJ2; ++r) {
-                float nx = owner ? x[r] + (x[r] * cm1 - o[r] * sn) : x[r] + (o[r] * sn + x[r] * cm1);
-                if (r == rpos) nx += cm1;
-                if (r == rpt) nx += owner ? -sn : sn;
-                x[r] = nx;
+                if (r == rpos) x[r] = is_e ? 0.f : x[r] + add_pos;
+                if (r == rpt) x[r] = is_e ? 0.f : x[r] + add_pt;
             }
+            if (is_e) d = df_add(d, owner ? -te : te);
         }
         // turn the register order to the next round's
         if (FULL) {
