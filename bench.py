@@ -517,6 +517,12 @@ def main():
         chunk = 16 if large else len(zs)
         out = torch.empty((chunk, wl.N, wl.N), dtype=torch.float32 if f32 else torch.float64, device="cuda")
         reps, warm = (2, 1) if large else (5, 3)
+        # the products' tile widths, measured once on the first chunk (outside the timing)
+        tune = None
+        if prec == L.LS_MIXED:
+            first = zs[:chunk]
+            with torch.cuda.stream(stream):
+                tune = ls.tune_eval(first, out[:len(first)])
 
         def all_slabs():
             for c0 in range(0, len(zs), chunk):
@@ -549,6 +555,7 @@ def main():
         # algorithmic flops per slab: 2 r0 r1 r2 (M) + 2 N r0 r1 (T) + 2 N^2 r0 (S)
         flops = ns * (2.0 * r0 * r1 * r2 + 2.0 * N * r0 * r1 + 2.0 * N * N * r0)
         res = {"slabs": ns, "N": N, "ranks": [r0, r1, r2], "dtype": "f32" if f32 else "f64", "ms": ms,
+               "tile_n_tuned": tune,
                "points_per_s": pts / (ms * 1e-3), "bytes_written": written,
                "write_gbs": written / (ms * 1e-3) / 1e9, "algorithmic_tflops": flops / (ms * 1e-3) / 1e12,
                "steps_ms": {k: v["ms"] / reps for k, v in steps.items() if k.startswith("eval")}}

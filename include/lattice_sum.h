@@ -304,6 +304,23 @@ int lattice_sum_eval_slab(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, vo
                           int32_t out_dtype);
 
 /*
+ * lattice_sum_tune_eval -- lattice_sum_eval_slab (same arguments, same
+ * result) on an LS_MIXED context, with the output tile width of its three
+ * tensor-core products (M = B x3 Z3 rows, T = M Z2^T, S = Z1 T^T, Eq.
+ * Tucker_singePot) chosen by measurement: in the first chunk of slabs each
+ * product runs at widths 32, 64 and 128 (one warm-up and two runs timed by
+ * CUDA events), and the fastest width is kept, process-wide, for products of
+ * that shape; later evaluations (any context) use it. Every width gives the
+ * same result bit for bit. `report` (host, `cap` bytes; may be NULL with
+ * cap 0) receives a JSON object: per product its shape, the three times in
+ * ms and the width kept. Synchronises the stream. Errors: as
+ * lattice_sum_eval_slab; LS_ERR_ARG on an LS_FP64 context or a report
+ * buffer that is too small.
+ */
+int lattice_sum_tune_eval(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev, int32_t out_dtype,
+                          char* report, int64_t cap);
+
+/*
  * lattice_sum_get_factors -- device pointers of the Tucker factors (valid
  * until lattice_sum_destroy; library-owned): Z[l] = double [r_l][N]
  * (orthonormal rows), core = double [r1][r2][r3]; ranks[3] receives r_l.

@@ -1160,7 +1160,12 @@ int lattice_sum_gemm_nt_mixed(const double* A, const double* B, int64_t M, int64
     return LS_OK;
 }
 
-int lattice_sum_eval_slab(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev, int32_t out_dtype) {
+}  // extern "C"
+
+namespace {
+
+int eval_impl(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev, int32_t out_dtype,
+              std::string* tune_report) {
     if (!ctx) return fail(nullptr, LS_ERR_ARG, "eval_slab: NULL context");
     if (!ctx->reduced) return fail(ctx, LS_ERR_STATE, "eval_slab: call rhosvd_reduce first");
     if (nslab < 0 || (nslab > 0 && (!z_index || !out_dev))) return fail(ctx, LS_ERR_ARG, "eval_slab: bad arguments");
@@ -1182,7 +1187,7 @@ int lattice_sum_eval_slab(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, vo
     if (ctx->p.precision == LS_MIXED) {
         // the three products on the tensor cores (two exact digits + two tails)
         int rc = dt_eval(&ctx->eval_cache, Zc, ctx->r, ctx->d_B, N, d_z, nslab, out_dev, out_dtype == LS_OUT_F32,
-                         DtOpts{}, st, &ctx->err);
+                         DtOpts{}, st, &ctx->err, tune_report);
         dfree(ctx, d_z);
         return rc;
     }
@@ -1199,6 +1204,31 @@ int lattice_sum_eval_slab(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, vo
     }
     dfree(ctx, work);
     dfree(ctx, d_z);
+    return LS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lattice_sum_eval_slab(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev, int32_t out_dtype) {
+    return eval_impl(ctx, z_index, nslab, out_dev, out_dtype, nullptr);
+}
+
+int lattice_sum_tune_eval(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev, int32_t out_dtype,
+                          char* report, int64_t cap) {
+    if (!ctx) return fail(nullptr, LS_ERR_ARG, "tune_eval: NULL context");
+    if (ctx->p.precision != LS_MIXED) return fail(ctx, LS_ERR_ARG, "tune_eval: the FP64 path has no tile widths to tune");
+    if (cap < 0 || (cap > 0 && !report)) return fail(ctx, LS_ERR_ARG, "tune_eval: bad report buffer");
+    std::string rep;
+    const int rc = eval_impl(ctx, z_index, nslab, out_dev, out_dtype, &rep);
+    if (rc != LS_OK) return rc;
+    const std::string js = "{" + rep + "}";
+    if (report && cap > 0) {
+        if ((int64_t)js.size() + 1 > cap) return fail(ctx, LS_ERR_ARG, "tune_eval: report buffer of %lld bytes, need %lld",
+                                                      (long long)cap, (long long)js.size() + 1);
+        memcpy(report, js.c_str(), js.size() + 1);
+    }
     return LS_OK;
 }
 

@@ -63,11 +63,14 @@
 #include <cuda.h>
 #include <cuda_fp16.h>
 
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "lattice_sum.h"
@@ -768,6 +771,23 @@ struct DtK {
     int kb_begin = 0, kb_end = -1;
 };
 
+// Tile widths chosen by measurement: product shape (output mode, M, N, K span in
+// k-blocks or -1 for per-batch ranges, batch) -> tile_n. Filled by dt_gemm_tuned, read
+// by dt_gemm when no width is asked for; shapes never tuned take the width by N.
+using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int64_t>;
+struct TuneTable {
+    std::mutex mu;
+    std::map<TuneKey, int> best;
+};
+TuneTable& tune_table() {
+    static TuneTable* t = new TuneTable();
+    return *t;
+}
+TuneKey tune_key(int mode, int64_t M, int64_t N, int64_t batch, const DtK& kr, int nkb) {
+    const int64_t span = kr.kb_lo ? -1 : (int64_t)((kr.kb_end < 0 ? nkb : kr.kb_end) - kr.kb_begin);
+    return TuneKey{mode, M, N, span, batch};
+}
+
 int dt_gemm(const DtOp& A, const DtOp& B, int64_t M, int64_t N, int64_t batch, const DtOut& out, const DtOpts& opt,
             int* flag, cudaStream_t st, std::string* err, DtK kr = DtK{}) {
     if (M <= 0 || N <= 0 || batch <= 0) return LS_OK;
@@ -779,6 +799,12 @@ int dt_gemm(const DtOp& A, const DtOp& B, int64_t M, int64_t N, int64_t batch, c
         (out.accumulate && out.mode != DT_F64))
         return tc_err(err, "dt gemm: bad operands", LS_ERR_ARG);
     int bn = opt.tile_n;
+    if (bn == 0) {
+        TuneTable& tt = tune_table();
+        std::lock_guard<std::mutex> g(tt.mu);
+        const auto it = tt.best.find(tune_key(out.mode, M, N, batch, kr, nkb));
+        if (it != tt.best.end()) bn = it->second;
+    }
     if (bn == 0) bn = N <= 32 ? 32 : N <= 64 ? 64 : 128;
     if (bn != 32 && bn != 64 && bn != 128) return tc_err(err, "dt gemm: tile_n must be 32, 64 or 128", LS_ERR_ARG);
     DtJob J;
@@ -824,6 +850,55 @@ int dt_gemm(const DtOp& A, const DtOp& B, int64_t M, int64_t N, int64_t batch, c
         default: e = launch_dt<128, DT_PAIR>(J, grid, flag, st); break;
     }
     if (e != cudaSuccess) return tc_err(err, std::string("dt gemm launch: ") + cudaGetErrorString(e));
+    return LS_OK;
+}
+
+// The product with each tile width in turn, timed by CUDA events on the stream (one run
+// to warm up, then two timed; the stream is synchronised), the fastest recorded for
+// its shape. Every width gives the same result bit for bit, so the product is left
+// computed; the output must not accumulate. Appends "name": {times, best} to report.
+int dt_gemm_tuned(const DtOp& A, const DtOp& B, int64_t M, int64_t N, int64_t batch, const DtOut& out, int* flag,
+                  cudaStream_t st, std::string* err, const char* name, std::string* report) {
+    if (M <= 0 || N <= 0 || batch <= 0) return LS_OK;
+    if (out.accumulate) return tc_err(err, "dt tune: accumulating products cannot be rerun", LS_ERR_ARG);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return tc_err(err, "dt tune: event creation failed");
+    }
+    const int widths[3] = {32, 64, 128};
+    float ms[3] = {0.f, 0.f, 0.f};
+    int rc = LS_OK;
+    for (int w = 0; w < 3 && rc == LS_OK; ++w) {
+        DtOpts o;
+        o.tile_n = widths[w];
+        rc = dt_gemm(A, B, M, N, batch, out, o, flag, st, err);
+        if (rc == LS_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = tc_err(err, "dt tune: event record failed");
+        for (int rep = 0; rep < 2 && rc == LS_OK; ++rep) rc = dt_gemm(A, B, M, N, batch, out, o, flag, st, err);
+        if (rc == LS_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms[w], e0, e1) != cudaSuccess))
+            rc = tc_err(err, "dt tune: timing failed");
+        ms[w] *= 0.5f;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != LS_OK) return rc;
+    int best = 0;
+    for (int w = 1; w < 3; ++w)
+        if (ms[w] < ms[best]) best = w;
+    {
+        const int nkb = (int)(A.kpad / DT_BK);
+        TuneTable& tt = tune_table();
+        std::lock_guard<std::mutex> g(tt.mu);
+        tt.best[tune_key(out.mode, M, N, batch, DtK{}, nkb)] = widths[best];
+    }
+    if (report) {
+        char buf[256];
+        snprintf(buf, sizeof buf, "%s\"%s\": {\"M\": %lld, \"N\": %lld, \"batch\": %lld, \"ms\": [%.4f, %.4f, %.4f], \"tile_n\": %d}",
+                 report->empty() ? "" : ", ", name, (long long)M, (long long)N, (long long)batch, ms[0], ms[1], ms[2],
+                 widths[best]);
+        *report += buf;
+    }
     return LS_OK;
 }
 
@@ -888,7 +963,7 @@ void dt_eval_free(DtEvalCache* c) {
 
 int dt_eval(DtEvalCache** cache, const double* const Z[3], const int32_t* r, const double* B, int64_t N,
             const int32_t* zidx, int nslab, void* out, int out_f32, const DtOpts& opt, cudaStream_t st,
-            std::string* err) {
+            std::string* err, std::string* tune_report) {
     const int64_t r0 = r[0], r1 = r[1], r2 = r[2];
     const int64_t k0 = pad32(r0), k1 = pad32(r1), k2 = pad32(r2);
     if (k0 > DT_MAXK4 || k1 > DT_MAXK4 || k2 > DT_MAXK4) return tc_err(err, "eval: rank above 4096", LS_ERR_ARG);
@@ -956,7 +1031,9 @@ int dt_eval(DtEvalCache** cache, const double* const Z[3], const int32_t* r, con
             if (dt_split(SrcF64{Z[2], 1, N, 0, zidx + s0}, r2, z2, st) != cudaSuccess)
                 return tc_err(err, "eval: split failed");
             // M[s][(a, b)] = sum_c core[(a, b)][c] Z2[c][z_s]
-            rc = dt_gemm(c.core, z2, r0 * r1, nm, 1, DtOut{Mt, r0 * r1, 0, DT_PAIR}, opt, fl.d, st, err);
+            const DtOut mo{Mt, r0 * r1, 0, DT_PAIR};
+            rc = tune_report && s0 == 0 ? dt_gemm_tuned(c.core, z2, r0 * r1, nm, 1, mo, fl.d, st, err, "M", tune_report)
+                                        : dt_gemm(c.core, z2, r0 * r1, nm, 1, mo, opt, fl.d, st, err);
             if (rc != LS_OK) return rc;
         }
         for (int s1 = 0; s1 < nm; s1 += tchunk) {
@@ -969,7 +1046,10 @@ int dt_eval(DtEvalCache** cache, const double* const Z[3], const int32_t* r, con
                 if (dt_split(SrcPair{Mt + (int64_t)s1 * r0 * r1, r1, 1, r0 * r1}, r1, m, st) != cudaSuccess)
                     return tc_err(err, "eval: split failed");
                 // T_s[y][a] = sum_b M_s[a][b] Z1^T[y][b]   (D[a][y], a on the lanes)
-                rc = dt_gemm(m, c.z1t, r0, N, ns, DtOut{Tt, r0, N * r0, DT_PAIR}, opt, fl.d, st, err);
+                const DtOut to{Tt, r0, N * r0, DT_PAIR};
+                rc = tune_report && s0 == 0 && s1 == 0
+                         ? dt_gemm_tuned(m, c.z1t, r0, N, ns, to, fl.d, st, err, "T", tune_report)
+                         : dt_gemm(m, c.z1t, r0, N, ns, to, opt, fl.d, st, err);
                 if (rc != LS_OK) return rc;
                 if (dt_split(SrcPair{Tt, r0, 1, N * r0}, r0, t, st) != cudaSuccess)
                     return tc_err(err, "eval: split failed");
@@ -978,7 +1058,10 @@ int dt_eval(DtEvalCache** cache, const double* const Z[3], const int32_t* r, con
                 Scope sc("eval.slab", st);
                 // S_s[x][y] = sum_a T_s[y][a] Z0^T[x][a]   (D[y][x], y on the lanes: rows of S contiguous)
                 void* o = static_cast<char*>(out) + (size_t)(s0 + s1) * N * N * esz;
-                rc = dt_gemm(t, c.z0t, N, N, ns, DtOut{o, N, N * N, out_f32 ? DT_F32 : DT_F64}, opt, fl.d, st, err);
+                const DtOut so{o, N, N * N, out_f32 ? DT_F32 : DT_F64};
+                rc = tune_report && s0 == 0 && s1 == 0
+                         ? dt_gemm_tuned(t, c.z0t, N, N, ns, so, fl.d, st, err, "S", tune_report)
+                         : dt_gemm(t, c.z0t, N, N, ns, so, opt, fl.d, st, err);
                 if (rc != LS_OK) return rc;
             }
         }

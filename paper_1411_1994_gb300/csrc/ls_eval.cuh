@@ -42,10 +42,13 @@ void dt_eval_free(DtEvalCache* c);
 // S_s[x][y] = sum_{a,b,c} B[a][b][c] Z0[a][x] Z1[b][y] Z2[c][zidx[s]] for the
 // nslab slabs (zidx: device int32), into out (nslab x N x N, FP32 if out_f32
 // else FP64). Builds *cache on first use. Synchronises to read the kernels'
-// status flag. Ranks up to 4096.
+// status flag. Ranks up to 4096. With tune_report, the first chunk's three
+// products are each timed at every tile width and the fastest width is kept for
+// their shapes (later products of those shapes use it); the timings are appended
+// to *tune_report as JSON members.
 int dt_eval(DtEvalCache** cache, const double* const Z[3], const int32_t* r, const double* B, int64_t N,
             const int32_t* zidx, int nslab, void* out, int out_f32, const DtOpts& opt, cudaStream_t st,
-            std::string* err);
+            std::string* err, std::string* tune_report = nullptr);
 
 // D = A B^T (A: M x K, B: N x K, D: M x N row-major; device memory) by the same
 // product, synchronised, with the status checked. K above 4096 runs in exact chunks

@@ -27,7 +27,8 @@ EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_create", "lattice_sum_add_de
             "lattice_sum_rhosvd_reduce", "lattice_sum_eval_slab", "lattice_sum_get_factors",
             "lattice_sum_read", "lattice_sum_profile", "lattice_sum_profile_report",
             "lattice_sum_eval_slab_noalloc", "lattice_sum_batch_reduce", "lattice_sum_gemm_nt",
-            "lattice_sum_gemm_nt_mixed", "lattice_sum_jacobi_eig", "lattice_sum_destroy", "lattice_sum_last_error")
+            "lattice_sum_gemm_nt_mixed", "lattice_sum_jacobi_eig", "lattice_sum_tune_eval", "lattice_sum_destroy",
+            "lattice_sum_last_error")
 
 
 class ls_params(C.Structure):
@@ -281,6 +282,18 @@ class LatticeSum:
         z = (C.c_int64 * max(len(z_index), 1))(*[int(x) for x in z_index])
         _check(self._lib.lattice_sum_eval_slab(self.ctx, z, len(z_index), C.c_void_p(out_ptr), out_dtype),
                self.ctx)
+
+    def tune_eval(self, z_index, out) -> dict:
+        """lattice_sum_tune_eval into the float32/float64 CUDA tensor `out` (len(z_index) x N x N):
+        the evaluation with its products' tile widths measured and kept; returns the report."""
+        import json
+        import torch
+        z = (C.c_int64 * max(len(z_index), 1))(*[int(x) for x in z_index])
+        buf = C.create_string_buffer(4096)
+        _check(self._lib.lattice_sum_tune_eval(self.ctx, z, len(z_index), C.c_void_p(out.data_ptr()),
+                                               LS_OUT_F32 if out.dtype == torch.float32 else LS_OUT_F64, buf,
+                                               C.c_int64(len(buf))), self.ctx)
+        return json.loads(buf.value.decode())
 
     def eval_slab_torch(self, z_index, dtype=None, out=None):
         import torch

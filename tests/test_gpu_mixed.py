@@ -3,14 +3,15 @@ head accumulation, FP64 orthogonalisation) against the FP64 path and the FP64
 oracle.
 
 Tolerances, from the arithmetic of the tensor-core contractions: every
-operand row is scaled by a power of two and split into a 6-bit head (whose
-products accumulate exactly in FP32 for K <= 1024) and a rest carried to
-2^-30 by three BF16 parts; the products that touch the rest accumulate in a
-second FP32 accumulator whose rounding is 2^-30 of the result. A contraction
-is then good to ~2^-30 of sum |a_k b_k|; with the cancellation of the core
-contraction the tests allow 1e-7 relative against the FP64 path for
-projections, the core and slabs, and the configuration's eps (1e-6) for the
-final slab values against the FP64 oracle, as the precision target requires.
+operand row is scaled by a power of two and written as two exact 7-bit
+digits and two 11-bit tails (FP16); the digit products accumulate exactly in
+FP32 (two levels), the products below them in a third accumulator at 2^-14
+of the result or less. A contraction is then good to ~2^-30 of
+sum |a_k b_k|; with the cancellation of the core contraction the tests allow
+1e-7 relative against the FP64 path for projections, the core and slabs, and
+the configuration's eps (1e-6) for the final slab values against the FP64
+oracle, as the precision target requires. The measured tile-width choice
+(lattice_sum_tune_eval) changes no result bit.
 """
 import math
 
@@ -112,3 +113,31 @@ def test_mixed_single_site_and_ragged_tiles():
         assert rel(sb, sa) < 1e-7, (wl.name, rel(sb, sa))
         a.close()
         b.close()
+
+
+def test_tuned_evaluation_is_bitwise_the_plain_one():
+    wl = W.config2()
+    s = scale_for(wl)
+    ls, _ = run(wl, s, L.LS_MIXED)
+    zs = [int(z) for z in wl.slabs[:16]]
+    plain = ls.eval_slab_torch(zs, dtype=torch.float32).cpu().numpy()
+    out = torch.empty((len(zs), wl.N, wl.N), dtype=torch.float32, device="cuda")
+    rep = ls.tune_eval(zs, out)
+    assert set(rep) == {"M", "T", "S"}, rep
+    for name, r in rep.items():
+        assert r["tile_n"] in (32, 64, 128) and len(r["ms"]) == 3 and min(r["ms"]) > 0.0, (name, r)
+    assert np.array_equal(out.cpu().numpy(), plain)
+    # later evaluations take the kept widths and still agree bit for bit
+    again = ls.eval_slab_torch(zs, dtype=torch.float32).cpu().numpy()
+    assert np.array_equal(again, plain)
+    ls.close()
+
+
+def test_tune_rejects_fp64_context():
+    wl = W.small_case(L=(3, 2, 2), eps=1e-6)
+    s = scale_for(wl)
+    ls, _ = run(wl, s, L.LS_FP64)
+    out = torch.empty((1, wl.N, wl.N), dtype=torch.float64, device="cuda")
+    with pytest.raises(L.LatticeSumError):
+        ls.tune_eval([wl.N // 2], out)
+    ls.close()
