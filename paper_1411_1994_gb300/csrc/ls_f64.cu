@@ -37,17 +37,36 @@ __global__ void k_genvec(double* g, int R, int64_t N, double h, double sinc_step
     }
 }
 
+// columns c0 .. c0 + ncols - 1, element (c, i) at out[c * N + i]: blocks walk the
+// (column, run of kAsmPer * blockDim.x elements) pairs in a grid-stride loop, so that a
+// launch of a few blocks per SM covers any number of columns; each thread keeps kAsmPer
+// independent sums (its elements blockDim.x apart) in flight
+constexpr int kAsmPer = 4;
 __global__ void k_assemble(const double* __restrict__ g, int64_t N, const int32_t* __restrict__ colq,
                            const int32_t* __restrict__ woff, const int32_t* __restrict__ wcnt,
-                           const int32_t* __restrict__ win, int64_t c0, double* __restrict__ out) {
-    const int64_t c = c0 + blockIdx.y;
-    const double* gq = g + (int64_t)colq[c] * 2 * N + N;
-    const int o = woff[c], n = wcnt[c];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int k = 0; k < n; ++k) acc += gq[i - win[o + k]];
-        out[c * N + i] = acc;
+                           const int32_t* __restrict__ win, int64_t c0, int64_t ncols, double* __restrict__ out) {
+    const int64_t run = (int64_t)kAsmPer * blockDim.x;
+    const int64_t runs = (N + run - 1) / run, items = ncols * runs;
+    for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+        const int64_t cl = w / runs, i0 = (w - cl * runs) * run + threadIdx.x, c = c0 + cl;
+        const double* gq = g + (int64_t)__ldg(colq + c) * 2 * N + N;
+        const int o = __ldg(woff + c), n = __ldg(wcnt + c);
+        double acc[kAsmPer];
+#pragma unroll
+        for (int u = 0; u < kAsmPer; ++u) acc[u] = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const double* gk = gq - __ldg(win + o + k);
+#pragma unroll
+            for (int u = 0; u < kAsmPer; ++u) {
+                const int64_t i = i0 + (int64_t)u * blockDim.x;
+                if (i < N) acc[u] += gk[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kAsmPer; ++u) {
+            const int64_t i = i0 + (int64_t)u * blockDim.x;
+            if (i < N) out[c * N + i] = acc[u];
+        }
     }
 }
 
@@ -835,12 +854,15 @@ cudaError_t launch_assemble(const double* g, int64_t N, const int32_t* colq, con
                             const int32_t* wcnt, const int32_t* win, int64_t c0, int64_t ncols,
                             double* out, cudaStream_t st) {
     if (ncols <= 0) return cudaSuccess;
-    for (int64_t s = 0; s < ncols; s += 65535) {
-        const int64_t n = ncols - s < 65535 ? ncols - s : 65535;
-        dim3 grid((unsigned)((N + 255) / 256 < 64 ? (N + 255) / 256 : 64), (unsigned)n);
-        k_assemble<<<grid, 256, 0, st>>>(g, N, colq, woff, wcnt, win, c0 + s, out);
-        count_kernels(1);
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            nsm = 1;
     }
+    const int64_t blocks = std::min<int64_t>(ncols * ((N + 256 * kAsmPer - 1) / (256 * kAsmPer)), (int64_t)nsm * 8);
+    k_assemble<<<(unsigned)blocks, 256, 0, st>>>(g, N, colq, woff, wcnt, win, c0, ncols, out);
+    count_kernels(1);
     return cudaGetLastError();
 }
 

@@ -1,12 +1,12 @@
 // FP64-grade products on tcgen05 tensor cores for sm_103a (the exact-slice
 // scheme below): the reduction's dense FP64 contractions (weighted Gram
 // matrices, Def. 4.1 / Thm 2.1; CholeskyQR products; the projection P = Z A^T,
-// Thm A.1(c)). One tile of 128 x 64 outputs per CTA, operands in 128B-swizzled
-// shared memory by TMA (one plain load per tile; no multicast), one thread
-// issuing tcgen05.mma for the CTA, four epilogue warps reading the
-// accumulators back with tcgen05.ld. Every mbarrier wait is bounded: on
-// timeout the kernel raises a flag, drains the copies it issued, frees its
-// TMEM and returns.
+// Thm A.1(c)). One tile of 128 x 64 outputs per CTA, operands in 64B-swizzled
+// shared memory by TMA through two stages of k-blocks of 32 (plain loads; no
+// multicast), one thread issuing tcgen05.mma for the CTA, four epilogue warps
+// reading the accumulators back with tcgen05.ld. Every mbarrier wait is
+// bounded: on timeout the kernel raises a flag, drains the copies it issued,
+// frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -29,9 +29,9 @@ namespace {
 
 using namespace tc5;
 
-constexpr int TBM = 128, TBN = 64, TBK = 64;
-constexpr int TILE_A = TBM * TBK * 2;          // bytes of one bf16 A tile (16 KB)
-constexpr int TILE_B = TBN * TBK * 2;          // 8 KB
+constexpr int TBM = 128, TBN = 64, TBK = 32;
+constexpr int TILE_A = TBM * TBK * 2;          // bytes of one bf16 A tile (8 KB)
+constexpr int TILE_B = TBN * TBK * 2;          // 4 KB
 constexpr int TC_THREADS = 192;                // warp 0 TMA, warp 1 MMA + TMEM, warps 2-5 epilogue
 
 enum OutMode : int { OUT_F64 = 0, OUT_F32 = 1 };
@@ -57,12 +57,14 @@ struct TcOut {
 // the exact level sums by integer Horner steps (levels 0-3 and 4-7), converts
 // once to FP64 and applies 2^(E_a + E_b): a product is good to about 2^-53 of
 // sum_k |a_k| |b_k|, as an FP64 dot product is, while the arithmetic runs on
-// the tensor cores. One stage of 8 slices x (128 + 64) rows x 64 k fills
-// 192 KB of shared memory; the eight accumulators fill TMEM's 512 columns.
+// the tensor cores. A stage of 8 slices x (128 + 64) rows x 32 k takes 96 KB of
+// shared memory, so that the next k-block loads while the MMAs of this one run;
+// the eight accumulators fill TMEM's 512 columns.
 // ---------------------------------------------------------------------------
 constexpr int XSL = 8;                              // slices (digits)
 constexpr int XKCHUNK = 512;                        // K per exact accumulation
-constexpr int XSTAGE = XSL * (TILE_A + TILE_B);     // 192 KB
+constexpr int XSTAGE = XSL * (TILE_A + TILE_B);     // 96 KB
+constexpr int XNST = 2;                             // stages
 constexpr int XTMEM = XSL * TBN;                    // 512 columns
 
 struct X64Job {
@@ -87,9 +89,9 @@ struct X64Group {
 __global__ void __launch_bounds__(TC_THREADS, 1) k_x64_gemm(const __grid_constant__ X64Group G, int* flag) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + XSTAGE);
-    uint64_t* empty = full + 1;
-    uint64_t* accum = empty + 1;      // accumulators of a chunk complete
+    uint64_t* full = (uint64_t*)(smem + XNST * XSTAGE);   // [XNST]
+    uint64_t* empty = full + XNST;                       // [XNST]
+    uint64_t* accum = empty + XNST;   // accumulators of a chunk complete
     uint64_t* drained = accum + 1;    // epilogue has read them
     uint32_t* tmem_slot = (uint32_t*)(drained + 1);
     int ji = 0;
@@ -103,8 +105,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_x64_gemm(const __grid_constan
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        mbar_init(full, 1);
-        mbar_init(empty, 1);
+        for (int s = 0; s < XNST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
         mbar_init(accum, 1);
         mbar_init(drained, 4);   // one arrival per epilogue warp
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -120,23 +124,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_x64_gemm(const __grid_constan
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // TMA producer: one stage, refilled once the MMAs of the previous k-block are done
+        // TMA producer: a ring of XNST stages, each refilled once the MMAs that read it are done
         int issued = 0;
         for (int kb = 0; kb < J.nkb; ++kb) {
-            if (kb > 0 && !mbar_wait(empty, (kb - 1) & 1, flag)) break;
+            const int s = kb % XNST, u = kb / XNST;
+            if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1, flag)) break;
             const int kx = kb * TBK;
-            mbar_expect_tx(full, XSTAGE);
+            unsigned char* st = smem + s * XSTAGE;
+            mbar_expect_tx(&full[s], XSTAGE);
 #pragma unroll
-            for (int i = 0; i < XSL; ++i) tma_load_3d(smem + i * TILE_A, &J.a[i], kx, m0, 0, full);
+            for (int i = 0; i < XSL; ++i) tma_load_3d(st + i * TILE_A, &J.a[i], kx, m0, 0, &full[s]);
 #pragma unroll
-            for (int j = 0; j < XSL; ++j) tma_load_3d(smem + XSL * TILE_A + j * TILE_B, &J.b[j], kx, n0, 0, full);
+            for (int j = 0; j < XSL; ++j) tma_load_3d(st + XSL * TILE_A + j * TILE_B, &J.b[j], kx, n0, 0, &full[s]);
             issued = kb + 1;
         }
-        if (issued > 0) {
-            long long it = 0;
-            while (!mbar_try_wait(full, (issued - 1) & 1) && ++it < kWaitLimit) {
-            }
-        }
+        // every issued stage must have landed before the CTA may exit
+        for (int j = issued > XNST ? issued - XNST : 0; j < issued; ++j) mbar_drain(&full[j % XNST], (j / XNST) & 1);
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: pair (i, j) into the accumulator of level i + j; a chunk starts from zero
         const uint32_t idesc = idesc_bf16(TBM, TBN);
@@ -146,23 +149,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_x64_gemm(const __grid_constan
             asm volatile("tcgen05.fence::after_thread_sync;");
             const int kbe = min(J.nkb, (c + 1) * kbc);
             for (int kb = c * kbc; kb < kbe; ++kb) {
-                if (!mbar_wait(full, kb & 1, flag)) { ok = false; break; }
+                const int s = kb % XNST;
+                if (!mbar_wait(&full[s], (kb / XNST) & 1, flag)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t base = smem_u32(smem);
+                const uint32_t base = smem_u32(smem + s * XSTAGE);
                 const bool first_kb = kb == c * kbc;
 #pragma unroll
                 for (int kk = 0; kk < TBK / 16; ++kk) {
-                    const uint64_t o = (uint64_t)((kk * 32) >> 4);
+                    const uint64_t o = (uint64_t)((kk * 32) >> 4);   // 16 bf16 = 32 bytes along K
 #pragma unroll
                     for (int l = 0; l < XSL; ++l)
 #pragma unroll
                         for (int i = 0; i <= l; ++i) {
-                            const uint64_t a = smem_desc_sw128(base + i * TILE_A) + o;
-                            const uint64_t b = smem_desc_sw128(base + XSL * TILE_A + (l - i) * TILE_B) + o;
+                            const uint64_t a = smem_desc_sw64(base + i * TILE_A) + o;
+                            const uint64_t b = smem_desc_sw64(base + XSL * TILE_A + (l - i) * TILE_B) + o;
                             mma_bf16(tmem + (uint32_t)(l * TBN), a, b, idesc, (!first_kb || kk || i) ? 1u : 0u);
                         }
                 }
-                mma_commit(empty);
+                mma_commit(&empty[s]);
             }
             mma_commit(accum);
         }
@@ -279,7 +283,7 @@ __global__ void __launch_bounds__(128) k_split_x64(const __grid_constant__ X64Sp
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-// rows x kpad bf16 matrices, `batch` of them back to back; box = box_rows x 64
+// rows x kpad bf16 matrices, `batch` of them back to back; box = box_rows x 32 (64-byte swizzle)
 bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t kpad, int64_t batch, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
@@ -288,7 +292,7 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t kpad, int6
     cuuint32_t box[3] = {(cuuint32_t)TBK, (cuuint32_t)box_rows, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -383,7 +387,7 @@ int gemm_x64(const X64Spec* sp, int n, int* flag, cudaStream_t st, std::string* 
     }
     g.n = n;
     if (blocks == 0) return LS_OK;
-    const size_t smem = XSTAGE + 1024 + 256;
+    const size_t smem = XNST * XSTAGE + 1024 + 256;
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [&] {
