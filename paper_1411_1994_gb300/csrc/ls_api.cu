@@ -452,7 +452,8 @@ namespace {
 // Scratch of one mode of one context during the reduction.
 struct RedMode {
     double *G = nullptr, *L = nullptr, *pd = nullptr, *cand = nullptr, *H = nullptr, *V = nullptr, *snap = nullptr,
-           *isl = nullptr, *w = nullptr, *vg = nullptr, *ytmp = nullptr, *Gz = nullptr, *Li = nullptr, *D2 = nullptr;
+           *isl = nullptr, *w = nullptr, *vg = nullptr, *ytmp = nullptr, *Gz = nullptr, *Li = nullptr, *D2 = nullptr,
+           *gate = nullptr;   // ||Y Y^T - I||_F before CholeskyQR (picks its first pass)
     // two-stage shared-memory eigen-solver: U0 = I + F1, S = U0^T U0, SLi, Uo, T1 = H Uo, Hp = Uo^T T1, F2
     double *U0 = nullptr, *S = nullptr, *SLi = nullptr, *Uo = nullptr, *T1 = nullptr, *Hp = nullptr, *F2 = nullptr;
     int32_t *piv = nullptr, *perm = nullptr;
@@ -645,6 +646,7 @@ int red_basis(RedState& R, CholJob* cj) {
         CUS(dalloc(ctx, &M.D2, (int64_t)r * r));
         CUS(dalloc(ctx, &M.ytmp, (int64_t)r * N));
         CUS(dalloc(ctx, &M.vg, C * M.k));
+        CUS(dalloc(ctx, &M.gate, 1));
         L[l] = M.L;
         U[l] = M.V;
         Hc[l] = M.H;
@@ -661,7 +663,7 @@ int red_basis(RedState& R, CholJob* cj) {
         kl[l] = M.k;
         ks[l] = M.k;
         rs[l] = r;
-        cj[l] = CholJob{M.Gz, M.Li, R.d_st + 3 + l, r};
+        cj[l] = CholJob{M.Gz, M.Li, R.d_st + 3 + l, r, M.gate};
     }
     {
         // FP64-grade products on the tensor cores (exact slices)
@@ -672,10 +674,21 @@ int red_basis(RedState& R, CholJob* cj) {
         if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: basis: %s", err.c_str());
     }
     {
+        // CholeskyQR2's first pass: where Y Y^T is within kSeriesGate of I (Frobenius), the
+        // series for (Y Y^T)^{-1/2} writes the transform; elsewhere the Cholesky factorisation
+        // launched next does (both read the same device-side distance, so no host decision)
         Scope sc("cholqr2", st);
         const int64_t r64[3] = {rs[0], rs[1], rs[2]};
+        const double* gc[3] = {Gz[0], Gz[1], Gz[2]};
+        double *Li[3], *D2[3], *gate[3];
+        for (int l = 0; l < 3; ++l) {
+            Li[l] = R.m[l].Li;
+            D2[l] = R.m[l].D2;
+            gate[l] = R.m[l].gate;
+        }
         std::string err;
         int rc = x64_gram(3, Yc, r64, N, nullptr, Gz, &R.d_st[9].flag, st, &err);
+        if (rc == LS_OK) rc = x64_lowdin(3, gc, rs, D2, Li, &R.d_st[9].flag, st, &err, gate);
         if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: CholeskyQR: %s", err.c_str());
     }
     return LS_OK;
@@ -805,7 +818,7 @@ int red_finish(RedState& R, ls_tucker_info* info) {
         for (void* q : {(void*)M.G, (void*)M.L, (void*)M.pd, (void*)M.cand, (void*)M.H, (void*)M.V, (void*)M.snap,
                         (void*)M.isl, (void*)M.w, (void*)M.piv, (void*)M.perm, (void*)M.vg, (void*)M.ytmp,
                         (void*)M.Gz, (void*)M.Li, (void*)M.D2, (void*)M.U0, (void*)M.S, (void*)M.SLi, (void*)M.Uo, (void*)M.T1,
-                        (void*)M.Hp, (void*)M.F2})
+                        (void*)M.Hp, (void*)M.F2, (void*)M.gate})
             dfree(ctx, q);
     }
     dfree(ctx, d_perm_t);

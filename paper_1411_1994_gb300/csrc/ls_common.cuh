@@ -76,8 +76,11 @@ cudaError_t launch_norm_columns(double* a, int64_t C, int64_t N, double* norms, 
 // overwritten) and Li = L^{-1} (lower, zeros above) for several matrices in
 // one cooperative launch. st: zeroed status per job; a non-positive pivot
 // raises FLAG_NOT_SPD (the pivot is replaced by 1 so the launch completes).
+// gate (device, may be NULL): the job is skipped, Li left as it is, when
+// *gate < kSeriesGate (the caller's series has written Li instead).
+constexpr double kSeriesGate = 0.1;
 struct CholJob {
-    double* A; double* Li; DevStatus* st; int r;
+    double* A; double* Li; DevStatus* st; int r; const double* gate = nullptr;
 };
 cudaError_t launch_chol_inv_multi(const CholJob* jobs, int njobs, int num_sms, cudaStream_t st);
 

@@ -592,6 +592,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 __global__ void __launch_bounds__(kEigThreads) k_chol32_multi(const CholJob* jobs) {
     const CholJob J = jobs[blockIdx.x];
+    if (J.gate && *J.gate < kSeriesGate) return;   // the series pass took this matrix
     const int r = J.r;
     extern __shared__ __align__(16) float A[];   // r x r, row-major (lower part)
     float* tmp = A + (size_t)r * r;               // r

@@ -618,7 +618,7 @@ constexpr int CHB = 32;
 // one cooperative grid, CTAs split between the jobs: a group barrier after
 // each panel step and after each block row of Li.
 struct CholMode {
-    double* A; double* Li; DevStatus* st; int r; int cta0; int ncta;
+    double* A; double* Li; DevStatus* st; int r; int cta0; int ncta; const double* gate;
 };
 struct CholArgs {
     const CholMode* m; int nmodes;
@@ -626,6 +626,8 @@ struct CholArgs {
 __global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
     __shared__ double D[CHB][CHB + 1];
     const CholMode J = Ar.m[find_job(Ar.m, Ar.nmodes)];
+    // the series pass took this matrix: every CTA of the job leaves together
+    if (J.gate && *J.gate < kSeriesGate) return;
     const int lb = blockIdx.x - J.cta0, nb = J.ncta;
     double* A = J.A;
     double* Li = J.Li;
@@ -1017,7 +1019,7 @@ cudaError_t launch_chol_inv_multi(const CholJob* jobs, int njobs, int num_sms, c
         int cta = 0;
         for (int m = 0; m < nj; ++m) {
             const CholJob& J = jobs[j0 + m];
-            hm[m] = CholMode{J.A, J.Li, J.st, J.r, cta, nc[m]};
+            hm[m] = CholMode{J.A, J.Li, J.st, J.r, cta, nc[m], J.gate};
             cta += nc[m];
         }
         CholMode* dm = nullptr;

@@ -605,8 +605,28 @@ struct LowdinSet {
     const double* D2[kX64MaxJobs];
     const double* D3[kX64MaxJobs];
     double* T[kX64MaxJobs];
+    double* gate[kX64MaxJobs];   // ||S - I||_F (gated form; else null)
     int k[kX64MaxJobs];
 };
+// gate[j] = ||S_j - I||_F, one block per matrix (fixed reduction order)
+__global__ void __launch_bounds__(1024) k_dist_identity(const __grid_constant__ LowdinSet L) {
+    const int j = blockIdx.x, k = L.k[j];
+    const int64_t n = (int64_t)k * k;
+    double acc = 0.0;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+        const double v = L.S[j][e] - ((e / k) == (e % k) ? 1.0 : 0.0);
+        acc = fma(v, v, acc);
+    }
+    __shared__ double red[32];
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        *L.gate[j] = sqrt(t);
+    }
+}
 __global__ void k_minus_identity(const __grid_constant__ LowdinSet L) {
     const int j = blockIdx.y, k = L.k[j];
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -617,12 +637,13 @@ __global__ void k_lowdin_combine(const __grid_constant__ LowdinSet L) {
     const int j = blockIdx.y, k = L.k[j];
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= (int64_t)k * k) return;
+    if (L.gate[j] && !(*L.gate[j] < kSeriesGate)) return;   // too far from I: the Cholesky pass takes it
     const double id = (e / k) == (e % k) ? 1.0 : 0.0;
     L.T[j][e] = id - 0.5 * L.Dl[j][e] + 0.375 * L.D2[j][e] - 0.3125 * L.D3[j][e];
 }
 
 int x64_lowdin(int n, const double* const S[], const int k[], double* const D2[], double* const T[], int* flag,
-               cudaStream_t st, std::string* err) {
+               cudaStream_t st, std::string* err, double* const gate[]) {
     for (int g0 = 0; g0 < n; g0 += kX64MaxJobs) {
         const int ng = std::min(kX64MaxJobs, n - g0);
         Arena ar(st);
@@ -641,6 +662,7 @@ int x64_lowdin(int n, const double* const S[], const int k[], double* const D2[]
             L.D2[i] = D2[l];
             L.D3[i] = D3[i];
             L.T[i] = T[l];
+            L.gate[i] = gate ? gate[l] : nullptr;
             L.k[i] = kk[i] = k[l];
             Dlc[i] = L.Dl[i];
             D2c[i] = D2[l];
@@ -648,6 +670,10 @@ int x64_lowdin(int n, const double* const S[], const int k[], double* const D2[]
             emax = std::max(emax, e);
         }
         const dim3 grid((unsigned)((emax + 255) / 256), (unsigned)ng);
+        if (gate) {
+            k_dist_identity<<<ng, 1024, 0, st>>>(L);
+            count_kernels(1);
+        }
         k_minus_identity<<<grid, 256, 0, st>>>(L);
         count_kernels(1);
         // Delta is symmetric: Delta^2 = Delta Delta^T and Delta^3 = Delta^2 Delta^T need no transposes

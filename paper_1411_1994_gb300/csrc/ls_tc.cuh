@@ -43,9 +43,11 @@ int x64_small(int n, const double* const A[], const int ta[], const double* cons
               const int k[], double* const out[], const double* const add[], int* flag, cudaStream_t st,
               std::string* err);
 // T_l = S_l^{-1/2} by the series I - Delta/2 + 3/8 Delta^2 - 5/16 Delta^3 (Delta = S_l - I);
-// D2_l receives Delta^2 (scratch of the caller).
+// D2_l receives Delta^2 (scratch of the caller). With gate (device doubles, one per
+// matrix): gate_l = ||Delta_l||_F, and T_l is written only where gate_l < kSeriesGate
+// (elsewhere a Cholesky pass gated on the same value writes it).
 int x64_lowdin(int n, const double* const S[], const int k[], double* const D2[], double* const T[], int* flag,
-               cudaStream_t st, std::string* err);
+               cudaStream_t st, std::string* err, double* const gate[] = nullptr);
 // D = A B^T (row-major, device memory), synchronised, with the status checked.
 int x64_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* D, cudaStream_t st,
                 std::string* err);
