@@ -4,8 +4,10 @@
 // [r0, r1) of G and of L and their residual diagonal d. Per step every CTA
 // reduces the published (max d, argmax, sum d) candidates of all CTAs in the
 // same order, reads row p of L from its owner's shared memory, computes its
-// rows of the new column l_j = (G_jp - L_j . L_p) / sqrt(d_p) (a thread per
-// row, FP64), updates d and publishes its next candidate into every CTA's shared
+// rows of the new column l_j = (G_jp - L_j . L_p) / sqrt(d_p) (FP64; each
+// dot product in four quarters, one per warp, so that the four SMSPs' FP64
+// units share the work, added in a fixed order), updates d and publishes its
+// next candidate into every CTA's shared
 // memory (double-buffered by step parity): one cluster barrier per step and no
 // global-memory traffic inside the loop. Greedy diagonal pivoting with ties to
 // the smaller index; the iteration stops when the remaining trace is <= delta
@@ -22,7 +24,9 @@ namespace ls {
 
 namespace {
 
-constexpr int kPcThreads = 128;
+constexpr int kPcThreads = 128;   // four warps: the quarters of each dot product
+
+static_assert(kPcThreads == 128, "the row dot products are split over exactly four warps");
 
 struct PcMode {
     const double* G; double* L; double* resid; int* piv; DevStatus* st; int C; int kmax; double delta;
@@ -59,8 +63,9 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cluster(PcArgs A) {
     double* Ls = Gs + (size_t)rp * ldG;                           // [rp][ldL]
     double* d = Ls + (size_t)rp * ldL;                            // [rp]
     double* lrow = d + rp;                                        // [kmax]
-    Cand* cand = reinterpret_cast<Cand*>(lrow + kmax);            // [2][cs]
-    __shared__ double s_dmax, s_sum;
+    double* part = lrow + kmax;                                   // [4][rp] quarter sums
+    Cand* cand = reinterpret_cast<Cand*>(part + 4 * (size_t)rp);  // [2][cs]
+    __shared__ double s_dmax, s_sum, s_inv;
     __shared__ int s_p;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -117,6 +122,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cluster(PcArgs A) {
                 s_p = key == 0 ? -1 : 0xffffff - (int)(key & 0xffffffull);
                 s_dmax = key == 0 ? 0.0 : mx;
                 s_sum = sm;
+                s_inv = mx > 0.0 ? 1.0 / sqrt(mx) : 0.0;   // once, not in every thread
             }
         }
         __syncthreads();
@@ -131,20 +137,28 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cluster(PcArgs A) {
             for (int t = tid; t < k; t += nthr) lrow[t] = src[t];
         }
         __syncthreads();
-        const double inv = 1.0 / sqrt(dmax);
-        // a thread per row: l_j = (G_jp - L_j . L_p) / sqrt(d_p), four partial sums
-        for (int jl = tid; jl < nr; jl += nthr) {
-            const double* lj = Ls + (size_t)jl * ldL;
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-            int t = 0;
-            for (; t + 3 < k; t += 4) {
-                a0 = fma(lj[t], lrow[t], a0);
-                a1 = fma(lj[t + 1], lrow[t + 1], a1);
-                a2 = fma(lj[t + 2], lrow[t + 2], a2);
-                a3 = fma(lj[t + 3], lrow[t + 3], a3);
+        const double inv = s_inv;
+        // L_j . L_p in quarters of the k range, warp w the w-th quarter of every row (a thread
+        // per row), two partial sums a thread
+        {
+            const int qlen = (k + 3) >> 2, t0 = min(k, warp * qlen), t1 = min(k, t0 + qlen);
+            for (int jl = lane; jl < nr; jl += 32) {
+                const double* lj = Ls + (size_t)jl * ldL;
+                double a0 = 0.0, a1 = 0.0;
+                int t = t0;
+                for (; t + 1 < t1; t += 2) {
+                    a0 = fma(lj[t], lrow[t], a0);
+                    a1 = fma(lj[t + 1], lrow[t + 1], a1);
+                }
+                if (t < t1) a0 = fma(lj[t], lrow[t], a0);
+                part[warp * rp + jl] = a0 + a1;
             }
-            for (; t < k; ++t) a0 = fma(lj[t], lrow[t], a0);
-            const double l = (Gs[(size_t)jl * ldG + p] - ((a0 + a1) + (a2 + a3))) * inv;
+        }
+        __syncthreads();
+        // l_j = (G_jp - L_j . L_p) / sqrt(d_p), the quarters added in order
+        for (int jl = tid; jl < nr; jl += nthr) {
+            const double dot = ((part[jl] + part[rp + jl]) + part[2 * rp + jl]) + part[3 * rp + jl];
+            const double l = (Gs[(size_t)jl * ldG + p] - dot) * inv;
             Ls[(size_t)jl * ldL + k] = l;
             d[jl] = (r0 + jl == p) ? 0.0 : fmax(d[jl] - l * l, 0.0);
         }
@@ -166,7 +180,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cluster(PcArgs A) {
 }
 
 size_t pc_smem(int C, int kmax, int cs, int rp) {
-    return 8 * ((size_t)rp * (C | 1) + (size_t)rp * (kmax | 1) + rp + kmax) + sizeof(Cand) * 2 * (size_t)cs;
+    return 8 * ((size_t)rp * (C | 1) + (size_t)rp * (kmax | 1) + rp + kmax + 4 * (size_t)rp) + sizeof(Cand) * 2 * (size_t)cs;
 }
 
 int smem_cap() {
