@@ -318,14 +318,16 @@ def run_batch(args, torch, B, L):
     s_of = [scale[(w.R, w.sinc_step, w.r_min, w.box_hi - w.box_lo)] for w in items]
     stream = torch.cuda.Stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    # each item's defect list as the C ABI takes it, built once (host input data)
+    defects_c = [L.make_defects(w.defects) if w.defects else [] for w in items]
 
     def step(batched):
         infos = []
         for j0 in range(0, len(items), args.batch_wave):
             ctxs = []
-            for w, s in zip(items[j0:j0 + args.batch_wave], s_of[j0:j0 + args.batch_wave]):
+            for j, (w, s) in enumerate(zip(items[j0:j0 + args.batch_wave], s_of[j0:j0 + args.batch_wave])):
                 c = L.LatticeSum.from_workload(w, s, L.LS_MIXED if batched else L.LS_FP64, stream=stream.cuda_stream)
-                c.add_defects(w.defects)
+                c.add_defects(defects_c[j0 + j])
                 ctxs.append(c)
             if batched:
                 infos += L.batch_reduce(ctxs, items[0].eps)
@@ -439,9 +441,12 @@ def main():
     except Exception:
         pass
 
+    # the defect list as the C ABI takes it, built once (host input data, like the workload)
+    defects_c = L.make_defects(wl.defects) if wl.defects else []
+
     def step(prec):
         ls = L.LatticeSum.from_workload(wl, s, prec, stream=stream.cuda_stream)
-        ls.add_defects(wl.defects)
+        ls.add_defects(defects_c)
         info = ls.rhosvd_reduce(wl.eps)
         ls.close()
         return info
@@ -490,7 +495,7 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ls = L.LatticeSum.from_workload(wl, s, prec, stream=stream.cuda_stream)
-            ls.add_defects(wl.defects)
+            ls.add_defects(defects_c)
             ls.rhosvd_reduce(wl.eps)
             for a in range(3):
                 ls.read(L.LS_READ_BASIS, a)

@@ -202,19 +202,18 @@ int append_columns(ls_ctx* ctx, int l, const std::vector<int32_t>& q, const std:
         mc.wincap = nw;
     }
     // descriptors live at d_desc: colq [0,cap), woff [cap,2cap), wcnt [2cap,3cap)
-    CU(cudaMemcpyAsync(mc.d_desc, mc.colq.data(), mc.C * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+    CU(upload_h2d(mc.d_desc, mc.colq.data(), mc.C * sizeof(int32_t), ctx->st));
     count_h2d((int64_t)(mc.C * sizeof(int32_t)));
-    CU(cudaMemcpyAsync(mc.d_desc + mc.cap, mc.woff.data(), mc.C * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+    CU(upload_h2d(mc.d_desc + mc.cap, mc.woff.data(), mc.C * sizeof(int32_t), ctx->st));
     count_h2d((int64_t)(mc.C * sizeof(int32_t)));
-    CU(cudaMemcpyAsync(mc.d_desc + 2 * mc.cap, mc.wcnt.data(), mc.C * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+    CU(upload_h2d(mc.d_desc + 2 * mc.cap, mc.wcnt.data(), mc.C * sizeof(int32_t), ctx->st));
     count_h2d((int64_t)(mc.C * sizeof(int32_t)));
-    CU(cudaMemcpyAsync(mc.d_win, mc.win.data(), mc.win.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+    CU(upload_h2d(mc.d_win, mc.win.data(), mc.win.size() * sizeof(int32_t), ctx->st));
     count_h2d((int64_t)(mc.win.size() * sizeof(int32_t)));
     Scope sc_asm("assemble", ctx->st);
     CU(launch_assemble(ctx->d_g, N, mc.d_desc, mc.d_desc + mc.cap, mc.d_desc + 2 * mc.cap, mc.d_win, c0, add,
                        mc.d_cols, ctx->st));
-    // the host vectors may be reallocated by the next append: finish the copies
-    CU(cudaStreamSynchronize(ctx->st));
+    // (the uploads went through pinned staging: the host vectors may change at once)
     return LS_OK;
 }
 
@@ -497,9 +496,9 @@ int red_prepare(RedState& R, PcholJob* pj) {
     CUS(dalloc(ctx, &ctx->d_tcol, 3 * T));
     CUS(dalloc(ctx, &ctx->d_xi, T));
     CUS(dalloc(ctx, &ctx->d_xin, T));
-    CUS(cudaMemcpyAsync(ctx->d_tcol, ctx->tcol.data(), 3 * T * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CUS(upload_h2d(ctx->d_tcol, ctx->tcol.data(), 3 * T * sizeof(int32_t), st));
     count_h2d(3 * T * sizeof(int32_t));
-    CUS(cudaMemcpyAsync(ctx->d_xi, ctx->xi.data(), T * sizeof(double), cudaMemcpyHostToDevice, st));
+    CUS(upload_h2d(ctx->d_xi, ctx->xi.data(), T * sizeof(double), st));
     count_h2d(T * sizeof(double));
     CUS(dalloc(ctx, &R.d_st, 10));
     CUS(cudaMemsetAsync(R.d_st, 0, 10 * sizeof(DevStatus), st));
@@ -523,7 +522,7 @@ int red_prepare(RedState& R, PcholJob* pj) {
         CUS(cudaMemsetAsync(ctx->d_sigma[l], 0, C * sizeof(double), st));
         std::vector<double> wh(C);
         for (int64_t c = 0; c < C; ++c) wh[c] = sqrt((double)mc.count[c]);
-        CUS(cudaMemcpyAsync(M.w, wh.data(), C * sizeof(double), cudaMemcpyHostToDevice, st));
+        CUS(upload_h2d(M.w, wh.data(), C * sizeof(double), st));
         count_h2d(C * sizeof(double));
         { Scope sc("norms", st); CUS(launch_norm_columns(mc.d_cols, C, N, ctx->d_norms[l], st)); }
         a[l] = mc.d_cols;
@@ -593,12 +592,16 @@ int red_after_pchol(RedState& R, JacobiJob* jj) {
 int red_select(RedState& R) {
     ls_ctx* ctx = R.ctx;
     cudaStream_t st = ctx->st;
-    for (int l = 0; l < 3; ++l) {
-        RedMode& M = R.m[l];
-        const int forced = R.forced ? std::max(1, R.forced[l]) : 0;
+    {
+        SortSelectJob jobs[3];
+        for (int l = 0; l < 3; ++l) {
+            RedMode& M = R.m[l];
+            const int forced = R.forced ? std::max(1, R.forced[l]) : 0;
+            jobs[l] = SortSelectJob{M.H, M.k, forced, M.cand + kPcholCand - 1, M.perm, ctx->d_sigma[l], M.isl,
+                                    R.d_sel + 3 * l};
+        }
         Scope sc("select", st);
-        CUS(launch_sort_select(M.H, M.k, R.eps, forced, R.floor_noise, M.cand + kPcholCand - 1, M.perm,
-                               ctx->d_sigma[l], M.isl, R.d_sel + 3 * l, st));
+        CUS(launch_sort_select(3, jobs, R.eps, R.floor_noise, st));
     }
     CUS(cudaMemcpyAsync(R.hs, R.d_st, 3 * sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
     CUS(cudaMemcpyAsync(R.hs + 6, R.d_st + 6, 3 * sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
@@ -796,9 +799,9 @@ int red_finish(RedState& R, ls_tucker_info* info) {
         } else {
             CUS(dalloc(ctx, &d_perm_t, T));
             CUS(dalloc(ctx, &d_off, Cs[0] + 1));
-            CUS(cudaMemcpyAsync(d_perm_t, perm.data(), T * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            CUS(upload_h2d(d_perm_t, perm.data(), T * sizeof(int32_t), st));
             count_h2d(T * sizeof(int32_t));
-            CUS(cudaMemcpyAsync(d_off, off.data(), (Cs[0] + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            CUS(upload_h2d(d_off, off.data(), (Cs[0] + 1) * sizeof(int32_t), st));
             count_h2d((Cs[0] + 1) * sizeof(int32_t));
             double *P1t = nullptr, *P2t = nullptr, *W = nullptr;
             CUS(dalloc(ctx, &P1t, (int64_t)Cs[1] * ctx->r[1]));
@@ -1193,7 +1196,7 @@ int eval_impl(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev,
     cudaStream_t st = ctx->st;
     int32_t* d_z = nullptr;
     CU(dalloc(ctx, &d_z, nslab));
-    CU(cudaMemcpyAsync(d_z, z.data(), nslab * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CU(upload_h2d(d_z, z.data(), nslab * sizeof(int32_t), st));
     count_h2d((int64_t)(nslab * sizeof(int32_t)));
     const double* Zc[3] = {ctx->d_Z[0], ctx->d_Z[1], ctx->d_Z[2]};
     Scope sc_eval("eval", st);

@@ -52,6 +52,16 @@ struct Scope {
     Scope& operator=(const Scope&) = delete;
 };
 
+// Launch-configuration queries cached per kernel (ls_eval.cu): the kernel's dynamic shared
+// memory limit is raised only when a launch needs more than before, and its resident
+// blocks per SM are asked of the driver once per (threads, shared memory).
+cudaError_t grow_smem(const void* kernel, size_t bytes);
+cudaError_t blocks_per_sm(const void* kernel, int threads, size_t smem, int* out);
+
+// Asynchronous host-to-device upload through pinned staging (ls_eval.cu): `src` may be
+// reused as soon as the call returns.
+cudaError_t upload_h2d(void* dst, const void* src, size_t bytes, cudaStream_t st);
+
 // message returned by lattice_sum_last_error(NULL) (calls without a context)
 void set_global_error(const char* msg);
 
@@ -134,10 +144,13 @@ cudaError_t launch_jacobi_multi(const JacobiJob* jobs, int njobs, int max_sweeps
 // and write out[0] = r, out[1] = discarded^2, out[2] = total (as doubles);
 // also inv_sqrt_lam[k] = 1/sqrt(lam[k]) and lam[k] <- sqrt(max(lam[k], 0)).
 // *extra (device, may be NULL) is energy outside the problem that belongs to
-// the discarded tail (and to the total).
-cudaError_t launch_sort_select(const double* G, int64_t C, double eps, int forced, double resolution,
-                               const double* extra, int32_t* perm, double* lam, double* inv_sqrt_lam, double* out,
-                               cudaStream_t st);
+// the discarded tail (and to the total). n jobs, one CTA each, in one launch
+// per 16 jobs.
+struct SortSelectJob {
+    const double* G; int64_t C; int forced; const double* extra; int32_t* perm; double* lam; double* inv_sqrt_lam;
+    double* out;
+};
+cudaError_t launch_sort_select(int n, const SortSelectJob* jobs, double eps, double resolution, cudaStream_t st);
 
 // Pivoted Cholesky G P = L L^T (greedy diagonal pivoting) of up to three
 // C x C PSD matrices in one cooperative launch, stopped when the trace of

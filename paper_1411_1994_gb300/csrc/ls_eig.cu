@@ -957,12 +957,12 @@ cudaError_t launch_chol32_multi(const CholJob* jobs, int njobs, cudaStream_t st)
     for (int m = 0; m < njobs; ++m) rmax = std::max(rmax, jobs[m].r);
     if (rmax > chol32_max_r()) return cudaErrorInvalidValue;
     const size_t smem = 4 * ((size_t)rmax * rmax + rmax);
-    cudaError_t e = cudaFuncSetAttribute(k_chol32_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = grow_smem((const void*)k_chol32_multi, smem);
     if (e != cudaSuccess) return e;
     CholJob* dj = nullptr;
     e = cudaMallocAsync(&dj, sizeof(CholJob) * njobs, st);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(dj, jobs, sizeof(CholJob) * njobs, cudaMemcpyHostToDevice, st);
+    e = upload_h2d(dj, jobs, sizeof(CholJob) * njobs, st);
     if (e == cudaSuccess) {
         k_chol32_multi<<<njobs, kEigThreads, smem, st>>>(dj);
         count_kernels(1);
@@ -994,7 +994,7 @@ cudaError_t launch_jacobi_blk(const DfJob* jobs, int njobs, int max_sweeps, cuda
     const BjLayout L1(kmax, rows_per);
     if (L1.f_bytes > (size_t)cap) return cudaErrorInvalidValue;
     const size_t smem = std::max(L1.e_bytes, L1.f_bytes);
-    cudaError_t e = cudaFuncSetAttribute(k_jacobi_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = grow_smem((const void*)k_jacobi_blk, smem);
     if (e != cudaSuccess) return e;
     std::vector<DfMode> hm(njobs);
     for (int m = 0; m < njobs; ++m) {
@@ -1004,7 +1004,7 @@ cudaError_t launch_jacobi_blk(const DfJob* jobs, int njobs, int max_sweeps, cuda
     DfMode* dm = nullptr;
     e = cudaMallocAsync(&dm, sizeof(DfMode) * njobs, st);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(dm, hm.data(), sizeof(DfMode) * njobs, cudaMemcpyHostToDevice, st);
+    e = upload_h2d(dm, hm.data(), sizeof(DfMode) * njobs, st);
     if (e == cudaSuccess) {
         const int cs = 1 + nF;
         BjArgs a{dm, max_sweeps > 63 ? 63 : max_sweeps, cs, rows_per};
@@ -1068,11 +1068,10 @@ cudaError_t launch_jacobi_gblk(const DfJob* jobs, int njobs, int max_sweeps, int
         }
         e = cudaMemsetAsync(ws, 0, 256, st);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ws + modes_at, hm.data(), sizeof(GbMode) * nm, cudaMemcpyHostToDevice, st);
+            e = upload_h2d(ws + modes_at, hm.data(), sizeof(GbMode) * nm, st);
         const size_t smem = 0;
         int per_sm = 0;
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_gblk, kGbThreads, smem);
+        if (e == cudaSuccess) e = blocks_per_sm((const void*)k_jacobi_gblk, kGbThreads, smem, &per_sm);
         if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
         if (e == cudaSuccess) {
             GbArgs a{reinterpret_cast<const GbMode*>(ws + modes_at), nm, max_sweeps > 63 ? 63 : max_sweeps,

@@ -67,6 +67,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <string>
@@ -902,38 +903,6 @@ int dt_gemm_tuned(const DtOp& A, const DtOp& B, int64_t M, int64_t N, int64_t ba
     return LS_OK;
 }
 
-// One pinned host buffer per process for the core's uploads, so that the copy is
-// asynchronous: a pageable upload of this size makes the host wait for the stream to
-// drain, and the GPU then idles while the host enqueues the next kernels. The next
-// upload waits for the previous copy (long finished: every reduction synchronises
-// its stream before it returns).
-struct PinnedStage {
-    std::mutex mu;
-    void* p = nullptr;
-    size_t cap = 0;
-    cudaEvent_t done = nullptr;
-};
-PinnedStage& pinned_stage() {
-    static PinnedStage* s = new PinnedStage();
-    return *s;
-}
-cudaError_t upload_pinned(void* dst, const void* src, size_t bytes, cudaStream_t st) {
-    PinnedStage& S = pinned_stage();
-    std::lock_guard<std::mutex> g(S.mu);
-    cudaError_t e;
-    if (S.done && (e = cudaEventSynchronize(S.done)) != cudaSuccess) return e;
-    if (bytes > S.cap) {
-        if (S.p) cudaFreeHost(S.p);
-        S.p = nullptr;
-        S.cap = 0;
-        if ((e = cudaMallocHost(&S.p, bytes)) != cudaSuccess) return e;
-        S.cap = bytes;
-    }
-    if (!S.done && (e = cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming)) != cudaSuccess) return e;
-    memcpy(S.p, src, bytes);
-    if ((e = cudaMemcpyAsync(dst, S.p, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
-    return cudaEventRecord(S.done, st);
-}
 
 // Scratch for a chunked product: the free device memory / div, clamped to [lo, hi]; a
 // need of at most lo is granted without asking the driver.
@@ -945,6 +914,113 @@ int64_t scratch_budget(int64_t need, int div, int64_t lo, int64_t hi) {
 }
 
 }  // namespace
+
+// Host-to-device uploads through a process-wide ring of pinned host memory: the
+// caller's bytes are copied into the ring at once (the caller may reuse its buffer
+// on return) and the copy runs asynchronously on the stream. A pageable upload
+// would make the host wait for the stream to drain first, and the GPU would idle
+// while the host enqueued the next kernels. A region of the ring is reused only
+// after the event recorded behind its copy has completed.
+namespace {
+struct PinnedRing {
+    std::mutex mu;
+    char* buf = nullptr;
+    size_t cap = 0, head = 0;
+    std::deque<std::tuple<size_t, size_t, cudaEvent_t>> inflight;   // [begin, end) in copy order
+    std::vector<cudaEvent_t> spare;
+};
+PinnedRing& pinned_ring() {
+    static PinnedRing* r = new PinnedRing();
+    return *r;
+}
+cudaError_t ring_retire_front(PinnedRing& R) {
+    cudaEvent_t e = std::get<2>(R.inflight.front());
+    const cudaError_t rc = cudaEventSynchronize(e);
+    R.spare.push_back(e);
+    R.inflight.pop_front();
+    return rc;
+}
+}  // namespace
+
+namespace {
+struct LaunchCache {
+    std::mutex mu;
+    std::map<const void*, size_t> smem;
+    std::map<std::tuple<const void*, int, size_t>, int> occ;
+};
+LaunchCache& launch_cache() {
+    static LaunchCache* c = new LaunchCache();
+    return *c;
+}
+}  // namespace
+
+cudaError_t grow_smem(const void* kernel, size_t bytes) {
+    LaunchCache& L = launch_cache();
+    std::lock_guard<std::mutex> g(L.mu);
+    size_t& done = L.smem[kernel];
+    if (bytes <= done) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done = bytes;
+    return e;
+}
+
+cudaError_t blocks_per_sm(const void* kernel, int threads, size_t smem, int* out) {
+    LaunchCache& L = launch_cache();
+    std::lock_guard<std::mutex> g(L.mu);
+    const auto key = std::make_tuple(kernel, threads, smem);
+    const auto it = L.occ.find(key);
+    if (it != L.occ.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kernel, threads, smem);
+    if (e == cudaSuccess) L.occ[key] = *out;
+    return e;
+}
+
+cudaError_t upload_h2d(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) return cudaSuccess;
+    PinnedRing& R = pinned_ring();
+    std::lock_guard<std::mutex> g(R.mu);
+    cudaError_t e;
+    const size_t need = (bytes + 255) & ~(size_t)255;
+    // copies already done free their regions
+    while (!R.inflight.empty() && cudaEventQuery(std::get<2>(R.inflight.front())) == cudaSuccess)
+        if ((e = ring_retire_front(R)) != cudaSuccess) return e;
+    if (need > R.cap) {
+        while (!R.inflight.empty())
+            if ((e = ring_retire_front(R)) != cudaSuccess) return e;
+        const size_t old = R.cap;
+        if (R.buf) cudaFreeHost(R.buf);
+        R.buf = nullptr;
+        R.cap = R.head = 0;
+        const size_t cap = std::max<size_t>({need, (size_t)8 << 20, 2 * old});
+        if ((e = cudaMallocHost(&R.buf, cap)) != cudaSuccess) return e;
+        R.cap = cap;
+    }
+    if (R.head + need > R.cap) R.head = 0;
+    // wait for the copies that still read the region about to be written (oldest first)
+    while (!R.inflight.empty()) {
+        bool overlap = false;
+        for (auto& f : R.inflight)
+            if (std::get<0>(f) < R.head + need && R.head < std::get<1>(f)) overlap = true;
+        if (!overlap) break;
+        if ((e = ring_retire_front(R)) != cudaSuccess) return e;
+    }
+    memcpy(R.buf + R.head, src, bytes);
+    if ((e = cudaMemcpyAsync(dst, R.buf + R.head, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    cudaEvent_t ev;
+    if (!R.spare.empty()) {
+        ev = R.spare.back();
+        R.spare.pop_back();
+    } else if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+        return e;
+    }
+    if ((e = cudaEventRecord(ev, st)) != cudaSuccess) return e;
+    R.inflight.emplace_back(R.head, R.head + need, ev);
+    R.head += need;
+    return cudaSuccess;
+}
 
 // Operands of the slab evaluation that depend only on the reduced tensor, built
 // on the first evaluation and kept with the context: Z0^T and Z1^T (rows y over
@@ -1131,7 +1207,7 @@ int dt_core(const double* P0, const double* P1, const double* P2, const int32_t*
     if (!d_kb || !a.ok() || !b.ok() || !W || !ws.ok() || !p0s.ok()) return tc_err(err, "core: out of memory", LS_ERR_OOM);
     {
         Scope sc("core.operands", st);
-        if (upload_pinned(d_kb, up.data(), up.size() * sizeof(int32_t), st) != cudaSuccess)
+        if (upload_h2d(d_kb, up.data(), up.size() * sizeof(int32_t), st) != cudaSuccess)
             return tc_err(err, "core: upload failed");
         count_h2d((int64_t)(up.size() * sizeof(int32_t)));
         // step 1's A operand over the padded term list: A[k][t] = P2[k][c2(t)]

@@ -554,56 +554,96 @@ __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// eigenvalue sort + eps-rank selection (single CTA)
+// eigenvalue sort + eps-rank selection, one CTA per matrix. The ranking compares
+// integer keys (doubles order like their sign-adjusted bit patterns), and the
+// tail sums are suffix sums taken by one warp (contiguous chunks a lane, then a
+// shuffle scan), so that neither the O(C^2) comparisons nor the C additions queue
+// on one SMSP's FP64 unit.
 // ---------------------------------------------------------------------------
-__global__ void k_sort_select(const double* G, int C, double eps, int forced, double resolution, const double* extra,
-                              int32_t* perm, double* lam, double* isl, double* out) {
+__device__ __forceinline__ unsigned long long order_key(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+struct SelJob {
+    const double* G; int C; int forced; const double* extra; int32_t* perm; double* lam; double* isl; double* out;
+};
+constexpr int kSelMax = 16;
+struct SelArgs {
+    SelJob j[kSelMax];
+    double eps, resolution;
+};
+__global__ void __launch_bounds__(1024) k_sort_select(const __grid_constant__ SelArgs A) {
+    const SelJob& J = A.j[blockIdx.x];
+    const int C = J.C;
+    const double* G = J.G;
+    extern __shared__ double s_lam[];                     // [C] sorted, then the suffix sums [C + 1]
+    double* suf = s_lam + C;
     for (int k = threadIdx.x; k < C; k += blockDim.x) {
         const double lk = G[(int64_t)k * C + k];
+        const unsigned long long kk = order_key(lk);
         int rank = 0;
         for (int j = 0; j < C; ++j) {
-            const double lj = G[(int64_t)j * C + j];
-            rank += (lj > lk) || (lj == lk && j < k);
+            const unsigned long long kj = order_key(G[(int64_t)j * C + j]);
+            rank += (kj > kk) || (kj == kk && j < k);
         }
-        perm[rank] = k;
-        lam[rank] = lk;
+        J.perm[rank] = k;
+        s_lam[rank] = lk;
+    }
+    __syncthreads();
+    // suffix sums of max(lambda, 0): suf[k] = sum_{j >= k}, suf[C] = 0 (warp 0)
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, per = (C + 31) / 32, b = lane * per, e = min(C, b + per);
+        double run = 0.0;
+        for (int j = e - 1; j >= b; --j) run += fmax(s_lam[j], 0.0);   // this chunk's total
+        // exclusive scan from the right: the totals of the chunks after this one
+        double after = 0.0, x = run;
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, x, o);
+            if (lane + o < 32) x += y;
+        }
+        after = __shfl_down_sync(0xffffffffu, x, 1);
+        if (lane == 31) after = 0.0;
+        double acc = after;
+        for (int j = e - 1; j >= b; --j) {
+            acc += fmax(s_lam[j], 0.0);
+            suf[j] = acc;
+        }
+        if (lane == 0) suf[C] = 0.0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         // energy outside the compressed problem belongs to the discarded tail
-        const double ex = extra ? fmax(*extra, 0.0) : 0.0;
-        double total = ex;
-        for (int k = C - 1; k >= 0; --k) total += fmax(lam[k], 0.0);
-        int r = C;
-        double tail = ex, tail_at_r = ex;
-        if (forced > 0) {
+        const double ex = J.extra ? fmax(*J.extra, 0.0) : 0.0;
+        const double total = ex + suf[0];
+        int r;
+        double tail_at_r;
+        if (J.forced > 0) {
             // a forced rank is clipped to the eigenvalues the FP64 Gram matrix resolves
             int nres = 0;
-            while (nres < C && lam[nres] > resolution) ++nres;
-            r = max(1, min(min(forced, C), nres));
-            for (int k = C - 1; k >= r; --k) tail += fmax(lam[k], 0.0);
-            tail_at_r = tail;
+            while (nres < C && s_lam[nres] > A.resolution) ++nres;
+            r = max(1, min(min(J.forced, C), nres));
+            tail_at_r = ex + suf[r];
         } else {
-            // suffix sums from the smallest eigenvalue; smallest r >= 1 whose tail qualifies
-            const double lim = eps * eps * total;
-            tail_at_r = ex;
-            r = C;
-            for (int k = C - 1; k >= 1; --k) {
-                tail += fmax(lam[k], 0.0);       // tail = sum_{j >= k}
-                if (tail <= lim) { r = k; tail_at_r = tail; }
-                else break;
+            // smallest r >= 1 whose tail qualifies (the suffix sums only fall with r)
+            const double lim = A.eps * A.eps * total;
+            int lo = 1, hi = C;   // suf[C] = 0 qualifies
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (ex + suf[mid] <= lim) hi = mid;
+                else lo = mid + 1;
             }
+            r = lo;
+            tail_at_r = ex + suf[r];
         }
-        out[0] = (double)r;
-        out[1] = tail_at_r;
-        out[2] = total;
+        J.out[0] = (double)r;
+        J.out[1] = tail_at_r;
+        J.out[2] = total;
     }
-    __syncthreads();
     // lam[] becomes the singular values sigma_k = sqrt(max(lambda_k, 0))
     for (int k = threadIdx.x; k < C; k += blockDim.x) {
-        const double lk = lam[k];
-        isl[k] = lk > 0.0 ? 1.0 / sqrt(lk) : 0.0;
-        lam[k] = sqrt(fmax(lk, 0.0));
+        const double lk = s_lam[k];
+        J.isl[k] = lk > 0.0 ? rsqrt(lk) : 0.0;
+        J.lam[k] = sqrt(fmax(lk, 0.0));
     }
 }
 
@@ -832,7 +872,7 @@ struct StoreRowAcc {     // C[m*ld + n] (+)= v
 template <class K>
 int coop_blocks(K kernel, int threads, size_t smem, int num_sms, int64_t want) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+    if (blocks_per_sm((const void*)kernel, threads, smem, &per_sm) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     int64_t cap = (int64_t)per_sm * num_sms;
     int64_t n = want < cap ? want : cap;
@@ -911,11 +951,11 @@ cudaError_t launch_jacobi_multi(const JacobiJob* jobs, int njobs, int max_sweeps
         want[m] = items <= 2048 ? 1 : (items + 1023) / 1024;
     }
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_jacobi_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = grow_smem((const void*)k_jacobi_multi, smem);
         if (e != cudaSuccess) return e;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_multi, 256, smem) != cudaSuccess || per_sm < 1)
+    if (blocks_per_sm((const void*)k_jacobi_multi, 256, smem, &per_sm) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     const int64_t resident = (int64_t)per_sm * num_sms;
     // a few large jobs: about two CTAs per SM in total (cheaper group barriers); many jobs:
@@ -936,7 +976,7 @@ cudaError_t launch_jacobi_multi(const JacobiJob* jobs, int njobs, int max_sweeps
         JacobiMode* dm = nullptr;
         cudaError_t e = cudaMallocAsync(&dm, sizeof(JacobiMode) * nj, st);
         if (e != cudaSuccess) return e;
-        e = cudaMemcpyAsync(dm, hm.data(), sizeof(JacobiMode) * nj, cudaMemcpyHostToDevice, st);
+        e = upload_h2d(dm, hm.data(), sizeof(JacobiMode) * nj, st);
         if (e == cudaSuccess) {
             JacobiArgs a{dm, nj, max_sweeps > 64 ? 64 : max_sweeps, tol};
             void* args[] = {&a};
@@ -949,12 +989,29 @@ cudaError_t launch_jacobi_multi(const JacobiJob* jobs, int njobs, int max_sweeps
     return cudaSuccess;
 }
 
-cudaError_t launch_sort_select(const double* G, int64_t C, double eps, int forced, double resolution,
-                               const double* extra, int32_t* perm, double* lam, double* inv_sqrt_lam, double* out,
-                               cudaStream_t st) {
-    k_sort_select<<<1, 1024, 0, st>>>(G, (int)C, eps, forced, resolution, extra, perm, lam, inv_sqrt_lam, out);
-    count_kernels(1);
-    return cudaGetLastError();
+cudaError_t launch_sort_select(int n, const SortSelectJob* jobs, double eps, double resolution, cudaStream_t st) {
+    for (int j0 = 0; j0 < n; j0 += kSelMax) {
+        const int nj = std::min(kSelMax, n - j0);
+        SelArgs a{};
+        a.eps = eps;
+        a.resolution = resolution;
+        int cmax = 1;
+        for (int i = 0; i < nj; ++i) {
+            const SortSelectJob& J = jobs[j0 + i];
+            a.j[i] = SelJob{J.G, (int)J.C, J.forced, J.extra, J.perm, J.lam, J.inv_sqrt_lam, J.out};
+            cmax = std::max(cmax, (int)J.C);
+        }
+        const size_t smem = sizeof(double) * (2 * (size_t)cmax + 1);
+        if (smem > 48 * 1024) {
+            cudaError_t e = grow_smem((const void*)k_sort_select, smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_sort_select<<<nj, 1024, smem, st>>>(a);
+        count_kernels(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cudaStream_t st) {
@@ -967,11 +1024,11 @@ cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cud
         want[m] = std::min<int64_t>(1024, std::max<int64_t>(1, (jobs[m].C + 7) / 8));
     }
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_pchol_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = grow_smem((const void*)k_pchol_multi, smem);
         if (e != cudaSuccess) return e;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pchol_multi, 256, smem) != cudaSuccess || per_sm < 1)
+    if (blocks_per_sm((const void*)k_pchol_multi, 256, smem, &per_sm) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     const int64_t resident = (int64_t)per_sm * num_sms;
     const int64_t cap = std::min<int64_t>(resident, std::max<int64_t>(num_sms, njobs));
@@ -989,7 +1046,7 @@ cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cud
         PcholMode* dm = nullptr;
         cudaError_t e = cudaMallocAsync(&dm, sizeof(PcholMode) * nj, st);
         if (e != cudaSuccess) return e;
-        e = cudaMemcpyAsync(dm, hm.data(), sizeof(PcholMode) * nj, cudaMemcpyHostToDevice, st);
+        e = upload_h2d(dm, hm.data(), sizeof(PcholMode) * nj, st);
         if (e == cudaSuccess) {
             PcholArgs a{dm, nj};
             void* args[] = {&a};
@@ -1007,7 +1064,7 @@ cudaError_t launch_chol_inv_multi(const CholJob* jobs, int njobs, int num_sms, c
     std::vector<int64_t> want(njobs);
     for (int m = 0; m < njobs; ++m) want[m] = std::max<int64_t>(1, ((int64_t)jobs[m].r * jobs[m].r + 1023) / 1024);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_inv_multi, 256, 0) != cudaSuccess || per_sm < 1)
+    if (blocks_per_sm((const void*)k_chol_inv_multi, 256, 0, &per_sm) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     const int64_t resident = (int64_t)per_sm * num_sms;
     const int64_t cap = std::min<int64_t>(resident, std::max<int64_t>(num_sms, njobs));
@@ -1025,7 +1082,7 @@ cudaError_t launch_chol_inv_multi(const CholJob* jobs, int njobs, int num_sms, c
         CholMode* dm = nullptr;
         cudaError_t e = cudaMallocAsync(&dm, sizeof(CholMode) * nj, st);
         if (e != cudaSuccess) return e;
-        e = cudaMemcpyAsync(dm, hm.data(), sizeof(CholMode) * nj, cudaMemcpyHostToDevice, st);
+        e = upload_h2d(dm, hm.data(), sizeof(CholMode) * nj, st);
         if (e == cudaSuccess) {
             CholArgs a{dm, nj};
             void* args[] = {&a};

@@ -15,6 +15,8 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "ls_common.cuh"
 
@@ -190,6 +192,36 @@ int smem_cap() {
     return std::max(0, v - 1024);
 }
 
+// The kernel's attributes are set once, and its dynamic shared memory only when a launch
+// needs more than before; whether a 16-CTA cluster fits one GPC is asked once per shared-
+// memory size. (These driver calls cost tens of microseconds of host time each, inside
+// every reduction otherwise.)
+std::mutex g_pc_mu;
+cudaError_t allow_cluster16() {
+    static cudaError_t e = cudaFuncSetAttribute(k_pchol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+cudaError_t reserve_smem(size_t bytes) {
+    static size_t done = 0;
+    std::lock_guard<std::mutex> g(g_pc_mu);
+    if (bytes <= done) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k_pchol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done = bytes;
+    return e;
+}
+bool cluster16_fits(cudaLaunchConfig_t cfg) {
+    static std::map<size_t, bool> known;
+    std::lock_guard<std::mutex> g(g_pc_mu);
+    const auto it = known.find(cfg.dynamicSmemBytes);
+    if (it != known.end()) return it->second;
+    int nclusters = 0;
+    cfg.gridDim = dim3(16);
+    const bool ok = cudaOccupancyMaxActiveClusters(&nclusters, k_pchol_cluster, &cfg) == cudaSuccess && nclusters >= 1;
+    if (!ok) cudaGetLastError();
+    known[cfg.dynamicSmemBytes] = ok;
+    return ok;
+}
+
 }  // namespace
 
 // largest cluster (16, else 8) whose CTAs can hold rows of G and L for C, kmax
@@ -212,14 +244,9 @@ cudaError_t launch_pchol_cluster(const PcholJob* jobs, int njobs, cudaStream_t s
     int cs = pchol_cluster_size(Cmax, kmaxm);
     if (cs == 0) return cudaErrorInvalidValue;
     cudaError_t e;
-    if (cs > 8) {
-        e = cudaFuncSetAttribute(k_pchol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
-    const int rp = (Cmax + cs - 1) / cs;
-    const size_t smem = pc_smem(Cmax, kmaxm, cs, rp);
-    e = cudaFuncSetAttribute(k_pchol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (cs > 8 && (e = allow_cluster16()) != cudaSuccess) return e;
+    size_t smem = pc_smem(Cmax, kmaxm, cs, (Cmax + cs - 1) / cs);
+    if ((e = reserve_smem(smem)) != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -232,15 +259,12 @@ cudaError_t launch_pchol_cluster(const PcholJob* jobs, int njobs, cudaStream_t s
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     // a 16-CTA cluster must fit one GPC: fall back to 8 where it does not
-    if (cs > 8) {
-        int nclusters = 0;
-        cfg.gridDim = dim3((unsigned)cs);
-        if (cudaOccupancyMaxActiveClusters(&nclusters, k_pchol_cluster, &cfg) != cudaSuccess || nclusters < 1) {
-            cudaGetLastError();
-            cs = 8;
-            if (pc_smem(Cmax, kmaxm, cs, (Cmax + cs - 1) / cs) > (size_t)smem_cap()) return cudaErrorInvalidValue;
-            attr[0].val.clusterDim.x = 8;
-        }
+    if (cs > 8 && !cluster16_fits(cfg)) {
+        cs = 8;
+        smem = pc_smem(Cmax, kmaxm, cs, (Cmax + cs - 1) / cs);
+        if (smem > (size_t)smem_cap()) return cudaErrorInvalidValue;
+        if ((e = reserve_smem(smem)) != cudaSuccess) return e;
+        attr[0].val.clusterDim.x = 8;
     }
     const int rp2 = (Cmax + cs - 1) / cs;
     cfg.dynamicSmemBytes = pc_smem(Cmax, kmaxm, cs, rp2);
@@ -252,7 +276,7 @@ cudaError_t launch_pchol_cluster(const PcholJob* jobs, int njobs, cudaStream_t s
     PcMode* dm = nullptr;
     e = cudaMallocAsync(&dm, sizeof(PcMode) * njobs, st);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(dm, hm.data(), sizeof(PcMode) * njobs, cudaMemcpyHostToDevice, st);
+    e = upload_h2d(dm, hm.data(), sizeof(PcMode) * njobs, st);
     if (e == cudaSuccess) {
         PcArgs a{dm, cs, rp2};
         cfg.gridDim = dim3((unsigned)(njobs * cs));

@@ -68,7 +68,7 @@ constexpr int XNST = 2;                             // stages
 constexpr int XTMEM = XSL * TBN;                    // 512 columns
 
 struct X64Job {
-    CUtensorMap a[XSL], b[XSL];
+    CUtensorMap a, b;     // (k, row, slice): the eight digit matrices of each operand
     int M, N, nkb;        // k-blocks of 64 over all of K
     int tiles_n, b0;      // tiles along N; first block of the job
     int transposed;       // D stored at out.p[n * out.ld + m]
@@ -133,9 +133,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_x64_gemm(const __grid_constan
             unsigned char* st = smem + s * XSTAGE;
             mbar_expect_tx(&full[s], XSTAGE);
 #pragma unroll
-            for (int i = 0; i < XSL; ++i) tma_load_3d(st + i * TILE_A, &J.a[i], kx, m0, 0, &full[s]);
+            for (int i = 0; i < XSL; ++i) tma_load_3d(st + i * TILE_A, &J.a, kx, m0, i, &full[s]);
 #pragma unroll
-            for (int j = 0; j < XSL; ++j) tma_load_3d(st + XSL * TILE_A + j * TILE_B, &J.b[j], kx, n0, 0, &full[s]);
+            for (int j = 0; j < XSL; ++j) tma_load_3d(st + XSL * TILE_A + j * TILE_B, &J.b, kx, n0, j, &full[s]);
             issued = kb + 1;
         }
         // every issued stage must have landed before the CTA may exit
@@ -371,9 +371,10 @@ int gemm_x64(const X64Spec* sp, int n, int* flag, cudaStream_t st, std::string* 
         if (kpad % TBK != 0 || s0.B->kpad != kpad || s0.out.mode != OUT_F64)
             return tc_err(err, "x64 gemm: bad operands", LS_ERR_ARG);
         X64Job& J = g.j[i];
-        for (int q = 0; q < XSL; ++q)
-            if (!make_map(&J.a[q], s0.A->d.p[q], s0.M, kpad, 1, TBM) || !make_map(&J.b[q], s0.B->d.p[q], s0.N, kpad, 1, TBN))
-                return tc_err(err, "x64 gemm: cuTensorMapEncodeTiled failed");
+        // the slices of an operand lie rows x kpad apart in one allocation: one map each
+        if (s0.M > s0.A->rows || s0.N > s0.B->rows ||
+            !make_map(&J.a, s0.A->d.p[0], s0.A->rows, kpad, XSL, TBM) || !make_map(&J.b, s0.B->d.p[0], s0.B->rows, kpad, XSL, TBN))
+            return tc_err(err, "x64 gemm: cuTensorMapEncodeTiled failed");
         J.M = (int)s0.M;
         J.N = (int)s0.N;
         J.nkb = (int)(kpad / TBK);

@@ -266,9 +266,11 @@ class LatticeSum:
         return cls(wl.N, wl.box_lo, wl.box_hi, wl.R, wl.sinc_step, t_scale, wl.blocks, precision, stream)
 
     def add_defects(self, defects):
+        """lattice_sum_add_defects for a sequence of Defect descriptions, or for an ls_defect
+        array already built by make_defects (reused across calls without re-marshalling)."""
         if len(defects) == 0:
             return
-        arr = make_defects(defects)
+        arr = defects if isinstance(defects, C.Array) else make_defects(defects)
         _check(self._lib.lattice_sum_add_defects(self.ctx, arr, len(defects)), self.ctx)
 
     def rhosvd_reduce(self, eps: float, forced_ranks: Optional[Sequence[int]] = None) -> dict:
