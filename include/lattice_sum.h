@@ -250,7 +250,7 @@ int lattice_sum_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, 
  *   (device, k x k row-major) the accumulated rotation I + F, whose columns
  *   are the eigenvectors; *sweeps (may be NULL) the sweeps taken.
  * - form 1: one thread-block cluster with the matrix in shared memory
- *   (k up to a device-dependent limit: 224 on GB300). form 2: one cooperative
+ *   (k up to a device-dependent limit: 208 on GB300). form 2: one cooperative
  *   grid with the matrix in global memory (any k). On the same input both
  *   forms give the same D and V.
  * - Synchronises `stream` (a cudaStream_t or NULL).

@@ -142,6 +142,8 @@ constexpr int kBlkThreads = 512;
 // padded strides: E rows K + 4 (16-byte aligned rows, column walks over 8 banks), 16 x 16
 // scratch rows 17 (row-wise walks conflict-free)
 constexpr int SP = BJ2 + 1, SPSQ = BJ2 * SP;
+// rows of F a half-warp updates at a time
+constexpr int kFR = 4;
 
 struct BjArgs {
     const DfMode* m; int max_sweeps; int cs; int rows_per;
@@ -153,7 +155,7 @@ __device__ __forceinline__ int bj_index(int I, int J, int u) { return u < BJ ? I
 // shared-memory layout: offsets in bytes
 struct BjLayout {
     int K, ldE, nb;
-    size_t ctl, D, E, Q, pb, act, tiles, qrem, F;   // CTA 0: ctl D E Q pb act tiles; others: ctl qrem F
+    size_t ctl, D, E, Q, pb, act, tiles, ndep, lists, qrem, F;   // CTA 0: ctl .. lists; others: ctl qrem F
     size_t e_bytes, f_bytes;
     __host__ __device__ BjLayout(int k, int rows_per) {
         int m = (k + BJ - 1) / BJ;
@@ -165,12 +167,14 @@ struct BjLayout {
         D = 16;
         E = D + 8 * (size_t)K;
         Q = E + 4 * (size_t)K * ldE;
-        pb = Q + 4 * (size_t)nb * BJ2SQ;
-        act = pb + 4 * (size_t)nb;
-        tiles = act + 4 * (size_t)nb;
-        e_bytes = tiles + 4 * (size_t)nb * nb;
+        pb = Q + 4 * (size_t)2 * nb * BJ2SQ;                 // Q, pb, act and F_Q: two rounds' worth
+        act = pb + 4 * (size_t)2 * nb;
+        tiles = act + 4 * (size_t)2 * nb;
+        ndep = tiles + 4 * (size_t)nb * nb;
+        lists = ndep + 4 * (size_t)m;
+        e_bytes = lists + (((size_t)m * nb * (nb - 1) / 2 + 15) & ~(size_t)15);
         qrem = 16;
-        F = qrem + 4 * (size_t)nb * SPSQ;
+        F = qrem + 4 * (size_t)2 * nb * SPSQ;
         f_bytes = F + 4 * (size_t)rows_per * K;
     }
 };
@@ -313,6 +317,14 @@ __device__ __forceinline__ unsigned int inner_sweep(float (&x)[BJ2], DF& d, int 
     return nrot;
 }
 
+// Round pipeline of the cluster form. CTA 0 holds D, E, Q and the tables; CTAs 1..cs-1
+// hold rows of F and run the inner sweeps. A round t splits CTA 0's tiles in two: the
+// "dependency" tiles, each holding an 8 x 8 block that round t + 1 pairs (one per pair-block
+// of round t + 1), and the rest. After the dependency tiles a cluster barrier lets CTAs 1..
+// run round t + 1's inner sweeps (and F's update of round t) while CTA 0 finishes the other
+// tiles of round t: those touch no block that round t + 1's inner sweeps read or write. Q,
+// the pair-block table, the rotation flags and F_Q are kept for two rounds (by parity). The
+// last round of a sweep is not overlapped: CTA 0 then scans for a qualifying pair.
 __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank(), cs = A.cs;
@@ -322,32 +334,32 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
     const BjLayout Ly(k, A.rows_per);
     const int K = Ly.K, ldE = Ly.ldE, nb = Ly.nb, m = 2 * nb;
     extern __shared__ __align__(16) unsigned char smem[];
-    // The matrix state lives in CTA 0. The inner sweeps run on every CTA of the cluster,
-    // on CTA 0's state through the cluster's shared-memory window; the tiles run on CTA 0
-    // alone, on its own shared memory; the other CTAs hold rows of F and receive F_Q.
     unsigned char* s0 = rank == 0 ? smem : cl.map_shared_rank(smem, 0);
     int* ctl = reinterpret_cast<int*>(smem + Ly.ctl);       // this CTA's copy of the stop decision
     DF* D = reinterpret_cast<DF*>(s0 + Ly.D);
     float* E = reinterpret_cast<float*>(s0 + Ly.E);
-    float* Q = reinterpret_cast<float*>(s0 + Ly.Q);
-    int* pb = reinterpret_cast<int*>(s0 + Ly.pb);           // this round's pair-blocks: I | J << 16
-    int* act = reinterpret_cast<int*>(s0 + Ly.act);         // pair-block rotated this round
-    float* El = reinterpret_cast<float*>(smem + Ly.E);      // CTA 0's own view of the same
+    float* Qr = reinterpret_cast<float*>(s0 + Ly.Q);         // [2][nb][16][16], Q = I + F_Q
+    int* pbr = reinterpret_cast<int*>(s0 + Ly.pb);           // [2][nb]: I | J << 16
+    int* actr = reinterpret_cast<int*>(s0 + Ly.act);         // [2][nb]: pair-block rotated
+    float* El = reinterpret_cast<float*>(smem + Ly.E);       // CTA 0's own views
     const float* Ql = reinterpret_cast<const float*>(smem + Ly.Q);
     const int* pbl = reinterpret_cast<const int*>(smem + Ly.pb);
     const int* actl = reinterpret_cast<const int*>(smem + Ly.act);
-    const int* tiles = reinterpret_cast<const int*>(smem + Ly.tiles);   // tiles a | b << 8, a < b
-    float* qrem = reinterpret_cast<float*>(smem + Ly.qrem); // CTAs >= 1: F_Q of the pair-blocks
-    float* F = reinterpret_cast<float*>(smem + Ly.F);       // CTAs >= 1: rows j0 .. j1 of F
-    __shared__ unsigned int s_active;                        // CTA 0: rotations of this sweep
+    int* tiles = reinterpret_cast<int*>(smem + Ly.tiles);    // tiles a | b << 8, a < b
+    int* ndep = reinterpret_cast<int*>(smem + Ly.ndep);      // per round: its dependency tiles
+    unsigned char* lists = smem + Ly.lists;                   // per round: dependency tiles, then the rest
+    float* qrem = reinterpret_cast<float*>(smem + Ly.qrem);  // CTAs >= 1: [2][nb] F_Q (rows of SP)
+    float* F = reinterpret_cast<float*>(smem + Ly.F);        // CTAs >= 1: rows j0 .. j1 of F
+    __shared__ unsigned int s_active;                         // CTA 0: rotations of this sweep
     unsigned int* active = rank == 0 ? &s_active : cl.map_shared_rank(&s_active, 0);
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
-    const int slot = warp * cs + rank, nslot = nw * cs;     // warps of the cluster, interleaved over CTAs
     const Crit qualifies{(float)J.abs_floor, (float)J.tau, (float)(J.tol * J.tol)};
     const int j0 = rank >= 1 ? min(K, (rank - 1) * A.rows_per) : 0;
     const int j1 = rank >= 1 ? min(K, j0 + A.rows_per) : 0;
     const int ntile = nb * (nb - 1) / 2;
+    const int nF = cs - 1;                                    // CTAs of F rows and inner sweeps
+    const int iw = (nb + nF - 1) / nF;                        // their warps 0 .. iw-1: inner sweeps
 
     int base = 0;
     if (rank == 0) {
@@ -357,10 +369,44 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
                 E[a * ldE + c] = (a < k && c < k && a != c) ? (float)J.H[(int64_t)a * k + c] : 0.f;
         if (tid == 0) {
             s_active = 0;
-            int* tl = const_cast<int*>(tiles);
             int n = 0;
             for (int a = 0; a < nb; ++a)
-                for (int b = a + 1; b < nb; ++b) tl[n++] = a | (b << 8);
+                for (int b = a + 1; b < nb; ++b) tiles[n++] = a | (b << 8);
+        }
+        __syncthreads();
+        // the tile order of each round t: first the tiles holding a block that round t + 1
+        // pairs (ndep[t] of them), then the others; in the last round of a sweep all tiles in
+        // order (ndep = 0). Round t pairs block X with (2 t - X) mod (m - 1), and m - 1 with t.
+        for (int t = warp; t < m - 1; t += nw) {
+            const bool next = t + 1 < m - 1;
+            const int n1 = m - 1, tt = t + 1;
+            auto partner = [&](int X) { return X == n1 ? tt : X == tt ? n1 : ((2 * tt - X) % n1 + n1) % n1; };
+            auto is_dep = [&](int i) {
+                const int ab = tiles[i];
+                int Ia, Ja, Ib, Jbb;
+                rr_pair_e(t, ab & 255, m, Ia, Ja);
+                rr_pair_e(t, ab >> 8, m, Ib, Jbb);
+                const int pI = partner(Ia), pJ = partner(Ja);
+                return pI == Ib || pI == Jbb || pJ == Ib || pJ == Jbb;
+            };
+            unsigned char* lt = lists + t * ntile;
+            int nd = 0;
+            for (int c0 = 0; c0 < ntile; c0 += 32) {
+                const int i = c0 + lane;
+                const bool dep = next && i < ntile && is_dep(i);
+                const unsigned bal = __ballot_sync(0xffffffffu, dep);
+                if (dep) lt[nd + __popc(bal & ((1u << lane) - 1))] = (unsigned char)i;
+                nd += __popc(bal);
+            }
+            int nr = nd;
+            for (int c0 = 0; c0 < ntile; c0 += 32) {
+                const int i = c0 + lane;
+                const bool rest = i < ntile && !(next && is_dep(i));
+                const unsigned bal = __ballot_sync(0xffffffffu, rest);
+                if (rest) lt[nr + __popc(bal & ((1u << lane) - 1))] = (unsigned char)i;
+                nr += __popc(bal);
+            }
+            if (lane == 0) ndep[t] = nd;
         }
         base = J.st->sweeps;
     } else {
@@ -368,205 +414,232 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
     }
     cl.sync();
 
+    // inner sweep of pair-block sub in round t (CTAs >= 1, warps 0 .. iw-1)
+    auto inner = [&](int t, int sub) {
+        const int par = t & 1;
+        int I, Jb;
+        rr_pair_e(t, sub, m, I, Jb);
+        const int pos = lane & (BJ2 - 1), gi = bj_index(I, Jb, pos);
+        float x[BJ2];
+        DF d{0.f, 0.f};
+        if (lane < BJ2) {
+#pragma unroll
+            for (int r = 0; r < BJ2; ++r) x[r] = E[bj_index(I, Jb, r) * ldE + gi];
+            d = D[gi];
+        } else {
+#pragma unroll
+            for (int r = 0; r < BJ2; ++r) x[r] = 0.f;
+        }
+        unsigned int nrot = t == 0 ? inner_sweep<true>(x, d, I, Jb, k, qualifies)
+                                   : inner_sweep<false>(x, d, I, Jb, k, qualifies);
+        for (int o = 16; o; o >>= 1) nrot += __shfl_xor_sync(0xffffffffu, nrot, o);
+        if (lane < BJ2) {
+#pragma unroll
+            for (int r = 0; r < BJ2; ++r) E[bj_index(I, Jb, r) * ldE + gi] = x[r];
+            D[gi] = d;
+        } else {
+            // F_Q to the F rows' CTAs, Q = I + F_Q to CTA 0
+            for (int c = 1; c < cs; ++c) {
+                float* qr = cl.map_shared_rank(qrem, c) + (size_t)par * nb * SPSQ + sub * SPSQ + pos;
+#pragma unroll
+                for (int r = 0; r < BJ2; ++r) qr[r * SP] = x[r];
+            }
+            float* Qs = Qr + (size_t)par * nb * BJ2SQ + sub * BJ2SQ;
+#pragma unroll
+            for (int r = 0; r < BJ2; ++r) Qs[r * BJ2 + pos] = x[r] + (r == pos ? 1.f : 0.f);
+        }
+        if (lane == 0) {
+            pbr[par * nb + sub] = I | (Jb << 16);
+            actr[par * nb + sub] = nrot > 0;
+            if (nrot) atomicAdd(active, nrot);
+        }
+    };
+    // the inner sweeps of round t on CTAs >= 1
+    auto inner_round = [&](int t) {
+        if (rank >= 1 && warp < iw)
+            for (int sub = (rank - 1) + nF * warp; sub < nb; sub += nF * iw) inner(t, sub);
+    };
+
+    // off-diagonal tiles of round t on CTA 0, tiles lists[l0 .. l1): E_ab <- Q_a^T E_ab Q_b,
+    // two tiles per warp (a half-warp each); lane: rows r0, r0 + 8 of the tile, columns
+    // c0..c0+7 (one block of the column pair-block); the product with Q_b takes the partner
+    // lane's half of the intermediate rows by shuffle
+    auto tile_range = [&](int t, int l0, int l1) {
+        const int par = t & 1;
+        const float* Q = Ql + (size_t)par * nb * BJ2SQ;
+        const int* pb = pbl + par * nb;
+        const int* act = actl + par * nb;
+        float* E = El;
+        const int h = lane >> 4, l16 = lane & 15;
+        const int r0 = l16 >> 1, c0 = (l16 & 1) * BJ;
+        for (int task0 = l0 + 2 * warp; task0 < l1; task0 += 2 * nw) {
+            const int task = task0 + h;
+            const bool live = task < l1;
+            const int ab = tiles[lists[t * ntile + (live ? task : task0)]];
+            const int a = ab & 255, b = ab >> 8;
+            if (__all_sync(0xffffffffu, !live || (!act[a] && !act[b]))) continue;
+            const int pa = pb[a], pbb = pb[b];
+            const int Ia = pa & 0xffff, Ja = pa >> 16, Ib = pbb & 0xffff, Jb2 = pbb >> 16;
+            const float* Qa = Q + a * BJ2SQ;
+            const float* Qb = Q + b * BJ2SQ;
+            const int colb = c0 ? Jb2 * BJ : Ib * BJ;
+            float t0[BJ], t1[BJ];
+#pragma unroll
+            for (int c = 0; c < BJ; ++c) { t0[c] = 0.f; t1[c] = 0.f; }
+#pragma unroll
+            for (int j = 0; j < BJ2; ++j) {
+                const float qa0 = Qa[j * BJ2 + r0], qa1 = Qa[j * BJ2 + r0 + BJ];
+                const float* xr = E + bj_index(Ia, Ja, j) * ldE + colb;
+                const float4 x0 = *reinterpret_cast<const float4*>(xr);
+                const float4 x1 = *reinterpret_cast<const float4*>(xr + 4);
+                const float xv[BJ] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                for (int c = 0; c < BJ; ++c) {
+                    t0[c] = fmaf(qa0, xv[c], t0[c]);
+                    t1[c] = fmaf(qa1, xv[c], t1[c]);
+                }
+            }
+            const int cp = c0 ^ BJ;
+            const int row0 = bj_index(Ia, Ja, r0), row1 = bj_index(Ia, Ja, r0 + BJ);
+#pragma unroll
+            for (int half_row = 0; half_row < 2; ++half_row) {
+                float z[BJ];
+#pragma unroll
+                for (int c = 0; c < BJ; ++c) z[c] = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < BJ; ++jj) {
+                    const float tv = half_row ? t1[jj] : t0[jj];
+                    const float ov = __shfl_xor_sync(0xffffffffu, tv, 1);
+                    const float4 qs0 = *reinterpret_cast<const float4*>(Qb + (c0 + jj) * BJ2 + c0);
+                    const float4 qs1 = *reinterpret_cast<const float4*>(Qb + (c0 + jj) * BJ2 + c0 + 4);
+                    const float4 qo0 = *reinterpret_cast<const float4*>(Qb + (cp + jj) * BJ2 + c0);
+                    const float4 qo1 = *reinterpret_cast<const float4*>(Qb + (cp + jj) * BJ2 + c0 + 4);
+                    z[0] = fmaf(tv, qs0.x, fmaf(ov, qo0.x, z[0]));
+                    z[1] = fmaf(tv, qs0.y, fmaf(ov, qo0.y, z[1]));
+                    z[2] = fmaf(tv, qs0.z, fmaf(ov, qo0.z, z[2]));
+                    z[3] = fmaf(tv, qs0.w, fmaf(ov, qo0.w, z[3]));
+                    z[4] = fmaf(tv, qs1.x, fmaf(ov, qo1.x, z[4]));
+                    z[5] = fmaf(tv, qs1.y, fmaf(ov, qo1.y, z[5]));
+                    z[6] = fmaf(tv, qs1.z, fmaf(ov, qo1.z, z[6]));
+                    z[7] = fmaf(tv, qs1.w, fmaf(ov, qo1.w, z[7]));
+                }
+                // every lane has read this tile's E rows (first product) before any store
+                __syncwarp();
+                if (live) {
+                    const int row = half_row ? row1 : row0;
+                    float* w = E + row * ldE + colb;
+                    *reinterpret_cast<float4*>(w) = make_float4(z[0], z[1], z[2], z[3]);
+                    *reinterpret_cast<float4*>(w + 4) = make_float4(z[4], z[5], z[6], z[7]);
+#pragma unroll
+                    for (int c = 0; c < BJ; ++c) E[(colb + c) * ldE + row] = z[c];
+                }
+            }
+            __syncwarp();
+        }
+    };
+    // F <- F + F_Q + F F_Q for round t on this CTA's rows (CTAs >= 1), by the half-warps of
+    // warps w0 .. nw-1: a half-warp per pair-block and a group of rows; lane x of the half
+    // holds column x of F_Q in registers
+    auto f_update = [&](int t, int w0) {
+        if (rank < 1 || warp < w0) return;
+        const float* fqs = qrem + (size_t)(t & 1) * nb * SPSQ;
+        const int hw = (tid - 32 * w0) >> 4, x = tid & 15, nhw = (nthr - 32 * w0) >> 4;
+        const unsigned int half = 0xffffu << (lane & 16);
+        const int nr = j1 - j0;
+        const int groups = max(1, nhw / nb);
+        for (int task = hw; task < groups * nb; task += nhw) {
+            const int a = task % nb, g = task / nb;
+            int Ia, Ja;
+            rr_pair_e(t, a, m, Ia, Ja);
+            float fcol[BJ2];
+            bool nz = false;
+#pragma unroll
+            for (int y = 0; y < BJ2; ++y) {
+                fcol[y] = fqs[a * SPSQ + y * SP + x];
+                nz |= fcol[y] != 0.f;
+            }
+            // F_Q = 0 (no rotation in this pair-block): F is unchanged
+            const bool any = __any_sync(half, nz);
+            // kFR rows at a time (independent chains; each element's sum keeps its order)
+            for (int jl0 = g * kFR; jl0 < nr && any; jl0 += groups * kFR) {
+                float acc[kFR];
+#pragma unroll
+                for (int q = 0; q < kFR; ++q) {
+                    const int jl = jl0 + q;
+                    if (jl >= nr) break;
+                    const int j = j0 + jl;
+                    const float* row = F + (size_t)jl * K;
+                    const float4 f0 = *reinterpret_cast<const float4*>(row + Ia * BJ);
+                    const float4 f1 = *reinterpret_cast<const float4*>(row + Ia * BJ + 4);
+                    const float4 f2 = *reinterpret_cast<const float4*>(row + Ja * BJ);
+                    const float4 f3 = *reinterpret_cast<const float4*>(row + Ja * BJ + 4);
+                    const float fv[BJ2] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w,
+                                           f2.x, f2.y, f2.z, f2.w, f3.x, f3.y, f3.z, f3.w};
+                    float v = row[bj_index(Ia, Ja, x)];
+#pragma unroll
+                    for (int y = 0; y < BJ2; ++y) v = fmaf(fv[y], fcol[y], v);
+                    // row j of F_Q (embedded) when j is one of the pair-block's indices
+                    const int bj = j / BJ;
+                    if (bj == Ia) v += fqs[a * SPSQ + (j - Ia * BJ) * SP + x];
+                    else if (bj == Ja) v += fqs[a * SPSQ + (BJ + j - Ja * BJ) * SP + x];
+                    acc[q] = v;
+                }
+                // every lane has read these rows before any store
+                __syncwarp(half);
+#pragma unroll
+                for (int q = 0; q < kFR; ++q)
+                    if (jl0 + q < nr) F[(size_t)(jl0 + q) * K + bj_index(Ia, Ja, x)] = acc[q];
+            }
+        }
+    };
+
     int sweep = 0;
-    bool done = false;
-    for (; sweep <= A.max_sweeps && !done; ++sweep) {
+    for (; sweep <= A.max_sweeps; ++sweep) {
+        // sweep start: CTA 0 records the finished sweep's rotations and looks for a pair that
+        // qualifies; every CTA reads the decision after the barrier
+        if (rank == 0) {
+            int need = 0;
+            for (int a = warp; a < k && !need; a += nw)
+                for (int c = a + 1 + lane; c < k; c += 32)
+                    if (qualifies(D[a], D[c], El[a * ldE + c])) { need = 1; break; }
+            need = __syncthreads_or(need);
+            if (tid == 0) {
+                int stop = 0;
+                if (!need) stop = 1;
+                else if (sweep == A.max_sweeps) {
+                    stop = 1;
+                    atomicCAS(&J.st->flag, FLAG_OK, FLAG_NOCONVERGE);
+                }
+                if (sweep > 0) J.st->sweep_active[(base + sweep - 1) & 63] = s_active;
+                s_active = 0;
+                for (int c = 0; c < cs; ++c) cl.map_shared_rank(ctl, c)[0] = stop;
+            }
+        }
+        cl.sync();
+        if (ctl[0]) break;
+        inner_round(0);
+        cl.sync();
         for (int t = 0; t < m - 1; ++t) {
-            if (t == 0) {
-                // sweep start: CTA 0 records the finished sweep's rotations and looks for a pair
-                // that qualifies; every CTA reads the decision after the barrier
-                if (rank == 0) {
-                    int need = 0;
-                    for (int a = warp; a < k && !need; a += nw)
-                        for (int c = a + 1 + lane; c < k; c += 32)
-                            if (qualifies(D[a], D[c], E[a * ldE + c])) { need = 1; break; }
-                    need = __syncthreads_or(need);
-                    if (tid == 0) {
-                        int stop = 0;
-                        if (!need) stop = 1;
-                        else if (sweep == A.max_sweeps) {
-                            stop = 1;
-                            atomicCAS(&J.st->flag, FLAG_OK, FLAG_NOCONVERGE);
-                        }
-                        if (sweep > 0) J.st->sweep_active[(base + sweep - 1) & 63] = s_active;
-                        s_active = 0;
-                        for (int c = 0; c < cs; ++c) cl.map_shared_rank(ctl, c)[0] = stop;
-                    }
-                }
+            const bool next = t + 1 < m - 1;   // round t + 1 is in this sweep: overlap it
+            const int nd = rank == 0 ? ndep[t] : 0;
+            if (rank == 0) tile_range(t, 0, nd);
+            if (next) {
                 cl.sync();
-                if (ctl[0]) { done = true; break; }
-            }
-            // the inner sweeps, a warp per pair-block over the cluster (their indices are
-            // disjoint), in registers: lanes 0..15 the columns of the subproblem and its
-            // diagonal, lanes 16..31 the columns of F_Q. The first round of a sweep gives each
-            // pair-block a full inner sweep (every pair within its two blocks); the other
-            // rounds only pair the two blocks' indices with each other (8 inner rounds), as
-            // every block's own pairs were rotated this sweep.
-            for (int sub = slot; sub < nb; sub += nslot) {
-                int I, Jb;
-                rr_pair_e(t, sub, m, I, Jb);
-                const int pos = lane & (BJ2 - 1), gi = bj_index(I, Jb, pos);
-                float x[BJ2];
-                DF d{0.f, 0.f};
-                if (lane < BJ2) {
-#pragma unroll
-                    for (int r = 0; r < BJ2; ++r) x[r] = E[bj_index(I, Jb, r) * ldE + gi];
-                    d = D[gi];
-                } else {
-#pragma unroll
-                    for (int r = 0; r < BJ2; ++r) x[r] = 0.f;
-                }
-                unsigned int nrot = t == 0 ? inner_sweep<true>(x, d, I, Jb, k, qualifies)
-                                           : inner_sweep<false>(x, d, I, Jb, k, qualifies);
-                for (int o = 16; o; o >>= 1) nrot += __shfl_xor_sync(0xffffffffu, nrot, o);
-                if (lane < BJ2) {
-#pragma unroll
-                    for (int r = 0; r < BJ2; ++r) E[bj_index(I, Jb, r) * ldE + gi] = x[r];
-                    D[gi] = d;
-                } else {
-                    // F_Q to the F rows' CTAs, Q = I + F_Q to CTA 0
-                    for (int c = 1; c < cs; ++c) {
-                        float* qr = cl.map_shared_rank(qrem, c) + sub * SPSQ + pos;
-#pragma unroll
-                        for (int r = 0; r < BJ2; ++r) qr[r * SP] = x[r];
-                    }
-#pragma unroll
-                    for (int r = 0; r < BJ2; ++r) Q[sub * BJ2SQ + r * BJ2 + pos] = x[r] + (r == pos ? 1.f : 0.f);
-                }
-                if (lane == 0) {
-                    pb[sub] = I | (Jb << 16);
-                    act[sub] = nrot > 0;
-                    if (nrot) atomicAdd(active, nrot);
-                }
-            }
-            cl.sync();
-            // off-diagonal tiles (a < b) on CTA 0: E_ab <- Q_a^T E_ab Q_b, two tiles per warp (a
-            // half-warp each); lane: rows r0, r0 + 8 of the tile, columns c0..c0+7 (one block of
-            // the column pair-block). The product with Q_b takes the partner lane's half of the
-            // intermediate rows by shuffle.
-            if (rank == 0) {
-                const int h = lane >> 4, l16 = lane & 15;
-                const int r0 = l16 >> 1, c0 = (l16 & 1) * BJ;
-                float* E = El;
-                const float* Q = Ql;
-                const int* pb = pbl;
-                const int* act = actl;
-                for (int task0 = 2 * warp; task0 < ntile; task0 += 2 * nw) {
-                    const int task = task0 + h;
-                    const bool live = task < ntile;
-                    const int ab = live ? tiles[task] : tiles[task0];
-                    const int a = ab & 255, b = ab >> 8;
-                    // a tile between two pair-blocks that did not rotate is unchanged (Q = I on both
-                    // sides); the warp skips when both of its tiles are such
-                    if (__all_sync(0xffffffffu, !live || (!act[a] && !act[b]))) continue;
-                    const int pa = pb[a], pbb = pb[b];
-                    const int Ia = pa & 0xffff, Ja = pa >> 16, Ib = pbb & 0xffff, Jb2 = pbb >> 16;
-                    const float* Qa = Q + a * BJ2SQ;
-                    const float* Qb = Q + b * BJ2SQ;
-                    const int colb = c0 ? Jb2 * BJ : Ib * BJ;   // first E column of this lane's 8
-                    float t0[BJ], t1[BJ];
-#pragma unroll
-                    for (int c = 0; c < BJ; ++c) { t0[c] = 0.f; t1[c] = 0.f; }
-#pragma unroll
-                    for (int j = 0; j < BJ2; ++j) {
-                        const float qa0 = Qa[j * BJ2 + r0], qa1 = Qa[j * BJ2 + r0 + BJ];
-                        const float* xr = E + bj_index(Ia, Ja, j) * ldE + colb;
-                        const float4 x0 = *reinterpret_cast<const float4*>(xr);
-                        const float4 x1 = *reinterpret_cast<const float4*>(xr + 4);
-                        const float xv[BJ] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-#pragma unroll
-                        for (int c = 0; c < BJ; ++c) {
-                            t0[c] = fmaf(qa0, xv[c], t0[c]);
-                            t1[c] = fmaf(qa1, xv[c], t1[c]);
-                        }
-                    }
-                    // Z[r][c0 + c] = sum_j T[r][j] Qb[j][c0 + c], one row at a time; T[r][j] for j in
-                    // this lane's block from t, for the other block from the partner lane (lane ^ 1)
-                    const int cp = c0 ^ BJ;
-                    const int row0 = bj_index(Ia, Ja, r0), row1 = bj_index(Ia, Ja, r0 + BJ);
-#pragma unroll
-                    for (int half_row = 0; half_row < 2; ++half_row) {
-                        float z[BJ];
-#pragma unroll
-                        for (int c = 0; c < BJ; ++c) z[c] = 0.f;
-#pragma unroll
-                        for (int jj = 0; jj < BJ; ++jj) {
-                            const float tv = half_row ? t1[jj] : t0[jj];
-                            const float ov = __shfl_xor_sync(0xffffffffu, tv, 1);
-                            const float4 qs0 = *reinterpret_cast<const float4*>(Qb + (c0 + jj) * BJ2 + c0);
-                            const float4 qs1 = *reinterpret_cast<const float4*>(Qb + (c0 + jj) * BJ2 + c0 + 4);
-                            const float4 qo0 = *reinterpret_cast<const float4*>(Qb + (cp + jj) * BJ2 + c0);
-                            const float4 qo1 = *reinterpret_cast<const float4*>(Qb + (cp + jj) * BJ2 + c0 + 4);
-                            z[0] = fmaf(tv, qs0.x, fmaf(ov, qo0.x, z[0]));
-                            z[1] = fmaf(tv, qs0.y, fmaf(ov, qo0.y, z[1]));
-                            z[2] = fmaf(tv, qs0.z, fmaf(ov, qo0.z, z[2]));
-                            z[3] = fmaf(tv, qs0.w, fmaf(ov, qo0.w, z[3]));
-                            z[4] = fmaf(tv, qs1.x, fmaf(ov, qo1.x, z[4]));
-                            z[5] = fmaf(tv, qs1.y, fmaf(ov, qo1.y, z[5]));
-                            z[6] = fmaf(tv, qs1.z, fmaf(ov, qo1.z, z[6]));
-                            z[7] = fmaf(tv, qs1.w, fmaf(ov, qo1.w, z[7]));
-                        }
-                        // every lane has read this tile's E rows (first product) before any store
-                        __syncwarp();
-                        if (live) {
-                            const int row = half_row ? row1 : row0;
-                            float* w = E + row * ldE + colb;
-                            *reinterpret_cast<float4*>(w) = make_float4(z[0], z[1], z[2], z[3]);
-                            *reinterpret_cast<float4*>(w + 4) = make_float4(z[4], z[5], z[6], z[7]);
-#pragma unroll
-                            for (int c = 0; c < BJ; ++c) E[(colb + c) * ldE + row] = z[c];
-                        }
-                    }
-                    __syncwarp();
-                }
-            }
-            if (rank >= 1) {
-                // F <- F + F_Q + F F_Q on this CTA's rows: a half-warp per pair-block and a group
-                // of rows; lane x of the half holds column x of F_Q in registers
-                const int hw = tid >> 4, x = tid & 15, nhw = nthr >> 4;
-                const unsigned int half = 0xffffu << (lane & 16);
-                const int nr = j1 - j0;
-                const int groups = max(1, nhw / nb);
-                if (hw < groups * nb) {
-                    const int a = hw % nb, g = hw / nb;
-                    int Ia, Ja;
-                    rr_pair_e(t, a, m, Ia, Ja);
-                    float fcol[BJ2];
-                    bool nz = false;
-#pragma unroll
-                    for (int y = 0; y < BJ2; ++y) {
-                        fcol[y] = qrem[a * SPSQ + y * SP + x];
-                        nz |= fcol[y] != 0.f;
-                    }
-                    // F_Q = 0 (no rotation in this pair-block): F is unchanged
-                    const bool any = __any_sync(half, nz);
-                    for (int jl = g; jl < nr && any; jl += groups) {
-                        const int j = j0 + jl;
-                        float* row = F + (size_t)jl * K;
-                        const float4 f0 = *reinterpret_cast<const float4*>(row + Ia * BJ);
-                        const float4 f1 = *reinterpret_cast<const float4*>(row + Ia * BJ + 4);
-                        const float4 f2 = *reinterpret_cast<const float4*>(row + Ja * BJ);
-                        const float4 f3 = *reinterpret_cast<const float4*>(row + Ja * BJ + 4);
-                        const float fv[BJ2] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w,
-                                               f2.x, f2.y, f2.z, f2.w, f3.x, f3.y, f3.z, f3.w};
-                        float acc = row[bj_index(Ia, Ja, x)];
-#pragma unroll
-                        for (int y = 0; y < BJ2; ++y) acc = fmaf(fv[y], fcol[y], acc);
-                        // row j of F_Q (embedded) when j is one of the pair-block's indices
-                        const int bj = j / BJ;
-                        if (bj == Ia) acc += qrem[a * SPSQ + (j - Ia * BJ) * SP + x];
-                        else if (bj == Ja) acc += qrem[a * SPSQ + (BJ + j - Ja * BJ) * SP + x];
-                        __syncwarp(half);
-                        row[bj_index(Ia, Ja, x)] = acc;
-                    }
-                }
+                // CTA 0: the other tiles of round t; CTAs >= 1: round t + 1's inner sweeps and
+                // round t's F update on their other warps
+                if (rank == 0) tile_range(t, nd, ntile);
+                inner_round(t + 1);
+                f_update(t, iw);
+            } else {
+                if (rank == 0) tile_range(t, nd, ntile);
+                f_update(t, 0);
             }
             cl.sync();
         }
     }
     if (rank == 0) {
         for (int a = tid; a < k; a += nthr) J.outD[(int64_t)a * J.ldd] = df_to(D[a]);
-        if (tid == 0) J.st->sweeps = base + sweep - 1;
+        if (tid == 0) J.st->sweeps = base + sweep;
     } else {
         for (int e = tid; e < (j1 - j0) * K; e += nthr) {
             const int jl = e / K, n = e - jl * K;

@@ -59,7 +59,7 @@ def _run(H, form, tol=1e-7):
     return D.cpu().numpy(), V.cpu().numpy(), sweeps
 
 
-@pytest.mark.parametrize("k,spectrum", [(40, "graded"), (185, "graded"), (200, "clustered"), (17, "graded")])
+@pytest.mark.parametrize("k,spectrum", [(40, "graded"), (185, "graded"), (200, "clustered"), (17, "graded"), (208, "graded")])
 def test_grid_form_equals_cluster_form(k, spectrum):
     H, _ = _matrix(k, 100 + k, spectrum)
     D1, V1, s1 = _run(H, 1)
