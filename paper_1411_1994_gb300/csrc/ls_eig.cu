@@ -114,6 +114,16 @@ struct Crit {
     }
 };
 
+// the device's SM count (queried once)
+int sm_count() {
+    static const int n = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 1;
+        return std::max(1, v);
+    }();
+    return n;
+}
 // dynamic shared memory available to the kernel (its static variables take a few bytes)
 int smem_optin() {
     int dev = 0, v = 0;
@@ -348,7 +358,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
     int* tiles = reinterpret_cast<int*>(smem + Ly.tiles);    // tiles a | b << 8, a < b
     int* ndep = reinterpret_cast<int*>(smem + Ly.ndep);      // per round: its dependency tiles
     unsigned char* lists = smem + Ly.lists;                   // per round: dependency tiles, then the rest
-    float* qrem = reinterpret_cast<float*>(smem + Ly.qrem);  // CTAs >= 1: [2][nb] F_Q (rows of SP)
+    float* qrem = reinterpret_cast<float*>(smem + Ly.qrem);  // CTAs >= 1: [2][nb] F_Q of own pair-blocks
     float* F = reinterpret_cast<float*>(smem + Ly.F);        // CTAs >= 1: rows j0 .. j1 of F
     __shared__ unsigned int s_active;                         // CTA 0: rotations of this sweep
     unsigned int* active = rank == 0 ? &s_active : cl.map_shared_rank(&s_active, 0);
@@ -438,12 +448,11 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
             for (int r = 0; r < BJ2; ++r) E[bj_index(I, Jb, r) * ldE + gi] = x[r];
             D[gi] = d;
         } else {
-            // F_Q to the F rows' CTAs, Q = I + F_Q to CTA 0
-            for (int c = 1; c < cs; ++c) {
-                float* qr = cl.map_shared_rank(qrem, c) + (size_t)par * nb * SPSQ + sub * SPSQ + pos;
+            // F_Q here (the F updates of the other CTAs read it through the cluster window),
+            // Q = I + F_Q to CTA 0
+            float* qr = qrem + (size_t)par * nb * SPSQ + sub * SPSQ + pos;
 #pragma unroll
-                for (int r = 0; r < BJ2; ++r) qr[r * SP] = x[r];
-            }
+            for (int r = 0; r < BJ2; ++r) qr[r * SP] = x[r];
             float* Qs = Qr + (size_t)par * nb * BJ2SQ + sub * BJ2SQ;
 #pragma unroll
             for (int r = 0; r < BJ2; ++r) Qs[r * BJ2 + pos] = x[r] + (r == pos ? 1.f : 0.f);
@@ -537,13 +546,20 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
             __syncwarp();
         }
     };
-    // F <- F + F_Q + F F_Q for round t on this CTA's rows (CTAs >= 1), by the half-warps of
-    // warps w0 .. nw-1: a half-warp per pair-block and a group of rows; lane x of the half
-    // holds column x of F_Q in registers
-    auto f_update = [&](int t, int w0) {
-        if (rank < 1 || warp < w0) return;
-        const float* fqs = qrem + (size_t)(t & 1) * nb * SPSQ;
-        const int hw = (tid - 32 * w0) >> 4, x = tid & 15, nhw = (nthr - 32 * w0) >> 4;
+    // F <- F + F_Q + F F_Q for round t on this CTA's rows (CTAs >= 1), by half-warps: a
+    // half-warp per pair-block and a group of rows; lane x of the half holds column x of F_Q in
+    // registers. Beside the inner sweeps (overlap) only the warps on the other SMSPs of the SM
+    // take part (warp w runs on SMSP w mod 4), so the inner sweeps' latency-bound chains keep
+    // their issue slots; otherwise every warp does.
+    auto f_update = [&](int t, bool overlap) {
+        if (rank < 1) return;
+        const int par = t & 1;
+        const bool split = overlap && iw < 4;
+        if (split && (warp & 3) < iw) return;
+        if (overlap && !split && warp < iw) return;
+        const int nwp = split ? (nw >> 2) * (4 - iw) : overlap ? nw - iw : nw;
+        const int wi = split ? (warp >> 2) * (4 - iw) + (warp & 3) - iw : overlap ? warp - iw : warp;
+        const int hw = 2 * wi + (lane >> 4), x = lane & 15, nhw = 2 * nwp;
         const unsigned int half = 0xffffu << (lane & 16);
         const int nr = j1 - j0;
         const int groups = max(1, nhw / nb);
@@ -551,11 +567,13 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
             const int a = task % nb, g = task / nb;
             int Ia, Ja;
             rr_pair_e(t, a, m, Ia, Ja);
+            // F_Q of pair-block a, from the CTA that ran its inner sweep
+            const float* fq = cl.map_shared_rank(qrem, 1 + a % nF) + (size_t)par * nb * SPSQ + a * SPSQ;
             float fcol[BJ2];
             bool nz = false;
 #pragma unroll
             for (int y = 0; y < BJ2; ++y) {
-                fcol[y] = fqs[a * SPSQ + y * SP + x];
+                fcol[y] = fq[y * SP + x];
                 nz |= fcol[y] != 0.f;
             }
             // F_Q = 0 (no rotation in this pair-block): F is unchanged
@@ -580,8 +598,8 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
                     for (int y = 0; y < BJ2; ++y) v = fmaf(fv[y], fcol[y], v);
                     // row j of F_Q (embedded) when j is one of the pair-block's indices
                     const int bj = j / BJ;
-                    if (bj == Ia) v += fqs[a * SPSQ + (j - Ia * BJ) * SP + x];
-                    else if (bj == Ja) v += fqs[a * SPSQ + (BJ + j - Ja * BJ) * SP + x];
+                    if (bj == Ia) v += pick16(fcol, j - Ia * BJ);
+                    else if (bj == Ja) v += pick16(fcol, BJ + j - Ja * BJ);
                     acc[q] = v;
                 }
                 // every lane has read these rows before any store
@@ -629,10 +647,10 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
                 // round t's F update on their other warps
                 if (rank == 0) tile_range(t, nd, ntile);
                 inner_round(t + 1);
-                f_update(t, iw);
+                f_update(t, true);
             } else {
                 if (rank == 0) tile_range(t, nd, ntile);
-                f_update(t, 0);
+                f_update(t, false);
             }
             cl.sync();
         }
@@ -1060,8 +1078,10 @@ cudaError_t launch_jacobi_blk(const DfJob* jobs, int njobs, int max_sweeps, cuda
     const BjLayout L0(kmax, 1);
     // one thread per rotation of an inner round
     if (L0.e_bytes > (size_t)cap || L0.nb * (BJ2 / 2) > kBlkThreads) return cudaErrorInvalidValue;
-    // F rows over nF CTAs (the F update carries about as much work as the tiles)
-    int nF = 3;
+    // F rows and inner sweeps over nF CTAs: seven (an 8-CTA cluster, two inner sweeps a CTA on
+    // their own SMSPs) while every cluster of the launch fits on the GPU at once; else three, so
+    // that twice as many matrices run side by side
+    int nF = njobs * 8 <= sm_count() ? 7 : 3;
     int rows_per = (L0.K + nF - 1) / nF;
     while (BjLayout(kmax, rows_per).f_bytes > (size_t)cap && nF < 7) rows_per = (L0.K + ++nF - 1) / nF;
     const BjLayout L1(kmax, rows_per);

@@ -40,9 +40,13 @@ def _lib():
     L.lib()
 
 
+# 6 lattices: 18 eigen-problems, each in an 8-CTA cluster (all fit on the GPU at once); 8
+# lattices: 24, more than 8-CTA clusters can hold side by side on 152 SMs, so the launch takes
+# 4-CTA clusters, while each individual reduction (3 problems) keeps 8-CTA ones
+@pytest.mark.parametrize("n", [6, 8])
 @pytest.mark.parametrize("precision", [L.LS_FP64, L.LS_MIXED])
-def test_batch_matches_individual_reductions(precision):
-    wls = small_batch()
+def test_batch_matches_individual_reductions(precision, n):
+    wls = small_batch(n)
     scales = [O.fit_t_scale(w.R, w.sinc_step, w.r_min, O.default_r_max(w))[0] for w in wls]
     batch = []
     for w, s in zip(wls, scales):
