@@ -469,6 +469,70 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
             for (int sub = (rank - 1) + nF * warp; sub < nb; sub += nF * iw) inner(t, sub);
     };
 
+    // the same tile rotation with a whole warp per tile (lanes 16..31 take the tile's rows 8..15),
+    // for the few tiles that the next round waits for: half the latency, the same arithmetic
+    auto tile_wide = [&](int t, int l0, int l1) {
+        const int par = t & 1;
+        const float* Q = Ql + (size_t)par * nb * BJ2SQ;
+        const int* pb = pbl + par * nb;
+        const int* act = actl + par * nb;
+        float* E = El;
+        const int l16 = lane & 15;
+        const int rr = (l16 >> 1) + BJ * (lane >> 4), c0 = (l16 & 1) * BJ;
+        for (int task = l0 + warp; task < l1; task += nw) {
+            const int ab = tiles[lists[t * ntile + task]];
+            const int a = ab & 255, b = ab >> 8;
+            if (!act[a] && !act[b]) continue;
+            const int pa = pb[a], pbb = pb[b];
+            const int Ia = pa & 0xffff, Ja = pa >> 16, Ib = pbb & 0xffff, Jb2 = pbb >> 16;
+            const float* Qa = Q + a * BJ2SQ;
+            const float* Qb = Q + b * BJ2SQ;
+            const int colb = c0 ? Jb2 * BJ : Ib * BJ;
+            float t0[BJ];
+#pragma unroll
+            for (int c = 0; c < BJ; ++c) t0[c] = 0.f;
+#pragma unroll
+            for (int j = 0; j < BJ2; ++j) {
+                const float qa = Qa[j * BJ2 + rr];
+                const float* xr = E + bj_index(Ia, Ja, j) * ldE + colb;
+                const float4 x0 = *reinterpret_cast<const float4*>(xr);
+                const float4 x1 = *reinterpret_cast<const float4*>(xr + 4);
+                const float xv[BJ] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                for (int c = 0; c < BJ; ++c) t0[c] = fmaf(qa, xv[c], t0[c]);
+            }
+            const int cp = c0 ^ BJ;
+            float z[BJ];
+#pragma unroll
+            for (int c = 0; c < BJ; ++c) z[c] = 0.f;
+#pragma unroll
+            for (int jj = 0; jj < BJ; ++jj) {
+                const float tv = t0[jj];
+                const float ov = __shfl_xor_sync(0xffffffffu, tv, 1);
+                const float4 qs0 = *reinterpret_cast<const float4*>(Qb + (c0 + jj) * BJ2 + c0);
+                const float4 qs1 = *reinterpret_cast<const float4*>(Qb + (c0 + jj) * BJ2 + c0 + 4);
+                const float4 qo0 = *reinterpret_cast<const float4*>(Qb + (cp + jj) * BJ2 + c0);
+                const float4 qo1 = *reinterpret_cast<const float4*>(Qb + (cp + jj) * BJ2 + c0 + 4);
+                z[0] = fmaf(tv, qs0.x, fmaf(ov, qo0.x, z[0]));
+                z[1] = fmaf(tv, qs0.y, fmaf(ov, qo0.y, z[1]));
+                z[2] = fmaf(tv, qs0.z, fmaf(ov, qo0.z, z[2]));
+                z[3] = fmaf(tv, qs0.w, fmaf(ov, qo0.w, z[3]));
+                z[4] = fmaf(tv, qs1.x, fmaf(ov, qo1.x, z[4]));
+                z[5] = fmaf(tv, qs1.y, fmaf(ov, qo1.y, z[5]));
+                z[6] = fmaf(tv, qs1.z, fmaf(ov, qo1.z, z[6]));
+                z[7] = fmaf(tv, qs1.w, fmaf(ov, qo1.w, z[7]));
+            }
+            // every lane has read this tile's E rows before any store
+            __syncwarp();
+            const int row = bj_index(Ia, Ja, rr);
+            float* w = E + row * ldE + colb;
+            *reinterpret_cast<float4*>(w) = make_float4(z[0], z[1], z[2], z[3]);
+            *reinterpret_cast<float4*>(w + 4) = make_float4(z[4], z[5], z[6], z[7]);
+#pragma unroll
+            for (int c = 0; c < BJ; ++c) E[(colb + c) * ldE + row] = z[c];
+            __syncwarp();
+        }
+    };
     // off-diagonal tiles of round t on CTA 0, tiles lists[l0 .. l1): E_ab <- Q_a^T E_ab Q_b,
     // two tiles per warp (a half-warp each); lane: rows r0, r0 + 8 of the tile, columns
     // c0..c0+7 (one block of the column pair-block); the product with Q_b takes the partner
@@ -640,7 +704,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_jacobi_blk(BjArgs A) {
         for (int t = 0; t < m - 1; ++t) {
             const bool next = t + 1 < m - 1;   // round t + 1 is in this sweep: overlap it
             const int nd = rank == 0 ? ndep[t] : 0;
-            if (rank == 0) tile_range(t, 0, nd);
+            if (rank == 0) tile_wide(t, 0, nd);
             if (next) {
                 cl.sync();
                 // CTA 0: the other tiles of round t; CTAs >= 1: round t + 1's inner sweeps and
