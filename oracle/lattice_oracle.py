@@ -16,9 +16,13 @@ matrix products only where the definition is a contraction.
 
 Parity status: every function here is pinned by the CPU tests
 (tests/test_oracle_pins.py) to closed forms, exact identities, brute-force
-1/|x-a| sums or the paper's error bound -- except ``fit_t_scale``, whose
-optimality is not pinned (only the error it reports is, by recomputation on a
-denser r-grid).
+1/|x-a| (and exp(-kappa |x-a|)/|x-a|) sums or the paper's error bound --
+except ``fit_t_scale``, whose optimality is not pinned (only the error it
+reports is, by recomputation on a denser r-grid).
+
+Kernels: the Newton kernel 1/r (kappa = 0) and the Yukawa kernel
+exp(-kappa r)/r (kappa > 0, Sec. 2.3, Eq. LalpYukawa), which share the sinc
+rule and differ only in the quadrature weights.
 """
 from __future__ import annotations
 
@@ -35,8 +39,10 @@ POINT = 1   # a defect that adds a charge at an arbitrary position
 # (a0) quadrature and generating vectors, Sec. 2.1
 # ---------------------------------------------------------------------------
 
-def sinc_quadrature(R: int, sinc_step: float, t_scale: float) -> Tuple[np.ndarray, np.ndarray]:
-    """Nodes t_q and weights w_q of the rank-R separable expansion of 1/r.
+def sinc_quadrature(R: int, sinc_step: float, t_scale: float,
+                    kappa: float = 0.0) -> Tuple[np.ndarray, np.ndarray]:
+    """Nodes t_q and weights w_q of the rank-R separable expansion of the
+    kernel: 1/r for kappa = 0, exp(-kappa r)/r for kappa > 0.
 
     Sec. 2.1, Eqs. (laplace), (hM), (sinc_Newt): 1/r = (2/sqrt(pi)) int_0^inf
     exp(-r^2 t^2) dt, discretised by a sinc rule with nodes on a uniform
@@ -47,25 +53,49 @@ def sinc_quadrature(R: int, sinc_step: float, t_scale: float) -> Tuple[np.ndarra
     R = M + 1 distinct Gaussians, q = 0..R-1:
         t_q = sinh(q h) / s,
         w_0 = h / (s sqrt(pi)),  w_q = 2 h cosh(q h) / (s sqrt(pi))  (q >= 1).
+
+    Yukawa (Sec. 2.3, Eq. LalpYukawa with rho = r^2): the Laplace-Gauss form
+    exp(-kappa r)/r = (2/sqrt(pi)) int_0^inf exp(-kappa^2/(4 t^2)) exp(-r^2 t^2) dt.
+    Reading: the printed exponent kappa^2/t^2 gives exp(-2 kappa r)/r; the
+    factor 1/4 is the one for which the identity holds (a pinned test
+    integrates both). The same sinc rule applies with each weight multiplied
+    by exp(-kappa^2/(4 t_q^2)); that factor is 0 at t_0 = 0, so the R nodes
+    are q = 1..R, each weight 2 h cosh(q h)/(s sqrt(pi)) exp(-kappa^2/(4 t_q^2)).
     """
-    q = np.arange(R, dtype=np.float64)
+    if kappa < 0.0:
+        raise ValueError("kappa must be >= 0")
+    q = np.arange(R, dtype=np.float64) + (1.0 if kappa > 0.0 else 0.0)
     u = q * sinc_step
     t = np.sinh(u) / t_scale
     w = 2.0 * sinc_step * np.cosh(u) / (t_scale * math.sqrt(math.pi))
-    w[0] = sinc_step / (t_scale * math.sqrt(math.pi))
+    if kappa > 0.0:
+        w = w * np.exp(-(kappa * kappa) / (4.0 * t * t))
+    else:
+        w[0] = sinc_step / (t_scale * math.sqrt(math.pi))
     return t, w
 
 
-def quadrature_rel_error(t: np.ndarray, w: np.ndarray, r: np.ndarray) -> np.ndarray:
-    """|r * sum_q w_q exp(-t_q^2 r^2) - 1|: relative error of the separable
-    expansion of 1/r at distances r (Sec. 2.1, Eq. sinc_conv)."""
+def kernel_value(r, kappa: float = 0.0):
+    """The kernel p(r): 1/r, or exp(-kappa r)/r (Sec. 2.3, Eq. LalpYukawa)."""
+    r = np.asarray(r, dtype=np.float64)
+    return np.exp(-kappa * r) / r
+
+
+def quadrature_rel_error(t: np.ndarray, w: np.ndarray, r: np.ndarray, kappa: float = 0.0) -> np.ndarray:
+    """r |sum_q w_q exp(-t_q^2 r^2) - p(r)|: the error of the separable
+    expansion of the kernel p at distances r, relative to 1/r (Sec. 2.1, Eq.
+    sinc_conv bounds the absolute error by C/a e^(-beta sqrt(M)) for r >= a).
+    For the Newton kernel this is the relative error |r sum - 1|. For the
+    Yukawa kernel it is the error relative to the unscreened 1/r: the relative
+    error of exp(-kappa r)/r itself, many decades down at large kappa r, is
+    neither reachable with a few terms nor felt in a lattice sum."""
     r = np.asarray(r, dtype=np.float64)
     s = np.exp(-np.outer(r * r, t * t)) @ w
-    return np.abs(r * s - 1.0)
+    return np.abs(r * s - np.exp(-kappa * r))
 
 
 def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float,
-                n_r: int = 600) -> Tuple[float, float]:
+                n_r: int = 600, kappa: float = 0.0) -> Tuple[float, float]:
     """Scale s of the substitution t = sinh(u)/s that minimises the maximum
     relative error of the expansion over [r_min, r_max] (Sec. 2.1: M, and here
     s, are chosen so that the kernel is reproduced to a tolerance; the paper's
@@ -74,8 +104,8 @@ def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float,
     r = np.geomspace(r_min, r_max, n_r)
 
     def err(log_s):
-        t, w = sinc_quadrature(R, sinc_step, math.exp(log_s))
-        return float(np.max(quadrature_rel_error(t, w, r)))
+        t, w = sinc_quadrature(R, sinc_step, math.exp(log_s), kappa)
+        return float(np.max(quadrature_rel_error(t, w, r, kappa)))
 
     grid = np.linspace(math.log(1e-2), math.log(1e5), 241)
     vals = [err(x) for x in grid]
@@ -306,10 +336,11 @@ def charged_centres(N, box_lo, box_hi, blocks, defects):
     return pos, z
 
 
-def brute_force(points: np.ndarray, centres: np.ndarray, charges: np.ndarray):
-    """Direct sum sum_nu Z_nu / |x - a_nu| (Eq. EwaldSumE with p = 1/r) at the
-    given points; also returns sum_nu |Z_nu| / |x - a_nu| and the minimum and
-    maximum distance to a centre, which bound the quadrature error."""
+def brute_force(points: np.ndarray, centres: np.ndarray, charges: np.ndarray, kappa: float = 0.0):
+    """Direct sum sum_nu Z_nu p(|x - a_nu|) (Eq. EwaldSumE; p = 1/r, or
+    exp(-kappa r)/r) at the given points; also returns sum_nu |Z_nu| p(|x - a_nu|)
+    and the minimum and maximum distance to a centre, which bound the
+    quadrature error."""
     points = np.atleast_2d(points)
     val = np.zeros(len(points))
     absval = np.zeros(len(points))
@@ -318,8 +349,9 @@ def brute_force(points: np.ndarray, centres: np.ndarray, charges: np.ndarray):
     for c0 in range(0, len(centres), 256):
         c = centres[c0:c0 + 256]
         d = np.sqrt(((points[:, None, :] - c[None, :, :]) ** 2).sum(-1))
-        val += (charges[c0:c0 + 256] / d).sum(1)
-        absval += (np.abs(charges[c0:c0 + 256]) / d).sum(1)
+        pd = np.exp(-kappa * d) / d
+        val += (charges[c0:c0 + 256] * pd).sum(1)
+        absval += (np.abs(charges[c0:c0 + 256]) * pd).sum(1)
         dmin = np.minimum(dmin, d.min(1))
         dmax = np.maximum(dmax, d.max(1))
     return val, absval, dmin, dmax
@@ -441,8 +473,8 @@ def full_from_canonical(cols, tcol, xi) -> np.ndarray:
 def pipeline(wl, t_scale: float, core: bool = True, ranks=None):
     """Quadrature -> generating vectors -> assembled and defect terms ->
     RHOSVD, for a workload description (N, box, R, sinc step, blocks,
-    defects, eps). Returns (terms, rhosvd result)."""
-    t, w = sinc_quadrature(wl.R, wl.sinc_step, t_scale)
+    defects, eps; kappa for the Yukawa kernel). Returns (terms, rhosvd result)."""
+    t, w = sinc_quadrature(wl.R, wl.sinc_step, t_scale, getattr(wl, "kappa", 0.0))
     g = generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w)
     cols, tcol, xi = canonical_terms(wl.N, wl.box_lo, wl.box_hi, g, wl.blocks, wl.defects)
     res = rhosvd(cols, tcol, xi, wl.eps, ranks=ranks, core=core)

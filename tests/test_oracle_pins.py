@@ -77,6 +77,77 @@ def test_fitted_scale_error_holds_on_dense_grid():
     assert dense < 1e-7
 
 
+# --- (a0) the Yukawa kernel: Sec. 2.3, Eq. LalpYukawa ----------------------
+
+def test_yukawa_laplace_gauss_identity_and_reading():
+    """By a plain trapezoid rule in t: (2/sqrt(pi)) int exp(-kappa^2/(4 t^2))
+    exp(-r^2 t^2) dt = exp(-kappa r)/r, the identity the oracle's weights use;
+    the exponent kappa^2/t^2 as printed integrates to exp(-2 kappa r)/r."""
+    tt = np.linspace(1e-9, 40.0, 800001)
+    for kappa, r in ((0.8, 0.7), (1.5, 2.0), (0.3, 5.0)):
+        quarter = (2.0 / math.sqrt(math.pi)) * np.trapezoid(np.exp(-kappa ** 2 / (4 * tt ** 2) - (r * tt) ** 2), tt)
+        printed = (2.0 / math.sqrt(math.pi)) * np.trapezoid(np.exp(-kappa ** 2 / tt ** 2 - (r * tt) ** 2), tt)
+        assert abs(quarter - math.exp(-kappa * r) / r) <= 1e-12 * math.exp(-kappa * r) / r + 1e-15
+        assert abs(printed - math.exp(-2 * kappa * r) / r) <= 1e-12 * math.exp(-2 * kappa * r) / r + 1e-15
+
+
+def test_fine_sinc_rule_reproduces_yukawa():
+    """A fine rule reproduces exp(-kappa r)/r to ~machine precision relative to
+    the kernel itself; a dropped screening factor, a wrong 1/4 or keeping the
+    zero-weight node t_0 = 0 leaves an O(1) error somewhere on the range."""
+    for kappa in (0.4, 0.8, 2.0):
+        t, w = O.sinc_quadrature(400, 0.05, 10.0, kappa)
+        assert t[0] > 0.0 and np.all(w >= 0.0) and np.all(np.diff(t) > 0.0)
+        r = np.geomspace(0.05, 20.0, 2000)
+        approx = np.exp(-np.outer(r * r, t * t)) @ w
+        assert np.max(np.abs(approx / (np.exp(-kappa * r) / r) - 1.0)) < 1e-11
+        assert np.max(O.quadrature_rel_error(t, w, r, kappa)) < 1e-12
+    # kappa = 0 is the Newton rule, bit for bit
+    t0, w0 = O.sinc_quadrature(24, 0.25, 13.0, 0.0)
+    t1, w1 = O.sinc_quadrature(24, 0.25, 13.0)
+    assert np.array_equal(t0, t1) and np.array_equal(w0, w1)
+
+
+def test_yukawa_fitted_scale_error_holds_on_dense_grid():
+    """For the 16^3 lattice's rank and range (R = 24, h = 0.25, r in
+    [0.25, sqrt(3) b]) and kappa = 0.5 the fitted rule's error relative to 1/r
+    is below 1e-6 and holds on a 10x denser grid."""
+    wl = W.config2()
+    rmax = O.default_r_max(wl)
+    s, e = O.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, rmax, kappa=0.5)
+    t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s, 0.5)
+    dense = np.max(O.quadrature_rel_error(t, w, np.geomspace(wl.r_min, rmax, 6000), 0.5))
+    assert dense < 1.2 * e
+    assert dense < 1e-6
+
+
+def test_yukawa_lattice_against_brute_force():
+    """A defected lattice with the Yukawa kernel: canonical tensor values at
+    sampled grid points vs the direct sum of Z exp(-kappa d)/d over the snapped
+    centres, within tau * sum |Z|/d (tau: the rule's error relative to 1/r)."""
+    wl = W.small_case(L=(4, 3, 3), N=60, R=20, frac_vac=0.2, frac_imp=0.1, kappa=0.6)
+    rmax = O.default_r_max(wl)
+    s, _ = O.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, rmax, kappa=wl.kappa)
+    t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s, wl.kappa)
+    g = O.generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w)
+    cols, tcol, xi = O.canonical_terms(wl.N, wl.box_lo, wl.box_hi, g, wl.blocks, wl.defects)
+    xs = O.cell_centres(wl.N, wl.box_lo, wl.box_hi)
+    rng = np.random.default_rng(4)
+    idx = rng.integers(0, wl.N, size=(20000, 3))
+    centres, charges = O.charged_centres(wl.N, wl.box_lo, wl.box_hi, wl.blocks, wl.defects)
+    bf, _, dmin, _ = O.brute_force(xs[idx], centres, charges, kappa=wl.kappa)
+    _, abs_newton, _, _ = O.brute_force(xs[idx], centres, charges)
+    keep = dmin >= wl.r_min
+    tens = (xi[:, None] * cols[0][tcol[:, 0]][:, idx[keep, 0]] * cols[1][tcol[:, 1]][:, idx[keep, 1]]
+            * cols[2][tcol[:, 2]][:, idx[keep, 2]]).sum(0)
+    tau = float(np.max(O.quadrature_rel_error(t, w, np.geomspace(wl.r_min, rmax, 6000), wl.kappa)))
+    err = np.abs(tens - bf[keep])
+    assert np.all(err <= tau * abs_newton[keep] * 1.001 + 1e-13)
+    # the screening is real: the Newton sum differs by far more than that
+    nb, _, _, _ = O.brute_force(xs[idx[keep]], centres, charges)
+    assert np.min(np.abs(nb - bf[keep]) - err) > 0.0
+
+
 # --- generating vectors and windows: Eqs. master_pot, sub_tens -------------
 
 def test_reference_tensor_reproduces_kernel():
