@@ -31,7 +31,12 @@
  *  - Reference vectors live on the doubled grid: g_q[j] = w_q^(1/3)
  *    exp(-t_q^2 ((j - N + 1/2) h)^2), j = 0..2N-1, with the sinc nodes
  *    t_q = sinh(q s_h)/t_scale, w_0 = s_h/(t_scale sqrt(pi)),
- *    w_q = 2 s_h cosh(q s_h)/(t_scale sqrt(pi)), q = 0..R-1 (s_h = sinc_step).
+ *    w_q = 2 s_h cosh(q s_h)/(t_scale sqrt(pi)), q = 0..R-1 (s_h = sinc_step)
+ *    for the Newton kernel 1/r. For the Yukawa kernel exp(-kappa r)/r
+ *    (kappa > 0; Sec. 2.3, Eq. LalpYukawa, read as exp(-kappa r)/r =
+ *    (2/sqrt(pi)) int exp(-kappa^2/(4 t^2)) exp(-r^2 t^2) dt) every weight is
+ *    multiplied by exp(-kappa^2/(4 t_q^2)) and the nodes are q = 1..R (the
+ *    node t = 0 has weight 0); row q - 1 of the reference vectors holds node q.
  *  - A window of a centre at vertex m is (W_m g_q)[i] = g_q[i - m + N].
  *  - Return value: LS_OK (0) or a negative LS_ERR_* code; the message is
  *    available from lattice_sum_last_error(ctx). A call made in the wrong
@@ -109,6 +114,9 @@ typedef struct {
                         /* lattice_sum_fit_t_scale                                       */
     int32_t precision;  /* LS_FP64 or LS_MIXED                                           */
     int32_t flags;      /* reserved, must be 0                                           */
+    double  kappa;      /* Yukawa screening: kernel exp(-kappa r)/r; 0 = Newton 1/r.    */
+                        /* Finite, >= 0, and small enough that the first node's         */
+                        /* factor exp(-kappa^2/(4 t_1^2)) keeps kappa^2/(4 t_1^2) <= 600 */
 } ls_params;
 
 typedef struct {
@@ -156,12 +164,25 @@ int lattice_sum_fit_t_scale(int32_t R, double sinc_step, double r_min, double r_
                             double* t_scale_out, double* max_rel_err_out);
 
 /*
+ * lattice_sum_fit_t_scale_kernel -- the same fit for the kernel of a given
+ * kappa (0: the Newton kernel, identical to lattice_sum_fit_t_scale; > 0: the
+ * Yukawa kernel exp(-kappa r)/r of Sec. 2.3, Eq. LalpYukawa). The error
+ * minimised is max_r r |sum_q w_q exp(-t_q^2 r^2) - p(r)|, the rule's error
+ * relative to 1/r (Eq. sinc_conv bounds the absolute error); for kappa = 0 it
+ * is the relative error above. LS_ERR_ARG on bad input (kappa < 0 or not
+ * finite included).
+ */
+int lattice_sum_fit_t_scale_kernel(int32_t R, double sinc_step, double kappa, double r_min, double r_max,
+                                   double* t_scale_out, double* max_rel_err_out);
+
+/*
  * lattice_sum_create -- reference vectors and assembled lattice sums.
  * Thm 3.1(A): for each block, mode l and rank index q the canonical vector
  * v[i] = sum_k g_q[i - m_k + N] over the block's L_l snapped site vertices
  * m_k. `blocks` (host, nblocks >= 1 entries) are copied. `stream` is a
  * cudaStream_t or NULL. On success *out holds a new context.
- * Errors: LS_ERR_ARG (bad sizes, a site outside the box), LS_ERR_OOM,
+ * Errors: LS_ERR_ARG (bad sizes, a site outside the box, kappa < 0 or too
+ * large for the sinc rule), LS_ERR_OOM,
  * LS_ERR_CUDA.
  */
 int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* blocks,

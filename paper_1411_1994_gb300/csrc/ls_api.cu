@@ -217,18 +217,25 @@ int append_columns(ls_ctx* ctx, int l, const std::vector<int32_t>& q, const std:
     return LS_OK;
 }
 
-double quad_max_err(int R, double hs, double s, const std::vector<double>& r) {
+// max over r of r |sum_q w_q exp(-t_q^2 r^2) - p(r)|, p(r) = exp(-kappa r)/r: the rule's error
+// relative to 1/r (the relative error for the Newton kernel, kappa = 0). Yukawa (Eq.
+// LalpYukawa with the Laplace-Gauss factor 1/4): each weight times exp(-kappa^2/(4 t_q^2)),
+// nodes q = 1..R (the node t = 0 has weight 0).
+double quad_max_err(int R, double hs, double s, double kappa, const std::vector<double>& r) {
     std::vector<double> t(R), w(R);
     const double spi = 1.7724538509055160273;
-    for (int q = 0; q < R; ++q) {
-        t[q] = sinh(q * hs) / s;
-        w[q] = (q == 0) ? hs / (s * spi) : 2.0 * hs * cosh(q * hs) / (s * spi);
+    const int q0 = kappa > 0.0 ? 1 : 0;
+    for (int i = 0; i < R; ++i) {
+        const int q = i + q0;
+        t[i] = sinh(q * hs) / s;
+        w[i] = (q == 0) ? hs / (s * spi) : 2.0 * hs * cosh(q * hs) / (s * spi);
+        if (kappa > 0.0) w[i] *= exp(-kappa * kappa / (4.0 * t[i] * t[i]));
     }
     double e = 0.0;
     for (double x : r) {
         double acc = 0.0;
-        for (int q = 0; q < R; ++q) acc += w[q] * exp(-t[q] * t[q] * x * x);
-        e = std::max(e, fabs(x * acc - 1.0));
+        for (int i = 0; i < R; ++i) acc += w[i] * exp(-t[i] * t[i] * x * x);
+        e = std::max(e, fabs(x * acc - exp(-kappa * x)));
     }
     return e;
 }
@@ -264,8 +271,14 @@ extern "C" {
 
 int lattice_sum_fit_t_scale(int32_t R, double sinc_step, double r_min, double r_max, double* t_scale_out,
                             double* max_rel_err_out) {
+    return lattice_sum_fit_t_scale_kernel(R, sinc_step, 0.0, r_min, r_max, t_scale_out, max_rel_err_out);
+}
+
+int lattice_sum_fit_t_scale_kernel(int32_t R, double sinc_step, double kappa, double r_min, double r_max,
+                                   double* t_scale_out, double* max_rel_err_out) {
     ls_ctx* ctx = nullptr;
-    if (R < 1 || R > 256 || !(sinc_step > 0) || !(r_min > 0) || !(r_max > r_min) || !t_scale_out)
+    if (R < 1 || R > 256 || !(sinc_step > 0) || !(r_min > 0) || !(r_max > r_min) || !t_scale_out ||
+        !(kappa >= 0.0) || !std::isfinite(kappa))
         return fail(ctx, LS_ERR_ARG, "fit_t_scale: bad arguments");
     std::vector<double> r(600);
     for (int i = 0; i < 600; ++i) r[i] = r_min * pow(r_max / r_min, i / 599.0);
@@ -275,21 +288,21 @@ int lattice_sum_fit_t_scale(int32_t R, double sinc_step, double r_min, double r_
     std::vector<double> xs(ns), es(ns);
     for (int i = 0; i < ns; ++i) {
         xs[i] = lo + (hi - lo) * i / (ns - 1);
-        es[i] = quad_max_err(R, sinc_step, exp(xs[i]), r);
+        es[i] = quad_max_err(R, sinc_step, exp(xs[i]), kappa, r);
         if (es[i] < best) { best = es[i]; bx = i; }
     }
     int bi = (int)bx;
     double a = xs[std::max(bi - 1, 0)], b = xs[std::min(bi + 1, ns - 1)];
     const double gr = (sqrt(5.0) - 1.0) / 2.0;
     double c = b - gr * (b - a), d = a + gr * (b - a);
-    double fc = quad_max_err(R, sinc_step, exp(c), r), fd = quad_max_err(R, sinc_step, exp(d), r);
+    double fc = quad_max_err(R, sinc_step, exp(c), kappa, r), fd = quad_max_err(R, sinc_step, exp(d), kappa, r);
     for (int it = 0; it < 60; ++it) {
-        if (fc < fd) { b = d; d = c; fd = fc; c = b - gr * (b - a); fc = quad_max_err(R, sinc_step, exp(c), r); }
-        else { a = c; c = d; fc = fd; d = a + gr * (b - a); fd = quad_max_err(R, sinc_step, exp(d), r); }
+        if (fc < fd) { b = d; d = c; fd = fc; c = b - gr * (b - a); fc = quad_max_err(R, sinc_step, exp(c), kappa, r); }
+        else { a = c; c = d; fc = fd; d = a + gr * (b - a); fd = quad_max_err(R, sinc_step, exp(d), kappa, r); }
     }
     const double x = 0.5 * (a + b);
     *t_scale_out = exp(x);
-    if (max_rel_err_out) *max_rel_err_out = quad_max_err(R, sinc_step, exp(x), r);
+    if (max_rel_err_out) *max_rel_err_out = quad_max_err(R, sinc_step, exp(x), kappa, r);
     return LS_OK;
 }
 
@@ -305,6 +318,14 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
     if (!(p.sinc_step > 0) || !(p.t_scale > 0)) return fail(ctx, LS_ERR_ARG, "create: sinc_step and t_scale must be > 0");
     if (p.precision != LS_FP64 && p.precision != LS_MIXED) return fail(ctx, LS_ERR_ARG, "create: unknown precision %d", p.precision);
     if (p.flags != 0) return fail(ctx, LS_ERR_ARG, "create: flags must be 0");
+    if (!(p.kappa >= 0.0) || !std::isfinite(p.kappa)) return fail(ctx, LS_ERR_ARG, "create: kappa must be finite and >= 0");
+    if (p.kappa > 0.0) {
+        // the smallest node's screening factor exp(-kappa^2/(4 t_1^2)) must not underflow
+        const double t1 = sinh(p.sinc_step) / p.t_scale;
+        if (p.kappa * p.kappa / (4.0 * t1 * t1) > 600.0)
+            return fail(ctx, LS_ERR_ARG, "create: kappa=%g too large for the sinc rule (t_1 = %g): its weight underflows",
+                        p.kappa, t1);
+    }
     ctx = new ls_ctx();
     ctx->p = p;
     ctx->st = static_cast<cudaStream_t>(stream);
@@ -343,7 +364,7 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
     {
         cudaError_t e2 = dalloc(ctx, &ctx->d_g, (int64_t)R * 2 * N);
         Scope sc_gen("genvec", ctx->st);
-        if (e2 == cudaSuccess) e2 = launch_genvec(ctx->d_g, R, N, ctx->h, p.sinc_step, p.t_scale, ctx->st);
+        if (e2 == cudaSuccess) e2 = launch_genvec(ctx->d_g, R, N, ctx->h, p.sinc_step, p.t_scale, p.kappa, ctx->st);
         if (e2 != cudaSuccess) rc = fail(ctx, LS_ERR_CUDA, "create: %s", cudaGetErrorString(e2));
     }
     for (int l = 0; l < 3 && rc == LS_OK; ++l) {

@@ -69,9 +69,10 @@ void set_global_error(const char* msg);
 // launchers implemented in ls_f64.cu (all enqueue on `st`, return cudaError)
 // ---------------------------------------------------------------------------
 
-// G0: g[q][j] = w_q^(1/3) exp(-t_q^2 ((j - N + 1/2) h)^2), q < R, j < 2N.
+// G0: g[q][j] = w_q^(1/3) exp(-t_q^2 ((j - N + 1/2) h)^2), q < R, j < 2N; for kappa > 0 the
+// Yukawa rule (nodes q + 1, weights times exp(-kappa^2/(4 t^2))).
 cudaError_t launch_genvec(double* g, int R, int64_t N, double h, double sinc_step, double t_scale,
-                          cudaStream_t st);
+                          double kappa, cudaStream_t st);
 
 // G1/G2: out[c][i] = sum_{k<wcnt[c]} g[colq[c]][i - win[woff[c]+k] + N],
 // for columns c in [c0, c0 + ncols); out has row stride N.

@@ -23,7 +23,7 @@ LS_OUT_F64, LS_OUT_F32 = 0, 1
 (LS_READ_GENVEC, LS_READ_COLUMNS, LS_READ_NORMS, LS_READ_TERMS, LS_READ_XI, LS_READ_SIGMA,
  LS_READ_BASIS, LS_READ_PROJ, LS_READ_CORE) = range(9)
 
-EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_create", "lattice_sum_add_defects",
+EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_fit_t_scale_kernel", "lattice_sum_create", "lattice_sum_add_defects",
             "lattice_sum_rhosvd_reduce", "lattice_sum_eval_slab", "lattice_sum_get_factors",
             "lattice_sum_read", "lattice_sum_profile", "lattice_sum_profile_report",
             "lattice_sum_eval_slab_noalloc", "lattice_sum_batch_reduce", "lattice_sum_gemm_nt",
@@ -34,7 +34,7 @@ EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_create", "lattice_sum_add_de
 class ls_params(C.Structure):
     _fields_ = [("N", C.c_int64), ("box_lo", C.c_double), ("box_hi", C.c_double), ("R", C.c_int32),
                 ("sinc_step", C.c_double), ("t_scale", C.c_double), ("precision", C.c_int32),
-                ("flags", C.c_int32)]
+                ("flags", C.c_int32), ("kappa", C.c_double)]
 
 
 class ls_block(C.Structure):
@@ -73,6 +73,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     P = C.POINTER
     lib.lattice_sum_fit_t_scale.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_double, P(C.c_double),
                                             P(C.c_double)]
+    lib.lattice_sum_fit_t_scale_kernel.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double,
+                                                   P(C.c_double), P(C.c_double)]
     lib.lattice_sum_create.argtypes = [P(C.c_void_p), P(ls_params), P(ls_block), C.c_int32, C.c_void_p]
     lib.lattice_sum_add_defects.argtypes = [C.c_void_p, P(ls_defect), C.c_int64]
     lib.lattice_sum_rhosvd_reduce.argtypes = [C.c_void_p, C.c_double, P(C.c_int32), P(ls_tucker_info)]
@@ -212,9 +214,12 @@ def jacobi_eig(H, tol: float = 1e-7, abs_floor: float = 0.0, form: int = 2):
     return D, V, sw.value
 
 
-def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float):
+def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float, kappa: float = 0.0):
     s, e = C.c_double(), C.c_double()
-    _check(lib().lattice_sum_fit_t_scale(R, sinc_step, r_min, r_max, C.byref(s), C.byref(e)))
+    if kappa == 0.0:
+        _check(lib().lattice_sum_fit_t_scale(R, sinc_step, r_min, r_max, C.byref(s), C.byref(e)))
+    else:
+        _check(lib().lattice_sum_fit_t_scale_kernel(R, sinc_step, kappa, r_min, r_max, C.byref(s), C.byref(e)))
     return s.value, e.value
 
 
@@ -247,10 +252,11 @@ class LatticeSum:
     """One lattice-sum context: create -> add_defects -> rhosvd_reduce ->
     eval_slab, each a direct call of the C ABI."""
 
-    def __init__(self, N, box_lo, box_hi, R, sinc_step, t_scale, blocks, precision=LS_FP64, stream=None):
+    def __init__(self, N, box_lo, box_hi, R, sinc_step, t_scale, blocks, precision=LS_FP64, stream=None,
+                 kappa=0.0):
         self._lib = lib()
         p = ls_params(int(N), float(box_lo), float(box_hi), int(R), float(sinc_step), float(t_scale),
-                      int(precision), 0)
+                      int(precision), 0, float(kappa))
         self._blocks = make_blocks(blocks)
         ctx = C.c_void_p()
         rc = self._lib.lattice_sum_create(C.byref(ctx), C.byref(p), self._blocks, len(blocks),
@@ -263,7 +269,8 @@ class LatticeSum:
 
     @classmethod
     def from_workload(cls, wl, t_scale, precision=LS_FP64, stream=None):
-        return cls(wl.N, wl.box_lo, wl.box_hi, wl.R, wl.sinc_step, t_scale, wl.blocks, precision, stream)
+        return cls(wl.N, wl.box_lo, wl.box_hi, wl.R, wl.sinc_step, t_scale, wl.blocks, precision, stream,
+                   getattr(wl, "kappa", 0.0))
 
     def add_defects(self, defects):
         """lattice_sum_add_defects for a sequence of Defect descriptions, or for an ls_defect

@@ -22,6 +22,11 @@ MUTATIONS = {
     "defect_sign": ("return defect.charge - blocks[defect.block].charge",
                     "return blocks[defect.block].charge - defect.charge"),
     "norms_not_in_xi": ("xin = xin * norms[a][tcol[:, a]]", "xin = xin"),
+    "yukawa_printed_exponent": ("w = w * np.exp(-(kappa * kappa) / (4.0 * t * t))",
+                                "w = w * np.exp(-(kappa * kappa) / (t * t))"),
+    "yukawa_factor_inverted": ("w = w * np.exp(-(kappa * kappa) / (4.0 * t * t))",
+                               "w = w * np.exp(-(kappa * kappa) * (t * t) / 4.0)"),
+    "yukawa_unscreened_brute_force": ("pd = np.exp(-kappa * d) / d", "pd = 1.0 / d"),
 }
 
 
