@@ -20,9 +20,13 @@ Parity status: every function here is pinned by the CPU tests
 except ``fit_t_scale``, whose optimality is not pinned (only the error it
 reports is, by recomputation on a denser r-grid).
 
-Kernels: the Newton kernel 1/r (kappa = 0) and the Yukawa kernel
-exp(-kappa r)/r (kappa > 0, Sec. 2.3, Eq. LalpYukawa), which share the sinc
-rule and differ only in the quadrature weights.
+Kernels (Sec. 2.3, Eqs. LalpSlater, LalpYukawa, LalpNewt, LalpPoly), all as a
+Laplace-Gauss integral p(r) = int_0^inf a(t) exp(-r^2 t^2) dt, so that they
+share the sinc rule and differ only in the quadrature weights:
+  YUKAWA (0): exp(-kappa r)/r, a = (2/sqrt(pi)) exp(-kappa^2/(4 t^2));
+              kappa = 0 is the Newton kernel 1/r;
+  SLATER (1): exp(-kappa r), a = (kappa/sqrt(pi)) t^-2 exp(-kappa^2/(4 t^2));
+  DIPOLE (2): 1/r^3, a = (4/sqrt(pi)) t^2 (kappa = 0).
 """
 from __future__ import annotations
 
@@ -30,6 +34,8 @@ import math
 from typing import List, Sequence, Tuple
 
 import numpy as np
+
+YUKAWA, SLATER, DIPOLE = 0, 1, 2   # kernel families (YUKAWA with kappa = 0: Newton)
 
 SITES = 0   # a defect that replaces the charge of a box of lattice sites
 POINT = 1   # a defect that adds a charge at an arbitrary position
@@ -40,7 +46,7 @@ POINT = 1   # a defect that adds a charge at an arbitrary position
 # ---------------------------------------------------------------------------
 
 def sinc_quadrature(R: int, sinc_step: float, t_scale: float,
-                    kappa: float = 0.0) -> Tuple[np.ndarray, np.ndarray]:
+                    kappa: float = 0.0, kernel: int = YUKAWA) -> Tuple[np.ndarray, np.ndarray]:
     """Nodes t_q and weights w_q of the rank-R separable expansion of the
     kernel: 1/r for kappa = 0, exp(-kappa r)/r for kappa > 0.
 
@@ -61,9 +67,28 @@ def sinc_quadrature(R: int, sinc_step: float, t_scale: float,
     integrates both). The same sinc rule applies with each weight multiplied
     by exp(-kappa^2/(4 t_q^2)); that factor is 0 at t_0 = 0, so the R nodes
     are q = 1..R, each weight 2 h cosh(q h)/(s sqrt(pi)) exp(-kappa^2/(4 t_q^2)).
+
+    Slater exp(-kappa r) (Eq. LalpSlater with its parameter kappa_S = kappa^2/4
+    and rho = r^2, then t -> t^2): a(t) = (kappa/sqrt(pi)) t^-2
+    exp(-kappa^2/(4 t^2)). Dipole 1/r^3 (Eq. LalpPoly extended to n = 3/2 with
+    Gamma(3/2) = sqrt(pi)/2, then t -> t^2): a(t) = (4/sqrt(pi)) t^2. Both
+    vanish at t = 0, so again q = 1..R, with w_q = 2 h cosh(q h)/s * a(t_q) / 2
+    (the merged +q and -q terms of the rule for (1/2) int_R a(t(u)) t'(u) du).
     """
     if kappa < 0.0:
         raise ValueError("kappa must be >= 0")
+    if kernel in (SLATER, DIPOLE):
+        if (kernel == SLATER) != (kappa > 0.0):
+            raise ValueError("the Slater kernel needs kappa > 0, the dipole kernel kappa = 0")
+        q = np.arange(R, dtype=np.float64) + 1.0
+        u = q * sinc_step
+        t = np.sinh(u) / t_scale
+        if kernel == SLATER:
+            a = (kappa / math.sqrt(math.pi)) / (t * t) * np.exp(-(kappa * kappa) / (4.0 * t * t))
+        else:
+            a = (4.0 / math.sqrt(math.pi)) * t * t
+        w = sinc_step * np.cosh(u) / t_scale * a
+        return t, w
     q = np.arange(R, dtype=np.float64) + (1.0 if kappa > 0.0 else 0.0)
     u = q * sinc_step
     t = np.sinh(u) / t_scale
@@ -75,27 +100,50 @@ def sinc_quadrature(R: int, sinc_step: float, t_scale: float,
     return t, w
 
 
-def kernel_value(r, kappa: float = 0.0):
-    """The kernel p(r): 1/r, or exp(-kappa r)/r (Sec. 2.3, Eq. LalpYukawa)."""
+def kernel_value(r, kappa: float = 0.0, kernel: int = YUKAWA):
+    """The kernel p(r): exp(-kappa r)/r (1/r at kappa = 0), exp(-kappa r), or 1/r^3
+    (Sec. 2.3)."""
     r = np.asarray(r, dtype=np.float64)
+    if kernel == SLATER:
+        return np.exp(-kappa * r)
+    if kernel == DIPOLE:
+        return 1.0 / (r * r * r)
     return np.exp(-kappa * r) / r
 
 
-def quadrature_rel_error(t: np.ndarray, w: np.ndarray, r: np.ndarray, kappa: float = 0.0) -> np.ndarray:
+def error_scale(r, kernel: int = YUKAWA):
+    """The scale m(r) the rule's error is measured against: 1/r for the
+    Yukawa/Newton family, 1 for Slater (bounded at 0), 1/r^3 for the dipole."""
+    r = np.asarray(r, dtype=np.float64)
+    if kernel == SLATER:
+        return np.ones_like(r)
+    if kernel == DIPOLE:
+        return 1.0 / (r * r * r)
+    return 1.0 / r
+
+
+def quadrature_rel_error(t: np.ndarray, w: np.ndarray, r: np.ndarray, kappa: float = 0.0,
+                         kernel: int = YUKAWA) -> np.ndarray:
     """r |sum_q w_q exp(-t_q^2 r^2) - p(r)|: the error of the separable
     expansion of the kernel p at distances r, relative to 1/r (Sec. 2.1, Eq.
     sinc_conv bounds the absolute error by C/a e^(-beta sqrt(M)) for r >= a).
     For the Newton kernel this is the relative error |r sum - 1|. For the
     Yukawa kernel it is the error relative to the unscreened 1/r: the relative
     error of exp(-kappa r)/r itself, many decades down at large kappa r, is
-    neither reachable with a few terms nor felt in a lattice sum."""
+    neither reachable with a few terms nor felt in a lattice sum. Slater: the
+    absolute error (the kernel is 1 at r = 0); dipole: the relative error
+    |r^3 sum - 1|."""
     r = np.asarray(r, dtype=np.float64)
     s = np.exp(-np.outer(r * r, t * t)) @ w
+    if kernel == SLATER:
+        return np.abs(s - np.exp(-kappa * r))
+    if kernel == DIPOLE:
+        return np.abs(r * r * r * s - 1.0)
     return np.abs(r * s - np.exp(-kappa * r))
 
 
 def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float,
-                n_r: int = 600, kappa: float = 0.0) -> Tuple[float, float]:
+                n_r: int = 600, kappa: float = 0.0, kernel: int = YUKAWA) -> Tuple[float, float]:
     """Scale s of the substitution t = sinh(u)/s that minimises the maximum
     relative error of the expansion over [r_min, r_max] (Sec. 2.1: M, and here
     s, are chosen so that the kernel is reproduced to a tolerance; the paper's
@@ -104,8 +152,8 @@ def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float,
     r = np.geomspace(r_min, r_max, n_r)
 
     def err(log_s):
-        t, w = sinc_quadrature(R, sinc_step, math.exp(log_s), kappa)
-        return float(np.max(quadrature_rel_error(t, w, r, kappa)))
+        t, w = sinc_quadrature(R, sinc_step, math.exp(log_s), kappa, kernel)
+        return float(np.max(quadrature_rel_error(t, w, r, kappa, kernel)))
 
     grid = np.linspace(math.log(1e-2), math.log(1e5), 241)
     vals = [err(x) for x in grid]
@@ -336,7 +384,8 @@ def charged_centres(N, box_lo, box_hi, blocks, defects):
     return pos, z
 
 
-def brute_force(points: np.ndarray, centres: np.ndarray, charges: np.ndarray, kappa: float = 0.0):
+def brute_force(points: np.ndarray, centres: np.ndarray, charges: np.ndarray, kappa: float = 0.0,
+                kernel: int = YUKAWA):
     """Direct sum sum_nu Z_nu p(|x - a_nu|) (Eq. EwaldSumE; p = 1/r, or
     exp(-kappa r)/r) at the given points; also returns sum_nu |Z_nu| p(|x - a_nu|)
     and the minimum and maximum distance to a centre, which bound the
@@ -349,7 +398,7 @@ def brute_force(points: np.ndarray, centres: np.ndarray, charges: np.ndarray, ka
     for c0 in range(0, len(centres), 256):
         c = centres[c0:c0 + 256]
         d = np.sqrt(((points[:, None, :] - c[None, :, :]) ** 2).sum(-1))
-        pd = np.exp(-kappa * d) / d
+        pd = kernel_value(d, kappa, kernel)
         val += (charges[c0:c0 + 256] * pd).sum(1)
         absval += (np.abs(charges[c0:c0 + 256]) * pd).sum(1)
         dmin = np.minimum(dmin, d.min(1))
@@ -474,7 +523,7 @@ def pipeline(wl, t_scale: float, core: bool = True, ranks=None):
     """Quadrature -> generating vectors -> assembled and defect terms ->
     RHOSVD, for a workload description (N, box, R, sinc step, blocks,
     defects, eps; kappa for the Yukawa kernel). Returns (terms, rhosvd result)."""
-    t, w = sinc_quadrature(wl.R, wl.sinc_step, t_scale, getattr(wl, "kappa", 0.0))
+    t, w = sinc_quadrature(wl.R, wl.sinc_step, t_scale, getattr(wl, "kappa", 0.0), getattr(wl, "kernel", YUKAWA))
     g = generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w)
     cols, tcol, xi = canonical_terms(wl.N, wl.box_lo, wl.box_hi, g, wl.blocks, wl.defects)
     res = rhosvd(cols, tcol, xi, wl.eps, ranks=ranks, core=core)

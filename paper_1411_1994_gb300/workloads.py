@@ -96,7 +96,8 @@ class Workload:
     defects: List[Defect]
     r_min: float = 0.25     # distance below which the quadrature is not asked to hold
     slabs: Optional[List[int]] = None   # z-indices to evaluate
-    kappa: float = 0.0      # Yukawa screening: kernel exp(-kappa r)/r (0: the Newton kernel 1/r)
+    kappa: float = 0.0      # kernel parameter: Yukawa exp(-kappa r)/r (0: Newton 1/r), Slater exp(-kappa r)
+    kernel: int = 0         # 0: Yukawa/Newton, 1: Slater, 2: dipole 1/r^3
 
     @property
     def n_sites(self) -> int:
@@ -266,15 +267,16 @@ def config5(seed=1005) -> Workload:
 
 
 def small_case(L=(3, 2, 2), N=48, R=16, eps=1e-8, frac_vac=0.0, frac_imp=0.0, seed=7,
-               sinc_step=0.3, kappa=0.0) -> Workload:
+               sinc_step=0.3, kappa=0.0, kernel=0) -> Workload:
     """A tiny workload whose full N^3 tensor fits in memory (tests)."""
     lo, hi = box_for(L)
     blocks = [centred_block(L)]
     rng = SplitMix64(seed)
     defects = point_defects(rng, blocks, frac_vac, frac_imp) if (frac_vac or frac_imp) else []
-    name = f"small_{L[0]}x{L[1]}x{L[2]}_N{N}_R{R}" + (f"_yukawa{kappa:g}" if kappa else "")
+    kname = {0: "yukawa", 1: "slater", 2: "dipole"}[kernel]
+    name = f"small_{L[0]}x{L[1]}x{L[2]}_N{N}_R{R}" + (f"_{kname}{kappa:g}" if (kappa or kernel) else "")
     return Workload(name, N, lo, hi, R, sinc_step, eps, blocks, defects, r_min=0.5,
-                    slabs=[N // 2, N // 3], kappa=kappa)
+                    slabs=[N // 2, N // 3], kappa=kappa, kernel=kernel)
 
 
 CONFIGS = {"c1": config1, "c2": config2, "c3": config3, "c5": config5}

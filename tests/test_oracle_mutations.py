@@ -26,7 +26,10 @@ MUTATIONS = {
                                 "w = w * np.exp(-(kappa * kappa) / (t * t))"),
     "yukawa_factor_inverted": ("w = w * np.exp(-(kappa * kappa) / (4.0 * t * t))",
                                "w = w * np.exp(-(kappa * kappa) * (t * t) / 4.0)"),
-    "yukawa_unscreened_brute_force": ("pd = np.exp(-kappa * d) / d", "pd = 1.0 / d"),
+    "yukawa_unscreened_kernel": ("        return 1.0 / (r * r * r)\n    return np.exp(-kappa * r) / r",
+                                 "        return 1.0 / (r * r * r)\n    return 1.0 / r"),
+    "slater_prefactor": ("a = (kappa / math.sqrt(math.pi)) / (t * t)", "a = (2.0 * kappa / math.sqrt(math.pi)) / (t * t)"),
+    "dipole_power": ("a = (4.0 / math.sqrt(math.pi)) * t * t", "a = (4.0 / math.sqrt(math.pi)) * t"),
 }
 
 

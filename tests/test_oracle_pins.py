@@ -148,6 +148,71 @@ def test_yukawa_lattice_against_brute_force():
     assert np.min(np.abs(nb - bf[keep]) - err) > 0.0
 
 
+# --- (a0) Slater and dipole kernels: Sec. 2.3, Eqs. LalpSlater, LalpPoly ---
+
+def test_slater_and_dipole_transforms():
+    """By trapezoid rules: Eq. LalpSlater as printed, exp(-2 sqrt(k rho)) =
+    sqrt(k/pi) int t^-3/2 exp(-k/t) exp(-rho t) dt, and the Laplace-Gauss forms
+    the oracle's weights use: exp(-kappa r) = (kappa/sqrt(pi)) int t^-2
+    exp(-kappa^2/(4 t^2)) exp(-r^2 t^2) dt and 1/r^3 = (4/sqrt(pi)) int t^2
+    exp(-r^2 t^2) dt (Eq. LalpPoly at n = 3/2, Gamma(3/2) = sqrt(pi)/2)."""
+    tt = np.linspace(1e-9, 60.0, 1200001)
+    for kappa, r in ((0.8, 0.7), (1.5, 2.0)):
+        k = kappa * kappa / 4.0
+        printed = math.sqrt(k / math.pi) * np.trapezoid(tt ** -1.5 * np.exp(-k / tt - r * r * tt), tt)
+        assert abs(printed - math.exp(-2.0 * math.sqrt(k) * r)) < 1e-9
+        gauss = (kappa / math.sqrt(math.pi)) * np.trapezoid(tt ** -2 * np.exp(-kappa ** 2 / (4 * tt ** 2) - (r * tt) ** 2), tt)
+        assert abs(gauss - math.exp(-kappa * r)) < 1e-12
+    for r in (0.6, 1.3, 3.0):
+        dip = (4.0 / math.sqrt(math.pi)) * np.trapezoid(tt ** 2 * np.exp(-(r * tt) ** 2), tt)
+        assert abs(dip * r ** 3 - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("kernel,kappa", [(O.SLATER, 0.8), (O.SLATER, 2.0), (O.DIPOLE, 0.0)])
+def test_fine_sinc_rule_reproduces_slater_and_dipole(kernel, kappa):
+    """A fine rule reproduces exp(-kappa r) and 1/r^3 to ~machine precision
+    relative to the kernel: a wrong power of t or prefactor leaves an O(1)
+    error."""
+    t, w = O.sinc_quadrature(400, 0.05, 10.0, kappa, kernel)
+    assert t[0] > 0.0 and np.all(w >= 0.0)
+    r = np.geomspace(0.05, 20.0, 2000)
+    approx = np.exp(-np.outer(r * r, t * t)) @ w
+    assert np.max(np.abs(approx / O.kernel_value(r, kappa, kernel) - 1.0)) < 1e-12
+    assert np.max(O.quadrature_rel_error(t, w, r, kappa, kernel)) < 1e-12
+    with pytest.raises(ValueError):
+        O.sinc_quadrature(20, 0.3, 10.0, 0.0 if kernel == O.SLATER else 0.5, kernel)
+
+
+@pytest.mark.parametrize("kernel,kappa", [(O.SLATER, 0.7), (O.DIPOLE, 0.0)])
+def test_slater_and_dipole_lattices_against_brute_force(kernel, kappa):
+    """Defected lattices with the Slater and dipole kernels: canonical tensor
+    values at sampled grid points vs the direct sum of Z p(d), within
+    tau * sum |Z| m(d) (m: the scale the rule's error tau is measured against,
+    1 for Slater and 1/d^3 for the dipole)."""
+    wl = W.small_case(L=(4, 3, 3), N=60, R=20, frac_vac=0.2, frac_imp=0.1, kappa=kappa, kernel=kernel)
+    rmax = O.default_r_max(wl)
+    s, _ = O.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, rmax, kappa=kappa, kernel=kernel)
+    t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s, kappa, kernel)
+    g = O.generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w)
+    cols, tcol, xi = O.canonical_terms(wl.N, wl.box_lo, wl.box_hi, g, wl.blocks, wl.defects)
+    xs = O.cell_centres(wl.N, wl.box_lo, wl.box_hi)
+    rng = np.random.default_rng(6)
+    idx = rng.integers(0, wl.N, size=(20000, 3))
+    centres, charges = O.charged_centres(wl.N, wl.box_lo, wl.box_hi, wl.blocks, wl.defects)
+    bf, absbf, dmin, _ = O.brute_force(xs[idx], centres, charges, kappa=kappa, kernel=kernel)
+    keep = dmin >= wl.r_min
+    if kernel == O.SLATER:
+        scale = np.full(int(keep.sum()), np.abs(charges).sum())
+    else:
+        scale = absbf[keep]
+    tens = (xi[:, None] * cols[0][tcol[:, 0]][:, idx[keep, 0]] * cols[1][tcol[:, 1]][:, idx[keep, 1]]
+            * cols[2][tcol[:, 2]][:, idx[keep, 2]]).sum(0)
+    tau = float(np.max(O.quadrature_rel_error(t, w, np.geomspace(wl.r_min, rmax, 6000), kappa, kernel)))
+    err = np.abs(tens - bf[keep])
+    assert np.all(err <= tau * scale * 1.001 + 1e-13)
+    assert np.max(err / np.abs(bf[keep]).max()) < 1e-4
+
+
 # --- generating vectors and windows: Eqs. master_pot, sub_tens -------------
 
 def test_reference_tensor_reproduces_kernel():
