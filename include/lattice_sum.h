@@ -37,6 +37,7 @@
  *    (2/sqrt(pi)) int exp(-kappa^2/(4 t^2)) exp(-r^2 t^2) dt) every weight is
  *    multiplied by exp(-kappa^2/(4 t_q^2)) and the nodes are q = 1..R (the
  *    node t = 0 has weight 0); row q - 1 of the reference vectors holds node q.
+ *    The Slater and dipole kernels: see LS_KERNEL_*.
  *  - A window of a centre at vertex m is (W_m g_q)[i] = g_q[i - m + N].
  *  - Return value: LS_OK (0) or a negative LS_ERR_* code; the message is
  *    available from lattice_sum_last_error(ctx). A call made in the wrong
@@ -114,10 +115,23 @@ typedef struct {
                         /* lattice_sum_fit_t_scale                                       */
     int32_t precision;  /* LS_FP64 or LS_MIXED                                           */
     int32_t flags;      /* reserved, must be 0                                           */
-    double  kappa;      /* Yukawa screening: kernel exp(-kappa r)/r; 0 = Newton 1/r.    */
-                        /* Finite, >= 0, and small enough that the first node's         */
-                        /* factor exp(-kappa^2/(4 t_1^2)) keeps kappa^2/(4 t_1^2) <= 600 */
+    double  kappa;      /* kernel parameter (see kernel); finite, >= 0, and small       */
+                        /* enough that kappa^2/(4 t_1^2) <= 600 (t_1 = sinh(s_h)/t_scale) */
+    int32_t kernel;     /* LS_KERNEL_YUKAWA: exp(-kappa r)/r, the Newton 1/r at kappa=0 */
+                        /* LS_KERNEL_SLATER: exp(-kappa r), kappa > 0                    */
+                        /* LS_KERNEL_DIPOLE: 1/r^3, kappa = 0                            */
 } ls_params;
+
+/* kernel families (Sec. 2.3), each a Laplace-Gauss integral
+ * p(r) = int_0^inf a(t) exp(-r^2 t^2) dt discretised by the same sinc rule:
+ *   YUKAWA a = (2/sqrt(pi)) exp(-kappa^2/(4 t^2))       (Eq. LalpYukawa, LalpNewt)
+ *   SLATER a = (kappa/sqrt(pi)) t^-2 exp(-kappa^2/(4 t^2)) (Eq. LalpSlater, t -> t^2)
+ *   DIPOLE a = (4/sqrt(pi)) t^2                          (Eq. LalpPoly, n = 3/2)
+ * with weights w_q = s_h a(t_q) cosh(q s_h)/t_scale (halved at q = 0). Only the
+ * Newton kernel has a(0) > 0 and uses q = 0..R-1; the others q = 1..R. */
+#define LS_KERNEL_YUKAWA 0
+#define LS_KERNEL_SLATER 1
+#define LS_KERNEL_DIPOLE 2
 
 typedef struct {
     int64_t L[3];        /* sites per axis (>= 1)                                        */
@@ -164,16 +178,17 @@ int lattice_sum_fit_t_scale(int32_t R, double sinc_step, double r_min, double r_
                             double* t_scale_out, double* max_rel_err_out);
 
 /*
- * lattice_sum_fit_t_scale_kernel -- the same fit for the kernel of a given
- * kappa (0: the Newton kernel, identical to lattice_sum_fit_t_scale; > 0: the
- * Yukawa kernel exp(-kappa r)/r of Sec. 2.3, Eq. LalpYukawa). The error
- * minimised is max_r r |sum_q w_q exp(-t_q^2 r^2) - p(r)|, the rule's error
- * relative to 1/r (Eq. sinc_conv bounds the absolute error); for kappa = 0 it
- * is the relative error above. LS_ERR_ARG on bad input (kappa < 0 or not
- * finite included).
+ * lattice_sum_fit_t_scale_kernel -- the same fit for a kernel family and
+ * parameter (LS_KERNEL_YUKAWA with kappa = 0 is lattice_sum_fit_t_scale).
+ * The error minimised is max_r |sum_q w_q exp(-t_q^2 r^2) - p(r)| / m(r) with
+ * m(r) = 1/r (Yukawa family: the relative error for the Newton kernel, and
+ * relative to the unscreened 1/r otherwise; Eq. sinc_conv bounds the absolute
+ * error), 1 (Slater, which is 1 at r = 0) or 1/r^3 (dipole: the relative
+ * error). LS_ERR_ARG on bad input (an unknown kernel, kappa < 0 or not
+ * finite, kappa = 0 for Slater or kappa != 0 for the dipole).
  */
-int lattice_sum_fit_t_scale_kernel(int32_t R, double sinc_step, double kappa, double r_min, double r_max,
-                                   double* t_scale_out, double* max_rel_err_out);
+int lattice_sum_fit_t_scale_kernel(int32_t R, double sinc_step, int32_t kernel, double kappa, double r_min,
+                                   double r_max, double* t_scale_out, double* max_rel_err_out);
 
 /*
  * lattice_sum_create -- reference vectors and assembled lattice sums.
@@ -181,8 +196,8 @@ int lattice_sum_fit_t_scale_kernel(int32_t R, double sinc_step, double kappa, do
  * v[i] = sum_k g_q[i - m_k + N] over the block's L_l snapped site vertices
  * m_k. `blocks` (host, nblocks >= 1 entries) are copied. `stream` is a
  * cudaStream_t or NULL. On success *out holds a new context.
- * Errors: LS_ERR_ARG (bad sizes, a site outside the box, kappa < 0 or too
- * large for the sinc rule), LS_ERR_OOM,
+ * Errors: LS_ERR_ARG (bad sizes, a site outside the box, an unknown kernel,
+ * a kappa the kernel does not take or too large for the sinc rule), LS_ERR_OOM,
  * LS_ERR_CUDA.
  */
 int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* blocks,

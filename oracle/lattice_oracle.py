@@ -148,6 +148,8 @@ def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float,
     relative error of the expansion over [r_min, r_max] (Sec. 2.1: M, and here
     s, are chosen so that the kernel is reproduced to a tolerance; the paper's
     C_0 plays the role of s). Coarse log-scan then golden-section refinement.
+    For kappa > 0, s is at most sinh(h) sqrt(2400)/kappa, so that no weight's
+    screening factor exp(-kappa^2/(4 t_q^2)) falls below e^-600.
     Returns (s, max relative error on the fitting grid)."""
     r = np.geomspace(r_min, r_max, n_r)
 
@@ -155,7 +157,11 @@ def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float,
         t, w = sinc_quadrature(R, sinc_step, math.exp(log_s), kappa, kernel)
         return float(np.max(quadrature_rel_error(t, w, r, kappa, kernel)))
 
-    grid = np.linspace(math.log(1e-2), math.log(1e5), 241)
+    hi = math.log(1e5)
+    if kappa > 0.0:
+        # keep the first node's screening factor representable: kappa^2/(4 t_1^2) <= 600
+        hi = min(hi, math.log(math.sinh(sinc_step) * math.sqrt(2400.0) / kappa))
+    grid = np.linspace(math.log(1e-2), hi, 241)
     vals = [err(x) for x in grid]
     i = int(np.argmin(vals))
     a, b = grid[max(i - 1, 0)], grid[min(i + 1, len(grid) - 1)]

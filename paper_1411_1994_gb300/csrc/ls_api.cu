@@ -217,27 +217,46 @@ int append_columns(ls_ctx* ctx, int l, const std::vector<int32_t>& q, const std:
     return LS_OK;
 }
 
-// max over r of r |sum_q w_q exp(-t_q^2 r^2) - p(r)|, p(r) = exp(-kappa r)/r: the rule's error
-// relative to 1/r (the relative error for the Newton kernel, kappa = 0). Yukawa (Eq.
-// LalpYukawa with the Laplace-Gauss factor 1/4): each weight times exp(-kappa^2/(4 t_q^2)),
-// nodes q = 1..R (the node t = 0 has weight 0).
-double quad_max_err(int R, double hs, double s, double kappa, const std::vector<double>& r) {
+// max over r of |sum_q w_q exp(-t_q^2 r^2) - p(r)| / m(r) for the kernel family (see
+// LS_KERNEL_*): p = exp(-kappa r)/r, m = 1/r (the Newton kernel at kappa = 0: the relative
+// error); p = exp(-kappa r), m = 1 (Slater); p = 1/r^3, m = 1/r^3 (dipole). Weights
+// w = h a(t) cosh(u)/s with the Laplace-Gauss densities a(t) of Sec. 2.3 (halved at u = 0).
+double quad_max_err(int R, double hs, double s, int kernel, double kappa, const std::vector<double>& r) {
     std::vector<double> t(R), w(R);
     const double spi = 1.7724538509055160273;
-    const int q0 = kappa > 0.0 ? 1 : 0;
+    const int q0 = (kernel == LS_KERNEL_YUKAWA && kappa == 0.0) ? 0 : 1;
     for (int i = 0; i < R; ++i) {
         const int q = i + q0;
         t[i] = sinh(q * hs) / s;
-        w[i] = (q == 0) ? hs / (s * spi) : 2.0 * hs * cosh(q * hs) / (s * spi);
-        if (kappa > 0.0) w[i] *= exp(-kappa * kappa / (4.0 * t[i] * t[i]));
+        if (kernel == LS_KERNEL_SLATER) {
+            w[i] = hs * cosh(q * hs) / s * (kappa / spi) / (t[i] * t[i]) * exp(-kappa * kappa / (4.0 * t[i] * t[i]));
+        } else if (kernel == LS_KERNEL_DIPOLE) {
+            w[i] = hs * cosh(q * hs) / s * (4.0 / spi) * t[i] * t[i];
+        } else {
+            w[i] = (q == 0) ? hs / (s * spi) : 2.0 * hs * cosh(q * hs) / (s * spi);
+            if (kappa > 0.0) w[i] *= exp(-kappa * kappa / (4.0 * t[i] * t[i]));
+        }
     }
     double e = 0.0;
     for (double x : r) {
         double acc = 0.0;
         for (int i = 0; i < R; ++i) acc += w[i] * exp(-t[i] * t[i] * x * x);
-        e = std::max(e, fabs(x * acc - exp(-kappa * x)));
+        double d;
+        if (kernel == LS_KERNEL_SLATER) d = fabs(acc - exp(-kappa * x));
+        else if (kernel == LS_KERNEL_DIPOLE) d = fabs(x * x * x * acc - 1.0);
+        else d = fabs(x * acc - exp(-kappa * x));
+        e = std::max(e, d);
     }
     return e;
+}
+
+// the kernel family and its parameter: LS_OK or a message
+const char* kernel_args_bad(int kernel, double kappa) {
+    if (kernel != LS_KERNEL_YUKAWA && kernel != LS_KERNEL_SLATER && kernel != LS_KERNEL_DIPOLE) return "unknown kernel";
+    if (!(kappa >= 0.0) || !std::isfinite(kappa)) return "kappa must be finite and >= 0";
+    if (kernel == LS_KERNEL_SLATER && !(kappa > 0.0)) return "the Slater kernel needs kappa > 0";
+    if (kernel == LS_KERNEL_DIPOLE && kappa != 0.0) return "the dipole kernel takes kappa = 0";
+    return nullptr;
 }
 
 }  // namespace
@@ -271,38 +290,43 @@ extern "C" {
 
 int lattice_sum_fit_t_scale(int32_t R, double sinc_step, double r_min, double r_max, double* t_scale_out,
                             double* max_rel_err_out) {
-    return lattice_sum_fit_t_scale_kernel(R, sinc_step, 0.0, r_min, r_max, t_scale_out, max_rel_err_out);
+    return lattice_sum_fit_t_scale_kernel(R, sinc_step, LS_KERNEL_YUKAWA, 0.0, r_min, r_max, t_scale_out,
+                                          max_rel_err_out);
 }
 
-int lattice_sum_fit_t_scale_kernel(int32_t R, double sinc_step, double kappa, double r_min, double r_max,
-                                   double* t_scale_out, double* max_rel_err_out) {
+int lattice_sum_fit_t_scale_kernel(int32_t R, double sinc_step, int32_t kernel, double kappa, double r_min,
+                                   double r_max, double* t_scale_out, double* max_rel_err_out) {
     ls_ctx* ctx = nullptr;
     if (R < 1 || R > 256 || !(sinc_step > 0) || !(r_min > 0) || !(r_max > r_min) || !t_scale_out ||
-        !(kappa >= 0.0) || !std::isfinite(kappa))
+        kernel_args_bad(kernel, kappa))
         return fail(ctx, LS_ERR_ARG, "fit_t_scale: bad arguments");
     std::vector<double> r(600);
     for (int i = 0; i < 600; ++i) r[i] = r_min * pow(r_max / r_min, i / 599.0);
     double best = 1e300, bx = 0.0;
-    const double lo = log(1e-2), hi = log(1e5);
+    const double lo = log(1e-2);
+    double hi = log(1e5);
+    // for kappa > 0 keep the first node's screening factor representable: kappa^2/(4 t_1^2) <= 600
+    if (kappa > 0.0) hi = std::min(hi, log(sinh(sinc_step) * sqrt(2400.0) / kappa));
+    if (!(hi > lo)) return fail(ctx, LS_ERR_ARG, "fit_t_scale: kappa=%g too large for sinc_step=%g", kappa, sinc_step);
     const int ns = 241;
     std::vector<double> xs(ns), es(ns);
     for (int i = 0; i < ns; ++i) {
         xs[i] = lo + (hi - lo) * i / (ns - 1);
-        es[i] = quad_max_err(R, sinc_step, exp(xs[i]), kappa, r);
+        es[i] = quad_max_err(R, sinc_step, exp(xs[i]), kernel, kappa, r);
         if (es[i] < best) { best = es[i]; bx = i; }
     }
     int bi = (int)bx;
     double a = xs[std::max(bi - 1, 0)], b = xs[std::min(bi + 1, ns - 1)];
     const double gr = (sqrt(5.0) - 1.0) / 2.0;
     double c = b - gr * (b - a), d = a + gr * (b - a);
-    double fc = quad_max_err(R, sinc_step, exp(c), kappa, r), fd = quad_max_err(R, sinc_step, exp(d), kappa, r);
+    double fc = quad_max_err(R, sinc_step, exp(c), kernel, kappa, r), fd = quad_max_err(R, sinc_step, exp(d), kernel, kappa, r);
     for (int it = 0; it < 60; ++it) {
-        if (fc < fd) { b = d; d = c; fd = fc; c = b - gr * (b - a); fc = quad_max_err(R, sinc_step, exp(c), kappa, r); }
-        else { a = c; c = d; fc = fd; d = a + gr * (b - a); fd = quad_max_err(R, sinc_step, exp(d), kappa, r); }
+        if (fc < fd) { b = d; d = c; fd = fc; c = b - gr * (b - a); fc = quad_max_err(R, sinc_step, exp(c), kernel, kappa, r); }
+        else { a = c; c = d; fc = fd; d = a + gr * (b - a); fd = quad_max_err(R, sinc_step, exp(d), kernel, kappa, r); }
     }
     const double x = 0.5 * (a + b);
     *t_scale_out = exp(x);
-    if (max_rel_err_out) *max_rel_err_out = quad_max_err(R, sinc_step, exp(x), kappa, r);
+    if (max_rel_err_out) *max_rel_err_out = quad_max_err(R, sinc_step, exp(x), kernel, kappa, r);
     return LS_OK;
 }
 
@@ -318,7 +342,7 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
     if (!(p.sinc_step > 0) || !(p.t_scale > 0)) return fail(ctx, LS_ERR_ARG, "create: sinc_step and t_scale must be > 0");
     if (p.precision != LS_FP64 && p.precision != LS_MIXED) return fail(ctx, LS_ERR_ARG, "create: unknown precision %d", p.precision);
     if (p.flags != 0) return fail(ctx, LS_ERR_ARG, "create: flags must be 0");
-    if (!(p.kappa >= 0.0) || !std::isfinite(p.kappa)) return fail(ctx, LS_ERR_ARG, "create: kappa must be finite and >= 0");
+    if (const char* why = kernel_args_bad(p.kernel, p.kappa)) return fail(ctx, LS_ERR_ARG, "create: %s", why);
     if (p.kappa > 0.0) {
         // the smallest node's screening factor exp(-kappa^2/(4 t_1^2)) must not underflow
         const double t1 = sinh(p.sinc_step) / p.t_scale;
@@ -364,7 +388,7 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
     {
         cudaError_t e2 = dalloc(ctx, &ctx->d_g, (int64_t)R * 2 * N);
         Scope sc_gen("genvec", ctx->st);
-        if (e2 == cudaSuccess) e2 = launch_genvec(ctx->d_g, R, N, ctx->h, p.sinc_step, p.t_scale, p.kappa, ctx->st);
+        if (e2 == cudaSuccess) e2 = launch_genvec(ctx->d_g, R, N, ctx->h, p.sinc_step, p.t_scale, p.kernel, p.kappa, ctx->st);
         if (e2 != cudaSuccess) rc = fail(ctx, LS_ERR_CUDA, "create: %s", cudaGetErrorString(e2));
     }
     for (int l = 0; l < 3 && rc == LS_OK; ++l) {

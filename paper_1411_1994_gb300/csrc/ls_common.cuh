@@ -69,10 +69,11 @@ void set_global_error(const char* msg);
 // launchers implemented in ls_f64.cu (all enqueue on `st`, return cudaError)
 // ---------------------------------------------------------------------------
 
-// G0: g[q][j] = w_q^(1/3) exp(-t_q^2 ((j - N + 1/2) h)^2), q < R, j < 2N; for kappa > 0 the
-// Yukawa rule (nodes q + 1, weights times exp(-kappa^2/(4 t^2))).
+// G0: g[q][j] = w_q^(1/3) exp(-t_q^2 ((j - N + 1/2) h)^2), q < R, j < 2N, for the kernel family
+// (LS_KERNEL_*) and its parameter kappa: weights w = h a(t) cosh(u)/s from the family's
+// Laplace-Gauss density a(t); nodes from q = 1 except for the Newton kernel.
 cudaError_t launch_genvec(double* g, int R, int64_t N, double h, double sinc_step, double t_scale,
-                          double kappa, cudaStream_t st);
+                          int kernel, double kappa, cudaStream_t st);
 
 // G1/G2: out[c][i] = sum_{k<wcnt[c]} g[colq[c]][i - win[woff[c]+k] + N],
 // for columns c in [c0, c0 + ncols); out has row stride N.

@@ -22,15 +22,27 @@ namespace {
 // ---------------------------------------------------------------------------
 // G0 / G1 / G2 and small elementwise kernels
 // ---------------------------------------------------------------------------
-__global__ void k_genvec(double* g, int R, int64_t N, double h, double sinc_step, double t_scale, double kappa) {
-    // the Newton kernel's nodes are q = 0..R-1; the Yukawa kernel's q = 1..R (its weight at t = 0 is 0)
-    const int row = blockIdx.y, q = row + (kappa > 0.0 ? 1 : 0);
+__global__ void k_genvec(double* g, int R, int64_t N, double h, double sinc_step, double t_scale, int kernel,
+                         double kappa) {
+    // the Newton kernel's nodes are q = 0..R-1; every other kernel's density vanishes at t = 0,
+    // so its nodes are q = 1..R
+    const bool newton = kernel == LS_KERNEL_YUKAWA && kappa == 0.0;
+    const int row = blockIdx.y, q = row + (newton ? 0 : 1);
     const double u = q * sinc_step;
     const double t = sinh(u) / t_scale;
     const double spi = 1.7724538509055160273;   // sqrt(pi)
-    double w = (q == 0) ? sinc_step / (t_scale * spi) : 2.0 * sinc_step * cosh(u) / (t_scale * spi);
-    // Yukawa exp(-kappa r)/r = (2/sqrt(pi)) int exp(-kappa^2/(4 t^2)) exp(-r^2 t^2) dt (Eq. LalpYukawa)
-    if (kappa > 0.0) w *= exp(-kappa * kappa / (4.0 * t * t));
+    double w;
+    if (kernel == LS_KERNEL_SLATER) {
+        // exp(-kappa r) = (kappa/sqrt(pi)) int t^-2 exp(-kappa^2/(4 t^2)) exp(-r^2 t^2) dt (Eq. LalpSlater)
+        w = sinc_step * cosh(u) / t_scale * (kappa / spi) / (t * t) * exp(-kappa * kappa / (4.0 * t * t));
+    } else if (kernel == LS_KERNEL_DIPOLE) {
+        // 1/r^3 = (4/sqrt(pi)) int t^2 exp(-r^2 t^2) dt (Eq. LalpPoly at n = 3/2)
+        w = sinc_step * cosh(u) / t_scale * (4.0 / spi) * t * t;
+    } else {
+        w = (q == 0) ? sinc_step / (t_scale * spi) : 2.0 * sinc_step * cosh(u) / (t_scale * spi);
+        // Yukawa exp(-kappa r)/r = (2/sqrt(pi)) int exp(-kappa^2/(4 t^2)) exp(-r^2 t^2) dt (Eq. LalpYukawa)
+        if (kappa > 0.0) w *= exp(-kappa * kappa / (4.0 * t * t));
+    }
     const double a = cbrt(w);
     const double t2 = t * t;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < 2 * N;
@@ -888,9 +900,9 @@ int coop_blocks(K kernel, int threads, size_t smem, int num_sms, int64_t want) {
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_genvec(double* g, int R, int64_t N, double h, double sinc_step, double t_scale,
-                          double kappa, cudaStream_t st) {
+                          int kernel, double kappa, cudaStream_t st) {
     dim3 grid((unsigned)((2 * N + 255) / 256 < 1024 ? (2 * N + 255) / 256 : 1024), R);
-    k_genvec<<<grid, 256, 0, st>>>(g, R, N, h, sinc_step, t_scale, kappa);
+    k_genvec<<<grid, 256, 0, st>>>(g, R, N, h, sinc_step, t_scale, kernel, kappa);
     count_kernels(1);
     return cudaGetLastError();
 }

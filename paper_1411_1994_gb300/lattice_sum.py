@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "liblattice_sum.so")
 
 LS_OK, LS_ERR_ARG, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_NOCONVERGE, LS_ERR_STATE, LS_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 LS_FP64, LS_MIXED = 0, 1
+LS_KERNEL_YUKAWA, LS_KERNEL_SLATER, LS_KERNEL_DIPOLE = 0, 1, 2   # exp(-kappa r)/r (1/r at kappa = 0), exp(-kappa r), 1/r^3
 LS_DEFECT_SITES, LS_DEFECT_POINT = 0, 1
 LS_OUT_F64, LS_OUT_F32 = 0, 1
 (LS_READ_GENVEC, LS_READ_COLUMNS, LS_READ_NORMS, LS_READ_TERMS, LS_READ_XI, LS_READ_SIGMA,
@@ -34,7 +35,7 @@ EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_fit_t_scale_kernel", "lattic
 class ls_params(C.Structure):
     _fields_ = [("N", C.c_int64), ("box_lo", C.c_double), ("box_hi", C.c_double), ("R", C.c_int32),
                 ("sinc_step", C.c_double), ("t_scale", C.c_double), ("precision", C.c_int32),
-                ("flags", C.c_int32), ("kappa", C.c_double)]
+                ("flags", C.c_int32), ("kappa", C.c_double), ("kernel", C.c_int32)]
 
 
 class ls_block(C.Structure):
@@ -73,8 +74,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     P = C.POINTER
     lib.lattice_sum_fit_t_scale.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_double, P(C.c_double),
                                             P(C.c_double)]
-    lib.lattice_sum_fit_t_scale_kernel.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double,
-                                                   P(C.c_double), P(C.c_double)]
+    lib.lattice_sum_fit_t_scale_kernel.argtypes = [C.c_int32, C.c_double, C.c_int32, C.c_double, C.c_double,
+                                                   C.c_double, P(C.c_double), P(C.c_double)]
     lib.lattice_sum_create.argtypes = [P(C.c_void_p), P(ls_params), P(ls_block), C.c_int32, C.c_void_p]
     lib.lattice_sum_add_defects.argtypes = [C.c_void_p, P(ls_defect), C.c_int64]
     lib.lattice_sum_rhosvd_reduce.argtypes = [C.c_void_p, C.c_double, P(C.c_int32), P(ls_tucker_info)]
@@ -214,12 +215,14 @@ def jacobi_eig(H, tol: float = 1e-7, abs_floor: float = 0.0, form: int = 2):
     return D, V, sw.value
 
 
-def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float, kappa: float = 0.0):
+def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float, kappa: float = 0.0,
+                kernel: int = LS_KERNEL_YUKAWA):
     s, e = C.c_double(), C.c_double()
-    if kappa == 0.0:
+    if kappa == 0.0 and kernel == LS_KERNEL_YUKAWA:
         _check(lib().lattice_sum_fit_t_scale(R, sinc_step, r_min, r_max, C.byref(s), C.byref(e)))
     else:
-        _check(lib().lattice_sum_fit_t_scale_kernel(R, sinc_step, kappa, r_min, r_max, C.byref(s), C.byref(e)))
+        _check(lib().lattice_sum_fit_t_scale_kernel(R, sinc_step, kernel, kappa, r_min, r_max, C.byref(s),
+                                                    C.byref(e)))
     return s.value, e.value
 
 
@@ -253,10 +256,10 @@ class LatticeSum:
     eval_slab, each a direct call of the C ABI."""
 
     def __init__(self, N, box_lo, box_hi, R, sinc_step, t_scale, blocks, precision=LS_FP64, stream=None,
-                 kappa=0.0):
+                 kappa=0.0, kernel=LS_KERNEL_YUKAWA):
         self._lib = lib()
         p = ls_params(int(N), float(box_lo), float(box_hi), int(R), float(sinc_step), float(t_scale),
-                      int(precision), 0, float(kappa))
+                      int(precision), 0, float(kappa), int(kernel))
         self._blocks = make_blocks(blocks)
         ctx = C.c_void_p()
         rc = self._lib.lattice_sum_create(C.byref(ctx), C.byref(p), self._blocks, len(blocks),
@@ -270,7 +273,7 @@ class LatticeSum:
     @classmethod
     def from_workload(cls, wl, t_scale, precision=LS_FP64, stream=None):
         return cls(wl.N, wl.box_lo, wl.box_hi, wl.R, wl.sinc_step, t_scale, wl.blocks, precision, stream,
-                   getattr(wl, "kappa", 0.0))
+                   getattr(wl, "kappa", 0.0), getattr(wl, "kernel", LS_KERNEL_YUKAWA))
 
     def add_defects(self, defects):
         """lattice_sum_add_defects for a sequence of Defect descriptions, or for an ls_defect

@@ -42,7 +42,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_binding_structs_match_header_sizes(lib):
     import ctypes as C
-    assert C.sizeof(L.ls_params) == 8 + 8 + 8 + 8 + 8 + 8 + 4 + 4 + 8
+    assert C.sizeof(L.ls_params) == 8 + 8 + 8 + 8 + 8 + 8 + 4 + 4 + 8 + 8
     assert C.sizeof(L.ls_block) == 3 * 8 * 3 + 8
     assert C.sizeof(L.ls_defect) == 4 + 4 + 3 * 8 + 3 * 8 + 3 * 8 + 8
 
@@ -68,36 +68,41 @@ def test_fit_t_scale_rejects_bad_input(lib):
         with pytest.raises(L.LatticeSumError) as ei:
             L.fit_t_scale(24, 0.25, 0.25, 40.0, kappa=kappa)
         assert ei.value.code == L.LS_ERR_ARG
+    for kernel, kappa in ((L.LS_KERNEL_SLATER, 0.0), (L.LS_KERNEL_DIPOLE, 0.5), (3, 0.0), (-1, 0.0)):
+        with pytest.raises(L.LatticeSumError) as ei:
+            L.fit_t_scale(24, 0.25, 0.25, 40.0, kappa=kappa, kernel=kernel)
+        assert ei.value.code == L.LS_ERR_ARG
 
 
-@pytest.mark.parametrize("kappa", [0.3, 0.5, 1.0])
-def test_fit_t_scale_yukawa_matches_oracle_quality(lib, kappa):
-    """The library's fit for the Yukawa kernel: its reported error is the
-    oracle's error of the same rule (relative to 1/r), and as good as the
+@pytest.mark.parametrize("kernel,kappa", [(0, 0.3), (0, 0.5), (0, 1.0), (1, 0.5), (1, 1.0), (2, 0.0)])
+def test_fit_t_scale_kernels_match_oracle_quality(lib, kernel, kappa):
+    """The library's fit for the Yukawa, Slater and dipole kernels: its
+    reported error is the oracle's error of the same rule, and as good as the
     oracle's own fit."""
     from oracle import lattice_oracle as O
     wl = W.config2()
     rmax = O.default_r_max(wl)
-    s_lib, e_lib = L.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, rmax, kappa=kappa)
-    s_or, e_or = O.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, rmax, kappa=kappa)
-    t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s_lib, kappa)
-    e_chk = float(np.max(O.quadrature_rel_error(t, w, np.geomspace(wl.r_min, rmax, 600), kappa)))
+    s_lib, e_lib = L.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, rmax, kappa=kappa, kernel=kernel)
+    s_or, e_or = O.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, rmax, kappa=kappa, kernel=kernel)
+    t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s_lib, kappa, kernel)
+    e_chk = float(np.max(O.quadrature_rel_error(t, w, np.geomspace(wl.r_min, rmax, 600), kappa, kernel)))
     assert abs(e_chk - e_lib) <= 1e-3 * e_lib
     assert e_lib <= 1.05 * e_or
-    assert e_lib < 2e-6
+    assert e_lib < 1e-5
 
 
 @pytest.mark.parametrize("bad", [dict(N=1), dict(R=0), dict(R=65), dict(box_hi=-6.0), dict(sinc_step=0.0),
                                  dict(t_scale=-1.0), dict(precision=7), dict(kappa=-1.0),
-                                 dict(kappa=float("nan")), dict(kappa=1e4)])
+                                 dict(kappa=float("nan")), dict(kappa=1e4), dict(kernel=3),
+                                 dict(kernel=L.LS_KERNEL_SLATER), dict(kernel=L.LS_KERNEL_DIPOLE, kappa=0.5)])
 def test_create_validates_arguments_on_host(lib, bad):
     kw = dict(N=64, box_lo=-6.0, box_hi=6.0, R=8, sinc_step=0.25, t_scale=10.0, precision=L.LS_FP64,
-              kappa=0.0)
+              kappa=0.0, kernel=L.LS_KERNEL_YUKAWA)
     kw.update(bad)
     blocks = [W.centred_block((2, 2, 2))]
     with pytest.raises(L.LatticeSumError) as ei:
         L.LatticeSum(kw["N"], kw["box_lo"], kw["box_hi"], kw["R"], kw["sinc_step"], kw["t_scale"], blocks,
-                     kw["precision"], kappa=kw["kappa"])
+                     kw["precision"], kappa=kw["kappa"], kernel=kw["kernel"])
     assert ei.value.code == L.LS_ERR_ARG
 
 

@@ -1,8 +1,9 @@
-"""The Yukawa kernel exp(-kappa r)/r (Sec. 2.3, Eq. LalpYukawa) through the
-C ABI against the FP64 oracle.
+"""The other kernels of Sec. 2.3 through the C ABI against the FP64 oracle:
+Yukawa exp(-kappa r)/r (Eq. LalpYukawa), Slater exp(-kappa r) (Eq.
+LalpSlater) and the dipole 1/r^3 (Eq. LalpPoly at n = 3/2).
 
-Only the reference vectors change (the quadrature weights gain the screening
-factor exp(-kappa^2/(4 t_q^2)) and the nodes start at q = 1); the rest of the
+Only the reference vectors change (the quadrature weights follow each
+kernel's Laplace-Gauss density and the nodes start at q = 1); the rest of the
 path is the one the Newton kernel takes. Tolerances are those of the Newton
 parity tests: reference and canonical vectors to 1e-13 of each vector's
 maximum (the same closed forms in FP64), term maps and charges bit-exact, the
@@ -33,26 +34,31 @@ def _lib():
     L.lib()
 
 
+YUK, SLA, DIP = L.LS_KERNEL_YUKAWA, L.LS_KERNEL_SLATER, L.LS_KERNEL_DIPOLE
 CASES = [W.small_case(L=(3, 2, 2), frac_vac=0.2, frac_imp=0.1, eps=1e-7, kappa=0.6),
          W.small_case(L=(5, 3, 2), N=70, frac_vac=0.1, eps=1e-6, kappa=1.2),
-         W.small_case(L=(4, 4, 4), N=64, R=20, frac_vac=0.15, frac_imp=0.05, eps=1e-6, kappa=0.3)]
+         W.small_case(L=(4, 4, 4), N=64, R=20, frac_vac=0.15, frac_imp=0.05, eps=1e-6, kappa=0.3),
+         W.small_case(L=(3, 2, 2), frac_vac=0.2, frac_imp=0.1, eps=1e-7, kappa=0.8, kernel=SLA),
+         W.small_case(L=(4, 4, 4), N=64, R=20, frac_vac=0.15, frac_imp=0.05, eps=1e-6, kappa=1.5, kernel=SLA),
+         W.small_case(L=(3, 2, 2), frac_vac=0.2, frac_imp=0.1, eps=1e-7, kernel=DIP),
+         W.small_case(L=(4, 4, 4), N=64, R=20, frac_vac=0.15, frac_imp=0.05, eps=1e-6, kernel=DIP)]
 
 
 def scale_for(wl):
-    s, _ = O.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, O.default_r_max(wl), kappa=wl.kappa)
+    s, _ = O.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, O.default_r_max(wl), kappa=wl.kappa, kernel=wl.kernel)
     return s
 
 
 @pytest.mark.parametrize("wl", CASES, ids=lambda w: w.name)
-def test_yukawa_vectors_and_terms_match_oracle(wl):
+def test_kernel_vectors_and_terms_match_oracle(wl):
     s = scale_for(wl)
-    t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s, wl.kappa)
+    t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s, wl.kappa, wl.kernel)
     g = O.generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w)
     cols, tcol, xi = O.canonical_terms(wl.N, wl.box_lo, wl.box_hi, g, wl.blocks, wl.defects)
     ls = P.gpu_ctx(wl, s)
     gg = ls.read(L.LS_READ_GENVEC).reshape(wl.R, 2 * wl.N)
     assert np.all(np.abs(gg - g) <= 1e-13 * np.abs(g).max(1, keepdims=True))
-    # the Newton rule's vectors are not these (the screening is applied)
+    # the Newton rule's vectors are not these (the kernel's weights are applied)
     tn, wn = O.sinc_quadrature(wl.R, wl.sinc_step, s)
     gn = O.generating_vectors(wl.N, wl.box_lo, wl.box_hi, tn, wn)
     assert np.max(np.abs(gg - gn)) > 1e-3 * np.abs(gn).max()
@@ -66,14 +72,14 @@ def test_yukawa_vectors_and_terms_match_oracle(wl):
 
 
 @pytest.mark.parametrize("wl", CASES, ids=lambda w: w.name)
-def test_yukawa_fp64_reduction_matches_oracle(wl):
+def test_kernel_fp64_reduction_matches_oracle(wl):
     s = scale_for(wl)
     P.check_reduction(wl, s)
     P.forced_rank_parity(wl, s)
 
 
-@pytest.mark.parametrize("wl", CASES[:2], ids=lambda w: w.name)
-def test_yukawa_mixed_within_eps(wl):
+@pytest.mark.parametrize("wl", CASES[0:2] + CASES[3:4] + CASES[5:6], ids=lambda w: w.name)
+def test_kernel_mixed_within_eps(wl):
     s = scale_for(wl)
     orc = P.oracle_run(wl, s)
     ls = P.gpu_ctx(wl, s, L.LS_MIXED)
@@ -84,12 +90,12 @@ def test_yukawa_mixed_within_eps(wl):
     ls.close()
 
 
-def test_yukawa_slabs_against_direct_screened_sum():
-    """Slab values of the FP64 path vs sum_s Z_s exp(-kappa d)/d over the
-    snapped centres, at points at least r_min from every centre: within
-    tau * sum_s |Z_s|/d_s (tau: the rule's error relative to 1/r) plus the
-    truncation bound."""
-    wl = CASES[2]
+@pytest.mark.parametrize("wl", [CASES[2], CASES[4], CASES[6]], ids=lambda w: w.name)
+def test_kernel_slabs_against_direct_sum(wl):
+    """Slab values of the FP64 path vs sum_s Z_s p(d_s) over the snapped
+    centres, at points at least r_min from every centre: within tau * sum_s
+    |Z_s| m(d_s) (tau: the rule's error measured against m = 1/r, 1 or 1/r^3)
+    plus the truncation bound."""
     s = scale_for(wl)
     ls = P.gpu_ctx(wl, s)
     info = ls.rhosvd_reduce(wl.eps)
@@ -97,24 +103,31 @@ def test_yukawa_slabs_against_direct_screened_sum():
     out = ls.eval_slab_torch(z).cpu().numpy()
     xs = O.cell_centres(wl.N, wl.box_lo, wl.box_hi)
     centres, charges = O.charged_centres(wl.N, wl.box_lo, wl.box_hi, wl.blocks, wl.defects)
-    t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s, wl.kappa)
+    t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s, wl.kappa, wl.kernel)
     tau = float(np.max(O.quadrature_rel_error(t, w, np.geomspace(wl.r_min, O.default_r_max(wl), 6000),
-                                              wl.kappa)))
+                                              wl.kappa, wl.kernel)))
     rng = np.random.default_rng(11)
     for k, zz in enumerate(z):
         ij = rng.integers(0, wl.N, size=(3000, 2))
         pts = np.stack([xs[ij[:, 0]], xs[ij[:, 1]], np.full(len(ij), xs[zz])], 1)
-        bf, _, dmin, _ = O.brute_force(pts, centres, charges, kappa=wl.kappa)
-        _, abs_newton, _, _ = O.brute_force(pts, centres, charges)
+        bf, absbf, dmin, _ = O.brute_force(pts, centres, charges, kappa=wl.kappa, kernel=wl.kernel)
         keep = dmin >= wl.r_min
+        if wl.kernel == SLA:
+            scale = np.full(int(keep.sum()), np.abs(charges).sum())
+        elif wl.kernel == DIP:
+            scale = absbf[keep]
+        else:
+            scale = O.brute_force(pts, centres, charges)[1][keep]
         val = out[k][ij[keep, 0], ij[keep, 1]]
-        assert np.all(np.abs(val - bf[keep]) <= tau * abs_newton[keep] * 1.01 + info["bound_abs"])
+        assert np.all(np.abs(val - bf[keep]) <= tau * scale * 1.01 + info["bound_abs"])
     ls.close()
 
 
-def test_yukawa_rejects_bad_kappa():
+def test_kernel_rejects_bad_parameters():
     wl = CASES[0]
-    for kappa in (-0.1, float("nan"), 1e4):
+    for kernel, kappa in ((YUK, -0.1), (YUK, float("nan")), (YUK, 1e4), (SLA, 0.0), (SLA, 1e4), (DIP, 0.5),
+                          (7, 0.0)):
         with pytest.raises(L.LatticeSumError) as ei:
-            L.LatticeSum(wl.N, wl.box_lo, wl.box_hi, wl.R, wl.sinc_step, 10.0, wl.blocks, kappa=kappa)
+            L.LatticeSum(wl.N, wl.box_lo, wl.box_hi, wl.R, wl.sinc_step, 10.0, wl.blocks, kappa=kappa,
+                         kernel=kernel)
         assert ei.value.code == L.LS_ERR_ARG
