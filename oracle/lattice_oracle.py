@@ -206,13 +206,51 @@ def snap(pos: float, N: int, box_lo: float, box_hi: float) -> int:
     return int(m)
 
 
+_GL_X, _GL_W = np.polynomial.legendre.leggauss(24)
+
+
+def gaussian_cell_average(t: float, a: float, b: float) -> float:
+    """(1/(b - a)) int_a^b exp(-t^2 x^2) dx. Where t (b - a) <= 10 the integrand
+    is smooth on the cell on the scale of its width and a 24-point
+    Gauss-Legendre rule gives it to rounding (degree 47, error of order
+    (t (b - a)/2)^48 / 48!). Wider cells (a narrow Gaussian) never straddle 0
+    (cell ends are multiples of h), so the error-function form (sqrt(pi) /
+    (2 t (b - a))) (erfc(t a) - erfc(t b)) (mirrored for a cell below 0) has
+    no cancellation there: erfc(t a) exceeds erfc(t b) by a factor of at
+    least e^100."""
+    if t == 0.0:
+        return 1.0
+    if t * (b - a) <= 10.0:
+        mid, half = 0.5 * (a + b), 0.5 * (b - a)
+        x = mid + half * _GL_X
+        return 0.5 * float(np.sum(_GL_W * np.exp(-(t * x) ** 2)))
+    if a >= 0.0:
+        d = math.erfc(t * a) - math.erfc(t * b)
+    else:
+        d = math.erfc(-t * b) - math.erfc(-t * a)
+    return math.sqrt(math.pi) / (2.0 * t * (b - a)) * d
+
+
 def generating_vectors(N: int, box_lo: float, box_hi: float,
-                       t: np.ndarray, w: np.ndarray) -> np.ndarray:
+                       t: np.ndarray, w: np.ndarray, galerkin: bool = False) -> np.ndarray:
     """Canonical vectors of the reference tensor on the doubled grid,
     Eq. (master_pot): p_q[j] = w_q^(1/3) exp(-t_q^2 xt_j^2) on the 2N cell
     centres xt_j = (j - N + 1/2) h of [-b, b] (collocation reading). The same
-    vectors serve all three modes (Eq. sinc_general). Shape (R, 2N)."""
+    vectors serve all three modes (Eq. sinc_general). Shape (R, 2N).
+
+    galerkin: Eq. (galten) with piecewise-constant basis functions, each entry
+    the integral of the Gaussian over its cell [(j - N) h, (j - N + 1) h].
+    Reading: divided by the cell width, i.e. cell averages, so that the tensor
+    holds cell averages of the kernel (Eq. galten divided by h^3) on the same
+    scale as the collocated values."""
     h = mesh_size(N, box_lo, box_hi)
+    if galerkin:
+        g = np.empty((len(t), 2 * N))
+        for q in range(len(t)):
+            c = np.cbrt(w[q])
+            for j in range(2 * N):
+                g[q, j] = c * gaussian_cell_average(float(t[q]), (j - N) * h, (j - N + 1) * h)
+        return g
     xt = (np.arange(2 * N, dtype=np.float64) - N + 0.5) * h
     return np.cbrt(w)[:, None] * np.exp(-np.outer(t * t, xt * xt))
 
@@ -530,7 +568,7 @@ def pipeline(wl, t_scale: float, core: bool = True, ranks=None):
     RHOSVD, for a workload description (N, box, R, sinc step, blocks,
     defects, eps; kappa for the Yukawa kernel). Returns (terms, rhosvd result)."""
     t, w = sinc_quadrature(wl.R, wl.sinc_step, t_scale, getattr(wl, "kappa", 0.0), getattr(wl, "kernel", YUKAWA))
-    g = generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w)
+    g = generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w, getattr(wl, "galerkin", False))
     cols, tcol, xi = canonical_terms(wl.N, wl.box_lo, wl.box_hi, g, wl.blocks, wl.defects)
     res = rhosvd(cols, tcol, xi, wl.eps, ranks=ranks, core=core)
     return {"t": t, "w": w, "g": g, "cols": cols, "tcol": tcol, "xi": xi}, res

@@ -98,6 +98,7 @@ class Workload:
     slabs: Optional[List[int]] = None   # z-indices to evaluate
     kappa: float = 0.0      # kernel parameter: Yukawa exp(-kappa r)/r (0: Newton 1/r), Slater exp(-kappa r)
     kernel: int = 0         # 0: Yukawa/Newton, 1: Slater, 2: dipole 1/r^3
+    galerkin: bool = False  # reference vectors as cell averages (Eq. galten) instead of collocation
 
     @property
     def n_sites(self) -> int:
@@ -267,7 +268,7 @@ def config5(seed=1005) -> Workload:
 
 
 def small_case(L=(3, 2, 2), N=48, R=16, eps=1e-8, frac_vac=0.0, frac_imp=0.0, seed=7,
-               sinc_step=0.3, kappa=0.0, kernel=0) -> Workload:
+               sinc_step=0.3, kappa=0.0, kernel=0, galerkin=False) -> Workload:
     """A tiny workload whose full N^3 tensor fits in memory (tests)."""
     lo, hi = box_for(L)
     blocks = [centred_block(L)]
@@ -275,8 +276,9 @@ def small_case(L=(3, 2, 2), N=48, R=16, eps=1e-8, frac_vac=0.0, frac_imp=0.0, se
     defects = point_defects(rng, blocks, frac_vac, frac_imp) if (frac_vac or frac_imp) else []
     kname = {0: "yukawa", 1: "slater", 2: "dipole"}[kernel]
     name = f"small_{L[0]}x{L[1]}x{L[2]}_N{N}_R{R}" + (f"_{kname}{kappa:g}" if (kappa or kernel) else "")
+    name += "_galerkin" if galerkin else ""
     return Workload(name, N, lo, hi, R, sinc_step, eps, blocks, defects, r_min=0.5,
-                    slabs=[N // 2, N // 3], kappa=kappa, kernel=kernel)
+                    slabs=[N // 2, N // 3], kappa=kappa, kernel=kernel, galerkin=galerkin)
 
 
 CONFIGS = {"c1": config1, "c2": config2, "c3": config3, "c5": config5}

@@ -28,6 +28,8 @@ MUTATIONS = {
                                "w = w * np.exp(-(kappa * kappa) * (t * t) / 4.0)"),
     "yukawa_unscreened_kernel": ("        return 1.0 / (r * r * r)\n    return np.exp(-kappa * r) / r",
                                  "        return 1.0 / (r * r * r)\n    return 1.0 / r"),
+    "galerkin_cell_shift": ("g[q, j] = c * gaussian_cell_average(float(t[q]), (j - N) * h, (j - N + 1) * h)",
+                            "g[q, j] = c * gaussian_cell_average(float(t[q]), (j - N + 0.5) * h, (j - N + 1.5) * h)"),
     "slater_prefactor": ("a = (kappa / math.sqrt(math.pi)) / (t * t)", "a = (2.0 * kappa / math.sqrt(math.pi)) / (t * t)"),
     "dipole_power": ("a = (4.0 / math.sqrt(math.pi)) * t * t", "a = (4.0 / math.sqrt(math.pi)) * t"),
 }

@@ -213,6 +213,53 @@ def test_slater_and_dipole_lattices_against_brute_force(kernel, kappa):
     assert np.max(err / np.abs(bf[keep]).max()) < 1e-4
 
 
+# --- (a0) Galerkin reference vectors: Eq. galten ----------------------------
+
+def test_galerkin_cell_average_matches_composite_rule():
+    """Cell averages of exp(-t^2 x^2) against a 400-panel composite
+    Gauss-Legendre rule, over t from 0 to 300 (both of the oracle's branches)
+    and cells on both sides of 0."""
+    xg, wg = np.polynomial.legendre.leggauss(16)
+
+    def composite(t, a, b, n=400):
+        e = np.linspace(a, b, n + 1)
+        m, hh = 0.5 * (e[1:] + e[:-1]), 0.5 * (e[1:] - e[:-1])
+        return float(np.sum(wg[None, :] * np.exp(-(t * (m[:, None] + hh[:, None] * xg[None, :])) ** 2)
+                            * hh[:, None])) / (b - a)
+    for t in (0.0, 1e-4, 0.02, 0.5, 3.0, 30.0, 300.0):
+        for a, b in ((-0.3, -0.2), (0.0, 0.1), (0.2, 0.3), (2.0, 2.1), (-5.1, -5.0), (-0.1, 0.0)):
+            ref = composite(t, a, b)
+            v = O.gaussian_cell_average(t, a, b)
+            assert abs(v - ref) <= 1e-13 * abs(ref) + 1e-300, (t, a, b, v, ref)
+
+
+def test_galerkin_vectors_telescope_and_approach_collocation():
+    """h sum_j p_q[j] over the doubled grid is w_q^(1/3) int_-b^b exp(-t^2 x^2)
+    dx = w_q^(1/3) sqrt(pi)/t erf(t b) (b = N h); and on a fine grid the cell
+    average differs from the collocated value by the midpoint-rule term
+    (h^2/24) d^2/dx^2 exp(-t^2 x^2), which a cell shifted by any fraction of h
+    would turn into an O(h) difference."""
+    N, lo, hi = 40, -3.0, 3.0
+    h = (hi - lo) / N
+    t, w = O.sinc_quadrature(12, 0.3, 8.0)
+    g = O.generating_vectors(N, lo, hi, t, w, galerkin=True)
+    for q in range(len(t)):
+        exact = 2 * N * h if t[q] == 0.0 else math.sqrt(math.pi) / t[q] * math.erf(t[q] * N * h)
+        assert abs(h * g[q].sum() - np.cbrt(w[q]) * exact) <= 1e-13 * np.cbrt(w[q]) * exact
+    N2 = 4000
+    h2 = (hi - lo) / N2
+    tq = np.array([0.7, 1.3])
+    wq = np.ones(2)
+    gg = O.generating_vectors(N2, lo, hi, tq, wq, galerkin=True)
+    gc = O.generating_vectors(N2, lo, hi, tq, wq)
+    x = (np.arange(2 * N2) - N2 + 0.5) * h2
+    for q in range(2):
+        f2 = (4 * tq[q] ** 4 * x * x - 2 * tq[q] ** 2) * np.exp(-(tq[q] * x) ** 2)
+        sel = np.abs(f2) > 1e-3
+        ratio = (gg[q] - gc[q])[sel] / (h2 * h2 / 24 * f2[sel])
+        assert np.all(np.abs(ratio - 1.0) < 1e-3)
+
+
 # --- generating vectors and windows: Eqs. master_pot, sub_tens -------------
 
 def test_reference_tensor_reproduces_kernel():
