@@ -114,7 +114,7 @@ typedef struct {
     double  t_scale;    /* substitution scale s in t = sinh(u)/s (> 0); see             */
                         /* lattice_sum_fit_t_scale                                       */
     int32_t precision;  /* LS_FP64 or LS_MIXED                                           */
-    int32_t flags;      /* reserved, must be 0                                           */
+    int32_t flags;      /* 0 or LS_FLAG_GALERKIN                                         */
     double  kappa;      /* kernel parameter (see kernel); finite, >= 0, and small       */
                         /* enough that kappa^2/(4 t_1^2) <= 600 (t_1 = sinh(s_h)/t_scale) */
     int32_t kernel;     /* LS_KERNEL_YUKAWA: exp(-kappa r)/r, the Newton 1/r at kappa=0 */
@@ -129,6 +129,11 @@ typedef struct {
  *   DIPOLE a = (4/sqrt(pi)) t^2                          (Eq. LalpPoly, n = 3/2)
  * with weights w_q = s_h a(t_q) cosh(q s_h)/t_scale (halved at q = 0). Only the
  * Newton kernel has a(0) > 0 and uses q = 0..R-1; the others q = 1..R. */
+/* flags: reference vectors as cell averages, (1/h) int over [(j-N)h, (j-N+1)h] of
+ * exp(-t_q^2 x^2) times w_q^(1/3), i.e. Eq. (galten) with piecewise-constant basis
+ * functions divided by the cell volume, instead of collocation at cell centres */
+#define LS_FLAG_GALERKIN 1
+
 #define LS_KERNEL_YUKAWA 0
 #define LS_KERNEL_SLATER 1
 #define LS_KERNEL_DIPOLE 2

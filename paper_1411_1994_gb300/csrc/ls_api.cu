@@ -341,7 +341,7 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
     if (p.R < 1 || p.R > 64) return fail(ctx, LS_ERR_ARG, "create: R=%d out of range [1,64]", p.R);
     if (!(p.sinc_step > 0) || !(p.t_scale > 0)) return fail(ctx, LS_ERR_ARG, "create: sinc_step and t_scale must be > 0");
     if (p.precision != LS_FP64 && p.precision != LS_MIXED) return fail(ctx, LS_ERR_ARG, "create: unknown precision %d", p.precision);
-    if (p.flags != 0) return fail(ctx, LS_ERR_ARG, "create: flags must be 0");
+    if ((p.flags & ~LS_FLAG_GALERKIN) != 0) return fail(ctx, LS_ERR_ARG, "create: unknown flags 0x%x", p.flags);
     if (const char* why = kernel_args_bad(p.kernel, p.kappa)) return fail(ctx, LS_ERR_ARG, "create: %s", why);
     if (p.kappa > 0.0) {
         // the smallest node's screening factor exp(-kappa^2/(4 t_1^2)) must not underflow
@@ -388,7 +388,8 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
     {
         cudaError_t e2 = dalloc(ctx, &ctx->d_g, (int64_t)R * 2 * N);
         Scope sc_gen("genvec", ctx->st);
-        if (e2 == cudaSuccess) e2 = launch_genvec(ctx->d_g, R, N, ctx->h, p.sinc_step, p.t_scale, p.kernel, p.kappa, ctx->st);
+        if (e2 == cudaSuccess) e2 = launch_genvec(ctx->d_g, R, N, ctx->h, p.sinc_step, p.t_scale, p.kernel, p.kappa,
+                                                      (p.flags & LS_FLAG_GALERKIN) != 0, ctx->st);
         if (e2 != cudaSuccess) rc = fail(ctx, LS_ERR_CUDA, "create: %s", cudaGetErrorString(e2));
     }
     for (int l = 0; l < 3 && rc == LS_OK; ++l) {

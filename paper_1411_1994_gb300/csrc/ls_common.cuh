@@ -72,8 +72,9 @@ void set_global_error(const char* msg);
 // G0: g[q][j] = w_q^(1/3) exp(-t_q^2 ((j - N + 1/2) h)^2), q < R, j < 2N, for the kernel family
 // (LS_KERNEL_*) and its parameter kappa: weights w = h a(t) cosh(u)/s from the family's
 // Laplace-Gauss density a(t); nodes from q = 1 except for the Newton kernel.
+// galerkin: each entry the average of the Gaussian over its cell [(j - N) h, (j - N + 1) h].
 cudaError_t launch_genvec(double* g, int R, int64_t N, double h, double sinc_step, double t_scale,
-                          int kernel, double kappa, cudaStream_t st);
+                          int kernel, double kappa, bool galerkin, cudaStream_t st);
 
 // G1/G2: out[c][i] = sum_{k<wcnt[c]} g[colq[c]][i - win[woff[c]+k] + N],
 // for columns c in [c0, c0 + ncols); out has row stride N.

@@ -22,8 +22,14 @@ namespace {
 // ---------------------------------------------------------------------------
 // G0 / G1 / G2 and small elementwise kernels
 // ---------------------------------------------------------------------------
+// Gauss-Legendre rule on [-1, 1] for the Galerkin cell averages
+constexpr int kGl = 24;
+struct GlRule {
+    double x[kGl], w[kGl];
+};
+
 __global__ void k_genvec(double* g, int R, int64_t N, double h, double sinc_step, double t_scale, int kernel,
-                         double kappa) {
+                         double kappa, int galerkin, GlRule gl) {
     // the Newton kernel's nodes are q = 0..R-1; every other kernel's density vanishes at t = 0,
     // so its nodes are q = 1..R
     const bool newton = kernel == LS_KERNEL_YUKAWA && kappa == 0.0;
@@ -48,8 +54,66 @@ __global__ void k_genvec(double* g, int R, int64_t N, double h, double sinc_step
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < 2 * N;
          j += (int64_t)gridDim.x * blockDim.x) {
         const double x = ((double)(j - N) + 0.5) * h;
-        g[row * 2 * N + j] = a * exp(-t2 * (x * x));
+        double v;
+        if (!galerkin) {
+            v = exp(-t2 * (x * x));
+        } else if (t == 0.0) {
+            v = 1.0;
+        } else if (t * h <= 10.0) {
+            // average over the cell [x - h/2, x + h/2]: the Gaussian is smooth on the cell's scale
+            double acc = 0.0;
+#pragma unroll 4
+            for (int i = 0; i < kGl; ++i) {
+                const double y = t * (x + 0.5 * h * gl.x[i]);
+                acc += gl.w[i] * exp(-y * y);
+            }
+            v = 0.5 * acc;
+        } else {
+            // a narrow Gaussian: the cell lies on one side of 0, and erfc of its near end dominates
+            const double c0 = x - 0.5 * h, c1 = x + 0.5 * h;
+            const double d = c0 >= 0.0 ? erfc(t * c0) - erfc(t * c1) : erfc(-t * c1) - erfc(-t * c0);
+            v = 0.88622692545275801365 / (t * h) * d;   // sqrt(pi)/2
+        }
+        g[row * 2 * N + j] = a * v;
     }
+}
+
+// nodes and weights of the n-point Gauss-Legendre rule: the roots of P_n by Newton's method
+// from the Chebyshev-like start cos(pi (i + 3/4) / (n + 1/2)), P_n and P_n' by the three-term
+// recurrence; w_i = 2 / ((1 - x_i^2) P_n'(x_i)^2)
+GlRule gauss_legendre() {
+    GlRule r{};
+    const int n = kGl;
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double x = cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+        }
+        const double wi = 2.0 / ((1.0 - x * x) * dp * dp);
+        r.x[i] = -x;
+        r.w[i] = wi;
+        r.x[n - 1 - i] = x;
+        r.w[n - 1 - i] = wi;
+    }
+    return r;
 }
 
 // columns c0 .. c0 + ncols - 1, element (c, i) at out[c * N + i]: blocks walk the
@@ -900,9 +964,10 @@ int coop_blocks(K kernel, int threads, size_t smem, int num_sms, int64_t want) {
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_genvec(double* g, int R, int64_t N, double h, double sinc_step, double t_scale,
-                          int kernel, double kappa, cudaStream_t st) {
+                          int kernel, double kappa, bool galerkin, cudaStream_t st) {
+    static const GlRule gl = gauss_legendre();
     dim3 grid((unsigned)((2 * N + 255) / 256 < 1024 ? (2 * N + 255) / 256 : 1024), R);
-    k_genvec<<<grid, 256, 0, st>>>(g, R, N, h, sinc_step, t_scale, kernel, kappa);
+    k_genvec<<<grid, 256, 0, st>>>(g, R, N, h, sinc_step, t_scale, kernel, kappa, galerkin ? 1 : 0, gl);
     count_kernels(1);
     return cudaGetLastError();
 }

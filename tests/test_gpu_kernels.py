@@ -1,6 +1,8 @@
 """The other kernels of Sec. 2.3 through the C ABI against the FP64 oracle:
 Yukawa exp(-kappa r)/r (Eq. LalpYukawa), Slater exp(-kappa r) (Eq.
-LalpSlater) and the dipole 1/r^3 (Eq. LalpPoly at n = 3/2).
+LalpSlater) and the dipole 1/r^3 (Eq. LalpPoly at n = 3/2); and Galerkin
+reference vectors (cell averages, Eq. galten) for the Newton and Yukawa
+kernels.
 
 Only the reference vectors change (the quadrature weights follow each
 kernel's Laplace-Gauss density and the nodes start at q = 1); the rest of the
@@ -41,7 +43,9 @@ CASES = [W.small_case(L=(3, 2, 2), frac_vac=0.2, frac_imp=0.1, eps=1e-7, kappa=0
          W.small_case(L=(3, 2, 2), frac_vac=0.2, frac_imp=0.1, eps=1e-7, kappa=0.8, kernel=SLA),
          W.small_case(L=(4, 4, 4), N=64, R=20, frac_vac=0.15, frac_imp=0.05, eps=1e-6, kappa=1.5, kernel=SLA),
          W.small_case(L=(3, 2, 2), frac_vac=0.2, frac_imp=0.1, eps=1e-7, kernel=DIP),
-         W.small_case(L=(4, 4, 4), N=64, R=20, frac_vac=0.15, frac_imp=0.05, eps=1e-6, kernel=DIP)]
+         W.small_case(L=(4, 4, 4), N=64, R=20, frac_vac=0.15, frac_imp=0.05, eps=1e-6, kernel=DIP),
+         W.small_case(L=(3, 2, 2), frac_vac=0.2, frac_imp=0.1, eps=1e-7, galerkin=True),
+         W.small_case(L=(4, 4, 4), N=64, R=20, frac_vac=0.15, frac_imp=0.05, eps=1e-6, kappa=0.5, galerkin=True)]
 
 
 def scale_for(wl):
@@ -53,12 +57,13 @@ def scale_for(wl):
 def test_kernel_vectors_and_terms_match_oracle(wl):
     s = scale_for(wl)
     t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s, wl.kappa, wl.kernel)
-    g = O.generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w)
+    g = O.generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w, wl.galerkin)
     cols, tcol, xi = O.canonical_terms(wl.N, wl.box_lo, wl.box_hi, g, wl.blocks, wl.defects)
     ls = P.gpu_ctx(wl, s)
     gg = ls.read(L.LS_READ_GENVEC).reshape(wl.R, 2 * wl.N)
     assert np.all(np.abs(gg - g) <= 1e-13 * np.abs(g).max(1, keepdims=True))
-    # the Newton rule's vectors are not these (the kernel's weights are applied)
+    # the collocated Newton rule's vectors are not these (the kernel's weights or the cell
+    # averages are applied)
     tn, wn = O.sinc_quadrature(wl.R, wl.sinc_step, s)
     gn = O.generating_vectors(wl.N, wl.box_lo, wl.box_hi, tn, wn)
     assert np.max(np.abs(gg - gn)) > 1e-3 * np.abs(gn).max()
@@ -78,7 +83,7 @@ def test_kernel_fp64_reduction_matches_oracle(wl):
     P.forced_rank_parity(wl, s)
 
 
-@pytest.mark.parametrize("wl", CASES[0:2] + CASES[3:4] + CASES[5:6], ids=lambda w: w.name)
+@pytest.mark.parametrize("wl", CASES[0:2] + CASES[3:4] + CASES[5:6] + CASES[8:9], ids=lambda w: w.name)
 def test_kernel_mixed_within_eps(wl):
     s = scale_for(wl)
     orc = P.oracle_run(wl, s)

@@ -108,7 +108,7 @@ def test_point_and_cluster_defects_match_oracle():
 
 def oracle_run(wl, s, eps=None, ranks=None):
     t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s, wl.kappa, wl.kernel)
-    g = O.generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w)
+    g = O.generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w, wl.galerkin)
     cols, tcol, xi = O.canonical_terms(wl.N, wl.box_lo, wl.box_hi, g, wl.blocks, wl.defects)
     res = O.rhosvd(cols, tcol, xi, wl.eps if eps is None else eps, ranks=ranks)
     ncols, _, xin = O.normalise_terms(cols, tcol, xi)
