@@ -128,6 +128,29 @@ def centred_block(L, L_max=None, k0=(0, 0, 0), spacing=1.0, charge=1.0) -> Block
     return Block(tuple(int(x) for x in L), origin, (spacing,) * 3, charge)
 
 
+def skewed_lattice_blocks(L, a1: float, a2, a3, origin=(0.0, 0.0, 0.0), charge=1.0) -> List[Block]:
+    """Sec. 4.4 classes (B) and (C): the lattice of sites origin + i (a1, 0, 0)
+    + j a2 + k a3, 0 <= i < L[0], 0 <= j < L[1], 0 <= k < L[2], with the first
+    lattice vector along x, as a union of rectangular blocks (class A input).
+    Class (B), a3 = (0, 0, d3) and a2 skewed in the (x, y) plane (a
+    parallelogram lattice): one L[0] x 1 x L[2] block per j, so the summation
+    stays agglomerated in two indices and the rank grows like L[1]. Class (C),
+    a3 skewed as well: one L[0] x 1 x 1 block per (j, k), rank growing like
+    L[1] L[2]."""
+    a2, a3 = tuple(float(x) for x in a2), tuple(float(x) for x in a3)
+    blocks = []
+    if a3[0] == 0.0 and a3[1] == 0.0:
+        for j in range(L[1]):
+            o = tuple(origin[d] + j * a2[d] for d in range(3))
+            blocks.append(Block((int(L[0]), 1, int(L[2])), o, (float(a1), 1.0, a3[2]), charge))
+    else:
+        for k in range(L[2]):
+            for j in range(L[1]):
+                o = tuple(origin[d] + j * a2[d] + k * a3[d] for d in range(3))
+                blocks.append(Block((int(L[0]), 1, 1), o, (float(a1), 1.0, 1.0), charge))
+    return blocks
+
+
 def box_for(L_max, spacing=1.0) -> Tuple[float, float]:
     b = (max(L_max) - 1) * spacing + 9.0 * spacing
     return -b / 2.0, b / 2.0

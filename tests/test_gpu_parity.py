@@ -252,6 +252,25 @@ def test_small_cases_fp64(wl):
     forced_rank_parity(wl, s)
 
 
+@pytest.mark.parametrize("cls", ["B", "C"])
+def test_skewed_lattices_fp64(cls):
+    """Sec. 4.4 classes (B) and (C): a parallelogram lattice and a lattice
+    skewed in two directions (unions of rectangular blocks), with vacancies
+    placed at skewed sites as point charges: the full reduction checks."""
+    L3 = (6, 5, 3)
+    a2 = (0.5, 1.0, 0.0)
+    a3 = (0.0, 0.0, 1.0) if cls == "B" else (0.3, 0.25, 1.0)
+    origin = (-4.0, -2.6, -1.2)
+    blocks = W.skewed_lattice_blocks(L3, 1.0, a2, a3, origin)
+    defects = [W.Defect(W.DEFECT_POINT, pos=tuple(origin[d] + i * (1.0 if d == 0 else 0.0) + j * a2[d] + k * a3[d]
+                                                  for d in range(3)), charge=-1.0)
+               for (i, j, k) in ((1, 1, 0), (4, 2, 1), (2, 4, 2))]
+    wl = W.Workload("skew" + cls, 56, -8.0, 8.0, 16, 0.3, 1e-6, blocks, defects, r_min=0.5, slabs=[28, 20])
+    s = scale_for(wl)
+    check_reduction(wl, s)
+    forced_rank_parity(wl, s)
+
+
 def test_cubic_lattice_modes_are_equivalent():
     """A defect-free cubic centred lattice is symmetric under axis
     permutations: equal spectra in all modes and symmetric slabs."""
