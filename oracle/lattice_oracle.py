@@ -111,17 +111,6 @@ def kernel_value(r, kappa: float = 0.0, kernel: int = YUKAWA):
     return np.exp(-kappa * r) / r
 
 
-def error_scale(r, kernel: int = YUKAWA):
-    """The scale m(r) the rule's error is measured against: 1/r for the
-    Yukawa/Newton family, 1 for Slater (bounded at 0), 1/r^3 for the dipole."""
-    r = np.asarray(r, dtype=np.float64)
-    if kernel == SLATER:
-        return np.ones_like(r)
-    if kernel == DIPOLE:
-        return 1.0 / (r * r * r)
-    return 1.0 / r
-
-
 def quadrature_rel_error(t: np.ndarray, w: np.ndarray, r: np.ndarray, kappa: float = 0.0,
                          kernel: int = YUKAWA) -> np.ndarray:
     """r |sum_q w_q exp(-t_q^2 r^2) - p(r)|: the error of the separable
