@@ -518,6 +518,47 @@ def core_tensor(P, tcol, xi, chunk=512) -> np.ndarray:
     return B.reshape(r1, r2, r3)
 
 
+def als_refine(cols, tcol, xi, Z0, sweeps: int = 3, chunk: int = 512):
+    """ALS refinement of a rank-(r1, r2, r3) Tucker approximation of the
+    canonical tensor sum_nu xi_nu a1 (x) a2 (x) a3 (Thm A.1(a)-(c)).
+
+    Thm A.1(a): the best rank-r Tucker approximation maximises ||mu||^2, mu =
+    sum_nu xi_nu (Y1^T a1_nu) (x) (Y2^T a2_nu) (x) (Y3^T a3_nu), over
+    orthonormal Y_l; (b) the maximiser is found by ALS from the RHOSVD start.
+    One ALS step for mode l, with the other two bases fixed, maximises
+    ||Y_l^T B_l||_F for the N x (r_m r_n) matrix B_l = sum_nu xi_nu a_l,nu
+    (x) vec((Y_m^T a_m,nu) (x) (Y_n^T a_n,nu)), so Y_l = its r_l leading left
+    singular vectors (an SVD of B_l). (c) The core is the projection with the
+    final bases. ``cols`` are the terms' vectors (normalised inside, norms
+    moved into xi, as in ``rhosvd``), ``Z0`` the starting bases.
+
+    Returns (Z, core, history), history[s] = ||mu|| after sweep s (history[0]:
+    the start). ||A - A_r||^2 = ||A||^2 - ||mu||^2 for orthonormal bases, so
+    a non-decreasing history is a non-increasing error."""
+    ncols, _, xin = normalise_terms(cols, tcol, xi)
+    Z = [np.array(z, dtype=np.float64) for z in Z0]
+    r = [z.shape[1] for z in Z]
+
+    def core_of(Z):
+        return core_tensor([Z[a].T @ ncols[a].T for a in range(3)], tcol, xin)
+    history = [float(np.linalg.norm(core_of(Z)))]
+    for _ in range(sweeps):
+        for l in range(3):
+            m, n = [a for a in range(3) if a != l]
+            Pm, Pn = Z[m].T @ ncols[m].T, Z[n].T @ ncols[n].T
+            N = ncols[l].shape[1]
+            B = np.zeros((N, r[m] * r[n]))
+            for s0 in range(0, len(xin), chunk):
+                sl = slice(s0, s0 + chunk)
+                al = ncols[l][tcol[sl, l]].T * xin[sl]                       # (N, terms)
+                kr = (Pm[:, None, tcol[sl, m]] * Pn[None, :, tcol[sl, n]]).reshape(r[m] * r[n], -1)
+                B += al @ kr.T
+            U, _, _ = np.linalg.svd(B, full_matrices=False)
+            Z[l] = U[:, :r[l]]
+        history.append(float(np.linalg.norm(core_of(Z))))
+    return Z, core_of(Z), history
+
+
 # ---------------------------------------------------------------------------
 # (d) evaluation on slabs (n-mode products, Eq. Tucker_singePot)
 # ---------------------------------------------------------------------------

@@ -30,6 +30,7 @@ MUTATIONS = {
                                  "        return 1.0 / (r * r * r)\n    return 1.0 / r"),
     "galerkin_cell_shift": ("g[q, j] = c * gaussian_cell_average(float(t[q]), (j - N) * h, (j - N + 1) * h)",
                             "g[q, j] = c * gaussian_cell_average(float(t[q]), (j - N + 0.5) * h, (j - N + 1.5) * h)"),
+    "als_unweighted_terms": ("al = ncols[l][tcol[sl, l]].T * xin[sl]", "al = ncols[l][tcol[sl, l]].T"),
     "slater_prefactor": ("a = (kappa / math.sqrt(math.pi)) / (t * t)", "a = (2.0 * kappa / math.sqrt(math.pi)) / (t * t)"),
     "dipole_power": ("a = (4.0 / math.sqrt(math.pi)) * t * t", "a = (4.0 / math.sqrt(math.pi)) * t"),
 }

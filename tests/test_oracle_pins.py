@@ -600,6 +600,64 @@ def test_defect_free_lattice_needs_at_most_rank_R():
     assert np.linalg.norm(full - O.full_from_tucker(res["Z"], res["B"])) <= 1e-12 * np.linalg.norm(full)
 
 
+# --- ALS refinement after RHOSVD: Thm A.1(a)-(c) ------------------------------
+
+def _hooi_full(T, Z0, sweeps):
+    """HOOI on the explicit N^3 tensor by mode unfoldings: for mode l, the
+    leading left singular vectors of the mode-l unfolding of T x_m Y_m^T x_n
+    Y_n^T. Written on the full tensor, apart from the canonical route."""
+    Z = [np.array(z) for z in Z0]
+    norms = []
+    for _ in range(sweeps):
+        for l in range(3):
+            Y = T
+            for a in range(3):
+                if a != l:
+                    Y = np.moveaxis(np.tensordot(Y, Z[a], axes=([a], [0])), -1, a)
+            U, _, _ = np.linalg.svd(np.moveaxis(Y, l, 0).reshape(T.shape[l], -1), full_matrices=False)
+            Z[l] = U[:, :Z[l].shape[1]]
+        core = np.einsum("ijk,ia,jb,kc->abc", T, Z[0], Z[1], Z[2])
+        norms.append(float(np.linalg.norm(core)))
+    return Z, norms
+
+
+def test_als_matches_full_tensor_hooi_and_improves_on_rhosvd():
+    """From the RHOSVD start, ALS on the canonical terms and HOOI on the
+    explicit tensor give the same core norms sweep by sweep; the norms do not
+    decrease (Thm A.1(a): ALS ascends the dual objective), the error
+    ||A - A_r||^2 = ||A||^2 - ||mu||^2 holds against the explicit tensor, and
+    the refined error is at most the RHOSVD error."""
+    wl = W.small_case(L=(3, 2, 2), N=24, R=10, frac_vac=0.3, frac_imp=0.2, eps=1e-3)
+    s, t, w, g, cols, tcol, xi = _terms(wl)
+    res = O.rhosvd(cols, tcol, xi, wl.eps, ranks=(4, 3, 3))
+    Z, core, hist = O.als_refine(cols, tcol, xi, res["Z"], sweeps=4)
+    full = O.full_from_canonical(cols, tcol, xi)
+    _, norms_full = _hooi_full(full, res["Z"], 4)
+    assert np.allclose(hist[1:], norms_full, rtol=1e-10, atol=0)
+    assert all(b >= a * (1 - 1e-13) for a, b in zip(hist, hist[1:]))
+    for a in range(3):
+        assert np.max(np.abs(Z[a].T @ Z[a] - np.eye(Z[a].shape[1]))) < 1e-12
+    approx = np.einsum("abc,ia,jb,kc->ijk", core, Z[0], Z[1], Z[2])
+    err2 = float(np.sum((full - approx) ** 2))
+    assert abs(err2 - (np.sum(full ** 2) - hist[-1] ** 2)) <= 1e-9 * np.sum(full ** 2)
+    rh = np.einsum("abc,ia,jb,kc->ijk", res["B"], res["Z"][0], res["Z"][1], res["Z"][2])
+    assert err2 <= float(np.sum((full - rh) ** 2)) * (1 + 1e-12)
+    assert hist[-1] > hist[0]
+
+
+def test_als_fixed_point_at_exact_rank():
+    """A defect-free lattice has exact Tucker rank <= R (Thm 3.1): with the
+    RHOSVD bases of that rank the core already holds the whole norm, and ALS
+    keeps it there."""
+    wl = W.small_case(L=(3, 2, 2), N=24, R=8, eps=1e-12)
+    s, t, w, g, cols, tcol, xi = _terms(wl)
+    res = O.rhosvd(cols, tcol, xi, 1e-14)
+    Z, core, hist = O.als_refine(cols, tcol, xi, res["Z"], sweeps=2)
+    full = O.full_from_canonical(cols, tcol, xi)
+    assert abs(hist[0] - np.linalg.norm(full)) <= 1e-12 * np.linalg.norm(full)
+    assert abs(hist[-1] - hist[0]) <= 1e-12 * hist[0]
+
+
 # --- (d) slabs ---------------------------------------------------------------
 
 def test_slab_evaluation_matches_full_tensors(defected_small):
