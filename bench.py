@@ -1,8 +1,10 @@
 #!/usr/bin/env python
 """Throughput of the lattice-sum hot path on GB300: lattice potentials summed
 per second, one step = create (reference vectors + assembled lattice sums) +
-add_defects + rhosvd_reduce on one seeded synthetic workload (default: the
-16^3 lattice, N = 1024, R = 24, 5% vacancies + 2% impurities, eps = 1e-6).
+add_defects + rhosvd_reduce on one seeded synthetic workload. The default is
+the workload the metric is quoted on: the step-shaped lattice (a 48x48x24 and
+a 24^3 block, 3% vacancies, N = 4096, R = 28, eps = 1e-6), mixed path against
+the plain FP64 GPU path on the same inputs.
 
 Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU
 oracle on the host cores instead, on a bounded sample of the same workload.
@@ -37,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--batch-items", type=int, default=256, help="c4: configurations in the batch")
     ap.add_argument("--batch-wave", type=int, default=32, help="c4: contexts reduced per batch_reduce call")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
@@ -45,6 +47,20 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
+
+
+def load_peaks():
+    """HBM GB/s and dense BF16 TFLOP/s: the measured figures of MEASURED_PEAKS.json, else the
+    fallback figures of an earlier GB300 measurement (6800 GB/s, 1900 TFLOP/s burst), marked so."""
+    try:
+        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        if p.get("hbm_gbs") and p.get("bf16_tflops"):
+            p["source"] = "measured (MEASURED_PEAKS.json)"
+            return p
+    except Exception:
+        pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "source": "fallback (no MEASURED_PEAKS.json): 6.8 TB/s, 1.9 PFLOP/s bf16 burst"}
 
 
 def workload(name):
@@ -69,18 +85,77 @@ def oracle_step(wl, s):
     O.pipeline(wl, s, core=True)
 
 
-def time_oracle(wl, budget_s, min_steps=1):
+# the oracle's core einsum is run in full below this many flops (2 r0 r1 r2 T); above it, on a
+# sample of the terms and extrapolated (its time is linear in the number of terms)
+FULL_CORE_FLOPS = 4e11
+CORE_SAMPLE_TERMS = 1024
+GRAM_SAMPLE_ROWS = 2048
+
+
+def oracle_sample(wl, s, ranks=None):
+    """One bounded oracle step on the host cores, as the CPU baseline of the workload.
+
+    Small workloads: the whole oracle pipeline (quadrature, per-site window sums, dgesdd
+    RHOSVD, core einsum). Where the core einsum is too large for a bounded sample (the step
+    lattice: 2 r^3 T ~ 1.4e13 flop), everything but the core is timed in full and the core on
+    its first CORE_SAMPLE_TERMS terms, scaled to all T terms. The 256^3 lattice: (a) + (b)
+    (quadrature, window sums, normalisation) and the Gram matrix of mode 0 on a
+    GRAM_SAMPLE_ROWS-row slice are timed; the rest is extrapolated at that product's rate:
+    per mode the R-SVD of the N x C side matrix (6 N C^2 + 20 C^3 flop), the projection
+    (2 N r C), and the core (2 r0 r1 r2 T), with r the ranks of the GPU reduction.
+
+    Returns (seconds for one whole step, measured seconds, description of the sample)."""
     from oracle import lattice_oracle as O
-    s, _ = O.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, O.default_r_max(wl))
-    times = []
+    t0 = time.perf_counter()
+    t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s, wl.kappa, wl.kernel)
+    g = O.generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w, wl.galerkin)
+    cols, tcol, xi = O.canonical_terms(wl.N, wl.box_lo, wl.box_hi, g, wl.blocks, wl.defects)
+    T = len(xi)
+    C = [c.shape[0] for c in cols]
+    if wl.N >= 16384:
+        ncols, _, _ = O.normalise_terms(cols, tcol, xi)
+        t1 = time.perf_counter()
+        a = np.ascontiguousarray(ncols[0][:, :GRAM_SAMPLE_ROWS])
+        a @ a.T
+        t2 = time.perf_counter()
+        rate = 2.0 * GRAM_SAMPLE_ROWS * C[0] ** 2 / (t2 - t1)
+        r = ranks or [min(c, 1) for c in C]
+        rest = sum(6.0 * wl.N * c * c + 20.0 * c ** 3 + 2.0 * wl.N * rr * c for c, rr in zip(C, r))
+        rest += 2.0 * r[0] * r[1] * r[2] * T
+        total = (t1 - t0) + rest / rate
+        how = (f"extrapolated: (a)+(b) timed ({t1 - t0:.2f} s), Gram of mode 0 on {GRAM_SAMPLE_ROWS} of "
+               f"{wl.N} rows timed ({t2 - t1:.2f} s, {rate / 1e9:.1f} GFLOP/s); per mode 6NC^2+20C^3 "
+               f"(R-SVD) + 2NrC (projection) and 2 r0 r1 r2 T (core) at that rate, r = {r} from the GPU")
+        return total, t2 - t0, how
+    res = O.rhosvd(cols, tcol, xi, wl.eps, core=False)
+    r = res["r"]
+    core_flops = 2.0 * r[0] * r[1] * r[2] * T
+    if core_flops <= FULL_CORE_FLOPS:
+        O.core_tensor(res["P"], tcol, res["xi"])
+        t2 = time.perf_counter()
+        return t2 - t0, t2 - t0, "full oracle pipeline (quadrature, per-site window sums, dgesdd RHOSVD, core einsum)"
+    t1 = time.perf_counter()
+    n = min(CORE_SAMPLE_TERMS, T)
+    O.core_tensor(res["P"], tcol[:n], res["xi"][:n])
+    t2 = time.perf_counter()
+    total = (t1 - t0) + (t2 - t1) * T / n
+    how = (f"(a)+(b)+(c1)+(c2) timed in full ({t1 - t0:.2f} s: quadrature, per-site window sums, dgesdd "
+           f"RHOSVD, projections); core einsum timed on {n} of {T} terms ({t2 - t1:.2f} s) and scaled to "
+           f"all terms (extrapolated, ranks {r})")
+    return total, t2 - t0, how
+
+
+def time_oracle(wl, s, budget_s, ranks=None):
+    """Bounded oracle samples for budget_s seconds of host time (at least one)."""
+    totals, measured, how = [], 0.0, ""
     t_end = time.perf_counter() + budget_s
-    while len(times) < min_steps or time.perf_counter() < t_end:
-        t0 = time.perf_counter()
-        oracle_step(wl, s)
-        times.append(time.perf_counter() - t0)
-        if len(times) >= 50:
+    while not totals or time.perf_counter() < t_end:
+        tot, m, how = oracle_sample(wl, s, ranks)
+        totals.append(tot)
+        measured += m
+        if len(totals) >= 50:
             break
-    return times
+    return totals, measured, how
 
 
 def cores_used():
@@ -141,24 +216,51 @@ def run_reference(args):
     from oracle import lattice_oracle as O
     s, _ = O.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, O.default_r_max(wl))
     for _ in range(args.warmup):
-        oracle_step(wl, s)
-    times = []
+        oracle_sample(wl, s)
+    totals, how = [], ""
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle_step(wl, s)
-        times.append(time.perf_counter() - t0)
-    ms = 1e3 * sum(times) / len(times)
+        tot, _, how = oracle_sample(wl, s)
+        totals.append(tot)
+    ms = 1e3 * sum(totals) / len(totals)
     value = wl.units / (ms / 1e3)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "potentials/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-            "config": config_of(wl, args, {"l2": "n/a (CPU)"}),
+            "config": config_of(wl, args, {"l2": "n/a (CPU)", "path": "fp64 oracle (CPU)"}),
             "cpu_baseline": {"value": value, "unit": "potentials/s", "cores": cores_used(), "kind": "oracle",
-                             "sample": f"{args.steps} full oracle pipelines of {wl.name} "
-                                       "(quadrature, per-site window sums, dgesdd RHOSVD, core einsum)"},
+                             "sample": f"{args.steps} samples of {wl.name}, each: {how}"},
             "e2e": {"value": value, "unit": "potentials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def oracle_errors(wl, s, zs, xs, rows):
+    """Error of each path's Tucker result against the oracle on sampled grid rows: row (x, :, z)
+    of the untruncated canonical tensor sum_t xi_t a0[c0(t)] (x) a1[c1(t)] (x) a2[c2(t)] is exact
+    in the oracle's terms (Eq. Can_LatticeSum_full), one weighted sum of mode-1 vectors per row.
+    Reports the relative L2 error over the sampled values, the largest absolute error, and that
+    error relative to the largest sampled value."""
+    from oracle import lattice_oracle as O
+    t, w = O.sinc_quadrature(wl.R, wl.sinc_step, s, wl.kappa, wl.kernel)
+    g = O.generating_vectors(wl.N, wl.box_lo, wl.box_hi, t, w, wl.galerkin)
+    cols, tcol, xi = O.canonical_terms(wl.N, wl.box_lo, wl.box_hi, g, wl.blocks, wl.defects)
+    ncols, _, xin = O.normalise_terms(cols, tcol, xi)
+    ref = []
+    for z, xx in zip(zs, xs):
+        part = []
+        for x in xx:
+            wt = xin * ncols[0][tcol[:, 0], x] * ncols[2][tcol[:, 2], z]
+            part.append(np.bincount(tcol[:, 1], weights=wt, minlength=ncols[1].shape[0]) @ ncols[1])
+        ref.append(np.stack(part))
+    ref = np.stack(ref)
+    out = {"reference": "oracle: exact rows of the untruncated canonical tensor (FP64)",
+           "points": int(ref.size), "slabs": list(zs), "rows_per_slab": len(xs[0]), "eps": wl.eps}
+    for name, got in rows.items():
+        d = got - ref
+        out[name] = {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref)),
+                     "max_abs": float(np.abs(d).max()),
+                     "max_rel_to_max": float(np.abs(d).max() / np.abs(ref).max())}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -286,7 +388,7 @@ def roofline(report, info, N, steps, precision, peaks):
         peak = peaks.get("bf16_tflops")
         out.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak if peak else None, "traffic": None,
-                    "peak_source": "of measured bf16 burst (MEASURED_PEAKS.json); the 13 digit MMAs per k16 step "
+                    "peak_source": f"bf16 burst, {peaks.get('source')}; the digit MMAs per k16 step "
                                    "of the exact split products are counted as overhead, not as work"})
     return out
 
@@ -435,11 +537,7 @@ def main():
     s, _ = L.fit_t_scale(wl.R, wl.sinc_step, wl.r_min, math.sqrt(3.0) * (wl.box_hi - wl.box_lo))
     stream = torch.cuda.Stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    peaks = load_peaks()
 
     # the defect list as the C ABI takes it, built once (host input data, like the workload)
     defects_c = L.make_defects(wl.defects) if wl.defects else []
@@ -578,6 +676,21 @@ def main():
                 "write_gbs": written / t / 1e9, "frac_of_measured_hbm": written / t / 1e9 / hbm if hbm else None}
         return res
 
+    def gpu_rows(prec, zs, xs):
+        """Rows xs[k] of slab zs[k] of the path's Tucker result, FP64 output, on the host."""
+        ls = L.LatticeSum.from_workload(wl, s, prec, stream=stream.cuda_stream)
+        ls.add_defects(defects_c)
+        ls.rhosvd_reduce(wl.eps)
+        got = []
+        with torch.cuda.stream(stream):
+            for z, xx in zip(zs, xs):
+                sl = ls.eval_slab_torch([z])
+                got.append(sl[0, xx].cpu().numpy())
+                del sl
+        torch.cuda.synchronize()
+        ls.close()
+        return np.stack(got)
+
     head_prec = L.LS_MIXED if args.precision == "mixed" else L.LS_FP64
     head = timed(head_prec, True)
     head_e2e = None if large else e2e(head_prec)
@@ -600,18 +713,29 @@ def main():
         a.close()
         b.close()
 
+    # sampled grid rows of each path's Tucker result (FP64 output), for the error against the
+    # oracle's exact rows of the untruncated canonical tensor (outside every timed region)
+    acc_z = [int(z) for z in (wl.slabs or [wl.N // 2])[:(4 if large else 8)]]
+    rng = np.random.default_rng(wl.N)
+    acc_x = [[int(x) for x in rng.choice(wl.N, size=(8 if large else 16), replace=False)] for _ in acc_z]
+    rows = {args.precision: gpu_rows(head_prec, acc_z, acc_x)}
+    if other is not None:
+        rows["fp64"] = gpu_rows(L.LS_FP64, acc_z, acc_x)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
-    cpu = None
-    if not args.no_cpu_baseline and world == 1 and not large:
-        times = time_oracle(wl, args.cpu_seconds)
-        cpu = {"value": wl.units / statistics.mean(times), "unit": "potentials/s", "cores": cores_used(),
-               "kind": "oracle",
-               "sample": f"{len(times)} full oracle pipelines of {wl.name} on the host cores "
-                         f"(mean {statistics.mean(times):.2f} s each)"}
     info = head["info"]
+    cpu = None
+    error_vs_oracle = None
+    if not args.no_cpu_baseline and world == 1:
+        totals, measured, how = time_oracle(wl, s, args.cpu_seconds, ranks=info["r"])
+        mean_s = statistics.mean(totals)
+        cpu = {"value": wl.units / mean_s, "unit": "potentials/s", "cores": cores_used(), "kind": "oracle",
+               "sample": f"{len(totals)} samples of {wl.name} on the host cores ({measured:.1f} s of host time; "
+                         f"{mean_s:.2f} s per step), each: {how}"}
+        error_vs_oracle = oracle_errors(wl, s, acc_z, acc_x, rows)
     line = {
         "metric": METRIC, "value": head["value"], "unit": "potentials/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
@@ -632,8 +756,10 @@ def main():
     }
     if large:
         line["large_case_note"] = ("mixed path only (the FP64-path core is ~7e14 DFMA); no e2e read-back of the "
-                                   "~87 GB core and no oracle pipeline (its SVD and core do not fit a bounded CPU "
-                                   "sample); slabs evaluated 16 at a time")
+                                   "~87 GB core; the CPU baseline is an extrapolation from a timed sample (see "
+                                   "cpu_baseline.sample); slabs evaluated 16 at a time")
+    if error_vs_oracle is not None:
+        line["error_vs_oracle"] = error_vs_oracle
     if other is not None:
         line["fp64_path"] = {"value": other["value"], "ms_per_step": other["ms_per_step"],
                              "steps_ms": {k: v["ms"] / args.steps for k, v in other["report"].get("steps", {}).items()}}

@@ -419,14 +419,16 @@ int lattice_sum_profile_report(char* buf, int64_t cap, int64_t* needed_bytes);
  * this library holds until the process exits. A slab needs
  * 8 * (r0 * r1 + r0 * N) bytes of it; larger requests return LS_ERR_ARG and
  * compute nothing; more slabs than fit at once are processed in chunks. The
- * call makes no cudaMalloc, cudaFree or other allocating call. The first call
- * on each device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture on
- * the device begins. All calls share the one array, and it keeps the last
- * call's contents (every element a call reads was written earlier in the same
- * call, so nothing needs clearing): calls whose kernels overlap on the GPU
- * (other streams, other host threads) race on it, so serialise them. Errors
- * are read with lattice_sum_last_error(NULL). Asynchronous on `stream`.
+ * call makes no cudaMalloc, cudaFree or other allocating call, and no host-to-
+ * device copy: the slab indices reach the array as kernel arguments. The first
+ * call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current, and looks it up again when the device's context has
+ * been re-created (cudaDeviceReset); make that first call before any stream
+ * capture on the device begins. All calls share the one array, and it keeps
+ * the last call's contents (every element a call reads was written earlier in
+ * the same call, so nothing needs clearing): calls whose kernels overlap on the
+ * GPU (other streams, other host threads) race on it, so serialise them.
+ * Errors are read with lattice_sum_last_error(NULL). Asynchronous on `stream`.
  */
 int lattice_sum_eval_slab_noalloc(const double* Z0, const double* Z1, const double* Z2, const double* core,
                                   const int32_t* ranks, int64_t N, const int64_t* z_index, int32_t nslab,

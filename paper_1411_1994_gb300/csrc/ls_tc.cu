@@ -691,6 +691,35 @@ int x64_lowdin(int n, const double* const S[], const int k[], double* const D2[]
     return LS_OK;
 }
 
+// D_l = X_l Y_l^T for general strided operands (see X64Mat). Taken as D^T = Y X^T with a
+// transposed store, so that the epilogue's lanes (rows of the 128-row tile) write
+// consecutive entries of a row of D.
+int x64_nt(int n, const X64Mat X[], const X64Mat Y[], double* const D[], const int64_t ld[], int* flag,
+           cudaStream_t st, std::string* err) {
+    for (int g0 = 0; g0 < n; g0 += kX64MaxJobs) {
+        const int ng = std::min(kX64MaxJobs, n - g0);
+        Arena ar(st);
+        SplitBatch sb(st);
+        std::vector<X64Op> xs(ng), ys(ng);
+        std::vector<X64Spec> sp(ng);
+        for (int i = 0; i < ng; ++i) {
+            const int l = g0 + i;
+            if (X[l].cols != Y[l].cols) return tc_err(err, "x64_nt: inner sizes differ", LS_ERR_ARG);
+            const int64_t kp = pad64(std::max<int64_t>(X[l].cols, 1));
+            ys[i] = x64_alloc(ar, Y[l].rows, kp);
+            xs[i] = x64_alloc(ar, X[l].rows, kp);
+            if (!xs[i].ok() || !ys[i].ok()) return tc_err(err, "x64_nt: out of memory", LS_ERR_OOM);
+            sb.add(Y[l].p, Y[l].rows, Y[l].cols, Y[l].si, Y[l].sk, Y[l].rs, ys[i]);
+            sb.add(X[l].p, X[l].rows, X[l].cols, X[l].si, X[l].sk, X[l].rs, xs[i]);
+            sp[i] = X64Spec{&ys[i], &xs[i], Y[l].rows, X[l].rows, TcOut{D[l], ld[l], 0, OUT_F64, 0}, 1};
+        }
+        if (sb.flush() != cudaSuccess) return tc_err(err, "x64_nt: split failed");
+        int rc = gemm_x64(sp.data(), ng, flag, st, err);
+        if (rc != LS_OK) return rc;
+    }
+    return LS_OK;
+}
+
 // D = A B^T (A: M x K, B: N x K, D: M x N, row-major), then a synchronised status check
 int x64_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* D, cudaStream_t st,
                 std::string* err) {

@@ -48,6 +48,17 @@ int x64_small(int n, const double* const A[], const int ta[], const double* cons
 // (elsewhere a Cholesky pass gated on the same value writes it).
 int x64_lowdin(int n, const double* const S[], const int k[], double* const D2[], double* const T[], int* flag,
                cudaStream_t st, std::string* err, double* const gate[] = nullptr);
+// A strided FP64 operand: entry (i, k) = p[i * si + k * sk], i < rows, k < cols, row i scaled
+// by rs[i] when rs (device) is given. A row-major matrix is {p, rows, cols, cols, 1}; its
+// transpose is {p, cols_of_p, rows_of_p, 1, cols_of_p}.
+struct X64Mat {
+    const double* p;
+    int64_t rows, cols, si, sk;
+    const double* rs;
+};
+// D_l = X_l Y_l^T (X_l: rows_x x K, Y_l: rows_y x K; D_l: rows_x x rows_y, row stride ld_l).
+int x64_nt(int n, const X64Mat X[], const X64Mat Y[], double* const D[], const int64_t ld[], int* flag,
+           cudaStream_t st, std::string* err);
 // D = A B^T (row-major, device memory), synchronised, with the status checked.
 int x64_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, int64_t K, double* D, cudaStream_t st,
                 std::string* err);
