@@ -114,7 +114,7 @@ typedef struct {
     double  t_scale;    /* substitution scale s in t = sinh(u)/s (> 0); see             */
                         /* lattice_sum_fit_t_scale                                       */
     int32_t precision;  /* LS_FP64 or LS_MIXED                                           */
-    int32_t flags;      /* 0 or LS_FLAG_GALERKIN                                         */
+    int32_t flags;      /* LS_FLAG_GALERKIN, LS_FLAG_SVD_GRAM or LS_FLAG_SVD_ONESIDED, OR-ed */
     double  kappa;      /* kernel parameter (see kernel); finite, >= 0, and small       */
                         /* enough that kappa^2/(4 t_1^2) <= 600 (t_1 = sinh(s_h)/t_scale) */
     int32_t kernel;     /* LS_KERNEL_YUKAWA: exp(-kappa r)/r, the Newton 1/r at kappa=0 */
@@ -133,6 +133,14 @@ typedef struct {
  * exp(-t_q^2 x^2) times w_q^(1/3), i.e. Eq. (galten) with piecewise-constant basis
  * functions divided by the cell volume, instead of collocation at cell centres */
 #define LS_FLAG_GALERKIN 1
+/* flags: how lattice_sum_rhosvd_reduce finds the singular values of the side
+ * matrices (Def. 4.1). LS_FLAG_SVD_ONESIDED: without squaring them (the
+ * default of LS_FP64 contexts; see lattice_sum_rhosvd_reduce), good down to
+ * about u sigma_1. LS_FLAG_SVD_GRAM: from the eigenvalues of the FP64 Gram
+ * matrix (the default of LS_MIXED contexts), good to about sqrt(8 u T) sigma_1,
+ * which suffices for eps >= 1e-6. At most one of the two. */
+#define LS_FLAG_SVD_GRAM 2
+#define LS_FLAG_SVD_ONESIDED 4
 
 #define LS_KERNEL_YUKAWA 0
 #define LS_KERNEL_SLATER 1
@@ -236,9 +244,21 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n);
  * (sum_{k>r} s_k^2)^(1/2) <= eps (sum_k s_k^2)^(1/2). The projections
  * P_l = Z_l^T A_l and the core
  * mu = sum_nu xi_nu P1[:,c1] (x) P2[:,c2] (x) P3[:,c3] follow.
+ * That is the Gram route (LS_FLAG_SVD_GRAM; LS_MIXED contexts). It squares
+ * the singular values: they are resolved to about sqrt(8 u T) sigma_1.
+ * The non-squaring route (LS_FLAG_SVD_ONESIDED; LS_FP64 contexts): the Gram
+ * route gives a basis Q1 of every direction 1e3 times above the Gram noise;
+ * the residual rows E = A_w - (A_w Q1^T) Q1 give, by the same route, a basis
+ * Q2 of the rest of the range, orthogonal to Q1; one-sided (Hestenes) Jacobi
+ * in FP64 on the rows of B = [Q1; Q2] A_w^T gives the singular values and the
+ * rotation M without forming B B^T; the eps rule (with E's energy outside Q2
+ * in the tail) picks r and Z = M_r [Q1; Q2]. Singular values are then good
+ * to about u sigma_1 and the Tucker result agrees with a dense SVD's to FP64
+ * rounding over the conditioning of the truncation (sigma_1 / gap).
  * `forced_ranks` (host, 3 entries or NULL) overrides the eps rule (each
- * clipped to C_l and to the eigenvalues of the FP64 Gram matrix above its
- * rounding noise 8 u T). Fills *info (may be NULL). Synchronises the stream.
+ * clipped to C_l and, on the Gram route, to the eigenvalues of the FP64 Gram
+ * matrix above its rounding noise 8 u T; on the non-squaring route, to the
+ * dimension of Q). Fills *info (may be NULL). Synchronises the stream.
  * Errors: LS_ERR_ARG (eps <= 0 and no forced ranks), LS_ERR_STATE (called
  * twice), LS_ERR_NOCONVERGE, LS_ERR_TIMEOUT, LS_ERR_OOM, LS_ERR_CUDA.
  */

@@ -341,7 +341,10 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
     if (p.R < 1 || p.R > 64) return fail(ctx, LS_ERR_ARG, "create: R=%d out of range [1,64]", p.R);
     if (!(p.sinc_step > 0) || !(p.t_scale > 0)) return fail(ctx, LS_ERR_ARG, "create: sinc_step and t_scale must be > 0");
     if (p.precision != LS_FP64 && p.precision != LS_MIXED) return fail(ctx, LS_ERR_ARG, "create: unknown precision %d", p.precision);
-    if ((p.flags & ~LS_FLAG_GALERKIN) != 0) return fail(ctx, LS_ERR_ARG, "create: unknown flags 0x%x", p.flags);
+    if ((p.flags & ~(LS_FLAG_GALERKIN | LS_FLAG_SVD_GRAM | LS_FLAG_SVD_ONESIDED)) != 0)
+        return fail(ctx, LS_ERR_ARG, "create: unknown flags 0x%x", p.flags);
+    if ((p.flags & LS_FLAG_SVD_GRAM) && (p.flags & LS_FLAG_SVD_ONESIDED))
+        return fail(ctx, LS_ERR_ARG, "create: LS_FLAG_SVD_GRAM and LS_FLAG_SVD_ONESIDED exclude each other");
     if (const char* why = kernel_args_bad(p.kernel, p.kappa)) return fail(ctx, LS_ERR_ARG, "create: %s", why);
     if (p.kappa > 0.0) {
         // the smallest node's screening factor exp(-kappa^2/(4 t_1^2)) must not underflow
@@ -522,6 +525,15 @@ struct RedState {
     DevStatus hs[10] = {};
     double floor_noise = 0.0;
     int64_t T = 0;
+    // the non-squaring route of the FP64 path runs the Gram-route phases twice with these set:
+    // kind 1 = candidate basis of the side matrix (all eigen-directions above cand_res, no
+    // projection or core), kind 2 = the same for the residual rows E of the side matrix
+    // (weights = the rows' norms, floor_noise given, the basis made orthogonal to reorth)
+    int kind = 0;
+    double cand_res[3] = {0.0, 0.0, 0.0};
+    const double* reorth[3] = {nullptr, nullptr, nullptr};
+    int reorth_m[3] = {0, 0, 0};
+    bool drop[3] = {false, false, false};   // kind 2: no residual direction above cand_res in this mode
 };
 
 #define CUS(call)                                                                                     \
@@ -538,14 +550,16 @@ int red_prepare(RedState& R, PcholJob* pj) {
     cudaStream_t st = ctx->st;
     const int64_t N = ctx->p.N;
     const int64_t T = R.T = (int64_t)ctx->xi.size();
-    R.floor_noise = 8.0 * 1.1102230246251565e-16 * (double)T;   // rounding noise of the Gram matrix (trace T)
-    CUS(dalloc(ctx, &ctx->d_tcol, 3 * T));
-    CUS(dalloc(ctx, &ctx->d_xi, T));
-    CUS(dalloc(ctx, &ctx->d_xin, T));
-    CUS(upload_h2d(ctx->d_tcol, ctx->tcol.data(), 3 * T * sizeof(int32_t), st));
-    count_h2d(3 * T * sizeof(int32_t));
-    CUS(upload_h2d(ctx->d_xi, ctx->xi.data(), T * sizeof(double), st));
-    count_h2d(T * sizeof(double));
+    if (R.kind != 2) {
+        R.floor_noise = 8.0 * 1.1102230246251565e-16 * (double)T;   // rounding noise of the Gram matrix (trace T)
+        CUS(dalloc(ctx, &ctx->d_tcol, 3 * T));
+        CUS(dalloc(ctx, &ctx->d_xi, T));
+        CUS(dalloc(ctx, &ctx->d_xin, T));
+        CUS(upload_h2d(ctx->d_tcol, ctx->tcol.data(), 3 * T * sizeof(int32_t), st));
+        count_h2d(3 * T * sizeof(int32_t));
+        CUS(upload_h2d(ctx->d_xi, ctx->xi.data(), T * sizeof(double), st));
+        count_h2d(T * sizeof(double));
+    }
     CUS(dalloc(ctx, &R.d_st, 10));
     CUS(cudaMemsetAsync(R.d_st, 0, 10 * sizeof(DevStatus), st));
     CUS(dalloc(ctx, &R.d_sel, 9));
@@ -561,22 +575,31 @@ int red_prepare(RedState& R, PcholJob* pj) {
         CUS(dalloc(ctx, &ctx->d_sigma[l], C));
         CUS(dalloc(ctx, &M.G, C * C));
         CUS(dalloc(ctx, &M.L, C * C));
+        // a residual that is all rounding stops the pivoted Cholesky before its first column:
+        // L = 0 then gives H = 0 and the mode is dropped
+        if (R.kind == 2) CUS(cudaMemsetAsync(M.L, 0, C * C * sizeof(double), st));
         CUS(dalloc(ctx, &M.pd, C));
         CUS(dalloc(ctx, &M.cand, kPcholCand));
         CUS(dalloc(ctx, &M.piv, C));
         CUS(dalloc(ctx, &M.w, C));
         CUS(cudaMemsetAsync(ctx->d_sigma[l], 0, C * sizeof(double), st));
-        std::vector<double> wh(C);
-        for (int64_t c = 0; c < C; ++c) wh[c] = sqrt((double)mc.count[c]);
-        CUS(upload_h2d(M.w, wh.data(), C * sizeof(double), st));
-        count_h2d(C * sizeof(double));
+        if (R.kind != 2) {
+            std::vector<double> wh(C);
+            for (int64_t c = 0; c < C; ++c) wh[c] = sqrt((double)mc.count[c]);
+            CUS(upload_h2d(M.w, wh.data(), C * sizeof(double), st));
+            count_h2d(C * sizeof(double));
+        }
         { Scope sc("norms", st); CUS(launch_norm_columns(mc.d_cols, C, N, ctx->d_norms[l], st)); }
+        // residual rows: unit rows weighted by their norms (G = E E^T)
+        if (R.kind == 2) CUS(cudaMemcpyAsync(M.w, ctx->d_norms[l], C * sizeof(double), cudaMemcpyDeviceToDevice, st));
         a[l] = mc.d_cols;
         w[l] = M.w;
         G[l] = M.G;
         // pivoted Cholesky: the energy left outside the pivot columns (<= delta) is discarded with
-        // the tail; with the eps rule delta = 1e-4 eps^2 T, with forced ranks the Gram noise
-        const double delta = R.forced ? (double)C * R.floor_noise : 1e-4 * R.eps * R.eps * (double)T;
+        // the tail; with the eps rule delta = 1e-4 eps^2 T, with forced ranks and in the passes of
+        // the non-squaring route the Gram noise
+        const double delta =
+            (R.forced || R.kind != 0) ? (double)C * R.floor_noise : 1e-4 * R.eps * R.eps * (double)T;
         pj[l] = PcholJob{M.G, M.L, M.pd, M.cand, M.piv, R.d_st + l, C, (int)C, delta};
     }
     {
@@ -621,7 +644,7 @@ int red_after_pchol(RedState& R, JacobiJob* jj) {
         Cs[l] = ctx->mode[l].C;
         // directions whose Rayleigh quotients both stay below tau = 1e-3 eps^2 T / k are discarded
         // together whatever their mixing; forced ranks resolve everything
-        const double tau = R.forced ? 0.0 : 1e-3 * R.eps * R.eps * (double)R.T / (double)k;
+        const double tau = (R.forced || R.kind != 0) ? 0.0 : 1e-3 * R.eps * R.eps * (double)R.T / (double)k;
         jj[l] = JacobiJob{M.H, M.V, M.snap, R.d_st + l, k, R.floor_noise, tau};
     }
     {
@@ -642,9 +665,11 @@ int red_select(RedState& R) {
         SortSelectJob jobs[3];
         for (int l = 0; l < 3; ++l) {
             RedMode& M = R.m[l];
-            const int forced = R.forced ? std::max(1, R.forced[l]) : 0;
+            // candidate bases: every eigen-direction above cand_res (a forced rank of k, clipped)
+            const int forced = R.kind != 0 ? M.k : (R.forced ? std::max(1, R.forced[l]) : 0);
             jobs[l] = SortSelectJob{M.H, M.k, forced, M.cand + kPcholCand - 1, M.perm, ctx->d_sigma[l], M.isl,
                                     R.d_sel + 3 * l};
+            if (R.kind != 0) jobs[l].resolution = R.cand_res[l];
         }
         Scope sc("select", st);
         CUS(launch_sort_select(3, jobs, R.eps, R.floor_noise, st));
@@ -722,6 +747,34 @@ int red_basis(RedState& R, CholJob* cj) {
         if (rc == LS_OK) rc = x64_basis(3, vgc, kl, perm, w, isl, a, Cs, N, rs, Y, &R.d_st[9].flag, st, &err);
         if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: basis: %s", err.c_str());
     }
+    if (R.kind == 2) {
+        // the residual's basis, made orthogonal to the first pass's: Y -= (Y Q1^T) Q1
+        Scope sc("basis", st);
+        double *S[3], *D[3];
+        X64Mat xs[3], ys[3];
+        int64_t ld[3];
+        for (int l = 0; l < 3; ++l) {
+            const int64_t m1 = R.reorth_m[l];
+            CUS(dalloc(ctx, &S[l], (int64_t)rs[l] * m1));
+            CUS(dalloc(ctx, &D[l], (int64_t)rs[l] * N));
+        }
+        std::string err;
+        const int m1i[3] = {R.reorth_m[0], R.reorth_m[1], R.reorth_m[2]};
+        const int64_t m1l[3] = {R.reorth_m[0], R.reorth_m[1], R.reorth_m[2]};
+        int rc = x64_project(3, Yc, rs, R.reorth, m1l, N, S, &R.d_st[9].flag, st, &err);   // S = Y Q1^T
+        for (int l = 0; l < 3; ++l) {
+            xs[l] = X64Mat{S[l], rs[l], m1i[l], m1i[l], 1, nullptr};          // S: r x m1
+            ys[l] = X64Mat{R.reorth[l], N, m1i[l], 1, N, nullptr};           // Q1^T: N x m1
+            ld[l] = N;
+        }
+        if (rc == LS_OK) rc = x64_nt(3, xs, ys, D, ld, &R.d_st[9].flag, st, &err);      // D = S Q1
+        if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: residual basis: %s", err.c_str());
+        for (int l = 0; l < 3; ++l) {
+            CUS(launch_sub(Y[l], D[l], (int64_t)rs[l] * N, st));
+            dfree(ctx, S[l]);
+            dfree(ctx, D[l]);
+        }
+    }
     {
         // CholeskyQR2's first pass: where Y Y^T is within kSeriesGate of I (Frobenius), the
         // series for (Y Y^T)^{-1/2} writes the transform; elsewhere the Cholesky factorisation
@@ -779,6 +832,9 @@ int red_cholqr_mid(RedState& R) {
     return LS_OK;
 }
 
+int red_project_core(RedState& R, ls_tucker_info* info);
+int red_release(RedState& R, ls_tucker_info* info);
+
 // after the second factorisation: Z = L^{-1} Y', projections, core, info
 int red_finish(RedState& R, ls_tucker_info* info) {
     ls_ctx* ctx = R.ctx;
@@ -800,6 +856,16 @@ int red_finish(RedState& R, ls_tucker_info* info) {
         int rc = x64_apply(3, Li, rs, src, N, dst, &R.d_st[9].flag, st, &err);
         if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: CholeskyQR: %s", err.c_str());
     }
+    if (R.kind != 0) return red_release(R, nullptr);
+    return red_project_core(R, info);
+}
+
+// (c2) projection, (c3) core, release of the scratch, status and info (Z in ctx->d_Z)
+int red_project_core(RedState& R, ls_tucker_info* info) {
+    ls_ctx* ctx = R.ctx;
+    cudaStream_t st = ctx->st;
+    const int64_t N = ctx->p.N;
+    const int64_t T = R.T;
     {
         // (c2) projection P_l = Z_l^T A_l, both paths: FP64-grade exact-slice products on the
         // tensor cores (the dense FP64 contraction the truncation rests on)
@@ -862,6 +928,18 @@ int red_finish(RedState& R, ls_tucker_info* info) {
             dfree(ctx, W);
         }
     }
+    dfree(ctx, d_perm_t);
+    dfree(ctx, d_off);
+    return red_release(R, info);
+}
+
+// frees the reduction scratch, reads the statuses back (synchronising the stream), checks
+// them and, for a full reduction (kind 0), fills the info and marks the context reduced
+int red_release(RedState& R, ls_tucker_info* info) {
+    ls_ctx* ctx = R.ctx;
+    cudaStream_t st = ctx->st;
+    const int64_t T = R.T;
+    int32_t Cs[3] = {(int32_t)ctx->mode[0].C, (int32_t)ctx->mode[1].C, (int32_t)ctx->mode[2].C};
     for (int l = 0; l < 3; ++l) {
         RedMode& M = R.m[l];
         for (void* q : {(void*)M.G, (void*)M.L, (void*)M.pd, (void*)M.cand, (void*)M.H, (void*)M.V, (void*)M.snap,
@@ -869,15 +947,17 @@ int red_finish(RedState& R, ls_tucker_info* info) {
                         (void*)M.Gz, (void*)M.Li, (void*)M.D2, (void*)M.U0, (void*)M.S, (void*)M.SLi, (void*)M.Uo, (void*)M.T1,
                         (void*)M.Hp, (void*)M.F2, (void*)M.gate})
             dfree(ctx, q);
+        const int k = M.k;
+        M = RedMode{};
+        M.k = k;
     }
-    dfree(ctx, d_perm_t);
-    dfree(ctx, d_off);
     dfree(ctx, R.d_sel);
+    R.d_sel = nullptr;
     CUS(cudaMemcpyAsync(&R.hs[3], R.d_st + 3, 3 * sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
     CUS(cudaMemcpyAsync(&R.hs[9], R.d_st + 9, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
     count_d2h(4 * sizeof(DevStatus));
     double xin_norm2 = 0.0;
-    if (info) {
+    if (info && R.kind == 0) {
         std::vector<double> xin(T);
         CUS(cudaMemcpyAsync(xin.data(), ctx->d_xin, T * sizeof(double), cudaMemcpyDeviceToHost, st));
         count_d2h(T * sizeof(double));
@@ -887,13 +967,15 @@ int red_finish(RedState& R, ls_tucker_info* info) {
         CUS(cudaStreamSynchronize(st));
     }
     dfree(ctx, R.d_st);
+    R.d_st = nullptr;
     if (R.hs[9].flag == FLAG_TIMEOUT)
         return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: a tensor-core product's bounded wait timed out");
     for (int l = 3; l < 6; ++l) {
         if (R.hs[l].flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: Cholesky grid barrier timed out");
-        if (R.hs[l].flag == FLAG_NOT_SPD)
+        if (R.hs[l].flag == FLAG_NOT_SPD && !R.drop[l - 3])
             return fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: CholeskyQR2 met a non-positive pivot (mode %d)", l - 3);
     }
+    if (R.kind != 0) return LS_OK;
     if (info) {
         memset(info, 0, sizeof *info);
         double ssum = 0.0;
@@ -1043,7 +1125,8 @@ int eigen_all(std::vector<RedState>& R, ls_ctx* const* ctxs, int n, const std::v
 // the cooperative steps (pivoted Cholesky, Jacobi iteration, the two Cholesky
 // factorisations of CholeskyQR2) of all 3n modes as one launch each on the
 // first context's stream, so that no two cooperative grids run at once.
-int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, ls_tucker_info* infos) {
+int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, ls_tucker_info* infos,
+                const RedState* pass = nullptr, RedState* pass_out = nullptr) {
     std::vector<RedState> R(n);
     std::vector<PcholJob> pj(3 * (size_t)n);
     std::vector<JacobiJob> jj(3 * (size_t)n);
@@ -1082,6 +1165,7 @@ int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, l
         return LS_OK;
     };
     for (int i = 0; i < n; ++i) {
+        if (pass) R[i] = *pass;   // a pass of the non-squaring route (one context)
         R[i].ctx = ctxs[i];
         R[i].eps = eps;
         R[i].forced = forced;
@@ -1118,6 +1202,10 @@ int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, l
     }
     if (int rc = sync_all()) return rc;
     for (int i = 0; i < n; ++i)
+        if (R[i].kind == 2)
+            for (int l = 0; l < 3; ++l)   // nothing above the threshold: the kept energy at r = 1 is below it
+                R[i].drop[l] = R[i].sel[l][2] - R[i].sel[l][1] <= R[i].cand_res[l];
+    for (int i = 0; i < n; ++i)
         if (int rc = red_basis(R[i], &cj[3 * i])) return rc;
     if (int rc = chol_all()) return rc;
     for (int i = 0; i < n; ++i)
@@ -1127,7 +1215,258 @@ int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, l
         int rc = red_finish(R[i], infos ? &infos[i] : nullptr);
         if (rc != LS_OK && first_err == LS_OK) first_err = rc;
     }
+    if (pass_out) *pass_out = R[0];
     return first_err;
+}
+
+// a failing CUDA call inside reduce_accurate: the scratch context goes too
+#define CUB(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return bail(fail(ctx, e_ == cudaErrorMemoryAllocation ? LS_ERR_OOM : LS_ERR_CUDA, "%s: %s (%s:%d)", \
+                             #call, cudaGetErrorString(e_), __FILE__, __LINE__));                  \
+    } while (0)
+
+// Whether a context takes the non-squaring route: FP64 contexts by default, either
+// precision on request (LS_FLAG_SVD_ONESIDED), neither with LS_FLAG_SVD_GRAM.
+bool one_sided(const ls_ctx* ctx) {
+    if (ctx->p.flags & LS_FLAG_SVD_GRAM) return false;
+    return ctx->p.precision == LS_FP64 || (ctx->p.flags & LS_FLAG_SVD_ONESIDED);
+}
+
+// The non-squaring route (Def. 4.1 with the singular values of each side matrix itself):
+//  1. the Gram route's candidate basis Q1: every eigen-direction of the weighted Gram matrix
+//     1e3 times above its rounding noise 8 u T (all of them well conditioned);
+//  2. the residual rows E = A_w - (A_w Q1^T) Q1 (the part of the side matrix outside Q1,
+//     formed without squaring) and, by the same route on E, a basis Q2 of its range,
+//     orthogonal to Q1: E's Gram matrix resolves singular values down to about
+//     sqrt(u ||A|| ||E||) instead of sqrt(u) ||A||;
+//  3. one-sided Jacobi on the rows of B = Q A_w^T, Q = [Q1; Q2]: the singular values and
+//     the rotation M, with no product B B^T; the eps rule (or a forced rank) on those values,
+//     with E's energy outside Q2 in the discarded tail;
+//  4. Z = M_r Q, the leading r rotated basis vectors; then the projection and the core.
+int reduce_accurate(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_info* info) {
+    cudaStream_t st = ctx->st;
+    const int64_t N = ctx->p.N;
+    const double u = 1.1102230246251565e-16;
+    const int64_t T = (int64_t)ctx->xi.size();
+    int64_t C[3];
+    for (int l = 0; l < 3; ++l) C[l] = ctx->mode[l].C;
+    // 1. candidate basis Q1 (in ctx->d_Z, m1 rows)
+    RedState p1, r1;
+    p1.kind = 1;
+    for (int l = 0; l < 3; ++l) p1.cand_res[l] = 1e3 * 8.0 * u * (double)T;
+    {
+        ls_ctx* one[1] = {ctx};
+        Scope sc("svd.pass1", st);
+        if (int rc = reduce_many(one, 1, eps, nullptr, nullptr, &p1, &r1)) return rc;
+    }
+    int m1[3];
+    double tail1[3];
+    for (int l = 0; l < 3; ++l) {
+        m1[l] = ctx->r[l];
+        tail1[l] = std::max(r1.sel[l][1], 0.0);
+        dfree(ctx, ctx->d_P[l]);
+        ctx->d_P[l] = nullptr;
+    }
+    DevStatus* ds = nullptr;   // [0]: the tensor-core products' flag; [1..3]: the one-sided Jacobi
+    CU(dalloc(ctx, &ds, 4));
+    CU(cudaMemsetAsync(ds, 0, 4 * sizeof(DevStatus), st));
+    int* flag = &ds[0].flag;
+    double* w[3];
+    for (int l = 0; l < 3; ++l) {
+        std::vector<double> wh(C[l]);
+        for (int64_t c = 0; c < C[l]; ++c) wh[c] = sqrt((double)ctx->mode[l].count[c]);
+        CU(dalloc(ctx, &w[l], C[l]));
+        CU(upload_h2d(w[l], wh.data(), C[l] * sizeof(double), st));
+        count_h2d(C[l] * sizeof(double));
+    }
+    // 2. residual rows E (the columns of a scratch context) and their basis Q2
+    ls_ctx* e = new ls_ctx();
+    e->p = ctx->p;
+    e->st = st;
+    e->num_sms = ctx->num_sms;
+    e->h = ctx->h;
+    auto bail = [&](int rc) {
+        if (!e->err.empty() && ctx->err.empty()) ctx->err = e->err;
+        lattice_sum_destroy(e);
+        return rc;
+    };
+    {
+        Scope sc("svd.residual", st);
+        double *B1[3], *D[3], *B1m[3];
+        X64Mat xs[3], ys[3];
+        int64_t ld[3];
+        for (int l = 0; l < 3; ++l) {
+            ModeCols& em = e->mode[l];
+            em.C = em.cap = C[l];
+            em.count.assign(C[l], 1);
+            if (dalloc(e, &em.d_cols, C[l] * N) != cudaSuccess || dalloc(ctx, &B1[l], (int64_t)m1[l] * C[l]) != cudaSuccess ||
+                dalloc(ctx, &D[l], C[l] * N) != cudaSuccess)
+                return bail(fail(ctx, LS_ERR_OOM, "rhosvd_reduce: out of device memory (residual rows)"));
+            B1m[l] = B1[l];
+            xs[l] = X64Mat{ctx->d_Z[l], m1[l], N, N, 1, nullptr};       // Q1
+            ys[l] = X64Mat{ctx->mode[l].d_cols, C[l], N, N, 1, w[l]};   // A_w (rows)
+            ld[l] = C[l];
+        }
+        std::string err;
+        int rc = x64_nt(3, xs, ys, B1m, ld, flag, st, &err);              // B1 = Q1 A_w^T (m1 x C)
+        for (int l = 0; l < 3; ++l) {
+            xs[l] = X64Mat{B1[l], C[l], m1[l], 1, C[l], nullptr};        // B1^T (C x m1)
+            ys[l] = X64Mat{ctx->d_Z[l], N, m1[l], 1, N, nullptr};        // Q1^T (N x m1)
+            ld[l] = N;
+        }
+        if (rc == LS_OK) rc = x64_nt(3, xs, ys, D, ld, flag, st, &err);  // D = B1^T Q1 (C x N)
+        if (rc != LS_OK) return bail(fail(ctx, rc, "rhosvd_reduce: residual rows: %s", err.c_str()));
+        for (int l = 0; l < 3; ++l) {
+            if (launch_resid_rows(ctx->mode[l].d_cols, w[l], D[l], C[l], N, e->mode[l].d_cols, st) != cudaSuccess)
+                return bail(fail(ctx, LS_ERR_CUDA, "rhosvd_reduce: residual rows launch failed"));
+            dfree(ctx, B1[l]);
+            dfree(ctx, D[l]);
+        }
+    }
+    // E carries the rounding dE of the two products that formed it, ||dE||_F^2 <= about
+    // 2 u^2 T (m1 + 1) (each entry of B1^T Q1 to u sum_i |B1_ic| |Q1_in|, and sum_c w_c^2 = T).
+    // An eigenvalue lambda of E E^T moves by about 2 sqrt(lambda) ||dE v|| (the matrix is
+    // graded), so a direction is real when lambda is well above ||dE||^2: candidates are
+    // taken 100 times above floor = 64 u^2 T (m1 + 1), i.e. singular values above
+    // 80 u sqrt(T (m1 + 1)) (about 1e-13 of sigma_1 on the 16^3 lattice).
+    RedState p2, r2;
+    p2.kind = 2;
+    p2.floor_noise = 0.0;
+    for (int l = 0; l < 3; ++l) {
+        (void)tail1;
+        const double fl = 64.0 * u * u * (double)T * (double)(m1[l] + 1);
+        p2.floor_noise = std::max(p2.floor_noise, fl);
+        p2.cand_res[l] = 1e2 * fl;
+        p2.reorth[l] = ctx->d_Z[l];
+        p2.reorth_m[l] = m1[l];
+    }
+    {
+        ls_ctx* one[1] = {e};
+        Scope sc("svd.pass2", st);
+        if (int rc = reduce_many(one, 1, eps, nullptr, nullptr, &p2, &r2)) return bail(rc);
+    }
+    int m2[3], m[3];
+    double tail2[3];
+    for (int l = 0; l < 3; ++l) {
+        m2[l] = r2.drop[l] ? 0 : (int)std::min<int64_t>(e->r[l], std::max<int64_t>(0, C[l] - m1[l]));
+        tail2[l] = std::max(r2.drop[l] ? r2.sel[l][2] : r2.sel[l][1], 0.0);
+        m[l] = m1[l] + m2[l];
+    }
+    // 3. B = Q A_w^T and its one-sided Jacobi SVD
+    double *Q[3], *Bm[3], *Mr[3], *sig2[3], *isl[3], *extra = nullptr, *sel = nullptr;
+    int32_t* perm[3];
+    {
+        Scope sc("svd.onesided", st);
+        X64Mat xs[3], ys[3];
+        int64_t ld[3];
+        for (int l = 0; l < 3; ++l) {
+            if (dalloc(ctx, &Q[l], (int64_t)m[l] * N) != cudaSuccess || dalloc(ctx, &Bm[l], (int64_t)m[l] * C[l]) != cudaSuccess ||
+                dalloc(ctx, &Mr[l], (int64_t)m[l] * m[l]) != cudaSuccess || dalloc(ctx, &sig2[l], m[l]) != cudaSuccess ||
+                dalloc(ctx, &isl[l], m[l]) != cudaSuccess || dalloc(ctx, &perm[l], m[l]) != cudaSuccess)
+                return bail(fail(ctx, LS_ERR_OOM, "rhosvd_reduce: out of device memory (one-sided Jacobi)"));
+            if (cudaMemcpyAsync(Q[l], ctx->d_Z[l], (size_t)m1[l] * N * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                (m2[l] > 0 && cudaMemcpyAsync(Q[l] + (int64_t)m1[l] * N, e->d_Z[l], (size_t)m2[l] * N * sizeof(double),
+                                              cudaMemcpyDeviceToDevice, st) != cudaSuccess))
+                return bail(fail(ctx, LS_ERR_CUDA, "rhosvd_reduce: basis copy failed"));
+            xs[l] = X64Mat{Q[l], m[l], N, N, 1, nullptr};
+            ys[l] = X64Mat{ctx->mode[l].d_cols, C[l], N, N, 1, w[l]};
+            ld[l] = C[l];
+        }
+        std::string err;
+        int rc = x64_nt(3, xs, ys, Bm, ld, flag, st, &err);               // B = Q A_w^T (m x C)
+        if (rc != LS_OK) return bail(fail(ctx, rc, "rhosvd_reduce: B = Q A^T: %s", err.c_str()));
+        OsjJob jobs[3];
+        for (int l = 0; l < 3; ++l)
+            jobs[l] = OsjJob{Bm[l], C[l], (int)C[l], Mr[l], m[l], sig2[l], ds + 1 + l, 8.0 * u * sqrt((double)C[l])};
+        if (launch_osj(jobs, 3, 40, ctx->num_sms, st) != cudaSuccess)
+            return bail(fail(ctx, LS_ERR_CUDA, "rhosvd_reduce: one-sided Jacobi launch failed"));
+    }
+    // eps rule (or forced rank) on sigma^2, with the energy outside Q in the tail
+    double hsel[3][3];
+    DevStatus hds[4];
+    {
+        Scope sc("select", st);
+        if (dalloc(ctx, &extra, 3) != cudaSuccess || dalloc(ctx, &sel, 9) != cudaSuccess)
+            return bail(fail(ctx, LS_ERR_OOM, "rhosvd_reduce: out of device memory (selection)"));
+        CUB(upload_h2d(extra, tail2, sizeof tail2, st));
+        count_h2d(sizeof tail2);
+        SortSelectJob jobs[3];
+        for (int l = 0; l < 3; ++l) {
+            CUB(cudaMemsetAsync(ctx->d_sigma[l], 0, C[l] * sizeof(double), st));
+            const int fr = forced ? std::max(1, std::min(forced[l], m[l])) : 0;
+            jobs[l] = SortSelectJob{sig2[l], m[l], fr, extra + l, perm[l], ctx->d_sigma[l], isl[l], sel + 3 * l};
+            jobs[l].dstride = 1;
+            jobs[l].resolution = 0.0;
+        }
+        CUB(launch_sort_select(3, jobs, eps, 0.0, st));
+        CUB(cudaMemcpyAsync(hsel, sel, sizeof hsel, cudaMemcpyDeviceToHost, st));
+        CUB(cudaMemcpyAsync(hds, ds, sizeof hds, cudaMemcpyDeviceToHost, st));
+        count_d2h(sizeof hsel + sizeof hds);
+        CUB(cudaStreamSynchronize(st));
+    }
+    for (int l = 0; l < 4; ++l)
+        if (hds[l].flag == FLAG_TIMEOUT) return bail(fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: a bounded wait timed out"));
+    for (int l = 0; l < 3; ++l)
+        if (hds[1 + l].flag == FLAG_NOCONVERGE)
+            return bail(fail(ctx, LS_ERR_NOCONVERGE, "rhosvd_reduce: one-sided Jacobi did not converge (mode %d)", l));
+    // 4. Z = M_r Q
+    {
+        Scope sc("svd.basis", st);
+        double* Ms[3];
+        X64Mat xs[3], ys[3];
+        int64_t ld[3];
+        for (int l = 0; l < 3; ++l) {
+            ctx->r[l] = (int32_t)hsel[l][0];
+            dfree(ctx, ctx->d_Z[l]);
+            ctx->d_Z[l] = nullptr;
+            if (dalloc(ctx, &ctx->d_Z[l], (int64_t)ctx->r[l] * N) != cudaSuccess ||
+                dalloc(ctx, &ctx->d_P[l], (int64_t)ctx->r[l] * C[l]) != cudaSuccess ||
+                dalloc(ctx, &Ms[l], (int64_t)ctx->r[l] * m[l]) != cudaSuccess)
+                return bail(fail(ctx, LS_ERR_OOM, "rhosvd_reduce: out of device memory (basis)"));
+            CUB(launch_gather_rows(Mr[l], m[l], perm[l], ctx->r[l], Ms[l], st));
+            xs[l] = X64Mat{Ms[l], ctx->r[l], m[l], m[l], 1, nullptr};   // M_r (r x m)
+            ys[l] = X64Mat{Q[l], N, m[l], 1, N, nullptr};                // Q^T (N x m)
+            ld[l] = N;
+        }
+        std::string err;
+        int rc = x64_nt(3, xs, ys, ctx->d_Z, ld, flag, st, &err);
+        if (rc != LS_OK) return bail(fail(ctx, rc, "rhosvd_reduce: basis: %s", err.c_str()));
+        for (int l = 0; l < 3; ++l) {
+            for (void* q : {(void*)Ms[l], (void*)Q[l], (void*)Bm[l], (void*)Mr[l], (void*)sig2[l], (void*)isl[l],
+                            (void*)perm[l], (void*)w[l]})
+                dfree(ctx, q);
+        }
+        dfree(ctx, extra);
+    }
+    lattice_sum_destroy(e);
+    // projection, core, statuses and info, as the Gram route finishes
+    RedState rf;
+    rf.ctx = ctx;
+    rf.eps = eps;
+    rf.forced = forced;
+    rf.T = T;
+    rf.floor_noise = 64.0 * u * u * (double)T;   // the singular values' own rounding, squared, per column
+    rf.d_sel = sel;
+    rf.d_st = ds;   // [0] as the products' flag slot is read at [9]: use a fresh status block
+    {
+        DevStatus* d10 = nullptr;
+        CU(dalloc(ctx, &d10, 10));
+        CU(cudaMemsetAsync(d10, 0, 10 * sizeof(DevStatus), st));
+        dfree(ctx, ds);
+        rf.d_st = d10;
+    }
+    for (int l = 0; l < 3; ++l) {
+        for (int j = 0; j < 3; ++j) rf.sel[l][j] = hsel[l][j];
+        rf.sweeps[l] = hds[1 + l].sweeps;
+        int64_t rot = 0;
+        for (int k = 0; k < hds[1 + l].sweeps && k < 64; ++k) rot += hds[1 + l].sweep_active[k];
+        rf.rotations[l] = rot;
+        rf.m[l].k = r1.m[l].k;
+    }
+    return red_project_core(rf, info);
 }
 
 }  // namespace
@@ -1139,7 +1478,8 @@ int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ran
     if (ctx->reduced) return fail(ctx, LS_ERR_STATE, "rhosvd_reduce: already reduced");
     if (!forced_ranks && !(eps > 0.0)) return fail(ctx, LS_ERR_ARG, "rhosvd_reduce: eps must be > 0");
     ls_ctx* one[1] = {ctx};
-    const int rc = reduce_many(one, 1, eps, forced_ranks, info);
+    const int rc = one_sided(ctx) ? reduce_accurate(ctx, eps, forced_ranks, info)
+                                  : reduce_many(one, 1, eps, forced_ranks, info);
     // a large reduction leaves tens of GB of freed scratch in the stream-ordered pool
     // (the stream is synchronised here): when the device runs short, give it back beyond a
     // few GB, so that other allocators on the device can use it
@@ -1162,7 +1502,20 @@ int lattice_sum_batch_reduce(ls_ctx* const* ctxs, int32_t n, double eps, ls_tuck
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return fail(nullptr, LS_ERR_ARG, "batch_reduce: context %d listed twice", i);
     }
-    int rc = reduce_many(ctxs, n, eps, nullptr, infos);
+    // contexts on the non-squaring route one by one, the others together
+    std::vector<ls_ctx*> gram;
+    std::vector<int> gi;
+    int rc = LS_OK;
+    for (int i = 0; i < n && rc == LS_OK; ++i) {
+        if (one_sided(ctxs[i])) rc = reduce_accurate(ctxs[i], eps, nullptr, infos ? &infos[i] : nullptr);
+        else { gram.push_back(ctxs[i]); gi.push_back(i); }
+    }
+    if (rc == LS_OK && !gram.empty()) {
+        std::vector<ls_tucker_info> gin(gram.size());
+        rc = reduce_many(gram.data(), (int)gram.size(), eps, nullptr, infos ? gin.data() : nullptr);
+        if (infos)
+            for (size_t j = 0; j < gram.size(); ++j) infos[gi[j]] = gin[j];
+    }
     if (rc != LS_OK) {
         for (int i = 0; i < n; ++i)
             if (!ctxs[i]->err.empty()) {

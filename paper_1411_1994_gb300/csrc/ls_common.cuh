@@ -152,6 +152,8 @@ cudaError_t launch_jacobi_multi(const JacobiJob* jobs, int njobs, int max_sweeps
 struct SortSelectJob {
     const double* G; int64_t C; int forced; const double* extra; int32_t* perm; double* lam; double* inv_sqrt_lam;
     double* out;
+    int64_t dstride = 0;      // stride between the C values read from G (0: C + 1, the diagonal)
+    double resolution = -1.0; // this job's resolution (< 0: the launch's)
 };
 cudaError_t launch_sort_select(int n, const SortSelectJob* jobs, double eps, double resolution, cudaStream_t st);
 
@@ -193,5 +195,25 @@ cudaError_t launch_core_f64(const double* P0, const double* P1t, const double* P
 cudaError_t launch_eval_f64(const double* const Z[3], const int32_t* r, const double* B, int64_t N,
                             const int32_t* zidx, int nslab, double* work, void* out, int out_f32,
                             cudaStream_t st);
+
+// One-sided (Hestenes) Jacobi in FP64 (ls_osj.cu): rows of B (m x C, row stride ldb) are
+// rotated in pairs, in place, until every pair is orthogonal to within tol (|b_p . b_q| <=
+// tol ||b_p|| ||b_q||); M (m x m, row-major) receives the accumulated rotation (rows: the
+// left singular vectors of the original B as combinations of its rows' index), sig2 (m)
+// the squared row norms (the squared singular values, unsorted). st: zeroed status;
+// st->sweeps receives the sweeps taken (the last one rotates nothing), sweep_active[] the
+// rotations of each sweep; FLAG_NOCONVERGE after max_sweeps (<= 60). Up to three
+// matrices per cooperative launch.
+struct OsjJob {
+    double* B; int64_t ldb; int C; double* M; int m; double* sig2; DevStatus* st; double tol;
+};
+cudaError_t launch_osj(const OsjJob* jobs, int njobs, int max_sweeps, int num_sms, cudaStream_t st);
+// E[c][n] = w[c] A[c][n] - D[c][n] (w may be NULL: 1), rows x N.
+cudaError_t launch_resid_rows(const double* A, const double* w, const double* D, int64_t rows, int64_t N, double* E,
+                              cudaStream_t st);
+// Y[e] -= D[e], e < n.
+cudaError_t launch_sub(double* Y, const double* D, int64_t n, cudaStream_t st);
+// out[j][:] = M[perm[j]][:] (rows of length m), j < r.
+cudaError_t launch_gather_rows(const double* M, int m, const int32_t* perm, int r, double* out, cudaStream_t st);
 
 }  // namespace ls

@@ -645,6 +645,7 @@ __device__ __forceinline__ unsigned long long order_key(double v) {
 }
 struct SelJob {
     const double* G; int C; int forced; const double* extra; int32_t* perm; double* lam; double* isl; double* out;
+    int64_t dstride; double resolution;
 };
 constexpr int kSelMax = 16;
 struct SelArgs {
@@ -655,14 +656,15 @@ __global__ void __launch_bounds__(1024) k_sort_select(const __grid_constant__ Se
     const SelJob& J = A.j[blockIdx.x];
     const int C = J.C;
     const double* G = J.G;
+    const int64_t ds = J.dstride;
     extern __shared__ double s_lam[];                     // [C] sorted, then the suffix sums [C + 1]
     double* suf = s_lam + C;
     for (int k = threadIdx.x; k < C; k += blockDim.x) {
-        const double lk = G[(int64_t)k * C + k];
+        const double lk = G[(int64_t)k * ds];
         const unsigned long long kk = order_key(lk);
         int rank = 0;
         for (int j = 0; j < C; ++j) {
-            const unsigned long long kj = order_key(G[(int64_t)j * C + j]);
+            const unsigned long long kj = order_key(G[(int64_t)j * ds]);
             rank += (kj > kk) || (kj == kk && j < k);
         }
         J.perm[rank] = k;
@@ -698,8 +700,9 @@ __global__ void __launch_bounds__(1024) k_sort_select(const __grid_constant__ Se
         double tail_at_r;
         if (J.forced > 0) {
             // a forced rank is clipped to the eigenvalues the FP64 Gram matrix resolves
+            const double res = J.resolution >= 0.0 ? J.resolution : A.resolution;
             int nres = 0;
-            while (nres < C && s_lam[nres] > A.resolution) ++nres;
+            while (nres < C && s_lam[nres] > res) ++nres;
             r = max(1, min(min(J.forced, C), nres));
             tail_at_r = ex + suf[r];
         } else {
@@ -1078,7 +1081,8 @@ cudaError_t launch_sort_select(int n, const SortSelectJob* jobs, double eps, dou
         int cmax = 1;
         for (int i = 0; i < nj; ++i) {
             const SortSelectJob& J = jobs[j0 + i];
-            a.j[i] = SelJob{J.G, (int)J.C, J.forced, J.extra, J.perm, J.lam, J.inv_sqrt_lam, J.out};
+            a.j[i] = SelJob{J.G, (int)J.C, J.forced, J.extra, J.perm, J.lam, J.inv_sqrt_lam, J.out,
+                            J.dstride > 0 ? J.dstride : J.C + 1, J.resolution};
             cmax = std::max(cmax, (int)J.C);
         }
         const size_t smem = sizeof(double) * (2 * (size_t)cmax + 1);

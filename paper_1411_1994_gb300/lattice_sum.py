@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(HERE, "_lib", "liblattice_sum.so")
 LS_OK, LS_ERR_ARG, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_NOCONVERGE, LS_ERR_STATE, LS_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 LS_FP64, LS_MIXED = 0, 1
 LS_FLAG_GALERKIN = 1   # reference vectors as cell averages (Eq. galten) instead of collocation
+LS_FLAG_SVD_GRAM = 2       # singular values from the FP64 Gram matrix (default of LS_MIXED)
+LS_FLAG_SVD_ONESIDED = 4   # singular values without squaring (default of LS_FP64)
 LS_KERNEL_YUKAWA, LS_KERNEL_SLATER, LS_KERNEL_DIPOLE = 0, 1, 2   # exp(-kappa r)/r (1/r at kappa = 0), exp(-kappa r), 1/r^3
 LS_DEFECT_SITES, LS_DEFECT_POINT = 0, 1
 LS_OUT_F64, LS_OUT_F32 = 0, 1
@@ -257,10 +259,10 @@ class LatticeSum:
     eval_slab, each a direct call of the C ABI."""
 
     def __init__(self, N, box_lo, box_hi, R, sinc_step, t_scale, blocks, precision=LS_FP64, stream=None,
-                 kappa=0.0, kernel=LS_KERNEL_YUKAWA, galerkin=False):
+                 kappa=0.0, kernel=LS_KERNEL_YUKAWA, galerkin=False, flags=0):
         self._lib = lib()
         p = ls_params(int(N), float(box_lo), float(box_hi), int(R), float(sinc_step), float(t_scale),
-                      int(precision), LS_FLAG_GALERKIN if galerkin else 0, float(kappa), int(kernel))
+                      int(precision), (LS_FLAG_GALERKIN if galerkin else 0) | int(flags), float(kappa), int(kernel))
         self._blocks = make_blocks(blocks)
         ctx = C.c_void_p()
         rc = self._lib.lattice_sum_create(C.byref(ctx), C.byref(p), self._blocks, len(blocks),
@@ -272,9 +274,10 @@ class LatticeSum:
         self.info = None
 
     @classmethod
-    def from_workload(cls, wl, t_scale, precision=LS_FP64, stream=None):
+    def from_workload(cls, wl, t_scale, precision=LS_FP64, stream=None, flags=0):
         return cls(wl.N, wl.box_lo, wl.box_hi, wl.R, wl.sinc_step, t_scale, wl.blocks, precision, stream,
-                   getattr(wl, "kappa", 0.0), getattr(wl, "kernel", LS_KERNEL_YUKAWA), getattr(wl, "galerkin", False))
+                   getattr(wl, "kappa", 0.0), getattr(wl, "kernel", LS_KERNEL_YUKAWA), getattr(wl, "galerkin", False),
+                   flags)
 
     def add_defects(self, defects):
         """lattice_sum_add_defects for a sequence of Defect descriptions, or for an ls_defect

@@ -107,11 +107,12 @@ def test_create_validates_arguments_on_host(lib, bad):
 
 
 def test_create_rejects_unknown_flags(lib):
-    """Only LS_FLAG_GALERKIN is a known flag; anything else is refused on the
-    host before the device is touched."""
+    """LS_FLAG_GALERKIN, LS_FLAG_SVD_GRAM and LS_FLAG_SVD_ONESIDED are the known
+    flags, and the two singular-value routes exclude each other; anything else
+    is refused on the host before the device is touched."""
     import ctypes as C
     blocks = L.make_blocks([W.centred_block((2, 2, 2))])
-    for flags in (2, 4, 0x100, -1):
+    for flags in (L.LS_FLAG_SVD_GRAM | L.LS_FLAG_SVD_ONESIDED, 8, 0x100, -1):
         p = L.ls_params(64, -6.0, 6.0, 8, 0.25, 10.0, L.LS_FP64, flags, 0.0, L.LS_KERNEL_YUKAWA)
         ctx = C.c_void_p()
         rc = L.lib().lattice_sum_create(C.byref(ctx), C.byref(p), blocks, 1, None)

@@ -41,8 +41,8 @@ def scale_for(wl):
     return s
 
 
-def run(wl, s, prec, forced=None):
-    ls = L.LatticeSum.from_workload(wl, s, prec)
+def run(wl, s, prec, forced=None, flags=0):
+    ls = L.LatticeSum.from_workload(wl, s, prec, flags=flags)
     ls.add_defects(wl.defects)
     info = ls.rhosvd_reduce(wl.eps, forced_ranks=forced)
     return ls, info
@@ -57,7 +57,9 @@ def rel(a, b):
                                 W.config2()], ids=lambda w: w.name)
 def test_mixed_contractions_match_fp64_path(wl):
     s = scale_for(wl)
-    a, ia = run(wl, s, L.LS_FP64)
+    # the FP64 path on the mixed path's singular-value route (the Gram route), so that the
+    # bases are the same and only the contractions differ
+    a, ia = run(wl, s, L.LS_FP64, flags=L.LS_FLAG_SVD_GRAM)
     b, ib = run(wl, s, L.LS_MIXED)
     assert ib["r"] == ia["r"]
     for m in range(3):
@@ -96,7 +98,45 @@ def test_mixed_slabs_meet_eps_against_oracle():
         worst = max(worst, float(np.max(np.abs(out[k] - ref))))
     err = math.sqrt(num / den)
     assert err <= wl.eps, err
+    # the largest pointwise error, relative to the largest value: also within eps
+    assert worst <= wl.eps * float(np.max(np.abs(out))), worst
     ls.close()
+
+
+@pytest.mark.parametrize("wl", [W.config2(), W.small_case(L=(4, 3, 2), N=64, frac_vac=0.15, frac_imp=0.1, eps=1e-6)],
+                         ids=lambda w: w.name)
+def test_mixed_against_fp64_path_at_common_ranks(wl):
+    """The mixed path (Gram route, tensor-core contractions) against the FP64
+    path (non-squaring route, FP64 contractions) at the FP64 path's ranks:
+    the Gram route's subspace and the contractions together stay within
+    1e-7 of the FP64 result on slabs, far inside eps."""
+    s = scale_for(wl)
+    a, ia = run(wl, s, L.LS_FP64)
+    b, ib = run(wl, s, L.LS_MIXED, forced=ia["r"])
+    assert ib["r"] == ia["r"]
+    z = wl.slabs[:8]
+    sa = a.eval_slab_torch(z).cpu().numpy()
+    sb = b.eval_slab_torch(z).cpu().numpy()
+    assert rel(sb, sa) < 1e-7, rel(sb, sa)
+    a.close()
+    b.close()
+
+
+def test_mixed_context_on_the_non_squaring_route():
+    """LS_FLAG_SVD_ONESIDED on a mixed context: its ranks and bases are the FP64
+    path's (same route), and its slabs agree with them to the contractions'
+    accuracy."""
+    wl = W.small_case(L=(3, 2, 2), frac_vac=0.2, frac_imp=0.1, eps=1e-8)
+    s = scale_for(wl)
+    a, ia = run(wl, s, L.LS_FP64)
+    b, ib = run(wl, s, L.LS_MIXED, flags=L.LS_FLAG_SVD_ONESIDED)
+    assert ib["r"] == ia["r"]
+    for m in range(3):
+        assert np.array_equal(a.read(L.LS_READ_BASIS, m), b.read(L.LS_READ_BASIS, m))
+    z = wl.slabs
+    assert rel(b.eval_slab_torch(z).cpu().numpy(), a.eval_slab_torch(z).cpu().numpy()) < 1e-7
+    a.close()
+    b.close()
 
 
 def test_mixed_single_site_and_ragged_tiles():
@@ -104,7 +144,7 @@ def test_mixed_single_site_and_ragged_tiles():
     leave ragged tensor-core tiles in every dimension."""
     for wl in (W.small_case(L=(1, 1, 1), N=33, eps=1e-6), W.small_case(L=(7, 3, 2), N=70, frac_vac=0.1, eps=1e-5)):
         s = scale_for(wl)
-        a, ia = run(wl, s, L.LS_FP64)
+        a, ia = run(wl, s, L.LS_FP64, flags=L.LS_FLAG_SVD_GRAM)
         b, ib = run(wl, s, L.LS_MIXED)
         assert ib["r"] == ia["r"]
         z = [0, wl.N // 2, wl.N - 1]
