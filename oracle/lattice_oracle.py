@@ -560,6 +560,144 @@ def als_refine(cols, tcol, xi, Z0, sweeps: int = 3, chunk: int = 512):
 
 
 # ---------------------------------------------------------------------------
+# Tucker-reference variant: Thm 3.1(B), Sec. 4.1 (Eqs. Tuck_LatticeKi,
+# Tuck_LatticeSum_full), Thm 4.3 (Tucker-Sum-to-Tucker)
+# ---------------------------------------------------------------------------
+
+def reference_tucker(g: np.ndarray, eps_ref: float):
+    """The rank-r "reference" Tucker tensor of Eq. (TuckRef_sum) on the doubled
+    grid. Reading: the paper obtains it from the canonical reference tensor
+    (its Table 2.1 uses an ALS Can-to-Tucker); here it is the RHOSVD of the
+    reference canonical tensor P = sum_q g_q (x) g_q (x) g_q (Def. 4.1, Thm
+    A.1(c)): the side matrix has the unit vectors g_q/|g_q| as columns (Eq.
+    CP_form), Z = its leading left singular vectors at the relative threshold
+    eps_ref (same rule as the lattice sum), and the core b = sum_q
+    (Z^T g_q) (x) (Z^T g_q) (x) (Z^T g_q). The three modes share g, so they
+    share Z.
+
+    Returns (t, b, sigma): t (r, 2N) the reference Tucker vectors as rows,
+    b (r, r, r), sigma the singular values of the side matrix."""
+    norms = np.sqrt((g * g).sum(1))
+    U, S, _ = np.linalg.svd((g / norms[:, None]).T, full_matrices=False)
+    r = truncation_rank(S, eps_ref)
+    Z = U[:, :r]
+    h = Z.T @ g.T                               # (r, R): Z^T g_q
+    b = np.einsum("iq,jq,kq->ijk", h, h, h)
+    return Z.T.copy(), b, S
+
+
+def tucker_terms(N, box_lo, box_hi, t, b, blocks, defects):
+    """The lattice sum with defects as a sum of Tucker tensors, Sec. 4.1:
+    U_hat = U_0 + sum_s U_s (Eq. Tuck_LatticeSum_full).
+
+    * each rectangular block contributes its assembled Tucker tensor (Thm
+      3.1(B), Eq. Tuck_LatticeSum): mode-l side matrix sum_k W_{m_k} t_m (one
+      1D window sum per Tucker vector and mode), core = charge * b;
+    * each defect contributes the shifted reference Tucker tensor
+      (Eq. Tuck_LatticeKi): side matrix W_m t_m at its vertex (a cluster of
+      sites: the sum of its windows per mode), core = (charge change) * b;
+      a POINT defect: its charge times b at its snapped vertex.
+
+    Returns a list of (F, core, keys): F = 3 arrays (N, r) of side matrices,
+    core (r, r, r), keys = per mode the tuple of window vertices (terms with
+    equal keys share a side matrix)."""
+    r = t.shape[0]
+    terms = []
+    bidx = [block_vertex_indices(bl, N, box_lo, box_hi) for bl in blocks]
+
+    def side(ms):
+        F = np.zeros((N, r))
+        for m in ms:
+            for k in range(r):
+                F[:, k] += window(t[k], m, N)
+        return F
+
+    for bi, bl in enumerate(blocks):
+        keys = [("block", bi, a) for a in range(3)]
+        terms.append(([side(bidx[bi][a]) for a in range(3)], bl.charge * b, keys))
+    for d in defects:
+        if d.kind == SITES:
+            ms = [tuple(bidx[d.block][a][d.site[a] + e] for e in range(d.extent[a])) for a in range(3)]
+        else:
+            ms = [(snap(d.pos[a], N, box_lo, box_hi),) for a in range(3)]
+        terms.append(([side(ms[a]) for a in range(3)], defect_charge(d, blocks) * b, [("win",) + ms[a] for a in range(3)]))
+    return terms
+
+
+def tucker_full(terms) -> np.ndarray:
+    """The full tensor sum_s core_s x1 F1 x2 F2 x3 F3 of a list of Tucker terms (small N)."""
+    N = terms[0][0][0].shape[0]
+    T = np.zeros((N, N, N))
+    for F, core, _ in terms:
+        T += np.einsum("abc,ia,jb,kc->ijk", core, F[0], F[1], F[2], optimize=True)
+    return T
+
+
+def reference_tucker_full(N, box_lo, box_hi, t, b, blocks, defects) -> np.ndarray:
+    """The same lattice sum built site by site from shifted reference Tucker
+    tensors, sum_sites Z_s W_s T_ref (Eq. WindowTuck_sum), before any 1D
+    agglomeration (the identity Thm 3.1(B) asserts). Small N only."""
+    pos, z = charged_centres(N, box_lo, box_hi, blocks, defects)
+    h = mesh_size(N, box_lo, box_hi)
+    T = np.zeros((N, N, N))
+    for p, q in zip(pos, z):
+        m = [int(round((p[a] - box_lo) / h)) for a in range(3)]
+        F = [np.stack([window(t[k], m[a], N) for k in range(t.shape[0])], 1) for a in range(3)]
+        T += q * np.einsum("abc,ia,jb,kc->ijk", b, F[0], F[1], F[2], optimize=True)
+    return T
+
+
+def tucker_sum_rhosvd(terms, eps, ranks=None):
+    """Generalized RHOSVD of a sum of Tucker tensors, Thm 4.3 (Tucker-Sum-to-
+    Tucker), Sec. 4.3 (Eq. SideMTuckS).
+
+    Reading. Thm 4.3 takes the Tucker tensors of the sum as orthogonal (Sec.
+    4.1); what its bound uses is that every side matrix has spectral norm at
+    most 1, so that a projection error in one mode is not amplified by the
+    other two. The assembled block vectors (Thm 3.1(B); the paper notes they
+    lose orthogonality) and cluster windows do not have it, and
+    orthonormalising them (Gram-Schmidt) is ill-conditioned: windowed and
+    assembled Tucker vectors are nearly dependent (condition numbers of 1e6 -
+    1e7 on small lattices), so the orthonormal basis is known only to about
+    u * cond. Here each term's side matrix F_l is scaled to unit Frobenius norm
+    (which bounds its spectral norm by 1) and the scale is moved into its core:
+    F_l -> F_l / |F_l|_F, B_s -> B_s prod_l |F_l|_F. For rank-one terms with
+    unit vectors this is the RHOSVD of a canonical sum (Thm A.1), which the
+    paper names as the special case of the generalized scheme.
+
+    The agglomerated side matrix of mode l concatenates the scaled side
+    matrices of all terms (Eq. SideMTuckS; a side matrix shared by k terms
+    enters k times, or once with weight sqrt(k): the same left singular vectors
+    and values). Its truncated SVD gives Z_l (the eps rule of
+    ``truncation_rank``, or forced ``ranks``); the core is the projection
+    sum_s B_s x_l (Z_l^T F_s) of the sum itself. The bound of Thm 4.3(a) is
+    |B_hat| sum_l (sum_{k > r_l} sigma_{l,k}^2)^(1/2) with
+    |B_hat|^2 = sum_s ||B_s||^2 prod_l |F_{s,l}|_F^2.
+
+    Returns a dict: Z (3 x (N, r_l)), sigma, r, d, B (core), bound, Bhat."""
+    out = {"Z": [], "sigma": [], "r": [], "d": []}
+    scale = [[float(np.linalg.norm(F[a])) for a in range(3)] for F, _, _ in terms]
+    for a in range(3):
+        side = np.concatenate([F[a] / sc[a] for (F, _, _), sc in zip(terms, scale)], axis=1)
+        U, S, _ = np.linalg.svd(side, full_matrices=False)
+        r = truncation_rank(S, eps) if ranks is None else int(ranks[a])
+        out["Z"].append(U[:, :r])
+        out["sigma"].append(S)
+        out["r"].append(r)
+        out["d"].append(math.sqrt(float(np.sum(S[r:] ** 2))))
+    B = np.zeros(tuple(out["r"]))
+    Bhat2 = 0.0
+    for (F, core, _), sc in zip(terms, scale):
+        P = [out["Z"][a].T @ F[a] for a in range(3)]
+        B += np.einsum("abc,ia,jb,kc->ijk", core, P[0], P[1], P[2], optimize=True)
+        Bhat2 += float(np.sum(core * core)) * (sc[0] * sc[1] * sc[2]) ** 2
+    out["B"] = B
+    out["Bhat"] = math.sqrt(Bhat2)
+    out["bound"] = out["Bhat"] * sum(out["d"])
+    return out
+
+
+# ---------------------------------------------------------------------------
 # (d) evaluation on slabs (n-mode products, Eq. Tucker_singePot)
 # ---------------------------------------------------------------------------
 

@@ -33,6 +33,14 @@ MUTATIONS = {
     "als_unweighted_terms": ("al = ncols[l][tcol[sl, l]].T * xin[sl]", "al = ncols[l][tcol[sl, l]].T"),
     "slater_prefactor": ("a = (kappa / math.sqrt(math.pi)) / (t * t)", "a = (2.0 * kappa / math.sqrt(math.pi)) / (t * t)"),
     "dipole_power": ("a = (4.0 / math.sqrt(math.pi)) * t * t", "a = (4.0 / math.sqrt(math.pi)) * t"),
+    "tucker_bhat_unscaled": ("Bhat2 += float(np.sum(core * core)) * (sc[0] * sc[1] * sc[2]) ** 2",
+                             "Bhat2 += float(np.sum(core * core))"),
+    "tucker_defect_new_charge": ("terms.append(([side(ms[a]) for a in range(3)], defect_charge(d, blocks) * b,",
+                                 "terms.append(([side(ms[a]) for a in range(3)], d.charge * b,"),
+    "tucker_core_mode_swap": ("P = [out[\"Z\"][a].T @ F[a] for a in range(3)]",
+                              "P = [out[\"Z\"][a].T @ F[(a + 1) % 3] for a in range(3)]"),
+    "tucker_reference_unprojected": ("h = Z.T @ g.T                               # (r, R): Z^T g_q",
+                                     "h = Z.T @ (g / np.sqrt((g * g).sum(1))[:, None]).T"),
 }
 
 

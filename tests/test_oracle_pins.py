@@ -681,3 +681,130 @@ def test_paper_rank_claims_fixture():
         claims = json.load(f)
     assert claims["thm_3_1_rank_factor"] == 1
     assert claims["sec_4_4_sublattice_rank_factor_max"] == 2
+
+
+# --- Tucker-reference variant: Thm 3.1(B), Sec. 4.1, Thm 4.3 ----------------
+
+@pytest.fixture(scope="module")
+def tucker_small():
+    """A 4x3x3 lattice with vacancies, impurities, a 2x2x2 cluster and an off-lattice
+    charge; reference Tucker tensor at eps_ref = 1e-7."""
+    wl = W.small_case(L=(4, 3, 3), N=40, frac_vac=0.15, frac_imp=0.1, eps=1e-6)
+    defects = list(wl.defects) + [W.Defect(W.DEFECT_SITES, 0, (1, 1, 0), (2, 2, 2), charge=1.3),
+                                  W.Defect(W.DEFECT_POINT, pos=(0.37, -1.1, 0.5), charge=0.7)]
+    s, t, w, g, cols, tcol, xi = _terms(wl)
+    tt, b, sig = O.reference_tucker(g, 1e-7)
+    terms = O.tucker_terms(wl.N, wl.box_lo, wl.box_hi, tt, b, wl.blocks, defects)
+    return wl, defects, g, tt, b, sig, terms
+
+
+def test_reference_tucker_within_thm_A1d_bound():
+    """The reference Tucker tensor (RHOSVD of the reference canonical tensor on the
+    doubled grid) is within the Thm A.1(d) bound of the canonical reference tensor,
+    its vectors are orthonormal, and a tiny threshold reproduces it."""
+    wl = W.small_case(L=(1, 1, 1), N=20, R=12, eps=1e-6)
+    s, t, w, g, cols, tcol, xi = _terms(wl)
+    P = np.einsum("qi,qj,qk->ijk", g, g, g)
+    for eps_ref in (1e-3, 1e-6, 1e-10):
+        tt, b, sig = O.reference_tucker(g, eps_ref)
+        assert np.max(np.abs(tt @ tt.T - np.eye(tt.shape[0]))) < 1e-13
+        T = np.einsum("abc,ai,bj,ck->ijk", b, tt, tt, tt)
+        r = tt.shape[0]
+        d = math.sqrt(float(np.sum(sig[r:] ** 2)))
+        xi = np.sqrt((g * g).sum(1)) ** 3
+        assert np.linalg.norm(P - T) <= np.linalg.norm(xi) * 3 * d * (1 + 1e-9) + 1e-14 * np.linalg.norm(P)
+    tt, b, sig = O.reference_tucker(g, 1e-15)
+    T = np.einsum("abc,ai,bj,ck->ijk", b, tt, tt, tt)
+    assert np.linalg.norm(P - T) <= 1e-12 * np.linalg.norm(P)
+
+
+def test_tucker_lattice_sum_sitewise_identity(tucker_small):
+    """Thm 3.1(B) and Eq. (Tuck_LatticeSum_full): the assembled Tucker block terms plus
+    the shifted reference Tucker defect terms equal the site-by-site sum of shifted
+    reference Tucker tensors with the net charges (an exact identity)."""
+    wl, defects, g, tt, b, sig, terms = tucker_small
+    A = O.tucker_full(terms)
+    S = O.reference_tucker_full(wl.N, wl.box_lo, wl.box_hi, tt, b, wl.blocks, defects)
+    assert np.linalg.norm(A - S) <= 1e-13 * np.linalg.norm(S)
+
+
+def test_tucker_lattice_sum_near_canonical_sum(tucker_small):
+    """The Tucker lattice sum differs from the canonical one (the same lattice and
+    defects) by at most the reference approximation error times the sum of |charges|."""
+    wl, defects, g, tt, b, sig, terms = tucker_small
+    cols, tcol, xi = O.canonical_terms(wl.N, wl.box_lo, wl.box_hi, g, wl.blocks, defects)
+    C = O.full_from_canonical(cols, tcol, xi)
+    A = O.tucker_full(terms)
+    P = np.einsum("qi,qj,qk->ijk", g, g, g)
+    Tref = np.einsum("abc,ai,bj,ck->ijk", b, tt, tt, tt)
+    pos, z = O.charged_centres(wl.N, wl.box_lo, wl.box_hi, wl.blocks, defects)
+    assert np.linalg.norm(A - C) <= np.sum(np.abs(z)) * np.linalg.norm(P - Tref) * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-4, 1e-6, 1e-8])
+def test_tucker_sum_within_thm43_bound(tucker_small, eps):
+    """Thm 4.3(a): ||U_hat - U_r|| <= |B_hat| sum_l (sum_{k>r_l} sigma_{l,k}^2)^(1/2),
+    on the full tensor; the bases orthonormal."""
+    wl, defects, g, tt, b, sig, terms = tucker_small
+    full = O.tucker_full(terms)
+    res = O.tucker_sum_rhosvd(terms, eps)
+    approx = O.full_from_tucker(res["Z"], res["B"])
+    err = np.linalg.norm(full - approx)
+    assert err <= res["bound"] * (1 + 1e-9) + 1e-14 * np.linalg.norm(full), (err, res["bound"])
+    for Z in res["Z"]:
+        assert np.max(np.abs(Z.T @ Z - np.eye(Z.shape[1]))) < 1e-13
+    # the orthogonal projection of U_hat onto the bases, by explicit mode products
+    P = [Z @ Z.T for Z in res["Z"]]
+    proj = np.einsum("ia,jb,kc,abc->ijk", P[0], P[1], P[2], full, optimize=True)
+    assert np.linalg.norm(proj - approx) <= 1e-12 * np.linalg.norm(full)
+
+
+def test_tucker_sum_tiny_eps_reproduces(tucker_small):
+    wl, defects, g, tt, b, sig, terms = tucker_small
+    full = O.tucker_full(terms)
+    res = O.tucker_sum_rhosvd(terms, 1e-15)
+    assert np.linalg.norm(full - O.full_from_tucker(res["Z"], res["B"])) <= 1e-12 * np.linalg.norm(full)
+
+
+def test_tucker_sum_of_rank_one_terms_is_the_canonical_rhosvd(defected_small):
+    """Sec. 4.1: the RHOSVD of a canonical sum is the special case of the generalized
+    scheme for rank-one Tucker tensors. Each canonical term as a Tucker term (side
+    matrices the term's three vectors, core its charge): the same singular values,
+    ranks, result and bound as ``rhosvd``."""
+    wl, cols, tcol, xi, full = defected_small
+    terms = [([cols[a][tcol[t, a]][:, None] for a in range(3)], np.array([[[xi[t]]]]), None)
+             for t in range(len(xi))]
+    for eps in (1e-3, 1e-6):
+        a = O.tucker_sum_rhosvd(terms, eps)
+        c = O.rhosvd(cols, tcol, xi, eps)
+        assert a["r"] == c["r"]
+        for l in range(3):
+            n = len(c["sigma"][l])
+            assert np.allclose(a["sigma"][l][:n], c["sigma"][l], rtol=0, atol=1e-12 * c["sigma"][l][0])
+        ta, tc = O.full_from_tucker(a["Z"], a["B"]), O.full_from_tucker(c["Z"], c["B"])
+        assert np.linalg.norm(ta - tc) <= 1e-12 * np.linalg.norm(tc)
+        assert abs(a["bound"] - c["bound"]) <= 1e-10 * c["bound"]
+
+
+def test_tucker_core_as_canonical_sum(tucker_small):
+    """The core of Thm 4.3 written as a canonical sum: the reference core is
+    b = sum_q h_q^(x3) with h_q = Z_ref^T g_q, so each term's projection
+    sum_s B_s x_l (Z_l^T F_s) equals the canonical core (Thm A.1(c)) of the lattice
+    sum whose reference vectors are the projected g'_q = Z_ref Z_ref^T g_q, with the
+    same bases Z_l (the form the CUDA path contracts)."""
+    wl, defects, g, tt, b, sig, terms = tucker_small
+    res = O.tucker_sum_rhosvd(terms, 1e-6)
+    gp = (tt.T @ (tt @ g.T)).T                     # rows g'_q
+    cols, tcol, xi = O.canonical_terms(wl.N, wl.box_lo, wl.box_hi, gp, wl.blocks, defects)
+    P = [res["Z"][a].T @ cols[a].T for a in range(3)]
+    Bc = O.core_tensor(P, tcol, xi)
+    assert np.linalg.norm(Bc - res["B"]) <= 1e-12 * np.linalg.norm(res["B"])
+    # and |B_hat|^2 = ||b||^2 sum_s charge_s^2 prod_l |F_{s,l}|_F^2 with
+    # ||b||^2 = sum_{q,q'} (h_q . h_q')^3, h_q = Z_ref^T g_q (the form the CUDA path uses)
+    h = tt @ g.T
+    b2 = float(np.sum((h.T @ h) ** 3))
+    assert abs(b2 - float(np.sum(b * b))) <= 1e-12 * b2
+    R = g.shape[0]
+    bh2 = sum(xi[s_idx * R] ** 2 * b2 * np.prod([np.linalg.norm(F[a]) ** 2 for a in range(3)])
+              for s_idx, (F, core, keys) in enumerate(terms))
+    assert abs(math.sqrt(bh2) - res["Bhat"]) <= 1e-12 * res["Bhat"]
