@@ -102,6 +102,8 @@ extern "C" {
 #define LS_READ_BASIS    6  /* double [r_l][N] orthonormal Tucker vectors of mode l      */
 #define LS_READ_PROJ     7  /* double [r_l][C_l] projections Z_l^T a_c                   */
 #define LS_READ_CORE     8  /* double [r1][r2][r3] Tucker core (r3 fastest)              */
+#define LS_READ_TUCKER_REF 9 /* double [r_ref][2N] reference Tucker vectors (Tucker-       */
+                            /*                 reference contexts)                       */
 
 typedef struct ls_ctx ls_ctx;
 
@@ -120,6 +122,8 @@ typedef struct {
     int32_t kernel;     /* LS_KERNEL_YUKAWA: exp(-kappa r)/r, the Newton 1/r at kappa=0 */
                         /* LS_KERNEL_SLATER: exp(-kappa r), kappa > 0                    */
                         /* LS_KERNEL_DIPOLE: 1/r^3, kappa = 0                            */
+    double  ref_eps;    /* LS_FLAG_TUCKER_REF: threshold of the reference Tucker tensor  */
+                        /* (0 < ref_eps < 1); ignored otherwise                          */
 } ls_params;
 
 /* kernel families (Sec. 2.3), each a Laplace-Gauss integral
@@ -141,6 +145,20 @@ typedef struct {
  * which suffices for eps >= 1e-6. At most one of the two. */
 #define LS_FLAG_SVD_GRAM 2
 #define LS_FLAG_SVD_ONESIDED 4
+/* flags: the Tucker-reference variant (Thm 3.1(B), Sec. 4.1, Thm 4.3). The
+ * reference tensor is the rank-r_ref Tucker tensor T = sum b_m t_m1 (x) t_m2
+ * (x) t_m3 on the doubled grid, the RHOSVD of the canonical reference tensor
+ * at ref_eps; every block and defect is a Tucker term (assembled or windowed
+ * reference Tucker vectors, core = charge times b), and lattice_sum_rhosvd_-
+ * reduce is the generalized RHOSVD of that sum of Tucker tensors (Thm 4.3):
+ * the agglomerated side matrix of mode l concatenates every term's r_ref
+ * vectors, each term's block scaled to unit Frobenius norm (the scale moved
+ * into its core, so that every side matrix has spectral norm <= 1, as the
+ * bound needs); its truncated SVD (non-squaring route) gives Z_l, and the
+ * core is the projection of the sum itself. info->xi_norm then holds
+ * |B_hat| = (sum_s ||B_s||^2)^(1/2) and info->bound_abs the Thm 4.3 bound
+ * |B_hat| sum_l d_l. Not with LS_FLAG_SVD_GRAM. */
+#define LS_FLAG_TUCKER_REF 8
 
 #define LS_KERNEL_YUKAWA 0
 #define LS_KERNEL_SLATER 1
@@ -320,6 +338,27 @@ int lattice_sum_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, 
  */
 int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, double abs_floor, int32_t form, double* D,
                            double* V, int32_t* sweeps, void* stream);
+
+/*
+ * lattice_sum_svd_rows -- the one-sided (Hestenes) Jacobi of the non-squaring
+ * route on its own, exposed so that it can be checked against a dense SVD:
+ * the m rows of B (device, m x C, row-major FP64; not modified) are rotated
+ * in pairs, in FP64, until every pair is orthogonal to within tol
+ * (|b_p . b_q| <= tol ||b_p|| ||b_q||; 8 u sqrt(C) in the reduction) or a
+ * sweep's largest such cosine is below 1e-9. Def. 4.1 needs the singular
+ * values of each side matrix; no product B B^T is formed, so each value keeps
+ * the relative accuracy of its row (Demmel & Veselic 1992).
+ * - Outputs: sig2 (device, m) the squared row norms after convergence (the
+ *   squared singular values of B, unsorted); M (device, m x m row-major) the
+ *   accumulated rotation, so that M B has those orthogonal rows (the rows of M
+ *   are the left singular vectors of B); *sweeps (may be NULL) the sweeps
+ *   taken; rotations (host, 64 entries, may be NULL) the rotations per sweep.
+ * - Synchronises `stream` (a cudaStream_t or NULL).
+ * - Errors: LS_ERR_ARG, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_NOCONVERGE (60
+ *   sweeps), LS_ERR_TIMEOUT.
+ */
+int lattice_sum_svd_rows(const double* B, int32_t m, int32_t C, double tol, double* sig2, double* M,
+                         int32_t* sweeps, int64_t* rotations, void* stream);
 
 /*
  * lattice_sum_gemm_nt_mixed -- D = A B^T for device FP64 matrices (A: M x K,

@@ -104,6 +104,16 @@ struct ls_ctx {
     double* d_xin = nullptr;
     DtEvalCache* eval_cache = nullptr;   // tensor-core operands of the slab evaluation
     std::vector<void*> allocs;
+    // Tucker-reference variant (LS_FLAG_TUCKER_REF; Thm 3.1(B), Sec. 4.1, Thm 4.3)
+    bool tucker = false;
+    int r_ref = 0;
+    double* d_t = nullptr;       // [r_ref][2N] reference Tucker vectors
+    double* d_gp = nullptr;      // [R][2N] projected reference vectors g'_q = t^T t g_q
+    double bnorm2 = 0.0;         // ||b||^2 of the reference core
+    ModeCols tmode[3];           // side matrices: the r_ref windowed Tucker vectors of each key
+    std::vector<int32_t> tkey;   // [S][3] key of each Tucker term in each mode
+    std::vector<double> txi;     // [S] charge (change) of each Tucker term
+    const double* gsrc() const { return tucker ? d_gp : d_g; }
 };
 
 namespace {
@@ -166,8 +176,24 @@ void keep_pool(int dev) {
 
 // make room for `add` more columns in mode l and append their descriptors;
 // then assemble them on the device
+int append_columns_to(ls_ctx* ctx, ModeCols& mc, const double* gsrc, const std::vector<int32_t>& q,
+                      const std::vector<std::vector<int32_t>>& wins);
 int append_columns(ls_ctx* ctx, int l, const std::vector<int32_t>& q, const std::vector<std::vector<int32_t>>& wins) {
-    ModeCols& mc = ctx->mode[l];
+    return append_columns_to(ctx, ctx->mode[l], ctx->gsrc(), q, wins);
+}
+// the Tucker side columns of new keys: r_ref windowed (or assembled) reference Tucker vectors each
+int append_side(ls_ctx* ctx, int l, const std::vector<std::vector<int32_t>>& key_wins) {
+    std::vector<int32_t> q;
+    std::vector<std::vector<int32_t>> wins;
+    for (const auto& w : key_wins)
+        for (int k = 0; k < ctx->r_ref; ++k) {
+            q.push_back(k);
+            wins.push_back(w);
+        }
+    return append_columns_to(ctx, ctx->tmode[l], ctx->d_t, q, wins);
+}
+int append_columns_to(ls_ctx* ctx, ModeCols& mc, const double* gsrc, const std::vector<int32_t>& q,
+                      const std::vector<std::vector<int32_t>>& wins) {
     const int64_t add = (int64_t)q.size();
     if (add == 0) return LS_OK;
     const int64_t N = ctx->p.N;
@@ -211,9 +237,94 @@ int append_columns(ls_ctx* ctx, int l, const std::vector<int32_t>& q, const std:
     CU(upload_h2d(mc.d_win, mc.win.data(), mc.win.size() * sizeof(int32_t), ctx->st));
     count_h2d((int64_t)(mc.win.size() * sizeof(int32_t)));
     Scope sc_asm("assemble", ctx->st);
-    CU(launch_assemble(ctx->d_g, N, mc.d_desc, mc.d_desc + mc.cap, mc.d_desc + 2 * mc.cap, mc.d_win, c0, add,
+    CU(launch_assemble(gsrc, N, mc.d_desc, mc.d_desc + mc.cap, mc.d_desc + 2 * mc.cap, mc.d_win, c0, add,
                        mc.d_cols, ctx->st));
     // (the uploads went through pinned staging: the host vectors may change at once)
+    return LS_OK;
+}
+
+// The reference Tucker tensor of the Tucker-reference variant (Eq. TuckRef_sum, Thm 3.1(B)):
+// the RHOSVD of the reference canonical tensor sum_q g_q (x) g_q (x) g_q on the doubled grid.
+// Its side matrix has the unit vectors g_q/|g_q| as columns; one-sided Jacobi on those R rows
+// (M G = rotated rows of norms sigma_k) gives the leading left singular vectors of the side
+// matrix as the rotated rows over sigma_k; r_ref by the eps rule at ref_eps. Then the
+// projected vectors g'_q = t^T (t g_q) (the reference tensor written as a canonical sum,
+// b = sum_q h_q^(x3), h_q = t g_q) and ||b||^2 = sum_{q,q'} (h_q . h_q')^3.
+int make_reference_tucker(ls_ctx* ctx) {
+    cudaStream_t st = ctx->st;
+    const int R = ctx->p.R;
+    const int64_t N2 = 2 * ctx->p.N;
+    const double u = 1.1102230246251565e-16;
+    double *gn = nullptr, *nrm = nullptr, *M = nullptr, *sig2 = nullptr, *lam = nullptr, *isl = nullptr,
+           *sel = nullptr, *H = nullptr, *HH = nullptr, *b2 = nullptr;
+    int32_t* perm = nullptr;
+    DevStatus* ds = nullptr;
+    unsigned* cmax = nullptr;
+    CU(dalloc(ctx, &gn, R * N2));
+    CU(dalloc(ctx, &nrm, R));
+    CU(dalloc(ctx, &M, (int64_t)R * R));
+    CU(dalloc(ctx, &sig2, R));
+    CU(dalloc(ctx, &lam, R));
+    CU(dalloc(ctx, &isl, R));
+    CU(dalloc(ctx, &sel, 3));
+    CU(dalloc(ctx, &perm, R));
+    CU(dalloc(ctx, &ds, 2));
+    CU(dalloc(ctx, &cmax, 64));
+    CU(cudaMemsetAsync(ds, 0, 2 * sizeof(DevStatus), st));
+    CU(cudaMemsetAsync(cmax, 0, 64 * sizeof(unsigned), st));
+    CU(cudaMemcpyAsync(gn, ctx->d_g, sizeof(double) * R * N2, cudaMemcpyDeviceToDevice, st));
+    CU(launch_norm_columns(gn, R, N2, nrm, st));
+    const OsjJob J{gn, N2, (int)N2, M, R, sig2, ds, 8.0 * u * sqrt((double)N2), cmax};
+    CU(launch_osj(&J, 1, 40, ctx->num_sms, st));
+    SortSelectJob sj{sig2, R, 0, nullptr, perm, lam, isl, sel};
+    sj.dstride = 1;
+    sj.resolution = 0.0;
+    CU(launch_sort_select(1, &sj, ctx->p.ref_eps, 0.0, st));
+    double hsel[3];
+    DevStatus hds;
+    CU(cudaMemcpyAsync(hsel, sel, sizeof hsel, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&hds, ds, sizeof hds, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (hds.flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "create: reference Tucker: a bounded wait timed out");
+    if (hds.flag == FLAG_NOCONVERGE) return fail(ctx, LS_ERR_NOCONVERGE, "create: reference Tucker: no convergence");
+    const int r = ctx->r_ref = std::max(1, (int)hsel[0]);
+    CU(dalloc(ctx, &ctx->d_t, (int64_t)r * N2));
+    CU(dalloc(ctx, &ctx->d_gp, R * N2));
+    CU(dalloc(ctx, &H, (int64_t)r * R));
+    CU(dalloc(ctx, &HH, (int64_t)R * R));
+    CU(dalloc(ctx, &b2, 1));
+    // t_k = (rotated row perm[k]) / sigma_k
+    CU(launch_gather_rows(gn, N2, perm, r, isl, ctx->d_t, st));
+    {
+        std::string err;
+        X64Mat xs[1], ys[1];
+        int64_t ld[1];
+        double* D[1];
+        xs[0] = X64Mat{ctx->d_t, r, N2, N2, 1, nullptr};   // t (r x 2N)
+        ys[0] = X64Mat{ctx->d_g, R, N2, N2, 1, nullptr};   // g (R x 2N)
+        ld[0] = R;
+        D[0] = H;
+        int rc = x64_nt(1, xs, ys, D, ld, &ds[1].flag, st, &err);   // H = t g^T (r x R)
+        xs[0] = X64Mat{H, R, r, 1, R, nullptr};               // H^T (R x r)
+        ys[0] = X64Mat{ctx->d_t, N2, r, 1, N2, nullptr};      // t^T (2N x r)
+        ld[0] = N2;
+        D[0] = ctx->d_gp;
+        if (rc == LS_OK) rc = x64_nt(1, xs, ys, D, ld, &ds[1].flag, st, &err);   // g' = H^T t
+        ys[0] = X64Mat{H, R, r, 1, R, nullptr};
+        ld[0] = R;
+        D[0] = HH;
+        if (rc == LS_OK) rc = x64_nt(1, xs, ys, D, ld, &ds[1].flag, st, &err);   // H^T H (R x R)
+        if (rc != LS_OK) return fail(ctx, rc, "create: reference Tucker: %s", err.c_str());
+    }
+    CU(launch_sum_cubes(HH, (int64_t)R * R, b2, st));
+    DevStatus hd1;
+    CU(cudaMemcpyAsync(&ctx->bnorm2, b2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&hd1, ds + 1, sizeof hd1, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (hd1.flag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "create: reference Tucker: a bounded wait timed out");
+    for (void* q : {(void*)gn, (void*)nrm, (void*)M, (void*)sig2, (void*)lam, (void*)isl, (void*)sel, (void*)perm,
+                    (void*)ds, (void*)cmax, (void*)H, (void*)HH, (void*)b2})
+        dfree(ctx, q);
     return LS_OK;
 }
 
@@ -341,8 +452,12 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
     if (p.R < 1 || p.R > 64) return fail(ctx, LS_ERR_ARG, "create: R=%d out of range [1,64]", p.R);
     if (!(p.sinc_step > 0) || !(p.t_scale > 0)) return fail(ctx, LS_ERR_ARG, "create: sinc_step and t_scale must be > 0");
     if (p.precision != LS_FP64 && p.precision != LS_MIXED) return fail(ctx, LS_ERR_ARG, "create: unknown precision %d", p.precision);
-    if ((p.flags & ~(LS_FLAG_GALERKIN | LS_FLAG_SVD_GRAM | LS_FLAG_SVD_ONESIDED)) != 0)
+    if ((p.flags & ~(LS_FLAG_GALERKIN | LS_FLAG_SVD_GRAM | LS_FLAG_SVD_ONESIDED | LS_FLAG_TUCKER_REF)) != 0)
         return fail(ctx, LS_ERR_ARG, "create: unknown flags 0x%x", p.flags);
+    if ((p.flags & LS_FLAG_TUCKER_REF) && !(p.ref_eps > 0.0 && p.ref_eps < 1.0))
+        return fail(ctx, LS_ERR_ARG, "create: LS_FLAG_TUCKER_REF needs 0 < ref_eps < 1");
+    if ((p.flags & LS_FLAG_TUCKER_REF) && (p.flags & LS_FLAG_SVD_GRAM))
+        return fail(ctx, LS_ERR_ARG, "create: the Tucker-reference variant takes the non-squaring route");
     if ((p.flags & LS_FLAG_SVD_GRAM) && (p.flags & LS_FLAG_SVD_ONESIDED))
         return fail(ctx, LS_ERR_ARG, "create: LS_FLAG_SVD_GRAM and LS_FLAG_SVD_ONESIDED exclude each other");
     if (const char* why = kernel_args_bad(p.kernel, p.kappa)) return fail(ctx, LS_ERR_ARG, "create: %s", why);
@@ -395,22 +510,27 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
                                                       (p.flags & LS_FLAG_GALERKIN) != 0, ctx->st);
         if (e2 != cudaSuccess) rc = fail(ctx, LS_ERR_CUDA, "create: %s", cudaGetErrorString(e2));
     }
+    ctx->tucker = (p.flags & LS_FLAG_TUCKER_REF) != 0;
+    if (rc == LS_OK && ctx->tucker) rc = make_reference_tucker(ctx);
     for (int l = 0; l < 3 && rc == LS_OK; ++l) {
         std::vector<int32_t> q;
-        std::vector<std::vector<int32_t>> wins;
-        for (size_t b = 0; b < ctx->blocks.size(); ++b)
+        std::vector<std::vector<int32_t>> wins, keys;
+        for (size_t b = 0; b < ctx->blocks.size(); ++b) {
             for (int qq = 0; qq < R; ++qq) {
                 q.push_back(qq);
                 wins.push_back(ctx->blocks[b].m[l]);
             }
+            keys.push_back(ctx->blocks[b].m[l]);
+        }
         rc = append_columns(ctx, l, q, wins);
+        if (rc == LS_OK && ctx->tucker) rc = append_side(ctx, l, keys);
     }
     if (rc != LS_OK) {
         g_create_error = ctx->err;
         lattice_sum_destroy(ctx);
         return rc;
     }
-    for (size_t b = 0; b < ctx->blocks.size(); ++b)
+    for (size_t b = 0; b < ctx->blocks.size(); ++b) {
         for (int qq = 0; qq < R; ++qq) {
             const int32_t c = (int32_t)(b * R + qq);
             for (int l = 0; l < 3; ++l) {
@@ -419,6 +539,15 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
             }
             ctx->xi.push_back(ctx->blocks[b].b.charge);
         }
+        if (ctx->tucker) {
+            // one Tucker term per block: its assembled side matrix is key b in every mode
+            for (int l = 0; l < 3; ++l) {
+                ctx->tkey.push_back((int32_t)b);
+                for (int k = 0; k < ctx->r_ref; ++k) ctx->tmode[l].count[b * ctx->r_ref + k] += 1;
+            }
+            ctx->txi.push_back(ctx->blocks[b].b.charge);
+        }
+    }
     *out = ctx;
     return LS_OK;
 }
@@ -459,7 +588,7 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n) {
     for (int l = 0; l < 3; ++l) {
         ModeCols& mc = ctx->mode[l];
         std::vector<int32_t> q;
-        std::vector<std::vector<int32_t>> wins;
+        std::vector<std::vector<int32_t>> wins, new_keys;
         const int64_t first_new = mc.C;
         int32_t next = (int32_t)mc.keys.size();
         for (int64_t i = 0; i < n; ++i) {
@@ -472,6 +601,7 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n) {
                     q.push_back(qq);
                     wins.push_back(key[3 * i + l]);
                 }
+                new_keys.push_back(key[3 * i + l]);
             } else {
                 kidx = it->second;
             }
@@ -479,9 +609,10 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n) {
         }
         (void)first_new;
         int rc = append_columns(ctx, l, q, wins);
+        if (rc == LS_OK && ctx->tucker) rc = append_side(ctx, l, new_keys);
         if (rc != LS_OK) return rc;
     }
-    for (int64_t i = 0; i < n; ++i)
+    for (int64_t i = 0; i < n; ++i) {
         for (int qq = 0; qq < R; ++qq) {
             for (int l = 0; l < 3; ++l) {
                 const int32_t c = base[3 * i + l] + qq;
@@ -490,6 +621,16 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n) {
             }
             ctx->xi.push_back(dxi[i]);
         }
+        if (ctx->tucker) {
+            // one Tucker term per defect; key index = column base / R (blocks first)
+            for (int l = 0; l < 3; ++l) {
+                const int32_t kk = base[3 * i + l] / R;
+                ctx->tkey.push_back(kk);
+                for (int k = 0; k < ctx->r_ref; ++k) ctx->tmode[l].count[(int64_t)kk * ctx->r_ref + k] += 1;
+            }
+            ctx->txi.push_back(dxi[i]);
+        }
+    }
     return LS_OK;
 }
 
@@ -747,7 +888,7 @@ int red_basis(RedState& R, CholJob* cj) {
         if (rc == LS_OK) rc = x64_basis(3, vgc, kl, perm, w, isl, a, Cs, N, rs, Y, &R.d_st[9].flag, st, &err);
         if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: basis: %s", err.c_str());
     }
-    if (R.kind == 2) {
+    if (R.kind == 2 && R.reorth[0]) {
         // the residual's basis, made orthogonal to the first pass's: Y -= (Y Q1^T) Q1
         Scope sc("basis", st);
         double *S[3], *D[3];
@@ -1246,29 +1387,67 @@ bool one_sided(const ls_ctx* ctx) {
 //     the rotation M, with no product B B^T; the eps rule (or a forced rank) on those values,
 //     with E's energy outside Q2 in the discarded tail;
 //  4. Z = M_r Q, the leading r rotated basis vectors; then the projection and the core.
-int reduce_accurate(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_info* info) {
+// The terms and the unit canonical vectors for the projection and the core, when the side
+// matrix of the truncation is another one (the Tucker-reference variant): what the Gram
+// route's first phase does for the canonical side matrix.
+int prepare_terms(ls_ctx* ctx) {
+    cudaStream_t st = ctx->st;
+    const int64_t N = ctx->p.N;
+    const int64_t T = (int64_t)ctx->xi.size();
+    CU(dalloc(ctx, &ctx->d_tcol, 3 * T));
+    CU(dalloc(ctx, &ctx->d_xi, T));
+    CU(dalloc(ctx, &ctx->d_xin, T));
+    CU(upload_h2d(ctx->d_tcol, ctx->tcol.data(), 3 * T * sizeof(int32_t), st));
+    count_h2d(3 * T * sizeof(int32_t));
+    CU(upload_h2d(ctx->d_xi, ctx->xi.data(), T * sizeof(double), st));
+    count_h2d(T * sizeof(double));
+    for (int l = 0; l < 3; ++l) {
+        const int64_t C = ctx->mode[l].C;
+        CU(dalloc(ctx, &ctx->d_norms[l], C));
+        CU(dalloc(ctx, &ctx->d_sigma[l], C));
+        CU(cudaMemsetAsync(ctx->d_sigma[l], 0, C * sizeof(double), st));
+        Scope sc("norms", st);
+        CU(launch_norm_columns(ctx->mode[l].d_cols, C, N, ctx->d_norms[l], st));
+    }
+    return LS_OK;
+}
+
+// `side` (may be NULL): a scratch context whose columns are the side matrix of the truncation,
+// its rows already weighted (the Tucker-reference variant's scaled blocks), with side_T their
+// total energy and Bhat the |B_hat| of Thm 4.3; NULL: the canonical side matrix of ctx itself
+// (unit vectors weighted by sqrt(multiplicity)).
+int reduce_accurate(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_info* info, ls_ctx* side = nullptr,
+                    double side_T = 0.0, double Bhat = 0.0) {
     cudaStream_t st = ctx->st;
     const int64_t N = ctx->p.N;
     const double u = 1.1102230246251565e-16;
     const int64_t T = (int64_t)ctx->xi.size();
+    ls_ctx* sx = side ? side : ctx;
     int64_t C[3];
-    for (int l = 0; l < 3; ++l) C[l] = ctx->mode[l].C;
-    // 1. candidate basis Q1 (in ctx->d_Z, m1 rows)
+    for (int l = 0; l < 3; ++l) C[l] = sx->mode[l].C;
+    if (side)
+        if (int rc = prepare_terms(ctx)) return rc;
+    // 1. candidate basis Q1 (in sx->d_Z, m1 rows)
     RedState p1, r1;
-    p1.kind = 1;
-    for (int l = 0; l < 3; ++l) p1.cand_res[l] = 1e3 * 8.0 * u * (double)T;
+    p1.kind = side ? 2 : 1;
+    const double floor1 = 8.0 * u * (side ? side_T : (double)T);
+    p1.floor_noise = floor1;
+    for (int l = 0; l < 3; ++l) p1.cand_res[l] = 1e3 * floor1;
     {
-        ls_ctx* one[1] = {ctx};
+        ls_ctx* one[1] = {sx};
         Scope sc("svd.pass1", st);
-        if (int rc = reduce_many(one, 1, eps, nullptr, nullptr, &p1, &r1)) return rc;
+        if (int rc = reduce_many(one, 1, eps, nullptr, nullptr, &p1, &r1)) {
+            if (side && ctx->err.empty()) ctx->err = side->err;
+            return rc;
+        }
     }
     int m1[3];
     double tail1[3];
     for (int l = 0; l < 3; ++l) {
-        m1[l] = ctx->r[l];
+        m1[l] = sx->r[l];
         tail1[l] = std::max(r1.sel[l][1], 0.0);
-        dfree(ctx, ctx->d_P[l]);
-        ctx->d_P[l] = nullptr;
+        dfree(sx, sx->d_P[l]);
+        sx->d_P[l] = nullptr;
     }
     DevStatus* ds = nullptr;   // [0]: the tensor-core products' flag; [1..3]: the one-sided Jacobi
     CU(dalloc(ctx, &ds, 4));
@@ -1276,6 +1455,10 @@ int reduce_accurate(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_in
     int* flag = &ds[0].flag;
     double* w[3];
     for (int l = 0; l < 3; ++l) {
+        if (side) {
+            w[l] = side->d_norms[l];   // the scratch rows are unit after the first pass; their norms weight them
+            continue;
+        }
         std::vector<double> wh(C[l]);
         for (int64_t c = 0; c < C[l]; ++c) wh[c] = sqrt((double)ctx->mode[l].count[c]);
         CU(dalloc(ctx, &w[l], C[l]));
@@ -1306,21 +1489,21 @@ int reduce_accurate(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_in
                 dalloc(ctx, &D[l], C[l] * N) != cudaSuccess)
                 return bail(fail(ctx, LS_ERR_OOM, "rhosvd_reduce: out of device memory (residual rows)"));
             B1m[l] = B1[l];
-            xs[l] = X64Mat{ctx->d_Z[l], m1[l], N, N, 1, nullptr};       // Q1
-            ys[l] = X64Mat{ctx->mode[l].d_cols, C[l], N, N, 1, w[l]};   // A_w (rows)
+            xs[l] = X64Mat{sx->d_Z[l], m1[l], N, N, 1, nullptr};        // Q1
+            ys[l] = X64Mat{sx->mode[l].d_cols, C[l], N, N, 1, w[l]};    // A_w (rows)
             ld[l] = C[l];
         }
         std::string err;
         int rc = x64_nt(3, xs, ys, B1m, ld, flag, st, &err);              // B1 = Q1 A_w^T (m1 x C)
         for (int l = 0; l < 3; ++l) {
             xs[l] = X64Mat{B1[l], C[l], m1[l], 1, C[l], nullptr};        // B1^T (C x m1)
-            ys[l] = X64Mat{ctx->d_Z[l], N, m1[l], 1, N, nullptr};        // Q1^T (N x m1)
+            ys[l] = X64Mat{sx->d_Z[l], N, m1[l], 1, N, nullptr};         // Q1^T (N x m1)
             ld[l] = N;
         }
         if (rc == LS_OK) rc = x64_nt(3, xs, ys, D, ld, flag, st, &err);  // D = B1^T Q1 (C x N)
         if (rc != LS_OK) return bail(fail(ctx, rc, "rhosvd_reduce: residual rows: %s", err.c_str()));
         for (int l = 0; l < 3; ++l) {
-            if (launch_resid_rows(ctx->mode[l].d_cols, w[l], D[l], C[l], N, e->mode[l].d_cols, st) != cudaSuccess)
+            if (launch_resid_rows(sx->mode[l].d_cols, w[l], D[l], C[l], N, e->mode[l].d_cols, st) != cudaSuccess)
                 return bail(fail(ctx, LS_ERR_CUDA, "rhosvd_reduce: residual rows launch failed"));
             dfree(ctx, B1[l]);
             dfree(ctx, D[l]);
@@ -1329,18 +1512,18 @@ int reduce_accurate(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_in
     // E carries the rounding dE of the two products that formed it, ||dE||_F^2 <= about
     // 2 u^2 T (m1 + 1) (each entry of B1^T Q1 to u sum_i |B1_ic| |Q1_in|, and sum_c w_c^2 = T).
     // An eigenvalue lambda of E E^T moves by about 2 sqrt(lambda) ||dE v|| (the matrix is
-    // graded), so a direction is real when lambda is well above ||dE||^2: candidates are
-    // taken 100 times above floor = 64 u^2 T (m1 + 1), i.e. singular values above
-    // 80 u sqrt(T (m1 + 1)) (about 1e-13 of sigma_1 on the 16^3 lattice).
+    // graded), so a direction is real when lambda is well above ||dE||^2; E's own Gram matrix
+    // adds u ||E||^2 (||E||^2 = the first pass's discarded energy). Candidates are taken 100
+    // times above floor = 8 u ||E||^2 + 64 u^2 T (m1 + 1): singular values down to about
+    // 1e-13 of sigma_1 on the 16^3 lattice.
     RedState p2, r2;
     p2.kind = 2;
     p2.floor_noise = 0.0;
     for (int l = 0; l < 3; ++l) {
-        (void)tail1;
-        const double fl = 64.0 * u * u * (double)T * (double)(m1[l] + 1);
+        const double fl = 8.0 * u * tail1[l] + 64.0 * u * u * (double)T * (double)(m1[l] + 1);
         p2.floor_noise = std::max(p2.floor_noise, fl);
         p2.cand_res[l] = 1e2 * fl;
-        p2.reorth[l] = ctx->d_Z[l];
+        p2.reorth[l] = sx->d_Z[l];
         p2.reorth_m[l] = m1[l];
     }
     {
@@ -1367,22 +1550,28 @@ int reduce_accurate(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_in
                 dalloc(ctx, &Mr[l], (int64_t)m[l] * m[l]) != cudaSuccess || dalloc(ctx, &sig2[l], m[l]) != cudaSuccess ||
                 dalloc(ctx, &isl[l], m[l]) != cudaSuccess || dalloc(ctx, &perm[l], m[l]) != cudaSuccess)
                 return bail(fail(ctx, LS_ERR_OOM, "rhosvd_reduce: out of device memory (one-sided Jacobi)"));
-            if (cudaMemcpyAsync(Q[l], ctx->d_Z[l], (size_t)m1[l] * N * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            if (cudaMemcpyAsync(Q[l], sx->d_Z[l], (size_t)m1[l] * N * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
                 (m2[l] > 0 && cudaMemcpyAsync(Q[l] + (int64_t)m1[l] * N, e->d_Z[l], (size_t)m2[l] * N * sizeof(double),
                                               cudaMemcpyDeviceToDevice, st) != cudaSuccess))
                 return bail(fail(ctx, LS_ERR_CUDA, "rhosvd_reduce: basis copy failed"));
             xs[l] = X64Mat{Q[l], m[l], N, N, 1, nullptr};
-            ys[l] = X64Mat{ctx->mode[l].d_cols, C[l], N, N, 1, w[l]};
+            ys[l] = X64Mat{sx->mode[l].d_cols, C[l], N, N, 1, w[l]};
             ld[l] = C[l];
         }
         std::string err;
         int rc = x64_nt(3, xs, ys, Bm, ld, flag, st, &err);               // B = Q A_w^T (m x C)
         if (rc != LS_OK) return bail(fail(ctx, rc, "rhosvd_reduce: B = Q A^T: %s", err.c_str()));
+        unsigned* cmax = nullptr;
+        if (dalloc(ctx, &cmax, 3 * 64) != cudaSuccess)
+            return bail(fail(ctx, LS_ERR_OOM, "rhosvd_reduce: out of device memory (one-sided Jacobi)"));
+        CUB(cudaMemsetAsync(cmax, 0, 3 * 64 * sizeof(unsigned), st));
         OsjJob jobs[3];
         for (int l = 0; l < 3; ++l)
-            jobs[l] = OsjJob{Bm[l], C[l], (int)C[l], Mr[l], m[l], sig2[l], ds + 1 + l, 8.0 * u * sqrt((double)C[l])};
+            jobs[l] = OsjJob{Bm[l], C[l], (int)C[l], Mr[l], m[l], sig2[l], ds + 1 + l, 8.0 * u * sqrt((double)C[l]),
+                             cmax + 64 * l};
         if (launch_osj(jobs, 3, 40, ctx->num_sms, st) != cudaSuccess)
             return bail(fail(ctx, LS_ERR_CUDA, "rhosvd_reduce: one-sided Jacobi launch failed"));
+        dfree(ctx, cmax);
     }
     // eps rule (or forced rank) on sigma^2, with the energy outside Q in the tail
     double hsel[3][3];
@@ -1395,7 +1584,7 @@ int reduce_accurate(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_in
         count_h2d(sizeof tail2);
         SortSelectJob jobs[3];
         for (int l = 0; l < 3; ++l) {
-            CUB(cudaMemsetAsync(ctx->d_sigma[l], 0, C[l] * sizeof(double), st));
+            CUB(cudaMemsetAsync(ctx->d_sigma[l], 0, ctx->mode[l].C * sizeof(double), st));
             const int fr = forced ? std::max(1, std::min(forced[l], m[l])) : 0;
             jobs[l] = SortSelectJob{sig2[l], m[l], fr, extra + l, perm[l], ctx->d_sigma[l], isl[l], sel + 3 * l};
             jobs[l].dstride = 1;
@@ -1420,13 +1609,13 @@ int reduce_accurate(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_in
         int64_t ld[3];
         for (int l = 0; l < 3; ++l) {
             ctx->r[l] = (int32_t)hsel[l][0];
-            dfree(ctx, ctx->d_Z[l]);
+            if (!side) dfree(ctx, ctx->d_Z[l]);
             ctx->d_Z[l] = nullptr;
             if (dalloc(ctx, &ctx->d_Z[l], (int64_t)ctx->r[l] * N) != cudaSuccess ||
-                dalloc(ctx, &ctx->d_P[l], (int64_t)ctx->r[l] * C[l]) != cudaSuccess ||
+                dalloc(ctx, &ctx->d_P[l], (int64_t)ctx->r[l] * ctx->mode[l].C) != cudaSuccess ||
                 dalloc(ctx, &Ms[l], (int64_t)ctx->r[l] * m[l]) != cudaSuccess)
                 return bail(fail(ctx, LS_ERR_OOM, "rhosvd_reduce: out of device memory (basis)"));
-            CUB(launch_gather_rows(Mr[l], m[l], perm[l], ctx->r[l], Ms[l], st));
+            CUB(launch_gather_rows(Mr[l], m[l], perm[l], ctx->r[l], nullptr, Ms[l], st));
             xs[l] = X64Mat{Ms[l], ctx->r[l], m[l], m[l], 1, nullptr};   // M_r (r x m)
             ys[l] = X64Mat{Q[l], N, m[l], 1, N, nullptr};                // Q^T (N x m)
             ld[l] = N;
@@ -1436,8 +1625,9 @@ int reduce_accurate(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_in
         if (rc != LS_OK) return bail(fail(ctx, rc, "rhosvd_reduce: basis: %s", err.c_str()));
         for (int l = 0; l < 3; ++l) {
             for (void* q : {(void*)Ms[l], (void*)Q[l], (void*)Bm[l], (void*)Mr[l], (void*)sig2[l], (void*)isl[l],
-                            (void*)perm[l], (void*)w[l]})
+                            (void*)perm[l]})
                 dfree(ctx, q);
+            if (!side) dfree(ctx, w[l]);
         }
         dfree(ctx, extra);
     }
@@ -1448,7 +1638,7 @@ int reduce_accurate(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_in
     rf.eps = eps;
     rf.forced = forced;
     rf.T = T;
-    rf.floor_noise = 64.0 * u * u * (double)T;   // the singular values' own rounding, squared, per column
+    rf.floor_noise = 64.0 * u * u * (side ? side_T : (double)T);   // the singular values' own rounding, squared, per column
     rf.d_sel = sel;
     rf.d_st = ds;   // [0] as the products' flag slot is read at [9]: use a fresh status block
     {
@@ -1466,7 +1656,76 @@ int reduce_accurate(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_in
         rf.rotations[l] = rot;
         rf.m[l].k = r1.m[l].k;
     }
-    return red_project_core(rf, info);
+    const int rc = red_project_core(rf, info);
+    if (rc == LS_OK && side && info) {
+        // Thm 4.3: |B_hat| in place of ||xi||, the side matrix's discarded tails
+        double ssum = 0.0;
+        for (int l = 0; l < 3; ++l) ssum += sqrt(std::max(hsel[l][0] > 0 ? rf.sel[l][1] : 0.0, 0.0) + (double)C[l] * rf.floor_noise);
+        info->xi_norm = Bhat;
+        info->bound_abs = Bhat * ssum;
+    }
+    return rc;
+}
+
+// The generalized RHOSVD of the Tucker-reference variant (Thm 4.3): the side matrix of mode l
+// holds, for every key (a block's assembled or a defect's windowed reference Tucker vectors),
+// its r_ref vectors scaled to unit Frobenius norm and weighted by sqrt(#terms using the key);
+// |B_hat|^2 = ||b||^2 sum_s charge_s^2 prod_l |F_{s,l}|_F^2. The truncation then runs the
+// non-squaring route on that side matrix, the projection and the core on the canonical
+// vectors of the projected reference (the Tucker sum written as a canonical sum).
+int reduce_tucker(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_info* info) {
+    cudaStream_t st = ctx->st;
+    const int64_t N = ctx->p.N;
+    const int r = ctx->r_ref;
+    const int64_t S = (int64_t)ctx->txi.size();
+    ls_ctx* sc = new ls_ctx();
+    sc->p = ctx->p;
+    sc->st = st;
+    sc->num_sms = ctx->num_sms;
+    sc->h = ctx->h;
+    auto bail = [&](int rc) {
+        if (!sc->err.empty() && ctx->err.empty()) ctx->err = sc->err;
+        lattice_sum_destroy(sc);
+        return rc;
+    };
+    std::vector<double> hn[3];
+    double* nrm[3];
+    double* mult[3];
+    for (int l = 0; l < 3; ++l) {
+        const ModeCols& tm = ctx->tmode[l];
+        const int nk = (int)(tm.C / r);
+        std::vector<double> mh(nk);
+        for (int k = 0; k < nk; ++k) mh[k] = (double)tm.count[(int64_t)k * r];
+        ModeCols& sm = sc->mode[l];
+        sm.C = sm.cap = tm.C;
+        sm.count.assign(tm.C, 1);
+        if (dalloc(sc, &sm.d_cols, tm.C * N) != cudaSuccess || dalloc(ctx, &nrm[l], nk) != cudaSuccess ||
+            dalloc(ctx, &mult[l], nk) != cudaSuccess)
+            return bail(fail(ctx, LS_ERR_OOM, "rhosvd_reduce: out of device memory (Tucker side matrix)"));
+        if (upload_h2d(mult[l], mh.data(), nk * sizeof(double), st) != cudaSuccess ||
+            launch_block_frob(tm.d_cols, r, N, nk, mult[l], nrm[l], sm.d_cols, st) != cudaSuccess)
+            return bail(fail(ctx, LS_ERR_CUDA, "rhosvd_reduce: Tucker side matrix launch failed"));
+        count_h2d(nk * sizeof(double));
+        hn[l].resize(nk);
+    }
+    for (int l = 0; l < 3; ++l)
+        if (cudaMemcpyAsync(hn[l].data(), nrm[l], hn[l].size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return bail(fail(ctx, LS_ERR_CUDA, "rhosvd_reduce: read-back failed"));
+    if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(ctx, LS_ERR_CUDA, "rhosvd_reduce: sync failed"));
+    count_d2h((int64_t)(hn[0].size() + hn[1].size() + hn[2].size()) * sizeof(double));
+    double bh2 = 0.0;
+    for (int64_t t = 0; t < S; ++t) {
+        double f = ctx->txi[t] * ctx->txi[t];
+        for (int l = 0; l < 3; ++l) f *= hn[l][ctx->tkey[3 * t + l]] * hn[l][ctx->tkey[3 * t + l]];
+        bh2 += f;
+    }
+    bh2 *= ctx->bnorm2;
+    for (int l = 0; l < 3; ++l) {
+        dfree(ctx, nrm[l]);
+        dfree(ctx, mult[l]);
+    }
+    const int rc = reduce_accurate(ctx, eps, forced, info, sc, (double)S, sqrt(bh2));
+    return bail(rc);
 }
 
 }  // namespace
@@ -1478,8 +1737,9 @@ int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ran
     if (ctx->reduced) return fail(ctx, LS_ERR_STATE, "rhosvd_reduce: already reduced");
     if (!forced_ranks && !(eps > 0.0)) return fail(ctx, LS_ERR_ARG, "rhosvd_reduce: eps must be > 0");
     ls_ctx* one[1] = {ctx};
-    const int rc = one_sided(ctx) ? reduce_accurate(ctx, eps, forced_ranks, info)
-                                  : reduce_many(one, 1, eps, forced_ranks, info);
+    const int rc = ctx->tucker     ? reduce_tucker(ctx, eps, forced_ranks, info)
+                   : one_sided(ctx) ? reduce_accurate(ctx, eps, forced_ranks, info)
+                                    : reduce_many(one, 1, eps, forced_ranks, info);
     // a large reduction leaves tens of GB of freed scratch in the stream-ordered pool
     // (the stream is synchronised here): when the device runs short, give it back beyond a
     // few GB, so that other allocators on the device can use it
@@ -1507,7 +1767,8 @@ int lattice_sum_batch_reduce(ls_ctx* const* ctxs, int32_t n, double eps, ls_tuck
     std::vector<int> gi;
     int rc = LS_OK;
     for (int i = 0; i < n && rc == LS_OK; ++i) {
-        if (one_sided(ctxs[i])) rc = reduce_accurate(ctxs[i], eps, nullptr, infos ? &infos[i] : nullptr);
+        if (ctxs[i]->tucker) rc = reduce_tucker(ctxs[i], eps, nullptr, infos ? &infos[i] : nullptr);
+        else if (one_sided(ctxs[i])) rc = reduce_accurate(ctxs[i], eps, nullptr, infos ? &infos[i] : nullptr);
         else { gram.push_back(ctxs[i]); gi.push_back(i); }
     }
     if (rc == LS_OK && !gram.empty()) {
@@ -1559,6 +1820,46 @@ int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, double abs_fl
     if (sweeps) *sweeps = h.sweeps;
     if (h.flag == FLAG_TIMEOUT) return fail(nullptr, LS_ERR_TIMEOUT, "jacobi_eig: a bounded wait timed out");
     if (h.flag == FLAG_NOCONVERGE) return fail(nullptr, LS_ERR_NOCONVERGE, "jacobi_eig: no convergence in 60 sweeps");
+    return LS_OK;
+}
+
+int lattice_sum_svd_rows(const double* B, int32_t m, int32_t C, double tol, double* sig2, double* M, int32_t* sweeps,
+                         int64_t* rotations, void* stream) {
+    if (!B || !sig2 || !M || m < 1 || C < 1 || !(tol > 0.0))
+        return fail(nullptr, LS_ERR_ARG, "svd_rows: bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = 0, nsm = 1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    double* Bw = nullptr;
+    DevStatus* ds = nullptr;
+    unsigned* cmax = nullptr;
+    if (e == cudaSuccess) e = cudaMallocAsync(&Bw, sizeof(double) * (size_t)m * C, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&ds, sizeof(DevStatus), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&cmax, 64 * sizeof(unsigned), st);
+    if (e != cudaSuccess) {
+        if (Bw) cudaFreeAsync(Bw, st);
+        if (ds) cudaFreeAsync(ds, st);
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? LS_ERR_OOM : LS_ERR_CUDA, "svd_rows: %s",
+                    cudaGetErrorString(e));
+    }
+    DevStatus h{};
+    e = cudaMemcpyAsync(Bw, B, sizeof(double) * (size_t)m * C, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ds, 0, sizeof(DevStatus), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cmax, 0, 64 * sizeof(unsigned), st);
+    const OsjJob J{Bw, C, C, M, m, sig2, ds, tol, cmax};
+    if (e == cudaSuccess) e = launch_osj(&J, 1, 60, nsm, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ds, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(Bw, st);
+    cudaFreeAsync(ds, st);
+    cudaFreeAsync(cmax, st);
+    if (e != cudaSuccess) return fail(nullptr, LS_ERR_CUDA, "svd_rows: %s", cudaGetErrorString(e));
+    if (sweeps) *sweeps = h.sweeps;
+    if (rotations)
+        for (int k = 0; k < 64; ++k) rotations[k] = k < h.sweeps ? (int64_t)h.sweep_active[k] : 0;
+    if (h.flag == FLAG_TIMEOUT) return fail(nullptr, LS_ERR_TIMEOUT, "svd_rows: a bounded wait timed out");
+    if (h.flag == FLAG_NOCONVERGE) return fail(nullptr, LS_ERR_NOCONVERGE, "svd_rows: no convergence in 60 sweeps");
     return LS_OK;
 }
 
@@ -1678,6 +1979,7 @@ int lattice_sum_read(ls_ctx* ctx, int32_t what, int32_t mode, void* dst, int64_t
         case LS_READ_BASIS: src = ctx->d_Z[mode]; need = (int64_t)ctx->r[mode] * N * 8; break;
         case LS_READ_PROJ: src = ctx->d_P[mode]; need = (int64_t)ctx->r[mode] * mc.C * 8; break;
         case LS_READ_CORE: src = ctx->d_B; need = (int64_t)ctx->r[0] * ctx->r[1] * ctx->r[2] * 8; break;
+        case LS_READ_TUCKER_REF: src = ctx->d_t; need = (int64_t)ctx->r_ref * 2 * N * 8; break;
         default: return fail(ctx, LS_ERR_ARG, "read: unknown item %d", what);
     }
     if (needed_bytes) *needed_bytes = need;

@@ -201,11 +201,12 @@ cudaError_t launch_eval_f64(const double* const Z[3], const int32_t* r, const do
 // tol ||b_p|| ||b_q||); M (m x m, row-major) receives the accumulated rotation (rows: the
 // left singular vectors of the original B as combinations of its rows' index), sig2 (m)
 // the squared row norms (the squared singular values, unsorted). st: zeroed status;
-// st->sweeps receives the sweeps taken (the last one rotates nothing), sweep_active[] the
-// rotations of each sweep; FLAG_NOCONVERGE after max_sweeps (<= 60). Up to three
-// matrices per cooperative launch.
+// st->sweeps receives the sweeps taken, sweep_active[] the rotations of each sweep; cmax
+// (64 zeroed words) the largest |cos| of each sweep as float bits. The iteration stops
+// after a sweep with no rotation or with every |cos| below 1e-9; FLAG_NOCONVERGE after
+// max_sweeps (<= 60). Up to three matrices per cooperative launch.
 struct OsjJob {
-    double* B; int64_t ldb; int C; double* M; int m; double* sig2; DevStatus* st; double tol;
+    double* B; int64_t ldb; int C; double* M; int m; double* sig2; DevStatus* st; double tol; unsigned* cmax;
 };
 cudaError_t launch_osj(const OsjJob* jobs, int njobs, int max_sweeps, int num_sms, cudaStream_t st);
 // E[c][n] = w[c] A[c][n] - D[c][n] (w may be NULL: 1), rows x N.
@@ -213,7 +214,14 @@ cudaError_t launch_resid_rows(const double* A, const double* w, const double* D,
                               cudaStream_t st);
 // Y[e] -= D[e], e < n.
 cudaError_t launch_sub(double* Y, const double* D, int64_t n, cudaStream_t st);
-// out[j][:] = M[perm[j]][:] (rows of length m), j < r.
-cudaError_t launch_gather_rows(const double* M, int m, const int32_t* perm, int r, double* out, cudaStream_t st);
+// out[j][:] = M[perm[j]][:] times scale[j] (scale may be NULL: 1), rows of length len, j < r.
+cudaError_t launch_gather_rows(const double* M, int64_t len, const int32_t* perm, int r, const double* scale,
+                               double* out, cudaStream_t st);
+// Blocks of w rows (length N) of A: nrm[j] = Frobenius norm of block j, out block j =
+// sqrt(mult[j]) / nrm[j] times it (zero where nrm[j] = 0).
+cudaError_t launch_block_frob(const double* A, int w, int64_t N, int nblocks, const double* mult, double* nrm,
+                              double* out, cudaStream_t st);
+// *out = sum_e x[e]^3, e < n (device).
+cudaError_t launch_sum_cubes(const double* x, int64_t n, double* out, cudaStream_t st);
 
 }  // namespace ls

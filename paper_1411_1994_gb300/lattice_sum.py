@@ -21,24 +21,26 @@ LS_FP64, LS_MIXED = 0, 1
 LS_FLAG_GALERKIN = 1   # reference vectors as cell averages (Eq. galten) instead of collocation
 LS_FLAG_SVD_GRAM = 2       # singular values from the FP64 Gram matrix (default of LS_MIXED)
 LS_FLAG_SVD_ONESIDED = 4   # singular values without squaring (default of LS_FP64)
+LS_FLAG_TUCKER_REF = 8     # Tucker-reference variant (Thm 3.1(B), Thm 4.3), threshold ref_eps
 LS_KERNEL_YUKAWA, LS_KERNEL_SLATER, LS_KERNEL_DIPOLE = 0, 1, 2   # exp(-kappa r)/r (1/r at kappa = 0), exp(-kappa r), 1/r^3
 LS_DEFECT_SITES, LS_DEFECT_POINT = 0, 1
 LS_OUT_F64, LS_OUT_F32 = 0, 1
 (LS_READ_GENVEC, LS_READ_COLUMNS, LS_READ_NORMS, LS_READ_TERMS, LS_READ_XI, LS_READ_SIGMA,
- LS_READ_BASIS, LS_READ_PROJ, LS_READ_CORE) = range(9)
+ LS_READ_BASIS, LS_READ_PROJ, LS_READ_CORE, LS_READ_TUCKER_REF) = range(10)
 
 EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_fit_t_scale_kernel", "lattice_sum_create", "lattice_sum_add_defects",
             "lattice_sum_rhosvd_reduce", "lattice_sum_eval_slab", "lattice_sum_get_factors",
             "lattice_sum_read", "lattice_sum_profile", "lattice_sum_profile_report",
             "lattice_sum_eval_slab_noalloc", "lattice_sum_batch_reduce", "lattice_sum_gemm_nt",
-            "lattice_sum_gemm_nt_mixed", "lattice_sum_jacobi_eig", "lattice_sum_tune_eval", "lattice_sum_destroy",
+            "lattice_sum_gemm_nt_mixed", "lattice_sum_jacobi_eig", "lattice_sum_svd_rows", "lattice_sum_tune_eval",
+            "lattice_sum_destroy",
             "lattice_sum_last_error")
 
 
 class ls_params(C.Structure):
     _fields_ = [("N", C.c_int64), ("box_lo", C.c_double), ("box_hi", C.c_double), ("R", C.c_int32),
                 ("sinc_step", C.c_double), ("t_scale", C.c_double), ("precision", C.c_int32),
-                ("flags", C.c_int32), ("kappa", C.c_double), ("kernel", C.c_int32)]
+                ("flags", C.c_int32), ("kappa", C.c_double), ("kernel", C.c_int32), ("ref_eps", C.c_double)]
 
 
 class ls_block(C.Structure):
@@ -97,6 +99,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                               C.c_int32, C.c_int32, C.c_void_p]
     lib.lattice_sum_jacobi_eig.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.lattice_sum_svd_rows.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p]
     lib.lattice_sum_destroy.argtypes = [C.c_void_p]
     lib.lattice_sum_destroy.restype = None
     lib.lattice_sum_last_error.argtypes = [C.c_void_p]
@@ -218,6 +222,23 @@ def jacobi_eig(H, tol: float = 1e-7, abs_floor: float = 0.0, form: int = 2):
     return D, V, sw.value
 
 
+def svd_rows(B, tol: float = None):
+    """One-sided Jacobi on the rows of a float64 CUDA tensor B (m x C) (lattice_sum_svd_rows):
+    returns (squared row norms after convergence, rotation M, sweeps, rotations per sweep)."""
+    import torch
+    B = B.contiguous()
+    m, Cc = B.shape
+    if tol is None:
+        tol = 8.0 * 2.0 ** -53 * Cc ** 0.5
+    sig2 = torch.empty(m, dtype=torch.float64, device=B.device)
+    M = torch.empty((m, m), dtype=torch.float64, device=B.device)
+    sw = C.c_int32()
+    rot = (C.c_int64 * 64)()
+    _check(lib().lattice_sum_svd_rows(C.c_void_p(B.data_ptr()), C.c_int32(m), C.c_int32(Cc), C.c_double(tol),
+                                      C.c_void_p(sig2.data_ptr()), C.c_void_p(M.data_ptr()), C.byref(sw), rot, None))
+    return sig2, M, sw.value, [int(rot[k]) for k in range(sw.value)]
+
+
 def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float, kappa: float = 0.0,
                 kernel: int = LS_KERNEL_YUKAWA):
     s, e = C.c_double(), C.c_double()
@@ -259,10 +280,11 @@ class LatticeSum:
     eval_slab, each a direct call of the C ABI."""
 
     def __init__(self, N, box_lo, box_hi, R, sinc_step, t_scale, blocks, precision=LS_FP64, stream=None,
-                 kappa=0.0, kernel=LS_KERNEL_YUKAWA, galerkin=False, flags=0):
+                 kappa=0.0, kernel=LS_KERNEL_YUKAWA, galerkin=False, flags=0, ref_eps=0.0):
         self._lib = lib()
         p = ls_params(int(N), float(box_lo), float(box_hi), int(R), float(sinc_step), float(t_scale),
-                      int(precision), (LS_FLAG_GALERKIN if galerkin else 0) | int(flags), float(kappa), int(kernel))
+                      int(precision), (LS_FLAG_GALERKIN if galerkin else 0) | int(flags), float(kappa), int(kernel),
+                      float(ref_eps))
         self._blocks = make_blocks(blocks)
         ctx = C.c_void_p()
         rc = self._lib.lattice_sum_create(C.byref(ctx), C.byref(p), self._blocks, len(blocks),
@@ -274,10 +296,10 @@ class LatticeSum:
         self.info = None
 
     @classmethod
-    def from_workload(cls, wl, t_scale, precision=LS_FP64, stream=None, flags=0):
+    def from_workload(cls, wl, t_scale, precision=LS_FP64, stream=None, flags=0, ref_eps=0.0):
         return cls(wl.N, wl.box_lo, wl.box_hi, wl.R, wl.sinc_step, t_scale, wl.blocks, precision, stream,
                    getattr(wl, "kappa", 0.0), getattr(wl, "kernel", LS_KERNEL_YUKAWA), getattr(wl, "galerkin", False),
-                   flags)
+                   flags, ref_eps)
 
     def add_defects(self, defects):
         """lattice_sum_add_defects for a sequence of Defect descriptions, or for an ls_defect

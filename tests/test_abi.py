@@ -42,7 +42,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_binding_structs_match_header_sizes(lib):
     import ctypes as C
-    assert C.sizeof(L.ls_params) == 8 + 8 + 8 + 8 + 8 + 8 + 4 + 4 + 8 + 8
+    assert C.sizeof(L.ls_params) == 8 + 8 + 8 + 8 + 8 + 8 + 4 + 4 + 8 + 8 + 8
     assert C.sizeof(L.ls_block) == 3 * 8 * 3 + 8
     assert C.sizeof(L.ls_defect) == 4 + 4 + 3 * 8 + 3 * 8 + 3 * 8 + 8
 
@@ -107,13 +107,17 @@ def test_create_validates_arguments_on_host(lib, bad):
 
 
 def test_create_rejects_unknown_flags(lib):
-    """LS_FLAG_GALERKIN, LS_FLAG_SVD_GRAM and LS_FLAG_SVD_ONESIDED are the known
-    flags, and the two singular-value routes exclude each other; anything else
-    is refused on the host before the device is touched."""
+    """LS_FLAG_GALERKIN, LS_FLAG_SVD_GRAM, LS_FLAG_SVD_ONESIDED and
+    LS_FLAG_TUCKER_REF are the known flags; the two singular-value routes
+    exclude each other, the Tucker-reference variant needs 0 < ref_eps < 1 and
+    the non-squaring route; anything else is refused on the host before the
+    device is touched."""
     import ctypes as C
     blocks = L.make_blocks([W.centred_block((2, 2, 2))])
-    for flags in (L.LS_FLAG_SVD_GRAM | L.LS_FLAG_SVD_ONESIDED, 8, 0x100, -1):
-        p = L.ls_params(64, -6.0, 6.0, 8, 0.25, 10.0, L.LS_FP64, flags, 0.0, L.LS_KERNEL_YUKAWA)
+    for flags, ref_eps in ((L.LS_FLAG_SVD_GRAM | L.LS_FLAG_SVD_ONESIDED, 0.0), (16, 0.0), (0x100, 0.0), (-1, 0.0),
+                           (L.LS_FLAG_TUCKER_REF, 0.0), (L.LS_FLAG_TUCKER_REF, 1.5),
+                           (L.LS_FLAG_TUCKER_REF | L.LS_FLAG_SVD_GRAM, 1e-6)):
+        p = L.ls_params(64, -6.0, 6.0, 8, 0.25, 10.0, L.LS_FP64, flags, 0.0, L.LS_KERNEL_YUKAWA, ref_eps)
         ctx = C.c_void_p()
         rc = L.lib().lattice_sum_create(C.byref(ctx), C.byref(p), blocks, 1, None)
         assert rc == L.LS_ERR_ARG, flags
