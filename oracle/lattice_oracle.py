@@ -728,6 +728,35 @@ def full_from_canonical(cols, tcol, xi) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
+# Galerkin matrix of the Tucker potential in a rank-one basis, Eq. (nuc_pot)
+# ---------------------------------------------------------------------------
+
+def galerkin_matrix(Z, B, basis) -> np.ndarray:
+    """v_km = <G_k (.) G_m, T> (Eq. nuc_pot) for rank-one basis functions
+    G_k = g_k^1 (x) g_k^2 (x) g_k^3 (``basis[l]``: (nb, N), row k = g_k^l) and
+    the Tucker tensor T = B x1 Z1 x2 Z2 x3 Z3: the Hadamard product of two
+    rank-one tensors is rank one, (g_k^l (.) g_m^l) per mode, so the scalar
+    product is the core contracted with the three 1D projections
+    Z_l^T (g_k^l (.) g_m^l). The grid inner product, without the cell volume
+    h^3 (times h^3 it is the midpoint rule for the integral of v g_k g_m).
+    Returns V (nb, nb)."""
+    M = [np.einsum("ki,mi,ia->kma", basis[l], basis[l], Z[l], optimize=True) for l in range(3)]
+    return np.einsum("abc,kma,kmb,kmc->km", B, M[0], M[1], M[2], optimize=True)
+
+
+def galerkin_matrix_full(T, basis) -> np.ndarray:
+    """The same matrix from the definition on the full N^3 tensor: the sum over
+    all grid points of T times g_k g_m (small N only)."""
+    nb = basis[0].shape[0]
+    V = np.zeros((nb, nb))
+    for k in range(nb):
+        for m in range(nb):
+            w = [basis[l][k] * basis[l][m] for l in range(3)]
+            V[k, m] = np.einsum("ijl,i,j,l->", T, w[0], w[1], w[2])
+    return V
+
+
+# ---------------------------------------------------------------------------
 # whole pipeline (a) + (b) + (c), as timed for the CPU baseline
 # ---------------------------------------------------------------------------
 

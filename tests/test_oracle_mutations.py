@@ -39,6 +39,12 @@ MUTATIONS = {
                                  "terms.append(([side(ms[a]) for a in range(3)], d.charge * b,"),
     "tucker_core_mode_swap": ("P = [out[\"Z\"][a].T @ F[a] for a in range(3)]",
                               "P = [out[\"Z\"][a].T @ F[(a + 1) % 3] for a in range(3)]"),
+    "galerkin_no_hadamard": ('M = [np.einsum("ki,mi,ia->kma", basis[l], basis[l], Z[l], optimize=True) for l in range(3)]',
+                             'M = [np.einsum("ki,mi,ia->kma", basis[l], np.ones_like(basis[l]), Z[l], optimize=True) '
+                             'for l in range(3)]'),
+    "galerkin_mode_swap": ('M = [np.einsum("ki,mi,ia->kma", basis[l], basis[l], Z[l], optimize=True) for l in range(3)]',
+                           'M = [np.einsum("ki,mi,ia->kma", basis[l], basis[l], Z[(l + 1) % 3], optimize=True) '
+                           'for l in range(3)]'),
     "tucker_reference_unprojected": ("h = Z.T @ g.T                               # (r, R): Z^T g_q",
                                      "h = Z.T @ (g / np.sqrt((g * g).sum(1))[:, None]).T"),
 }

@@ -808,3 +808,72 @@ def test_tucker_core_as_canonical_sum(tucker_small):
     bh2 = sum(xi[s_idx * R] ** 2 * b2 * np.prod([np.linalg.norm(F[a]) ** 2 for a in range(3)])
               for s_idx, (F, core, keys) in enumerate(terms))
     assert abs(math.sqrt(bh2) - res["Bhat"]) <= 1e-12 * res["Bhat"]
+
+
+# --- Galerkin matrix of the Tucker potential, Eq. (nuc_pot) ----------------------
+
+def _gaussian_basis(x, centres, alphas):
+    return [np.exp(-alphas[:, None] * (x[None, :] - centres[:, l:l + 1]) ** 2) for l in range(3)]
+
+
+def test_galerkin_matrix_equals_full_tensor_definition(defected_small):
+    """The 1D Hadamard/scalar-product form equals the sum over the full grid of
+    T g_k g_m, for a non-symmetric Tucker tensor (a defected lattice)."""
+    wl, cols, tcol, xi, full = defected_small
+    res = O.rhosvd(cols, tcol, xi, 1e-6)
+    T = O.full_from_tucker(res["Z"], res["B"])
+    x = O.cell_centres(wl.N, wl.box_lo, wl.box_hi)
+    rng = np.random.default_rng(11)
+    basis = _gaussian_basis(x, rng.uniform(-2.0, 2.0, (5, 3)), rng.uniform(0.3, 2.0, 5))
+    V = O.galerkin_matrix(res["Z"], res["B"], basis)
+    Vf = O.galerkin_matrix_full(T, basis)
+    assert np.max(np.abs(V - Vf)) <= 1e-12 * np.max(np.abs(Vf))
+    assert np.max(np.abs(V - V.T)) <= 1e-13 * np.max(np.abs(V))
+
+
+def test_galerkin_matrix_of_constant_potential_is_overlap_product():
+    """T = 1 everywhere (Z_l = ones / sqrt(N), core N^(3/2)): v_km is the product over
+    the modes of the 1D overlaps sum_i g_k^l(i) g_m^l(i)."""
+    N = 40
+    x = np.linspace(-3.0, 3.0, N)
+    rng = np.random.default_rng(5)
+    basis = _gaussian_basis(x, rng.uniform(-1.0, 1.0, (4, 3)), rng.uniform(0.5, 3.0, 4))
+    Z = [np.ones((N, 1)) / math.sqrt(N) for _ in range(3)]
+    B = np.array([[[N ** 1.5]]])
+    V = O.galerkin_matrix(Z, B, basis)
+    S = [basis[l] @ basis[l].T for l in range(3)]
+    assert np.max(np.abs(V - S[0] * S[1] * S[2])) <= 1e-12 * np.max(np.abs(V))
+
+
+def test_galerkin_matrix_converges_to_gaussian_nuclear_attraction():
+    """A single unit charge and s-type Gaussians exp(-alpha |x - A|^2): h^3 v_km tends to
+    the closed-form nuclear attraction integral (2 pi / p) exp(-mu |A - B|^2)
+    F0(p |P - C|^2), F0(t) = (1/2) sqrt(pi/t) erf(sqrt t) (p = alpha + beta,
+    mu = alpha beta / p, P = (alpha A + beta B)/p), at second order in h: the midpoint
+    rule on the collocated potential."""
+    from scipy.special import erf
+    errs = []
+    for N in (64, 128):
+        wl = W.small_case(L=(1, 1, 1), N=N, R=24, eps=1e-10, sinc_step=0.25)
+        s, _ = O.fit_t_scale(wl.R, wl.sinc_step, 0.02, O.default_r_max(wl))
+        s, t, w, g, cols, tcol, xi = _terms(wl, s)
+        res = O.rhosvd(cols, tcol, xi, 1e-10)
+        x = O.cell_centres(wl.N, wl.box_lo, wl.box_hi)
+        h = x[1] - x[0]
+        a = O.charged_centres(wl.N, wl.box_lo, wl.box_hi, wl.blocks, wl.defects)[0][0]
+        rng = np.random.default_rng(0)
+        alph = rng.uniform(0.8, 2.0, 4)
+        cen = a + rng.uniform(-1.0, 1.0, (4, 3))
+        V = O.galerkin_matrix(res["Z"], res["B"], _gaussian_basis(x, cen, alph)) * h ** 3
+        A = np.zeros((4, 4))
+        for k in range(4):
+            for m in range(4):
+                p = alph[k] + alph[m]
+                mu = alph[k] * alph[m] / p
+                P = (alph[k] * cen[k] + alph[m] * cen[m]) / p
+                tt = p * float(np.sum((P - a) ** 2))
+                F0 = 1.0 if tt < 1e-14 else 0.5 * math.sqrt(math.pi / tt) * erf(math.sqrt(tt))
+                A[k, m] = 2.0 * math.pi / p * math.exp(-mu * float(np.sum((cen[k] - cen[m]) ** 2))) * F0
+        errs.append(float(np.max(np.abs(V - A) / np.abs(A))))
+    assert errs[1] < 2e-3, errs
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
