@@ -332,12 +332,14 @@ int lattice_sum_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, 
  *   (k up to a device-dependent limit: 208 on GB300). form 2: one cooperative
  *   grid with the matrix in global memory (any k). On the same input both
  *   forms give the same D and V.
+ * - max_sweeps: the sweep limit (1..60; 0 = 60), after which the call
+ *   returns LS_ERR_NOCONVERGE.
  * - Synchronises `stream` (a cudaStream_t or NULL).
- * - Errors: LS_ERR_ARG, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_NOCONVERGE (60
- *   sweeps), LS_ERR_TIMEOUT.
+ * - Errors: LS_ERR_ARG, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_NOCONVERGE,
+ *   LS_ERR_TIMEOUT.
  */
-int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, double abs_floor, int32_t form, double* D,
-                           double* V, int32_t* sweeps, void* stream);
+int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, double abs_floor, int32_t form,
+                           int32_t max_sweeps, double* D, double* V, int32_t* sweeps, void* stream);
 
 /*
  * lattice_sum_svd_rows -- the one-sided (Hestenes) Jacobi of the non-squaring
@@ -353,12 +355,34 @@ int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, double abs_fl
  *   accumulated rotation, so that M B has those orthogonal rows (the rows of M
  *   are the left singular vectors of B); *sweeps (may be NULL) the sweeps
  *   taken; rotations (host, 64 entries, may be NULL) the rotations per sweep.
+ * - max_sweeps: the sweep limit (1..60; 0 = 60), after which the call
+ *   returns LS_ERR_NOCONVERGE.
  * - Synchronises `stream` (a cudaStream_t or NULL).
- * - Errors: LS_ERR_ARG, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_NOCONVERGE (60
- *   sweeps), LS_ERR_TIMEOUT.
+ * - Errors: LS_ERR_ARG, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_NOCONVERGE,
+ *   LS_ERR_TIMEOUT.
  */
-int lattice_sum_svd_rows(const double* B, int32_t m, int32_t C, double tol, double* sig2, double* M,
-                         int32_t* sweeps, int64_t* rotations, void* stream);
+int lattice_sum_svd_rows(const double* B, int32_t m, int32_t C, double tol, int32_t max_sweeps, double* sig2,
+                         double* M, int32_t* sweeps, int64_t* rotations, void* stream);
+
+/*
+ * Failure-path hooks (no counterpart in the paper): they let tests drive the
+ * library's error paths without faulting the GPU.
+ *
+ * lattice_sum_test_fail_alloc -- the n-th device allocation of a context
+ * from now (n = 0: the next one) reports cudaErrorMemoryAllocation, so that
+ * the call making it returns LS_ERR_OOM; n < 0 switches the injection off.
+ * Process-wide, one shot. A context whose call failed can still be destroyed.
+ *
+ * lattice_sum_test_bounded_wait -- runs the bounded group barrier that the
+ * cooperative kernels use between their rounds, in a two-CTA grid with
+ * spin_limit polls (each with a short sleep): with absent = 0 both CTAs
+ * arrive and the call returns LS_OK; with absent = 1 the second CTA leaves
+ * without arriving, the first one's wait runs out and the call returns
+ * LS_ERR_TIMEOUT, the kernel having ended normally (the context stays
+ * usable). Synchronises `stream`. Errors: LS_ERR_ARG, LS_ERR_OOM, LS_ERR_CUDA.
+ */
+int lattice_sum_test_fail_alloc(int64_t n);
+int lattice_sum_test_bounded_wait(int32_t absent, int64_t spin_limit, void* stream);
 
 /*
  * lattice_sum_gemm_nt_mixed -- D = A B^T for device FP64 matrices (A: M x K,
@@ -419,6 +443,22 @@ int lattice_sum_eval_slab(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, vo
  */
 int lattice_sum_tune_eval(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev, int32_t out_dtype,
                           char* report, int64_t cap);
+
+/*
+ * lattice_sum_galerkin -- the Galerkin matrix of the reduced potential in a
+ * rank-one basis, Eq. (nuc_pot): for basis functions G_k = g_k^1 (x) g_k^2
+ * (x) g_k^3 sampled at the grid's cell centres,
+ *   V[k][m] = <G_k (.) G_m, T> = sum_abc B_abc M1_a M2_b M3_c,
+ *   M_l = Z_l^T (g_k^l (.) g_m^l)     (1D Hadamard and scalar products),
+ * the grid inner product (times h^3 it is the midpoint rule for the integral
+ * of v g_k g_m). basis[l] (host array of 3 device pointers) holds double
+ * [nb][N], row k = g_k^l; V (device, nb x nb, row-major) receives the
+ * symmetric matrix. The products run in the FP64-grade tensor-core arithmetic
+ * of lattice_sum_gemm_nt. Synchronises the stream.
+ * Errors: LS_ERR_ARG, LS_ERR_STATE (before the reduction), LS_ERR_OOM,
+ * LS_ERR_CUDA, LS_ERR_TIMEOUT.
+ */
+int lattice_sum_galerkin(ls_ctx* ctx, const double* const* basis, int32_t nb, double* V);
 
 /*
  * lattice_sum_get_factors -- device pointers of the Tucker factors (valid

@@ -137,10 +137,16 @@ int fail(ls_ctx* ctx, int code, const char* fmt, ...) {
                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                       \
     } while (0)
 
+// failure injection for tests: the n-th context allocation from now fails (-1: none)
+std::atomic<long long> g_fail_after{-1};
+
 template <class T>
 cudaError_t dalloc(ls_ctx* ctx, T** p, int64_t count) {
     *p = nullptr;
     if (count <= 0) count = 1;
+    long long n = g_fail_after.load();
+    while (n >= 0 && !g_fail_after.compare_exchange_weak(n, n - 1)) {}
+    if (n == 0) return cudaErrorMemoryAllocation;
     void* q = nullptr;
     cudaError_t e = cudaMallocAsync(&q, (size_t)count * sizeof(T), ctx->st);
     if (e != cudaSuccess) return e;
@@ -508,7 +514,8 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
         Scope sc_gen("genvec", ctx->st);
         if (e2 == cudaSuccess) e2 = launch_genvec(ctx->d_g, R, N, ctx->h, p.sinc_step, p.t_scale, p.kernel, p.kappa,
                                                       (p.flags & LS_FLAG_GALERKIN) != 0, ctx->st);
-        if (e2 != cudaSuccess) rc = fail(ctx, LS_ERR_CUDA, "create: %s", cudaGetErrorString(e2));
+        if (e2 != cudaSuccess)
+            rc = fail(ctx, e2 == cudaErrorMemoryAllocation ? LS_ERR_OOM : LS_ERR_CUDA, "create: %s", cudaGetErrorString(e2));
     }
     ctx->tucker = (p.flags & LS_FLAG_TUCKER_REF) != 0;
     if (rc == LS_OK && ctx->tucker) rc = make_reference_tucker(ctx);
@@ -1796,10 +1803,12 @@ int lattice_sum_gemm_nt(const double* A, const double* B, int64_t M, int64_t N, 
     return LS_OK;
 }
 
-int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, double abs_floor, int32_t form, double* D,
-                           double* V, int32_t* sweeps, void* stream) {
-    if (!H || !D || !V || k < 1 || !(tol > 0.0) || !(abs_floor >= 0.0) || (form != 1 && form != 2))
+int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, double abs_floor, int32_t form,
+                           int32_t max_sweeps, double* D, double* V, int32_t* sweeps, void* stream) {
+    if (!H || !D || !V || k < 1 || !(tol > 0.0) || !(abs_floor >= 0.0) || (form != 1 && form != 2) ||
+        max_sweeps < 0 || max_sweeps > 60)
         return fail(nullptr, LS_ERR_ARG, "jacobi_eig: bad arguments");
+    const int ms = max_sweeps ? max_sweeps : 60;
     if (form == 1 && k > jacobi_blk_max_k())
         return fail(nullptr, LS_ERR_ARG, "jacobi_eig: k = %d exceeds the cluster form (%d)", k, jacobi_blk_max_k());
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1812,21 +1821,22 @@ int lattice_sum_jacobi_eig(const double* H, int32_t k, double tol, double abs_fl
     int dev = 0, nsm = 1;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = form == 1 ? launch_jacobi_blk(&J, 1, 60, st) : launch_jacobi_gblk(&J, 1, 60, nsm, st);
+    if (e == cudaSuccess) e = form == 1 ? launch_jacobi_blk(&J, 1, ms, st) : launch_jacobi_gblk(&J, 1, ms, nsm, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ds, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFreeAsync(ds, st);
     if (e != cudaSuccess) return fail(nullptr, LS_ERR_CUDA, "jacobi_eig: %s", cudaGetErrorString(e));
     if (sweeps) *sweeps = h.sweeps;
     if (h.flag == FLAG_TIMEOUT) return fail(nullptr, LS_ERR_TIMEOUT, "jacobi_eig: a bounded wait timed out");
-    if (h.flag == FLAG_NOCONVERGE) return fail(nullptr, LS_ERR_NOCONVERGE, "jacobi_eig: no convergence in 60 sweeps");
+    if (h.flag == FLAG_NOCONVERGE) return fail(nullptr, LS_ERR_NOCONVERGE, "jacobi_eig: no convergence in %d sweeps", ms);
     return LS_OK;
 }
 
-int lattice_sum_svd_rows(const double* B, int32_t m, int32_t C, double tol, double* sig2, double* M, int32_t* sweeps,
-                         int64_t* rotations, void* stream) {
-    if (!B || !sig2 || !M || m < 1 || C < 1 || !(tol > 0.0))
+int lattice_sum_svd_rows(const double* B, int32_t m, int32_t C, double tol, int32_t max_sweeps, double* sig2,
+                         double* M, int32_t* sweeps, int64_t* rotations, void* stream) {
+    if (!B || !sig2 || !M || m < 1 || C < 1 || !(tol > 0.0) || max_sweeps < 0 || max_sweeps > 60)
         return fail(nullptr, LS_ERR_ARG, "svd_rows: bad arguments");
+    const int ms = max_sweeps ? max_sweeps : 60;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int dev = 0, nsm = 1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1848,7 +1858,7 @@ int lattice_sum_svd_rows(const double* B, int32_t m, int32_t C, double tol, doub
     if (e == cudaSuccess) e = cudaMemsetAsync(ds, 0, sizeof(DevStatus), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(cmax, 0, 64 * sizeof(unsigned), st);
     const OsjJob J{Bw, C, C, M, m, sig2, ds, tol, cmax};
-    if (e == cudaSuccess) e = launch_osj(&J, 1, 60, nsm, st);
+    if (e == cudaSuccess) e = launch_osj(&J, 1, ms, nsm, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ds, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFreeAsync(Bw, st);
@@ -1859,7 +1869,29 @@ int lattice_sum_svd_rows(const double* B, int32_t m, int32_t C, double tol, doub
     if (rotations)
         for (int k = 0; k < 64; ++k) rotations[k] = k < h.sweeps ? (int64_t)h.sweep_active[k] : 0;
     if (h.flag == FLAG_TIMEOUT) return fail(nullptr, LS_ERR_TIMEOUT, "svd_rows: a bounded wait timed out");
-    if (h.flag == FLAG_NOCONVERGE) return fail(nullptr, LS_ERR_NOCONVERGE, "svd_rows: no convergence in 60 sweeps");
+    if (h.flag == FLAG_NOCONVERGE) return fail(nullptr, LS_ERR_NOCONVERGE, "svd_rows: no convergence in %d sweeps", ms);
+    return LS_OK;
+}
+
+int lattice_sum_test_fail_alloc(int64_t n) {
+    g_fail_after.store(n < 0 ? -1 : (long long)n);
+    return LS_OK;
+}
+
+int lattice_sum_test_bounded_wait(int32_t absent, int64_t spin_limit, void* stream) {
+    if ((absent != 0 && absent != 1) || spin_limit < 1) return fail(nullptr, LS_ERR_ARG, "test_bounded_wait: bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevStatus* ds = nullptr;
+    cudaError_t e = cudaMallocAsync(&ds, sizeof(DevStatus), st);
+    if (e != cudaSuccess) return fail(nullptr, LS_ERR_OOM, "test_bounded_wait: %s", cudaGetErrorString(e));
+    DevStatus h{};
+    e = cudaMemsetAsync(ds, 0, sizeof(DevStatus), st);
+    if (e == cudaSuccess) e = launch_wait_probe(ds, absent, spin_limit, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ds, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(ds, st);
+    if (e != cudaSuccess) return fail(nullptr, LS_ERR_CUDA, "test_bounded_wait: %s", cudaGetErrorString(e));
+    if (h.flag == FLAG_TIMEOUT) return fail(nullptr, LS_ERR_TIMEOUT, "test_bounded_wait: the wait ran out after %lld polls", (long long)spin_limit);
     return LS_OK;
 }
 
@@ -1945,6 +1977,65 @@ int lattice_sum_tune_eval(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, vo
                                                       (long long)cap, (long long)js.size() + 1);
         memcpy(report, js.c_str(), js.size() + 1);
     }
+    return LS_OK;
+}
+
+int lattice_sum_galerkin(ls_ctx* ctx, const double* const* basis, int32_t nb, double* V) {
+    if (!ctx) return fail(nullptr, LS_ERR_ARG, "galerkin: NULL context");
+    if (!ctx->reduced) return fail(ctx, LS_ERR_STATE, "galerkin: call rhosvd_reduce first");
+    if (!basis || !basis[0] || !basis[1] || !basis[2] || nb < 1 || nb > 65535 || !V)
+        return fail(ctx, LS_ERR_ARG, "galerkin: bad arguments");
+    cudaStream_t st = ctx->st;
+    const int64_t N = ctx->p.N;
+    const int32_t* r = ctx->r;
+    const int64_t npairs = (int64_t)nb * (nb + 1) / 2;
+    // pairs in chunks: the Hadamard rows (np x N), the projections and Y (np x r0 r1) within ~1 GB
+    const int64_t per = std::max<int64_t>(N, (int64_t)r[0] * r[1]) * 8 * 3;
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(npairs, ((int64_t)1 << 30) / std::max<int64_t>(per, 1)));
+    std::vector<int2> hp;
+    hp.reserve(npairs);
+    for (int k = 0; k < nb; ++k)
+        for (int m = k; m < nb; ++m) hp.push_back(make_int2(k, m));
+    int2* d_pairs = nullptr;
+    double *H = nullptr, *M[3] = {nullptr, nullptr, nullptr}, *Y = nullptr;
+    int* flag = nullptr;
+    CU(dalloc(ctx, &d_pairs, npairs));
+    CU(dalloc(ctx, &H, 3 * chunk * N));
+    for (int l = 0; l < 3; ++l) CU(dalloc(ctx, &M[l], chunk * r[l]));
+    CU(dalloc(ctx, &Y, chunk * r[0] * r[1]));
+    CU(dalloc(ctx, &flag, 1));
+    CU(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    CU(upload_h2d(d_pairs, hp.data(), npairs * sizeof(int2), st));
+    count_h2d(npairs * sizeof(int2));
+    Scope sc("galerkin", st);
+    for (int64_t p0 = 0; p0 < npairs; p0 += chunk) {
+        const int np = (int)std::min<int64_t>(chunk, npairs - p0);
+        X64Mat xs[3], ys[3];
+        double* D[3];
+        int64_t ld[3];
+        for (int l = 0; l < 3; ++l) {
+            CU(launch_hadamard_pairs(basis[l], N, d_pairs + p0, np, H + l * chunk * N, st));
+            xs[l] = X64Mat{H + l * chunk * N, np, N, N, 1, nullptr};   // Hadamard rows
+            ys[l] = X64Mat{ctx->d_Z[l], r[l], N, N, 1, nullptr};      // Z_l (r_l x N)
+            D[l] = M[l];
+            ld[l] = r[l];
+        }
+        std::string err;
+        int rc = x64_nt(3, xs, ys, D, ld, flag, st, &err);                         // M_l = H_l Z_l^T
+        xs[0] = X64Mat{M[2], np, r[2], r[2], 1, nullptr};                          // M2 (np x r2)
+        ys[0] = X64Mat{ctx->d_B, (int64_t)r[0] * r[1], r[2], r[2], 1, nullptr};    // core rows (a,b)
+        D[0] = Y;
+        ld[0] = (int64_t)r[0] * r[1];
+        if (rc == LS_OK) rc = x64_nt(1, xs, ys, D, ld, flag, st, &err);            // Y = M2 B^T
+        if (rc != LS_OK) return fail(ctx, rc, "galerkin: %s", err.c_str());
+        CU(launch_galerkin_contract(Y, M[0], M[1], r[0], r[1], d_pairs + p0, np, nb, V, st));
+    }
+    int hflag = 0;
+    CU(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    count_d2h(sizeof(int));
+    CU(cudaStreamSynchronize(st));
+    for (void* q : {(void*)d_pairs, (void*)H, (void*)M[0], (void*)M[1], (void*)M[2], (void*)Y, (void*)flag}) dfree(ctx, q);
+    if (hflag == FLAG_TIMEOUT) return fail(ctx, LS_ERR_TIMEOUT, "galerkin: a tensor-core product's bounded wait timed out");
     return LS_OK;
 }
 

@@ -221,7 +221,17 @@ cudaError_t launch_gather_rows(const double* M, int64_t len, const int32_t* perm
 // sqrt(mult[j]) / nrm[j] times it (zero where nrm[j] = 0).
 cudaError_t launch_block_frob(const double* A, int w, int64_t N, int nblocks, const double* mult, double* nrm,
                               double* out, cudaStream_t st);
+// The bounded group barrier of the cooperative kernels with `limit` polls, in a two-CTA grid
+// whose second CTA arrives (absent = 0) or does not (absent = 1): the failure-path probe.
+cudaError_t launch_wait_probe(DevStatus* st, int absent, long long limit, cudaStream_t stream);
 // *out = sum_e x[e]^3, e < n (device).
 cudaError_t launch_sum_cubes(const double* x, int64_t n, double* out, cudaStream_t st);
+
+// Galerkin matrix steps (ls_galerkin.cu), Eq. (nuc_pot): H[p][i] = g[k_p][i] g[m_p][i] for
+// the pairs (k_p, m_p) (g: nb rows of length N); and, per pair, v_p = sum_a M0[p][a]
+// sum_b Y[p][a r1 + b] M1[p][b], stored at V[k][m] and V[m][k] (V: nb x nb).
+cudaError_t launch_hadamard_pairs(const double* g, int64_t N, const int2* pairs, int np, double* H, cudaStream_t st);
+cudaError_t launch_galerkin_contract(const double* Y, const double* M0, const double* M1, int r0, int r1,
+                                     const int2* pairs, int np, int nb, double* V, cudaStream_t st);
 
 }  // namespace ls

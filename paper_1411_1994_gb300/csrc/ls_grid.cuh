@@ -16,7 +16,7 @@ constexpr long long kSpinLimit = 1LL << 24;   // ~1-2 s of polling with nanoslee
 // co-resident (cooperative launch). On timeout the flag is raised and every
 // CTA returns false.
 // ---------------------------------------------------------------------------
-__device__ bool group_barrier(DevStatus* st, unsigned int nblocks) {
+__device__ bool group_barrier_n(DevStatus* st, unsigned int nblocks, long long limit) {
     __shared__ int s_ok;
     __syncthreads();
     if (nblocks <= 1) return true;
@@ -35,7 +35,7 @@ __device__ bool group_barrier(DevStatus* st, unsigned int nblocks) {
             long long it = 0;
             while (*vgen == g) {
                 if (*vflag != FLAG_OK) { ok = 0; break; }
-                if (++it > kSpinLimit) { atomicCAS(&st->flag, FLAG_OK, FLAG_TIMEOUT); ok = 0; break; }
+                if (++it > limit) { atomicCAS(&st->flag, FLAG_OK, FLAG_TIMEOUT); ok = 0; break; }
                 __nanosleep(32);
             }
         }
@@ -46,6 +46,8 @@ __device__ bool group_barrier(DevStatus* st, unsigned int nblocks) {
     __syncthreads();
     return s_ok != 0;
 }
+
+__device__ bool group_barrier(DevStatus* st, unsigned int nblocks) { return group_barrier_n(st, nblocks, kSpinLimit); }
 
 }  // namespace
 }  // namespace ls

@@ -223,6 +223,14 @@ __global__ void __launch_bounds__(256) k_sum_cubes(const double* __restrict__ x,
 
 unsigned blocks_for(int64_t n) { return (unsigned)((n + 255) / 256); }
 
+// The bounded group barrier on its own: a two-CTA cooperative grid in which CTA 1 arrives
+// (absent = 0) or returns without arriving (absent = 1); CTA 0 waits with `limit` polls, so
+// with an absent partner the wait runs out and raises FLAG_TIMEOUT instead of hanging.
+__global__ void k_wait_probe(DevStatus* st, int absent, long long limit) {
+    if (blockIdx.x == 1 && absent) return;
+    group_barrier_n(st, 2u, limit);
+}
+
 }  // namespace
 
 cudaError_t launch_osj(const OsjJob* jobs, int njobs, int max_sweeps, int num_sms, cudaStream_t st) {
@@ -261,6 +269,12 @@ cudaError_t launch_osj(const OsjJob* jobs, int njobs, int max_sweeps, int num_sm
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_wait_probe(DevStatus* st, int absent, long long limit, cudaStream_t stream) {
+    void* args[] = {&st, &absent, &limit};
+    count_kernels(1);
+    return cudaLaunchCooperativeKernel((void*)k_wait_probe, dim3(2), dim3(32), args, 0, stream);
 }
 
 cudaError_t launch_resid_rows(const double* A, const double* w, const double* D, int64_t rows, int64_t N, double* E,

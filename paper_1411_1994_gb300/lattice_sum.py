@@ -33,6 +33,7 @@ EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_fit_t_scale_kernel", "lattic
             "lattice_sum_read", "lattice_sum_profile", "lattice_sum_profile_report",
             "lattice_sum_eval_slab_noalloc", "lattice_sum_batch_reduce", "lattice_sum_gemm_nt",
             "lattice_sum_gemm_nt_mixed", "lattice_sum_jacobi_eig", "lattice_sum_svd_rows", "lattice_sum_tune_eval",
+            "lattice_sum_test_fail_alloc", "lattice_sum_test_bounded_wait", "lattice_sum_galerkin",
             "lattice_sum_destroy",
             "lattice_sum_last_error")
 
@@ -97,10 +98,12 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                         C.c_void_p]
     lib.lattice_sum_gemm_nt_mixed.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
                                               C.c_int32, C.c_int32, C.c_void_p]
-    lib.lattice_sum_jacobi_eig.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_void_p,
-                                           C.c_void_p, C.c_void_p, C.c_void_p]
-    lib.lattice_sum_svd_rows.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p, C.c_void_p,
-                                         C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.lattice_sum_jacobi_eig.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.lattice_sum_test_fail_alloc.argtypes = [C.c_int64]
+    lib.lattice_sum_test_bounded_wait.argtypes = [C.c_int32, C.c_int64, C.c_void_p]
+    lib.lattice_sum_svd_rows.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_int32, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.lattice_sum_destroy.argtypes = [C.c_void_p]
     lib.lattice_sum_destroy.restype = None
     lib.lattice_sum_last_error.argtypes = [C.c_void_p]
@@ -207,9 +210,10 @@ def gemm_nt_mixed(A, B, dtype=None, tile_n: int = 0):
     return D
 
 
-def jacobi_eig(H, tol: float = 1e-7, abs_floor: float = 0.0, form: int = 2):
+def jacobi_eig(H, tol: float = 1e-7, abs_floor: float = 0.0, form: int = 2, max_sweeps: int = 0):
     """One run of the block Jacobi (lattice_sum_jacobi_eig) on a symmetric float64 CUDA tensor:
-    returns (diagonal, V = I + F, sweeps); form 1 = cluster (shared memory), 2 = grid."""
+    returns (diagonal, V = I + F, sweeps); form 1 = cluster (shared memory), 2 = grid;
+    max_sweeps 0 = the default limit (60)."""
     import torch
     H = H.contiguous()
     k = H.shape[0]
@@ -217,12 +221,12 @@ def jacobi_eig(H, tol: float = 1e-7, abs_floor: float = 0.0, form: int = 2):
     V = torch.empty((k, k), dtype=torch.float64, device=H.device)
     sw = C.c_int32()
     _check(lib().lattice_sum_jacobi_eig(C.c_void_p(H.data_ptr()), C.c_int32(k), C.c_double(tol),
-                                        C.c_double(abs_floor), C.c_int32(form),
+                                        C.c_double(abs_floor), C.c_int32(form), C.c_int32(max_sweeps),
                                         C.c_void_p(D.data_ptr()), C.c_void_p(V.data_ptr()), C.byref(sw), None))
     return D, V, sw.value
 
 
-def svd_rows(B, tol: float = None):
+def svd_rows(B, tol: float = None, max_sweeps: int = 0):
     """One-sided Jacobi on the rows of a float64 CUDA tensor B (m x C) (lattice_sum_svd_rows):
     returns (squared row norms after convergence, rotation M, sweeps, rotations per sweep)."""
     import torch
@@ -235,8 +239,18 @@ def svd_rows(B, tol: float = None):
     sw = C.c_int32()
     rot = (C.c_int64 * 64)()
     _check(lib().lattice_sum_svd_rows(C.c_void_p(B.data_ptr()), C.c_int32(m), C.c_int32(Cc), C.c_double(tol),
-                                      C.c_void_p(sig2.data_ptr()), C.c_void_p(M.data_ptr()), C.byref(sw), rot, None))
+                                      C.c_int32(max_sweeps), C.c_void_p(sig2.data_ptr()), C.c_void_p(M.data_ptr()), C.byref(sw), rot, None))
     return sig2, M, sw.value, [int(rot[k]) for k in range(sw.value)]
+
+
+def test_fail_alloc(n: int):
+    """lattice_sum_test_fail_alloc: the n-th context allocation from now fails (n < 0: off)."""
+    _check(lib().lattice_sum_test_fail_alloc(C.c_int64(int(n))))
+
+
+def test_bounded_wait(absent: int, spin_limit: int):
+    """lattice_sum_test_bounded_wait: the return code (LS_OK or LS_ERR_TIMEOUT) of the probe."""
+    return int(lib().lattice_sum_test_bounded_wait(C.c_int32(int(absent)), C.c_int64(int(spin_limit)), None))
 
 
 def fit_t_scale(R: int, sinc_step: float, r_min: float, r_max: float, kappa: float = 0.0,
@@ -350,6 +364,17 @@ class LatticeSum:
         _check(self._lib.lattice_sum_read(self.ctx, what, mode, arr.ctypes.data_as(C.c_void_p), need.value,
                                           None), self.ctx)
         return arr
+
+    def galerkin(self, basis):
+        """lattice_sum_galerkin for three float64 CUDA tensors (nb x N), row k = g_k^l; returns the
+        nb x nb Galerkin matrix (a float64 CUDA tensor)."""
+        import torch
+        basis = [b.contiguous() for b in basis]
+        nb = basis[0].shape[0]
+        V = torch.empty((nb, nb), dtype=torch.float64, device=basis[0].device)
+        ptrs = (C.c_void_p * 3)(*[b.data_ptr() for b in basis])
+        _check(self._lib.lattice_sum_galerkin(self.ctx, ptrs, nb, C.c_void_p(V.data_ptr())), self.ctx)
+        return V
 
     def factors(self):
         Z = (C.c_void_p * 3)()

@@ -146,6 +146,6 @@ def test_bad_arguments():
     x = torch.zeros((3, 4), dtype=torch.float64, device="cuda")
     import ctypes as C
     for m, Cc, tol in ((0, 4, 1e-15), (3, 0, 1e-15), (3, 4, 0.0)):
-        rc = L.lib().lattice_sum_svd_rows(C.c_void_p(x.data_ptr()), m, Cc, C.c_double(tol), C.c_void_p(x.data_ptr()),
-                                          C.c_void_p(x.data_ptr()), None, None, None)
+        rc = L.lib().lattice_sum_svd_rows(C.c_void_p(x.data_ptr()), m, Cc, C.c_double(tol), 0,
+                                          C.c_void_p(x.data_ptr()), C.c_void_p(x.data_ptr()), None, None, None)
         assert rc == L.LS_ERR_ARG
