@@ -445,6 +445,30 @@ int lattice_sum_tune_eval(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, vo
                           char* report, int64_t cap);
 
 /*
+ * lattice_sum_als_refine -- ALS refinement of the reduced Tucker tensor,
+ * Thm A.1(a)-(b): the best rank-(r1, r2, r3) Tucker approximation maximises
+ * the core norm ||mu|| over orthonormal bases, and alternating maximisation
+ * from the RHOSVD start finds it. One step for mode l, the other two bases
+ * fixed: Y_l <- the r_l leading left singular vectors of the N x r_m r_n
+ * matrix B_l = sum_nu xi_nu a_l,nu (x) (Y_m^T a_m,nu) (x) (Y_n^T a_n,nu).
+ * B_l lies in the range of the mode-l side matrix, so the step works in the
+ * orthonormal basis Q_l of that range which the non-squaring route keeps:
+ * B_l = Q_l^T S_l, S_l = (Q_l A_l^T) W_l (m_l x r_m r_n; W_l the terms
+ * grouped by their mode-l vector, as the core's first step), and its leading
+ * left singular vectors come from one-sided Jacobi on the rows of S_l (no
+ * squaring). `sweeps` (0..100) sweeps over the modes l = 1, 2, 3; then the
+ * projections and the core are recomputed (Thm A.1(c)). Ranks do not
+ * change. history (host, sweeps + 1 entries, may be NULL): ||mu|| at the
+ * start and after each sweep (non-decreasing: ||A - A_r||^2 = ||A||^2 -
+ * ||mu||^2). info (may be NULL): the reduction's report (its bound still
+ * holds), with sweeps[] = the ALS sweeps. Needs a context reduced on the
+ * non-squaring route (LS_FP64, or LS_FLAG_SVD_ONESIDED). Synchronises the
+ * stream. Errors: LS_ERR_ARG, LS_ERR_STATE, LS_ERR_OOM, LS_ERR_CUDA,
+ * LS_ERR_NOCONVERGE, LS_ERR_TIMEOUT.
+ */
+int lattice_sum_als_refine(ls_ctx* ctx, int32_t sweeps, double* history, ls_tucker_info* info);
+
+/*
  * lattice_sum_galerkin -- the Galerkin matrix of the reduced potential in a
  * rank-one basis, Eq. (nuc_pot): for basis functions G_k = g_k^1 (x) g_k^2
  * (x) g_k^3 sampled at the grid's cell centres,

@@ -99,6 +99,9 @@ struct ls_ctx {
     double* d_Z[3] = {nullptr, nullptr, nullptr};
     double* d_P[3] = {nullptr, nullptr, nullptr};
     double* d_B = nullptr;
+    double* d_Q[3] = {nullptr, nullptr, nullptr};   // non-squaring route: orthonormal basis of each side matrix's range
+    int32_t mq[3] = {0, 0, 0};                      // its dimension
+    ls_tucker_info last_info{};                     // what the reduction reported
     int32_t* d_tcol = nullptr;
     double* d_xi = nullptr;
     double* d_xin = nullptr;
@@ -1009,11 +1012,13 @@ int red_finish(RedState& R, ls_tucker_info* info) {
 }
 
 // (c2) projection, (c3) core, release of the scratch, status and info (Z in ctx->d_Z)
+int red_core(RedState& R, ls_tucker_info* info);
+int red_project_core_noproj(RedState& R, ls_tucker_info* info) { return red_core(R, info); }
+
 int red_project_core(RedState& R, ls_tucker_info* info) {
     ls_ctx* ctx = R.ctx;
     cudaStream_t st = ctx->st;
     const int64_t N = ctx->p.N;
-    const int64_t T = R.T;
     {
         // (c2) projection P_l = Z_l^T A_l, both paths: FP64-grade exact-slice products on the
         // tensor cores (the dense FP64 contraction the truncation rests on)
@@ -1033,6 +1038,14 @@ int red_project_core(RedState& R, ls_tucker_info* info) {
         int rc = x64_project(3, Z, rs, a, Cs, N, P, &R.d_st[9].flag, st, &err);
         if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: projection: %s", err.c_str());
     }
+    return red_core(R, info);
+}
+
+// (c3) the core from the projections in ctx->d_P, then release, statuses and info
+int red_core(RedState& R, ls_tucker_info* info) {
+    ls_ctx* ctx = R.ctx;
+    cudaStream_t st = ctx->st;
+    const int64_t T = R.T;
     { Scope sc("fold", st); CUS(launch_fold_norms(ctx->d_xi, ctx->d_tcol, T, ctx->d_norms[0], ctx->d_norms[1], ctx->d_norms[2], ctx->d_xin, st)); }
     // (c3) core: terms grouped by their mode-0 vector (counting sort on the host)
     int32_t Cs[3] = {(int32_t)ctx->mode[0].C, (int32_t)ctx->mode[1].C, (int32_t)ctx->mode[2].C};
@@ -1631,9 +1644,12 @@ int reduce_accurate(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_in
         int rc = x64_nt(3, xs, ys, ctx->d_Z, ld, flag, st, &err);
         if (rc != LS_OK) return bail(fail(ctx, rc, "rhosvd_reduce: basis: %s", err.c_str()));
         for (int l = 0; l < 3; ++l) {
-            for (void* q : {(void*)Ms[l], (void*)Q[l], (void*)Bm[l], (void*)Mr[l], (void*)sig2[l], (void*)isl[l],
-                            (void*)perm[l]})
+            for (void* q : {(void*)Ms[l], (void*)Bm[l], (void*)Mr[l], (void*)sig2[l], (void*)isl[l], (void*)perm[l]})
                 dfree(ctx, q);
+            // the range basis stays with the context (the ALS refinement restricts its SVDs to it)
+            dfree(ctx, ctx->d_Q[l]);
+            ctx->d_Q[l] = Q[l];
+            ctx->mq[l] = m[l];
             if (!side) dfree(ctx, w[l]);
         }
         dfree(ctx, extra);
@@ -1744,9 +1760,12 @@ int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ran
     if (ctx->reduced) return fail(ctx, LS_ERR_STATE, "rhosvd_reduce: already reduced");
     if (!forced_ranks && !(eps > 0.0)) return fail(ctx, LS_ERR_ARG, "rhosvd_reduce: eps must be > 0");
     ls_ctx* one[1] = {ctx};
-    const int rc = ctx->tucker     ? reduce_tucker(ctx, eps, forced_ranks, info)
-                   : one_sided(ctx) ? reduce_accurate(ctx, eps, forced_ranks, info)
-                                    : reduce_many(one, 1, eps, forced_ranks, info);
+    ls_tucker_info mine{};
+    ls_tucker_info* inf = info ? info : &mine;
+    const int rc = ctx->tucker     ? reduce_tucker(ctx, eps, forced_ranks, inf)
+                   : one_sided(ctx) ? reduce_accurate(ctx, eps, forced_ranks, inf)
+                                    : reduce_many(one, 1, eps, forced_ranks, inf);
+    if (rc == LS_OK) ctx->last_info = *inf;
     // a large reduction leaves tens of GB of freed scratch in the stream-ordered pool
     // (the stream is synchronised here): when the device runs short, give it back beyond a
     // few GB, so that other allocators on the device can use it
@@ -1978,6 +1997,174 @@ int lattice_sum_tune_eval(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, vo
         memcpy(report, js.c_str(), js.size() + 1);
     }
     return LS_OK;
+}
+
+int lattice_sum_als_refine(ls_ctx* ctx, int32_t sweeps, double* history, ls_tucker_info* info) {
+    if (!ctx) return fail(nullptr, LS_ERR_ARG, "als_refine: NULL context");
+    if (!ctx->reduced) return fail(ctx, LS_ERR_STATE, "als_refine: call rhosvd_reduce first");
+    if (sweeps < 0 || sweeps > 100) return fail(ctx, LS_ERR_ARG, "als_refine: sweeps out of range [0, 100]");
+    for (int l = 0; l < 3; ++l)
+        if (!ctx->d_Q[l])
+            return fail(ctx, LS_ERR_STATE, "als_refine: needs the range bases of the non-squaring route "
+                                           "(an LS_FP64 context, or LS_FLAG_SVD_ONESIDED)");
+    cudaStream_t st = ctx->st;
+    const int64_t N = ctx->p.N;
+    const int64_t T = (int64_t)ctx->xi.size();
+    const double u = 1.1102230246251565e-16;
+    const int32_t* r = ctx->r;
+    int64_t C[3];
+    for (int l = 0; l < 3; ++l) C[l] = ctx->mode[l].C;
+    const int* m = ctx->mq;
+    Scope sc_all("als", st);
+    DevStatus* ds = nullptr;   // [0]: the tensor-core products' flag, [1]: the one-sided Jacobi
+    double* scal = nullptr;
+    CU(dalloc(ctx, &ds, 2));
+    CU(dalloc(ctx, &scal, 1));
+    CU(cudaMemsetAsync(ds, 0, 2 * sizeof(DevStatus), st));
+    int* flag = &ds[0].flag;
+    // history[0]: ||core|| of the start
+    double h0 = 0.0;
+    CU(launch_sum_squares(ctx->d_B, (int64_t)r[0] * r[1] * r[2], scal, st));
+    CU(cudaMemcpyAsync(&h0, scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (history) history[0] = sqrt(h0);
+    // K_l = Q_l A_l^T (m_l x C_l): the unit canonical vectors in the range bases
+    double* K[3];
+    double* Pt[3];
+    {
+        X64Mat xs[3], ys[3];
+        int64_t ld[3];
+        for (int l = 0; l < 3; ++l) {
+            CU(dalloc(ctx, &K[l], (int64_t)m[l] * C[l]));
+            CU(dalloc(ctx, &Pt[l], C[l] * r[l]));
+            xs[l] = X64Mat{ctx->d_Q[l], m[l], N, N, 1, nullptr};
+            ys[l] = X64Mat{ctx->mode[l].d_cols, C[l], N, N, 1, nullptr};
+            ld[l] = C[l];
+            CU(launch_transpose(ctx->d_P[l], r[l], C[l], Pt[l], st));
+        }
+        std::string err;
+        int rc = x64_nt(3, xs, ys, K, ld, flag, st, &err);
+        if (rc != LS_OK) return fail(ctx, rc, "als_refine: %s", err.c_str());
+    }
+    // per mode: the terms grouped by their mode-l vector, with the columns reordered (l, m, n)
+    int32_t *d_tc[3], *d_perm[3], *d_off[3];
+    for (int l = 0; l < 3; ++l) {
+        const int mm = l == 0 ? 1 : 0, nn = l == 2 ? 1 : 2;
+        std::vector<int32_t> tc(3 * T), off(C[l] + 1, 0), perm(T);
+        for (int64_t t = 0; t < T; ++t) {
+            tc[3 * t] = ctx->tcol[3 * t + l];
+            tc[3 * t + 1] = ctx->tcol[3 * t + mm];
+            tc[3 * t + 2] = ctx->tcol[3 * t + nn];
+            off[tc[3 * t] + 1] += 1;
+        }
+        for (int64_t c = 0; c < C[l]; ++c) off[c + 1] += off[c];
+        std::vector<int32_t> pos(off.begin(), off.end() - 1);
+        for (int64_t t = 0; t < T; ++t) perm[pos[tc[3 * t]]++] = (int32_t)t;
+        CU(dalloc(ctx, &d_tc[l], 3 * T));
+        CU(dalloc(ctx, &d_perm[l], T));
+        CU(dalloc(ctx, &d_off[l], C[l] + 1));
+        CU(upload_h2d(d_tc[l], tc.data(), 3 * T * sizeof(int32_t), st));
+        CU(upload_h2d(d_perm[l], perm.data(), T * sizeof(int32_t), st));
+        CU(upload_h2d(d_off[l], off.data(), (C[l] + 1) * sizeof(int32_t), st));
+        count_h2d((3 * T + T + C[l] + 1) * sizeof(int32_t));
+    }
+    for (int s = 1; s <= sweeps; ++s) {
+        double kept = 0.0;
+        for (int l = 0; l < 3; ++l) {
+            // Thm A.1(b): Y_l <- the r_l leading left singular vectors of B_l = A_l^T W_l,
+            // W_l[c] = sum_{t: c_l(t) = c} xin_t P_m[:, c_m(t)] (x) P_n[:, c_n(t)]; within the range
+            // basis, B_l = Q_l^T S_l with S_l = K_l W_l (m_l x r_m r_n)
+            const int mm = l == 0 ? 1 : 0, nn = l == 2 ? 1 : 2;
+            const int64_t w = (int64_t)r[mm] * r[nn];
+            double *W = nullptr, *S = nullptr, *M = nullptr, *sig2 = nullptr, *lam = nullptr, *isl = nullptr,
+                   *sel = nullptr, *Ms = nullptr;
+            int32_t* pm = nullptr;
+            unsigned* cmax = nullptr;
+            CU(dalloc(ctx, &W, C[l] * w));
+            CU(dalloc(ctx, &S, (int64_t)m[l] * w));
+            CU(dalloc(ctx, &M, (int64_t)m[l] * m[l]));
+            CU(dalloc(ctx, &sig2, m[l]));
+            CU(dalloc(ctx, &lam, m[l]));
+            CU(dalloc(ctx, &isl, m[l]));
+            CU(dalloc(ctx, &pm, m[l]));
+            CU(dalloc(ctx, &sel, 3));
+            CU(dalloc(ctx, &cmax, 64));
+            CU(dalloc(ctx, &Ms, (int64_t)r[l] * m[l]));
+            CU(cudaMemsetAsync(cmax, 0, 64 * sizeof(unsigned), st));
+            CU(cudaMemsetAsync(&ds[1], 0, sizeof(DevStatus), st));
+            CU(launch_core_step1_f64(Pt[mm], Pt[nn], r[mm], r[nn], d_tc[l], ctx->d_xin, d_perm[l], d_off[l], 0,
+                                     (int)C[l], W, st));
+            std::string err;
+            X64Mat xs[1] = {X64Mat{K[l], m[l], C[l], C[l], 1, nullptr}};   // K_l (m x C)
+            X64Mat ys[1] = {X64Mat{W, w, C[l], 1, w, nullptr}};            // W_l^T (r_m r_n x C)
+            double* D[1] = {S};
+            int64_t ld[1] = {w};
+            int rc = x64_nt(1, xs, ys, D, ld, flag, st, &err);
+            if (rc != LS_OK) return fail(ctx, rc, "als_refine: %s", err.c_str());
+            const OsjJob J{S, w, (int)w, M, m[l], sig2, &ds[1], 8.0 * u * sqrt((double)w), cmax};
+            CU(launch_osj(&J, 1, 60, ctx->num_sms, st));
+            SortSelectJob sj{sig2, m[l], r[l], nullptr, pm, lam, isl, sel};
+            sj.dstride = 1;
+            sj.resolution = 0.0;
+            CU(launch_sort_select(1, &sj, 1e-300, 0.0, st));
+            CU(launch_gather_rows(M, m[l], pm, r[l], nullptr, Ms, st));
+            xs[0] = X64Mat{Ms, r[l], m[l], m[l], 1, nullptr};                // M_r (r x m)
+            ys[0] = X64Mat{ctx->d_Q[l], N, m[l], 1, N, nullptr};             // Q^T (N x m)
+            D[0] = ctx->d_Z[l];
+            ld[0] = N;
+            rc = x64_nt(1, xs, ys, D, ld, flag, st, &err);                   // Y_l = M_r Q_l
+            const double* Zc[1] = {ctx->d_Z[l]};
+            const double* ac[1] = {ctx->mode[l].d_cols};
+            const int rl[1] = {r[l]};
+            const int64_t Cl[1] = {C[l]};
+            double* Pl[1] = {ctx->d_P[l]};
+            if (rc == LS_OK) rc = x64_project(1, Zc, rl, ac, Cl, N, Pl, flag, st, &err);   // P_l = Y_l A_l^T
+            if (rc != LS_OK) return fail(ctx, rc, "als_refine: %s", err.c_str());
+            CU(launch_transpose(ctx->d_P[l], r[l], C[l], Pt[l], st));
+            double hsel[3];
+            DevStatus hd[2];
+            CU(cudaMemcpyAsync(hsel, sel, sizeof hsel, cudaMemcpyDeviceToHost, st));
+            CU(cudaMemcpyAsync(hd, ds, sizeof hd, cudaMemcpyDeviceToHost, st));
+            count_d2h(sizeof hsel + sizeof hd);
+            CU(cudaStreamSynchronize(st));
+            if (hd[0].flag == FLAG_TIMEOUT || hd[1].flag == FLAG_TIMEOUT)
+                return fail(ctx, LS_ERR_TIMEOUT, "als_refine: a bounded wait timed out");
+            if (hd[1].flag == FLAG_NOCONVERGE)
+                return fail(ctx, LS_ERR_NOCONVERGE, "als_refine: one-sided Jacobi did not converge (mode %d)", l);
+            kept = std::max(hsel[2] - hsel[1], 0.0);   // ||Y_l^T B_l||^2 = the kept singular values squared
+            for (void* q : {(void*)W, (void*)S, (void*)M, (void*)sig2, (void*)lam, (void*)isl, (void*)pm, (void*)sel,
+                            (void*)cmax, (void*)Ms})
+                dfree(ctx, q);
+        }
+        if (history) history[s] = sqrt(kept);
+    }
+    for (int l = 0; l < 3; ++l)
+        for (void* q : {(void*)K[l], (void*)Pt[l], (void*)d_tc[l], (void*)d_perm[l], (void*)d_off[l]}) dfree(ctx, q);
+    dfree(ctx, scal);
+    dfree(ctx, ds);
+    // Thm A.1(c): the core of the refined bases; the evaluation operands are rebuilt on demand
+    dt_eval_free(ctx->eval_cache);
+    ctx->eval_cache = nullptr;
+    dfree(ctx, ctx->d_B);
+    ctx->d_B = nullptr;
+    ctx->reduced = false;
+    RedState rf;
+    rf.ctx = ctx;
+    rf.T = T;
+    rf.floor_noise = 0.0;
+    CU(dalloc(ctx, &rf.d_st, 10));
+    CU(cudaMemsetAsync(rf.d_st, 0, 10 * sizeof(DevStatus), st));
+    CU(dalloc(ctx, &rf.d_sel, 9));
+    for (int l = 0; l < 3; ++l) rf.sel[l][0] = r[l];
+    ls_tucker_info tmp;
+    const int rc = red_project_core_noproj(rf, &tmp);
+    if (rc == LS_OK && info) {
+        // the reduction's report still holds: ALS does not increase the error (Thm A.1(b)), so
+        // the RHOSVD bound bounds the refined tensor too; sweeps = the ALS sweeps
+        *info = ctx->last_info;
+        for (int l = 0; l < 3; ++l) info->sweeps[l] = sweeps;
+    }
+    return rc;
 }
 
 int lattice_sum_galerkin(ls_ctx* ctx, const double* const* basis, int32_t nb, double* V) {

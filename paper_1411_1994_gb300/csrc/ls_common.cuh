@@ -190,6 +190,14 @@ cudaError_t launch_core_f64(const double* P0, const double* P1t, const double* P
                             const int32_t* tcol, const double* xin, const int32_t* perm, const int32_t* off,
                             double* W, int64_t w_cols, double* B, cudaStream_t st);
 
+// The grouped first step of launch_core_f64 alone, for the groups [cbeg, cbeg + ncols):
+// W[c - cbeg][j*r2+k] = sum_{t in group c} xin[t] P1t[c1(t)][j] P2t[c2(t)][k] with
+// c1 = tcol[3t+1], c2 = tcol[3t+2] (the ALS refinement passes the term columns with the
+// mode of the update first).
+cudaError_t launch_core_step1_f64(const double* P1t, const double* P2t, int r1, int r2, const int32_t* tcol,
+                                  const double* xin, const int32_t* perm, const int32_t* off, int cbeg, int ncols,
+                                  double* W, cudaStream_t st);
+
 // Slab evaluation (FP64 arithmetic): out[s][x][y] for nslab z indices.
 // work holds >= r0*r1*nslab + r0*N*nslab doubles.
 cudaError_t launch_eval_f64(const double* const Z[3], const int32_t* r, const double* B, int64_t N,
@@ -224,6 +232,8 @@ cudaError_t launch_block_frob(const double* A, int w, int64_t N, int nblocks, co
 // The bounded group barrier of the cooperative kernels with `limit` polls, in a two-CTA grid
 // whose second CTA arrives (absent = 0) or does not (absent = 1): the failure-path probe.
 cudaError_t launch_wait_probe(DevStatus* st, int absent, long long limit, cudaStream_t stream);
+// *out = sum_e x[e]^2, e < n (device).
+cudaError_t launch_sum_squares(const double* x, int64_t n, double* out, cudaStream_t st);
 // *out = sum_e x[e]^3, e < n (device).
 cudaError_t launch_sum_cubes(const double* x, int64_t n, double* out, cudaStream_t st);
 

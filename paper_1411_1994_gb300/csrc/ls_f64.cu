@@ -1214,6 +1214,17 @@ cudaError_t launch_core_f64(const double* P0, const double* P1t, const double* P
     return cudaSuccess;
 }
 
+cudaError_t launch_core_step1_f64(const double* P1t, const double* P2t, int r1, int r2, const int32_t* tcol,
+                                  const double* xin, const int32_t* perm, const int32_t* off, int cbeg, int ncols,
+                                  double* W, cudaStream_t st) {
+    const int64_t nn = (int64_t)r1 * r2;
+    if (ncols < 1 || nn < 1) return cudaSuccess;
+    dim3 grid((unsigned)((nn + 256 * kCoreOut - 1) / (256 * kCoreOut)), (unsigned)ncols);
+    k_core_group_f64<<<grid, 256, 0, st>>>(P1t, P2t, r1, r2, tcol, xin, perm, off, cbeg, W);
+    count_kernels(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_eval_f64(const double* const Z[3], const int32_t* r, const double* B, int64_t N,
                             const int32_t* zidx, int nslab, double* work, void* out, int out_f32,
                             cudaStream_t st) {

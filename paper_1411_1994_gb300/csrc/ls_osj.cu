@@ -206,10 +206,11 @@ __global__ void __launch_bounds__(256) k_block_frob(const double* __restrict__ A
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) o[e] = a[e] * s_f;
 }
 
-// out = sum_e x[e]^3 (one CTA, fixed order)
-__global__ void __launch_bounds__(256) k_sum_cubes(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
+// out = sum_e x[e]^p, p = 2 or 3 (one CTA, fixed order)
+__global__ void __launch_bounds__(256) k_sum_powers(const double* __restrict__ x, int64_t n, int p,
+                                                    double* __restrict__ out) {
     double acc = 0.0;
-    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc = fma(x[e] * x[e], x[e], acc);
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc = fma(p == 3 ? x[e] * x[e] : x[e], x[e], acc);
     __shared__ double red[8];
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -309,7 +310,13 @@ cudaError_t launch_block_frob(const double* A, int w, int64_t N, int nblocks, co
 }
 
 cudaError_t launch_sum_cubes(const double* x, int64_t n, double* out, cudaStream_t st) {
-    k_sum_cubes<<<1, 256, 0, st>>>(x, n, out);
+    k_sum_powers<<<1, 256, 0, st>>>(x, n, 3, out);
+    count_kernels(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_squares(const double* x, int64_t n, double* out, cudaStream_t st) {
+    k_sum_powers<<<1, 256, 0, st>>>(x, n, 2, out);
     count_kernels(1);
     return cudaGetLastError();
 }

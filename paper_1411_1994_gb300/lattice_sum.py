@@ -34,7 +34,7 @@ EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_fit_t_scale_kernel", "lattic
             "lattice_sum_eval_slab_noalloc", "lattice_sum_batch_reduce", "lattice_sum_gemm_nt",
             "lattice_sum_gemm_nt_mixed", "lattice_sum_jacobi_eig", "lattice_sum_svd_rows", "lattice_sum_tune_eval",
             "lattice_sum_test_fail_alloc", "lattice_sum_test_bounded_wait", "lattice_sum_galerkin",
-            "lattice_sum_destroy",
+            "lattice_sum_als_refine", "lattice_sum_destroy",
             "lattice_sum_last_error")
 
 
@@ -364,6 +364,14 @@ class LatticeSum:
         _check(self._lib.lattice_sum_read(self.ctx, what, mode, arr.ctypes.data_as(C.c_void_p), need.value,
                                           None), self.ctx)
         return arr
+
+    def als_refine(self, sweeps: int):
+        """lattice_sum_als_refine: returns (history of ||core|| (sweeps + 1 values), info)."""
+        hist = (C.c_double * (int(sweeps) + 1))()
+        info = ls_tucker_info()
+        _check(self._lib.lattice_sum_als_refine(self.ctx, int(sweeps), hist, C.byref(info)), self.ctx)
+        self.info = info.as_dict()
+        return [hist[i] for i in range(int(sweeps) + 1)], self.info
 
     def galerkin(self, basis):
         """lattice_sum_galerkin for three float64 CUDA tensors (nb x N), row k = g_k^l; returns the
