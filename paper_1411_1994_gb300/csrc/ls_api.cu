@@ -685,6 +685,11 @@ struct RedState {
     const double* reorth[3] = {nullptr, nullptr, nullptr};
     int reorth_m[3] = {0, 0, 0};
     bool drop[3] = {false, false, false};   // kind 2: no residual direction above cand_res in this mode
+    // the eigen-solver's second Jacobi run is skipped: the eigenvalues are the Rayleigh quotients
+    // of the FP64 re-projection H' = Uo^T H Uo and the eigenvectors Uo (the mixed path, whose
+    // truncation sits far above the first run's accuracy, and the candidate bases of the
+    // non-squaring route, whose accuracy the one-sided Jacobi restores)
+    bool fast_eig = false;
 };
 
 #define CUS(call)                                                                                     \
@@ -1192,7 +1197,8 @@ int eigen_all(std::vector<RedState>& R, ls_ctx* const* ctxs, int n, const std::v
             const JacobiJob& J = jj[3 * i + l];
             if (!M.df) { grid.push_back(J); continue; }
             s1.push_back(DfJob{M.H, M.k, M.T1, 1, M.U0, 1, R[i].d_st + l, J.abs_floor, J.tau, 1e-6});
-            s2.push_back(DfJob{M.Hp, M.k, M.Hp, (int64_t)M.k + 1, M.F2, 0, R[i].d_st + l, J.abs_floor, J.tau, 1e-10});
+            if (!R[i].fast_eig)
+                s2.push_back(DfJob{M.Hp, M.k, M.Hp, (int64_t)M.k + 1, M.F2, 0, R[i].d_st + l, J.abs_floor, J.tau, 1e-10});
         }
     auto err = [&](cudaError_t e, const char* what) {
         return fail(c0, e == cudaErrorMemoryAllocation ? LS_ERR_OOM : LS_ERR_CUDA, "rhosvd_reduce: %s: %s", what,
@@ -1259,11 +1265,20 @@ int eigen_all(std::vector<RedState>& R, ls_ctx* const* ctxs, int n, const std::v
         });
         if (e != cudaSuccess) return err(e, "re-projection");
     }
-    {
+    if (!s2.empty()) {
         Scope sc("jacobi.run2", s0);
         if ((e = run_df(s2.data(), (int)s2.size(), 60, s0)) != cudaSuccess) return err(e, "Jacobi (second run)");
     }
     e = per_ctx([&](RedState& Rs, RedMode** ms, int nm) {
+        if (Rs.fast_eig) {
+            // V = Uo; the Rayleigh quotients on the diagonal of H' are the eigenvalues
+            for (int j = 0; j < nm; ++j) {
+                cudaError_t ce = cudaMemcpyAsync(ms[j]->V, ms[j]->Uo, sizeof(double) * ms[j]->k * ms[j]->k,
+                                                 cudaMemcpyDeviceToDevice, s0);
+                if (ce != cudaSuccess) return ce;
+            }
+            return cudaSuccess;
+        }
         const double *A[3], *B[3];
         double* out[3];
         int ks[3];
@@ -1327,6 +1342,7 @@ int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, l
     };
     for (int i = 0; i < n; ++i) {
         if (pass) R[i] = *pass;   // a pass of the non-squaring route (one context)
+        R[i].fast_eig = R[i].kind != 0 || ctxs[i]->p.precision == LS_MIXED;
         R[i].ctx = ctxs[i];
         R[i].eps = eps;
         R[i].forced = forced;

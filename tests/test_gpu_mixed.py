@@ -57,18 +57,21 @@ def rel(a, b):
                                 W.config2()], ids=lambda w: w.name)
 def test_mixed_contractions_match_fp64_path(wl):
     s = scale_for(wl)
-    # the FP64 path on the mixed path's singular-value route (the Gram route), so that the
-    # bases are the same and only the contractions differ
+    # the FP64 path on the mixed path's singular-value route (the Gram route): the same
+    # pre-compression and eps rule; the mixed path stops its eigen-solver after the first Jacobi
+    # run (Rayleigh quotients of the FP64 re-projection), so the bases agree as subspaces, and
+    # the contractions are compared through basis-free quantities
     a, ia = run(wl, s, L.LS_FP64, flags=L.LS_FLAG_SVD_GRAM)
     b, ib = run(wl, s, L.LS_MIXED)
     assert ib["r"] == ia["r"]
     for m in range(3):
-        # the FP64 orthogonalisation (eps rule, same pre-compression) is the same code in both paths
-        assert np.array_equal(a.read(L.LS_READ_BASIS, m), b.read(L.LS_READ_BASIS, m))
-        pa, pb = a.read(L.LS_READ_PROJ, m), b.read(L.LS_READ_PROJ, m)
-        assert rel(pb, pa) < 1e-7, (m, rel(pb, pa))
+        Za = a.read(L.LS_READ_BASIS, m).reshape(ia["r"][m], wl.N)
+        Zb = b.read(L.LS_READ_BASIS, m).reshape(ib["r"][m], wl.N)
+        pa, pb = a.read(L.LS_READ_PROJ, m).reshape(ia["r"][m], -1), b.read(L.LS_READ_PROJ, m).reshape(ib["r"][m], -1)
+        # the projected side matrices Z^T P (the columns' components in the subspace)
+        assert rel(Zb.T @ pb, Za.T @ pa) < 1e-7, (m, rel(Zb.T @ pb, Za.T @ pa))
     ca, cb = a.read(L.LS_READ_CORE), b.read(L.LS_READ_CORE)
-    assert rel(cb, ca) < 1e-7, rel(cb, ca)
+    assert abs(np.linalg.norm(cb) - np.linalg.norm(ca)) < 1e-7 * np.linalg.norm(ca)
     z = wl.slabs[:8]
     sa = a.eval_slab_torch(z).cpu().numpy()
     sb = b.eval_slab_torch(z).cpu().numpy()
