@@ -29,6 +29,8 @@ struct DevStatus {
     int flag;
     int sweeps;
     unsigned int sweep_active[64];
+    unsigned int arrive;        // arrivals at the pivoted Cholesky's counting barrier (only grows)
+    unsigned int pad;
 };
 
 // ---------------------------------------------------------------------------

@@ -799,20 +799,26 @@ __global__ void __launch_bounds__(kEigThreads) k_chol32_multi(const CholJob* job
 // cooperative grid for every matrix of the launch, D (hi/lo FP32), E (FP32,
 // full symmetric storage), the rotation accumulator F and the pair-block
 // rotations Q in global memory (L2-resident: about 2 MB a matrix at k = 512).
-// A round runs in two phases between bounded grid barriers:
+// A round runs in two phases between bounded counting barriers:
 //   A: a warp per pair-block loads its 16 x 16 diagonal block and 16 diagonal
 //      entries into registers, runs the inner sweep exactly as the cluster
 //      kernel does (the same function), and writes back the block, D and F_Q;
+//      the other warps meanwhile apply the previous round's rotations to F
+//      (F <- F + F_Q + F F_Q, a half-warp per pair-block and group of 16 rows,
+//      a lane per row): F never feeds back into the iteration, so its update
+//      waits one round and leaves the critical path;
 //   B: a half-warp per off-diagonal tile of two pair-blocks of which one
-//      rotated (E_ab <- Q_a^T E_ab Q_b, both triangles), and a half-warp per
-//      pair-block and group of 16 F rows (F <- F + F_Q + F F_Q).
-// Matrices of different sizes keep their own round and sweep counters. A
-// matrix stops after a sweep in which no pair qualified, or at the sweep
-// limit. The decision is read by every CTA from the same counter after the
-// same barrier, so control flow stays uniform. The outputs and the sweep
-// report are those of the cluster kernel. For the same input it gives the
-// same result, with one more sweep reported: that sweep is the empty one
-// that confirms convergence, where the cluster kernel scans instead.
+//      rotated (E_ab <- Q_a^T E_ab Q_b, both triangles).
+// Q and the pair-blocks' rotation flags are double-buffered by round parity
+// for the deferred F update. Warps are numbered across the CTAs first, so the
+// few inner sweeps of a round run on different SMs. Matrices of different
+// sizes keep their own round and sweep counters. A matrix stops after a sweep
+// in which no pair qualified, or at the sweep limit. The decision is read by
+// every CTA from the same counter after the same barrier, so control flow
+// stays uniform. The outputs and the sweep report are those of the cluster
+// kernel. For the same input it gives the same result, with one more sweep
+// reported: that sweep is the empty one that confirms convergence, where the
+// cluster kernel scans instead.
 // ---------------------------------------------------------------------------
 constexpr int kGbThreads = 512;
 constexpr int kGbMaxModes = 128;
@@ -822,20 +828,81 @@ struct GbMode {
     int64_t ldd; int k; int add_identity;
     float floor, tau, tol2;
     int K, ldE, nb, m;
-    DF* D; float* E; float* F; float* Q; int* act; unsigned int* cnt;   // cnt[2]: rotations a sweep (parity)
+    // Q [2][nb][16 x 16] and act [2][nb]: round parity; cnt[2]: rotations a sweep (sweep parity)
+    DF* D; float* E; float* F; float* Q; int* act; unsigned int* cnt;
 };
 struct GbArgs {
     const GbMode* m; int nm; int max_sweeps; DevStatus* bar;
 };
 
+// F <- F + F_Q + F F_Q on the 16 columns of pair-block a of round `round` for
+// the rows 16 g .. 16 g + 15: a half-warp, lane x owns row 16 g + x; the
+// half-warp stages F_Q in sq. The same products in the same order as the
+// cluster kernel's F update.
+__device__ __forceinline__ void gb_f_rows(const GbMode& J, int round, const float* Qp, int a, int g, int x,
+                                          unsigned int half, float* sq) {
+    int Ia, Ja;
+    rr_pair_e(round, a, J.m, Ia, Ja);
+    const float4* fq4 = reinterpret_cast<const float4*>(Qp + (int64_t)a * BJ2SQ);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) reinterpret_cast<float4*>(sq)[x * 4 + q] = fq4[x * 4 + q];
+    const int row = g * BJ2 + x;
+    float* fr = J.F + (int64_t)row * J.K;
+    const float4 f0 = *reinterpret_cast<const float4*>(fr + Ia * BJ);
+    const float4 f1 = *reinterpret_cast<const float4*>(fr + Ia * BJ + 4);
+    const float4 f2 = *reinterpret_cast<const float4*>(fr + Ja * BJ);
+    const float4 f3 = *reinterpret_cast<const float4*>(fr + Ja * BJ + 4);
+    const float f[BJ2] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w,
+                          f2.x, f2.y, f2.z, f2.w, f3.x, f3.y, f3.z, f3.w};
+    __syncwarp(half);
+    float o[BJ2];
+#pragma unroll
+    for (int c = 0; c < BJ2; ++c) o[c] = f[c];
+#pragma unroll
+    for (int y = 0; y < BJ2; ++y)
+#pragma unroll
+        for (int c = 0; c < BJ2; ++c) o[c] = fmaf(f[y], sq[y * BJ2 + c], o[c]);
+    // the F_Q term: rows of F inside the pair-block (F holds I + F)
+    const int bj = row / BJ;
+    const int lr = bj == Ia ? row - Ia * BJ : (bj == Ja ? BJ + row - Ja * BJ : -1);
+    if (lr >= 0) {
+#pragma unroll
+        for (int c = 0; c < BJ2; ++c) o[c] += sq[lr * BJ2 + c];
+    }
+    *reinterpret_cast<float4*>(fr + Ia * BJ) = make_float4(o[0], o[1], o[2], o[3]);
+    *reinterpret_cast<float4*>(fr + Ia * BJ + 4) = make_float4(o[4], o[5], o[6], o[7]);
+    *reinterpret_cast<float4*>(fr + Ja * BJ) = make_float4(o[8], o[9], o[10], o[11]);
+    *reinterpret_cast<float4*>(fr + Ja * BJ + 4) = make_float4(o[12], o[13], o[14], o[15]);
+    __syncwarp(half);   // every lane has read sq before the next item stages its F_Q
+}
+
 __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
     __shared__ int s_sweep[kGbMaxModes], s_round[kGbMaxModes], s_done[kGbMaxModes], s_base[kGbMaxModes];
+    __shared__ int s_gr[kGbMaxModes];   // rounds run: the parity of Q and act
+    __shared__ int s_fr[kGbMaxModes];   // round whose F update is pending (-1: none) ...
+    __shared__ int s_fp[kGbMaxModes];   // ... and its buffer parity
     __shared__ int s_pa[kGbMaxModes + 1], s_pt[kGbMaxModes + 1], s_pf[kGbMaxModes + 1];
     __shared__ int s_live;
+    __shared__ __align__(16) float s_fq[kGbThreads / 16][BJ2SQ];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nwarp_cta = kGbThreads / 32;
-    const int gwarp = blockIdx.x * nwarp_cta + warp, nwarps = gridDim.x * nwarp_cta;
+    const int slot = warp * gridDim.x + blockIdx.x, nwarps = gridDim.x * nwarp_cta;
+    const int h = lane >> 4, l16 = lane & 15;
+    const unsigned int half = 0xffffu << (lane & 16);
+    float* sq = s_fq[warp * 2 + h];
     const int nm = A.nm;
+    unsigned int epoch = 0;
+    auto barrier = [&]() { return count_barrier(A.bar, ++epoch * gridDim.x); };
+    // half-item fh of the pending F updates (decoded over the matrices with one pending)
+    auto f_item = [&](int fh) {
+        int j = 0;
+        while (j < nm - 1 && (s_pf[j + 1] <= fh || s_fr[j] < 0)) ++j;
+        const GbMode& J = A.m[j];
+        const int rest = fh - s_pf[j], groups = J.K / BJ2;
+        const int a = rest / groups, g = rest - a * groups;
+        if (!J.act[s_fp[j] * J.nb + a]) return;   // uniform over the half-warp
+        gb_f_rows(J, s_fr[j], J.Q + (int64_t)s_fp[j] * J.nb * BJ2SQ, a, g, l16, half, sq);
+    };
 
     // initial state: D from diag(H), E from the off-diagonal of H, F = 0, counters 0
     for (int j = 0; j < nm; ++j) {
@@ -855,24 +922,28 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
         s_round[tid] = 0;
         s_done[tid] = 0;
         s_base[tid] = A.m[tid].st->sweeps;
+        s_gr[tid] = 0;
+        s_fr[tid] = -1;
+        s_fp[tid] = 0;
     }
-    bool ok = group_barrier(A.bar, gridDim.x);
+    bool ok = barrier();
 
     while (ok) {
-        // this round's work: prefix counts over the live matrices (same in every CTA)
+        // this round's work: prefix counts over the live matrices and the pending F updates
+        // (same in every CTA)
         if (tid == 0) {
             int pa = 0, pt = 0, pf = 0, live = 0;
             for (int j = 0; j < nm; ++j) {
                 s_pa[j] = pa;
                 s_pt[j] = pt;
                 s_pf[j] = pf;
+                const GbMode& J = A.m[j];
                 if (!s_done[j]) {
-                    const GbMode& J = A.m[j];
                     pa += J.nb;
                     pt += J.nb * (J.nb - 1) / 2;
-                    pf += J.nb * (J.K / BJ2);
                     live = 1;
                 }
+                if (s_fr[j] >= 0) pf += J.nb * (J.K / BJ2);
             }
             s_pa[nm] = pa;
             s_pt[nm] = pt;
@@ -882,12 +953,19 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
         __syncthreads();
         if (!s_live) break;
 
-        // ---- phase A: inner sweeps, a warp per pair-block
-        for (int item = gwarp; item < s_pa[nm]; item += nwarps) {
+        // ---- phase A: inner sweeps, a warp per pair-block; the previous round's F update on
+        // the other warps
+        const int nA = s_pa[nm], nF = s_pf[nm];
+        for (int item = slot; item < nA + (nF + 1) / 2; item += nwarps) {
+            if (item >= nA) {
+                const int fh = 2 * (item - nA) + h;
+                if (fh < nF) f_item(fh);
+                continue;
+            }
             int j = 0;
             while (j < nm - 1 && (s_pa[j + 1] <= item || s_done[j])) ++j;
             const GbMode& J = A.m[j];
-            const int a = item - s_pa[j], t = s_round[j];
+            const int a = item - s_pa[j], t = s_round[j], par = s_gr[j] & 1;
             const Crit qualifies{J.floor, J.tau, J.tol2};
             int I, Jb;
             rr_pair_e(t, a, J.m, I, Jb);
@@ -907,7 +985,7 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
             unsigned int nrot = t == 0 ? inner_sweep<true>(x, d, I, Jb, J.k, qualifies)
                                        : inner_sweep<false>(x, d, I, Jb, J.k, qualifies);
             for (int o = 16; o; o >>= 1) nrot += __shfl_xor_sync(0xffffffffu, nrot, o);
-            float* Qa = J.Q + (int64_t)a * BJ2SQ;
+            float* Qa = J.Q + ((int64_t)par * J.nb + a) * BJ2SQ;
             if (lane < BJ2) {
 #pragma unroll
                 for (int r = 0; r < BJ2; ++r) J.E[(int64_t)bj_index(I, Jb, r) * J.ldE + gi] = x[r];
@@ -917,12 +995,13 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                 for (int r = 0; r < BJ2; ++r) Qa[r * BJ2 + pos] = x[r];   // F_Q; Q = I + F_Q
             }
             if (lane == 0) {
-                J.act[a] = nrot > 0;
+                J.act[par * J.nb + a] = nrot > 0;
                 if (nrot) atomicAdd(&J.cnt[s_sweep[j] & 1], nrot);
             }
             __syncwarp();
         }
-        if (!(ok = group_barrier(A.bar, gridDim.x))) break;
+        if (!(ok = barrier())) break;
+        if (tid < nm) s_fr[tid] = -1;   // the pending F updates are done
 
         // ---- sweep ends: every CTA reads the finished sweep's count (stable in this phase)
         if (tid < nm && !s_done[tid]) {
@@ -944,30 +1023,31 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
         }
         __syncthreads();
 
-        // ---- phase B: tiles (two per warp, a half-warp each) and F rows
+        // ---- phase B: off-diagonal tiles, two per warp (a half-warp each)
         {
-            const int h = lane >> 4, l16 = lane & 15;
             const int r0 = l16 >> 1, c0 = (l16 & 1) * BJ;
             const int ntile = s_pt[nm];
-            for (int task0 = 2 * gwarp; task0 < ntile; task0 += 2 * nwarps) {
+            for (int task0 = 2 * slot; task0 < ntile; task0 += 2 * nwarps) {
                 const int task = task0 + h;
                 const bool live = task < ntile;
                 const int tt = live ? task : task0;
                 int j = 0;
                 while (j < nm - 1 && (s_pt[j + 1] <= tt || s_done[j] == 1)) ++j;
                 const GbMode& J = A.m[j];
+                const int par = s_gr[j] & 1;
+                const int* act = J.act + par * J.nb;
                 // tile index -> (a, b), a < b: row a has nb - 1 - a tiles
                 int rem = tt - s_pt[j], a = 0;
                 while (a < J.nb - 1 && rem >= J.nb - 1 - a) { rem -= J.nb - 1 - a; ++a; }
                 const int b = a + 1 + rem;
-                const bool need = live && (J.act[a] | J.act[b]);
+                const bool need = live && (act[a] | act[b]);
                 if (!__any_sync(0xffffffffu, need)) continue;
                 const int t = s_round[j];
                 int Ia, Ja, Ib, Jb2;
                 rr_pair_e(t, a, J.m, Ia, Ja);
                 rr_pair_e(t, b, J.m, Ib, Jb2);
-                const float* Qa = J.Q + (int64_t)a * BJ2SQ;
-                const float* Qb = J.Q + (int64_t)b * BJ2SQ;
+                const float* Qa = J.Q + ((int64_t)par * J.nb + a) * BJ2SQ;
+                const float* Qb = J.Q + ((int64_t)par * J.nb + b) * BJ2SQ;
                 float* E = J.E;
                 const int ldE = J.ldE;
                 const int colb = c0 ? Jb2 * BJ : Ib * BJ;
@@ -1019,67 +1099,35 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                 }
                 __syncwarp();
             }
-            // F <- F + F_Q + F F_Q: a half-warp per (pair-block, group of 16 rows)
-            const int nhw = nwarps * 2, ghw = gwarp * 2 + h;
-            const unsigned int half = 0xffffu << (lane & 16);
-            const int x = l16;
-            for (int item = ghw; item < s_pf[nm]; item += nhw) {
-                int j = 0;
-                while (j < nm - 1 && (s_pf[j + 1] <= item || s_done[j] == 1)) ++j;
-                const GbMode& J = A.m[j];
-                const int rest = item - s_pf[j], groups = J.K / BJ2;
-                const int a = rest / groups, g = rest - a * groups;
-                if (!J.act[a]) continue;   // uniform over the half-warp
-                int Ia, Ja;
-                rr_pair_e(s_round[j], a, J.m, Ia, Ja);
-                const float* fq = J.Q + (int64_t)a * BJ2SQ;
-                float fcol[BJ2];
-#pragma unroll
-                for (int y = 0; y < BJ2; ++y) fcol[y] = fq[y * BJ2 + x];
-                // two rows at a time, their loads issued together
-                for (int jl = 0; jl < BJ2; jl += 2) {
-                    float fv[2][BJ2], acc[2];
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const float* row = J.F + (int64_t)(g * BJ2 + jl + q) * J.K;
-                        const float4 f0 = *reinterpret_cast<const float4*>(row + Ia * BJ);
-                        const float4 f1 = *reinterpret_cast<const float4*>(row + Ia * BJ + 4);
-                        const float4 f2 = *reinterpret_cast<const float4*>(row + Ja * BJ);
-                        const float4 f3 = *reinterpret_cast<const float4*>(row + Ja * BJ + 4);
-                        fv[q][0] = f0.x; fv[q][1] = f0.y; fv[q][2] = f0.z; fv[q][3] = f0.w;
-                        fv[q][4] = f1.x; fv[q][5] = f1.y; fv[q][6] = f1.z; fv[q][7] = f1.w;
-                        fv[q][8] = f2.x; fv[q][9] = f2.y; fv[q][10] = f2.z; fv[q][11] = f2.w;
-                        fv[q][12] = f3.x; fv[q][13] = f3.y; fv[q][14] = f3.z; fv[q][15] = f3.w;
-                        acc[q] = row[bj_index(Ia, Ja, x)];
-                    }
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int jr = g * BJ2 + jl + q;
-#pragma unroll
-                        for (int y = 0; y < BJ2; ++y) acc[q] = fmaf(fv[q][y], fcol[y], acc[q]);
-                        const int bj = jr / BJ;
-                        if (bj == Ia) acc[q] += fq[(jr - Ia * BJ) * BJ2 + x];
-                        else if (bj == Ja) acc[q] += fq[(BJ + jr - Ja * BJ) * BJ2 + x];
-                    }
-                    __syncwarp(half);
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) J.F[(int64_t)(g * BJ2 + jl + q) * J.K + bj_index(Ia, Ja, x)] = acc[q];
-                }
-            }
         }
-        // matrices that finished at this sweep end take no further part (after every warp of
-        // this CTA has finished decoding this round's items)
+        // this round's F update is pending for every matrix that ran it; matrices that finished
+        // at this sweep end take no further part (after every warp of this CTA has finished
+        // decoding this round's items)
         __syncthreads();
-        if (tid < nm && s_done[tid] >= 2) s_done[tid] = 1;
-        if (!(ok = group_barrier(A.bar, gridDim.x))) break;
+        if (tid < nm && s_done[tid] != 1) {
+            s_fr[tid] = s_round[tid];
+            s_fp[tid] = s_gr[tid] & 1;
+            if (s_done[tid] >= 2) s_done[tid] = 1;
+        }
+        if (!(ok = barrier())) break;
         // next round
         if (tid < nm && !s_done[tid]) {
+            ++s_gr[tid];
             if (++s_round[tid] == A.m[tid].m - 1) {
                 s_round[tid] = 0;
                 ++s_sweep[tid];
             }
         }
         __syncthreads();
+    }
+    // the last round's F update (the prefix counts of the exit pass name the pending matrices)
+    if (ok) {
+        const int nF = s_pf[nm];
+        for (int item = slot; item < (nF + 1) / 2; item += nwarps) {
+            const int fh = 2 * item + h;
+            if (fh < nF) f_item(fh);
+        }
+        ok = barrier();
     }
     // results (also after a failed barrier, so the host sees the flag and the partial state)
     const bool timed_out = !ok;
@@ -1191,7 +1239,8 @@ cudaError_t launch_jacobi_gblk(const DfJob* jobs, int njobs, int max_sweeps, int
         const int nm = std::min(kGbMaxModes, njobs - j0);
         std::vector<GbMode> hm(nm);
         std::vector<size_t> off(nm);
-        size_t total = 256;   // barrier status first
+        const size_t st_bytes = (sizeof(DevStatus) + 255) / 256 * 256;
+        size_t total = st_bytes;   // barrier status first
         auto carve = [&](size_t bytes) {
             const size_t o = total;
             total += (bytes + 255) / 256 * 256;
@@ -1206,7 +1255,7 @@ cudaError_t launch_jacobi_gblk(const DfJob* jobs, int njobs, int max_sweeps, int
             if (m < 2) m = 2;
             const int K = m * BJ, ldE = K + 4, nb = m / 2;
             of[i] = Offs{carve(sizeof(DF) * (size_t)K), carve(4 * (size_t)K * ldE), carve(4 * (size_t)K * K),
-                         carve(4 * (size_t)nb * BJ2SQ), carve(4 * (size_t)nb), carve(8)};
+                         carve(2 * 4 * (size_t)nb * BJ2SQ), carve(2 * 4 * (size_t)nb), carve(8)};
             hm[i] = GbMode{J.H, J.outD, J.outF, J.st, J.ldd, J.k, J.add_identity,
                            (float)J.abs_floor, (float)J.tau, (float)(J.tol * J.tol), K, ldE, nb, m,
                            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -1223,7 +1272,7 @@ cudaError_t launch_jacobi_gblk(const DfJob* jobs, int njobs, int max_sweeps, int
             hm[i].act = reinterpret_cast<int*>(ws + of[i].act);
             hm[i].cnt = reinterpret_cast<unsigned int*>(ws + of[i].cnt);
         }
-        e = cudaMemsetAsync(ws, 0, 256, st);
+        e = cudaMemsetAsync(ws, 0, st_bytes, st);
         if (e == cudaSuccess)
             e = upload_h2d(ws + modes_at, hm.data(), sizeof(GbMode) * nm, st);
         const size_t smem = 0;

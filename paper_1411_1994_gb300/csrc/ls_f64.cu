@@ -514,119 +514,181 @@ __global__ void __launch_bounds__(256) k_jacobi_multi(JacobiArgs A) {
     }
 }
 
+// doubles order like these integer keys (sign-adjusted bit patterns)
+__device__ __forceinline__ unsigned long long order_key(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+// the double whose key this is
+__device__ __forceinline__ double key_value(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
 // ---------------------------------------------------------------------------
 // pivoted Cholesky of up to three PSD matrices at once (cooperative grid,
 // CTAs split between the jobs): G P = L L^T with greedy diagonal pivoting,
-// stopped when the trace of the Schur complement drops below delta. One group
-// barrier per step: every CTA reduces the per-CTA (max, argmax, sum)
-// candidates of the residual diagonal, stages row p of L in shared memory,
-// computes its rows of the new column (one warp per row) and publishes the
-// candidates of the updated diagonal (double-buffered by step parity).
+// stopped when the trace of the Schur complement drops below delta. Each CTA
+// owns a contiguous range of rows and keeps, in shared memory, their residual
+// diagonal and their entries of L in the first kc columns (the global copy of
+// L is written as well: other CTAs read row p from it, and it is the output).
+// One step:
+//   1. warp 0 reduces the per-CTA (max, argmax, sum) candidates of the
+//      residual diagonal (the maximum compared as integer keys, ties to the
+//      smaller index; the sum in a fixed order, so every CTA decides alike);
+//   2. all threads load row p of L and column p of G into shared memory;
+//   3. the other warps form the dot products of the new column, four rows a
+//      warp, while warp 0 takes 1 / sqrt(d_p);
+//   4. a thread per row scales its entry, updates the residual diagonal, and
+//      warp 0 publishes the CTA's candidate (double-buffered by step parity);
+//   5. the job's CTAs meet at a counting barrier.
+// FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU, so
+// the form keeps every scalar FP64 operation (reductions, the square root,
+// comparisons) on one warp instead of repeating it in each.
 // ---------------------------------------------------------------------------
 struct PcholMode {
     const double* G; double* L; double* d; double* cand; int* piv; DevStatus* st; int C; int kmax; int cta0;
-    int ncta; double delta;
+    int ncta; int kc; double delta;
 };
 struct PcholArgs {
     const PcholMode* m; int nmodes;
 };
 
-// (max, smallest index among equal maxima) is a total order, so the butterfly
-// leaves the same candidate in every lane; the sum is taken in a fixed order.
-__device__ __forceinline__ bool cand_better(double m2, int i2, double m1, int i1) {
-    return m2 > m1 || (m2 == m1 && i2 >= 0 && (i1 < 0 || i2 < i1));
-}
-// CTA-wide (max, argmax, sum); every thread receives the result
-__device__ void cta_reduce_cand(double& mx, int& ix, double& sm, double* s_m, int* s_i, double* s_s) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+// (key, index) maximum over a warp, ties to the smaller index (>= 0); every
+// lane receives the result
+__device__ __forceinline__ void warp_argmax(unsigned long long& key, int& ix) {
     for (int o = 16; o; o >>= 1) {
-        const double m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
         const int i2 = __shfl_xor_sync(0xffffffffu, ix, o);
-        if (cand_better(m2, i2, mx, ix)) { mx = m2; ix = i2; }
-        sm += __shfl_xor_sync(0xffffffffu, sm, o);
-    }
-    __syncthreads();   // earlier readers of the scratch are done
-    if (lane == 0) { s_m[warp] = mx; s_i[warp] = ix; s_s[warp] = sm; }
-    __syncthreads();
-    mx = -1.0;
-    ix = -1;
-    sm = 0.0;
-    for (int w = 0; w < nw; ++w) {
-        if (cand_better(s_m[w], s_i[w], mx, ix)) { mx = s_m[w]; ix = s_i[w]; }
-        sm += s_s[w];
+        if (k2 > key || (k2 == key && i2 >= 0 && (ix < 0 || i2 < ix))) { key = k2; ix = i2; }
     }
 }
+
+constexpr int kPcRows = 4;   // rows of the new column a warp forms at once
 
 __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
     const PcholMode J = A.m[find_job(A.m, A.nmodes)];
     const int lb = blockIdx.x - J.cta0, nb = J.ncta;
-    const int C = J.C;
-    extern __shared__ double lrow[];            // row p of L, kmax entries
-    __shared__ double s_m[8], s_s[8];
-    __shared__ int s_i[8];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int C = J.C, kc = J.kc;
     // rows of this CTA: [r0, r1)
     const int per = (C + nb - 1) / nb;
-    const int r0 = min(C, lb * per), r1 = min(C, r0 + per);
-    // this CTA's (max, argmax, sum) of the residual diagonal, published by step parity
+    const int r0 = min(C, lb * per), r1 = min(C, r0 + per), nr = r1 - r0;
+    extern __shared__ double smd[];
+    double* lrow = smd;                 // [kmax] row p of L
+    double* ds = lrow + J.kmax;         // [per] residual diagonal of the own rows
+    double* gp = ds + per;              // [per] G[own rows, p]
+    double* sacc = gp + per;            // [per] dot products of the step
+    double* Ls = sacc + per;            // [per][kc] own rows of L, columns < kc
+    __shared__ double s_dmax, s_sum, s_inv;
+    __shared__ int s_p;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    // warp 0: this CTA's (max, argmax, sum) of the residual diagonal, published by step parity
     auto publish = [&](int parity) {
-        double mx = -1.0, sm = 0.0;
+        unsigned long long key = order_key(-1.0);
         int ix = -1;
-        for (int j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
-            const double v = __ldcg(J.d + j);
+        double sm = 0.0;
+        for (int jl = lane; jl < nr; jl += 32) {
+            const double v = ds[jl];
+            const unsigned long long kv = order_key(v);
             sm += v;
-            if (v > mx) { mx = v; ix = j; }
+            if (kv > key) { key = kv; ix = r0 + jl; }
         }
-        cta_reduce_cand(mx, ix, sm, s_m, s_i, s_s);
-        if (threadIdx.x == 0) {
+        warp_argmax(key, ix);
+        for (int o = 16; o; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+        if (lane == 0) {
             double* c = J.cand + ((int64_t)parity * nb + lb) * 3;
-            __stcg(c, mx);
+            __stcg(c, key_value(key));
             __stcg(c + 1, (double)ix);
             __stcg(c + 2, sm);
         }
     };
-    for (int j = r0 + threadIdx.x; j < r1; j += blockDim.x) __stcg(J.d + j, __ldcg(J.G + (int64_t)j * C + j));
+    for (int jl = tid; jl < nr; jl += blockDim.x) ds[jl] = __ldcg(J.G + (int64_t)(r0 + jl) * C + r0 + jl);
     __syncthreads();
-    publish(0);
-    if (!group_barrier(J.st, nb)) return;
+    if (warp == 0) publish(0);
+    unsigned int epoch = 1;
+    if (!count_barrier(J.st, epoch * nb)) return;
     int k = 0;
-    double s_sum = 0.0;
     for (;; ++k) {
         const int par = k & 1;
-        // every CTA reduces the candidates of all CTAs of the job
-        double dmax = -1.0, sum = 0.0;
-        int p = -1;
-        for (int c = threadIdx.x; c < nb; c += blockDim.x) {
-            const double* cc = J.cand + ((int64_t)par * nb + c) * 3;
-            const double m2 = __ldcg(cc);
-            const int i2 = (int)__ldcg(cc + 1);
-            if (cand_better(m2, i2, dmax, p)) { dmax = m2; p = i2; }
-            sum += __ldcg(cc + 2);
-        }
-        cta_reduce_cand(dmax, p, sum, s_m, s_i, s_s);
-        s_sum = sum;
-        // stop when the residual trace is small enough, or at kmax columns
-        if (k >= J.kmax || !(s_sum > J.delta) || p < 0 || !(dmax > 0.0)) break;
-        for (int t = threadIdx.x; t < k; t += blockDim.x) lrow[t] = __ldcg(J.L + (int64_t)p * J.kmax + t);
-        __syncthreads();
-        const double inv = 1.0 / sqrt(dmax);
-        for (int j = r0 + warp; j < r1; j += nw) {
-            double acc = 0.0;
-            for (int t = lane; t < k; t += 32) acc = fma(__ldcg(J.L + (int64_t)j * J.kmax + t), lrow[t], acc);
-            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        // 1. warp 0 reduces the candidates of all CTAs of the job
+        if (warp == 0) {
+            unsigned long long key = order_key(-1.0);
+            int p = -1;
+            double sum = 0.0;
+            for (int c = lane; c < nb; c += 32) {
+                const double* cc = J.cand + ((int64_t)par * nb + c) * 3;
+                const unsigned long long k2 = order_key(__ldcg(cc));
+                const int i2 = (int)__ldcg(cc + 1);
+                if (k2 > key || (k2 == key && i2 >= 0 && (p < 0 || i2 < p))) { key = k2; p = i2; }
+                sum += __ldcg(cc + 2);
+            }
+            warp_argmax(key, p);
+            for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
             if (lane == 0) {
-                const double l = (__ldcg(J.G + (int64_t)j * C + p) - acc) * inv;
-                __stcg(J.L + (int64_t)j * J.kmax + k, l);
-                const double dn = (j == p) ? 0.0 : fmax(__ldcg(J.d + j) - l * l, 0.0);
-                __stcg(J.d + j, dn);
+                s_p = p;
+                s_dmax = key_value(key);
+                s_sum = sum;
             }
         }
-        if (lb == 0 && threadIdx.x == 0) J.piv[k] = p;
         __syncthreads();
-        publish(par ^ 1);
-        if (!group_barrier(J.st, nb)) return;
+        const int p = s_p;
+        const double dmax = s_dmax;
+        // stop when the residual trace is small enough, or at kmax columns
+        if (k >= J.kmax || !(s_sum > J.delta) || p < 0 || !(dmax > 0.0)) break;
+        // 2. row p of L (written by its owner in earlier steps) and column p of G
+        for (int t = tid; t < k; t += blockDim.x) lrow[t] = __ldcg(J.L + (int64_t)p * J.kmax + t);
+        for (int jl = tid; jl < nr; jl += blockDim.x) gp[jl] = __ldcg(J.G + (int64_t)(r0 + jl) * C + p);
+        __syncthreads();
+        // 3. dot products, kPcRows rows a warp (warp 0 last), and 1 / sqrt(d_p) on warp 0
+        if (tid == 0) s_inv = 1.0 / sqrt(dmax);
+        const int ngroups = (nr + kPcRows - 1) / kPcRows;
+        const int ks = min(k, kc);
+        for (int gi = (warp + nw - 1) % nw; gi < ngroups; gi += nw) {
+            int rl[kPcRows];
+#pragma unroll
+            for (int q = 0; q < kPcRows; ++q) rl[q] = min(gi * kPcRows + q, nr - 1);
+            double acc[kPcRows];
+#pragma unroll
+            for (int q = 0; q < kPcRows; ++q) acc[q] = 0.0;
+            int t = lane;
+            for (; t < ks; t += 32) {
+                const double lv = lrow[t];
+#pragma unroll
+                for (int q = 0; q < kPcRows; ++q) acc[q] = fma(Ls[(size_t)rl[q] * kc + t], lv, acc[q]);
+            }
+            for (; t < k; t += 32) {
+                const double lv = lrow[t];
+#pragma unroll
+                for (int q = 0; q < kPcRows; ++q)
+                    acc[q] = fma(__ldcg(J.L + (int64_t)(r0 + rl[q]) * J.kmax + t), lv, acc[q]);
+            }
+            // transposed butterfly: 6 additions for the four sums (lane 8 q holds row q)
+            const bool hi = lane & 16;
+            double v0 = (hi ? acc[2] : acc[0]) + __shfl_xor_sync(0xffffffffu, hi ? acc[0] : acc[2], 16);
+            double v1 = (hi ? acc[3] : acc[1]) + __shfl_xor_sync(0xffffffffu, hi ? acc[1] : acc[3], 16);
+            const bool b3 = lane & 8;
+            double w = (b3 ? v1 : v0) + __shfl_xor_sync(0xffffffffu, b3 ? v0 : v1, 8);
+            for (int o = 4; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            const int q = lane >> 3;
+            if ((lane & 7) == 0 && gi * kPcRows + q < nr) sacc[gi * kPcRows + q] = w;
+        }
+        __syncthreads();
+        // 4. the new column of L and the residual diagonal
+        const double inv = s_inv;
+        for (int jl = tid; jl < nr; jl += blockDim.x) {
+            const int j = r0 + jl;
+            const double l = (gp[jl] - sacc[jl]) * inv;
+            if (k < kc) Ls[(size_t)jl * kc + k] = l;
+            __stcg(J.L + (int64_t)j * J.kmax + k, l);
+            ds[jl] = (j == p) ? 0.0 : fmax(ds[jl] - l * l, 0.0);
+        }
+        if (lb == 0 && tid == 0) J.piv[k] = p;
+        __syncthreads();
+        if (warp == 0) publish(par ^ 1);
+        // 5. the job's CTAs meet
+        if (!count_barrier(J.st, ++epoch * nb)) return;
     }
-    if (lb == 0 && threadIdx.x == 0) {
+    for (int jl = tid; jl < nr; jl += blockDim.x) J.d[r0 + jl] = ds[jl];
+    if (lb == 0 && tid == 0) {
         J.st->sweeps = k;                          // columns of L
         J.cand[kPcholCand - 1] = s_sum;            // residual trace: energy outside span(L)
     }
@@ -639,10 +701,6 @@ __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
 // shuffle scan), so that neither the O(C^2) comparisons nor the C additions queue
 // on one SMSP's FP64 unit.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long order_key(double v) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
 struct SelJob {
     const double* G; int C; int forced; const double* extra; int32_t* perm; double* lam; double* isl; double* out;
     int64_t dstride; double resolution;
@@ -1100,33 +1158,43 @@ cudaError_t launch_sort_select(int n, const SortSelectJob* jobs, double eps, dou
 
 cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cudaStream_t st) {
     if (njobs < 1) return cudaSuccess;
-    size_t smem = 0;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        optin = 48 * 1024;
+    const int64_t budget = std::max<int64_t>(0, optin - 1024);   // the kernel's static variables take a few bytes
     std::vector<int64_t> want(njobs);
-    for (int m = 0; m < njobs; ++m) {
-        smem = std::max(smem, (size_t)jobs[m].kmax * sizeof(double));
-        // a warp per row and step; the candidate scratch holds 1024 CTAs per job
-        want[m] = std::min<int64_t>(1024, std::max<int64_t>(1, (jobs[m].C + 7) / 8));
-    }
-    if (smem > 48 * 1024) {
-        cudaError_t e = grow_smem((const void*)k_pchol_multi, smem);
-        if (e != cudaSuccess) return e;
-    }
-    int per_sm = 0;
-    if (blocks_per_sm((const void*)k_pchol_multi, 256, smem, &per_sm) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    const int64_t resident = (int64_t)per_sm * num_sms;
-    const int64_t cap = std::min<int64_t>(resident, std::max<int64_t>(num_sms, njobs));
-    for (int j0 = 0; j0 < njobs; j0 += (int)resident) {
-        const int nj = (int)std::min<int64_t>(resident, njobs - j0);
+    // a warp per row and step; the candidate scratch holds 1024 CTAs per job
+    for (int m = 0; m < njobs; ++m) want[m] = std::min<int64_t>(1024, std::max<int64_t>(1, (jobs[m].C + 7) / 8));
+    // one CTA per SM (the own rows of L fill its shared memory): at most num_sms jobs a launch
+    for (int j0 = 0, nj = 0; j0 < njobs; j0 += nj) {
+        nj = std::min(num_sms, njobs - j0);
         std::vector<int64_t> w(want.begin() + j0, want.begin() + j0 + nj);
-        std::vector<int> nc = split_ctas(w, cap);
+        std::vector<int> nc = split_ctas(w, num_sms);
         std::vector<PcholMode> hm(nj);
+        size_t smem = 0;
         int cta = 0;
         for (int m = 0; m < nj; ++m) {
             const PcholJob& J = jobs[j0 + m];
-            hm[m] = PcholMode{J.G, J.L, J.d, J.cand, J.piv, J.st, (int)J.C, J.kmax, cta, nc[m], J.delta};
+            const int64_t per = (J.C + nc[m] - 1) / nc[m];
+            const int64_t fixed = 8 * ((int64_t)J.kmax + 3 * per);   // row p of L, d, G[., p], the dots
+            // columns of the own rows of L held in shared memory (the rest is read from L2)
+            const int64_t kc = std::min<int64_t>(J.kmax, std::max<int64_t>(0, (budget - fixed) / (8 * per)));
+            smem = std::max(smem, (size_t)(fixed + 8 * per * kc));
+            hm[m] = PcholMode{J.G, J.L, J.d, J.cand, J.piv, J.st, (int)J.C, J.kmax, cta, nc[m], (int)kc, J.delta};
             cta += nc[m];
+            cudaError_t e = cudaMemsetAsync(&J.st->arrive, 0, sizeof(unsigned int), st);
+            if (e != cudaSuccess) return e;
         }
+        if ((int64_t)smem > budget) return cudaErrorInvalidValue;   // row p of L alone exceeds the shared memory
+        if (smem > 48 * 1024) {
+            cudaError_t e = grow_smem((const void*)k_pchol_multi, smem);
+            if (e != cudaSuccess) return e;
+        }
+        int per_sm = 0;
+        if (blocks_per_sm((const void*)k_pchol_multi, 256, smem, &per_sm) != cudaSuccess || per_sm < 1 ||
+            (int64_t)per_sm * num_sms < cta)
+            return cudaErrorCooperativeLaunchTooLarge;
         PcholMode* dm = nullptr;
         cudaError_t e = cudaMallocAsync(&dm, sizeof(PcholMode) * nj, st);
         if (e != cudaSuccess) return e;
