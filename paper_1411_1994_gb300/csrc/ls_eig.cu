@@ -834,6 +834,7 @@ struct GbMode {
 struct GbArgs {
     const GbMode* m; int nm; int max_sweeps; DevStatus* bar;
 };
+static_assert(sizeof(GbMode) % sizeof(int) == 0 && alignof(GbMode) <= 16, "descriptors are copied as words");
 
 // F <- F + F_Q + F F_Q on the 16 columns of pair-block a of round `round` for
 // the rows 16 g .. 16 g + 15: a half-warp, lane x owns row 16 g + x; the
@@ -858,16 +859,30 @@ __device__ __forceinline__ void gb_f_rows(const GbMode& J, int round, const floa
     float o[BJ2];
 #pragma unroll
     for (int c = 0; c < BJ2; ++c) o[c] = f[c];
+    // F_Q rows as float4 broadcasts: a quarter of the shared-memory reads of scalar ones
+    const float4* sq4 = reinterpret_cast<const float4*>(sq);
 #pragma unroll
     for (int y = 0; y < BJ2; ++y)
 #pragma unroll
-        for (int c = 0; c < BJ2; ++c) o[c] = fmaf(f[y], sq[y * BJ2 + c], o[c]);
+        for (int c4 = 0; c4 < BJ2 / 4; ++c4) {
+            const float4 q = sq4[y * (BJ2 / 4) + c4];
+            o[4 * c4] = fmaf(f[y], q.x, o[4 * c4]);
+            o[4 * c4 + 1] = fmaf(f[y], q.y, o[4 * c4 + 1]);
+            o[4 * c4 + 2] = fmaf(f[y], q.z, o[4 * c4 + 2]);
+            o[4 * c4 + 3] = fmaf(f[y], q.w, o[4 * c4 + 3]);
+        }
     // the F_Q term: rows of F inside the pair-block (F holds I + F)
     const int bj = row / BJ;
     const int lr = bj == Ia ? row - Ia * BJ : (bj == Ja ? BJ + row - Ja * BJ : -1);
     if (lr >= 0) {
 #pragma unroll
-        for (int c = 0; c < BJ2; ++c) o[c] += sq[lr * BJ2 + c];
+        for (int c4 = 0; c4 < BJ2 / 4; ++c4) {
+            const float4 q = sq4[lr * (BJ2 / 4) + c4];
+            o[4 * c4] += q.x;
+            o[4 * c4 + 1] += q.y;
+            o[4 * c4 + 2] += q.z;
+            o[4 * c4 + 3] += q.w;
+        }
     }
     *reinterpret_cast<float4*>(fr + Ia * BJ) = make_float4(o[0], o[1], o[2], o[3]);
     *reinterpret_cast<float4*>(fr + Ia * BJ + 4) = make_float4(o[4], o[5], o[6], o[7]);
@@ -883,21 +898,35 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
     __shared__ int s_fp[kGbMaxModes];   // ... and its buffer parity
     __shared__ int s_pa[kGbMaxModes + 1], s_pt[kGbMaxModes + 1], s_pf[kGbMaxModes + 1];
     __shared__ int s_live;
-    __shared__ __align__(16) float s_fq[kGbThreads / 16][BJ2SQ];
+    // per half-warp: F_Q of an F item (phase A) or E_ab, Q_a, Q_b of a tile (phase B)
+    extern __shared__ __align__(16) float gb_smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nwarp_cta = kGbThreads / 32;
     const int slot = warp * gridDim.x + blockIdx.x, nwarps = gridDim.x * nwarp_cta;
+    // the warps in the order 1, 2, 3, 5, ..., 15, then 0, 4, 8, 12 (those of warp 0's SMSP)
+    const int fslot = ((warp & 3) == 0 ? nwarp_cta - nwarp_cta / 4 + (warp >> 2) : warp - 1 - (warp >> 2)) * gridDim.x +
+                      blockIdx.x;
     const int h = lane >> 4, l16 = lane & 15;
     const unsigned int half = 0xffffu << (lane & 16);
-    float* sq = s_fq[warp * 2 + h];
+    float* sq = gb_smem + (size_t)(warp * 2 + h) * 3 * BJ2SQ;
     const int nm = A.nm;
+    // the job descriptors in shared memory (read in every phase; global reads would miss L1
+    // after each barrier's fence)
+    GbMode* Ms = reinterpret_cast<GbMode*>(gb_smem + (size_t)(kGbThreads / 16) * 3 * BJ2SQ);
+    {
+        const int words = nm * (int)(sizeof(GbMode) / sizeof(int));
+        const int* src = reinterpret_cast<const int*>(A.m);
+        int* dst = reinterpret_cast<int*>(Ms);
+        for (int i = tid; i < words; i += kGbThreads) dst[i] = src[i];
+        __syncthreads();
+    }
     unsigned int epoch = 0;
     auto barrier = [&]() { return count_barrier(A.bar, ++epoch * gridDim.x); };
     // half-item fh of the pending F updates (decoded over the matrices with one pending)
     auto f_item = [&](int fh) {
         int j = 0;
         while (j < nm - 1 && (s_pf[j + 1] <= fh || s_fr[j] < 0)) ++j;
-        const GbMode& J = A.m[j];
+        const GbMode& J = Ms[j];
         const int rest = fh - s_pf[j], groups = J.K / BJ2;
         const int a = rest / groups, g = rest - a * groups;
         if (!J.act[s_fp[j] * J.nb + a]) return;   // uniform over the half-warp
@@ -906,7 +935,7 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
 
     // initial state: D from diag(H), E from the off-diagonal of H, F = 0, counters 0
     for (int j = 0; j < nm; ++j) {
-        const GbMode& J = A.m[j];
+        const GbMode& J = Ms[j];
         const int64_t ne = (int64_t)J.K * J.ldE;
         for (int64_t e = blockIdx.x * (int64_t)kGbThreads + tid; e < ne; e += (int64_t)gridDim.x * kGbThreads) {
             const int r = (int)(e / J.ldE), c = (int)(e - (int64_t)r * J.ldE);
@@ -921,7 +950,7 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
         s_sweep[tid] = 0;
         s_round[tid] = 0;
         s_done[tid] = 0;
-        s_base[tid] = A.m[tid].st->sweeps;
+        s_base[tid] = Ms[tid].st->sweeps;
         s_gr[tid] = 0;
         s_fr[tid] = -1;
         s_fp[tid] = 0;
@@ -937,7 +966,7 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                 s_pa[j] = pa;
                 s_pt[j] = pt;
                 s_pf[j] = pf;
-                const GbMode& J = A.m[j];
+                const GbMode& J = Ms[j];
                 if (!s_done[j]) {
                     pa += J.nb;
                     pt += J.nb * (J.nb - 1) / 2;
@@ -956,15 +985,10 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
         // ---- phase A: inner sweeps, a warp per pair-block; the previous round's F update on
         // the other warps
         const int nA = s_pa[nm], nF = s_pf[nm];
-        for (int item = slot; item < nA + (nF + 1) / 2; item += nwarps) {
-            if (item >= nA) {
-                const int fh = 2 * (item - nA) + h;
-                if (fh < nF) f_item(fh);
-                continue;
-            }
+        for (int item = slot; item < nA; item += nwarps) {
             int j = 0;
             while (j < nm - 1 && (s_pa[j + 1] <= item || s_done[j])) ++j;
-            const GbMode& J = A.m[j];
+            const GbMode& J = Ms[j];
             const int a = item - s_pa[j], t = s_round[j], par = s_gr[j] & 1;
             const Crit qualifies{J.floor, J.tau, J.tol2};
             int I, Jb;
@@ -1000,12 +1024,18 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
             }
             __syncwarp();
         }
+        // the F items, on the warps of the other three SMSPs first (the inner sweeps, on warp 0,
+        // are the round's critical path)
+        for (int fw = fslot; 2 * fw < nF; fw += nwarps) {
+            const int fh = 2 * fw + h;
+            if (fh < nF) f_item(fh);
+        }
         if (!(ok = barrier())) break;
         if (tid < nm) s_fr[tid] = -1;   // the pending F updates are done
 
         // ---- sweep ends: every CTA reads the finished sweep's count (stable in this phase)
         if (tid < nm && !s_done[tid]) {
-            const GbMode& J = A.m[tid];
+            const GbMode& J = Ms[tid];
             if (s_round[tid] == J.m - 2) {
                 const int sw = s_sweep[tid];
                 const unsigned int c = *(volatile unsigned int*)&J.cnt[sw & 1];
@@ -1033,7 +1063,7 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                 const int tt = live ? task : task0;
                 int j = 0;
                 while (j < nm - 1 && (s_pt[j + 1] <= tt || s_done[j] == 1)) ++j;
-                const GbMode& J = A.m[j];
+                const GbMode& J = Ms[j];
                 const int par = s_gr[j] & 1;
                 const int* act = J.act + par * J.nb;
                 // tile index -> (a, b), a < b: row a has nb - 1 - a tiles
@@ -1046,10 +1076,36 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                 int Ia, Ja, Ib, Jb2;
                 rr_pair_e(t, a, J.m, Ia, Ja);
                 rr_pair_e(t, b, J.m, Ib, Jb2);
-                const float* Qa = J.Q + ((int64_t)par * J.nb + a) * BJ2SQ;
-                const float* Qb = J.Q + ((int64_t)par * J.nb + b) * BJ2SQ;
-                float* E = J.E;
-                const int ldE = J.ldE;
+                // the tile's E rows (16 x 16), Q_a and Q_b into shared memory: one round of
+                // independent loads (the grid barrier's fence leaves nothing of them in L1)
+                float* sE = sq;
+                float* sQa = sq + BJ2SQ;
+                float* sQb = sq + 2 * BJ2SQ;
+                {
+                    const float4* qa4 = reinterpret_cast<const float4*>(J.Q + ((int64_t)par * J.nb + a) * BJ2SQ);
+                    const float4* qb4 = reinterpret_cast<const float4*>(J.Q + ((int64_t)par * J.nb + b) * BJ2SQ);
+                    const float* er = J.E + (int64_t)bj_index(Ia, Ja, l16) * J.ldE;
+                    float4 v[12];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        v[q] = qa4[l16 * 4 + q];
+                        v[4 + q] = qb4[l16 * 4 + q];
+                    }
+                    v[8] = *reinterpret_cast<const float4*>(er + Ib * BJ);
+                    v[9] = *reinterpret_cast<const float4*>(er + Ib * BJ + 4);
+                    v[10] = *reinterpret_cast<const float4*>(er + Jb2 * BJ);
+                    v[11] = *reinterpret_cast<const float4*>(er + Jb2 * BJ + 4);
+                    __syncwarp();   // the previous tile's readers of this staging area are done
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        reinterpret_cast<float4*>(sQa)[l16 * 4 + q] = v[q];
+                        reinterpret_cast<float4*>(sQb)[l16 * 4 + q] = v[4 + q];
+                        reinterpret_cast<float4*>(sE)[l16 * 4 + q] = v[8 + q];
+                    }
+                    __syncwarp();
+                }
+                const float* Qa = sQa;
+                const float* Qb = sQb;
                 const int colb = c0 ? Jb2 * BJ : Ib * BJ;
                 float t0[BJ], t1[BJ];
 #pragma unroll
@@ -1058,7 +1114,7 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                 for (int jj = 0; jj < BJ2; ++jj) {
                     const float qa0 = Qa[jj * BJ2 + r0] + (jj == r0 ? 1.f : 0.f);
                     const float qa1 = Qa[jj * BJ2 + r0 + BJ] + (jj == r0 + BJ ? 1.f : 0.f);
-                    const float* xr = E + (int64_t)bj_index(Ia, Ja, jj) * ldE + colb;
+                    const float* xr = sE + jj * BJ2 + c0;
                     const float4 x0 = *reinterpret_cast<const float4*>(xr);
                     const float4 x1 = *reinterpret_cast<const float4*>(xr + 4);
                     const float xv[BJ] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
@@ -1068,6 +1124,8 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                         t1[c] = fmaf(qa1, xv[c], t1[c]);
                     }
                 }
+                float* E = J.E;
+                const int ldE = J.ldE;
                 const int cp = c0 ^ BJ;
                 const int row0 = bj_index(Ia, Ja, r0), row1 = bj_index(Ia, Ja, r0 + BJ);
 #pragma unroll
@@ -1079,10 +1137,15 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                     for (int jj = 0; jj < BJ; ++jj) {
                         const float tv = half_row ? t1[jj] : t0[jj];
                         const float ov = __shfl_xor_sync(0xffffffffu, tv, 1);
+                        const float4* qs4 = reinterpret_cast<const float4*>(Qb + (c0 + jj) * BJ2 + c0);
+                        const float4* qo4 = reinterpret_cast<const float4*>(Qb + (cp + jj) * BJ2 + c0);
+                        const float4 s0 = qs4[0], s1 = qs4[1], o0 = qo4[0], o1 = qo4[1];
+                        const float qsv[BJ] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+                        const float qov[BJ] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
 #pragma unroll
                         for (int c = 0; c < BJ; ++c) {
-                            const float qs = Qb[(c0 + jj) * BJ2 + c0 + c] + ((c0 + jj) == (c0 + c) ? 1.f : 0.f);
-                            const float qo = Qb[(cp + jj) * BJ2 + c0 + c] + ((cp + jj) == (c0 + c) ? 1.f : 0.f);
+                            const float qs = qsv[c] + ((c0 + jj) == (c0 + c) ? 1.f : 0.f);
+                            const float qo = qov[c] + ((cp + jj) == (c0 + c) ? 1.f : 0.f);
                             z[c] = fmaf(tv, qs, fmaf(ov, qo, z[c]));
                         }
                     }
@@ -1113,7 +1176,7 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
         // next round
         if (tid < nm && !s_done[tid]) {
             ++s_gr[tid];
-            if (++s_round[tid] == A.m[tid].m - 1) {
+            if (++s_round[tid] == Ms[tid].m - 1) {
                 s_round[tid] = 0;
                 ++s_sweep[tid];
             }
@@ -1132,7 +1195,7 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
     // results (also after a failed barrier, so the host sees the flag and the partial state)
     const bool timed_out = !ok;
     for (int j = 0; j < nm; ++j) {
-        const GbMode& J = A.m[j];
+        const GbMode& J = Ms[j];
         for (int64_t e = blockIdx.x * (int64_t)kGbThreads + tid; e < (int64_t)J.k * J.k; e += (int64_t)gridDim.x * kGbThreads) {
             const int r = (int)(e / J.k), c = (int)(e - (int64_t)r * J.k);
             J.outF[e] = (double)J.F[(int64_t)r * J.K + c] + ((J.add_identity && r == c) ? 1.0 : 0.0);
@@ -1275,8 +1338,10 @@ cudaError_t launch_jacobi_gblk(const DfJob* jobs, int njobs, int max_sweeps, int
         e = cudaMemsetAsync(ws, 0, st_bytes, st);
         if (e == cudaSuccess)
             e = upload_h2d(ws + modes_at, hm.data(), sizeof(GbMode) * nm, st);
-        const size_t smem = 0;
+        // 96 KB of staging, then the job descriptors
+        const size_t smem = (size_t)(kGbThreads / 16) * 3 * BJ2SQ * sizeof(float) + sizeof(GbMode) * nm;
         int per_sm = 0;
+        if (e == cudaSuccess) e = grow_smem((const void*)k_jacobi_gblk, smem);
         if (e == cudaSuccess) e = blocks_per_sm((const void*)k_jacobi_gblk, kGbThreads, smem, &per_sm);
         if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
         if (e == cudaSuccess) {
