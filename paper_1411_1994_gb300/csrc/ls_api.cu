@@ -1297,6 +1297,93 @@ int eigen_all(std::vector<RedState>& R, ls_ctx* const* ctxs, int n, const std::v
     return LS_OK;
 }
 
+// The grid form of the pivoted Cholesky for the jobs beyond a cluster's shared memory,
+// panel by panel: each launch takes up to kPcholPanel pivots of every unfinished job and
+// leaves the panel's columns in Lp (zero past the last pivot), and the FP64-grade
+// tensor-core product G -= Lp Lp^T turns G into the Schur complement the next panel
+// starts from. The panel kernel reads where to continue from the device, so panels and
+// products queue kPcholGroup at a time with one read-back a group (a job that ended
+// takes no pivots and yields a zero panel). The panel's own updates stay in FP64.
+constexpr int kPcholPanel = 64, kPcholGroup = 4;
+int pchol_grid(ls_ctx* c0, std::vector<PcholJob> jobs, cudaStream_t st) {
+    const int n = (int)jobs.size();
+    if (n == 0) return LS_OK;
+    int* d_rep = nullptr;
+    double* d_lp = nullptr;
+    int64_t lp_total = 0;
+    for (const PcholJob& J : jobs) lp_total += J.C * kPcholPanel;
+    if (cudaMallocAsync(&d_rep, sizeof(int) * 2 * n, st) != cudaSuccess ||
+        cudaMallocAsync(&d_lp, sizeof(double) * lp_total, st) != cudaSuccess) {
+        if (d_rep) cudaFreeAsync(d_rep, st);
+        return fail(c0, LS_ERR_OOM, "rhosvd_reduce: pivoted Cholesky: out of memory");
+    }
+    for (int64_t j = 0, off = 0; j < n; off += jobs[j].C * kPcholPanel, ++j) jobs[j].Lp = d_lp + off;
+    std::vector<int> rep(2 * n), prev(n, 0);
+    std::vector<int> live(n);
+    for (int j = 0; j < n; ++j) live[j] = j;
+    int rc = LS_OK;
+    while (!live.empty() && rc == LS_OK) {
+        std::vector<PcholJob> lj;
+        std::vector<const double*> L;
+        std::vector<int64_t> ld, C;
+        std::vector<int> k0, kb;
+        std::vector<double*> S;
+        std::vector<const int*> skip;
+        for (int j : live) {
+            skip.push_back(&jobs[j].st->done);   // the job ended: its Schur complement is not wanted
+            lj.push_back(jobs[j]);
+            L.push_back(jobs[j].Lp);
+            ld.push_back(kPcholPanel);
+            k0.push_back(0);
+            kb.push_back(kPcholPanel);
+            C.push_back(jobs[j].C);
+            S.push_back(const_cast<double*>(jobs[j].G));
+        }
+        const int m = (int)lj.size();
+        int64_t Cmax = 1;
+        for (const PcholJob& J : lj) Cmax = std::max<int64_t>(Cmax, J.C);
+        // one cluster a matrix where its rows' panel columns fit the cluster's shared memory
+        const bool cl = pchol_cpanel_fits(Cmax, kPcholPanel);
+        for (int g = 0; g < kPcholGroup && rc == LS_OK; ++g) {
+            cudaError_t e;
+            {
+                Scope sc("pchol.panel", st);
+                e = cl ? launch_pchol_cpanel(lj.data(), kPcholPanel, m, d_rep, st)
+                       : launch_pchol_panel(lj.data(), kPcholPanel, m, c0->num_sms, d_rep, st);
+            }
+            if (e != cudaSuccess) {
+                rc = fail(c0, LS_ERR_CUDA, "rhosvd_reduce: pivoted Cholesky panel: %s", cudaGetErrorString(e));
+                break;
+            }
+            Scope sc("pchol.schur", st);
+            std::string err;
+            int r2 = x64_syrk_sub(m, L.data(), ld.data(), k0.data(), kb.data(), C.data(), S.data(),
+                                  &lj[0].st->flag, st, &err, skip.data());
+            if (r2 != LS_OK) rc = fail(c0, r2, "rhosvd_reduce: Schur complement: %s", err.c_str());
+        }
+        if (rc != LS_OK) break;
+        cudaError_t e = cudaMemcpyAsync(rep.data(), d_rep, sizeof(int) * 2 * m, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            rc = fail(c0, LS_ERR_CUDA, "rhosvd_reduce: pivoted Cholesky read-back: %s", cudaGetErrorString(e));
+            break;
+        }
+        count_d2h(sizeof(int) * 2 * m);
+        std::vector<int> next;
+        for (int i = 0; i < m; ++i) {
+            const int j = live[i];
+            // ended, or no progress in a whole group (a failed barrier, whose flag the caller reports)
+            if (rep[2 * i + 1] || rep[2 * i] >= jobs[j].kmax || rep[2 * i] <= prev[j]) continue;
+            prev[j] = rep[2 * i];
+            next.push_back(j);
+        }
+        live.swap(next);
+    }
+    cudaFreeAsync(d_lp, st);
+    cudaFreeAsync(d_rep, st);
+    return rc;
+}
+
 // The reduction of n contexts: per-context phases on each context's stream;
 // the cooperative steps (pivoted Cholesky, Jacobi iteration, the two Cholesky
 // factorisations of CholeskyQR2) of all 3n modes as one launch each on the
@@ -1355,8 +1442,8 @@ int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, l
         std::vector<PcholJob> small, large;
         for (const PcholJob& J : pj) (pchol_cluster_size((int)J.C, J.kmax) > 0 ? small : large).push_back(J);
         cudaError_t e = launch_pchol_cluster(small.data(), (int)small.size(), s0);
-        if (e == cudaSuccess) e = launch_pchol_multi(large.data(), (int)large.size(), c0->num_sms, s0);
         if (e != cudaSuccess) return fail(c0, LS_ERR_CUDA, "rhosvd_reduce: pivoted Cholesky launch: %s", cudaGetErrorString(e));
+        if (int rc = pchol_grid(c0, large, s0)) return rc;
     }
     for (int i = 0; i < n; ++i) {
         if (int rc = scatter(ctxs[i])) return rc;

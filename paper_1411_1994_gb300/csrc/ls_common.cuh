@@ -29,8 +29,8 @@ struct DevStatus {
     int flag;
     int sweeps;
     unsigned int sweep_active[64];
-    unsigned int arrive;        // arrivals at the pivoted Cholesky's counting barrier (only grows)
-    unsigned int pad;
+    unsigned int arrive;        // arrivals at a counting barrier (only grows)
+    int done;                   // the pivoted Cholesky: the stopping rule ended the factorisation
 };
 
 // ---------------------------------------------------------------------------
@@ -159,23 +159,33 @@ struct SortSelectJob {
 };
 cudaError_t launch_sort_select(int n, const SortSelectJob* jobs, double eps, double resolution, cudaStream_t st);
 
-// Pivoted Cholesky G P = L L^T (greedy diagonal pivoting) of up to three
-// C x C PSD matrices in one cooperative launch, stopped when the trace of
-// the remaining Schur complement is <= delta or after kmax columns. Each
-// job: L (C x kmax, row-major, column t = t-th pivot step), d (C scratch),
-// cand (kPcholCand doubles of scratch; its last element receives the final
-// residual trace), piv (kmax), st (zeroed; st->sweeps receives the number k
-// of columns).
+// Pivoted Cholesky G P = L L^T (greedy diagonal pivoting) of C x C PSD
+// matrices, stopped when the trace of the remaining Schur complement is
+// <= delta or after kmax columns. Each job: G (C x C; the grid form overwrites
+// it with the Schur complement), L (C x kmax, row-major, column t = t-th pivot
+// step), d (C scratch), cand (kPcholCand doubles of scratch; its last element
+// receives the final residual trace), piv (kmax), st (zeroed; st->sweeps
+// receives the number k of columns).
 constexpr int kPcholCand = 6 * 1024 + 8;
 struct PcholJob {
     const double* G; double* L; double* d; double* cand; int* piv; DevStatus* st; int64_t C; int kmax; double delta;
+    double* Lp = nullptr;   // the grid form: C x panel, the last panel's columns (zero past its last pivot)
 };
-cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cudaStream_t st);
+// One panel of the grid form: each job continues at column st->sweeps (G
+// holding the Schur complement G - L[:, :k] L[:, :k]^T) and takes up to
+// `panel` pivots; d_report (2 njobs ints, may be NULL) receives each job's
+// (columns so far, done).
+cudaError_t launch_pchol_panel(const PcholJob* jobs, int panel, int njobs, int num_sms, int* d_report, cudaStream_t st);
+
 // The same factorisation held in shared memory by one thread-block cluster per
 // matrix (ls_pchol.cu; same jobs and outputs): usable when
 // pchol_cluster_size(C, kmax) > 0 for every job.
 int pchol_cluster_size(int C, int kmax);
 cudaError_t launch_pchol_cluster(const PcholJob* jobs, int njobs, cudaStream_t st);
+// The panel of the grid form held by one cluster per matrix (ls_pchol.cu; same jobs,
+// outputs and report): usable when pchol_cpanel_fits(max C, panel).
+bool pchol_cpanel_fits(int64_t Cmax, int panel);
+cudaError_t launch_pchol_cpanel(const PcholJob* jobs, int panel, int njobs, int* d_report, cudaStream_t st);
 // xin[t] = xi[t] * n0[tc[3t]] * n1[tc[3t+1]] * n2[tc[3t+2]].
 cudaError_t launch_fold_norms(const double* xi, const int32_t* tcol, int64_t T, const double* n0,
                               const double* n1, const double* n2, double* xin, cudaStream_t st);

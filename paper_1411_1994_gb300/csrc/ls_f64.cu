@@ -525,29 +525,40 @@ __device__ __forceinline__ double key_value(unsigned long long k) {
 }
 
 // ---------------------------------------------------------------------------
-// pivoted Cholesky of up to three PSD matrices at once (cooperative grid,
-// CTAs split between the jobs): G P = L L^T with greedy diagonal pivoting,
-// stopped when the trace of the Schur complement drops below delta. Each CTA
-// owns a contiguous range of rows and keeps, in shared memory, their residual
-// diagonal and their entries of L in the first kc columns (the global copy of
-// L is written as well: other CTAs read row p from it, and it is the output).
-// One step:
+// Pivoted Cholesky of up to three PSD matrices at once, one panel of pivots a
+// launch (cooperative grid, CTAs split between the jobs): G P = L L^T with
+// greedy diagonal pivoting, stopped when the trace of the Schur complement
+// drops below delta. The launch continues the factorisation at column
+// k0 = st->sweeps of L with S = G - L[:, :k0] L[:, :k0]^T, the Schur complement
+// that the caller's tensor-core product formed after the previous panel, and
+// takes up to pw pivots, or fewer where the stopping rule ends it; it also
+// writes the panel's columns to Lp (C x pw, zero past the last pivot taken:
+// zero throughout once the factorisation has ended), so that the caller can
+// queue the next Schur update S -= Lp Lp^T without reading anything back. Each CTA owns a
+// contiguous range of rows and keeps, in shared memory, their residual
+// diagonal and their entries of L in the panel's first kc columns (the global
+// copy of L is written as well: other CTAs read row p from it, and it is the
+// output). One step:
 //   1. warp 0 reduces the per-CTA (max, argmax, sum) candidates of the
 //      residual diagonal (the maximum compared as integer keys, ties to the
 //      smaller index; the sum in a fixed order, so every CTA decides alike);
-//   2. all threads load row p of L and column p of G into shared memory;
-//   3. the other warps form the dot products of the new column, four rows a
-//      warp, while warp 0 takes 1 / sqrt(d_p);
+//   2. all threads load the panel part of row p of L and column p of S into
+//      shared memory;
+//   3. the other warps form the in-panel dot products of the new column, four
+//      rows a warp, while warp 0 takes 1 / sqrt(d_p);
 //   4. a thread per row scales its entry, updates the residual diagonal, and
 //      warp 0 publishes the CTA's candidate (double-buffered by step parity);
 //   5. the job's CTAs meet at a counting barrier.
-// FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU, so
-// the form keeps every scalar FP64 operation (reductions, the square root,
-// comparisons) on one warp instead of repeating it in each.
+// FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU: the
+// panel form leaves the bulk of it (the products with the earlier columns) to
+// the tensor cores, and keeps every scalar FP64 operation (reductions, the
+// square root, comparisons) on one warp instead of repeating it in each.
+// st->sweeps receives the columns of L so far, st->done 1 once the stopping
+// rule ended the factorisation, cand[kPcholCand - 1] the residual trace.
 // ---------------------------------------------------------------------------
 struct PcholMode {
-    const double* G; double* L; double* d; double* cand; int* piv; DevStatus* st; int C; int kmax; int cta0;
-    int ncta; int kc; double delta;
+    const double* S; double* L; double* Lp; double* d; double* cand; int* piv; DevStatus* st; int C; int kmax;
+    int cta0; int ncta; int kc; int pw; double delta;
 };
 struct PcholArgs {
     const PcholMode* m; int nmodes;
@@ -572,12 +583,22 @@ __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
     // rows of this CTA: [r0, r1)
     const int per = (C + nb - 1) / nb;
     const int r0 = min(C, lb * per), r1 = min(C, r0 + per), nr = r1 - r0;
+    const int pw = J.pw;
+    // where the previous panel left the factorisation (every CTA reads the same words)
+    const int k0 = *(volatile int*)&J.st->sweeps;
+    if (*(volatile int*)&J.st->done || k0 >= J.kmax) {
+        // ended: a zero panel, so that the queued Schur update changes nothing
+        for (int64_t e = threadIdx.x; e < (int64_t)nr * pw; e += blockDim.x) J.Lp[(int64_t)r0 * pw + e] = 0.0;
+        if (lb == 0 && threadIdx.x == 0) J.st->done = 1;
+        return;
+    }
+    const int kend = min(J.kmax, k0 + pw);
     extern __shared__ double smd[];
-    double* lrow = smd;                 // [kmax] row p of L
-    double* ds = lrow + J.kmax;         // [per] residual diagonal of the own rows
-    double* gp = ds + per;              // [per] G[own rows, p]
+    double* lrow = smd;                 // [pw] the panel part of row p of L
+    double* ds = lrow + pw;             // [per] residual diagonal of the own rows
+    double* gp = ds + per;              // [per] S[own rows, p]
     double* sacc = gp + per;            // [per] dot products of the step
-    double* Ls = sacc + per;            // [per][kc] own rows of L, columns < kc
+    double* Ls = sacc + per;            // [per][kc] own rows of L, the panel's first kc columns
     __shared__ double s_dmax, s_sum, s_inv;
     __shared__ int s_p;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
@@ -601,12 +622,15 @@ __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
             __stcg(c + 2, sm);
         }
     };
-    for (int jl = tid; jl < nr; jl += blockDim.x) ds[jl] = __ldcg(J.G + (int64_t)(r0 + jl) * C + r0 + jl);
+    // the residual diagonal: diag(G) at the start, else as the previous panel left it
+    for (int jl = tid; jl < nr; jl += blockDim.x)
+        ds[jl] = k0 == 0 ? __ldcg(J.S + (int64_t)(r0 + jl) * C + r0 + jl) : __ldcg(J.d + r0 + jl);
     __syncthreads();
     if (warp == 0) publish(0);
     unsigned int epoch = 1;
     if (!count_barrier(J.st, epoch * nb)) return;
-    int k = 0;
+    int k = k0;
+    bool done = false;
     for (;; ++k) {
         const int par = k & 1;
         // 1. warp 0 reduces the candidates of all CTAs of the job
@@ -632,16 +656,24 @@ __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
         __syncthreads();
         const int p = s_p;
         const double dmax = s_dmax;
-        // stop when the residual trace is small enough, or at kmax columns
-        if (k >= J.kmax || !(s_sum > J.delta) || p < 0 || !(dmax > 0.0)) break;
-        // 2. row p of L (written by its owner in earlier steps) and column p of G
-        for (int t = tid; t < k; t += blockDim.x) lrow[t] = __ldcg(J.L + (int64_t)p * J.kmax + t);
-        for (int jl = tid; jl < nr; jl += blockDim.x) gp[jl] = __ldcg(J.G + (int64_t)(r0 + jl) * C + p);
+        // stop when the residual trace is small enough, or at kmax columns; the panel ends at kend
+        if (k >= J.kmax || !(s_sum > J.delta) || p < 0 || !(dmax > 0.0)) {
+            done = true;
+            break;
+        }
+        if (k >= kend) break;
+        // 2. the panel part of row p of L (written by its owner in earlier steps) and column p of S
+        for (int t = k0 + tid; t < k; t += blockDim.x) lrow[t - k0] = __ldcg(J.L + (int64_t)p * J.kmax + t);
+        // S[j][p] from S's upper triangle (the Schur updates leave the lower one behind)
+        for (int jl = tid; jl < nr; jl += blockDim.x) {
+            const int j = r0 + jl;
+            gp[jl] = __ldcg(J.S + (j < p ? (int64_t)j * C + p : (int64_t)p * C + j));
+        }
         __syncthreads();
         // 3. dot products, kPcRows rows a warp (warp 0 last), and 1 / sqrt(d_p) on warp 0
         if (tid == 0) s_inv = 1.0 / sqrt(dmax);
         const int ngroups = (nr + kPcRows - 1) / kPcRows;
-        const int ks = min(k, kc);
+        const int kk = k - k0, ks = min(kk, kc);   // in-panel columns before k; those in shared memory
         for (int gi = (warp + nw - 1) % nw; gi < ngroups; gi += nw) {
             int rl[kPcRows];
 #pragma unroll
@@ -655,11 +687,11 @@ __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
 #pragma unroll
                 for (int q = 0; q < kPcRows; ++q) acc[q] = fma(Ls[(size_t)rl[q] * kc + t], lv, acc[q]);
             }
-            for (; t < k; t += 32) {
+            for (; t < kk; t += 32) {
                 const double lv = lrow[t];
 #pragma unroll
                 for (int q = 0; q < kPcRows; ++q)
-                    acc[q] = fma(__ldcg(J.L + (int64_t)(r0 + rl[q]) * J.kmax + t), lv, acc[q]);
+                    acc[q] = fma(__ldcg(J.Lp + (int64_t)(r0 + rl[q]) * pw + t), lv, acc[q]);
             }
             // transposed butterfly: 6 additions for the four sums (lane 8 q holds row q)
             const bool hi = lane & 16;
@@ -677,8 +709,9 @@ __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
         for (int jl = tid; jl < nr; jl += blockDim.x) {
             const int j = r0 + jl;
             const double l = (gp[jl] - sacc[jl]) * inv;
-            if (k < kc) Ls[(size_t)jl * kc + k] = l;
+            if (kk < kc) Ls[(size_t)jl * kc + kk] = l;
             __stcg(J.L + (int64_t)j * J.kmax + k, l);
+            __stcg(J.Lp + (int64_t)j * pw + kk, l);
             ds[jl] = (j == p) ? 0.0 : fmax(ds[jl] - l * l, 0.0);
         }
         if (lb == 0 && tid == 0) J.piv[k] = p;
@@ -688,8 +721,14 @@ __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
         if (!count_barrier(J.st, ++epoch * nb)) return;
     }
     for (int jl = tid; jl < nr; jl += blockDim.x) J.d[r0 + jl] = ds[jl];
+    // the panel's columns past the last pivot taken are zero
+    for (int64_t e = tid; e < (int64_t)nr * (pw - (k - k0)); e += blockDim.x) {
+        const int64_t jl = e / (pw - (k - k0)), t = (k - k0) + e % (pw - (k - k0));
+        J.Lp[(r0 + jl) * pw + t] = 0.0;
+    }
     if (lb == 0 && tid == 0) {
         J.st->sweeps = k;                          // columns of L
+        J.st->done = done ? 1 : 0;
         J.cand[kPcholCand - 1] = s_sum;            // residual trace: energy outside span(L)
     }
 }
@@ -1156,7 +1195,15 @@ cudaError_t launch_sort_select(int n, const SortSelectJob* jobs, double eps, dou
     return cudaSuccess;
 }
 
-cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cudaStream_t st) {
+// (columns of L so far, done) of every job of a panel launch, for the caller's one read-back
+__global__ void k_pchol_report(const PcholMode* m, int n, int* out) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        out[2 * j] = m[j].st->sweeps;
+        out[2 * j + 1] = m[j].st->done;
+    }
+}
+
+cudaError_t launch_pchol_panel(const PcholJob* jobs, int panel, int njobs, int num_sms, int* d_report, cudaStream_t st) {
     if (njobs < 1) return cudaSuccess;
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1164,7 +1211,7 @@ cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cud
         optin = 48 * 1024;
     const int64_t budget = std::max<int64_t>(0, optin - 1024);   // the kernel's static variables take a few bytes
     std::vector<int64_t> want(njobs);
-    // a warp per row and step; the candidate scratch holds 1024 CTAs per job
+    // a warp per four rows and step; the candidate scratch holds 1024 CTAs per job
     for (int m = 0; m < njobs; ++m) want[m] = std::min<int64_t>(1024, std::max<int64_t>(1, (jobs[m].C + 7) / 8));
     // one CTA per SM (the own rows of L fill its shared memory): at most num_sms jobs a launch
     for (int j0 = 0, nj = 0; j0 < njobs; j0 += nj) {
@@ -1176,17 +1223,19 @@ cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cud
         int cta = 0;
         for (int m = 0; m < nj; ++m) {
             const PcholJob& J = jobs[j0 + m];
+            if (!J.Lp || panel < 1) return cudaErrorInvalidValue;
             const int64_t per = (J.C + nc[m] - 1) / nc[m];
-            const int64_t fixed = 8 * ((int64_t)J.kmax + 3 * per);   // row p of L, d, G[., p], the dots
-            // columns of the own rows of L held in shared memory (the rest is read from L2)
-            const int64_t kc = std::min<int64_t>(J.kmax, std::max<int64_t>(0, (budget - fixed) / (8 * per)));
+            const int64_t fixed = 8 * ((int64_t)panel + 3 * per);   // row p of L, d, S[., p], the dots
+            // panel columns of the own rows of L held in shared memory (the rest is read from L2)
+            const int64_t kc = std::min<int64_t>(panel, std::max<int64_t>(0, (budget - fixed) / (8 * per)));
             smem = std::max(smem, (size_t)(fixed + 8 * per * kc));
-            hm[m] = PcholMode{J.G, J.L, J.d, J.cand, J.piv, J.st, (int)J.C, J.kmax, cta, nc[m], (int)kc, J.delta};
+            hm[m] = PcholMode{J.G, J.L, J.Lp, J.d, J.cand, J.piv, J.st, (int)J.C, J.kmax, cta, nc[m], (int)kc, panel,
+                              J.delta};
             cta += nc[m];
             cudaError_t e = cudaMemsetAsync(&J.st->arrive, 0, sizeof(unsigned int), st);
             if (e != cudaSuccess) return e;
         }
-        if ((int64_t)smem > budget) return cudaErrorInvalidValue;   // row p of L alone exceeds the shared memory
+        if ((int64_t)smem > budget) return cudaErrorInvalidValue;
         if (smem > 48 * 1024) {
             cudaError_t e = grow_smem((const void*)k_pchol_multi, smem);
             if (e != cudaSuccess) return e;
@@ -1204,6 +1253,11 @@ cudaError_t launch_pchol_multi(const PcholJob* jobs, int njobs, int num_sms, cud
             void* args[] = {&a};
             count_kernels(1);
             e = cudaLaunchCooperativeKernel((void*)k_pchol_multi, dim3(cta), dim3(256), args, smem, st);
+        }
+        if (e == cudaSuccess && d_report) {
+            k_pchol_report<<<1, 128, 0, st>>>(dm, nj, d_report + 2 * j0);
+            count_kernels(1);
+            e = cudaGetLastError();
         }
         cudaFreeAsync(dm, st);
         if (e != cudaSuccess) return e;

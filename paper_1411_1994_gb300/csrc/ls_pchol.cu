@@ -181,8 +181,186 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cluster(PcArgs A) {
     cl.sync();
 }
 
+// ---------------------------------------------------------------------------
+// The panel form for matrices whose rows of G do not fit a cluster: one
+// cluster per matrix continues the factorisation at column k0 = st->sweeps,
+// with S = G - L[:, :k0] L[:, :k0]^T in global memory (the Schur complement the
+// caller's tensor-core product formed after the previous panel), and takes up
+// to pw pivots. CTA r keeps its rows' residual diagonal and their entries of
+// the panel's columns in shared memory; column p of S comes from global memory
+// (one round trip a step), row p of the panel from its owner's shared memory.
+// The panel's columns also go to Lp (C x pw, zero past the last pivot taken,
+// zero throughout once the factorisation has ended), so that the caller can
+// queue the Schur update S -= Lp Lp^T without a read-back. The same steps,
+// candidate keys and quarter sums as the whole-matrix kernel above.
+// ---------------------------------------------------------------------------
+struct CpMode {
+    const double* S; double* L; double* Lp; double* d; double* resid; int* piv; DevStatus* st; int C; int kmax;
+    double delta;
+};
+struct CpArgs {
+    const CpMode* m; int cs; int rows_per; int pw;
+};
+
+__global__ void __launch_bounds__(kPcThreads) k_pchol_cpanel(CpArgs A) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const CpMode J = A.m[blockIdx.x / A.cs];
+    const int C = J.C, kmax = J.kmax, rp = A.rows_per, pw = A.pw;
+    const int ldL = pw | 1;
+    const int r0 = min(C, rank * rp), r1 = min(C, r0 + rp), nr = r1 - r0;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    // where the previous panel left the factorisation (every CTA reads the same words)
+    const int k0 = *(volatile int*)&J.st->sweeps;
+    if (*(volatile int*)&J.st->done || k0 >= kmax) {
+        for (int64_t e = tid; e < (int64_t)nr * pw; e += nthr) J.Lp[(int64_t)r0 * pw + e] = 0.0;
+        if (rank == 0 && tid == 0) J.st->done = 1;
+        return;   // every CTA of the cluster leaves here: no cluster barrier is pending
+    }
+    const int kend = min(kmax, k0 + pw);
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* Ls = reinterpret_cast<double*>(smem);                 // [rp][ldL] the panel's columns
+    double* d = Ls + (size_t)rp * ldL;                            // [rp]
+    double* lrow = d + rp;                                        // [pw]
+    double* part = lrow + pw;                                     // [4][rp] quarter sums
+    double* gcol = part + 4 * (size_t)rp;                         // [rp] S[own rows, p]
+    Cand* cand = reinterpret_cast<Cand*>(gcol + rp);              // [2][cs]
+    __shared__ double s_dmax, s_sum, s_inv;
+    __shared__ int s_p;
+
+    for (int jl = tid; jl < nr; jl += nthr)
+        d[jl] = k0 == 0 ? J.S[(int64_t)(r0 + jl) * C + r0 + jl] : J.d[r0 + jl];
+    __syncthreads();
+    auto publish = [&](int parity) {
+        if (warp != 0) return;
+        unsigned long long key = 0;
+        double sm = 0.0, mx = 0.0;
+        for (int jl = lane; jl < nr; jl += 32) {
+            const double v = d[jl];
+            sm += v;
+            const unsigned long long kk = cand_key(v, r0 + jl);
+            if (kk > key) { key = kk; mx = v; }
+        }
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+            const double m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+            if (k2 > key) { key = k2; mx = m2; }
+            sm += __shfl_xor_sync(0xffffffffu, sm, o);
+        }
+        if (lane < A.cs) cl.map_shared_rank(cand, lane)[parity * A.cs + rank] = Cand{sm, mx, (long long)key, 0};
+    };
+    publish(0);
+    cl.sync();
+    int k = k0;
+    bool done = false;
+    double sum = 0.0;
+    for (;; ++k) {
+        const int par = (k - k0) & 1;
+        if (warp == 0) {
+            unsigned long long key = 0;
+            double sm = 0.0, mx = 0.0;
+            if (lane < A.cs) {
+                const Cand c = cand[par * A.cs + lane];
+                key = (unsigned long long)c.key;
+                sm = c.sum;
+                mx = c.mx;
+            }
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+                const double m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+                if (k2 > key) { key = k2; mx = m2; }
+                sm += __shfl_xor_sync(0xffffffffu, sm, o);
+            }
+            if (lane == 0) {
+                s_p = key == 0 ? -1 : 0xffffff - (int)(key & 0xffffffull);
+                s_dmax = key == 0 ? 0.0 : mx;
+                s_sum = sm;
+                s_inv = mx > 0.0 ? 1.0 / sqrt(mx) : 0.0;
+            }
+        }
+        __syncthreads();
+        const double dmax = s_dmax;
+        const int p = s_p;
+        sum = s_sum;
+        if (k >= kmax || !(sum > J.delta) || p < 0 || !(dmax > 0.0)) {
+            done = true;
+            break;
+        }
+        if (k >= kend) break;
+        const int kk = k - k0;
+        // the panel part of row p from its owner, column p of S for the own rows
+        {
+            const int owner = p / rp;
+            const double* src = cl.map_shared_rank(Ls, owner) + (size_t)(p - owner * rp) * ldL;
+            for (int t = tid; t < kk; t += nthr) lrow[t] = src[t];
+            // S[j][p] from S's upper triangle (the Schur updates leave the lower one behind)
+            for (int jl = tid; jl < nr; jl += nthr) {
+                const int j = r0 + jl;
+                gcol[jl] = __ldcg(J.S + (j < p ? (int64_t)j * C + p : (int64_t)p * C + j));
+            }
+        }
+        __syncthreads();
+        const double inv = s_inv;
+        {
+            const int qlen = (kk + 3) >> 2, t0 = min(kk, warp * qlen), t1 = min(kk, t0 + qlen);
+            for (int jl = lane; jl < nr; jl += 32) {
+                const double* lj = Ls + (size_t)jl * ldL;
+                double a0 = 0.0, a1 = 0.0;
+                int t = t0;
+                for (; t + 1 < t1; t += 2) {
+                    a0 = fma(lj[t], lrow[t], a0);
+                    a1 = fma(lj[t + 1], lrow[t + 1], a1);
+                }
+                if (t < t1) a0 = fma(lj[t], lrow[t], a0);
+                part[warp * rp + jl] = a0 + a1;
+            }
+        }
+        __syncthreads();
+        for (int jl = tid; jl < nr; jl += nthr) {
+            const double dot = ((part[jl] + part[rp + jl]) + part[2 * rp + jl]) + part[3 * rp + jl];
+            const double l = (gcol[jl] - dot) * inv;
+            Ls[(size_t)jl * ldL + kk] = l;
+            __stcg(J.L + (int64_t)(r0 + jl) * kmax + k, l);
+            __stcg(J.Lp + (int64_t)(r0 + jl) * pw + kk, l);
+            d[jl] = (r0 + jl == p) ? 0.0 : fmax(d[jl] - l * l, 0.0);
+        }
+        if (rank == 0 && tid == 0) J.piv[k] = p;
+        __syncthreads();
+        publish(par ^ 1);
+        cl.sync();
+    }
+    for (int jl = tid; jl < nr; jl += nthr) J.d[r0 + jl] = d[jl];
+    // the panel's columns past the last pivot taken are zero
+    const int taken = k - k0;
+    for (int64_t e = tid; e < (int64_t)nr * (pw - taken); e += nthr) {
+        const int64_t jl = e / (pw - taken), t = taken + e % (pw - taken);
+        J.Lp[(r0 + jl) * pw + t] = 0.0;
+    }
+    if (rank == 0 && tid == 0) {
+        J.st->sweeps = k;
+        J.st->done = done ? 1 : 0;
+        *J.resid = sum;
+    }
+    cl.sync();
+}
+
+size_t cp_smem(int cs, int rp, int pw) {
+    return 8 * ((size_t)rp * (pw | 1) + rp + pw + 4 * (size_t)rp + rp) + sizeof(Cand) * 2 * (size_t)cs;
+}
+
 size_t pc_smem(int C, int kmax, int cs, int rp) {
     return 8 * ((size_t)rp * (C | 1) + (size_t)rp * (kmax | 1) + rp + kmax + 4 * (size_t)rp) + sizeof(Cand) * 2 * (size_t)cs;
+}
+
+int sm_count_pc() {
+    static const int n = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 1;
+        return std::max(1, v);
+    }();
+    return n;
 }
 
 int smem_cap() {
@@ -220,6 +398,40 @@ bool cluster16_fits(cudaLaunchConfig_t cfg) {
     if (!ok) cudaGetLastError();
     known[cfg.dynamicSmemBytes] = ok;
     return ok;
+}
+
+
+// the panel kernel's attributes, as for the whole-matrix kernel
+cudaError_t cp_allow_cluster16() {
+    static cudaError_t e = cudaFuncSetAttribute(k_pchol_cpanel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+cudaError_t cp_reserve_smem(size_t bytes) {
+    static size_t done = 0;
+    std::lock_guard<std::mutex> g(g_pc_mu);
+    if (bytes <= done) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k_pchol_cpanel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done = bytes;
+    return e;
+}
+bool cp_cluster16_fits(cudaLaunchConfig_t cfg) {
+    static std::map<size_t, bool> known;
+    std::lock_guard<std::mutex> g(g_pc_mu);
+    const auto it = known.find(cfg.dynamicSmemBytes);
+    if (it != known.end()) return it->second;
+    int nclusters = 0;
+    cfg.gridDim = dim3(16);
+    const bool ok = cudaOccupancyMaxActiveClusters(&nclusters, k_pchol_cpanel, &cfg) == cudaSuccess && nclusters >= 1;
+    if (!ok) cudaGetLastError();
+    known[cfg.dynamicSmemBytes] = ok;
+    return ok;
+}
+// (columns so far, done) of every job of a panel launch, for the caller's one read-back
+__global__ void k_cpanel_report(const CpMode* m, int n, int* out) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        out[2 * j] = m[j].st->sweeps;
+        out[2 * j + 1] = m[j].st->done;
+    }
 }
 
 }  // namespace
@@ -282,6 +494,69 @@ cudaError_t launch_pchol_cluster(const PcholJob* jobs, int njobs, cudaStream_t s
         cfg.gridDim = dim3((unsigned)(njobs * cs));
         count_kernels(1);
         e = cudaLaunchKernelEx(&cfg, k_pchol_cluster, a);
+    }
+    cudaFreeAsync(dm, st);
+    return e;
+}
+
+// whether the panel form's clusters (16 CTAs, else 8) hold every job's rows for this panel width
+bool pchol_cpanel_fits(int64_t Cmax, int panel) {
+    const size_t cap = (size_t)smem_cap();
+    return cp_smem(8, (int)((Cmax + 7) / 8), panel) <= cap;
+}
+
+cudaError_t launch_pchol_cpanel(const PcholJob* jobs, int panel, int njobs, int* d_report, cudaStream_t st) {
+    if (njobs < 1) return cudaSuccess;
+    int64_t Cmax = 1;
+    for (int m = 0; m < njobs; ++m) {
+        Cmax = std::max<int64_t>(Cmax, jobs[m].C);
+        if (!jobs[m].Lp) return cudaErrorInvalidValue;
+    }
+    const size_t cap = (size_t)smem_cap();
+    // 16 CTAs a matrix while the clusters of the launch fit the GPU side by side, else 8
+    int cs = (njobs * 16 <= sm_count_pc() && cp_smem(16, (int)((Cmax + 15) / 16), panel) <= cap) ? 16 : 8;
+    if (cp_smem(cs, (int)((Cmax + cs - 1) / cs), panel) > cap) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (cs > 8 && (e = cp_allow_cluster16()) != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kPcThreads);
+    cfg.dynamicSmemBytes = cp_smem(cs, (int)((Cmax + cs - 1) / cs), panel);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if ((e = cp_reserve_smem(cfg.dynamicSmemBytes)) != cudaSuccess) return e;
+    // a 16-CTA cluster must fit one GPC: fall back to 8 where it does not
+    if (cs > 8 && !cp_cluster16_fits(cfg)) {
+        cs = 8;
+        attr[0].val.clusterDim.x = 8;
+        cfg.dynamicSmemBytes = cp_smem(cs, (int)((Cmax + cs - 1) / cs), panel);
+        if ((e = cp_reserve_smem(cfg.dynamicSmemBytes)) != cudaSuccess) return e;
+    }
+    const int rp = (int)((Cmax + cs - 1) / cs);
+    std::vector<CpMode> hm(njobs);
+    for (int m = 0; m < njobs; ++m) {
+        const PcholJob& J = jobs[m];
+        hm[m] = CpMode{J.G, J.L, J.Lp, J.d, J.cand + kPcholCand - 1, J.piv, J.st, (int)J.C, J.kmax, J.delta};
+    }
+    CpMode* dm = nullptr;
+    e = cudaMallocAsync(&dm, sizeof(CpMode) * njobs, st);
+    if (e != cudaSuccess) return e;
+    e = upload_h2d(dm, hm.data(), sizeof(CpMode) * njobs, st);
+    if (e == cudaSuccess) {
+        CpArgs a{dm, cs, rp, panel};
+        cfg.gridDim = dim3((unsigned)(njobs * cs));
+        count_kernels(1);
+        e = cudaLaunchKernelEx(&cfg, k_pchol_cpanel, a);
+    }
+    if (e == cudaSuccess && d_report) {
+        k_cpanel_report<<<1, 128, 0, st>>>(dm, njobs, d_report);
+        count_kernels(1);
+        e = cudaGetLastError();
     }
     cudaFreeAsync(dm, st);
     return e;

@@ -42,6 +42,7 @@ struct TcOut {
     int64_t zs;         // batch stride (elements)
     int mode;
     int accumulate;     // F64 only: D += result
+    int negate;         // F64 only: the result enters with a minus sign
 };
 
 // ---------------------------------------------------------------------------
@@ -72,6 +73,8 @@ struct X64Job {
     int M, N, nkb;        // k-blocks of 64 over all of K
     int tiles_n, b0;      // tiles along N; first block of the job
     int transposed;       // D stored at out.p[n * out.ld + m]
+    int upper;            // only tiles that reach the diagonal or above it (a symmetric D's upper part)
+    const int* skip;      // if given and nonzero when the CTA starts: nothing to do
     const int* ea;
     const int* eb;
     TcOut out;
@@ -81,6 +84,40 @@ struct X64Group {
     X64Job j[kX64MaxJobs];
     int n;
 };
+
+// RN((hi 2^28 + lo) 2^s) for |hi|, |lo| < 2^46: the recombined level sums as a double,
+// rounded once to nearest-even like fma((double)hi, 2^-35, (double)lo 2^-63) scaled by
+// 2^(s + 63), but built on the integer pipe (the bit length, a shift of the 128-bit sum,
+// the round bit and sticky bits, the exponent field): FP64 instructions run at a small
+// fraction of the integer rate on this GPU, and the epilogue converts every output entry
+// of every K-chunk. Results outside the normal range take the FP64 formula.
+__device__ __forceinline__ double rn_scaled(long long hi, long long lo, int s) {
+    const __int128 X = ((__int128)hi << 28) + (__int128)lo;
+    if (X == 0) return 0.0;
+    const bool neg = X < 0;
+    const unsigned __int128 A = neg ? (unsigned __int128)(-X) : (unsigned __int128)X;
+    const unsigned long long ah = (unsigned long long)(A >> 64), al = (unsigned long long)A;
+    const int nb = ah ? 128 - __clzll((long long)ah) : 64 - __clzll((long long)al);   // bit length, <= 75
+    int e = nb - 1 + s;                                                                 // unbiased exponent
+    unsigned long long m;                                                               // 53 significant bits
+    if (nb <= 53) {
+        m = al << (53 - nb);
+    } else {
+        const int sh = nb - 53;   // 1 .. 22
+        m = (al >> sh) | (sh < 64 ? (ah << (64 - sh)) : 0ull);
+        const unsigned long long rem = al & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (m & 1ull))) {
+            if (++m == (1ull << 53)) {
+                m >>= 1;
+                ++e;
+            }
+        }
+    }
+    if (e < -1022 || e > 1023) return ldexp(fma((double)hi, 0x1p-35, (double)lo * 0x1p-63), s + 63);
+    const unsigned long long bits =
+        (neg ? 0x8000000000000000ull : 0ull) | ((unsigned long long)(e + 1023) << 52) | (m & 0xfffffffffffffull);
+    return __longlong_as_double((long long)bits);
+}
 
 // One 128 x 64 output tile of one job per CTA, all of K: the K-chunks of 512 run in
 // turn on the same eight accumulators (the MMA warp waits until the epilogue has drained
@@ -100,6 +137,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_x64_gemm(const __grid_constan
     const int tile = (int)blockIdx.x - J.b0;
     const int tm = tile / J.tiles_n, tn = tile - tm * J.tiles_n;
     const int n0 = tn * TBN, m0 = tm * TBM;
+    if (J.upper && m0 >= n0 + TBN) return;   // strictly below the diagonal: not wanted
+    if (J.skip && *(volatile const int*)J.skip) return;
     const int kbc = XKCHUNK / TBK;
     const int nchunk = (J.nkb + kbc - 1) / kbc;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -194,8 +233,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_x64_gemm(const __grid_constan
                     for (int l = 0; l < 4; ++l) hi = hi * 128 + (long long)__float2int_rn(S[l][jj]);
 #pragma unroll
                     for (int l = 4; l < 8; ++l) lo = lo * 128 + (long long)__float2int_rn(S[l][jj]);
-                    // sum_l S_l 2^(-7(l+2)) = hi 2^-35 + lo 2^-63
-                    const double v = ldexp(fma((double)hi, 0x1p-35, (double)lo * 0x1p-63), er + J.eb[col]);
+                    // sum_l S_l 2^(-7(l+2)) = (hi 2^28 + lo) 2^-63, times 2^(E_a + E_b)
+                    const double v0 = rn_scaled(hi, lo, er + J.eb[col] - 63);
+                    const double v = J.out.negate ? -v0 : v0;
                     double* o = (double*)J.out.p +
                                 (J.transposed ? (int64_t)col * J.out.ld + row : (int64_t)row * J.out.ld + col);
                     *o = add ? *o + v : v;
@@ -356,6 +396,8 @@ struct X64Spec {
     int64_t M, N;
     TcOut out;
     int transposed;
+    int upper;   // compute only the tiles that reach the diagonal or above it
+    const int* skip = nullptr;   // device flag: the product is not wanted when it is nonzero
 };
 
 // up to kX64MaxJobs products in one launch; out.mode must be OUT_F64
@@ -381,6 +423,8 @@ int gemm_x64(const X64Spec* sp, int n, int* flag, cudaStream_t st, std::string* 
         J.tiles_n = (int)((s0.N + TBN - 1) / TBN);
         J.b0 = blocks;
         J.transposed = s0.transposed;
+        J.upper = s0.upper;
+        J.skip = s0.skip;
         J.ea = s0.A->e;
         J.eb = s0.B->e;
         J.out = s0.out;
@@ -421,6 +465,40 @@ int x64_gram(int n, const double* const a[], const int64_t C[], int64_t N, const
     if (sb.flush() != cudaSuccess) return tc_err(err, "x64_gram: split failed");
     for (int l = 0; l < n; ++l) sp[l] = X64Spec{&xs[l], &xs[l], C[l], C[l], TcOut{G[l], C[l], 0, OUT_F64, 0}, 0};
     return gemm_x64(sp.data(), n, flag, st, err);
+}
+
+// S_l -= L_l[:, k0_l : k0_l + kb_l] L_l[:, k0_l : k0_l + kb_l]^T on the tiles of S_l that
+// reach its diagonal or lie above it (S_l symmetric: its readers take S[min(i,j)][max(i,j)]):
+// L_l C_l x kmax_l (rows), S_l C_l x C_l; jobs with kb_l = 0 are skipped, and so are those
+// whose device flag skip[l] (if given) is nonzero when the product runs
+int x64_syrk_sub(int n, const double* const L[], const int64_t kmax[], const int k0[], const int kb[],
+                 const int64_t C[], double* const S[], int* flag, cudaStream_t st, std::string* err,
+                 const int* const skip[]) {
+    for (int l0 = 0; l0 < n; l0 += kX64MaxJobs) {
+        Arena ar(st);
+        SplitBatch sb(st);
+        std::vector<X64Op> xs;
+        std::vector<X64Spec> sp;
+        xs.reserve(kX64MaxJobs);
+        for (int l = l0; l < std::min(n, l0 + kX64MaxJobs); ++l) {
+            if (kb[l] <= 0) continue;
+            xs.push_back(x64_alloc(ar, C[l], pad64(kb[l])));
+            if (!xs.back().ok()) return tc_err(err, "x64_syrk_sub: out of memory", LS_ERR_OOM);
+            sb.add(L[l] + k0[l], C[l], kb[l], kmax[l], 1, nullptr, xs.back());
+        }
+        if (xs.empty()) continue;
+        if (sb.flush() != cudaSuccess) return tc_err(err, "x64_syrk_sub: split failed");
+        int i = 0;
+        for (int l = l0; l < std::min(n, l0 + kX64MaxJobs); ++l) {
+            if (kb[l] <= 0) continue;
+            sp.push_back(X64Spec{&xs[i], &xs[i], C[l], C[l], TcOut{S[l], C[l], 0, OUT_F64, 1, 1}, 0, 1,
+                                 skip ? skip[l] : nullptr});
+            ++i;
+        }
+        const int rc = gemm_x64(sp.data(), (int)sp.size(), flag, st, err);
+        if (rc != LS_OK) return rc;
+    }
+    return LS_OK;
 }
 
 // P_l = Z_l A_l^T: Z_l r_l x N, A_l C_l x N (rows), P_l r_l x C_l

@@ -18,6 +18,14 @@ namespace ls {
 int x64_gram(int n, const double* const a[], const int64_t C[], int64_t N, const double* const w[], double* const G[],
              int* flag, cudaStream_t st, std::string* err);
 // P_l = Z_l A_l^T  (Z_l: r_l x N, A_l: C_l x N, P_l: r_l x C_l).
+// S_l -= L_l[:, k0_l : k0_l + kb_l] L_l[:, k0_l : k0_l + kb_l]^T (the Schur complement after a
+// panel of the pivoted Cholesky) on the upper triangle of S_l and the tiles that cross its
+// diagonal (read S[min(i,j)][max(i,j)]): L_l C_l x kmax_l row-major, S_l C_l x C_l; kb_l = 0
+// skips job l
+// skips job l if the device flag skip[l] (when skip is given) is nonzero when the product runs
+int x64_syrk_sub(int n, const double* const L[], const int64_t kmax[], const int k0[], const int kb[],
+                 const int64_t C[], double* const S[], int* flag, cudaStream_t st, std::string* err,
+                 const int* const skip[] = nullptr);
 int x64_project(int n, const double* const Z[], const int r[], const double* const a[], const int64_t C[], int64_t N,
                 double* const P[], int* flag, cudaStream_t st, std::string* err);
 // dst_l = T_l src_l  (T_l: r_l x r_l, src_l and dst_l: r_l x N).
