@@ -690,6 +690,9 @@ struct RedState {
     // truncation sits far above the first run's accuracy, and the candidate bases of the
     // non-squaring route, whose accuracy the one-sided Jacobi restores)
     bool fast_eig = false;
+    // the batch: red_core leaves the release (which synchronises the stream) to the caller, so that
+    // the projections and cores of all contexts are queued before the first wait
+    bool defer_release = false;
 };
 
 #define CUS(call)                                                                                     \
@@ -1096,7 +1099,7 @@ int red_core(RedState& R, ls_tucker_info* info) {
     }
     dfree(ctx, d_perm_t);
     dfree(ctx, d_off);
-    return red_release(R, info);
+    return R.defer_release ? LS_OK : red_release(R, info);
 }
 
 // frees the reduction scratch, reads the statuses back (synchronising the stream), checks
@@ -1186,7 +1189,7 @@ cudaError_t join(cudaStream_t to, cudaStream_t from) {
 // and I + F2, and V = Uo + Uo F2; H' then takes the place of H. Both runs use
 // the block Jacobi, in one cluster's shared memory where k fits and in one
 // cooperative grid otherwise; beyond k = 8192 the FP64 grid Jacobi. The eps-rule tolerances: 1e-6 for the first run
-// (FP32), 1e-10 for the second; forced ranks use the same.
+// (FP32; 1e-4 where it is the only run), 1e-10 for the second; forced ranks use the same.
 int eigen_all(std::vector<RedState>& R, ls_ctx* const* ctxs, int n, const std::vector<JacobiJob>& jj, cudaStream_t s0) {
     ls_ctx* c0 = ctxs[0];
     std::vector<JacobiJob> grid;
@@ -1196,7 +1199,10 @@ int eigen_all(std::vector<RedState>& R, ls_ctx* const* ctxs, int n, const std::v
             RedMode& M = R[i].m[l];
             const JacobiJob& J = jj[3 * i + l];
             if (!M.df) { grid.push_back(J); continue; }
-            s1.push_back(DfJob{M.H, M.k, M.T1, 1, M.U0, 1, R[i].d_st + l, J.abs_floor, J.tau, 1e-6});
+            // a single run (fast_eig) stops at 1e-4: its Rayleigh quotients are then good to about
+            // k 1e-8 relative, far inside the truncation's eps, and its basis error is second order
+            s1.push_back(DfJob{M.H, M.k, M.T1, 1, M.U0, 1, R[i].d_st + l, J.abs_floor, J.tau,
+                               R[i].fast_eig ? 1e-4 : 1e-6});
             if (!R[i].fast_eig)
                 s2.push_back(DfJob{M.Hp, M.k, M.Hp, (int64_t)M.k + 1, M.F2, 0, R[i].d_st + l, J.abs_floor, J.tau, 1e-10});
         }
@@ -1475,8 +1481,17 @@ int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, l
     for (int i = 0; i < n; ++i)
         if (int rc = red_cholqr_mid(R[i])) return rc;
     int first_err = LS_OK;
+    std::vector<char> queued(n, 0);
     for (int i = 0; i < n; ++i) {
+        R[i].defer_release = n > 1 && R[i].kind == 0;
         int rc = red_finish(R[i], infos ? &infos[i] : nullptr);
+        queued[i] = rc == LS_OK && R[i].defer_release;
+        if (rc != LS_OK && first_err == LS_OK) first_err = rc;
+    }
+    // the releases after every context's projection and core are queued
+    for (int i = 0; i < n; ++i) {
+        if (!queued[i]) continue;
+        int rc = red_release(R[i], infos ? &infos[i] : nullptr);
         if (rc != LS_OK && first_err == LS_OK) first_err = rc;
     }
     if (pass_out) *pass_out = R[0];
