@@ -765,7 +765,11 @@ int red_prepare(RedState& R, PcholJob* pj) {
         // FP64-grade weighted Gram matrices on the tensor cores
         Scope sc("gram", st);
         std::string err;
-        int rc = x64_gram(3, a, Cs, N, w, G, &R.d_st[9].flag, st, &err);
+        // the panel forms of the pivoted Cholesky read G[min(i,j)][max(i,j)] only: their Gram
+        // matrices skip the tiles below the diagonal (the whole-matrix cluster form reads all)
+        int upper[3];
+        for (int l = 0; l < 3; ++l) upper[l] = pchol_cluster_size((int)Cs[l], (int)Cs[l]) > 0 ? 0 : 1;
+        int rc = x64_gram(3, a, Cs, N, w, G, &R.d_st[9].flag, st, &err, upper);
         if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: Gram: %s", err.c_str());
     }
     return LS_OK;

@@ -452,7 +452,7 @@ int gemm_x64(const X64Spec* sp, int n, int* flag, cudaStream_t st, std::string* 
 // FP64-grade products on the tensor cores (exact slices) -------------------
 // G_l = diag(w_l) A_l A_l^T diag(w_l), A_l: C_l rows of length N
 int x64_gram(int n, const double* const a[], const int64_t C[], int64_t N, const double* const w[], double* const G[],
-             int* flag, cudaStream_t st, std::string* err) {
+             int* flag, cudaStream_t st, std::string* err, const int* upper) {
     Arena ar(st);
     SplitBatch sb(st);
     std::vector<X64Op> xs(n);
@@ -463,7 +463,8 @@ int x64_gram(int n, const double* const a[], const int64_t C[], int64_t N, const
         sb.add(a[l], C[l], N, N, 1, w ? w[l] : nullptr, xs[l]);
     }
     if (sb.flush() != cudaSuccess) return tc_err(err, "x64_gram: split failed");
-    for (int l = 0; l < n; ++l) sp[l] = X64Spec{&xs[l], &xs[l], C[l], C[l], TcOut{G[l], C[l], 0, OUT_F64, 0}, 0};
+    for (int l = 0; l < n; ++l)
+        sp[l] = X64Spec{&xs[l], &xs[l], C[l], C[l], TcOut{G[l], C[l], 0, OUT_F64, 0}, 0, upper ? upper[l] : 0};
     return gemm_x64(sp.data(), n, flag, st, err);
 }
 

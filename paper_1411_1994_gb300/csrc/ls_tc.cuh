@@ -14,9 +14,11 @@ namespace ls {
 // sum |a_k||b_k|, as an FP64 dot product). `flag` (device int) receives
 // FLAG_TIMEOUT if a bounded wait gives up; no host synchronisation.
 // Each takes n <= 3 products (one per mode) and runs them in one launch.
-// G_l = diag(w_l) A_l A_l^T diag(w_l)  (A_l: C_l rows of length N; w may be NULL).
+// G_l = diag(w_l) A_l A_l^T diag(w_l)  (A_l: C_l rows of length N; w may be NULL). Where
+// upper[l] is nonzero, only the 128 x 64 tiles that reach the diagonal or lie above it are
+// formed (for readers of G[min(i,j)][max(i,j)]); the entries strictly below are not written.
 int x64_gram(int n, const double* const a[], const int64_t C[], int64_t N, const double* const w[], double* const G[],
-             int* flag, cudaStream_t st, std::string* err);
+             int* flag, cudaStream_t st, std::string* err, const int* upper = nullptr);
 // P_l = Z_l A_l^T  (Z_l: r_l x N, A_l: C_l x N, P_l: r_l x C_l).
 // S_l -= L_l[:, k0_l : k0_l + kb_l] L_l[:, k0_l : k0_l + kb_l]^T (the Schur complement after a
 // panel of the pivoted Cholesky) on the upper triangle of S_l and the tiles that cross its
