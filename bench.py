@@ -356,6 +356,30 @@ def step_flops(name, info, N):
     return None
 
 
+def traffic_record(step):
+    """DRAM bytes per launch of the step's kernel from the committed ncu summary under profiles/
+    (a `traffic_record:` line: step | kernel | sources | sha256 of the sources | bytes), taken only
+    while the sources hash as they did when the counters were captured; else None."""
+    import glob
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    for path in sorted(glob.glob(os.path.join(here, "profiles", "*.md"))):
+        for line in open(path):
+            if not line.startswith("traffic_record:"):
+                continue
+            parts = [x.strip() for x in line[len("traffic_record:"):].split("|")]
+            if len(parts) != 5 or parts[0] != step:
+                continue
+            h = hashlib.sha256()
+            for f in parts[2].split("+"):
+                src = os.path.join(here, "paper_1411_1994_gb300", "csrc", f)
+                if not os.path.exists(src):
+                    return None
+                h.update(open(src, "rb").read())
+            return float(parts[4]) if h.hexdigest() == parts[3] else None
+    return None
+
+
 def roofline(report, info, N, steps, precision, peaks):
     st = report.get("steps", {})
     if not st:
@@ -374,7 +398,8 @@ def roofline(report, info, N, steps, precision, peaks):
     if name == "jacobi":
         peak = FP32_PEAK_TFLOPS_DERIVED
         out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None,
+                    "traffic": traffic_record(name),
+                    "traffic_source": "k_jacobi_gblk, one ncu capture (profiles/k_jacobi_gblk_c3.md), bytes per launch",
                     "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz (FP32 on CUDA cores; "
                                    "an FFMA probe measured 73 TFLOP/s); the rotations are sequential rounds, "
                                    "so this step is bound by latency, not by this peak"})

@@ -1193,7 +1193,7 @@ cudaError_t join(cudaStream_t to, cudaStream_t from) {
 // and I + F2, and V = Uo + Uo F2; H' then takes the place of H. Both runs use
 // the block Jacobi, in one cluster's shared memory where k fits and in one
 // cooperative grid otherwise; beyond k = 8192 the FP64 grid Jacobi. The eps-rule tolerances: 1e-6 for the first run
-// (FP32; 1e-4 where it is the only run), 1e-10 for the second; forced ranks use the same.
+// (FP32; 1e-4 where it is the mixed path's only run), 1e-10 for the second; forced ranks use the same.
 int eigen_all(std::vector<RedState>& R, ls_ctx* const* ctxs, int n, const std::vector<JacobiJob>& jj, cudaStream_t s0) {
     ls_ctx* c0 = ctxs[0];
     std::vector<JacobiJob> grid;
@@ -1203,10 +1203,12 @@ int eigen_all(std::vector<RedState>& R, ls_ctx* const* ctxs, int n, const std::v
             RedMode& M = R[i].m[l];
             const JacobiJob& J = jj[3 * i + l];
             if (!M.df) { grid.push_back(J); continue; }
-            // a single run (fast_eig) stops at 1e-4: its Rayleigh quotients are then good to about
-            // k 1e-8 relative, far inside the truncation's eps, and its basis error is second order
+            // the mixed path's single run stops at 1e-4: its Rayleigh quotients are then good to
+            // about k 1e-8 relative, far inside the truncation's eps, and its basis error is second
+            // order; the candidate passes keep 1e-6 (the one-sided Jacobi after them converges in
+            // fewer sweeps on the more nearly orthogonal rows)
             s1.push_back(DfJob{M.H, M.k, M.T1, 1, M.U0, 1, R[i].d_st + l, J.abs_floor, J.tau,
-                               R[i].fast_eig ? 1e-4 : 1e-6});
+                               (R[i].fast_eig && R[i].kind == 0) ? 1e-4 : 1e-6});
             if (!R[i].fast_eig)
                 s2.push_back(DfJob{M.Hp, M.k, M.Hp, (int64_t)M.k + 1, M.F2, 0, R[i].d_st + l, J.abs_floor, J.tau, 1e-10});
         }
