@@ -834,7 +834,7 @@ constexpr int CHB = 32;
 
 // Blocked right-looking Cholesky A = L L^T (lower, in place) followed by the
 // triangular inverse Li = L^{-1} (lower, zeros above) of several matrices in
-// one cooperative grid, CTAs split between the jobs: a group barrier after
+// one cooperative grid, CTAs split between the jobs: a counting barrier after
 // each panel step and after each block row of Li.
 struct CholMode {
     double* A; double* Li; DevStatus* st; int r; int cta0; int ncta; const double* gate;
@@ -855,6 +855,8 @@ __global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
     const int64_t nthr = (int64_t)nb * blockDim.x;
     const int64_t gtid = (int64_t)lb * blockDim.x + threadIdx.x;
     const int nbk = (r + CHB - 1) / CHB;
+    unsigned int epoch = 0;   // counting barriers of the job's CTAs (st->arrive zeroed by the launcher)
+    __shared__ double s_rcp[CHB];   // 1 / L_kk of the panel
     for (int j0 = 0; j0 < r; j0 += CHB) {
         const int b = min(CHB, r - j0);
         if (lb == 0) {
@@ -868,9 +870,10 @@ __global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
                     const double d = D[k][k];
                     if (!(d > 0.0)) atomicCAS(&st->flag, FLAG_OK, FLAG_NOT_SPD);
                     D[k][k] = d > 0.0 ? sqrt(d) : 1.0;
+                    s_rcp[k] = 1.0 / D[k][k];   // one division a column, not one a row
                 }
                 __syncthreads();
-                for (int i = k + 1 + threadIdx.x; i < b; i += blockDim.x) D[i][k] /= D[k][k];
+                for (int i = k + 1 + threadIdx.x; i < b; i += blockDim.x) D[i][k] *= s_rcp[k];
                 __syncthreads();
                 for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
                     const int i = e / b, l = e % b;
@@ -883,12 +886,14 @@ __global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
                 __stcg(A + (int64_t)(j0 + i) * r + j0 + k, k <= i ? D[i][k] : 0.0);
             }
         }
-        if (!group_barrier(st, nb)) return;
-        // every CTA stages L11 in shared memory for the panel solve
+        if (!count_barrier(st, ++epoch * nb)) return;
+        // every CTA stages L11 (and the reciprocals of its diagonal) in shared memory for the panel solve
         for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
             const int i = e / b, k = e % b;
             D[i][k] = __ldcg(A + (int64_t)(j0 + i) * r + j0 + k);
         }
+        __syncthreads();
+        if (threadIdx.x < b) s_rcp[threadIdx.x] = 1.0 / D[threadIdx.x][threadIdx.x];
         __syncthreads();
         for (int64_t i = j0 + b + gtid; i < r; i += nthr) {
             double x[CHB];
@@ -896,20 +901,30 @@ __global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
             for (int k = 0; k < b; ++k) {
                 double s = x[k];
                 for (int l = 0; l < k; ++l) s -= x[l] * D[k][l];
-                x[k] = s / D[k][k];
+                x[k] = s * s_rcp[k];
             }
             for (int k = 0; k < b; ++k) __stcg(A + i * r + j0 + k, x[k]);
         }
-        if (!group_barrier(st, nb)) return;
+        if (!count_barrier(st, ++epoch * nb)) return;
         const int64_t n2 = r - j0 - b;
         for (int64_t e = gtid; e < n2 * n2; e += nthr) {
             const int64_t i = j0 + b + e / n2, k = j0 + b + e % n2;
             if (k > i) continue;
-            double s = __ldcg(A + i * r + k);
-            for (int l = 0; l < b; ++l) s -= __ldcg(A + i * r + j0 + l) * __ldcg(A + k * r + j0 + l);
-            __stcg(A + i * r + k, s);
+            // four partial sums: the loads of a row pair are independent and overlap in L2
+            const double* ai = A + i * r + j0;
+            const double* ak = A + k * r + j0;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int l = 0;
+            for (; l + 3 < b; l += 4) {
+                s0 = fma(__ldcg(ai + l), __ldcg(ak + l), s0);
+                s1 = fma(__ldcg(ai + l + 1), __ldcg(ak + l + 1), s1);
+                s2 = fma(__ldcg(ai + l + 2), __ldcg(ak + l + 2), s2);
+                s3 = fma(__ldcg(ai + l + 3), __ldcg(ak + l + 3), s3);
+            }
+            for (; l < b; ++l) s0 = fma(__ldcg(ai + l), __ldcg(ak + l), s0);
+            __stcg(A + i * r + k, __ldcg(A + i * r + k) - ((s0 + s1) + (s2 + s3)));
         }
-        if (!group_barrier(st, nb)) return;
+        if (!count_barrier(st, ++epoch * nb)) return;
     }
     // Li: zero the strict upper part, invert the diagonal blocks (one CTA each)
     for (int64_t e = gtid; e < (int64_t)r * r; e += nthr) {
@@ -939,7 +954,7 @@ __global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
         }
         __syncthreads();
     }
-    if (!group_barrier(st, nb)) return;
+    if (!count_barrier(st, ++epoch * nb)) return;
     // block rows I = 1..: Li[I][J] = -inv(L_II) sum_{K=J}^{I-1} L[I][K] Li[K][J]
     for (int I = 1; I < nbk; ++I) {
         const int i0 = I * CHB, bi = min(CHB, r - i0);
@@ -947,11 +962,20 @@ __global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
         for (int64_t e = gtid; e < (int64_t)bi * i0; e += nthr) {
             const int ii = (int)(e / i0), jj = (int)(e % i0);   // row i0+ii, column jj < i0
             const int J = jj / CHB;
-            double s = 0.0;
-            for (int kk = J * CHB; kk < i0; ++kk) s += __ldcg(A + (int64_t)(i0 + ii) * r + kk) * __ldcg(Li + (int64_t)kk * r + jj);
-            __stcg(Li + (int64_t)(i0 + ii) * r + jj, s);
+            // four partial sums: independent loads in flight
+            const double* ar = A + (int64_t)(i0 + ii) * r;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int kk = J * CHB;
+            for (; kk + 3 < i0; kk += 4) {
+                s0 = fma(__ldcg(ar + kk), __ldcg(Li + (int64_t)kk * r + jj), s0);
+                s1 = fma(__ldcg(ar + kk + 1), __ldcg(Li + (int64_t)(kk + 1) * r + jj), s1);
+                s2 = fma(__ldcg(ar + kk + 2), __ldcg(Li + (int64_t)(kk + 2) * r + jj), s2);
+                s3 = fma(__ldcg(ar + kk + 3), __ldcg(Li + (int64_t)(kk + 3) * r + jj), s3);
+            }
+            for (; kk < i0; ++kk) s0 = fma(__ldcg(ar + kk), __ldcg(Li + (int64_t)kk * r + jj), s0);
+            __stcg(Li + (int64_t)(i0 + ii) * r + jj, (s0 + s1) + (s2 + s3));
         }
-        if (!group_barrier(st, nb)) return;
+        if (!count_barrier(st, ++epoch * nb)) return;
         for (int64_t e = gtid; e < (int64_t)bi * i0; e += nthr) {
             const int ii = (int)(e / i0), jj = (int)(e % i0);
             double s = 0.0;
@@ -960,12 +984,12 @@ __global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
             // result for (ii, jj) reads column jj of S rows <= ii: write to a staging slot
             __stcg(A + (int64_t)(i0 + ii) * r + jj, s);   // the strict lower block part of A is no longer needed
         }
-        if (!group_barrier(st, nb)) return;
+        if (!count_barrier(st, ++epoch * nb)) return;
         for (int64_t e = gtid; e < (int64_t)bi * i0; e += nthr) {
             const int ii = (int)(e / i0), jj = (int)(e % i0);
             __stcg(Li + (int64_t)(i0 + ii) * r + jj, __ldcg(A + (int64_t)(i0 + ii) * r + jj));
         }
-        if (!group_barrier(st, nb)) return;
+        if (!count_barrier(st, ++epoch * nb)) return;
     }
 }
 
@@ -1283,6 +1307,8 @@ cudaError_t launch_chol_inv_multi(const CholJob* jobs, int njobs, int num_sms, c
         for (int m = 0; m < nj; ++m) {
             const CholJob& J = jobs[j0 + m];
             hm[m] = CholMode{J.A, J.Li, J.st, J.r, cta, nc[m], J.gate};
+            cudaError_t e0 = cudaMemsetAsync(&J.st->arrive, 0, sizeof(unsigned int), st);
+            if (e0 != cudaSuccess) return e0;
             cta += nc[m];
         }
         CholMode* dm = nullptr;
