@@ -159,6 +159,15 @@ typedef struct {
  * |B_hat| = (sum_s ||B_s||^2)^(1/2) and info->bound_abs the Thm 4.3 bound
  * |B_hat| sum_l d_l. Not with LS_FLAG_SVD_GRAM. */
 #define LS_FLAG_TUCKER_REF 8
+/* LS_FLAG_CACHE_GENVEC: keep the reference vectors g_q (Sec. 2.2: computed once and
+ * stored for repeated use) in a process-wide device cache keyed by everything they
+ * depend on (device, N, the grid step, R, sinc step, t-scale, kernel family, kappa,
+ * collocated or Galerkin entries; the doubles compared bit for bit). A context created
+ * with the flag copies them from the cache (device to device) when the key is present
+ * and adds them when it is not. The cache holds up to 8 entries (the oldest is freed
+ * first) until lattice_sum_cache_clear or process exit. Results do not change: the
+ * cached vectors are the bytes the kernel wrote. */
+#define LS_FLAG_CACHE_GENVEC 16
 
 #define LS_KERNEL_YUKAWA 0
 #define LS_KERNEL_SLATER 1
@@ -559,6 +568,13 @@ int lattice_sum_eval_slab_noalloc(const double* Z0, const double* Z1, const doub
 
 /* Frees every device buffer of the context (stream-ordered) and the context. */
 void lattice_sum_destroy(ls_ctx* ctx);
+
+/* lattice_sum_cache_clear -- frees the entries of the reference-vector cache
+ * (LS_FLAG_CACHE_GENVEC) on every device and returns how many there were (>= 0),
+ * or LS_ERR_CUDA. It synchronises the device of each entry (cudaFree); contexts keep
+ * their own copies and are not affected. Not to be called while another thread
+ * creates a context with the flag. */
+int lattice_sum_cache_clear(void);
 
 /* Message of the last failed call on ctx ("" if none); ctx may be NULL for
  * failures of lattice_sum_create. The string lives until the next call. */

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <deque>
 #include <atomic>
 #include <mutex>
 #include <map>
@@ -387,7 +388,30 @@ void count_h2d(int64_t n) { tracer().h2d += n; }
 void count_d2h(int64_t n) { tracer().d2h += n; }
 void set_global_error(const char* msg) { g_create_error = msg; }
 
+// The reference-vector cache (LS_FLAG_CACHE_GENVEC): the inputs of k_genvec, bit for bit,
+// and the vectors it wrote, in device memory owned by the cache (cudaMalloc: the entries
+// outlive every context and stream). FIFO of at most kGenvecCacheMax entries.
+struct GenvecKey {
+    int dev; int64_t N; double h; int R; double sinc_step, t_scale; int kernel; double kappa; int galerkin;
+    bool operator==(const GenvecKey& o) const {
+        return dev == o.dev && N == o.N && memcmp(&h, &o.h, 8) == 0 && R == o.R &&
+               memcmp(&sinc_step, &o.sinc_step, 8) == 0 && memcmp(&t_scale, &o.t_scale, 8) == 0 &&
+               kernel == o.kernel && memcmp(&kappa, &o.kappa, 8) == 0 && galerkin == o.galerkin;
+    }
+};
+struct GenvecEntry {
+    GenvecKey key;
+    double* d;
+};
+constexpr size_t kGenvecCacheMax = 8;
+std::mutex g_genvec_mu;
+std::deque<GenvecEntry>& genvec_cache() {
+    static std::deque<GenvecEntry>* c = new std::deque<GenvecEntry>();
+    return *c;
+}
+
 Scope::Scope(const char* n, cudaStream_t s) : name(n), st(s) {
+    nvtxRangePushA(n);
     Tracer& t = tracer();
     if (!t.on) return;
     std::lock_guard<std::mutex> g(t.mu);
@@ -397,6 +421,7 @@ Scope::Scope(const char* n, cudaStream_t s) : name(n), st(s) {
 }
 
 Scope::~Scope() {
+    nvtxRangePop();
     if (!a) return;
     Tracer& t = tracer();
     std::lock_guard<std::mutex> g(t.mu);
@@ -452,6 +477,7 @@ int lattice_sum_fit_t_scale_kernel(int32_t R, double sinc_step, int32_t kernel, 
 
 int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* blocks, int32_t nblocks,
                        void* stream) {
+    ls::NvtxRange nvtx_("lattice_sum_create");
     ls_ctx* ctx = nullptr;
     if (!out || !params || !blocks || nblocks < 1) return fail(ctx, LS_ERR_ARG, "create: NULL argument or no block");
     *out = nullptr;
@@ -461,7 +487,8 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
     if (p.R < 1 || p.R > 64) return fail(ctx, LS_ERR_ARG, "create: R=%d out of range [1,64]", p.R);
     if (!(p.sinc_step > 0) || !(p.t_scale > 0)) return fail(ctx, LS_ERR_ARG, "create: sinc_step and t_scale must be > 0");
     if (p.precision != LS_FP64 && p.precision != LS_MIXED) return fail(ctx, LS_ERR_ARG, "create: unknown precision %d", p.precision);
-    if ((p.flags & ~(LS_FLAG_GALERKIN | LS_FLAG_SVD_GRAM | LS_FLAG_SVD_ONESIDED | LS_FLAG_TUCKER_REF)) != 0)
+    if ((p.flags & ~(LS_FLAG_GALERKIN | LS_FLAG_SVD_GRAM | LS_FLAG_SVD_ONESIDED | LS_FLAG_TUCKER_REF |
+                     LS_FLAG_CACHE_GENVEC)) != 0)
         return fail(ctx, LS_ERR_ARG, "create: unknown flags 0x%x", p.flags);
     if ((p.flags & LS_FLAG_TUCKER_REF) && !(p.ref_eps > 0.0 && p.ref_eps < 1.0))
         return fail(ctx, LS_ERR_ARG, "create: LS_FLAG_TUCKER_REF needs 0 < ref_eps < 1");
@@ -515,8 +542,39 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
     {
         cudaError_t e2 = dalloc(ctx, &ctx->d_g, (int64_t)R * 2 * N);
         Scope sc_gen("genvec", ctx->st);
-        if (e2 == cudaSuccess) e2 = launch_genvec(ctx->d_g, R, N, ctx->h, p.sinc_step, p.t_scale, p.kernel, p.kappa,
-                                                      (p.flags & LS_FLAG_GALERKIN) != 0, ctx->st);
+        const size_t gbytes = sizeof(double) * (size_t)R * 2 * N;
+        const GenvecKey key{dev, N, ctx->h, R, p.sinc_step, p.t_scale, p.kernel, p.kappa,
+                            (p.flags & LS_FLAG_GALERKIN) ? 1 : 0};
+        bool hit = false;
+        if (e2 == cudaSuccess && (p.flags & LS_FLAG_CACHE_GENVEC)) {
+            std::lock_guard<std::mutex> g(g_genvec_mu);
+            for (const GenvecEntry& c : genvec_cache())
+                if (c.key == key) {
+                    e2 = cudaMemcpyAsync(ctx->d_g, c.d, gbytes, cudaMemcpyDeviceToDevice, ctx->st);
+                    hit = true;
+                    break;
+                }
+        }
+        if (e2 == cudaSuccess && !hit) {
+            e2 = launch_genvec(ctx->d_g, R, N, ctx->h, p.sinc_step, p.t_scale, p.kernel, p.kappa,
+                               (p.flags & LS_FLAG_GALERKIN) != 0, ctx->st);
+            if (e2 == cudaSuccess && (p.flags & LS_FLAG_CACHE_GENVEC)) {
+                // a new entry (the oldest goes once the cache is full); cudaFree of the evicted
+                // buffer waits for the device, so no copy from it is still pending
+                std::lock_guard<std::mutex> g(g_genvec_mu);
+                std::deque<GenvecEntry>& cache = genvec_cache();
+                if (cache.size() >= kGenvecCacheMax) {
+                    cudaFree(cache.front().d);
+                    cache.pop_front();
+                }
+                double* d = nullptr;
+                e2 = cudaMalloc(&d, gbytes);
+                if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(d, ctx->d_g, gbytes, cudaMemcpyDeviceToDevice, ctx->st);
+                if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(ctx->st);   // the entry is complete before others read it
+                if (e2 == cudaSuccess) cache.push_back(GenvecEntry{key, d});
+                else if (d) cudaFree(d);
+            }
+        }
         if (e2 != cudaSuccess)
             rc = fail(ctx, e2 == cudaErrorMemoryAllocation ? LS_ERR_OOM : LS_ERR_CUDA, "create: %s", cudaGetErrorString(e2));
     }
@@ -563,6 +621,7 @@ int lattice_sum_create(ls_ctx** out, const ls_params* params, const ls_block* bl
 }
 
 int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n) {
+    ls::NvtxRange nvtx_("lattice_sum_add_defects");
     if (!ctx) return fail(nullptr, LS_ERR_ARG, "add_defects: NULL context");
     if (ctx->reduced) return fail(ctx, LS_ERR_STATE, "add_defects: context already reduced");
     if (n < 0 || (n > 0 && !defects)) return fail(ctx, LS_ERR_ARG, "add_defects: bad defect array");
@@ -1880,6 +1939,7 @@ int reduce_tucker(ls_ctx* ctx, double eps, const int32_t* forced, ls_tucker_info
 extern "C" {
 
 int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ranks, ls_tucker_info* info) {
+    ls::NvtxRange nvtx_("lattice_sum_rhosvd_reduce");
     if (!ctx) return fail(nullptr, LS_ERR_ARG, "rhosvd_reduce: NULL context");
     if (ctx->reduced) return fail(ctx, LS_ERR_STATE, "rhosvd_reduce: already reduced");
     if (!forced_ranks && !(eps > 0.0)) return fail(ctx, LS_ERR_ARG, "rhosvd_reduce: eps must be > 0");
@@ -1904,6 +1964,7 @@ int lattice_sum_rhosvd_reduce(ls_ctx* ctx, double eps, const int32_t* forced_ran
 }
 
 int lattice_sum_batch_reduce(ls_ctx* const* ctxs, int32_t n, double eps, ls_tucker_info* infos) {
+    ls::NvtxRange nvtx_("lattice_sum_batch_reduce");
     if (!ctxs || n < 1) return fail(nullptr, LS_ERR_ARG, "batch_reduce: no contexts");
     if (!(eps > 0.0)) return fail(nullptr, LS_ERR_ARG, "batch_reduce: eps must be > 0");
     for (int i = 0; i < n; ++i) {
@@ -2103,11 +2164,13 @@ int eval_impl(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev,
 extern "C" {
 
 int lattice_sum_eval_slab(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev, int32_t out_dtype) {
+    ls::NvtxRange nvtx_("lattice_sum_eval_slab");
     return eval_impl(ctx, z_index, nslab, out_dev, out_dtype, nullptr);
 }
 
 int lattice_sum_tune_eval(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, void* out_dev, int32_t out_dtype,
                           char* report, int64_t cap) {
+    ls::NvtxRange nvtx_("lattice_sum_tune_eval");
     if (!ctx) return fail(nullptr, LS_ERR_ARG, "tune_eval: NULL context");
     if (ctx->p.precision != LS_MIXED) return fail(ctx, LS_ERR_ARG, "tune_eval: the FP64 path has no tile widths to tune");
     if (cap < 0 || (cap > 0 && !report)) return fail(ctx, LS_ERR_ARG, "tune_eval: bad report buffer");
@@ -2124,6 +2187,7 @@ int lattice_sum_tune_eval(ls_ctx* ctx, const int64_t* z_index, int32_t nslab, vo
 }
 
 int lattice_sum_als_refine(ls_ctx* ctx, int32_t sweeps, double* history, ls_tucker_info* info) {
+    ls::NvtxRange nvtx_("lattice_sum_als_refine");
     if (!ctx) return fail(nullptr, LS_ERR_ARG, "als_refine: NULL context");
     if (!ctx->reduced) return fail(ctx, LS_ERR_STATE, "als_refine: call rhosvd_reduce first");
     if (sweeps < 0 || sweeps > 100) return fail(ctx, LS_ERR_ARG, "als_refine: sweeps out of range [0, 100]");
@@ -2292,6 +2356,7 @@ int lattice_sum_als_refine(ls_ctx* ctx, int32_t sweeps, double* history, ls_tuck
 }
 
 int lattice_sum_galerkin(ls_ctx* ctx, const double* const* basis, int32_t nb, double* V) {
+    ls::NvtxRange nvtx_("lattice_sum_galerkin");
     if (!ctx) return fail(nullptr, LS_ERR_ARG, "galerkin: NULL context");
     if (!ctx->reduced) return fail(ctx, LS_ERR_STATE, "galerkin: call rhosvd_reduce first");
     if (!basis || !basis[0] || !basis[1] || !basis[2] || nb < 1 || nb > 65535 || !V)
@@ -2458,6 +2523,22 @@ void lattice_sum_destroy(ls_ctx* ctx) {
     for (void* p : ctx->allocs) cudaFreeAsync(p, ctx->st);
     ctx->allocs.clear();
     delete ctx;
+}
+
+int lattice_sum_cache_clear(void) {
+    std::lock_guard<std::mutex> g(ls::g_genvec_mu);
+    std::deque<ls::GenvecEntry>& cache = ls::genvec_cache();
+    const int n = (int)cache.size();
+    int dev0 = -1;
+    cudaGetDevice(&dev0);
+    bool ok = true;
+    for (const ls::GenvecEntry& c : cache) {
+        ok = ok && cudaSetDevice(c.key.dev) == cudaSuccess && cudaFree(c.d) == cudaSuccess;
+    }
+    cache.clear();
+    if (dev0 >= 0) cudaSetDevice(dev0);
+    if (!ok) return fail(nullptr, LS_ERR_CUDA, "cache_clear: cudaFree failed");
+    return n;
 }
 
 const char* lattice_sum_last_error(const ls_ctx* ctx) {

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lattice_sum.h"
 
 namespace ls {
@@ -41,8 +43,19 @@ void count_kernels(int n);
 void count_h2d(int64_t n);
 void count_d2h(int64_t n);
 
+// An NVTX range for the lifetime of the object (ABI calls and pipeline steps): a
+// timeline tool (Nsight Systems, ncu's NVTX filters) shows them by name; without a
+// tool attached the calls return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Records a CUDA-event pair around a step on a stream while tracing is on
-// (lattice_sum_profile); the pairs are reported by name.
+// (lattice_sum_profile); the pairs are reported by name. Every step is also an
+// NVTX range.
 struct Scope {
     const char* name;
     cudaStream_t st;

@@ -22,6 +22,7 @@ LS_FLAG_GALERKIN = 1   # reference vectors as cell averages (Eq. galten) instead
 LS_FLAG_SVD_GRAM = 2       # singular values from the FP64 Gram matrix (default of LS_MIXED)
 LS_FLAG_SVD_ONESIDED = 4   # singular values without squaring (default of LS_FP64)
 LS_FLAG_TUCKER_REF = 8     # Tucker-reference variant (Thm 3.1(B), Thm 4.3), threshold ref_eps
+LS_FLAG_CACHE_GENVEC = 16  # reference vectors from / into the process-wide device cache
 LS_KERNEL_YUKAWA, LS_KERNEL_SLATER, LS_KERNEL_DIPOLE = 0, 1, 2   # exp(-kappa r)/r (1/r at kappa = 0), exp(-kappa r), 1/r^3
 LS_DEFECT_SITES, LS_DEFECT_POINT = 0, 1
 LS_OUT_F64, LS_OUT_F32 = 0, 1
@@ -34,7 +35,7 @@ EXPORTED = ("lattice_sum_fit_t_scale", "lattice_sum_fit_t_scale_kernel", "lattic
             "lattice_sum_eval_slab_noalloc", "lattice_sum_batch_reduce", "lattice_sum_gemm_nt",
             "lattice_sum_gemm_nt_mixed", "lattice_sum_jacobi_eig", "lattice_sum_svd_rows", "lattice_sum_tune_eval",
             "lattice_sum_test_fail_alloc", "lattice_sum_test_bounded_wait", "lattice_sum_galerkin",
-            "lattice_sum_als_refine", "lattice_sum_destroy",
+            "lattice_sum_als_refine", "lattice_sum_cache_clear", "lattice_sum_destroy",
             "lattice_sum_last_error")
 
 
@@ -104,6 +105,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lattice_sum_test_bounded_wait.argtypes = [C.c_int32, C.c_int64, C.c_void_p]
     lib.lattice_sum_svd_rows.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_int32, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.lattice_sum_cache_clear.argtypes = []
     lib.lattice_sum_destroy.argtypes = [C.c_void_p]
     lib.lattice_sum_destroy.restype = None
     lib.lattice_sum_last_error.argtypes = [C.c_void_p]
@@ -155,6 +157,14 @@ def eval_slab_noalloc(Z, core, ranks, N, z_index, out_ptr, out_dtype=LS_OUT_F64,
                                                C.c_void_p(core), r, int(N), z, len(z_index),
                                                C.c_void_p(out_ptr), out_dtype,
                                                C.c_void_p(stream) if stream else None))
+
+
+def cache_clear() -> int:
+    """lattice_sum_cache_clear: frees the reference-vector cache; returns the entries freed."""
+    rc = lib().lattice_sum_cache_clear()
+    if rc < 0:
+        _check(rc)
+    return rc
 
 
 def batch_reduce(contexts, eps: float):
@@ -308,6 +318,10 @@ class LatticeSum:
         self.ctx = ctx
         self.N = int(N)
         self.info = None
+        # what the context was created from (a checkpoint records it)
+        self.params = {"N": int(N), "box_lo": float(box_lo), "box_hi": float(box_hi), "R": int(R),
+                       "sinc_step": float(sinc_step), "t_scale": float(t_scale), "precision": int(precision),
+                       "flags": int(p.flags), "kappa": float(kappa), "kernel": int(kernel), "ref_eps": float(ref_eps)}
 
     @classmethod
     def from_workload(cls, wl, t_scale, precision=LS_FP64, stream=None, flags=0, ref_eps=0.0):
@@ -391,6 +405,24 @@ class LatticeSum:
         _check(self._lib.lattice_sum_get_factors(self.ctx, Z, C.byref(core), r), self.ctx)
         return [Z[i] for i in range(3)], core.value, list(r)
 
+    def save(self, path: str, extra: Optional[dict] = None):
+        """Checkpoint of a reduced context as a .npz file: the Tucker vectors Z_l ([r_l][N] each),
+        the core ([r0][r1][r2]), the ranks, the singular values of each mode, the creation
+        parameters and the reduction's info (JSON), and `extra` (JSON) if given. Everything is
+        read back through lattice_sum_read; load_checkpoint restores it."""
+        import json
+        if self.info is None:
+            raise LatticeSumError(LS_ERR_STATE, "save: the context is not reduced")
+        ranks = [int(x) for x in self.info["r"]]
+        arrays = {f"Z{l}": self.read(LS_READ_BASIS, l).reshape(ranks[l], self.N) for l in range(3)}
+        arrays["core"] = self.read(LS_READ_CORE).reshape(ranks)
+        for l in range(3):
+            arrays[f"sigma{l}"] = self.read(LS_READ_SIGMA, l)
+        arrays["ranks"] = np.asarray(ranks, dtype=np.int32)
+        meta = {"format": "lattice_sum.tucker.v1", "params": self.params, "info": self.info, "extra": extra or {}}
+        arrays["meta"] = np.frombuffer(json.dumps(meta).encode(), dtype=np.uint8)
+        np.savez(path, **arrays)
+
     def close(self):
         if getattr(self, "ctx", None):
             self._lib.lattice_sum_destroy(self.ctx)
@@ -407,3 +439,52 @@ class LatticeSum:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Checkpoint:
+    """A Tucker result restored from LatticeSum.save: Z (three [r_l][N] arrays), core
+    ([r0][r1][r2]), ranks, sigma (per mode), params, info and extra (dicts). Its slabs are
+    evaluated on the GPU from device copies of the factors (eval_slab_torch)."""
+
+    def __init__(self, arrays, meta):
+        self.Z = [np.ascontiguousarray(arrays[f"Z{l}"]) for l in range(3)]
+        self.core = np.ascontiguousarray(arrays["core"])
+        self.ranks = [int(x) for x in arrays["ranks"]]
+        self.sigma = [arrays[f"sigma{l}"] for l in range(3)]
+        self.params = meta["params"]
+        self.info = meta["info"]
+        self.extra = meta.get("extra", {})
+        self.N = int(self.params["N"])
+        self._dev = None
+
+    def device_factors(self):
+        """The factors as float64 CUDA tensors (made once): ([Z0, Z1, Z2], core)."""
+        import torch
+        if self._dev is None:
+            self._dev = ([torch.from_numpy(z).cuda() for z in self.Z], torch.from_numpy(self.core).cuda())
+        return self._dev
+
+    def eval_slab_torch(self, z_index, dtype=None, out=None):
+        """Slabs z_index of the restored Tucker tensor (len x N x N, float64 or float32 CUDA
+        tensor), through lattice_sum_eval_slab_noalloc on the device copies of the factors;
+        its scratch limit applies (one slab's r0 (r1 + N) doubles)."""
+        import torch
+        dtype = dtype or torch.float64
+        Z, core = self.device_factors()
+        if out is None:
+            out = torch.empty((len(z_index), self.N, self.N), dtype=dtype, device="cuda")
+        eval_slab_noalloc([z.data_ptr() for z in Z], core.data_ptr(), self.ranks, self.N, z_index, out.data_ptr(),
+                          LS_OUT_F32 if dtype == torch.float32 else LS_OUT_F64,
+                          torch.cuda.current_stream().cuda_stream)
+        return out
+
+
+def load_checkpoint(path: str) -> Checkpoint:
+    """Restores a checkpoint written by LatticeSum.save."""
+    import json
+    with np.load(path) as f:
+        arrays = {k: f[k] for k in f.files}
+    meta = json.loads(arrays.pop("meta").tobytes().decode())
+    if meta.get("format") != "lattice_sum.tucker.v1":
+        raise ValueError(f"{path}: not a lattice-sum Tucker checkpoint")
+    return Checkpoint(arrays, meta)

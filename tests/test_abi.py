@@ -107,14 +107,14 @@ def test_create_validates_arguments_on_host(lib, bad):
 
 
 def test_create_rejects_unknown_flags(lib):
-    """LS_FLAG_GALERKIN, LS_FLAG_SVD_GRAM, LS_FLAG_SVD_ONESIDED and
-    LS_FLAG_TUCKER_REF are the known flags; the two singular-value routes
+    """LS_FLAG_GALERKIN, LS_FLAG_SVD_GRAM, LS_FLAG_SVD_ONESIDED,
+    LS_FLAG_TUCKER_REF and LS_FLAG_CACHE_GENVEC are the known flags; the two singular-value routes
     exclude each other, the Tucker-reference variant needs 0 < ref_eps < 1 and
     the non-squaring route; anything else is refused on the host before the
     device is touched."""
     import ctypes as C
     blocks = L.make_blocks([W.centred_block((2, 2, 2))])
-    for flags, ref_eps in ((L.LS_FLAG_SVD_GRAM | L.LS_FLAG_SVD_ONESIDED, 0.0), (16, 0.0), (0x100, 0.0), (-1, 0.0),
+    for flags, ref_eps in ((L.LS_FLAG_SVD_GRAM | L.LS_FLAG_SVD_ONESIDED, 0.0), (32, 0.0), (0x100, 0.0), (-1, 0.0),
                            (L.LS_FLAG_TUCKER_REF, 0.0), (L.LS_FLAG_TUCKER_REF, 1.5),
                            (L.LS_FLAG_TUCKER_REF | L.LS_FLAG_SVD_GRAM, 1e-6)):
         p = L.ls_params(64, -6.0, 6.0, 8, 0.25, 10.0, L.LS_FP64, flags, 0.0, L.LS_KERNEL_YUKAWA, ref_eps)
