@@ -379,6 +379,20 @@ class LatticeSum:
                                           None), self.ctx)
         return arr
 
+    def read_into(self, what: int, mode: int, out) -> int:
+        """lattice_sum_read into a caller-owned host array (numpy, or a CPU torch tensor, e.g. in
+        pinned memory so that the copy runs at the link's DMA rate); returns the bytes read."""
+        need = C.c_int64()
+        _check(self._lib.lattice_sum_read(self.ctx, what, mode, None, 0, C.byref(need)), self.ctx)
+        if hasattr(out, "data_ptr"):
+            ptr, size = out.data_ptr(), out.numel() * out.element_size()
+        else:
+            ptr, size = out.ctypes.data, out.nbytes
+        if size < need.value:
+            raise LatticeSumError(LS_ERR_ARG, f"read_into: {size} bytes given, {need.value} needed")
+        _check(self._lib.lattice_sum_read(self.ctx, what, mode, C.c_void_p(ptr), need.value, None), self.ctx)
+        return need.value
+
     def als_refine(self, sweeps: int):
         """lattice_sum_als_refine: returns (history of ||core|| (sweeps + 1 values), info)."""
         hist = (C.c_double * (int(sweeps) + 1))()

@@ -53,6 +53,12 @@ def test_checkpoint_round_trip(wl, tmp_path):
         assert np.array_equal(ck.Z[l], ls.read(L.LS_READ_BASIS, l).reshape(ck.ranks[l], w.N))
         assert np.array_equal(ck.sigma[l], ls.read(L.LS_READ_SIGMA, l))
     assert np.array_equal(ck.core.ravel(), ls.read(L.LS_READ_CORE))
+    # the same read into a caller's pinned buffer (what the e2e timing does)
+    pinned = torch.empty(int(np.prod(ck.ranks)), dtype=torch.float64, pin_memory=True)
+    assert ls.read_into(L.LS_READ_CORE, 0, pinned) == pinned.numel() * 8
+    assert np.array_equal(pinned.numpy(), ck.core.ravel())
+    with pytest.raises(L.LatticeSumError):
+        ls.read_into(L.LS_READ_CORE, 0, torch.empty(3, dtype=torch.float64))
     zs = [0, 5, w.N // 2, w.N - 1]
     ref = ls.eval_slab_torch(zs).cpu().numpy()
     got = ck.eval_slab_torch(zs)
