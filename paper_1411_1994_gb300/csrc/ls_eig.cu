@@ -797,28 +797,32 @@ __global__ void __launch_bounds__(kEigThreads) k_chol32_multi(const CholJob* job
 // ---------------------------------------------------------------------------
 // The same block Jacobi for matrices beyond one CTA's shared memory: one
 // cooperative grid for every matrix of the launch, D (hi/lo FP32), E (FP32,
-// full symmetric storage), the rotation accumulator F and the pair-block
-// rotations Q in global memory (L2-resident: about 2 MB a matrix at k = 512).
-// A round runs in two phases between bounded counting barriers:
-//   A: a warp per pair-block loads its 16 x 16 diagonal block and 16 diagonal
-//      entries into registers, runs the inner sweep exactly as the cluster
-//      kernel does (the same function), and writes back the block, D and F_Q;
-//      the other warps meanwhile apply the previous round's rotations to F
-//      (F <- F + F_Q + F F_Q, a half-warp per pair-block and group of 16 rows,
-//      a lane per row): F never feeds back into the iteration, so its update
-//      waits one round and leaves the critical path;
-//   B: a half-warp per off-diagonal tile of two pair-blocks of which one
-//      rotated (E_ab <- Q_a^T E_ab Q_b, both triangles).
-// Q and the pair-blocks' rotation flags are double-buffered by round parity
-// for the deferred F update. Warps are numbered across the CTAs first, so the
-// few inner sweeps of a round run on different SMs. Matrices of different
-// sizes keep their own round and sweep counters. A matrix stops after a sweep
-// in which no pair qualified, or at the sweep limit. The decision is read by
-// every CTA from the same counter after the same barrier, so control flow
-// stays uniform. The outputs and the sweep report are those of the cluster
-// kernel. For the same input it gives the same result, with one more sweep
-// reported: that sweep is the empty one that confirms convergence, where the
-// cluster kernel scans instead.
+// full symmetric storage, three buffers by round), the rotation accumulator F
+// and the pair-block rotations Q (two buffers by round) in global memory
+// (L2-resident: a few MB a matrix at k = 512). One phase a round, between
+// bounded counting barriers:
+//   - a warp per pair-block of round g (warp 0 of different SMs) forms its
+//     16 x 16 diagonal block of the state after round g - 1: the two diagonal
+//     8 x 8 blocks as round g - 1's inner sweeps left them (buffer g mod 3),
+//     the cross block from round g - 1's tile of the two pair-blocks that held
+//     them (buffer g - 1 mod 3) and that round's rotations, by the tile
+//     product's own arithmetic; it runs the inner sweep exactly as the cluster
+//     kernel does (the same function) and writes the block to buffer g + 1
+//     mod 3, D and F_Q;
+//   - meanwhile the other warps rotate round g - 1's tiles (E_ab <- Q_a^T E_ab
+//     Q_b, both triangles; a half-warp each, operands staged in shared memory)
+//     from buffer g - 1 mod 3 into buffer g mod 3, copying those of pair-blocks
+//     that did not rotate by the same arithmetic with Q = I, and apply round
+//     g - 1's rotations to F (F <- F + F_Q + F F_Q, a half-warp per pair-block
+//     and group of 16 rows, a lane per row).
+// So a round costs one barrier and its inner sweeps, with the tiles off the
+// critical path. Matrices of different sizes keep their own round and sweep
+// counters. A matrix stops after a sweep in which no pair qualified, or at the
+// sweep limit. The decision is read by every CTA from the same counter after
+// the same barrier, so control flow stays uniform. The outputs and the sweep
+// report are those of the cluster kernel. For the same input it gives the same
+// result, with one more sweep reported: that sweep is the empty one that
+// confirms convergence, where the cluster kernel scans instead.
 // ---------------------------------------------------------------------------
 constexpr int kGbThreads = 512;
 constexpr int kGbMaxModes = 128;
@@ -828,7 +832,8 @@ struct GbMode {
     int64_t ldd; int k; int add_identity;
     float floor, tau, tol2;
     int K, ldE, nb, m;
-    // Q [2][nb][16 x 16] and act [2][nb]: round parity; cnt[2]: rotations a sweep (sweep parity)
+    // E [3][K][ldE]: round mod 3; Q [2][nb][16 x 16] and act [2][nb]: round parity; cnt[3]:
+    // rotations a sweep (sweep mod 3)
     DF* D; float* E; float* F; float* Q; int* act; unsigned int* cnt;
 };
 struct GbArgs {
@@ -891,24 +896,41 @@ __device__ __forceinline__ void gb_f_rows(const GbMode& J, int round, const floa
     __syncwarp(half);   // every lane has read sq before the next item stages its F_Q
 }
 
+// pair-block of round t holding block X (blocks of BJ indices, m of them) and whether X is its
+// second half (the larger block index): the inverse of rr_pair_e
+__device__ __forceinline__ void rr_block_of(int t, int X, int m, int& i, int& second) {
+    const int n1 = m - 1, nb = m / 2;
+    if (X == n1) { i = 0; second = 1; return; }
+    if (X == t) { i = 0; second = 0; return; }
+    const int dd = (X - t + n1) % n1;
+    int a, b;
+    if (dd <= nb - 1) { i = dd; a = X; b = (t - dd + n1) % n1; }
+    else { i = n1 - dd; a = (t + i) % n1; b = X; }
+    second = X == max(a, b) ? 1 : 0;
+}
+
 __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
     __shared__ int s_sweep[kGbMaxModes], s_round[kGbMaxModes], s_done[kGbMaxModes], s_base[kGbMaxModes];
-    __shared__ int s_gr[kGbMaxModes];   // rounds run: the parity of Q and act
-    __shared__ int s_fr[kGbMaxModes];   // round whose F update is pending (-1: none) ...
-    __shared__ int s_fp[kGbMaxModes];   // ... and its buffer parity
+    __shared__ int s_gr[kGbMaxModes];   // global index of the matrix's next round (its A phase)
+    __shared__ int s_ran[kGbMaxModes];  // this phase runs the matrix's next round
+    __shared__ int s_pr[kGbMaxModes];   // round (within its sweep) whose tiles and F update are pending, -1: none
+    __shared__ int s_pg[kGbMaxModes];   // its global index
     __shared__ int s_pa[kGbMaxModes + 1], s_pt[kGbMaxModes + 1], s_pf[kGbMaxModes + 1];
     __shared__ int s_live;
-    // per half-warp: F_Q of an F item (phase A) or E_ab, Q_a, Q_b of a tile (phase B)
+    // per half-warp: F_Q of an F item, E_ab, Q_a, Q_b of a tile, or (the inner sweeps' warps) the
+    // previous round's tile, its rotations and the cross block they give
     extern __shared__ __align__(16) float gb_smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nwarp_cta = kGbThreads / 32;
     const int slot = warp * gridDim.x + blockIdx.x, nwarps = gridDim.x * nwarp_cta;
-    // the warps in the order 1, 2, 3, 5, ..., 15, then 0, 4, 8, 12 (those of warp 0's SMSP)
-    const int fslot = ((warp & 3) == 0 ? nwarp_cta - nwarp_cta / 4 + (warp >> 2) : warp - 1 - (warp >> 2)) * gridDim.x +
-                      blockIdx.x;
+    // the warps in the order 1, 2, 3, 5, ..., 15, then 4, 8, 12, 0 (warp 0 takes the inner sweeps)
+    const int frank = (warp & 3) == 0 ? (warp == 0 ? nwarp_cta - 1 : nwarp_cta - nwarp_cta / 4 + (warp >> 2) - 1)
+                                      : warp - 1 - (warp >> 2);
+    const int fslot = frank * gridDim.x + blockIdx.x;
     const int h = lane >> 4, l16 = lane & 15;
     const unsigned int half = 0xffffu << (lane & 16);
     float* sq = gb_smem + (size_t)(warp * 2 + h) * 3 * BJ2SQ;
+    float* sw = gb_smem + (size_t)(warp * 2) * 3 * BJ2SQ;   // the whole warp's staging (6 x 256 floats)
     const int nm = A.nm;
     // the job descriptors in shared memory (read in every phase; global reads would miss L1
     // after each barrier's fence)
@@ -922,18 +944,20 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
     }
     unsigned int epoch = 0;
     auto barrier = [&]() { return count_barrier(A.bar, ++epoch * gridDim.x); };
+    auto ebuf = [&](const GbMode& J, int g) { return J.E + (int64_t)(g % 3) * J.K * J.ldE; };
     // half-item fh of the pending F updates (decoded over the matrices with one pending)
     auto f_item = [&](int fh) {
         int j = 0;
-        while (j < nm - 1 && (s_pf[j + 1] <= fh || s_fr[j] < 0)) ++j;
+        while (j < nm - 1 && (s_pf[j + 1] <= fh || s_pr[j] < 0)) ++j;
         const GbMode& J = Ms[j];
         const int rest = fh - s_pf[j], groups = J.K / BJ2;
-        const int a = rest / groups, g = rest - a * groups;
-        if (!J.act[s_fp[j] * J.nb + a]) return;   // uniform over the half-warp
-        gb_f_rows(J, s_fr[j], J.Q + (int64_t)s_fp[j] * J.nb * BJ2SQ, a, g, l16, half, sq);
+        const int a = rest / groups, g = rest - a * groups, par = s_pg[j] & 1;
+        if (!J.act[par * J.nb + a]) return;   // uniform over the half-warp
+        gb_f_rows(J, s_pr[j], J.Q + (int64_t)par * J.nb * BJ2SQ, a, g, l16, half, sq);
     };
 
-    // initial state: D from diag(H), E from the off-diagonal of H, F = 0, counters 0
+    // initial state (buffer 0 = the state before round 0): D from diag(H), E from the
+    // off-diagonal of H, F = 0, counters 0
     for (int j = 0; j < nm; ++j) {
         const GbMode& J = Ms[j];
         const int64_t ne = (int64_t)J.K * J.ldE;
@@ -944,7 +968,7 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
         }
         const int64_t nf = (int64_t)J.K * J.K;
         for (int64_t e = blockIdx.x * (int64_t)kGbThreads + tid; e < nf; e += (int64_t)gridDim.x * kGbThreads) J.F[e] = 0.f;
-        if (blockIdx.x == 0 && tid < 2) J.cnt[tid] = 0;
+        if (blockIdx.x == 0 && tid < 3) J.cnt[tid] = 0;
     }
     if (tid < nm) {
         s_sweep[tid] = 0;
@@ -952,14 +976,19 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
         s_done[tid] = 0;
         s_base[tid] = Ms[tid].st->sweeps;
         s_gr[tid] = 0;
-        s_fr[tid] = -1;
-        s_fp[tid] = 0;
+        s_pr[tid] = -1;
+        s_pg[tid] = 0;
     }
     bool ok = barrier();
 
+    // One phase a round: the inner sweeps of every live matrix's next round g (warp 0 of
+    // different SMs; they read the state after round g - 1: the diagonal blocks from buffer
+    // g % 3, and their cross block from round g - 1's tile in buffer (g - 1) % 3 with that
+    // round's rotations, by the tile product's own arithmetic) beside the tiles and the F
+    // update of round g - 1 (the other warps: buffer (g - 1) % 3 into buffer g % 3, which the
+    // inner sweeps of round g - 1 have already filled with their diagonal blocks). One
+    // barrier a phase.
     while (ok) {
-        // this round's work: prefix counts over the live matrices and the pending F updates
-        // (same in every CTA)
         if (tid == 0) {
             int pa = 0, pt = 0, pf = 0, live = 0;
             for (int j = 0; j < nm; ++j) {
@@ -967,12 +996,13 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                 s_pt[j] = pt;
                 s_pf[j] = pf;
                 const GbMode& J = Ms[j];
-                if (!s_done[j]) {
-                    pa += J.nb;
+                s_ran[j] = !s_done[j];
+                if (s_ran[j]) pa += J.nb;
+                if (s_pr[j] >= 0) {
                     pt += J.nb * (J.nb - 1) / 2;
-                    live = 1;
+                    pf += J.nb * (J.K / BJ2);
                 }
-                if (s_fr[j] >= 0) pf += J.nb * (J.K / BJ2);
+                live |= s_ran[j] || s_pr[j] >= 0;
             }
             s_pa[nm] = pa;
             s_pt[nm] = pt;
@@ -982,37 +1012,123 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
         __syncthreads();
         if (!s_live) break;
 
-        // ---- phase A: inner sweeps, a warp per pair-block; the previous round's F update on
-        // the other warps
-        const int nA = s_pa[nm], nF = s_pf[nm];
+        // ---- inner sweeps of round g, a warp per pair-block
+        const int nA = s_pa[nm];
         for (int item = slot; item < nA; item += nwarps) {
             int j = 0;
-            while (j < nm - 1 && (s_pa[j + 1] <= item || s_done[j])) ++j;
+            while (j < nm - 1 && (s_pa[j + 1] <= item || !s_ran[j])) ++j;
             const GbMode& J = Ms[j];
-            const int a = item - s_pa[j], t = s_round[j], par = s_gr[j] & 1;
+            const int a = item - s_pa[j], t = s_round[j], g = s_gr[j], par = g & 1;
             const Crit qualifies{J.floor, J.tau, J.tol2};
             int I, Jb;
             rr_pair_e(t, a, J.m, I, Jb);
-            // the inner sweep in registers, as in the cluster kernel
             const int pos = lane & (BJ2 - 1);
             const int64_t gi = bj_index(I, Jb, pos);
+            const float* Ec = ebuf(J, g);   // the state after round g - 1
             float x[BJ2];
             DF d{0.f, 0.f};
-            if (lane < BJ2) {
+            if (g == 0) {
+                if (lane < BJ2) {
 #pragma unroll
-                for (int r = 0; r < BJ2; ++r) x[r] = J.E[(int64_t)bj_index(I, Jb, r) * J.ldE + gi];
-                d = J.D[gi];
+                    for (int r = 0; r < BJ2; ++r) x[r] = Ec[(int64_t)bj_index(I, Jb, r) * J.ldE + gi];
+                    d = J.D[gi];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < BJ2; ++r) x[r] = 0.f;
+                }
             } else {
+                // the cross block [I, Jb] after round g - 1: round g - 1 paired I and Jb into
+                // different pair-blocks; their tile (rows: the smaller pair-block index) rotated
+                const int tp = t == 0 ? J.m - 2 : t - 1, pp = (g - 1) & 1;
+                int ia, ha, ib, hb;
+                rr_block_of(tp, I, J.m, ia, ha);
+                rr_block_of(tp, Jb, J.m, ib, hb);
+                const bool swap = ia > ib;   // the tile's rows hold Jb: the block is [Jb, I]
+                const int ra = swap ? ib : ia, rb = swap ? ia : ib;
+                const int hr = swap ? hb : ha, hc = swap ? ha : hb;
+                int Ira, Jra, Irb, Jrb;
+                rr_pair_e(tp, ra, J.m, Ira, Jra);
+                rr_pair_e(tp, rb, J.m, Irb, Jrb);
+                float* sE = sw;
+                float* sQa = sw + BJ2SQ;
+                float* sQb = sw + 2 * BJ2SQ;
+                float* sT = sw + 3 * BJ2SQ;   // [8][16]: the tile rows hr*8 .. +7 of Q_a^T E
+                float* sR = sT + 8 * BJ2;     // [8][8]: the block
+                {
+                    const float* Ep = ebuf(J, g - 1);
+                    const float4* qa4 = reinterpret_cast<const float4*>(J.Q + ((int64_t)pp * J.nb + ra) * BJ2SQ);
+                    const float4* qb4 = reinterpret_cast<const float4*>(J.Q + ((int64_t)pp * J.nb + rb) * BJ2SQ);
+                    // lane: tile row lane / 2, its half (lane & 1) of the 16 columns; Q: float4s lane, lane + 32
+                    const int tr = lane >> 1, th = lane & 1;
+                    const float* er = Ep + (int64_t)bj_index(Ira, Jra, tr) * J.ldE + (th ? Jrb : Irb) * BJ;
+                    const float4 e0 = *reinterpret_cast<const float4*>(er);
+                    const float4 e1 = *reinterpret_cast<const float4*>(er + 4);
+                    const float4 a0 = qa4[lane], a1 = qa4[lane + 32], b0 = qb4[lane], b1 = qb4[lane + 32];
+                    __syncwarp();   // the previous item's readers of the staging area are done
+                    reinterpret_cast<float4*>(sE)[tr * 4 + th * 2] = e0;
+                    reinterpret_cast<float4*>(sE)[tr * 4 + th * 2 + 1] = e1;
+                    reinterpret_cast<float4*>(sQa)[lane] = a0;
+                    reinterpret_cast<float4*>(sQa)[lane + 32] = a1;
+                    reinterpret_cast<float4*>(sQb)[lane] = b0;
+                    reinterpret_cast<float4*>(sQb)[lane + 32] = b1;
+                    __syncwarp();
+                }
+                // T[row][col] = sum_jj (Q_a[jj][row] + [jj == row]) E[jj][col], rows hr*8 .. +7, in the
+                // tile product's order; four a lane
 #pragma unroll
-                for (int r = 0; r < BJ2; ++r) x[r] = 0.f;
+                for (int q = 0; q < 4; ++q) {
+                    const int e = lane + 32 * q, rr = e >> 4, col = e & 15, row = hr * BJ + rr;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int jj = 0; jj < BJ2; ++jj)
+                        acc = fmaf(sQa[jj * BJ2 + row] + (jj == row ? 1.f : 0.f), sE[jj * BJ2 + col], acc);
+                    sT[rr * BJ2 + col] = acc;
+                }
+                __syncwarp();
+                // the block: columns hc*8 .. +7 of T Q_b, the tile product's pairing of column halves
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int e = lane + 32 * q, rr = e >> 3, cc = e & 7;
+                    const int c0 = hc * BJ, cp = c0 ^ BJ, tc = c0 + cc;
+                    float z = 0.f;
+#pragma unroll
+                    for (int jj = 0; jj < BJ; ++jj) {
+                        const float tv = sT[rr * BJ2 + c0 + jj], ov = sT[rr * BJ2 + cp + jj];
+                        const float qs = sQb[(c0 + jj) * BJ2 + tc] + ((c0 + jj) == tc ? 1.f : 0.f);
+                        const float qo = sQb[(cp + jj) * BJ2 + tc] + ((cp + jj) == tc ? 1.f : 0.f);
+                        z = fmaf(tv, qs, fmaf(ov, qo, z));
+                    }
+                    sR[rr * BJ + cc] = z;
+                }
+                __syncwarp();
+                // the 16 x 16 block: diagonal blocks from buffer g % 3, the cross blocks from sR
+                // (sR = [I, Jb], or [Jb, I] when swapped; the other one is its transpose)
+                if (lane < BJ2) {
+#pragma unroll
+                    for (int r = 0; r < BJ2; ++r) {
+                        const bool rI = r < BJ, cI = pos < BJ;
+                        if (rI == cI) {
+                            x[r] = Ec[(int64_t)bj_index(I, Jb, r) * J.ldE + gi];
+                        } else {
+                            // [I, Jb][u][v] with u the row in block I, v the column in block Jb
+                            const int u = rI ? r : pos, v = rI ? pos - BJ : r - BJ;
+                            x[r] = swap ? sR[v * BJ + u] : sR[u * BJ + v];
+                        }
+                    }
+                    d = J.D[gi];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < BJ2; ++r) x[r] = 0.f;
+                }
             }
             unsigned int nrot = t == 0 ? inner_sweep<true>(x, d, I, Jb, J.k, qualifies)
                                        : inner_sweep<false>(x, d, I, Jb, J.k, qualifies);
             for (int o = 16; o; o >>= 1) nrot += __shfl_xor_sync(0xffffffffu, nrot, o);
+            float* En = ebuf(J, g + 1);   // the state after round g: its diagonal blocks
             float* Qa = J.Q + ((int64_t)par * J.nb + a) * BJ2SQ;
             if (lane < BJ2) {
 #pragma unroll
-                for (int r = 0; r < BJ2; ++r) J.E[(int64_t)bj_index(I, Jb, r) * J.ldE + gi] = x[r];
+                for (int r = 0; r < BJ2; ++r) En[(int64_t)bj_index(I, Jb, r) * J.ldE + gi] = x[r];
                 J.D[gi] = d;
             } else {
 #pragma unroll
@@ -1020,71 +1136,42 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
             }
             if (lane == 0) {
                 J.act[par * J.nb + a] = nrot > 0;
-                if (nrot) atomicAdd(&J.cnt[s_sweep[j] & 1], nrot);
+                if (nrot) atomicAdd(&J.cnt[s_sweep[j] % 3], nrot);
             }
             __syncwarp();
         }
-        // the F items, on the warps of the other three SMSPs first (the inner sweeps, on warp 0,
-        // are the round's critical path)
-        for (int fw = fslot; 2 * fw < nF; fw += nwarps) {
-            const int fh = 2 * fw + h;
-            if (fh < nF) f_item(fh);
-        }
-        if (!(ok = barrier())) break;
-        if (tid < nm) s_fr[tid] = -1;   // the pending F updates are done
 
-        // ---- sweep ends: every CTA reads the finished sweep's count (stable in this phase)
-        if (tid < nm && !s_done[tid]) {
-            const GbMode& J = Ms[tid];
-            if (s_round[tid] == J.m - 2) {
-                const int sw = s_sweep[tid];
-                const unsigned int c = *(volatile unsigned int*)&J.cnt[sw & 1];
-                if (blockIdx.x == 0) {
-                    J.st->sweep_active[(s_base[tid] + sw) & 63] = c;
-                    J.cnt[(sw + 1) & 1] = 0;
-                }
-                if (c == 0) {
-                    s_done[tid] = 2;          // converged: this sweep confirmed it
-                } else if (sw + 1 >= A.max_sweeps) {
-                    s_done[tid] = 3;          // sweep limit
-                    if (blockIdx.x == 0) atomicCAS(&J.st->flag, FLAG_OK, FLAG_NOCONVERGE);
-                }
-            }
-        }
-        __syncthreads();
-
-        // ---- phase B: off-diagonal tiles, two per warp (a half-warp each)
+        // ---- round g - 1's tiles (buffer (g - 1) % 3 rotated into buffer g % 3; a tile of two
+        // pair-blocks that did not rotate is copied by the same arithmetic with Q = I) and its
+        // F update, on the warps of the other SMSPs first
         {
             const int r0 = l16 >> 1, c0 = (l16 & 1) * BJ;
             const int ntile = s_pt[nm];
-            for (int task0 = 2 * slot; task0 < ntile; task0 += 2 * nwarps) {
+            for (int task0 = 2 * fslot; task0 < ntile; task0 += 2 * nwarps) {
                 const int task = task0 + h;
                 const bool live = task < ntile;
                 const int tt = live ? task : task0;
                 int j = 0;
-                while (j < nm - 1 && (s_pt[j + 1] <= tt || s_done[j] == 1)) ++j;
+                while (j < nm - 1 && (s_pt[j + 1] <= tt || s_pr[j] < 0)) ++j;
                 const GbMode& J = Ms[j];
-                const int par = s_gr[j] & 1;
-                const int* act = J.act + par * J.nb;
+                const int pg = s_pg[j], par = pg & 1;
                 // tile index -> (a, b), a < b: row a has nb - 1 - a tiles
                 int rem = tt - s_pt[j], a = 0;
                 while (a < J.nb - 1 && rem >= J.nb - 1 - a) { rem -= J.nb - 1 - a; ++a; }
                 const int b = a + 1 + rem;
-                const bool need = live && (act[a] | act[b]);
-                if (!__any_sync(0xffffffffu, need)) continue;
-                const int t = s_round[j];
+                const int t = s_pr[j];
                 int Ia, Ja, Ib, Jb2;
                 rr_pair_e(t, a, J.m, Ia, Ja);
                 rr_pair_e(t, b, J.m, Ib, Jb2);
-                // the tile's E rows (16 x 16), Q_a and Q_b into shared memory: one round of
-                // independent loads (the grid barrier's fence leaves nothing of them in L1)
+                const float* Es = ebuf(J, pg);
+                float* Ed = ebuf(J, pg + 1);
                 float* sE = sq;
                 float* sQa = sq + BJ2SQ;
                 float* sQb = sq + 2 * BJ2SQ;
                 {
                     const float4* qa4 = reinterpret_cast<const float4*>(J.Q + ((int64_t)par * J.nb + a) * BJ2SQ);
                     const float4* qb4 = reinterpret_cast<const float4*>(J.Q + ((int64_t)par * J.nb + b) * BJ2SQ);
-                    const float* er = J.E + (int64_t)bj_index(Ia, Ja, l16) * J.ldE;
+                    const float* er = Es + (int64_t)bj_index(Ia, Ja, l16) * J.ldE;
                     float4 v[12];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -1095,7 +1182,7 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                     v[9] = *reinterpret_cast<const float4*>(er + Ib * BJ + 4);
                     v[10] = *reinterpret_cast<const float4*>(er + Jb2 * BJ);
                     v[11] = *reinterpret_cast<const float4*>(er + Jb2 * BJ + 4);
-                    __syncwarp();   // the previous tile's readers of this staging area are done
+                    __syncwarp();   // the previous item's readers of this staging area are done
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         reinterpret_cast<float4*>(sQa)[l16 * 4 + q] = v[q];
@@ -1124,7 +1211,6 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                         t1[c] = fmaf(qa1, xv[c], t1[c]);
                     }
                 }
-                float* E = J.E;
                 const int ldE = J.ldE;
                 const int cp = c0 ^ BJ;
                 const int row0 = bj_index(Ia, Ja, r0), row1 = bj_index(Ia, Ja, r0 + BJ);
@@ -1149,48 +1235,57 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                             z[c] = fmaf(tv, qs, fmaf(ov, qo, z[c]));
                         }
                     }
-                    // every lane has read this tile's E rows (first product) before any store
-                    __syncwarp();
-                    if (live && need) {
+                    if (live) {
                         const int row = half_row ? row1 : row0;
-                        float* w = E + (int64_t)row * ldE + colb;
+                        float* w = Ed + (int64_t)row * ldE + colb;
                         *reinterpret_cast<float4*>(w) = make_float4(z[0], z[1], z[2], z[3]);
                         *reinterpret_cast<float4*>(w + 4) = make_float4(z[4], z[5], z[6], z[7]);
 #pragma unroll
-                        for (int c = 0; c < BJ; ++c) E[(int64_t)(colb + c) * ldE + row] = z[c];
+                        for (int c = 0; c < BJ; ++c) Ed[(int64_t)(colb + c) * ldE + row] = z[c];
                     }
                 }
                 __syncwarp();
             }
-        }
-        // this round's F update is pending for every matrix that ran it; matrices that finished
-        // at this sweep end take no further part (after every warp of this CTA has finished
-        // decoding this round's items)
-        __syncthreads();
-        if (tid < nm && s_done[tid] != 1) {
-            s_fr[tid] = s_round[tid];
-            s_fp[tid] = s_gr[tid] & 1;
-            if (s_done[tid] >= 2) s_done[tid] = 1;
-        }
-        if (!(ok = barrier())) break;
-        // next round
-        if (tid < nm && !s_done[tid]) {
-            ++s_gr[tid];
-            if (++s_round[tid] == Ms[tid].m - 1) {
-                s_round[tid] = 0;
-                ++s_sweep[tid];
+            const int nF = s_pf[nm];
+            for (int fw = fslot; 2 * fw < nF; fw += nwarps) {
+                const int fh = 2 * fw + h;
+                if (fh < nF) f_item(fh);
             }
         }
         __syncthreads();
-    }
-    // the last round's F update (the prefix counts of the exit pass name the pending matrices)
-    if (ok) {
-        const int nF = s_pf[nm];
-        for (int item = slot; item < (nF + 1) / 2; item += nwarps) {
-            const int fh = 2 * item + h;
-            if (fh < nF) f_item(fh);
+        if (!(ok = barrier())) break;
+        // the round just run is pending (tiles, F); the next one, or the end of the sweep
+        if (tid < nm) {
+            const int j = tid;
+            const GbMode& J = Ms[j];
+            if (s_ran[j]) {
+                s_pr[j] = s_round[j];
+                s_pg[j] = s_gr[j];
+                ++s_gr[j];
+                if (s_round[j] == J.m - 2) {
+                    const int sw = s_sweep[j];
+                    const unsigned int c = *(volatile unsigned int*)&J.cnt[sw % 3];
+                    if (blockIdx.x == 0) {
+                        J.st->sweep_active[(s_base[j] + sw) & 63] = c;
+                        J.cnt[(sw + 2) % 3] = 0;   // read two sweeps ago; added to next sweep but one
+                    }
+                    if (c == 0) {
+                        s_done[j] = 1;   // converged: this sweep confirmed it
+                    } else if (sw + 1 >= A.max_sweeps) {
+                        s_done[j] = 1;   // sweep limit
+                        if (blockIdx.x == 0) atomicCAS(&J.st->flag, FLAG_OK, FLAG_NOCONVERGE);
+                    } else {
+                        s_round[j] = 0;
+                        ++s_sweep[j];
+                    }
+                } else {
+                    ++s_round[j];
+                }
+            } else {
+                s_pr[j] = -1;
+            }
         }
-        ok = barrier();
+        __syncthreads();
     }
     // results (also after a failed barrier, so the host sees the flag and the partial state)
     const bool timed_out = !ok;
@@ -1317,8 +1412,8 @@ cudaError_t launch_jacobi_gblk(const DfJob* jobs, int njobs, int max_sweeps, int
             m += m & 1;
             if (m < 2) m = 2;
             const int K = m * BJ, ldE = K + 4, nb = m / 2;
-            of[i] = Offs{carve(sizeof(DF) * (size_t)K), carve(4 * (size_t)K * ldE), carve(4 * (size_t)K * K),
-                         carve(2 * 4 * (size_t)nb * BJ2SQ), carve(2 * 4 * (size_t)nb), carve(8)};
+            of[i] = Offs{carve(sizeof(DF) * (size_t)K), carve(3 * 4 * (size_t)K * ldE), carve(4 * (size_t)K * K),
+                         carve(2 * 4 * (size_t)nb * BJ2SQ), carve(2 * 4 * (size_t)nb), carve(16)};
             hm[i] = GbMode{J.H, J.outD, J.outF, J.st, J.ldd, J.k, J.add_identity,
                            (float)J.abs_floor, (float)J.tau, (float)(J.tol * J.tol), K, ldE, nb, m,
                            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
