@@ -812,7 +812,7 @@ __global__ void __launch_bounds__(kEigThreads) k_chol32_multi(const CholJob* job
 //   - meanwhile the other warps rotate round g - 1's tiles (E_ab <- Q_a^T E_ab
 //     Q_b, both triangles; a half-warp each, operands staged in shared memory)
 //     from buffer g - 1 mod 3 into buffer g mod 3, copying those of pair-blocks
-//     that did not rotate by the same arithmetic with Q = I, and apply round
+//     that did not rotate, and apply round
 //     g - 1's rotations to F (F <- F + F_Q + F F_Q, a half-warp per pair-block
 //     and group of 16 rows, a lane per row).
 // So a round costs one barrier and its inner sweeps, with the tiles off the
@@ -1142,8 +1142,8 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
         }
 
         // ---- round g - 1's tiles (buffer (g - 1) % 3 rotated into buffer g % 3; a tile of two
-        // pair-blocks that did not rotate is copied by the same arithmetic with Q = I) and its
-        // F update, on the warps of the other SMSPs first
+        // pair-blocks that did not rotate is copied) and its F update, on the warps of the other
+        // SMSPs first
         {
             const int r0 = l16 >> 1, c0 = (l16 & 1) * BJ;
             const int ntile = s_pt[nm];
@@ -1165,6 +1165,36 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                 rr_pair_e(t, b, J.m, Ib, Jb2);
                 const float* Es = ebuf(J, pg);
                 float* Ed = ebuf(J, pg + 1);
+                // a tile of two pair-blocks that did not rotate is copied (both triangles); the
+                // product runs where either half-warp's tile needs it (the other half's Q are then
+                // identities, so it copies exactly by the same arithmetic)
+                const int* act = J.act + par * J.nb;
+                if (!__any_sync(0xffffffffu, live && (act[a] | act[b]))) {
+                    if (live) {
+                        const int ra = bj_index(Ia, Ja, l16), rb = bj_index(Ib, Jb2, l16);
+                        const float* sa = Es + (int64_t)ra * J.ldE;
+                        const float* sb = Es + (int64_t)rb * J.ldE;
+                        float* da = Ed + (int64_t)ra * J.ldE;
+                        float* db = Ed + (int64_t)rb * J.ldE;
+                        const float4 u0 = *reinterpret_cast<const float4*>(sa + Ib * BJ);
+                        const float4 u1 = *reinterpret_cast<const float4*>(sa + Ib * BJ + 4);
+                        const float4 u2 = *reinterpret_cast<const float4*>(sa + Jb2 * BJ);
+                        const float4 u3 = *reinterpret_cast<const float4*>(sa + Jb2 * BJ + 4);
+                        const float4 w0 = *reinterpret_cast<const float4*>(sb + Ia * BJ);
+                        const float4 w1 = *reinterpret_cast<const float4*>(sb + Ia * BJ + 4);
+                        const float4 w2 = *reinterpret_cast<const float4*>(sb + Ja * BJ);
+                        const float4 w3 = *reinterpret_cast<const float4*>(sb + Ja * BJ + 4);
+                        *reinterpret_cast<float4*>(da + Ib * BJ) = u0;
+                        *reinterpret_cast<float4*>(da + Ib * BJ + 4) = u1;
+                        *reinterpret_cast<float4*>(da + Jb2 * BJ) = u2;
+                        *reinterpret_cast<float4*>(da + Jb2 * BJ + 4) = u3;
+                        *reinterpret_cast<float4*>(db + Ia * BJ) = w0;
+                        *reinterpret_cast<float4*>(db + Ia * BJ + 4) = w1;
+                        *reinterpret_cast<float4*>(db + Ja * BJ) = w2;
+                        *reinterpret_cast<float4*>(db + Ja * BJ + 4) = w3;
+                    }
+                    continue;
+                }
                 float* sE = sq;
                 float* sQa = sq + BJ2SQ;
                 float* sQb = sq + 2 * BJ2SQ;

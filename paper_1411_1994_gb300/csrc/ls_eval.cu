@@ -480,9 +480,9 @@ __device__ __forceinline__ unsigned short f16_of_fixed(long long R, long long& q
 // Split sources: element (b, i, k) of `batch` stacked operands (row i, column k).
 //   SrcF64:    p[b*sb + row(i)*si + k*sk], row(i) = ridx ? ridx[i] : i
 //   SrcPair:   the same over FP32 pairs (hi, lo) whose sum is the value
-//   SrcGather: w[t] P[i*ld + tcol[3t + mode]] with t = tmap[k] (0 where t < 0): the
-//              columns of a projected side matrix that the canonical terms use, in the
-//              order of a term list (one batch)
+//   SrcIdx:    w[k] P[i*ld + idx[k]] (0 where idx[k] < 0): the columns of a projected
+//              side matrix that the canonical terms use, in the order of a term list
+//              (one batch; idx and w resolved from the term map once, k_term_index)
 // mag() orders like |x|; exp_of() gives E with max|x| in [2^(E-1), 2^E) from it.
 struct SrcF64 {
     static constexpr bool pair = false;
@@ -516,19 +516,22 @@ struct SrcPair {
         return fixed_of(v.x, s) + fixed_of(v.y, s);
     }
 };
-struct SrcGather {
+
+// A gathered operand whose column map is already resolved: x(i, k) = w[k] P[i*ld + idx[k]]
+// (w may be NULL), 0 where idx[k] < 0: with idx[k] = tcol[3 tmap[k] + mode] and
+// w[k] = w[tmap[k]] resolved beforehand, an entry is two independent reads and one
+// dependent one.
+struct SrcIdx {
     static constexpr bool pair = false;
     const double* P;
     int64_t ld;
-    const int32_t* tmap;
-    const int32_t* tcol;
-    int mode;
+    const int32_t* idx;
     const double* w;
     __device__ double at(int64_t, int64_t i, int64_t k) const {
-        const int t = tmap[k];
-        if (t < 0) return 0.0;
-        const double v = P[i * ld + tcol[3 * (int64_t)t + mode]];
-        return w ? w[t] * v : v;
+        const int c = idx[k];
+        if (c < 0) return 0.0;
+        const double v = P[i * ld + c];
+        return w ? w[k] * v : v;
     }
     __device__ unsigned long long mag(int64_t b, int64_t i, int64_t k) const {
         return (unsigned long long)__double_as_longlong(at(b, i, k)) & 0x7fffffffffffffffull;
@@ -536,6 +539,17 @@ struct SrcGather {
     __device__ static int exp_of(unsigned long long mb) { return SrcF64::exp_of(mb); }
     __device__ long long fixed(int64_t b, int64_t i, int64_t k, int s) const { return fixed_of(at(b, i, k), s); }
 };
+// the core's column maps of modes 1 and 2 and the term weights over the padded term list
+__global__ void k_term_index(const int32_t* __restrict__ tmap, const int32_t* __restrict__ tcol,
+                             const double* __restrict__ xin, int64_t tpad, int32_t* __restrict__ idx1,
+                             int32_t* __restrict__ idx2, double* __restrict__ w1) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= tpad) return;
+    const int t = tmap[k];
+    idx1[k] = t < 0 ? -1 : tcol[3 * (int64_t)t + 1];
+    idx2[k] = t < 0 ? -1 : tcol[3 * (int64_t)t + 2];
+    w1[k] = t < 0 ? 0.0 : xin[t];
+}
 
 // The same four parts from an FP32 pair (hi, lo) in FP32 arithmetic: the scaled
 // value as a pair, nearest-integer digits (the differences are exact), the rest
@@ -657,10 +671,19 @@ __global__ void __launch_bounds__(256) k_split_tr(const float2* __restrict__ W, 
     const SrcPair src{W, 1, ld, 0};
     const int E = (n < rows && mb[n]) ? SrcPair::exp_of(mb[n]) : 0;
     if (blockIdx.y == 0 && ty == 0 && n < rows) exps[n] = E;
-    for (int kk = ty * 2; kk < 32; kk += 8) {
+    // the thread's eight entries loaded first (eight reads in flight), then split
+    float2 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int kk = ty * 2 + 8 * (q >> 1) + (q & 1);
+        v[q] = (n < rows && k0 + kk < cols) ? src.at(0, n, k0 + kk) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+        const int kk = ty * 2 + 8 * (q >> 1);
         unsigned short a[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
-        if (n < rows && k0 + kk < cols) split_entry(src, 0, n, k0 + kk, E, a[0], a[1], a[2], a[3]);
-        if (n < rows && k0 + kk + 1 < cols) split_entry(src, 0, n, k0 + kk + 1, E, c[0], c[1], c[2], c[3]);
+        if (n < rows && k0 + kk < cols) split_pair(v[q], E, a[0], a[1], a[2], a[3]);
+        if (n < rows && k0 + kk + 1 < cols) split_pair(v[q + 1], E, c[0], c[1], c[2], c[3]);
 #pragma unroll
         for (int p = 0; p < 4; ++p) tile[p][tx][kk >> 1] = (unsigned)a[p] | ((unsigned)c[p] << 16);
     }
@@ -1194,6 +1217,9 @@ int dt_core(const double* P0, const double* P1, const double* P2, const int32_t*
     Arena ar(st);
     int* d_kb = ar.get<int>((C0 + 1) + tpad);
     int32_t* d_tmap = d_kb + (C0 + 1);
+    int32_t* d_idx1 = ar.get<int32_t>(2 * tpad);
+    int32_t* d_idx2 = d_idx1 ? d_idx1 + tpad : nullptr;
+    double* d_w1 = ar.get<double>(tpad);
     // Output columns (j, k) in ranges of jc values of j, groups in chunks of gc (each
     // one exact K range of step 2, up to 4096): W (pairs) and its split form take
     // 16 bytes a (group, j, k), within about a third of the free memory (1 to 32 GB).
@@ -1204,14 +1230,18 @@ int dt_core(const double* P0, const double* P1, const double* P2, const int32_t*
     DtOp a = dt_alloc(ar, r2, tpad, 1), b = dt_alloc(ar, jc, tpad, 1);
     float2* W = ar.get<float2>(gc * jc * r2);
     DtOp ws = dt_alloc(ar, jc * r2, pad32(gc), 1), p0s = dt_alloc(ar, r0, pad32(gc), 1);
-    if (!d_kb || !a.ok() || !b.ok() || !W || !ws.ok() || !p0s.ok()) return tc_err(err, "core: out of memory", LS_ERR_OOM);
+    if (!d_kb || !d_idx1 || !d_w1 || !a.ok() || !b.ok() || !W || !ws.ok() || !p0s.ok())
+        return tc_err(err, "core: out of memory", LS_ERR_OOM);
     {
         Scope sc("core.operands", st);
         if (upload_h2d(d_kb, up.data(), up.size() * sizeof(int32_t), st) != cudaSuccess)
             return tc_err(err, "core: upload failed");
         count_h2d((int64_t)(up.size() * sizeof(int32_t)));
+        // the column maps and weights over the padded term list, once
+        k_term_index<<<(unsigned)((tpad + 255) / 256), 256, 0, st>>>(d_tmap, tcol, xin, tpad, d_idx1, d_idx2, d_w1);
+        count_kernels(1);
         // step 1's A operand over the padded term list: A[k][t] = P2[k][c2(t)]
-        if (dt_split(SrcGather{P2, (int64_t)C[2], d_tmap, tcol, 2, nullptr}, tpad, a, st) != cudaSuccess)
+        if (dt_split(SrcIdx{P2, (int64_t)C[2], d_idx2, nullptr}, tpad, a, st) != cudaSuccess)
             return tc_err(err, "core: split failed");
     }
     const DtOpts opt;
@@ -1222,7 +1252,7 @@ int dt_core(const double* P0, const double* P1, const double* P2, const int32_t*
         {
             Scope sc("core.operands", st);
             // step 1's B operand: B[j][t] = xin[t] P1[j][c1(t)], rows j0 .. j0 + nj
-            if (dt_split(SrcGather{P1 + j0 * C[1], (int64_t)C[1], d_tmap, tcol, 1, xin}, tpad, bj, st) != cudaSuccess)
+            if (dt_split(SrcIdx{P1 + j0 * C[1], (int64_t)C[1], d_idx1, d_w1}, tpad, bj, st) != cudaSuccess)
                 return tc_err(err, "core: split failed");
         }
         for (int64_t g0 = 0; g0 < C0; g0 += gc) {
