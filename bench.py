@@ -327,6 +327,14 @@ class ClockSampler:
 # roofline of the dominant step
 # ---------------------------------------------------------------------------
 
+# what the mixed path computes in: FP64-grade (exact BF16 slices, 2^-53) Gram, CholeskyQR2 and
+# projection; the eigen-solver's rotations in FP32 (hi/lo FP32 diagonal) with the eigenvalues
+# taken as Rayleigh quotients of an FP64-grade re-projection; core and slabs as BF16x-split
+# (two exact digits + two tails, FP16) tensor-core products with FP32 accumulation
+MIXED_DTYPE = ("f64-grade Gram/CholeskyQR2/projection (exact bf16 slices) + f32 Jacobi with f64-grade "
+               "Rayleigh quotients + fp16 digit+tail tensor-core core and slabs (f32 acc)")
+
+
 def step_flops(name, info, N):
     """Algorithmic FP64 / tensor flops of one pipeline step (all three modes): a
     symmetric product (Gram matrix) counts its N C^2 distinct multiply-adds
@@ -506,7 +514,7 @@ def run_batch(args, torch, B, L):
         "metric": METRIC, "value": head["value"], "unit": "potentials/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64 orthogonalisation + bf16 tensor-core contractions (exact 6-bit heads, f32 acc)",
+        "dtype": MIXED_DTYPE,
         "data": "synthetic (seeded)",
         "config": {"workload": f"c4_batch{len(items)}_L8-48_N512-2048_R20-28", "items": len(items),
                    "units_per_step": units, "wave": args.batch_wave, "eps": items[0].eps,
@@ -773,8 +781,8 @@ def main():
         "metric": METRIC, "value": head["value"], "unit": "potentials/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f64 orthogonalisation + bf16 tensor-core contractions "
-                                                         "(exact 6-bit heads, f32 acc)",
+        "dtype": ("f64 (Gram, CholeskyQR2, projection: f64-grade exact bf16 slices; singular values: f64 "
+                  "one-sided Jacobi; core and slabs: f64 CUDA cores)") if args.precision == "fp64" else MIXED_DTYPE,
         "data": "synthetic (seeded)",
         "config": config_of(wl, args, {"parallelism": f"replicas x{world}", "ranks": info["r"],
                                        "columns": info["C"], "terms": info["T"], "jacobi_sweeps": info["sweeps"]}),
