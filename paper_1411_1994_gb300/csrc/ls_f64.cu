@@ -857,6 +857,8 @@ __global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
     const int nbk = (r + CHB - 1) / CHB;
     unsigned int epoch = 0;   // counting barriers of the job's CTAs (st->arrive zeroed by the launcher)
     __shared__ double s_rcp[CHB];   // 1 / L_kk of the panel
+    __shared__ double colk[CHB];    // the column being eliminated, scaled
+    __shared__ double sI[CHB][CHB + 1], sK[CHB][CHB + 1];   // panel rows of a trailing tile
     for (int j0 = 0; j0 < r; j0 += CHB) {
         const int b = min(CHB, r - j0);
         if (lb == 0) {
@@ -866,18 +868,37 @@ __global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
             }
             __syncthreads();
             for (int k = 0; k < b; ++k) {
-                if (threadIdx.x == 0) {
+                // warp 0: the pivot d = D[k][k], y ~ d^(-1/2) (the FP32 seed and one Newton step
+                // in FP64, good to about 2^-46: this first factorisation only has to bring Y
+                // within reach of the second pass), then column k scaled into colk and D
+                if (threadIdx.x < 32) {
+                    const int i = threadIdx.x;
                     const double d = D[k][k];
-                    if (!(d > 0.0)) atomicCAS(&st->flag, FLAG_OK, FLAG_NOT_SPD);
-                    D[k][k] = d > 0.0 ? sqrt(d) : 1.0;
-                    s_rcp[k] = 1.0 / D[k][k];   // one division a column, not one a row
+                    double y = 1.0;
+                    if (d > 0.0) {
+                        y = (double)rsqrtf((float)d);
+                        y = y * fma(-0.5 * d, y * y, 1.5);
+                    } else if (i == 0) {
+                        atomicCAS(&st->flag, FLAG_OK, FLAG_NOT_SPD);
+                    }
+                    if (i == k) {
+                        D[k][k] = d > 0.0 ? d * y : 1.0;
+                        s_rcp[k] = y;
+                    } else if (i > k && i < b) {
+                        const double l = D[i][k] * y;
+                        D[i][k] = l;
+                        colk[i] = l;
+                    }
                 }
                 __syncthreads();
-                for (int i = k + 1 + threadIdx.x; i < b; i += blockDim.x) D[i][k] *= s_rcp[k];
-                __syncthreads();
-                for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-                    const int i = e / b, l = e % b;
-                    if (i > k && l > k && l <= i) D[i][l] -= D[i][k] * D[l][k];
+                // the rank-one update of the block: thread (row ty + 8 m, column tx)
+                {
+                    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+                    if (tx > k && tx < b) {
+                        const double lk = colk[tx];
+                        for (int i = ty; i < b; i += blockDim.x >> 5)
+                            if (i >= tx) D[i][tx] -= colk[i] * lk;
+                    }
                 }
                 __syncthreads();
             }
@@ -895,34 +916,55 @@ __global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
         __syncthreads();
         if (threadIdx.x < b) s_rcp[threadIdx.x] = 1.0 / D[threadIdx.x][threadIdx.x];
         __syncthreads();
-        for (int64_t i = j0 + b + gtid; i < r; i += nthr) {
-            double x[CHB];
-            for (int k = 0; k < b; ++k) x[k] = __ldcg(A + i * r + j0 + k);
-            for (int k = 0; k < b; ++k) {
-                double s = x[k];
-                for (int l = 0; l < k; ++l) s -= x[l] * D[k][l];
-                x[k] = s * s_rcp[k];
+        // the panel solve x L11^T = a for every row below the block: a warp per row, lane k
+        // holding x_k; step k lane k finishes x_k and every later lane takes its product (one
+        // FP64 instruction a step for the warp instead of one a row); rows over all CTAs
+        {
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwc = blockDim.x >> 5;
+            const double lkk_rcp = lane < b ? s_rcp[lane] : 1.0;
+            for (int64_t i = j0 + b + lb + (int64_t)nb * wid; i < r; i += (int64_t)nb * nwc) {
+                double acc = lane < b ? __ldcg(A + i * r + j0 + lane) : 0.0;
+                double xk = 0.0;
+                for (int k = 0; k < b; ++k) {
+                    const double xkk = __shfl_sync(0xffffffffu, acc * lkk_rcp, k);   // x_k (lane k's value)
+                    if (lane == k) xk = xkk;
+                    if (lane > k && lane < b) acc = fma(-xkk, D[lane][k], acc);
+                }
+                if (lane < b) __stcg(A + i * r + j0 + lane, xk);
             }
-            for (int k = 0; k < b; ++k) __stcg(A + i * r + j0 + k, x[k]);
         }
         if (!count_barrier(st, ++epoch * nb)) return;
-        const int64_t n2 = r - j0 - b;
-        for (int64_t e = gtid; e < n2 * n2; e += nthr) {
-            const int64_t i = j0 + b + e / n2, k = j0 + b + e % n2;
-            if (k > i) continue;
-            // four partial sums: the loads of a row pair are independent and overlap in L2
-            const double* ai = A + i * r + j0;
-            const double* ak = A + k * r + j0;
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            int l = 0;
-            for (; l + 3 < b; l += 4) {
-                s0 = fma(__ldcg(ai + l), __ldcg(ak + l), s0);
-                s1 = fma(__ldcg(ai + l + 1), __ldcg(ak + l + 1), s1);
-                s2 = fma(__ldcg(ai + l + 2), __ldcg(ak + l + 2), s2);
-                s3 = fma(__ldcg(ai + l + 3), __ldcg(ak + l + 3), s3);
+        // the trailing update A22 -= L21 L21^T on its lower 32 x 32 tiles, a CTA per tile: both
+        // tiles' panel rows staged in shared memory (coalesced), thread (ty, tx) four rows
+        {
+            const int n2 = r - j0 - b;
+            const int nt = (n2 + CHB - 1) / CHB;
+            const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+            for (int item = lb; item < nt * (nt + 1) / 2; item += nb) {
+                int ti = 0, rem = item;
+                while (rem > ti) { rem -= ti + 1; ++ti; }
+                const int tk = rem;   // tk <= ti
+                __syncthreads();   // the previous tile's readers of sI, sK are done
+                for (int e = threadIdx.x; e < CHB * CHB; e += blockDim.x) {
+                    const int rr = e >> 5, c = e & 31;
+                    const int ri = ti * CHB + rr, rk = tk * CHB + rr;
+                    sI[rr][c] = (ri < n2 && c < b) ? __ldcg(A + (int64_t)(j0 + b + ri) * r + j0 + c) : 0.0;
+                    sK[rr][c] = (rk < n2 && c < b) ? __ldcg(A + (int64_t)(j0 + b + rk) * r + j0 + c) : 0.0;
+                }
+                __syncthreads();
+                const int k = tk * CHB + tx;
+                if (k < n2) {
+                    for (int rr = ty; rr < CHB; rr += blockDim.x >> 5) {
+                        const int i = ti * CHB + rr;
+                        if (i >= n2 || k > i) continue;
+                        double acc = 0.0;
+#pragma unroll 8
+                        for (int l = 0; l < CHB; ++l) acc = fma(sI[rr][l], sK[tx][l], acc);
+                        double* o = A + (int64_t)(j0 + b + i) * r + j0 + b + k;
+                        __stcg(o, __ldcg(o) - acc);
+                    }
+                }
             }
-            for (; l < b; ++l) s0 = fma(__ldcg(ai + l), __ldcg(ak + l), s0);
-            __stcg(A + i * r + k, __ldcg(A + i * r + k) - ((s0 + s1) + (s2 + s3)));
         }
         if (!count_barrier(st, ++epoch * nb)) return;
     }
@@ -958,22 +1000,24 @@ __global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
     // block rows I = 1..: Li[I][J] = -inv(L_II) sum_{K=J}^{I-1} L[I][K] Li[K][J]
     for (int I = 1; I < nbk; ++I) {
         const int i0 = I * CHB, bi = min(CHB, r - i0);
-        // all (J, element) pairs of this block row in parallel: S first, kept in Li
-        for (int64_t e = gtid; e < (int64_t)bi * i0; e += nthr) {
+        // all (J, element) pairs of this block row in parallel: S first, kept in Li; each dot
+        // product over eight lanes (strided k), added by a butterfly
+        const int q8 = threadIdx.x & 7;
+        for (int64_t e8 = gtid; e8 < (int64_t)8 * bi * i0; e8 += nthr) {
+            const int64_t e = e8 >> 3;   // the eight lanes of an element take the same trip count
             const int ii = (int)(e / i0), jj = (int)(e % i0);   // row i0+ii, column jj < i0
             const int J = jj / CHB;
-            // four partial sums: independent loads in flight
             const double* ar = A + (int64_t)(i0 + ii) * r;
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            int kk = J * CHB;
-            for (; kk + 3 < i0; kk += 4) {
+            double s0 = 0.0, s1 = 0.0;
+            int kk = J * CHB + q8;
+            for (; kk + 8 < i0; kk += 16) {
                 s0 = fma(__ldcg(ar + kk), __ldcg(Li + (int64_t)kk * r + jj), s0);
-                s1 = fma(__ldcg(ar + kk + 1), __ldcg(Li + (int64_t)(kk + 1) * r + jj), s1);
-                s2 = fma(__ldcg(ar + kk + 2), __ldcg(Li + (int64_t)(kk + 2) * r + jj), s2);
-                s3 = fma(__ldcg(ar + kk + 3), __ldcg(Li + (int64_t)(kk + 3) * r + jj), s3);
+                s1 = fma(__ldcg(ar + kk + 8), __ldcg(Li + (int64_t)(kk + 8) * r + jj), s1);
             }
-            for (; kk < i0; ++kk) s0 = fma(__ldcg(ar + kk), __ldcg(Li + (int64_t)kk * r + jj), s0);
-            __stcg(Li + (int64_t)(i0 + ii) * r + jj, (s0 + s1) + (s2 + s3));
+            if (kk < i0) s0 = fma(__ldcg(ar + kk), __ldcg(Li + (int64_t)kk * r + jj), s0);
+            double sum = s0 + s1;
+            for (int o = 4; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (q8 == 0) __stcg(Li + (int64_t)(i0 + ii) * r + jj, sum);
         }
         if (!count_barrier(st, ++epoch * nb)) return;
         for (int64_t e = gtid; e < (int64_t)bi * i0; e += nthr) {
