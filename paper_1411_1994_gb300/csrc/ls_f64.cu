@@ -858,6 +858,14 @@ __global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
     unsigned int epoch = 0;   // counting barriers of the job's CTAs (st->arrive zeroed by the launcher)
     __shared__ double s_rcp[CHB];   // 1 / L_kk of the panel
     __shared__ double colk[CHB];    // the column being eliminated, scaled
+    // entry e of a lower triangle, row by row: (tri_r[e], tri_c[e]), tri_c <= tri_r
+    __shared__ unsigned char tri_r[CHB * (CHB + 1) / 2], tri_c[CHB * (CHB + 1) / 2];
+    for (int t = threadIdx.x; t < CHB; t += blockDim.x)
+        for (int c = 0; c <= t; ++c) {
+            tri_r[t * (t + 1) / 2 + c] = (unsigned char)t;
+            tri_c[t * (t + 1) / 2 + c] = (unsigned char)c;
+        }
+    __syncthreads();
     __shared__ double sI[CHB][CHB + 1], sK[CHB][CHB + 1];   // panel rows of a trailing tile
     for (int j0 = 0; j0 < r; j0 += CHB) {
         const int b = min(CHB, r - j0);
@@ -891,13 +899,13 @@ __global__ void __launch_bounds__(256) k_chol_inv_multi(CholArgs Ar) {
                     }
                 }
                 __syncthreads();
-                // the rank-one update of the block: thread (row ty + 8 m, column tx)
+                // the rank-one update of the trailing triangle (rows and columns k + 1 .. b - 1),
+                // one entry a thread through the triangle table: as few warps as entries need
                 {
-                    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-                    if (tx > k && tx < b) {
-                        const double lk = colk[tx];
-                        for (int i = ty; i < b; i += blockDim.x >> 5)
-                            if (i >= tx) D[i][tx] -= colk[i] * lk;
+                    const int n = b - 1 - k;
+                    for (int e = threadIdx.x; e < n * (n + 1) / 2; e += blockDim.x) {
+                        const int i = k + 1 + tri_r[e], l = k + 1 + tri_c[e];
+                        D[i][l] -= colk[i] * colk[l];
                     }
                 }
                 __syncthreads();
