@@ -39,11 +39,16 @@ struct DfMode {
     int64_t ldd; int k; int add_identity; double abs_floor; double tau; double tol;
 };
 
+// v mod n for 0 <= v < 2 n (one compare: the round-robin indices below stay in that range, and
+// a division by a runtime n is a long dependent chain on the critical path of a round)
+__device__ __forceinline__ int mod_lt2n(int v, int n) { return v >= n ? v - n : v; }
+
+// pair-block i (0 <= i < Cp / 2) of round t (0 <= t < Cp - 1) of the round-robin over Cp blocks
 __device__ __forceinline__ void rr_pair_e(int t, int i, int Cp, int& p, int& q) {
     const int n1 = Cp - 1;
     int a, b;
     if (i == 0) { a = n1; b = t; }
-    else { a = (t + i) % n1; b = (t - i + n1) % n1; }
+    else { a = mod_lt2n(t + i, n1); b = mod_lt2n(t - i + n1, n1); }
     p = min(a, b);
     q = max(a, b);
 }
@@ -902,10 +907,10 @@ __device__ __forceinline__ void rr_block_of(int t, int X, int m, int& i, int& se
     const int n1 = m - 1, nb = m / 2;
     if (X == n1) { i = 0; second = 1; return; }
     if (X == t) { i = 0; second = 0; return; }
-    const int dd = (X - t + n1) % n1;
+    const int dd = mod_lt2n(X - t + n1, n1);
     int a, b;
-    if (dd <= nb - 1) { i = dd; a = X; b = (t - dd + n1) % n1; }
-    else { i = n1 - dd; a = (t + i) % n1; b = X; }
+    if (dd <= nb - 1) { i = dd; a = X; b = mod_lt2n(t - dd + n1, n1); }
+    else { i = n1 - dd; a = mod_lt2n(t + i, n1); b = X; }
     second = X == max(a, b) ? 1 : 0;
 }
 
@@ -1054,6 +1059,17 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                 float* sQb = sw + 2 * BJ2SQ;
                 float* sT = sw + 3 * BJ2SQ;   // [8][16]: the tile rows hr*8 .. +7 of Q_a^T E
                 float* sR = sT + 8 * BJ2;     // [8][8]: the block
+                // the two diagonal blocks (buffer g % 3) and d, loaded beside the tile and its
+                // rotations below: one trip to L2 instead of two; the cross entries come later
+                if (lane < BJ2) {
+#pragma unroll
+                    for (int r = 0; r < BJ2; ++r)
+                        if ((r < BJ) == (pos < BJ)) x[r] = Ec[(int64_t)bj_index(I, Jb, r) * J.ldE + gi];
+                    d = J.D[gi];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < BJ2; ++r) x[r] = 0.f;
+                }
                 {
                     const float* Ep = ebuf(J, g - 1);
                     const float4* qa4 = reinterpret_cast<const float4*>(J.Q + ((int64_t)pp * J.nb + ra) * BJ2SQ);
@@ -1074,51 +1090,63 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
                     __syncwarp();
                 }
                 // T[row][col] = sum_jj (Q_a[jj][row] + [jj == row]) E[jj][col], rows hr*8 .. +7, in the
-                // tile product's order; four a lane
+                // tile product's order; a lane takes column lane & 15 of four consecutive rows (one
+                // float4 of Q_a and one entry of E a step)
+                {
+                    const int col = lane & 15, rq = (lane >> 4) * 4, row0 = hr * BJ + rq;
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int e = lane + 32 * q, rr = e >> 4, col = e & 15, row = hr * BJ + rr;
-                    float acc = 0.f;
+                    for (int jj = 0; jj < BJ2; ++jj) {
+                        const float4 q = *reinterpret_cast<const float4*>(sQa + jj * BJ2 + row0);
+                        const float e = sE[jj * BJ2 + col];
+                        acc[0] = fmaf(q.x + (jj == row0 ? 1.f : 0.f), e, acc[0]);
+                        acc[1] = fmaf(q.y + (jj == row0 + 1 ? 1.f : 0.f), e, acc[1]);
+                        acc[2] = fmaf(q.z + (jj == row0 + 2 ? 1.f : 0.f), e, acc[2]);
+                        acc[3] = fmaf(q.w + (jj == row0 + 3 ? 1.f : 0.f), e, acc[3]);
+                    }
 #pragma unroll
-                    for (int jj = 0; jj < BJ2; ++jj)
-                        acc = fmaf(sQa[jj * BJ2 + row] + (jj == row ? 1.f : 0.f), sE[jj * BJ2 + col], acc);
-                    sT[rr * BJ2 + col] = acc;
+                    for (int u = 0; u < 4; ++u) sT[(rq + u) * BJ2 + col] = acc[u];
                 }
                 __syncwarp();
-                // the block: columns hc*8 .. +7 of T Q_b, the tile product's pairing of column halves
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int e = lane + 32 * q, rr = e >> 3, cc = e & 7;
+                // the block: columns hc*8 .. +7 of T Q_b, the tile product's pairing of column halves;
+                // a lane takes column cc of rows rr and rr + 4 (the same Q_b entries for both)
+                {
+                    const int rr = lane >> 3, cc = lane & 7;
                     const int c0 = hc * BJ, cp = c0 ^ BJ, tc = c0 + cc;
-                    float z = 0.f;
+                    float qs[BJ], qo[BJ];
 #pragma unroll
                     for (int jj = 0; jj < BJ; ++jj) {
-                        const float tv = sT[rr * BJ2 + c0 + jj], ov = sT[rr * BJ2 + cp + jj];
-                        const float qs = sQb[(c0 + jj) * BJ2 + tc] + ((c0 + jj) == tc ? 1.f : 0.f);
-                        const float qo = sQb[(cp + jj) * BJ2 + tc] + ((cp + jj) == tc ? 1.f : 0.f);
-                        z = fmaf(tv, qs, fmaf(ov, qo, z));
+                        qs[jj] = sQb[(c0 + jj) * BJ2 + tc] + ((c0 + jj) == tc ? 1.f : 0.f);
+                        qo[jj] = sQb[(cp + jj) * BJ2 + tc] + ((cp + jj) == tc ? 1.f : 0.f);
                     }
-                    sR[rr * BJ + cc] = z;
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const float* trow = sT + (rr + 4 * h2) * BJ2;
+                        const float4 t0 = *reinterpret_cast<const float4*>(trow + c0);
+                        const float4 t1 = *reinterpret_cast<const float4*>(trow + c0 + 4);
+                        const float4 o0 = *reinterpret_cast<const float4*>(trow + cp);
+                        const float4 o1 = *reinterpret_cast<const float4*>(trow + cp + 4);
+                        const float tv[BJ] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+                        const float ov[BJ] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+                        float z = 0.f;
+#pragma unroll
+                        for (int jj = 0; jj < BJ; ++jj) z = fmaf(tv[jj], qs[jj], fmaf(ov[jj], qo[jj], z));
+                        sR[(rr + 4 * h2) * BJ + cc] = z;
+                    }
                 }
                 __syncwarp();
-                // the 16 x 16 block: diagonal blocks from buffer g % 3, the cross blocks from sR
-                // (sR = [I, Jb], or [Jb, I] when swapped; the other one is its transpose)
+                // the 16 x 16 block's cross entries from sR (sR = [I, Jb], or [Jb, I] when
+                // swapped; the other cross block is its transpose)
                 if (lane < BJ2) {
 #pragma unroll
                     for (int r = 0; r < BJ2; ++r) {
                         const bool rI = r < BJ, cI = pos < BJ;
-                        if (rI == cI) {
-                            x[r] = Ec[(int64_t)bj_index(I, Jb, r) * J.ldE + gi];
-                        } else {
+                        if (rI != cI) {
                             // [I, Jb][u][v] with u the row in block I, v the column in block Jb
                             const int u = rI ? r : pos, v = rI ? pos - BJ : r - BJ;
                             x[r] = swap ? sR[v * BJ + u] : sR[u * BJ + v];
                         }
                     }
-                    d = J.D[gi];
-                } else {
-#pragma unroll
-                    for (int r = 0; r < BJ2; ++r) x[r] = 0.f;
                 }
             }
             unsigned int nrot = t == 0 ? inner_sweep<true>(x, d, I, Jb, J.k, qualifies)
@@ -1143,7 +1171,8 @@ __global__ void __launch_bounds__(kGbThreads, 1) k_jacobi_gblk(GbArgs A) {
 
         // ---- round g - 1's tiles (buffer (g - 1) % 3 rotated into buffer g % 3; a tile of two
         // pair-blocks that did not rotate is copied) and its F update, on the warps of the other
-        // SMSPs first
+        // SMSPs first (warp 0's SMSP runs the inner sweep alone: sharing it slows the sweep more
+        // than the extra warps speed up the tiles)
         {
             const int r0 = l16 >> 1, c0 = (l16 & 1) * BJ;
             const int ntile = s_pt[nm];

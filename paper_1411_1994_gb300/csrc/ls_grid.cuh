@@ -52,25 +52,27 @@ __device__ bool group_barrier(DevStatus* st, unsigned int nblocks) { return grou
 // Counting barrier: st->arrive only grows (zeroed before the launch), so the
 // e-th barrier of nb CTAs waits for e * nb arrivals and needs neither a reset
 // nor a generation word: one atomic and a polled load, where group_barrier
-// takes a load, an atomic and, for the last CTA, two more atomics. Bounded
-// like group_barrier: on timeout, or when another CTA raised the flag, it
-// returns false.
+// takes a load, an atomic and, for the last CTA, two more atomics. The arrival
+// is a release at GPU scope (it orders the CTA's writes, which the CTA barrier
+// before it orders before thread 0's) and the poll an acquire, in place of two
+// full fences. Bounded like group_barrier: on timeout, or when another CTA
+// raised the flag, it returns false.
 __device__ bool count_barrier(DevStatus* st, unsigned int target) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(&st->arrive, 1u);
-        volatile unsigned int* va = &st->arrive;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&st->arrive) : "memory");
         volatile int* vflag = &st->flag;
         int ok = 1;
         long long it = 0;
-        while (*va < target) {
+        for (;;) {
+            unsigned int v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&st->arrive) : "memory");
+            if (v >= target) break;
             if (*vflag != FLAG_OK) { ok = 0; break; }
             if (++it > kSpinLimit) { atomicCAS(&st->flag, FLAG_OK, FLAG_TIMEOUT); ok = 0; break; }
             __nanosleep(20);
         }
-        __threadfence();
         if (*vflag != FLAG_OK) ok = 0;
         s_ok = ok;
     }
