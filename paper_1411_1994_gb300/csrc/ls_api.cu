@@ -17,6 +17,7 @@
 #include <mutex>
 #include <map>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "ls_common.cuh"
@@ -68,6 +69,39 @@ struct HostBlock {
     std::vector<int32_t> m[3];   // vertex index of each site, per mode
 };
 
+// Defect window lists of one mode -> key index (the order of first appearance), looked up by a
+// 64-bit hash of the list and compared on a hit: no allocation per lookup (a context with
+// thousands of defects looks one up per defect and mode).
+struct KeyIndex {
+    std::unordered_multimap<uint64_t, int32_t> by_hash;
+    std::vector<int32_t> flat;         // key k: flat[off[k] .. off[k + 1])
+    std::vector<int64_t> off{0};
+    static uint64_t hash(const int32_t* w, int n) {
+        uint64_t h = 1469598103934665603ull ^ (uint64_t)n;   // FNV-1a over the words
+        for (int i = 0; i < n; ++i) {
+            h ^= (uint32_t)w[i];
+            h *= 1099511628211ull;
+        }
+        return h;
+    }
+    int32_t size() const { return (int32_t)(off.size() - 1); }
+    int32_t find(const int32_t* w, int n, uint64_t h) const {
+        const auto rng = by_hash.equal_range(h);
+        for (auto it = rng.first; it != rng.second; ++it) {
+            const int32_t k = it->second;
+            if (off[k + 1] - off[k] == n && std::equal(w, w + n, flat.begin() + off[k])) return k;
+        }
+        return -1;
+    }
+    int32_t add(const int32_t* w, int n, uint64_t h) {
+        const int32_t k = size();
+        flat.insert(flat.end(), w, w + n);
+        off.push_back((int64_t)flat.size());
+        by_hash.emplace(h, k);
+        return k;
+    }
+};
+
 struct ModeCols {
     int64_t C = 0, cap = 0;
     double* d_cols = nullptr;                    // [cap][N]
@@ -75,9 +109,15 @@ struct ModeCols {
     int32_t* d_desc = nullptr;                   // colq | woff | wcnt (3 * cap) on device
     int32_t* d_win = nullptr;
     int64_t wincap = 0;
-    std::map<std::vector<int32_t>, int32_t> keys;   // defect window set -> key index
-    std::vector<int32_t> count;                     // terms per column
+    KeyIndex keys;                               // defect window set -> key index
+    std::vector<int32_t> count;                  // terms per column
 };
+
+// capacity for `more` elements, growing geometrically (repeated calls stay linear)
+template <class V>
+void reserve_more(V& v, size_t more) {
+    if (v.size() + more > v.capacity()) v.reserve(std::max(v.size() + more, 2 * v.capacity()));
+}
 
 }  // namespace
 
@@ -627,8 +667,11 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n) {
     if (n < 0 || (n > 0 && !defects)) return fail(ctx, LS_ERR_ARG, "add_defects: bad defect array");
     const int R = ctx->p.R;
     const int nb = (int)ctx->blocks.size();
-    // validate everything first so that a bad entry changes nothing
-    std::vector<std::vector<int32_t>> key(3 * (size_t)n);
+    // validate everything first so that a bad entry changes nothing; the window list of
+    // defect i on axis a is kflat[koff[3 i + a] .. koff[3 i + a + 1])
+    std::vector<int32_t> kflat;
+    std::vector<int64_t> koff(3 * (size_t)n + 1, 0);
+    kflat.reserve(3 * (size_t)n);
     std::vector<double> dxi(n);
     for (int64_t i = 0; i < n; ++i) {
         const ls_defect& d = defects[i];
@@ -638,7 +681,8 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n) {
             for (int a = 0; a < 3; ++a) {
                 if (d.extent[a] < 1 || d.site[a] < 0 || d.site[a] + d.extent[a] > hb.b.L[a])
                     return fail(ctx, LS_ERR_ARG, "defect %lld: sites out of block range on axis %d", (long long)i, a);
-                for (int64_t e = 0; e < d.extent[a]; ++e) key[3 * i + a].push_back(hb.m[a][d.site[a] + e]);
+                for (int64_t e = 0; e < d.extent[a]; ++e) kflat.push_back(hb.m[a][d.site[a] + e]);
+                koff[3 * i + a + 1] = (int64_t)kflat.size();
             }
             dxi[i] = d.charge - hb.b.charge;
         } else if (d.kind == LS_DEFECT_POINT) {
@@ -646,7 +690,8 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n) {
                 int32_t m;
                 if (!snap_vertex(ctx, d.pos[a], &m))
                     return fail(ctx, LS_ERR_ARG, "defect %lld: position outside the box", (long long)i);
-                key[3 * i + a].push_back(m);
+                kflat.push_back(m);
+                koff[3 * i + a + 1] = (int64_t)kflat.size();
             }
             dxi[i] = d.charge;
         } else {
@@ -658,29 +703,28 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n) {
         ModeCols& mc = ctx->mode[l];
         std::vector<int32_t> q;
         std::vector<std::vector<int32_t>> wins, new_keys;
-        const int64_t first_new = mc.C;
-        int32_t next = (int32_t)mc.keys.size();
         for (int64_t i = 0; i < n; ++i) {
-            auto it = mc.keys.find(key[3 * i + l]);
-            int32_t kidx;
-            if (it == mc.keys.end()) {
-                kidx = next++;
-                mc.keys.emplace(key[3 * i + l], kidx);
+            const int32_t* w = kflat.data() + koff[3 * i + l];
+            const int nw = (int)(koff[3 * i + l + 1] - koff[3 * i + l]);
+            const uint64_t hk = KeyIndex::hash(w, nw);
+            int32_t kidx = mc.keys.find(w, nw, hk);
+            if (kidx < 0) {
+                kidx = mc.keys.add(w, nw, hk);
+                const std::vector<int32_t> kv(w, w + nw);
                 for (int qq = 0; qq < R; ++qq) {
                     q.push_back(qq);
-                    wins.push_back(key[3 * i + l]);
+                    wins.push_back(kv);
                 }
-                new_keys.push_back(key[3 * i + l]);
-            } else {
-                kidx = it->second;
+                new_keys.push_back(kv);
             }
             base[3 * i + l] = (int32_t)(nb * R) + kidx * R;
         }
-        (void)first_new;
         int rc = append_columns(ctx, l, q, wins);
         if (rc == LS_OK && ctx->tucker) rc = append_side(ctx, l, new_keys);
         if (rc != LS_OK) return rc;
     }
+    reserve_more(ctx->tcol, 3 * (size_t)n * R);
+    reserve_more(ctx->xi, (size_t)n * R);
     for (int64_t i = 0; i < n; ++i) {
         for (int qq = 0; qq < R; ++qq) {
             for (int l = 0; l < 3; ++l) {
@@ -1011,8 +1055,15 @@ int red_basis(RedState& R, CholJob* cj) {
             gate[l] = R.m[l].gate;
         }
         std::string err;
-        int rc = x64_gram(3, Yc, r64, N, nullptr, Gz, &R.d_st[9].flag, st, &err);
-        if (rc == LS_OK) rc = x64_lowdin(3, gc, rs, D2, Li, &R.d_st[9].flag, st, &err, gate);
+        int rc;
+        {
+            Scope sg("cholqr2.gram", st);
+            rc = x64_gram(3, Yc, r64, N, nullptr, Gz, &R.d_st[9].flag, st, &err);
+        }
+        if (rc == LS_OK) {
+            Scope ss("cholqr2.series", st);
+            rc = x64_lowdin(3, gc, rs, D2, Li, &R.d_st[9].flag, st, &err, gate);
+        }
         if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: CholeskyQR: %s", err.c_str());
     }
     return LS_OK;
@@ -1042,11 +1093,19 @@ int red_cholqr_mid(RedState& R) {
     {
         const int64_t r64[3] = {rs[0], rs[1], rs[2]};
         std::string err;
-        int rc = x64_apply(3, Li, rs, src, N, dst, &R.d_st[9].flag, st, &err);
-        if (rc == LS_OK) rc = x64_gram(3, yc, r64, N, nullptr, Gz, &R.d_st[9].flag, st, &err);
+        int rc;
+        {
+            Scope sa("cholqr2.apply", st);
+            rc = x64_apply(3, Li, rs, src, N, dst, &R.d_st[9].flag, st, &err);
+        }
+        if (rc == LS_OK) {
+            Scope sg("cholqr2.gram", st);
+            rc = x64_gram(3, yc, r64, N, nullptr, Gz, &R.d_st[9].flag, st, &err);
+        }
         if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: CholeskyQR: %s", err.c_str());
     }
     {
+        Scope ss("cholqr2.series", st);
         std::string err;
         int rc = x64_lowdin(3, gc, rs, D2, T, &R.d_st[9].flag, st, &err);
         if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: CholeskyQR series: %s", err.c_str());
@@ -1062,7 +1121,6 @@ int red_finish(RedState& R, ls_tucker_info* info) {
     ls_ctx* ctx = R.ctx;
     cudaStream_t st = ctx->st;
     const int64_t N = ctx->p.N;
-    const int64_t T = R.T;
     {
         const double *Li[3], *src[3];
         double* dst[3];
@@ -1074,6 +1132,7 @@ int red_finish(RedState& R, ls_tucker_info* info) {
             rs[l] = ctx->r[l];
         }
         Scope sc("cholqr2", st);
+        Scope sa("cholqr2.apply", st);
         std::string err;
         int rc = x64_apply(3, Li, rs, src, N, dst, &R.d_st[9].flag, st, &err);
         if (rc != LS_OK) return fail(ctx, rc, "rhosvd_reduce: CholeskyQR: %s", err.c_str());
@@ -1487,6 +1546,7 @@ int reduce_many(ls_ctx* const* ctxs, int n, double eps, const int32_t* forced, l
             if (int rc = gather(ctxs[i])) return rc;
         {
             Scope sc("cholqr2", s0);
+            Scope sf("cholqr2.factor", s0);
             const int rmax = chol32_max_r();
             std::vector<CholJob> small, large;
             for (const CholJob& J : cj) (J.r <= rmax ? small : large).push_back(J);

@@ -576,6 +576,9 @@ __device__ __forceinline__ void warp_argmax(unsigned long long& key, int& ix) {
 
 constexpr int kPcRows = 4;   // rows of the new column a warp forms at once
 
+// rows of column p of S a thread of k_pchol_multi holds in registers (the rest in shared memory)
+constexpr int kPmRowsPerThread = 2;
+
 __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
     const PcholMode J = A.m[find_job(A.m, A.nmodes)];
     const int lb = blockIdx.x - J.cta0, nb = J.ncta;
@@ -662,13 +665,21 @@ __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
             break;
         }
         if (k >= kend) break;
-        // 2. the panel part of row p of L (written by its owner in earlier steps) and column p of S
-        for (int t = k0 + tid; t < k; t += blockDim.x) lrow[t - k0] = __ldcg(J.L + (int64_t)p * J.kmax + t);
-        // S[j][p] from S's upper triangle (the Schur updates leave the lower one behind)
-        for (int jl = tid; jl < nr; jl += blockDim.x) {
+        // 2. column p of S and the panel part of row p of L (written by its owner in earlier
+        // steps). S[j][p] comes from S's upper triangle (the Schur updates leave the lower one
+        // behind); a thread's first kPmRowsPerThread rows wait in registers, so that their trip
+        // to L2 runs beside the dot products (the thread finishes those rows in step 4)
+        double gc[kPmRowsPerThread];
+#pragma unroll
+        for (int u = 0; u < kPmRowsPerThread; ++u) {
+            const int jl = tid + u * (int)blockDim.x, j = r0 + jl;
+            gc[u] = jl < nr ? __ldcg(J.S + (j < p ? (int64_t)j * C + p : (int64_t)p * C + j)) : 0.0;
+        }
+        for (int jl = tid + kPmRowsPerThread * (int)blockDim.x; jl < nr; jl += blockDim.x) {
             const int j = r0 + jl;
             gp[jl] = __ldcg(J.S + (j < p ? (int64_t)j * C + p : (int64_t)p * C + j));
         }
+        for (int t = k0 + tid; t < k; t += blockDim.x) lrow[t - k0] = __ldcg(J.L + (int64_t)p * J.kmax + t);
         __syncthreads();
         // 3. dot products, kPcRows rows a warp (warp 0 last), and 1 / sqrt(d_p) on warp 0
         if (tid == 0) s_inv = 1.0 / sqrt(dmax);
@@ -706,14 +717,20 @@ __global__ void __launch_bounds__(256) k_pchol_multi(PcholArgs A) {
         __syncthreads();
         // 4. the new column of L and the residual diagonal
         const double inv = s_inv;
-        for (int jl = tid; jl < nr; jl += blockDim.x) {
+        auto finish = [&](int jl, double g) {
             const int j = r0 + jl;
-            const double l = (gp[jl] - sacc[jl]) * inv;
+            const double l = (g - sacc[jl]) * inv;
             if (kk < kc) Ls[(size_t)jl * kc + kk] = l;
             __stcg(J.L + (int64_t)j * J.kmax + k, l);
             __stcg(J.Lp + (int64_t)j * pw + kk, l);
             ds[jl] = (j == p) ? 0.0 : fmax(ds[jl] - l * l, 0.0);
+        };
+#pragma unroll
+        for (int u = 0; u < kPmRowsPerThread; ++u) {
+            const int jl = tid + u * (int)blockDim.x;
+            if (jl < nr) finish(jl, gc[u]);
         }
+        for (int jl = tid + kPmRowsPerThread * (int)blockDim.x; jl < nr; jl += blockDim.x) finish(jl, gp[jl]);
         if (lb == 0 && tid == 0) J.piv[k] = p;
         __syncthreads();
         if (warp == 0) publish(par ^ 1);

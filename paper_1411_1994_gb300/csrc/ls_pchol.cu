@@ -29,6 +29,9 @@ namespace {
 constexpr int kPcThreads = 128;   // four warps: the quarters of each dot product
 
 static_assert(kPcThreads == 128, "the row dot products are split over exactly four warps");
+// rows a thread of the panel kernel finishes (its rows' column of S waits in registers): the
+// launcher takes at most kCpRowsPerThread * kPcThreads rows a CTA
+constexpr int kCpRowsPerThread = 4;
 
 struct PcMode {
     const double* G; double* L; double* resid; int* piv; DevStatus* st; int C; int kmax; double delta;
@@ -224,8 +227,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cpanel(CpArgs A) {
     double* d = Ls + (size_t)rp * ldL;                            // [rp]
     double* lrow = d + rp;                                        // [pw]
     double* part = lrow + pw;                                     // [4][rp] quarter sums
-    double* gcol = part + 4 * (size_t)rp;                         // [rp] S[own rows, p]
-    Cand* cand = reinterpret_cast<Cand*>(gcol + rp);              // [2][cs]
+    Cand* cand = reinterpret_cast<Cand*>(part + 4 * (size_t)rp);  // [2][cs]
     __shared__ double s_dmax, s_sum, s_inv;
     __shared__ int s_p;
 
@@ -289,16 +291,20 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cpanel(CpArgs A) {
         }
         if (k >= kend) break;
         const int kk = k - k0;
-        // the panel part of row p from its owner, column p of S for the own rows
+        // column p of S for the own rows, into registers: S[j][p] from S's upper triangle (the
+        // Schur updates leave the lower one behind); its trip to L2 runs beside the dot products,
+        // and the thread that loads row jl is the one that finishes it below
+        double gc[kCpRowsPerThread];
+#pragma unroll
+        for (int u = 0; u < kCpRowsPerThread; ++u) {
+            const int jl = tid + u * kPcThreads, j = r0 + jl;
+            gc[u] = jl < nr ? __ldcg(J.S + (j < p ? (int64_t)j * C + p : (int64_t)p * C + j)) : 0.0;
+        }
+        // the panel part of row p from its owner
         {
             const int owner = p / rp;
             const double* src = cl.map_shared_rank(Ls, owner) + (size_t)(p - owner * rp) * ldL;
             for (int t = tid; t < kk; t += nthr) lrow[t] = src[t];
-            // S[j][p] from S's upper triangle (the Schur updates leave the lower one behind)
-            for (int jl = tid; jl < nr; jl += nthr) {
-                const int j = r0 + jl;
-                gcol[jl] = __ldcg(J.S + (j < p ? (int64_t)j * C + p : (int64_t)p * C + j));
-            }
         }
         __syncthreads();
         const double inv = s_inv;
@@ -317,9 +323,12 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cpanel(CpArgs A) {
             }
         }
         __syncthreads();
-        for (int jl = tid; jl < nr; jl += nthr) {
+#pragma unroll
+        for (int u = 0; u < kCpRowsPerThread; ++u) {
+            const int jl = tid + u * kPcThreads;
+            if (jl >= nr) break;
             const double dot = ((part[jl] + part[rp + jl]) + part[2 * rp + jl]) + part[3 * rp + jl];
-            const double l = (gcol[jl] - dot) * inv;
+            const double l = (gc[u] - dot) * inv;
             Ls[(size_t)jl * ldL + kk] = l;
             __stcg(J.L + (int64_t)(r0 + jl) * kmax + k, l);
             __stcg(J.Lp + (int64_t)(r0 + jl) * pw + kk, l);
@@ -346,7 +355,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol_cpanel(CpArgs A) {
 }
 
 size_t cp_smem(int cs, int rp, int pw) {
-    return 8 * ((size_t)rp * (pw | 1) + rp + pw + 4 * (size_t)rp + rp) + sizeof(Cand) * 2 * (size_t)cs;
+    return 8 * ((size_t)rp * (pw | 1) + rp + pw + 4 * (size_t)rp) + sizeof(Cand) * 2 * (size_t)cs;
 }
 
 size_t pc_smem(int C, int kmax, int cs, int rp) {
@@ -502,7 +511,7 @@ cudaError_t launch_pchol_cluster(const PcholJob* jobs, int njobs, cudaStream_t s
 // whether the panel form's clusters (16 CTAs, else 8) hold every job's rows for this panel width
 bool pchol_cpanel_fits(int64_t Cmax, int panel) {
     const size_t cap = (size_t)smem_cap();
-    return cp_smem(8, (int)((Cmax + 7) / 8), panel) <= cap;
+    return cp_smem(8, (int)((Cmax + 7) / 8), panel) <= cap && (Cmax + 7) / 8 <= kCpRowsPerThread * kPcThreads;
 }
 
 cudaError_t launch_pchol_cpanel(const PcholJob* jobs, int panel, int njobs, int* d_report, cudaStream_t st) {
@@ -538,6 +547,7 @@ cudaError_t launch_pchol_cpanel(const PcholJob* jobs, int panel, int njobs, int*
         if ((e = cp_reserve_smem(cfg.dynamicSmemBytes)) != cudaSuccess) return e;
     }
     const int rp = (int)((Cmax + cs - 1) / cs);
+    if (rp > kCpRowsPerThread * kPcThreads) return cudaErrorInvalidValue;
     std::vector<CpMode> hm(njobs);
     for (int m = 0; m < njobs; ++m) {
         const PcholJob& J = jobs[m];

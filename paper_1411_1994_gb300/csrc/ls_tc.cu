@@ -32,7 +32,6 @@ using namespace tc5;
 constexpr int TBM = 128, TBN = 64, TBK = 32;
 constexpr int TILE_A = TBM * TBK * 2;          // bytes of one bf16 A tile (8 KB)
 constexpr int TILE_B = TBN * TBK * 2;          // 4 KB
-constexpr int TC_THREADS = 192;                // warp 0 TMA, warp 1 MMA + TMEM, warps 2-5 epilogue
 
 enum OutMode : int { OUT_F64 = 0, OUT_F32 = 1 };
 
@@ -67,6 +66,10 @@ constexpr int XKCHUNK = 512;                        // K per exact accumulation
 constexpr int XSTAGE = XSL * (TILE_A + TILE_B);     // 96 KB
 constexpr int XNST = 2;                             // stages
 constexpr int XTMEM = XSL * TBN;                    // 512 columns
+// warp 0 TMA, warp 1 MMA + TMEM, warps 2-9 epilogue: two warps a TMEM lane quarter, each
+// holding the running FP64 sums of half the tile's columns in registers across the K-chunks
+constexpr int X64_THREADS = 320;
+constexpr int X64_EPI_COLS = TBN / 2;
 
 struct X64Job {
     CUtensorMap a, b;     // (k, row, slice): the eight digit matrices of each operand
@@ -121,9 +124,11 @@ __device__ __forceinline__ double rn_scaled(long long hi, long long lo, int s) {
 
 // One 128 x 64 output tile of one job per CTA, all of K: the K-chunks of 512 run in
 // turn on the same eight accumulators (the MMA warp waits until the epilogue has drained
-// them); the epilogue adds each chunk's recombined value into the output tile, which only
-// this CTA writes.
-__global__ void __launch_bounds__(TC_THREADS, 1) k_x64_gemm(const __grid_constant__ X64Group G, int* flag) {
+// them). The epilogue adds each chunk's recombined value to a running FP64 sum in
+// registers (the first chunk starting from the output where it accumulates) and writes
+// the tile, which only this CTA writes, once: the same additions in the same order as
+// adding every chunk into the output in turn.
+__global__ void __launch_bounds__(X64_THREADS, 1) k_x64_gemm(const __grid_constant__ X64Group G, int* flag) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + XNST * XSTAGE);   // [XNST]
@@ -149,7 +154,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_x64_gemm(const __grid_constan
             mbar_init(&empty[s], 1);
         }
         mbar_init(accum, 1);
-        mbar_init(drained, 4);   // one arrival per epilogue warp
+        mbar_init(drained, (X64_THREADS - 64) / 32);   // one arrival per epilogue warp
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -210,18 +215,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_x64_gemm(const __grid_constan
             mma_commit(accum);
         }
     } else if (warp >= 2) {
-        const int q = warp & 3;
+        const int q = warp & 3, c0 = ((warp - 2) >> 2) * X64_EPI_COLS;
         const int row = m0 + 32 * q + lane;
         const int er = row < J.M ? J.ea[row] : 0;
         const uint32_t lanes = (uint32_t)(32 * q) << 16;
+        double acc[X64_EPI_COLS];
+        bool all = true;
         for (int c = 0; c < nchunk; ++c) {
-            if (!mbar_wait(accum, c & 1, flag)) break;
+            if (!mbar_wait(accum, c & 1, flag)) { all = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const bool add = c > 0 || J.out.accumulate;
-            for (int cc = 0; cc < TBN; cc += 8) {
-                float S[XSL][8];
 #pragma unroll
-                for (int l = 0; l < XSL; ++l) tmem_ld8(tmem + lanes + (uint32_t)(l * TBN + cc), S[l]);
+            for (int g = 0; g < X64_EPI_COLS / 8; ++g) {
+                const int cc = c0 + 8 * g;
+                // the eight levels of eight columns: eight loads, one wait
+                uint32_t S[XSL][8];
+#pragma unroll
+                for (int l = 0; l < XSL; ++l) tmem_ld8_issue(tmem + lanes + (uint32_t)(l * TBN + cc), S[l]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int l = 0; l < XSL; ++l) reg_after_wait8(S[l]);
                 if (row >= J.M) continue;
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
@@ -230,20 +242,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_x64_gemm(const __grid_constan
                     // exact level sums (integers below 2^24), recombined by Horner steps in int64
                     long long hi = 0, lo = 0;
 #pragma unroll
-                    for (int l = 0; l < 4; ++l) hi = hi * 128 + (long long)__float2int_rn(S[l][jj]);
+                    for (int l = 0; l < 4; ++l) hi = hi * 128 + (long long)__float2int_rn(__uint_as_float(S[l][jj]));
 #pragma unroll
-                    for (int l = 4; l < 8; ++l) lo = lo * 128 + (long long)__float2int_rn(S[l][jj]);
+                    for (int l = 4; l < 8; ++l) lo = lo * 128 + (long long)__float2int_rn(__uint_as_float(S[l][jj]));
                     // sum_l S_l 2^(-7(l+2)) = (hi 2^28 + lo) 2^-63, times 2^(E_a + E_b)
                     const double v0 = rn_scaled(hi, lo, er + J.eb[col] - 63);
                     const double v = J.out.negate ? -v0 : v0;
-                    double* o = (double*)J.out.p +
-                                (J.transposed ? (int64_t)col * J.out.ld + row : (int64_t)row * J.out.ld + col);
-                    *o = add ? *o + v : v;
+                    double& a = acc[8 * g + jj];
+                    if (c > 0) {
+                        a = a + v;
+                    } else if (J.out.accumulate) {
+                        const double* o = (const double*)J.out.p +
+                                          (J.transposed ? (int64_t)col * J.out.ld + row : (int64_t)row * J.out.ld + col);
+                        a = *o + v;
+                    } else {
+                        a = v;
+                    }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(drained)) : "memory");
+        }
+        if (all && row < J.M) {
+#pragma unroll
+            for (int i = 0; i < X64_EPI_COLS; ++i) {
+                const int col = n0 + c0 + i;
+                if (col >= J.N) continue;
+                double* o = (double*)J.out.p + (J.transposed ? (int64_t)col * J.out.ld + row : (int64_t)row * J.out.ld + col);
+                *o = acc[i];
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -439,7 +467,7 @@ int gemm_x64(const X64Spec* sp, int n, int* flag, cudaStream_t st, std::string* 
         attr_err = cudaFuncSetAttribute(k_x64_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     });
     if (attr_err != cudaSuccess) return tc_err(err, "x64 gemm: cannot reserve shared memory");
-    k_x64_gemm<<<blocks, TC_THREADS, smem, st>>>(g, flag);
+    k_x64_gemm<<<blocks, X64_THREADS, smem, st>>>(g, flag);
     count_kernels(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return tc_err(err, std::string("x64 gemm launch: ") + cudaGetErrorString(e));
