@@ -651,8 +651,8 @@ __global__ void k_split_rows(Src src, int64_t rows, int64_t cols, int64_t batch,
 
 // Operand rows n of a pair matrix stored transposed, x(n, k) = W[k * ld + n] (k < cols):
 // pass 1 has a thread per row walk k (reads coalesced across rows); pass 2 splits
-// 32 x 64 tiles through shared memory so that both the reads (along n) and the
-// writes (along k) are contiguous.
+// 64 x 64 tiles through shared memory so that both the reads (along n) and the
+// writes (along k: 128 bytes of a row and part, a whole line) are contiguous.
 __global__ void k_rowmax_tr(const float2* __restrict__ W, int64_t ld, int64_t rows, int64_t cols,
                             unsigned long long* __restrict__ mb) {
     const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -661,25 +661,27 @@ __global__ void k_rowmax_tr(const float2* __restrict__ W, int64_t ld, int64_t ro
     for (int64_t k = 0; k < cols; ++k) m = max(m, __float_as_uint(W[k * ld + n].x) & 0x7fffffffu);
     mb[n] = m;
 }
+constexpr int kTrRows = 64, kTrK = 64;
 __global__ void __launch_bounds__(256) k_split_tr(const float2* __restrict__ W, int64_t ld, int64_t rows, int64_t cols,
                                                   int64_t kpad, const unsigned long long* __restrict__ mb,
                                                   unsigned short* __restrict__ parts, int* __restrict__ exps) {
-    __shared__ unsigned int tile[4][64][17];   // [part][row][k pairs of u16], padded
-    const int64_t n0 = blockIdx.x * 64, k0 = blockIdx.y * 32;
+    __shared__ unsigned int tile[4][kTrRows][kTrK / 2 + 1];   // [part][row][k pairs of u16], padded
+    const int64_t n0 = blockIdx.x * (int64_t)kTrRows, k0 = blockIdx.y * (int64_t)kTrK;
     const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // 64 rows x 4 k-lanes
     const int64_t n = n0 + tx;
     const SrcPair src{W, 1, ld, 0};
     const int E = (n < rows && mb[n]) ? SrcPair::exp_of(mb[n]) : 0;
     if (blockIdx.y == 0 && ty == 0 && n < rows) exps[n] = E;
-    // the thread's eight entries loaded first (eight reads in flight), then split
-    float2 v[8];
+    // the thread's sixteen entries loaded first (sixteen reads in flight), then split
+    constexpr int NV = kTrK / 4;
+    float2 v[NV];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < NV; ++q) {
         const int kk = ty * 2 + 8 * (q >> 1) + (q & 1);
         v[q] = (n < rows && k0 + kk < cols) ? src.at(0, n, k0 + kk) : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int q = 0; q < 8; q += 2) {
+    for (int q = 0; q < NV; q += 2) {
         const int kk = ty * 2 + 8 * (q >> 1);
         unsigned short a[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
         if (n < rows && k0 + kk < cols) split_pair(v[q], E, a[0], a[1], a[2], a[3]);
@@ -688,10 +690,10 @@ __global__ void __launch_bounds__(256) k_split_tr(const float2* __restrict__ W, 
         for (int p = 0; p < 4; ++p) tile[p][tx][kk >> 1] = (unsigned)a[p] | ((unsigned)c[p] << 16);
     }
     __syncthreads();
-    // write: each row n of the tile is 32 u16 = 16 words per part
+    // write: each row n of the tile is 64 u16 = 32 words per part, a warp per row and part
     const int64_t ps = rows * kpad;
-    for (int e = threadIdx.x; e < 4 * 64 * 16; e += 256) {
-        const int p = e / (64 * 16), rr = (e / 16) % 64, w = e % 16;
+    for (int e = threadIdx.x; e < 4 * kTrRows * (kTrK / 2); e += 256) {
+        const int p = e / (kTrRows * (kTrK / 2)), rr = (e / (kTrK / 2)) % kTrRows, w = e % (kTrK / 2);
         const int64_t nn = n0 + rr, kk = k0 + 2 * w;
         if (nn < rows && kk < kpad)
             reinterpret_cast<unsigned int*>(parts + p * ps + nn * kpad + kk)[0] = tile[p][rr][w];
@@ -780,8 +782,8 @@ cudaError_t dt_split_tr(const float2* W, int64_t ld, int64_t cols, const DtOp& d
     unsigned long long* mb = ar.get<unsigned long long>(d.rows);
     if (!mb) return cudaErrorMemoryAllocation;
     k_rowmax_tr<<<(unsigned)((d.rows + 255) / 256), 256, 0, st>>>(W, ld, d.rows, cols, mb);
-    k_split_tr<<<dim3((unsigned)((d.rows + 63) / 64), (unsigned)(d.kpad / 32)), 256, 0, st>>>(W, ld, d.rows, cols,
-                                                                                           d.kpad, mb, d.p, d.e);
+    k_split_tr<<<dim3((unsigned)((d.rows + kTrRows - 1) / kTrRows), (unsigned)((d.kpad + kTrK - 1) / kTrK)), 256, 0, st>>>(
+        W, ld, d.rows, cols, d.kpad, mb, d.p, d.e);
     count_kernels(2);
     return cudaGetLastError();
 }
