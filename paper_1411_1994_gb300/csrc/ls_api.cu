@@ -73,7 +73,8 @@ struct HostBlock {
 // 64-bit hash of the list and compared on a hit: no allocation per lookup (a context with
 // thousands of defects looks one up per defect and mode).
 struct KeyIndex {
-    std::unordered_multimap<uint64_t, int32_t> by_hash;
+    std::unordered_multimap<uint64_t, int32_t> by_hash;   // lists of two or more windows
+    std::vector<int32_t> single;       // one-window lists (point defects, single sites): by vertex
     std::vector<int32_t> flat;         // key k: flat[off[k] .. off[k + 1])
     std::vector<int64_t> off{0};
     static uint64_t hash(const int32_t* w, int n) {
@@ -86,6 +87,7 @@ struct KeyIndex {
     }
     int32_t size() const { return (int32_t)(off.size() - 1); }
     int32_t find(const int32_t* w, int n, uint64_t h) const {
+        if (n == 1 && w[0] >= 0) return w[0] < (int32_t)single.size() ? single[w[0]] : -1;
         const auto rng = by_hash.equal_range(h);
         for (auto it = rng.first; it != rng.second; ++it) {
             const int32_t k = it->second;
@@ -97,7 +99,12 @@ struct KeyIndex {
         const int32_t k = size();
         flat.insert(flat.end(), w, w + n);
         off.push_back((int64_t)flat.size());
-        by_hash.emplace(h, k);
+        if (n == 1 && w[0] >= 0) {
+            if (w[0] >= (int32_t)single.size()) single.resize((size_t)w[0] + 1, -1);
+            single[w[0]] = k;
+        } else {
+            by_hash.emplace(h, k);
+        }
         return k;
     }
 };
@@ -723,16 +730,23 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n) {
         if (rc == LS_OK && ctx->tucker) rc = append_side(ctx, l, new_keys);
         if (rc != LS_OK) return rc;
     }
+    // R terms a defect, one per quadrature node: term t's columns tcol[3 t + l], weight xi[t]
+    const size_t t0 = ctx->xi.size();
     reserve_more(ctx->tcol, 3 * (size_t)n * R);
     reserve_more(ctx->xi, (size_t)n * R);
+    ctx->tcol.resize(3 * (t0 + (size_t)n * R));
+    ctx->xi.resize(t0 + (size_t)n * R);
+    int32_t* tc = ctx->tcol.data() + 3 * t0;
+    double* xv = ctx->xi.data() + t0;
+    int32_t* cnt[3] = {ctx->mode[0].count.data(), ctx->mode[1].count.data(), ctx->mode[2].count.data()};
     for (int64_t i = 0; i < n; ++i) {
         for (int qq = 0; qq < R; ++qq) {
             for (int l = 0; l < 3; ++l) {
                 const int32_t c = base[3 * i + l] + qq;
-                ctx->tcol.push_back(c);
-                ctx->mode[l].count[c] += 1;
+                *tc++ = c;
+                cnt[l][c] += 1;
             }
-            ctx->xi.push_back(dxi[i]);
+            *xv++ = dxi[i];
         }
         if (ctx->tucker) {
             // one Tucker term per defect; key index = column base / R (blocks first)

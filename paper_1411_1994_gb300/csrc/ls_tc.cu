@@ -676,7 +676,7 @@ int x64_pchol_gram(int n, const double* const L[], const int64_t kmax[], const i
 // out_l first and the product added to it.
 int x64_small(int n, const double* const A[], const int ta[], const double* const B[], const int tb[],
               const int k[], double* const out[], const double* const add[], int* flag, cudaStream_t st,
-              std::string* err) {
+              std::string* err, const int* const skip[]) {
     for (int g0 = 0; g0 < n; g0 += kX64MaxJobs) {
         const int ng = std::min(kX64MaxJobs, n - g0);
         Arena ar(st);
@@ -695,7 +695,8 @@ int x64_small(int n, const double* const A[], const int ta[], const double* cons
             if (add && add[l] && add[l] != out[l] &&
                 cudaMemcpyAsync(out[l], add[l], sizeof(double) * kk * kk, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
                 return tc_err(err, "x64_small: copy failed");
-            sp[i] = X64Spec{&xs[i], &ys[i], kk, kk, TcOut{out[l], kk, 0, OUT_F64, (add && add[l]) ? 1 : 0}, 0};
+            sp[i] = X64Spec{&xs[i], &ys[i], kk, kk, TcOut{out[l], kk, 0, OUT_F64, (add && add[l]) ? 1 : 0}, 0, 0,
+                            skip ? skip[l] : nullptr};
         }
         if (sb.flush() != cudaSuccess) return tc_err(err, "x64_small: split failed");
         int rc = gemm_x64(sp.data(), ng, flag, st, err);
@@ -714,6 +715,7 @@ struct LowdinSet {
     const double* D3[kX64MaxJobs];
     double* T[kX64MaxJobs];
     double* gate[kX64MaxJobs];   // ||S - I||_F (gated form; else null)
+    int* off[kX64MaxJobs];       // gated form: 1 where the gate sends the matrix to the Cholesky pass
     int k[kX64MaxJobs];
 };
 // gate[j] = ||S_j - I||_F, one block per matrix (fixed reduction order)
@@ -732,7 +734,9 @@ __global__ void __launch_bounds__(1024) k_dist_identity(const __grid_constant__ 
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        *L.gate[j] = sqrt(t);
+        const double g = sqrt(t);
+        *L.gate[j] = g;
+        *L.off[j] = !(g < kSeriesGate);   // the test k_lowdin_combine makes
     }
 }
 __global__ void k_minus_identity(const __grid_constant__ LowdinSet L) {
@@ -778,18 +782,25 @@ int x64_lowdin(int n, const double* const S[], const int k[], double* const D2[]
             emax = std::max(emax, e);
         }
         const dim3 grid((unsigned)((emax + 255) / 256), (unsigned)ng);
+        // gated form: the powers of a matrix that the gate sends to the Cholesky pass are not
+        // formed (its products read the flag that k_dist_identity writes)
+        std::vector<const int*> offc(ng, nullptr);
         if (gate) {
+            int* off = ar.get<int>(ng);
+            if (!off) return tc_err(err, "x64_lowdin: out of memory", LS_ERR_OOM);
+            for (int i = 0; i < ng; ++i) offc[i] = L.off[i] = off + i;
             k_dist_identity<<<ng, 1024, 0, st>>>(L);
             count_kernels(1);
         }
         k_minus_identity<<<grid, 256, 0, st>>>(L);
         count_kernels(1);
         // Delta is symmetric: Delta^2 = Delta Delta^T and Delta^3 = Delta^2 Delta^T need no transposes
+        const int* const* skip = gate ? offc.data() : nullptr;
         int rc = x64_small(ng, Dlc.data(), zero.data(), Dlc.data(), one.data(), kk.data(), D2m.data(), nullptr, flag, st,
-                           err);
+                           err, skip);
         if (rc == LS_OK)
             rc = x64_small(ng, D2c.data(), zero.data(), Dlc.data(), one.data(), kk.data(), D3.data(), nullptr, flag, st,
-                           err);
+                           err, skip);
         if (rc != LS_OK) return rc;
         k_lowdin_combine<<<grid, 256, 0, st>>>(L);
         count_kernels(1);

@@ -48,14 +48,15 @@ int x64_pchol_vectors(int n, const double* const L[], const int64_t kmax[], cons
 int x64_pchol_gram(int n, const double* const L[], const int64_t kmax[], const int k[], const int64_t C[],
                    double* const H[], int* flag, cudaStream_t st, std::string* err);
 // out_l = op(A_l) op(B_l) (+ add_l) for k_l x k_l row-major matrices (ta/tb: 1 = transpose;
-// add may be null).
+// add may be null). skip (if given): device flags, product l not formed when *skip[l] != 0
+// as it runs.
 int x64_small(int n, const double* const A[], const int ta[], const double* const B[], const int tb[],
               const int k[], double* const out[], const double* const add[], int* flag, cudaStream_t st,
-              std::string* err);
+              std::string* err, const int* const skip[] = nullptr);
 // T_l = S_l^{-1/2} by the series I - Delta/2 + 3/8 Delta^2 - 5/16 Delta^3 (Delta = S_l - I);
 // D2_l receives Delta^2 (scratch of the caller). With gate (device doubles, one per
-// matrix): gate_l = ||Delta_l||_F, and T_l is written only where gate_l < kSeriesGate
-// (elsewhere a Cholesky pass gated on the same value writes it).
+// matrix): gate_l = ||Delta_l||_F, and T_l (and D2_l) are formed only where gate_l <
+// kSeriesGate (elsewhere a Cholesky pass gated on the same value writes T_l).
 int x64_lowdin(int n, const double* const S[], const int k[], double* const D2[], double* const T[], int* flag,
                cudaStream_t st, std::string* err, double* const gate[] = nullptr);
 // A strided FP64 operand: entry (i, k) = p[i * si + k * sk], i < rows, k < cols, row i scaled
