@@ -630,23 +630,28 @@ __global__ void k_rowmax(Src src, int64_t rows, int64_t cols, unsigned long long
     for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0 && m) atomicMax(mb + row, m);
 }
-// Pass 2: one thread per entry (row, k).
+// Pass 2: four consecutive entries (row, k .. k + 3) a thread (kpad is a multiple of 32),
+// each part's four values stored as one 8-byte word.
 template <class Src>
 __global__ void k_split_rows(Src src, int64_t rows, int64_t cols, int64_t batch, int64_t kpad,
                              const unsigned long long* __restrict__ mb, unsigned short* __restrict__ parts,
                              int* __restrict__ exps) {
     const int64_t row = blockIdx.y, b = row / rows, i = row - b * rows;
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t k = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
     if (k >= kpad) return;
     const int E = mb[row] ? Src::exp_of(mb[row]) : 0;
     if (k == 0) exps[row] = E;
-    unsigned short p0 = 0, p1 = 0, p2 = 0, p3 = 0;
-    if (k < cols) split_entry(src, b, i, k, E, p0, p1, p2, p3);
+    unsigned short q[4][4];   // [part][entry]
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        q[0][u] = q[1][u] = q[2][u] = q[3][u] = 0;
+        if (k + u < cols) split_entry(src, b, i, k + u, E, q[0][u], q[1][u], q[2][u], q[3][u]);
+    }
     const int64_t ps = batch * rows * kpad, off = row * kpad + k;
-    parts[off] = p0;
-    parts[ps + off] = p1;
-    parts[2 * ps + off] = p2;
-    parts[3 * ps + off] = p3;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+        *reinterpret_cast<uint2*>(parts + p * ps + off) =
+            make_uint2((unsigned)q[p][0] | ((unsigned)q[p][1] << 16), (unsigned)q[p][2] | ((unsigned)q[p][3] << 16));
 }
 
 // Operand rows n of a pair matrix stored transposed, x(n, k) = W[k * ld + n] (k < cols):
@@ -768,7 +773,7 @@ cudaError_t dt_split(Src src, int64_t cols, const DtOp& d, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(mb, 0, nrows * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     k_rowmax<Src><<<dim3((unsigned)((cols + 1023) / 1024), (unsigned)nrows), 256, 0, st>>>(src, d.rows, cols, mb);
-    k_split_rows<Src><<<dim3((unsigned)((d.kpad + 255) / 256), (unsigned)nrows), 256, 0, st>>>(
+    k_split_rows<Src><<<dim3((unsigned)((d.kpad / 4 + 255) / 256), (unsigned)nrows), 256, 0, st>>>(
         src, d.rows, cols, d.batch, d.kpad, mb, d.p, d.e);
     count_kernels(2);
     return cudaGetLastError();
