@@ -77,6 +77,25 @@ def test_fitted_scale_error_holds_on_dense_grid():
     assert dense < 1e-7
 
 
+def test_fitted_scale_is_a_local_minimum():
+    """Sec. 2.1 chooses the quadrature so that the kernel is reproduced to a tolerance; the
+    oracle's fit takes the scale s that minimises the largest relative error on its r-grid. The
+    returned error is the error at the returned s, and moving s by 0.1 %, 1 % or 3 % either way
+    gives no smaller error on the same grid (a search that kept the wrong half of a bracket, or
+    returned a bracket end, fails this)."""
+    for R, h, r0, r1 in ((24, 0.25, 0.25, 20.0), (28, 0.25, 0.25, 48.5), (20, 0.3, 0.5, 30.0)):
+        s, e = O.fit_t_scale(R, h, r0, r1)
+        r = np.geomspace(r0, r1, 600)
+
+        def err(sc):
+            t, w = O.sinc_quadrature(R, h, sc)
+            return float(np.max(O.quadrature_rel_error(t, w, r)))
+
+        assert err(s) == e
+        for f in (0.97, 0.99, 0.999, 1.001, 1.01, 1.03):
+            assert err(s * f) >= e * (1.0 - 1e-12), (R, f, err(s * f), e)
+
+
 # --- (a0) the Yukawa kernel: Sec. 2.3, Eq. LalpYukawa ----------------------
 
 def test_yukawa_laplace_gauss_identity_and_reading():
