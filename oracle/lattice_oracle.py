@@ -538,6 +538,13 @@ def als_refine(cols, tcol, xi, Z0, sweeps: int = 3, chunk: int = 512):
     ncols, _, xin = normalise_terms(cols, tcol, xi)
     Z = [np.array(z, dtype=np.float64) for z in Z0]
     r = [z.shape[1] for z in Z]
+    # B_l has min(N, r_m r_n) singular vectors: a start whose rank r_l exceeds that would leave
+    # Y_l with fewer columns than asked (the step could not keep the rank)
+    for l in range(3):
+        m, n = [a for a in range(3) if a != l]
+        if r[l] > min(ncols[l].shape[1], r[m] * r[n]):
+            raise ValueError(f"als_refine: rank {r[l]} of mode {l} exceeds min(N, r_m r_n) = "
+                             f"{min(ncols[l].shape[1], r[m] * r[n])}")
 
     def core_of(Z):
         return core_tensor([Z[a].T @ ncols[a].T for a in range(3)], tcol, xin)

@@ -677,6 +677,21 @@ def test_als_fixed_point_at_exact_rank():
     assert abs(hist[-1] - hist[0]) <= 1e-12 * hist[0]
 
 
+def test_als_refuses_a_start_rank_it_cannot_keep():
+    """One ALS step takes r_l leading singular vectors of the N x (r_m r_n) matrix B_l
+    (Thm A.1(b)); a start with r_l > r_m r_n cannot keep its rank, and the oracle says so
+    instead of returning a basis with fewer columns."""
+    wl = W.small_case(L=(3, 2, 2), N=24, R=10, frac_vac=0.3, frac_imp=0.2, eps=1e-3)
+    s, t, w, g, cols, tcol, xi = _terms(wl)
+    rng = np.random.default_rng(7)
+    Z0 = [np.linalg.qr(rng.standard_normal((wl.N, k)))[0] for k in (5, 2, 2)]
+    with pytest.raises(ValueError):
+        O.als_refine(cols, tcol, xi, Z0, sweeps=1)
+    Z0[0] = Z0[0][:, :4]   # r_0 = r_1 r_2 is allowed
+    Z, core, hist = O.als_refine(cols, tcol, xi, Z0, sweeps=1)
+    assert [z.shape[1] for z in Z] == [4, 2, 2]
+
+
 # --- (d) slabs ---------------------------------------------------------------
 
 def test_slab_evaluation_matches_full_tensors(defected_small):
