@@ -33,6 +33,23 @@ FP64_PEAK_TFLOPS_DERIVED = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk x flo
 FP32_PEAK_TFLOPS_DERIVED = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FFMA/clk x flops x max clock
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of a per-rank number over all ranks of the process group (the slowest rank's
+    time); x itself without one."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, seconds_per_step):
+    """Units of all ranks per second: every rank (one GPU each) runs its own replica of the
+    workload, so the job processes world x units in the slowest rank's step time."""
+    return world * units_per_rank / seconds_per_step
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -495,13 +512,10 @@ def run_batch(args, torch, B, L):
         clk = clocks.stop() if clocks else None
         L.profile(False)
         rep = L.profile_report()
-        total_ms = sum(a.elapsed_time(b) for a, b in ev)
-        if dist:
-            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, "cuda")
         ms = total_ms / args.steps
-        return {"value": world * units / (ms / 1e3), "ms_per_step": ms, "infos": infos, "report": rep, "clocks": clk}
+        return {"value": whole_job_rate(world, units, ms / 1e3), "ms_per_step": ms, "infos": infos, "report": rep,
+                "clocks": clk}
 
     head = timed(True, True)
     seq = None if args.no_compare else timed(False, False)
@@ -607,14 +621,11 @@ def main():
         clk = clocks.stop() if clocks else None
         L.profile(False)
         report = L.profile_report()
-        total_ms = sum(a.elapsed_time(b) for a, b in ev)
+        total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, "cuda")
         if dist:
-            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
             dist.barrier()
         ms = total_ms / args.steps
-        return {"value": world * wl.units / (ms / 1e3), "ms_per_step": ms, "info": info, "report": report,
+        return {"value": whole_job_rate(world, wl.units, ms / 1e3), "ms_per_step": ms, "info": info, "report": report,
                 "clocks": clk, "wall": wall}
 
     def e2e(prec):
@@ -645,7 +656,8 @@ def main():
         L.profile(False)
         rep = L.profile_report()
         n = len(times)
-        return {"value": world * wl.units / (sum(times) / n), "unit": "potentials/s",
+        mean_s = max_over_ranks(sum(times) / n, dist, "cuda")
+        return {"value": whole_job_rate(world, wl.units, mean_s), "unit": "potentials/s",
                 "h2d_bytes_per_step": int(rep["h2d_bytes"] // n), "d2h_bytes_per_step": int(rep["d2h_bytes"] // n)}
 
     def eval_timing(prec):
