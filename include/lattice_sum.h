@@ -262,11 +262,16 @@ int lattice_sum_add_defects(ls_ctx* ctx, const ls_defect* defects, int64_t n);
  * A A^T unchanged) is orthogonalised via its FP64 Gram matrix G: a pivoted
  * Cholesky G ~ L L^T keeps pivot columns until the remaining trace is below
  * 1e-4 eps^2 T (that remainder joins the discarded tail and the bound); the
- * k x k matrix H = L^T L is diagonalised by a two-stage Jacobi iteration
- * (FP32 rotations with the diagonal kept to about 48 bits, then FP64
- * re-projection and a second iteration to off-diagonal ratios of 1e-10);
- * the basis Y = A_w L U diag(1/lambda) is orthonormalised by CholeskyQR
- * (FP32 first factorisation, FP64 inverse-square-root series second).
+ * k x k matrix H = L^T L is diagonalised by a block Jacobi iteration (FP32
+ * rotations with the diagonal kept to about 48 bits) and an FP64-grade
+ * re-projection H' = U^T H U: on LS_MIXED contexts the iteration stops at an
+ * off-diagonal ratio of 1e-4 and the diagonal of H' gives the eigenvalues;
+ * with LS_FLAG_SVD_GRAM on an LS_FP64 context a second iteration on H' runs
+ * to off-diagonal ratios of 1e-10; the basis Y = A_w L U diag(1/lambda) is
+ * orthonormalised by CholeskyQR (first pass: the inverse-square-root series
+ * where Y Y^T is within 0.1 of I, else a Cholesky factorisation, FP32 in one
+ * CTA's shared memory while r fits there (about 238), FP64 on a cooperative
+ * grid above; second pass: the series in FP64-grade arithmetic).
  * r_l is the smallest rank whose discarded singular values satisfy
  * (sum_{k>r} s_k^2)^(1/2) <= eps (sum_k s_k^2)^(1/2). The projections
  * P_l = Z_l^T A_l and the core
