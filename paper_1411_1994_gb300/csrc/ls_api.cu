@@ -770,7 +770,8 @@ struct RedMode {
     double *G = nullptr, *L = nullptr, *pd = nullptr, *cand = nullptr, *H = nullptr, *V = nullptr, *snap = nullptr,
            *isl = nullptr, *w = nullptr, *vg = nullptr, *ytmp = nullptr, *Gz = nullptr, *Li = nullptr, *D2 = nullptr,
            *gate = nullptr;   // ||Y Y^T - I||_F before CholeskyQR (picks its first pass)
-    // two-stage shared-memory eigen-solver: U0 = I + F1, S = U0^T U0, SLi, Uo, T1 = H Uo, Hp = Uo^T T1, F2
+    // eigen-solver: U0 = I + F1 (first Jacobi run), S = U0^T U0, SLi, Uo, T1 = H Uo, Hp = Uo^T T1 (the
+    // FP64-grade re-projection), F2 (the second run, where one is taken)
     double *U0 = nullptr, *S = nullptr, *SLi = nullptr, *Uo = nullptr, *T1 = nullptr, *Hp = nullptr, *F2 = nullptr;
     int32_t *piv = nullptr, *perm = nullptr;
     int k = 0;
@@ -900,8 +901,8 @@ int red_after_pchol(RedState& R, JacobiJob* jj) {
         if (R.hs[l].flag == FLAG_TIMEOUT)
             return fail(ctx, LS_ERR_TIMEOUT, "rhosvd_reduce: pivoted Cholesky barrier timed out (mode %d)", l);
     CUS(cudaMemsetAsync(R.d_st, 0, 9 * sizeof(DevStatus), st));
-    // the two-stage FP32 Jacobi for every k up to this (the block form in shared memory or
-    // in one cooperative grid); beyond it the FP64 grid Jacobi
+    // the FP32 block Jacobi and its FP64-grade re-projection for every k up to this (the block
+    // form in shared memory or in one cooperative grid); beyond it the FP64 grid Jacobi
     const int kdf = 8192;
     const double* L[3];
     double* H[3];
