@@ -381,14 +381,16 @@ def step_flops(name, info, N):
     return None
 
 
-def traffic_record(step):
+def traffic_record(step, profiles_dir=None, sources_dir=None):
     """DRAM bytes per launch of the step's kernel from the committed ncu summary under profiles/
     (a `traffic_record:` line: step | kernel | sources | sha256 of the sources | bytes), taken only
     while the sources hash as they did when the counters were captured; else None."""
     import glob
     import hashlib
     here = os.path.dirname(os.path.abspath(__file__))
-    for path in sorted(glob.glob(os.path.join(here, "profiles", "*.md"))):
+    profiles_dir = profiles_dir or os.path.join(here, "profiles")
+    sources_dir = sources_dir or os.path.join(here, "paper_1411_1994_gb300", "csrc")
+    for path in sorted(glob.glob(os.path.join(profiles_dir, "*.md"))):
         for line in open(path):
             if not line.startswith("traffic_record:"):
                 continue
@@ -397,7 +399,7 @@ def traffic_record(step):
                 continue
             h = hashlib.sha256()
             for f in parts[2].split("+"):
-                src = os.path.join(here, "paper_1411_1994_gb300", "csrc", f)
+                src = os.path.join(sources_dir, f)
                 if not os.path.exists(src):
                     return None
                 h.update(open(src, "rb").read())
